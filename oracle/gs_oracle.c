@@ -1,0 +1,659 @@
+/*
+ * FP64 CPU oracle of the differentiable tile-based Gaussian splatting
+ * rasterizer that the joint pose and primitive optimisation runs every
+ * iteration (Sec. 4.3; the paper builds on the 3DGS image-formation model,
+ * Sec. 5, and states no rasterizer equations, so each step below is that model
+ * written out as mathematics).
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the product path may call, link or load
+ * this file: only the tests, the smoke check and the CPU-baseline leg of the
+ * benchmark use it. It shares no code, header, constant or table with the CUDA
+ * library; the two meet only in the seeded inputs they both consume.
+ *
+ * Readings taken where the paper is silent (all configurable through `cfg`):
+ *   near-plane cull z <= near; screen-space dilation Sigma2D + dil*I with the
+ *   opacity unchanged; Jacobian guard band |x/z| <= 1.3 (W/2)/fx (and for y);
+ *   3-sigma radius from the largest eigenvalue with the 0.1 floor; tile rect
+ *   [floor((u-r)/T), floor((u+r+T-1)/T)) clamped to the grid; pixel (i, j)
+ *   sampled at (i+0.5, j+0.5); alpha = min(alpha_max, o*exp(power)), skipped if
+ *   alpha < alpha_min or power > 0; compositing stops before the Gaussian that
+ *   would take T below t_min; orthonormal real SH with the Condon-Shortley
+ *   phase; colour = SH + 0.5 clamped at 0; dalpha/d(o*g) = 0 where alpha is
+ *   clamped; pose gradient for a left perturbation T_cw <- exp(xi^) T_cw,
+ *   xi = (rho, phi), without the SH view-direction path unless enabled.
+ *
+ * Every discrete decision records its margin. Items whose margin is below the
+ * configured relative threshold are flagged ambiguous so tests can exclude
+ * them: FP32 arithmetic on the GPU may legitimately take the other branch.
+ *
+ * cam[18] = R(9, row-major world->camera), t(3), fx, fy, cx, cy, width, height
+ * cfg[16] = tile, sh_degree, near, dilation, alpha_min, alpha_max, t_min,
+ *           bg(3), pose_grad_through_sh, margin_geo, margin_alpha, margin_T,
+ *           (2 unused)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define PI_D 3.14159265358979323846
+
+typedef struct {
+    double R[9], t[3], fx, fy, cx, cy;
+    int W, H;
+} Cam;
+
+typedef struct {
+    int tile, sh_degree, pose_through_sh;
+    double near_z, dil, a_min, a_max, t_min, bg[3], m_geo, m_alpha, m_T;
+} Cfg;
+
+static Cam read_cam(const double* c) {
+    Cam k;
+    for (int i = 0; i < 9; i++) k.R[i] = c[i];
+    for (int i = 0; i < 3; i++) k.t[i] = c[9 + i];
+    k.fx = c[12]; k.fy = c[13]; k.cx = c[14]; k.cy = c[15];
+    k.W = (int)c[16]; k.H = (int)c[17];
+    return k;
+}
+
+static Cfg read_cfg(const double* c) {
+    Cfg g;
+    g.tile = (int)c[0]; g.sh_degree = (int)c[1];
+    g.near_z = c[2]; g.dil = c[3]; g.a_min = c[4]; g.a_max = c[5]; g.t_min = c[6];
+    g.bg[0] = c[7]; g.bg[1] = c[8]; g.bg[2] = c[9];
+    g.pose_through_sh = (int)c[10];
+    g.m_geo = c[11]; g.m_alpha = c[12]; g.m_T = c[13];
+    return g;
+}
+
+/* ---------------------------------------------------------------------------
+ * Small dense helpers (3x3 row-major)
+ * ------------------------------------------------------------------------- */
+static void mat3_mul(const double* A, const double* B, double* C) {
+    double T[9];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            double s = 0;
+            for (int k = 0; k < 3; k++) s += A[3 * i + k] * B[3 * k + j];
+            T[3 * i + j] = s;
+        }
+    memcpy(C, T, sizeof T);
+}
+static void mat3_T(const double* A, double* B) {
+    double T[9];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) T[3 * i + j] = A[3 * j + i];
+    memcpy(B, T, sizeof T);
+}
+
+/* rotation matrix of the unit quaternion (w, x, y, z) */
+static void quat_to_rot(const double* q, double* R) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+static double dist_to_int(double v) { return fabs(v - nearbyint(v)); }
+
+/* ---------------------------------------------------------------------------
+ * Real spherical harmonics with the Condon-Shortley phase, degree <= 3.
+ *
+ * For a unit direction d = (x, y, z):
+ *   Y_l^0  = K_l^0 q_l^0(z)
+ *   Y_l^m  = sqrt(2) K_l^m q_l^m(z) Re((x + i y)^m)      m > 0
+ *   Y_l^-m = sqrt(2) K_l^m q_l^m(z) Im((x + i y)^m)      m > 0
+ * where q_l^m(z) = P_l^m(z) / (1 - z^2)^(m/2) (associated Legendre function
+ * with the phase (-1)^m, divided by sin^m theta; a polynomial in z) and
+ * K_l^m = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!). Coefficient index k = l^2 + l + m.
+ * Evaluated on forward-mode dual numbers so the gradient w.r.t. d is exact.
+ * ------------------------------------------------------------------------- */
+typedef struct { double v, d[3]; } Dual;
+
+static Dual dconst(double c) { Dual r = {c, {0, 0, 0}}; return r; }
+static Dual dvar(double c, int i) { Dual r = {c, {0, 0, 0}}; r.d[i] = 1; return r; }
+static Dual dadd(Dual a, Dual b) { Dual r; r.v = a.v + b.v; for (int i = 0; i < 3; i++) r.d[i] = a.d[i] + b.d[i]; return r; }
+static Dual dsub(Dual a, Dual b) { Dual r; r.v = a.v - b.v; for (int i = 0; i < 3; i++) r.d[i] = a.d[i] - b.d[i]; return r; }
+static Dual dmul(Dual a, Dual b) {
+    Dual r; r.v = a.v * b.v;
+    for (int i = 0; i < 3; i++) r.d[i] = a.d[i] * b.v + a.v * b.d[i];
+    return r;
+}
+static Dual dscale(Dual a, double s) { Dual r; r.v = a.v * s; for (int i = 0; i < 3; i++) r.d[i] = a.d[i] * s; return r; }
+
+static double factorial(int n) { double f = 1; for (int i = 2; i <= n; i++) f *= i; return f; }
+
+/* Y[16] values and dY[16][3] gradients w.r.t. (x, y, z) */
+void or_sh_basis(int degree, const double* dir, double* Y, double* dY) {
+    Dual x = dvar(dir[0], 0), y = dvar(dir[1], 1), z = dvar(dir[2], 2);
+    Dual A[4], B[4];            /* Re, Im of (x + i y)^m */
+    A[0] = dconst(1); B[0] = dconst(0);
+    for (int m = 1; m <= 3; m++) {
+        A[m] = dsub(dmul(x, A[m - 1]), dmul(y, B[m - 1]));
+        B[m] = dadd(dmul(x, B[m - 1]), dmul(y, A[m - 1]));
+    }
+    Dual q[4][4];               /* q[l][m] */
+    for (int m = 0; m <= 3; m++) {
+        double dfact = 1;       /* (2m-1)!! */
+        for (int k = 2 * m - 1; k > 1; k -= 2) dfact *= k;
+        q[m][m] = dconst(((m & 1) ? -1.0 : 1.0) * dfact);
+        if (m + 1 <= 3) q[m + 1][m] = dscale(dmul(z, q[m][m]), 2 * m + 1);
+        for (int l = m + 2; l <= 3; l++)
+            q[l][m] = dscale(dsub(dscale(dmul(z, q[l - 1][m]), 2 * l - 1),
+                                  dscale(q[l - 2][m], l + m - 1)), 1.0 / (l - m));
+    }
+    for (int k = 0; k < 16; k++) { Y[k] = 0; dY[3 * k] = dY[3 * k + 1] = dY[3 * k + 2] = 0; }
+    for (int l = 0; l <= degree; l++) {
+        for (int m = -l; m <= l; m++) {
+            int am = m < 0 ? -m : m;
+            double K = sqrt((2 * l + 1) / (4 * PI_D) * factorial(l - am) / factorial(l + am));
+            Dual val;
+            if (m == 0) val = dscale(q[l][0], K);
+            else if (m > 0) val = dscale(dmul(q[l][am], A[am]), sqrt(2.0) * K);
+            else val = dscale(dmul(q[l][am], B[am]), sqrt(2.0) * K);
+            int k = l * l + l + m;
+            Y[k] = val.v;
+            for (int i = 0; i < 3; i++) dY[3 * k + i] = val.d[i];
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Projection (EWA splatting + SH colour), one view.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int culled;
+    double p[3], qn[4], qlen, Rq[9], s[3], Sig[9], Sc[9], J[6], S2[4], det;
+    int clamp_x, clamp_y;
+    double dir[3], dlen, d[3], Y[16], dY[48], raw[3];
+} ProjState;
+
+static void project_one(int64_t i, const double* mean_opa, const double* scale, const double* quat,
+                        const double* sh, const Cam* k, const Cfg* g, ProjState* st,
+                        double* mean2d, double* conic, double* opac, double* rgb, double* depth,
+                        int32_t* rect, uint8_t* clampm, uint8_t* amb) {
+    memset(st, 0, sizeof *st);
+    st->culled = 1;
+    double mu[3] = {mean_opa[4 * i], mean_opa[4 * i + 1], mean_opa[4 * i + 2]};
+    double logit = mean_opa[4 * i + 3];
+    for (int r = 0; r < 3; r++)
+        st->p[r] = k->R[3 * r] * mu[0] + k->R[3 * r + 1] * mu[1] + k->R[3 * r + 2] * mu[2] + k->t[r];
+    double x = st->p[0], y = st->p[1], z = st->p[2];
+    uint8_t a = 0;
+    if (fabs(z - g->near_z) < g->m_geo * fmax(1.0, fabs(z))) a |= 1;
+    for (int c = 0; c < 4; c++) rect[4 * i + c] = 0;
+    depth[i] = z;
+    if (amb) amb[i] = a;
+    if (!(z > g->near_z) || !isfinite(x) || !isfinite(y)) return;
+
+    double q[4] = {quat[4 * i], quat[4 * i + 1], quat[4 * i + 2], quat[4 * i + 3]};
+    st->qlen = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+    for (int c = 0; c < 4; c++) st->qn[c] = q[c] / st->qlen;
+    quat_to_rot(st->qn, st->Rq);
+    for (int c = 0; c < 3; c++) st->s[c] = exp(scale[4 * i + c]);
+    double M[9];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) M[3 * r + c] = st->Rq[3 * r + c] * st->s[c];
+    double MT[9];
+    mat3_T(M, MT);
+    mat3_mul(M, MT, st->Sig);
+    double RT[9], tmp[9];
+    mat3_T(k->R, RT);
+    mat3_mul(k->R, st->Sig, tmp);
+    mat3_mul(tmp, RT, st->Sc);
+
+    double limx = 1.3 * (k->W * 0.5) / k->fx, limy = 1.3 * (k->H * 0.5) / k->fy;
+    double xz = x / z, yz = y / z;
+    if (fabs(fabs(xz) - limx) < g->m_geo * limx) a |= 2;
+    if (fabs(fabs(yz) - limy) < g->m_geo * limy) a |= 2;
+    st->clamp_x = xz < -limx || xz > limx;
+    st->clamp_y = yz < -limy || yz > limy;
+    double cxz = xz < -limx ? -limx : (xz > limx ? limx : xz);
+    double cyz = yz < -limy ? -limy : (yz > limy ? limy : yz);
+    double* J = st->J;
+    J[0] = k->fx / z; J[1] = 0; J[2] = -k->fx * cxz / z;
+    J[3] = 0; J[4] = k->fy / z; J[5] = -k->fy * cyz / z;
+    /* S2 = J Sc J^T + dil I */
+    double JS[6];
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 3; c++)
+            JS[3 * r + c] = J[3 * r] * st->Sc[c] + J[3 * r + 1] * st->Sc[3 + c] + J[3 * r + 2] * st->Sc[6 + c];
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 2; c++)
+            st->S2[2 * r + c] = JS[3 * r] * J[3 * c] + JS[3 * r + 1] * J[3 * c + 1] + JS[3 * r + 2] * J[3 * c + 2];
+    st->S2[0] += g->dil;
+    st->S2[3] += g->dil;
+    double A = st->S2[0], Bc = st->S2[1], C = st->S2[3];
+    st->det = A * C - Bc * Bc;
+    if (fabs(st->det) < g->m_geo * A * C) a |= 1;
+    if (amb) amb[i] = a;
+    if (!(st->det > 0)) return;
+    double u = k->fx * x / z + k->cx, v = k->fy * y / z + k->cy;
+    double mid = 0.5 * (A + C);
+    double lam = mid + sqrt(fmax(0.1, mid * mid - st->det));
+    double q3 = 3.0 * sqrt(lam);
+    if (dist_to_int(q3) < g->m_geo * fmax(1.0, q3)) a |= 1;
+    double r = ceil(q3);
+    int T = g->tile;
+    int tx = (k->W + T - 1) / T, ty = (k->H + T - 1) / T;
+    double e[4] = {(u - r) / T, (v - r) / T, (u + r + T - 1) / T, (v + r + T - 1) / T};
+    for (int c = 0; c < 4; c++)
+        if (dist_to_int(e[c]) < g->m_geo * fmax(1.0, fabs(e[c]))) a |= 1;
+    double lim[4] = {tx, ty, tx, ty};
+    int rc[4];
+    for (int c = 0; c < 4; c++) {
+        double f = floor(e[c]);
+        if (f < 0) f = 0;
+        if (f > lim[c]) f = lim[c];
+        rc[c] = (int)f;
+    }
+    if (amb) amb[i] = a;
+    if (!isfinite(u) || !isfinite(v)) return;
+    if ((rc[2] - rc[0]) * (rc[3] - rc[1]) == 0) return;
+
+    /* colour from SH in the direction camera centre -> mean */
+    double cpos[3];
+    for (int c = 0; c < 3; c++) cpos[c] = -(RT[3 * c] * k->t[0] + RT[3 * c + 1] * k->t[1] + RT[3 * c + 2] * k->t[2]);
+    for (int c = 0; c < 3; c++) st->dir[c] = mu[c] - cpos[c];
+    st->dlen = sqrt(st->dir[0] * st->dir[0] + st->dir[1] * st->dir[1] + st->dir[2] * st->dir[2]);
+    for (int c = 0; c < 3; c++) st->d[c] = st->dir[c] / st->dlen;
+    or_sh_basis(g->sh_degree, st->d, st->Y, st->dY);
+    int ncoef = (g->sh_degree + 1) * (g->sh_degree + 1);
+    double col[3];
+    uint8_t cm = 0;
+    for (int ch = 0; ch < 3; ch++) {
+        double s = 0.5;
+        for (int kk = 0; kk < ncoef; kk++) s += st->Y[kk] * sh[48 * i + 3 * kk + ch];
+        st->raw[ch] = s;
+        if (fabs(s) < g->m_geo) a |= 2;
+        col[ch] = s > 0 ? s : 0;
+        if (s < 0) cm |= (uint8_t)(1 << ch);
+    }
+    double o = 1.0 / (1.0 + exp(-logit));
+    if (!isfinite(st->raw[0]) || !isfinite(st->raw[1]) || !isfinite(st->raw[2]) || !isfinite(o)) return;
+
+    st->culled = 0;
+    mean2d[2 * i] = u; mean2d[2 * i + 1] = v;
+    conic[3 * i] = C / st->det; conic[3 * i + 1] = -Bc / st->det; conic[3 * i + 2] = A / st->det;
+    opac[i] = o;
+    for (int ch = 0; ch < 3; ch++) rgb[3 * i + ch] = col[ch];
+    for (int c = 0; c < 4; c++) rect[4 * i + c] = rc[c];
+    if (clampm) clampm[i] = cm;
+    if (amb) amb[i] = a;
+}
+
+/* Returns the number of visible Gaussians. Outputs are per Gaussian; culled ones
+ * get n_tiles = 0 and an all-zero rect. depth_key is the depth rounded to fp32. */
+int64_t or_project(int64_t n, const double* mean_opa, const double* scale, const double* quat, const double* sh,
+                   const double* cam, const double* cfg, double* mean2d, double* conic, double* opac,
+                   double* rgb, double* depth, float* depth_key, int32_t* rect, int32_t* n_tiles,
+                   uint8_t* clampm, uint8_t* amb) {
+    Cam k = read_cam(cam);
+    Cfg g = read_cfg(cfg);
+    int64_t vis = 0;
+#pragma omp parallel for schedule(static) reduction(+ : vis)
+    for (int64_t i = 0; i < n; i++) {
+        ProjState st;
+        mean2d[2 * i] = mean2d[2 * i + 1] = 0;
+        conic[3 * i] = conic[3 * i + 1] = conic[3 * i + 2] = 0;
+        opac[i] = 0;
+        rgb[3 * i] = rgb[3 * i + 1] = rgb[3 * i + 2] = 0;
+        if (clampm) clampm[i] = 0;
+        project_one(i, mean_opa, scale, quat, sh, &k, &g, &st, mean2d, conic, opac, rgb, depth, rect, clampm, amb);
+        depth_key[i] = (float)depth[i];
+        n_tiles[i] = (rect[4 * i + 2] - rect[4 * i]) * (rect[4 * i + 3] - rect[4 * i + 1]);
+        vis += !st.culled;
+    }
+    return vis;
+}
+
+/* ---------------------------------------------------------------------------
+ * Per-tile lists: every (tile, Gaussian) pair whose rect holds the tile, each
+ * tile's list ordered by (fp32 depth bits, Gaussian id).
+ * ------------------------------------------------------------------------- */
+typedef struct { uint32_t key; int32_t id; } KeyId;
+
+static int cmp_keyid(const void* pa, const void* pb) {
+    const KeyId* a = (const KeyId*)pa;
+    const KeyId* b = (const KeyId*)pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return (a->id > b->id) - (a->id < b->id);
+}
+
+/* tile_start has tiles_x*tiles_y+1 entries. Returns the total pair count; fills
+ * ids only if it fits in capacity. */
+int64_t or_tile_lists(int64_t n, const int32_t* rect, const float* depth_key, int tiles_x, int tiles_y,
+                      int64_t* tile_start, int32_t* ids, int64_t capacity) {
+    int64_t nt = (int64_t)tiles_x * tiles_y;
+    for (int64_t t = 0; t <= nt; t++) tile_start[t] = 0;
+    for (int64_t i = 0; i < n; i++)
+        for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ty++)
+            for (int tx = rect[4 * i]; tx < rect[4 * i + 2]; tx++) tile_start[(int64_t)ty * tiles_x + tx + 1]++;
+    for (int64_t t = 0; t < nt; t++) tile_start[t + 1] += tile_start[t];
+    int64_t total = tile_start[nt];
+    if (total > capacity) return total;
+    int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (nt > 0 ? nt : 1));
+    for (int64_t t = 0; t < nt; t++) fill[t] = tile_start[t];
+    for (int64_t i = 0; i < n; i++)
+        for (int ty = rect[4 * i + 1]; ty < rect[4 * i + 3]; ty++)
+            for (int tx = rect[4 * i]; tx < rect[4 * i + 2]; tx++) ids[fill[(int64_t)ty * tiles_x + tx]++] = (int32_t)i;
+    free(fill);
+#pragma omp parallel
+    {
+        KeyId* buf = NULL;
+        int64_t cap = 0;
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t t = 0; t < nt; t++) {
+            int64_t b = tile_start[t], e = tile_start[t + 1];
+            if (e - b > cap) { cap = e - b; buf = (KeyId*)realloc(buf, sizeof(KeyId) * cap); }
+            for (int64_t j = b; j < e; j++) {
+                uint32_t bits;
+                memcpy(&bits, &depth_key[ids[j]], 4);
+                buf[j - b].key = bits;
+                buf[j - b].id = ids[j];
+            }
+            qsort(buf, (size_t)(e - b), sizeof(KeyId), cmp_keyid);
+            for (int64_t j = b; j < e; j++) ids[j] = buf[j - b].id;
+        }
+        free(buf);
+    }
+    return total;
+}
+
+/* ---------------------------------------------------------------------------
+ * Front-to-back alpha compositing, per pixel.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double alpha, T, g, og;  /* alpha, transmittance before it, exp(power), o*exp(power) */
+    int32_t id;
+    int clamped;
+} Contrib;
+
+/* Walks the pixel's list; records composited Gaussians into rec (if non-NULL).
+ * Returns the number composited; sets *n_contrib, *T_out, color. */
+static int composite_pixel(const Cfg* g, double px, double py, const int32_t* ids, int64_t len,
+                           const double* mean2d, const double* conic, const double* opac, const double* rgb,
+                           double* color, double* T_out, int32_t* n_contrib, uint8_t* amb, Contrib* rec) {
+    double T = 1.0, C[3] = {0, 0, 0};
+    int nrec = 0;
+    int32_t last = 0;
+    for (int64_t j = 0; j < len; j++) {
+        int32_t id = ids[j];
+        double dx = px - mean2d[2 * id], dy = py - mean2d[2 * id + 1];
+        double a = conic[3 * id], b = conic[3 * id + 1], c = conic[3 * id + 2];
+        double power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
+        if (power > 0) continue;
+        double G = exp(power);
+        double og = opac[id] * G;
+        if (fabs(og - g->a_max) < g->m_alpha * g->a_max) *amb = 1;
+        double alpha = og < g->a_max ? og : g->a_max;
+        if (fabs(alpha - g->a_min) < g->m_alpha * g->a_min) *amb = 1;
+        if (alpha < g->a_min) continue;
+        double testT = T * (1.0 - alpha);
+        if (fabs(testT - g->t_min) < g->m_T * g->t_min) *amb = 1;
+        if (testT < g->t_min) break;
+        for (int ch = 0; ch < 3; ch++) C[ch] += alpha * T * rgb[3 * id + ch];
+        if (rec) {
+            rec[nrec].alpha = alpha; rec[nrec].T = T; rec[nrec].g = G; rec[nrec].og = og;
+            rec[nrec].id = id; rec[nrec].clamped = !(og < g->a_max);
+        }
+        nrec++;
+        T = testT;
+        last = (int32_t)(j + 1);
+    }
+    for (int ch = 0; ch < 3; ch++) color[ch] = C[ch] + T * g->bg[ch];
+    *T_out = T;
+    *n_contrib = last;
+    return nrec;
+}
+
+void or_render_fwd(const double* cam, const double* cfg, const int64_t* tile_start, const int32_t* ids,
+                   const double* mean2d, const double* conic, const double* opac, const double* rgb,
+                   double* color, double* t_final, int32_t* n_contrib, uint8_t* amb_px) {
+    Cam k = read_cam(cam);
+    Cfg g = read_cfg(cfg);
+    int T = g.tile, tx = (k.W + T - 1) / T;
+    int64_t HW = (int64_t)k.W * k.H;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t pix = 0; pix < HW; pix++) {
+        int x = (int)(pix % k.W), y = (int)(pix / k.W);
+        int64_t t = (int64_t)(y / T) * tx + x / T;
+        double col[3], Tf;
+        int32_t nc;
+        uint8_t a = 0;
+        composite_pixel(&g, x + 0.5, y + 0.5, ids + tile_start[t], tile_start[t + 1] - tile_start[t], mean2d,
+                        conic, opac, rgb, col, &Tf, &nc, &a, NULL);
+        for (int ch = 0; ch < 3; ch++) color[ch * HW + pix] = col[ch];
+        t_final[pix] = Tf;
+        n_contrib[pix] = nc;
+        if (amb_px) amb_px[pix] = a;
+    }
+}
+
+/* Adjoint of the compositing, one view. For each pixel the forward is
+ * recomputed front to back with the transmittance before each Gaussian stored;
+ * with C = sum_i alpha_i T_i c_i + T_N bg,
+ *   dC/dc_i     = alpha_i T_i
+ *   dC/dalpha_i = T_i c_i - (sum_{j>i} alpha_j T_j c_j + T_N bg) / (1 - alpha_i).
+ * Then alpha = min(a_max, o g), g = exp(power),
+ * power = -(a dx^2 + c dy^2)/2 - b dx dy, d = pixel - mean2d.
+ * g2d[9*i] = dL/d(u, v, conic a, b, c, opacity, r, g, b) summed over pixels. */
+void or_render_bwd(const double* cam, const double* cfg, const int64_t* tile_start, const int32_t* ids,
+                   const double* mean2d, const double* conic, const double* opac, const double* rgb,
+                   const double* dL_dcolor, int64_t n, double* g2d) {
+    Cam k = read_cam(cam);
+    Cfg g = read_cfg(cfg);
+    int T = g.tile, tx = (k.W + T - 1) / T, ty = (k.H + T - 1) / T;
+    int64_t HW = (int64_t)k.W * k.H, nt = (int64_t)tx * ty;
+    int64_t P = tile_start[nt];
+    /* one partial per list entry so tiles can run in parallel; summed in list order below */
+    double* part = (double*)calloc((size_t)(P > 0 ? P : 1) * 9, sizeof(double));
+#pragma omp parallel
+    {
+        int64_t cap = 0;
+        Contrib* rec = NULL;
+#pragma omp for schedule(dynamic, 8)
+        for (int64_t t = 0; t < nt; t++) {
+            int64_t b0 = tile_start[t], len = tile_start[t + 1] - b0;
+            if (len > cap) { cap = len; rec = (Contrib*)realloc(rec, sizeof(Contrib) * cap); }
+            int x0 = (int)(t % tx) * T, y0 = (int)(t / tx) * T;
+            for (int y = y0; y < y0 + T && y < k.H; y++)
+                for (int x = x0; x < x0 + T && x < k.W; x++) {
+                    int64_t pix = (int64_t)y * k.W + x;
+                    double col[3], Tf, px = x + 0.5, py = y + 0.5;
+                    int32_t nc;
+                    uint8_t a = 0;
+                    int nr = composite_pixel(&g, px, py, ids + b0, len, mean2d, conic, opac, rgb, col, &Tf, &nc, &a, rec);
+                    double gC[3] = {dL_dcolor[pix], dL_dcolor[HW + pix], dL_dcolor[2 * HW + pix]};
+                    double total[3] = {0, 0, 0};
+                    for (int r = 0; r < nr; r++)
+                        for (int ch = 0; ch < 3; ch++) total[ch] += rec[r].alpha * rec[r].T * rgb[3 * rec[r].id + ch];
+                    double prefix[3] = {0, 0, 0};
+                    int r = 0;
+                    for (int64_t j = 0; j < len && r < nr; j++) {
+                        if (ids[b0 + j] != rec[r].id) continue;
+                        Contrib* c = &rec[r];
+                        int32_t id = c->id;
+                        double* pp = part + 9 * (b0 + j);
+                        double dalpha = 0;
+                        for (int ch = 0; ch < 3; ch++) {
+                            double ci = rgb[3 * id + ch];
+                            prefix[ch] += c->alpha * c->T * ci;
+                            double after = total[ch] - prefix[ch];
+                            pp[6 + ch] += c->alpha * c->T * gC[ch];
+                            dalpha += gC[ch] * (c->T * ci - (after + Tf * g.bg[ch]) / (1.0 - c->alpha));
+                        }
+                        if (!c->clamped) {
+                            double dpower = dalpha * c->og;
+                            double dx = px - mean2d[2 * id], dy = py - mean2d[2 * id + 1];
+                            double ca = conic[3 * id], cb = conic[3 * id + 1], cc = conic[3 * id + 2];
+                            /* dpower/du = a dx + b dy, dpower/dv = b dx + c dy (d = pixel - mean) */
+                            pp[0] += dpower * (ca * dx + cb * dy);
+                            pp[1] += dpower * (cb * dx + cc * dy);
+                            pp[2] += dpower * (-0.5 * dx * dx);
+                            pp[3] += dpower * (-dx * dy);
+                            pp[4] += dpower * (-0.5 * dy * dy);
+                            pp[5] += dalpha * c->g;
+                        }
+                        r++;
+                    }
+                }
+        }
+        free(rec);
+    }
+    for (int64_t i = 0; i < 9 * n; i++) g2d[i] = 0;
+    for (int64_t j = 0; j < P; j++)
+        for (int c = 0; c < 9; c++) g2d[9 * (int64_t)ids[j] + c] += part[9 * j + c];
+    free(part);
+}
+
+/* ---------------------------------------------------------------------------
+ * Adjoint of the projection, one view: from g2d (per Gaussian, as written by
+ * or_render_bwd) to the parameter gradients and the camera pose gradient.
+ * Outputs are overwritten (culled Gaussians get zeros). g_pose[6] = dL/d(rho, phi)
+ * for T_cw <- exp(xi^) T_cw.
+ * ------------------------------------------------------------------------- */
+static void sym2_from(double a, double b, double c, double* M) { M[0] = a; M[1] = b; M[2] = b; M[3] = c; }
+
+void or_project_bwd(int64_t n, const double* mean_opa, const double* scale, const double* quat, const double* sh,
+                    const double* cam, const double* cfg, const double* g2d, double* g_mean, double* g_logit,
+                    double* g_logscale, double* g_quat, double* g_sh, double* g_pose) {
+    Cam k = read_cam(cam);
+    Cfg g = read_cfg(cfg);
+    double pose[6] = {0, 0, 0, 0, 0, 0};
+    int ncoef = (g.sh_degree + 1) * (g.sh_degree + 1);
+    for (int64_t i = 0; i < n; i++) {
+        ProjState st;
+        double m2[2], cn[3], op, col[3], dep;
+        int32_t rc[4];
+        for (int c = 0; c < 3; c++) g_mean[3 * i + c] = 0, g_logscale[3 * i + c] = 0;
+        for (int c = 0; c < 4; c++) g_quat[4 * i + c] = 0;
+        for (int c = 0; c < 48; c++) g_sh[48 * i + c] = 0;
+        g_logit[i] = 0;
+        /* project_one indexes its outputs by i; point it at local storage */
+        project_one(0, mean_opa + 4 * i, scale + 4 * i, quat + 4 * i, sh + 48 * i, &k, &g, &st, m2, cn, &op, col,
+                    &dep, rc, NULL, NULL);
+        if (st.culled) continue;
+        const double* G = g2d + 9 * i;
+        double x = st.p[0], y = st.p[1], z = st.p[2];
+
+        /* opacity */
+        g_logit[i] = G[5] * op * (1 - op);
+
+        /* colour: rgb = max(SH(d) + 0.5, 0) */
+        double graw[3];
+        for (int ch = 0; ch < 3; ch++) graw[ch] = st.raw[ch] > 0 ? G[6 + ch] : 0;
+        double gd[3] = {0, 0, 0};
+        for (int kk = 0; kk < ncoef; kk++)
+            for (int ch = 0; ch < 3; ch++) {
+                double shv = sh[48 * i + 3 * kk + ch];
+                g_sh[48 * i + 3 * kk + ch] = graw[ch] * st.Y[kk];
+                for (int c = 0; c < 3; c++) gd[c] += graw[ch] * shv * st.dY[3 * kk + c];
+            }
+        /* d = dir/|dir|: dL/ddir = (gd - d (d.gd)) / |dir| */
+        double dd = gd[0] * st.d[0] + gd[1] * st.d[1] + gd[2] * st.d[2];
+        double gdir[3];
+        for (int c = 0; c < 3; c++) gdir[c] = (gd[c] - st.d[c] * dd) / st.dlen;
+        for (int c = 0; c < 3; c++) g_mean[3 * i + c] += gdir[c];
+        if (g.pose_through_sh) {
+            /* dir = mu - centre, centre = -R^T t; left perturbation moves the centre by -R^T rho */
+            for (int r = 0; r < 3; r++)
+                pose[r] += k.R[3 * r] * gdir[0] + k.R[3 * r + 1] * gdir[1] + k.R[3 * r + 2] * gdir[2];
+        }
+
+        /* conic = S2^-1: dL/dS2 = -Q dL/dQ Q with the full symmetric dL/dQ */
+        double Q[4], GQ[4], GS[4], t4[4];
+        sym2_from(st.S2[3] / st.det, -st.S2[1] / st.det, st.S2[0] / st.det, Q);
+        sym2_from(G[2], 0.5 * G[3], G[4], GQ);
+        for (int r = 0; r < 2; r++)
+            for (int c = 0; c < 2; c++) t4[2 * r + c] = Q[2 * r] * GQ[c] + Q[2 * r + 1] * GQ[2 + c];
+        for (int r = 0; r < 2; r++)
+            for (int c = 0; c < 2; c++) GS[2 * r + c] = -(t4[2 * r] * Q[c] + t4[2 * r + 1] * Q[2 + c]);
+
+        /* S2 = J Sc J^T + dil I: dL/dSc = J^T GS J, dL/dJ = 2 GS J Sc */
+        const double* J = st.J;
+        double GSc[9], GJ[6], JSc[6];
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) {
+                double s = 0;
+                for (int a = 0; a < 2; a++)
+                    for (int b = 0; b < 2; b++) s += J[3 * a + r] * GS[2 * a + b] * J[3 * b + c];
+                GSc[3 * r + c] = s;
+            }
+        for (int r = 0; r < 2; r++)
+            for (int c = 0; c < 3; c++)
+                JSc[3 * r + c] = J[3 * r] * st.Sc[c] + J[3 * r + 1] * st.Sc[3 + c] + J[3 * r + 2] * st.Sc[6 + c];
+        for (int r = 0; r < 2; r++)
+            for (int c = 0; c < 3; c++) GJ[3 * r + c] = 2 * (GS[2 * r] * JSc[c] + GS[2 * r + 1] * JSc[3 + c]);
+
+        /* mean2d and J as functions of p = (x, y, z) */
+        double gp[3] = {0, 0, 0};
+        gp[0] += G[0] * k.fx / z;
+        gp[2] += -G[0] * k.fx * x / (z * z);
+        gp[1] += G[1] * k.fy / z;
+        gp[2] += -G[1] * k.fy * y / (z * z);
+        gp[2] += GJ[0] * (-k.fx / (z * z)) + GJ[4] * (-k.fy / (z * z));
+        if (st.clamp_x) {
+            double c = x / z < 0 ? -1.3 * (k.W * 0.5) / k.fx : 1.3 * (k.W * 0.5) / k.fx;
+            gp[2] += GJ[2] * (k.fx * c / (z * z));
+        } else {
+            gp[0] += GJ[2] * (-k.fx / (z * z));
+            gp[2] += GJ[2] * (2 * k.fx * x / (z * z * z));
+        }
+        if (st.clamp_y) {
+            double c = y / z < 0 ? -1.3 * (k.H * 0.5) / k.fy : 1.3 * (k.H * 0.5) / k.fy;
+            gp[2] += GJ[5] * (k.fy * c / (z * z));
+        } else {
+            gp[1] += GJ[5] * (-k.fy / (z * z));
+            gp[2] += GJ[5] * (2 * k.fy * y / (z * z * z));
+        }
+
+        /* Sc = R Sig R^T: dL/dSig = R^T GSc R */
+        double RT[9], t9[9], GSig[9];
+        mat3_T(k.R, RT);
+        mat3_mul(RT, GSc, t9);
+        mat3_mul(t9, k.R, GSig);
+        /* Sig = M M^T, M = Rq diag(s): dL/dM = 2 GSig M */
+        double M[9], GM[9];
+        for (int r = 0; r < 3; r++)
+            for (int c = 0; c < 3; c++) M[3 * r + c] = st.Rq[3 * r + c] * st.s[c];
+        mat3_mul(GSig, M, GM);
+        for (int c = 0; c < 9; c++) GM[c] *= 2;
+        double GRq[9];
+        for (int c = 0; c < 3; c++) {
+            double gs = 0;
+            for (int r = 0; r < 3; r++) {
+                gs += GM[3 * r + c] * st.Rq[3 * r + c];
+                GRq[3 * r + c] = GM[3 * r + c] * st.s[c];
+            }
+            g_logscale[3 * i + c] = gs * st.s[c];
+        }
+        /* rotation matrix of the normalised quaternion */
+        double w = st.qn[0], qx = st.qn[1], qy = st.qn[2], qz = st.qn[3];
+        double gq[4];
+        gq[0] = 2 * (-qz * GRq[1] + qy * GRq[2] + qz * GRq[3] - qx * GRq[5] - qy * GRq[6] + qx * GRq[7]);
+        gq[1] = 2 * (qy * GRq[1] + qz * GRq[2] + qy * GRq[3] - 2 * qx * GRq[4] - w * GRq[5] + qz * GRq[6] + w * GRq[7] - 2 * qx * GRq[8]);
+        gq[2] = 2 * (-2 * qy * GRq[0] + qx * GRq[1] + w * GRq[2] + qx * GRq[3] + qz * GRq[5] - w * GRq[6] + qz * GRq[7] - 2 * qy * GRq[8]);
+        gq[3] = 2 * (-2 * qz * GRq[0] - w * GRq[1] + qx * GRq[2] + w * GRq[3] - 2 * qz * GRq[4] + qy * GRq[5] + qx * GRq[6] + qy * GRq[7]);
+        double qd = gq[0] * st.qn[0] + gq[1] * st.qn[1] + gq[2] * st.qn[2] + gq[3] * st.qn[3];
+        for (int c = 0; c < 4; c++) g_quat[4 * i + c] = (gq[c] - st.qn[c] * qd) / st.qlen;
+
+        /* p = R mu + t */
+        for (int c = 0; c < 3; c++) g_mean[3 * i + c] += RT[3 * c] * gp[0] + RT[3 * c + 1] * gp[1] + RT[3 * c + 2] * gp[2];
+
+        /* pose, left perturbation: dp = rho + phi x p, dSc = phi^ Sc - Sc phi^ */
+        pose[0] += gp[0]; pose[1] += gp[1]; pose[2] += gp[2];
+        pose[3] += st.p[1] * gp[2] - st.p[2] * gp[1];
+        pose[4] += st.p[2] * gp[0] - st.p[0] * gp[2];
+        pose[5] += st.p[0] * gp[1] - st.p[1] * gp[0];
+        double A1[9], A2[9], Mx[9];
+        mat3_mul(st.Sc, GSc, A1);
+        mat3_mul(GSc, st.Sc, A2);
+        for (int c = 0; c < 9; c++) Mx[c] = A1[c] - A2[c];
+        pose[3] += Mx[5] - Mx[7];
+        pose[4] += Mx[6] - Mx[2];
+        pose[5] += Mx[1] - Mx[3];
+    }
+    for (int c = 0; c < 6; c++) g_pose[c] = pose[c];
+}

@@ -1,0 +1,234 @@
+"""Seeded synthetic inputs shared by the CUDA path, the tests and the bench.
+
+This module draws numbers only. It holds none of the rasterizer's arithmetic
+(no projection, no SH evaluation, no compositing), so the FP64 oracle and the
+CUDA path can both consume its arrays without sharing any method code.
+
+The scene shapes follow the paper's captures (Sec. 5): ordered camera paths,
+images 1200-1920 px wide, about one million small, roughly isotropic
+primitives of the kind direct sampling produces (Sec. 4.2, Sec. 6.3).
+
+Layout of a Gaussian set (float32, structure of arrays):
+  mean_opa [N, 4]  world position x, y, z and the opacity logit
+  scale    [N, 4]  log-scales along the three principal axes, then 0
+  quat     [N, 4]  rotation quaternion (w, x, y, z), not normalised
+  sh       [N, 48] SH coefficients, coefficient-major: sh[g, 3*k + c]
+A camera is a dict with R (3x3 world-to-camera rotation, row-major), t (3),
+fx, fy, cx, cy, width, height. The camera looks down +z.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+# Standard deviation of the SH DC coefficient that spreads colours by about
+# 0.2 around mid-grey (colour = 0.5 + 0.282 * DC for degree-0 SH).
+DC_STD = 0.709
+
+
+@dataclass
+class Scene:
+    mean_opa: np.ndarray
+    scale: np.ndarray
+    quat: np.ndarray
+    sh: np.ndarray
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.mean_opa.shape[0])
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def gaussians(rng: np.random.Generator, n: int, lo, hi, log_scale_mu: float,
+              log_scale_sd: float, sh_degree: int, band_sd: float = 0.05) -> Scene:
+    """Gaussians with means uniform in the box [lo, hi]."""
+    lo = np.asarray(lo, np.float64)
+    hi = np.asarray(hi, np.float64)
+    mean = lo + (hi - lo) * rng.random((n, 3))
+    logit = rng.standard_normal(n)
+    mean_opa = np.concatenate([mean, logit[:, None]], 1).astype(np.float32)
+    scale = np.zeros((n, 4), np.float32)
+    scale[:, :3] = rng.normal(log_scale_mu, log_scale_sd, (n, 3))
+    quat = rng.standard_normal((n, 4)).astype(np.float32)
+    sh = np.zeros((n, 48), np.float32)
+    sh[:, 0:3] = rng.normal(0.0, DC_STD, (n, 3))
+    n_coef = (sh_degree + 1) ** 2
+    if n_coef > 1:
+        sh[:, 3:3 * n_coef] = rng.normal(0.0, band_sd, (n, 3 * n_coef - 3))
+    return Scene(mean_opa, scale, quat, sh, sh_degree)
+
+
+def frustum_gaussians(rng, n, width, height, f, zmin, zmax, log_scale_mu,
+                      log_scale_sd, sh_degree) -> Scene:
+    """Gaussians uniform in depth and uniform across the image at that depth."""
+    z = zmin + (zmax - zmin) * rng.random(n)
+    x = (rng.random(n) - 0.5) * width * z / f
+    y = (rng.random(n) - 0.5) * height * z / f
+    sc = gaussians(rng, n, [0, 0, 0], [1, 1, 1], log_scale_mu, log_scale_sd, sh_degree)
+    sc.mean_opa[:, 0] = x
+    sc.mean_opa[:, 1] = y
+    sc.mean_opa[:, 2] = z
+    return sc
+
+
+def camera(R, t, f, width, height, fy=None, dtype=np.float32) -> dict:
+    """Pinhole camera with the principal point at the image centre. Stored in
+    float32 (the values both the CUDA path and the oracle consume) unless dtype
+    says otherwise."""
+    return dict(R=np.asarray(R, dtype).reshape(3, 3), t=np.asarray(t, dtype).reshape(3),
+                fx=float(f), fy=float(f if fy is None else fy), cx=width / 2.0, cy=height / 2.0,
+                width=int(width), height=int(height))
+
+
+def _yaw(a: float) -> np.ndarray:
+    c, s = math.cos(a), math.sin(a)
+    return np.array([[c, 0, s], [0, 1, 0], [-s, 0, c]], np.float64)
+
+
+def camera_path(rng, n_views, step_m=0.3, step_deg=5.0):
+    """Camera-to-world rotations and centres along a smooth random path.
+
+    Consecutive frames are step_m apart and turn by step_deg about the vertical
+    axis; the turn direction changes sign with probability 0.25 per frame so the
+    path wiggles but stays smooth. Returns a list of (R_cw, centre).
+    """
+    yaw = 0.0
+    sign = 1.0 if rng.random() < 0.5 else -1.0
+    c = np.zeros(3)
+    out = []
+    for k in range(n_views):
+        out.append((_yaw(yaw), c.copy()))
+        if rng.random() < 0.25:
+            sign = -sign
+        yaw += sign * math.radians(step_deg) * 0.5
+        fwd = _yaw(yaw) @ np.array([0.0, 0.0, 1.0])
+        c = c + step_m * fwd
+        yaw += sign * math.radians(step_deg) * 0.5
+    # centre the path's yaw range on the box axis
+    mid = sum(math.atan2(r[0, 2], r[2, 2]) for r, _ in out) / n_views
+    back = _yaw(-mid)
+    return [(back @ r, back @ p) for r, p in out]
+
+
+def world_to_camera(R_cw: np.ndarray, centre: np.ndarray):
+    R = R_cw.T
+    t = -R @ centre
+    return R, t
+
+
+def perturb_pose(rng, R, t, rot_sd=0.01, trans_sd=0.01):
+    """Left-multiplies the world-to-camera pose by a random small rigid motion."""
+    w = rng.normal(0, rot_sd, 3)
+    th = float(np.linalg.norm(w))
+    K = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]])
+    if th > 0:
+        dR = np.eye(3) + math.sin(th) / th * K + (1 - math.cos(th)) / th ** 2 * K @ K
+    else:
+        dR = np.eye(3)
+    dt = rng.normal(0, trans_sd, 3)
+    return dR @ R, dR @ t + dt
+
+
+# ---------------------------------------------------------------------------
+# Named workloads
+# ---------------------------------------------------------------------------
+
+def tiny_scene(seed=1000, n=1000, width=64, height=64, f=80.0, sh_degree=0):
+    """Single 64x64 view, fx=fy=80, 1,000 Gaussians in the frustum at depth 2-6,
+    log-scales N(-3, 0.5), random quaternions, opacity sigmoid(N(0,1)), SH0."""
+    rng = _rng(seed)
+    sc = frustum_gaussians(rng, n, width, height, f, 2.0, 6.0, -3.0, 0.5, sh_degree)
+    cam = camera(np.eye(3), np.zeros(3), f, width, height)
+    return sc, cam, rng
+
+
+def view_720p_scene(seed=1001, n=200_000):
+    """Single 1280x720 view, fx=fy=1000, 200k Gaussians in a 20x10x30 m box in
+    front of the camera, log-scales N(-4, 0.7), SH degree 3."""
+    rng = _rng(seed)
+    sc = gaussians(rng, n, [-10, -5, 2], [10, 5, 32], -4.0, 0.7, 3)
+    cam = camera(np.eye(3), np.zeros(3), 1000.0, 1280, 720)
+    return sc, cam, rng
+
+
+def multiview_scene(seed=1002, n=1_000_000, n_views=8, sizes=None, f_per_width=1500.0 / 1920.0):
+    """n Gaussians (SH3) in a 30x15x50 m box and n_views cameras on a smooth path
+    (0.3 m and 5 degrees between frames). sizes: list of (width, height) per view
+    (default 1920x1080). The focal length keeps a 65-degree horizontal field of view."""
+    rng = _rng(seed)
+    sc = gaussians(rng, n, [-15, -7.5, 2], [15, 7.5, 52], -4.0, 0.7, 3)
+    if sizes is None:
+        sizes = [(1920, 1080)] * n_views
+    cams = []
+    for (R_cw, c), (w, h) in zip(camera_path(rng, n_views), sizes):
+        R, t = world_to_camera(R_cw, c)
+        cams.append(camera(R, t, f_per_width * w, w, h))
+    return sc, cams, rng
+
+
+UNEVEN_SIZES = [(640, 480), (1280, 720), (1600, 1200), (1920, 1080)]
+
+
+def uneven_sizes(rng, n_views):
+    idx = rng.integers(0, len(UNEVEN_SIZES), n_views)
+    return [UNEVEN_SIZES[i] for i in idx]
+
+
+def uneven_multiview_scene(seed=1003, n=2_000_000, n_views=16):
+    rng = _rng(seed + 7919)
+    sizes = uneven_sizes(rng, n_views)
+    return multiview_scene(seed, n, n_views, sizes)
+
+
+def image(rng, width, height, lo=0.0, hi=1.0):
+    return (lo + (hi - lo) * rng.random((3, height, width))).astype(np.float32)
+
+
+def scene_subset(sc: Scene, idx) -> Scene:
+    return Scene(sc.mean_opa[idx].copy(), sc.scale[idx].copy(), sc.quat[idx].copy(),
+                 sc.sh[idx].copy(), sc.sh_degree)
+
+
+def projected_items(rng, n_items, tiles_x, tiles_y, tile, max_rect=4, depth_levels=None):
+    """Synthetic projected splats for testing the sort and the compositing on their
+    own: random centres, conics, opacities, colours, depths and tile rects.
+
+    Returned arrays follow the projected-buffer layout (mean2d [n,2],
+    conic_opa [n,4], rgb_depth [n,4], rect [n,4] int32 tile bounds, n_tiles [n]).
+    depth_levels: if given, depths are drawn from that many discrete values so
+    that exact ties occur.
+    """
+    W, H = tiles_x * tile, tiles_y * tile
+    mean2d = np.stack([rng.random(n_items) * W, rng.random(n_items) * H], 1).astype(np.float32)
+    # conic from a random SPD 2x2 matrix with eigenvalues in [0.5, 30] px^2
+    ang = rng.random(n_items) * math.pi
+    l1 = np.exp(rng.uniform(math.log(0.5), math.log(30.0), n_items))
+    l2 = np.exp(rng.uniform(math.log(0.5), math.log(30.0), n_items))
+    c, s = np.cos(ang), np.sin(ang)
+    a = c * c / l1 + s * s / l2
+    b = c * s * (1 / l1 - 1 / l2)
+    d = s * s / l1 + c * c / l2
+    opa = 1.0 / (1.0 + np.exp(-rng.standard_normal(n_items)))
+    conic_opa = np.stack([a, b, d, opa], 1).astype(np.float32)
+    if depth_levels:
+        depth = (1.0 + rng.integers(0, depth_levels, n_items)).astype(np.float32)
+    else:
+        depth = rng.uniform(0.5, 50.0, n_items).astype(np.float32)
+    rgb = rng.random((n_items, 3)).astype(np.float32)
+    rgb_depth = np.concatenate([rgb, depth[:, None]], 1).astype(np.float32)
+    x0 = rng.integers(0, tiles_x, n_items)
+    y0 = rng.integers(0, tiles_y, n_items)
+    x1 = np.minimum(x0 + rng.integers(1, max_rect + 1, n_items), tiles_x)
+    y1 = np.minimum(y0 + rng.integers(1, max_rect + 1, n_items), tiles_y)
+    rect = np.stack([x0, y0, x1, y1], 1).astype(np.int32)
+    # a share of culled items (empty rect)
+    culled = rng.random(n_items) < 0.1
+    rect[culled] = 0
+    n_tiles = ((rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])).astype(np.int32)
+    return dict(mean2d=mean2d, conic_opa=conic_opa, rgb_depth=rgb_depth, rect=rect, n_tiles=n_tiles)
