@@ -1,0 +1,267 @@
+/*
+ * gs.h - C ABI of the GB300 (sm_103a) differentiable Gaussian splatting
+ * rasterizer: the hot path of the joint pose and primitive optimisation of
+ * "On-the-fly Reconstruction for Large-Scale Novel View Synthesis from Unposed
+ * Images" (Sec. 4.3), its direct spawn sampling (Sec. 4.2, Eq. 1-3) and the
+ * optimiser step that closes each iteration.
+ *
+ * The paper gives the problem (render the current Gaussians from the current
+ * poses, compare with the images, update poses and primitives; Sec. 4.3) and
+ * builds its rasterizer on the 3DGS image-formation model (Sec. 5). The entry
+ * points follow the stages of that model:
+ *   gs_project     EWA projection, screen bounds, SH colour      (per view x Gaussian)
+ *   gs_sort        per-tile duplication and depth ordering       (integer work)
+ *   gs_render_fwd  front-to-back alpha compositing               (per pixel)
+ *   gs_render_bwd  adjoint of the three stages above, including the camera
+ *                  pose gradient as an SE(3) tangent (Sec. 4.3: poses get
+ *                  gradients from Gaussian positions and rotations, not SH)
+ *   gs_adam_step / gs_pose_step   sparse Adam over visible Gaussians and the
+ *                  pose update (Sec. 4.3)
+ *   gs_l1_loss     L1 photometric loss and its gradient
+ *   gs_spawn_propose  direct spawn sampling (Sec. 4.2)
+ *
+ * Conventions shared by every call
+ *  - All tensor arguments are DEVICE pointers owned by the caller unless a
+ *    comment says "host". The library never allocates, frees or synchronises;
+ *    every call only enqueues kernels on `stream` (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream), so a sequence of calls can be
+ *    captured into a CUDA graph.
+ *  - float32 throughout. Layouts are structure-of-arrays with 16-byte rows.
+ *  - A view's camera looks down +z; pixel (i, j) is sampled at (i+0.5, j+0.5);
+ *    u = fx x/z + cx, v = fy y/z + cy.
+ *  - Return value: GS_OK, or GS_ERR_INVALID_ARG when a host-side check of
+ *    sizes/pointers fails (nothing is enqueued), or GS_ERR_CUDA when a launch
+ *    fails. Data-dependent failures (a pair buffer that is too small) are
+ *    reported through a device status word the caller reads after it syncs.
+ *  - Non-finite Gaussians are culled, never trapped.
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_OK 0
+#define GS_ERR_INVALID_ARG (-1)
+#define GS_ERR_CAPACITY (-2)
+#define GS_ERR_CUDA (-3)
+#define GS_ERR_TIMEOUT (-4)
+
+#define GS_MAX_VIEWS 64
+
+/* Pinhole camera, world -> camera: p = R mu + t (R row-major). 72 bytes. */
+typedef struct gs_camera {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t width, height;
+} gs_camera;
+
+/* Rasterizer settings (the paper states none of these; the values in the
+ * comments are the defaults of gs_config_default). */
+typedef struct gs_config {
+    int32_t tile;                 /* tile edge in pixels: 16 */
+    int32_t sh_degree;            /* 0..3 */
+    float near_z;                 /* cull if z <= near_z: 0.2 */
+    float dilation;               /* screen-space low-pass added to Sigma2D: 0.3 px^2 */
+    float alpha_min;              /* skip a Gaussian below this alpha: 1/255 */
+    float alpha_max;              /* alpha clamp: 0.99 */
+    float t_min;                  /* stop before T would fall below this: 1e-4 */
+    float bg[3];                  /* background colour: 0 */
+    int32_t pose_grad_through_sh; /* 1: pose gradient also through the SH view direction: 0 */
+    int32_t schedule;             /* render scheduling: 0 = one CTA per tile, 1 = persistent CTAs
+                                     pulling tiles, largest first, from a work queue */
+    int32_t accumulate;           /* gs_render_bwd / gs_project_bwd: 0 overwrite the gradient
+                                     buffers, 1 add to them (per-view launches of one step): 0 */
+    int32_t reserved;
+} gs_config;
+
+void gs_config_default(gs_config* cfg);
+
+/* Geometry of a batch of views rendered together (host struct, passed by
+ * pointer and copied by value into kernel parameters). Item index of
+ * (view v, Gaussian g) is v * n + g. Tiles of all views share one global tile
+ * index: tile_base[v] + ty * tiles_x[v] + tx. Pixels of view v start at
+ * pix_base[v] in every per-pixel buffer; colour buffers hold 3 planes per view
+ * ([3][height][width] starting at 3 * pix_base[v]). */
+typedef struct gs_frame {
+    int32_t n_views;
+    int32_t tile;
+    int32_t width[GS_MAX_VIEWS];
+    int32_t height[GS_MAX_VIEWS];
+    int32_t tiles_x[GS_MAX_VIEWS];
+    int32_t tiles_y[GS_MAX_VIEWS];
+    int32_t tile_base[GS_MAX_VIEWS + 1];
+    int64_t pix_base[GS_MAX_VIEWS + 1];
+} gs_frame;
+
+/* Fills f from host arrays width[n_views], height[n_views]. tile must be 16.
+ * Returns GS_ERR_INVALID_ARG for n_views outside 1..GS_MAX_VIEWS, a
+ * non-positive size or more than 2^31 tiles or pixels in total. */
+int gs_frame_init(gs_frame* f, int32_t n_views, const int32_t* width, const int32_t* height, int32_t tile);
+
+/* Gaussian parameters, structure of arrays, n Gaussians (paper Sec. 3: position,
+ * scale, rotation, opacity, SH):
+ *   mean_opa [n][4]  x, y, z, opacity logit (opacity = sigmoid)
+ *   scale    [n][4]  log-scales sx, sy, sz, unused
+ *   quat     [n][4]  w, x, y, z (normalised inside)
+ *   sh       [n][48] SH coefficient k (k = l^2 + l + m) of channel c at sh[48 g + 3 k + c]
+ * Each row must be 16-byte aligned. */
+typedef struct gs_gaussians {
+    float* mean_opa;
+    float* scale;
+    float* quat;
+    float* sh;
+    int64_t n;
+} gs_gaussians;
+
+/* Per (view, Gaussian) projection outputs, n_views * n items:
+ *   mean2d    [items][2]  u, v in pixels
+ *   conic_opa [items][4]  inverse 2D covariance (a, b, c) of [[a,b],[b,c]], opacity
+ *   rgb_depth [items][4]  colour (clamped at 0), camera-space depth z
+ *   rect      [items][4]  uint16 tile bounds x0, y0, x1, y1 (half-open)
+ *   n_tiles   [items]     (x1-x0)*(y1-y0); 0 marks a culled item */
+typedef struct gs_projected {
+    float* mean2d;
+    float* conic_opa;
+    float* rgb_depth;
+    uint16_t* rect;
+    int32_t* n_tiles;
+} gs_projected;
+
+/* EWA projection + SH colour for every (view, Gaussian) (3DGS model the paper
+ * builds on, Sec. 5; cull, dilation, guard band, radius and rect readings as
+ * documented in DESIGN). cams: device array of f->n_views cameras. */
+int gs_project(const gs_gaussians* g, const gs_camera* cams, const gs_frame* f, const gs_config* cfg,
+               const gs_projected* out, void* stream);
+
+/* Sorted (tile, Gaussian) pairs.
+ *   src     [capacity]  sorted pair -> item index (view * n + g)
+ *   emit    [capacity]  sorted pair -> emission slot; the pairs of one item
+ *                       occupy slots offset[item] .. offset[item]+n_tiles-1
+ *   offset  [n_views*n] first emission slot of each visible item
+ *   range   [2 * total tiles]  [start, end) of each tile's pairs in src/emit
+ *   count   device int64[1]: number of pairs (written by gs_sort)
+ *   status  device int32[1]: GS_OK, or GS_ERR_CAPACITY if count > capacity (then
+ *           only the first `capacity` pairs exist and renders are incomplete) */
+typedef struct gs_pairs {
+    uint32_t* src;
+    uint32_t* emit;
+    uint32_t* offset;
+    uint32_t* range;
+    int64_t capacity;
+    int64_t* count;
+    int32_t* status;
+} gs_pairs;
+
+/* Scratch bytes gs_sort needs for n Gaussians, the frame's views and a pair
+ * capacity. */
+size_t gs_sort_workspace_size(int64_t n, const gs_frame* f, int64_t capacity);
+
+/* Per-tile duplication and ordering. Visible items are first ordered by fp32
+ * depth (stable LSD radix sort, ties by item index), their pairs are emitted
+ * in that order, then a stable radix sort on the global tile index yields, per
+ * tile, the Gaussians in (depth bits, Gaussian id) order. ws: device scratch of
+ * at least gs_sort_workspace_size bytes, 256-byte aligned. */
+int gs_sort(const gs_projected* p, int64_t n, const gs_frame* f, const gs_pairs* out, void* ws, size_t ws_bytes,
+            void* stream);
+
+/* Forward image and the per-pixel state the adjoint needs.
+ *   color     [sum_v 3 * H_v * W_v]  planar RGB per view
+ *   t_final   [sum_v H_v * W_v]      final transmittance
+ *   n_contrib [sum_v H_v * W_v]      1 + list position of the last composited
+ *                                     Gaussian (0 if none) */
+typedef struct gs_image {
+    float* color;
+    float* t_final;
+    int32_t* n_contrib;
+} gs_image;
+
+/* Scratch bytes gs_render_fwd / gs_render_bwd need (work queue of the
+ * persistent schedule); 0 is valid when cfg->schedule == 0. */
+size_t gs_render_workspace_size(const gs_frame* f);
+
+/* Front-to-back alpha compositing (3DGS model): per pixel, over the tile's
+ * depth-ordered list, alpha = min(alpha_max, o exp(-d^T conic d / 2)), skipped
+ * below alpha_min, stopping before T would fall below t_min; colour =
+ * sum alpha T rgb + T_final bg. */
+int gs_render_fwd(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
+                  const gs_image* out, void* ws, size_t ws_bytes, void* stream);
+
+/* Gradients w.r.t. the Gaussian parameters, same layout as gs_gaussians.
+ * visible [n] = 1 if the Gaussian has at least one pair in any view. */
+typedef struct gs_grads {
+    float* mean_opa;
+    float* scale;
+    float* quat;
+    float* sh;
+    uint8_t* visible;
+} gs_grads;
+
+/* Scratch bytes gs_render_bwd needs for the pair capacity and n Gaussians. */
+size_t gs_backward_workspace_size(int64_t n, const gs_frame* f, int64_t capacity);
+
+/* Adjoint of project + sort + render_fwd for all views at once.
+ *   dL_dcolor  same layout as gs_image.color
+ *   grads      OVERWRITTEN with dL/d(parameters) summed over views
+ *   dL_dpose   [n_views][6] OVERWRITTEN: dL/dxi for the left perturbation
+ *              T_cw <- exp(xi^) T_cw, xi = (rho, phi) (translation first)
+ *   d_proj     optional [n_views*n][9], NULL to skip: dL/d(u, v, conic a, b,
+ *              c, opacity, r, g, b) per item (the 2D adjoint, for testing)
+ * Per tile the blending state is recomputed back to front from t_final and
+ * n_contrib; each (tile, Gaussian) pair gets one partial written to its
+ * emission slot and partials are summed per Gaussian in a fixed order: no
+ * atomics, bit-reproducible. */
+int gs_render_bwd(const gs_gaussians* g, const gs_camera* cams, const gs_projected* p, const gs_pairs* pairs,
+                  const gs_frame* f, const gs_config* cfg, const gs_image* fwd, const float* dL_dcolor,
+                  const gs_grads* grads, float* dL_dpose, float* d_proj, void* ws, size_t ws_bytes, void* stream);
+
+/* The two halves of gs_render_bwd, for callers that schedule or time them
+ * separately; they share the workspace (which must persist between them).
+ * gs_composite_bwd: per-tile adjoint of the compositing, one partial per
+ *   (tile, Gaussian) pair into the workspace.
+ * gs_project_bwd: per-Gaussian sum of those partials over all views and the
+ *   adjoint of the projection, pose gradient reduction.
+ * Arguments as for gs_render_bwd. */
+int gs_composite_bwd(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
+                     const gs_image* fwd, const float* dL_dcolor, int64_t n, void* ws, size_t ws_bytes,
+                     void* stream);
+int gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, const gs_projected* p, const gs_pairs* pairs,
+                   const gs_frame* f, const gs_config* cfg, const gs_grads* grads, float* dL_dpose, float* d_proj,
+                   void* ws, size_t ws_bytes, void* stream);
+
+/* Number of kernels this library has launched since it was loaded (host-side
+ * counter; diagnostics for benchmarks). */
+int64_t gs_launch_count(void);
+
+/* Learning rates of the parameter groups and the Adam constants. */
+typedef struct gs_adam_config {
+    float lr_mean, lr_opacity, lr_scale, lr_rot, lr_sh_dc, lr_sh_rest;
+    float beta1, beta2, eps;
+} gs_adam_config;
+
+/* Sparse Adam over Gaussians with visible[g] != 0 (others untouched); params,
+ * m, v in the gs_gaussians layout; step >= 1 (bias correction). */
+int gs_adam_step(const gs_gaussians* params, const gs_grads* grads, const gs_gaussians* m, const gs_gaussians* v,
+                 const gs_adam_config* cfg, int32_t step, void* stream);
+
+/* Pose update: Adam on the tangent gradient dL_dpose [n_views][6] with moments
+ * m, v [n_views][6], then T_cw <- exp(delta^) T_cw with delta the Adam step;
+ * cams updated in place. lr_t for rho, lr_r for phi. */
+int gs_pose_step(gs_camera* cams, int32_t n_views, const float* dL_dpose, float* m, float* v, float lr_t,
+                 float lr_r, float beta1, float beta2, float eps, int32_t step, void* stream);
+
+/* L1 loss: loss[0] = sum |color - target| / count (deterministic reduction),
+ * dL_dcolor = sign(color - target) / count. ws: 4 * 4096 bytes. */
+int gs_l1_loss(const float* color, const float* target, int64_t count, float* dL_dcolor, float* loss, void* ws,
+               size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

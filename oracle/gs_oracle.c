@@ -29,7 +29,10 @@
  * cam[18] = R(9, row-major world->camera), t(3), fx, fy, cx, cy, width, height
  * cfg[16] = tile, sh_degree, near, dilation, alpha_min, alpha_max, t_min,
  *           bg(3), pose_grad_through_sh, margin_geo, margin_alpha, margin_T,
- *           (2 unused)
+ *           margin_rect_px, (1 unused)
+ * margin_geo is relative (near plane, determinant, radius, guard band, colour
+ * clamp); margin_rect_px is the distance in pixels of a tile-rect edge from a
+ * tile boundary; margin_alpha and margin_T are relative.
  */
 #include <math.h>
 #include <stdint.h>
@@ -45,7 +48,7 @@ typedef struct {
 
 typedef struct {
     int tile, sh_degree, pose_through_sh;
-    double near_z, dil, a_min, a_max, t_min, bg[3], m_geo, m_alpha, m_T;
+    double near_z, dil, a_min, a_max, t_min, bg[3], m_geo, m_alpha, m_T, m_rect;
 } Cfg;
 
 static Cam read_cam(const double* c) {
@@ -63,7 +66,7 @@ static Cfg read_cfg(const double* c) {
     g.near_z = c[2]; g.dil = c[3]; g.a_min = c[4]; g.a_max = c[5]; g.t_min = c[6];
     g.bg[0] = c[7]; g.bg[1] = c[8]; g.bg[2] = c[9];
     g.pose_through_sh = (int)c[10];
-    g.m_geo = c[11]; g.m_alpha = c[12]; g.m_T = c[13];
+    g.m_geo = c[11]; g.m_alpha = c[12]; g.m_T = c[13]; g.m_rect = c[14];
     return g;
 }
 
@@ -238,9 +241,12 @@ static void project_one(int64_t i, const double* mean_opa, const double* scale, 
     int T = g->tile;
     int tx = (k->W + T - 1) / T, ty = (k->H + T - 1) / T;
     double e[4] = {(u - r) / T, (v - r) / T, (u + r + T - 1) / T, (v + r + T - 1) / T};
-    for (int c = 0; c < 4; c++)
-        if (dist_to_int(e[c]) < g->m_geo * fmax(1.0, fabs(e[c]))) a |= 1;
     double lim[4] = {tx, ty, tx, ty};
+    /* an edge near a tile boundary inside the grid may round either way in fp32 */
+    for (int c = 0; c < 4; c++) {
+        double k = nearbyint(e[c]);
+        if (k >= 1 && k <= lim[c] && dist_to_int(e[c]) * T < g->m_rect) a |= 1;
+    }
     int rc[4];
     for (int c = 0; c < 4; c++) {
         double f = floor(e[c]);

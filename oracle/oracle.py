@@ -62,11 +62,12 @@ class Config:
     margin_geo: float = 1e-5
     margin_alpha: float = 1e-5
     margin_T: float = 1e-4
+    margin_rect_px: float = 2e-3
 
     def array(self) -> np.ndarray:
         return np.array([self.tile, self.sh_degree, self.near_z, self.dilation, self.alpha_min,
                          self.alpha_max, self.t_min, *self.bg, self.pose_grad_through_sh,
-                         self.margin_geo, self.margin_alpha, self.margin_T, 0, 0], np.float64)
+                         self.margin_geo, self.margin_alpha, self.margin_T, self.margin_rect_px, 0], np.float64)
 
 
 def cam_array(cam: dict) -> np.ndarray:

@@ -1,0 +1,409 @@
+// Adjoint of the projection (K7) and the per-view pose reduction.
+//
+// One thread per Gaussian walks all views in a fixed order: it sums the
+// Gaussian's per-pair partials (contiguous emission slots, written by the
+// compositing adjoint), recomputes the projection for that view, applies the
+// chain rule to every parameter and accumulates over views in registers, so
+// each gradient row is written once, without atomics. Each view's pose
+// gradient is reduced per CTA in a fixed order and then across CTAs by
+// k_pose_reduce: the whole backward pass is deterministic.
+#include "common.cuh"
+#include "sh.cuh"
+
+namespace gs {
+
+constexpr int kPBThreads = 128;
+
+__device__ __forceinline__ void block_sum6(float (&x)[6], float* s_red /* [kPBThreads/32][6] */, float* out6) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 6; c++) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x[c] += __shfl_xor_sync(0xffffffffu, x[c], o);
+    }
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 6; c++) s_red[w * 6 + c] = x[c];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        float s = 0.f;
+        for (int k = 0; k < kPBThreads / 32; k++) s += s_red[k * 6 + threadIdx.x];
+        out6[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPBThreads) k_project_bwd(
+    const float4* __restrict__ mean_opa, const float4* __restrict__ scale, const float4* __restrict__ quat,
+    const float4* __restrict__ sh, int64_t n, const gs_camera* __restrict__ cams, gs_frame f, gs_config cfg,
+    const int32_t* __restrict__ n_tiles, const uint32_t* __restrict__ offset, const float4* __restrict__ part0,
+    const float4* __restrict__ part1, const float* __restrict__ part2, int64_t capacity,
+    float4* __restrict__ g_mean_opa, float4* __restrict__ g_scale, float4* __restrict__ g_quat,
+    float4* __restrict__ g_sh, uint8_t* __restrict__ visible, float* __restrict__ d_proj,
+    float* __restrict__ pose_part) {
+    __shared__ gs_camera s_cam[GS_MAX_VIEWS];
+    __shared__ float s_red[(kPBThreads / 32) * 6];
+    const int nv = f.n_views;
+    for (int i = threadIdx.x; i < nv * (int)(sizeof(gs_camera) / 4); i += kPBThreads)
+        reinterpret_cast<float*>(s_cam)[i] = reinterpret_cast<const float*>(cams)[i];
+    __syncthreads();
+    const int64_t g = (int64_t)blockIdx.x * kPBThreads + threadIdx.x;
+    const bool valid = g < n;
+    float4 mo = make_float4(0.f, 0.f, 0.f, 0.f), s4 = mo, q4 = make_float4(1.f, 0.f, 0.f, 0.f);
+    if (valid) { mo = mean_opa[g]; s4 = scale[g]; q4 = quat[g]; }
+    // parameter-space quantities shared by all views
+    const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
+    const float qi = rsqrtf(qn2);
+    const float qw = q4.x * qi, qx = q4.y * qi, qy = q4.z * qi, qz = q4.w * qi;
+    float Rq[9];
+    Rq[0] = 1.f - 2.f * (qy * qy + qz * qz); Rq[1] = 2.f * (qx * qy - qw * qz); Rq[2] = 2.f * (qx * qz + qw * qy);
+    Rq[3] = 2.f * (qx * qy + qw * qz); Rq[4] = 1.f - 2.f * (qx * qx + qz * qz); Rq[5] = 2.f * (qy * qz - qw * qx);
+    Rq[6] = 2.f * (qx * qz - qw * qy); Rq[7] = 2.f * (qy * qz + qw * qx); Rq[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    const float sv[3] = {expf(s4.x), expf(s4.y), expf(s4.z)};
+    const float opa = 1.f / (1.f + expf(-mo.w));
+    const int ncoef = (cfg.sh_degree + 1) * (cfg.sh_degree + 1);
+
+    float gm[3] = {0.f, 0.f, 0.f}, glogit = 0.f, gls[3] = {0.f, 0.f, 0.f}, gRq[9];
+#pragma unroll
+    for (int c = 0; c < 9; c++) gRq[c] = 0.f;
+    float gsh[48];
+#pragma unroll
+    for (int c = 0; c < 48; c++) gsh[c] = 0.f;
+    bool any_vis = false;
+
+    for (int v = 0; v < nv; v++) {
+        float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const int64_t item = (int64_t)v * n + g;
+        const int nt = valid ? n_tiles[item] : 0;
+        if (nt > 0) {
+            any_vis = true;
+            const gs_camera& c = s_cam[v];
+            // 1. sum this item's pair partials
+            const uint32_t off = offset[item];
+            float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
+            float a2 = 0.f;
+            for (int k = 0; k < nt; k++) {
+                const int64_t e = (int64_t)off + k;
+                if (e >= capacity) break;
+                const float4 p0 = part0[e], p1 = part1[e];
+                a0.x += p0.x; a0.y += p0.y; a0.z += p0.z; a0.w += p0.w;
+                a1.x += p1.x; a1.y += p1.y; a1.z += p1.z; a1.w += p1.w;
+                a2 += part2[e];
+            }
+            const float du = a0.x, dv = a0.y, dA = a0.z, dB = a0.w, dC = a1.x, dop = a1.y;
+            const float dr = a1.z, dg = a1.w, db = a2;
+            if (d_proj) {
+                float* o = d_proj + 9 * item;
+                o[0] = du; o[1] = dv; o[2] = dA; o[3] = dB; o[4] = dC; o[5] = dop; o[6] = dr; o[7] = dg; o[8] = db;
+            }
+            // 2. recompute the projection
+            const float x = c.R[0] * mo.x + c.R[1] * mo.y + c.R[2] * mo.z + c.t[0];
+            const float y = c.R[3] * mo.x + c.R[4] * mo.y + c.R[5] * mo.z + c.t[1];
+            const float z = c.R[6] * mo.x + c.R[7] * mo.y + c.R[8] * mo.z + c.t[2];
+            float RRq[9];  // R_cam * Rq
+#pragma unroll
+            for (int r = 0; r < 3; r++)
+#pragma unroll
+                for (int k = 0; k < 3; k++)
+                    RRq[3 * r + k] = c.R[3 * r] * Rq[k] + c.R[3 * r + 1] * Rq[3 + k] + c.R[3 * r + 2] * Rq[6 + k];
+            float T[9];
+#pragma unroll
+            for (int r = 0; r < 3; r++)
+#pragma unroll
+                for (int k = 0; k < 3; k++) T[3 * r + k] = RRq[3 * r + k] * sv[k];
+            const float limx = 1.3f * 0.5f * (float)c.width / c.fx;
+            const float limy = 1.3f * 0.5f * (float)c.height / c.fy;
+            const float iz = 1.f / z;
+            const float xz = x * iz, yz = y * iz;
+            const bool clx = xz < -limx || xz > limx, cly = yz < -limy || yz > limy;
+            const float txz = fminf(limx, fmaxf(-limx, xz)), tyz = fminf(limy, fmaxf(-limy, yz));
+            const float J00 = c.fx * iz, J02 = -c.fx * txz * iz, J11 = c.fy * iz, J12 = -c.fy * tyz * iz;
+            float M0[3], M1[3];  // rows of M = J T
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                M0[k] = J00 * T[k] + J02 * T[6 + k];
+                M1[k] = J11 * T[3 + k] + J12 * T[6 + k];
+            }
+            const float Sa = M0[0] * M0[0] + M0[1] * M0[1] + M0[2] * M0[2] + cfg.dilation;
+            const float Sb = M0[0] * M1[0] + M0[1] * M1[1] + M0[2] * M1[2];
+            const float Sc = M1[0] * M1[0] + M1[1] * M1[1] + M1[2] * M1[2] + cfg.dilation;
+            const float idet = 1.f / (Sa * Sc - Sb * Sb);
+            const float Qa = Sc * idet, Qb = -Sb * idet, Qc = Sa * idet;
+
+            // 3. opacity
+            glogit += dop * opa * (1.f - opa);
+
+            // 4. colour: rgb = max(0.5 + sum_k Y_k(d) sh_k, 0), d = (mu - centre)/|mu - centre|
+            const float ccx = -(c.R[0] * c.t[0] + c.R[3] * c.t[1] + c.R[6] * c.t[2]);
+            const float ccy = -(c.R[1] * c.t[0] + c.R[4] * c.t[1] + c.R[7] * c.t[2]);
+            const float ccz = -(c.R[2] * c.t[0] + c.R[5] * c.t[1] + c.R[8] * c.t[2]);
+            float ddx = mo.x - ccx, ddy = mo.y - ccy, ddz = mo.z - ccz;
+            const float il = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+            ddx *= il; ddy *= il; ddz *= il;
+            float Y[16];
+            sh_eval_basis(cfg.sh_degree, ddx, ddy, ddz, Y);
+            const float4* shg = sh + 12 * g;
+            float cf[48];
+#pragma unroll
+            for (int r = 0; r < 12; r++) {
+                if (4 * r < 3 * ncoef) {
+                    const float4 q = shg[r];
+                    cf[4 * r] = q.x; cf[4 * r + 1] = q.y; cf[4 * r + 2] = q.z; cf[4 * r + 3] = q.w;
+                } else {
+                    cf[4 * r] = cf[4 * r + 1] = cf[4 * r + 2] = cf[4 * r + 3] = 0.f;
+                }
+            }
+            float raw0 = 0.5f, raw1 = 0.5f, raw2 = 0.5f;
+#pragma unroll
+            for (int k = 0; k < 16; k++)
+                if (k < ncoef) {
+                    raw0 += Y[k] * cf[3 * k]; raw1 += Y[k] * cf[3 * k + 1]; raw2 += Y[k] * cf[3 * k + 2];
+                }
+            const float g0 = raw0 > 0.f ? dr : 0.f, g1 = raw1 > 0.f ? dg : 0.f, g2 = raw2 > 0.f ? db : 0.f;
+#pragma unroll
+            for (int k = 0; k < 16; k++)
+                if (k < ncoef) {
+                    gsh[3 * k] += g0 * Y[k]; gsh[3 * k + 1] += g1 * Y[k]; gsh[3 * k + 2] += g2 * Y[k];
+                }
+            if (cfg.sh_degree > 0) {
+                float3 dY[16];
+                sh_basis_grad(cfg.sh_degree, ddx, ddy, ddz, dY);
+                float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+#pragma unroll
+                for (int k = 1; k < 16; k++)
+                    if (k < ncoef) {
+                        const float s = g0 * cf[3 * k] + g1 * cf[3 * k + 1] + g2 * cf[3 * k + 2];
+                        gdx += s * dY[k].x; gdy += s * dY[k].y; gdz += s * dY[k].z;
+                    }
+                const float dd = gdx * ddx + gdy * ddy + gdz * ddz;
+                const float gx = (gdx - ddx * dd) * il, gy = (gdy - ddy * dd) * il, gz = (gdz - ddz * dd) * il;
+                gm[0] += gx; gm[1] += gy; gm[2] += gz;
+                if (cfg.pose_grad_through_sh) {
+                    // centre = -R^T t moves by -R^T rho under exp(xi^): dL/drho += R dL/ddir
+                    pose[0] += c.R[0] * gx + c.R[1] * gy + c.R[2] * gz;
+                    pose[1] += c.R[3] * gx + c.R[4] * gy + c.R[5] * gz;
+                    pose[2] += c.R[6] * gx + c.R[7] * gy + c.R[8] * gz;
+                }
+            }
+
+            // 5. conic = S^-1: dL/dS = -Q dL/dQ Q, dL/dQ = [[dA, dB/2], [dB/2, dC]]
+            const float hB = 0.5f * dB;
+            const float t00 = Qa * dA + Qb * hB, t01 = Qa * hB + Qb * dC;
+            const float t10 = Qb * dA + Qc * hB, t11 = Qb * hB + Qc * dC;
+            const float GS00 = -(t00 * Qa + t01 * Qb);
+            const float GS01 = -(t00 * Qb + t01 * Qc);
+            const float GS11 = -(t10 * Qb + t11 * Qc);
+            // 6. S = M M^T + dil I: dL/dM = 2 GS M
+            float GM0[3], GM1[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                GM0[k] = 2.f * (GS00 * M0[k] + GS01 * M1[k]);
+                GM1[k] = 2.f * (GS01 * M0[k] + GS11 * M1[k]);
+            }
+            // 7. M = J T: dL/dJ = GM T^T (entries J00, J02, J11, J12), dL/dT = J^T GM
+            const float GJ00 = GM0[0] * T[0] + GM0[1] * T[1] + GM0[2] * T[2];
+            const float GJ02 = GM0[0] * T[6] + GM0[1] * T[7] + GM0[2] * T[8];
+            const float GJ11 = GM1[0] * T[3] + GM1[1] * T[4] + GM1[2] * T[5];
+            const float GJ12 = GM1[0] * T[6] + GM1[1] * T[7] + GM1[2] * T[8];
+            float GT[9];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                GT[k] = J00 * GM0[k];
+                GT[3 + k] = J11 * GM1[k];
+                GT[6 + k] = J02 * GM0[k] + J12 * GM1[k];
+            }
+            // 8. T = R Rq diag(s): dL/d(Rq diag s) = R^T GT
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                float gsk = 0.f;
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+                    const float h = c.R[r] * GT[k] + c.R[3 + r] * GT[3 + k] + c.R[6 + r] * GT[6 + k];  // (R^T GT)[r][k]
+                    gsk += h * Rq[3 * r + k];
+                    gRq[3 * r + k] += h * sv[k];
+                }
+                gls[k] += gsk * sv[k];
+            }
+            // 9. p = (x, y, z): through the 2D mean and J
+            float gpx = du * c.fx * iz, gpy = dv * c.fy * iz;
+            float gpz = -(du * c.fx * x + dv * c.fy * y) * iz * iz;
+            gpz += -(GJ00 * c.fx + GJ11 * c.fy) * iz * iz;
+            if (clx) {
+                gpz += GJ02 * c.fx * txz * iz * iz;
+            } else {
+                gpx += -GJ02 * c.fx * iz * iz;
+                gpz += 2.f * GJ02 * c.fx * x * iz * iz * iz;
+            }
+            if (cly) {
+                gpz += GJ12 * c.fy * tyz * iz * iz;
+            } else {
+                gpy += -GJ12 * c.fy * iz * iz;
+                gpz += 2.f * GJ12 * c.fy * y * iz * iz * iz;
+            }
+            // mean: p = R mu + t
+            gm[0] += c.R[0] * gpx + c.R[3] * gpy + c.R[6] * gpz;
+            gm[1] += c.R[1] * gpx + c.R[4] * gpy + c.R[7] * gpz;
+            gm[2] += c.R[2] * gpx + c.R[5] * gpy + c.R[8] * gpz;
+            // 10. pose, left perturbation: dp = rho + phi x p, dT = phi^ T
+            pose[0] += gpx; pose[1] += gpy; pose[2] += gpz;
+            pose[3] += y * gpz - z * gpy;
+            pose[4] += z * gpx - x * gpz;
+            pose[5] += x * gpy - y * gpx;
+            // tr(T GT^T phi^): N = T GT^T, dphi = (N12 - N21, N20 - N02, N01 - N10)
+            float N01 = 0.f, N10 = 0.f, N02 = 0.f, N20 = 0.f, N12 = 0.f, N21 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                N01 += T[k] * GT[3 + k]; N10 += T[3 + k] * GT[k];
+                N02 += T[k] * GT[6 + k]; N20 += T[6 + k] * GT[k];
+                N12 += T[3 + k] * GT[6 + k]; N21 += T[6 + k] * GT[3 + k];
+            }
+            pose[3] += N12 - N21;
+            pose[4] += N20 - N02;
+            pose[5] += N01 - N10;
+        }
+        float out6[6];
+        block_sum6(pose, s_red, out6);
+        if (threadIdx.x < 6) pose_part[((int64_t)v * gridDim.x + blockIdx.x) * 6 + threadIdx.x] = out6[threadIdx.x];
+    }
+    if (!valid) return;
+    // quaternion: rotation-matrix gradient -> normalised quaternion -> raw quaternion
+    float gq[4];
+    gq[0] = 2.f * (-qz * gRq[1] + qy * gRq[2] + qz * gRq[3] - qx * gRq[5] - qy * gRq[6] + qx * gRq[7]);
+    gq[1] = 2.f * (qy * gRq[1] + qz * gRq[2] + qy * gRq[3] - 2.f * qx * gRq[4] - qw * gRq[5] + qz * gRq[6] +
+                   qw * gRq[7] - 2.f * qx * gRq[8]);
+    gq[2] = 2.f * (-2.f * qy * gRq[0] + qx * gRq[1] + qw * gRq[2] + qx * gRq[3] + qz * gRq[5] - qw * gRq[6] +
+                   qz * gRq[7] - 2.f * qy * gRq[8]);
+    gq[3] = 2.f * (-2.f * qz * gRq[0] - qw * gRq[1] + qx * gRq[2] + qw * gRq[3] - 2.f * qz * gRq[4] + qy * gRq[5] +
+                   qx * gRq[6] + qy * gRq[7]);
+    const float qd = gq[0] * qw + gq[1] * qx + gq[2] * qy + gq[3] * qz;
+    float4 o_mo = make_float4(gm[0], gm[1], gm[2], glogit);
+    float4 o_sc = make_float4(gls[0], gls[1], gls[2], 0.f);
+    float4 o_q = make_float4((gq[0] - qw * qd) * qi, (gq[1] - qx * qd) * qi, (gq[2] - qy * qd) * qi,
+                             (gq[3] - qz * qd) * qi);
+    float4* gs_row = g_sh + 12 * g;
+    if (cfg.accumulate) {
+        const float4 a = g_mean_opa[g], b = g_scale[g], c = g_quat[g];
+        o_mo.x += a.x; o_mo.y += a.y; o_mo.z += a.z; o_mo.w += a.w;
+        o_sc.x += b.x; o_sc.y += b.y; o_sc.z += b.z;
+        o_q.x += c.x; o_q.y += c.y; o_q.z += c.z; o_q.w += c.w;
+#pragma unroll
+        for (int r = 0; r < 12; r++) {
+            const float4 h = gs_row[r];
+            gsh[4 * r] += h.x; gsh[4 * r + 1] += h.y; gsh[4 * r + 2] += h.z; gsh[4 * r + 3] += h.w;
+        }
+        any_vis = any_vis || visible[g];
+    }
+    g_mean_opa[g] = o_mo;
+    g_scale[g] = o_sc;
+    g_quat[g] = o_q;
+#pragma unroll
+    for (int r = 0; r < 12; r++) gs_row[r] = make_float4(gsh[4 * r], gsh[4 * r + 1], gsh[4 * r + 2], gsh[4 * r + 3]);
+    visible[g] = any_vis ? 1 : 0;
+}
+
+// dL/dxi of view v = sum over CTAs of pose_part[v][b][6], fixed tree order.
+__global__ void __launch_bounds__(256) k_pose_reduce(const float* __restrict__ pose_part, int64_t nb,
+                                                     float* __restrict__ dL_dpose) {
+    __shared__ float s[256][6];
+    const int v = blockIdx.x;
+    float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int64_t b = threadIdx.x; b < nb; b += 256)
+#pragma unroll
+        for (int c = 0; c < 6; c++) acc[c] += pose_part[((int64_t)v * nb + b) * 6 + c];
+#pragma unroll
+    for (int c = 0; c < 6; c++) s[threadIdx.x][c] = acc[c];
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+#pragma unroll
+            for (int c = 0; c < 6; c++) s[threadIdx.x][c] += s[threadIdx.x + h][c];
+        __syncthreads();
+    }
+    if (threadIdx.x < 6) dL_dpose[v * 6 + threadIdx.x] = s[0][threadIdx.x];
+}
+
+int launch_render_bwd(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
+                      const gs_image* fwd, const float* dL_dcolor, float4* part0, float4* part1, float* part2,
+                      cudaStream_t s);
+
+struct BwdWs {
+    float4 *part0, *part1;
+    float *part2, *pose_part;
+};
+
+static BwdWs carve_bwd(char* base, size_t cap, int64_t n, int n_views, int64_t capacity, size_t* used) {
+    Carve c{base, 0, cap};
+    BwdWs w;
+    w.part0 = c.take<float4>(capacity);
+    w.part1 = c.take<float4>(capacity);
+    w.part2 = c.take<float>(capacity);
+    w.pose_part = c.take<float>((size_t)n_views * ceil_div(n, kPBThreads) * 6);
+    *used = c.used;
+    return w;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" size_t gs_backward_workspace_size(int64_t n, const gs_frame* f, int64_t capacity) {
+    if (!f || n < 0 || capacity < 0) return 0;
+    size_t used = 0;
+    carve_bwd(nullptr, 0, n, f->n_views, capacity, &used);
+    return used;
+}
+
+static int check_bwd_common(const gs_frame* f, const gs_config* cfg) {
+    if (!f || !cfg || f->n_views < 1 || f->n_views > GS_MAX_VIEWS || f->tile != 16 || cfg->tile != 16 ||
+        cfg->sh_degree < 0 || cfg->sh_degree > 3)
+        return GS_ERR_INVALID_ARG;
+    return GS_OK;
+}
+
+extern "C" int gs_composite_bwd(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f,
+                                const gs_config* cfg, const gs_image* fwd, const float* dL_dcolor, int64_t n,
+                                void* ws, size_t ws_bytes, void* stream) {
+    if (!p || !pairs || !fwd || !dL_dcolor || n < 0 || check_bwd_common(f, cfg) != GS_OK) return GS_ERR_INVALID_ARG;
+    size_t need = 0;
+    BwdWs w = carve_bwd((char*)ws, ws_bytes, n, f->n_views, pairs->capacity, &need);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) return GS_ERR_INVALID_ARG;
+    if (n == 0) return GS_OK;
+    return launch_render_bwd(p, pairs, f, cfg, fwd, dL_dcolor, w.part0, w.part1, w.part2, (cudaStream_t)stream);
+}
+
+extern "C" int gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, const gs_projected* p,
+                              const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg, const gs_grads* grads,
+                              float* dL_dpose, float* d_proj, void* ws, size_t ws_bytes, void* stream) {
+    if (!g || !cams || !p || !pairs || !grads || !dL_dpose || g->n < 0 || check_bwd_common(f, cfg) != GS_OK)
+        return GS_ERR_INVALID_ARG;
+    if (!grads->mean_opa || !grads->scale || !grads->quat || !grads->sh || !grads->visible) return GS_ERR_INVALID_ARG;
+    size_t need = 0;
+    BwdWs w = carve_bwd((char*)ws, ws_bytes, g->n, f->n_views, pairs->capacity, &need);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (g->n == 0) {
+        cudaMemsetAsync(dL_dpose, 0, sizeof(float) * 6 * f->n_views, s);
+        GS_CUDA_CHECK_LAUNCH();
+        return GS_OK;
+    }
+    const int64_t nb = ceil_div(g->n, kPBThreads);
+    k_project_bwd<<<(unsigned)nb, kPBThreads, 0, s>>>(
+        (const float4*)g->mean_opa, (const float4*)g->scale, (const float4*)g->quat, (const float4*)g->sh, g->n, cams,
+        *f, *cfg, p->n_tiles, pairs->offset, w.part0, w.part1, w.part2, pairs->capacity, (float4*)grads->mean_opa,
+        (float4*)grads->scale, (float4*)grads->quat, (float4*)grads->sh, grads->visible, d_proj, w.pose_part);
+    count_launch();
+    k_pose_reduce<<<f->n_views, 256, 0, s>>>(w.pose_part, nb, dL_dpose);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
+extern "C" int gs_render_bwd(const gs_gaussians* g, const gs_camera* cams, const gs_projected* p,
+                             const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg, const gs_image* fwd,
+                             const float* dL_dcolor, const gs_grads* grads, float* dL_dpose, float* d_proj, void* ws,
+                             size_t ws_bytes, void* stream) {
+    if (!g || !fwd || !dL_dcolor) return GS_ERR_INVALID_ARG;
+    int rc = gs_composite_bwd(p, pairs, f, cfg, fwd, dL_dcolor, g->n, ws, ws_bytes, stream);
+    if (rc != GS_OK) return rc;
+    return gs_project_bwd(g, cams, p, pairs, f, cfg, grads, dL_dpose, d_proj, ws, ws_bytes, stream);
+}

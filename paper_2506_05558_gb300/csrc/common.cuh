@@ -1,0 +1,79 @@
+// Internal helpers shared by the sm_103a kernels of libgs (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gs.h"
+
+#define GS_CUDA_CHECK_LAUNCH()                         \
+    do {                                               \
+        if (cudaPeekAtLastError() != cudaSuccess) {    \
+            (void)cudaGetLastError();                  \
+            return GS_ERR_CUDA;                        \
+        }                                              \
+    } while (0)
+
+namespace gs {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr int kWarp = 32;
+
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Global tile index -> view (binary search over the frame's tile bases).
+__device__ __forceinline__ int view_of_tile(const gs_frame& f, int tile) {
+    int lo = 0, hi = f.n_views - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (f.tile_base[mid] <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// 2^x on the MUFU unit (PTX ex2.approx, flush-to-zero for denormals).
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Host-side count of kernels this library has launched (diagnostics).
+void count_launch();
+
+// Bytes rounded up to 256 so carved sub-buffers stay aligned.
+__host__ __device__ inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+// Bump allocator over a caller-owned scratch buffer.
+struct Carve {
+    char* base;
+    size_t used;
+    size_t cap;
+    template <class T>
+    T* take(size_t count) {
+        size_t b = align256(count * sizeof(T));
+        T* p = reinterpret_cast<T*>(base ? base + used : nullptr);
+        used += b;
+        return p;
+    }
+    bool ok() const { return used <= cap; }
+};
+
+// Scratch bytes of the device-wide scan for up to n_max inputs.
+size_t scan_workspace_bytes(int64_t n_max);
+
+// Stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits
+// [0, bits), 8 bits per pass. The pair count is min(n_max, *n_dev). Buffers
+// (ka, va) hold the input; (kb, vb) are the alternates. Returns true when the
+// sorted result ends in (kb, vb). hist: 256 * radix_blocks(n_max) uint32.
+int64_t radix_blocks(int64_t n_max);
+bool radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, int64_t n_max,
+                      const uint32_t* n_dev, int bits, uint32_t* hist, void* scan_ws, cudaStream_t s);
+
+}  // namespace gs

@@ -1,0 +1,206 @@
+// Optimiser step of the joint optimisation (Sec. 4.3): sparse Adam over the
+// Gaussians visible in the step's views, Adam + SE(3) retraction for the
+// camera poses, and the L1 photometric loss with its gradient.
+#include "common.cuh"
+
+namespace gs {
+
+// One thread per 16-byte parameter row. Rows are laid out segment by segment
+// (mean_opa | scale | quat | sh) so every warp reads contiguous memory.
+__global__ void __launch_bounds__(256) k_adam(float4* __restrict__ p_mo, float4* __restrict__ p_sc,
+                                              float4* __restrict__ p_q, float4* __restrict__ p_sh,
+                                              const float4* __restrict__ g_mo, const float4* __restrict__ g_sc,
+                                              const float4* __restrict__ g_q, const float4* __restrict__ g_sh,
+                                              float4* __restrict__ m_mo, float4* __restrict__ m_sc,
+                                              float4* __restrict__ m_q, float4* __restrict__ m_sh,
+                                              float4* __restrict__ v_mo, float4* __restrict__ v_sc,
+                                              float4* __restrict__ v_q, float4* __restrict__ v_sh,
+                                              const uint8_t* __restrict__ visible, int64_t n, gs_adam_config c,
+                                              float bc1, float bc2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 15 * n) return;
+    int64_t g, row;
+    float4 *P, *M, *V;
+    const float4* G;
+    float4 lr;
+    if (i < n) {
+        g = i; row = i; P = p_mo; G = g_mo; M = m_mo; V = v_mo;
+        lr = make_float4(c.lr_mean, c.lr_mean, c.lr_mean, c.lr_opacity);
+    } else if (i < 2 * n) {
+        g = i - n; row = g; P = p_sc; G = g_sc; M = m_sc; V = v_sc;
+        lr = make_float4(c.lr_scale, c.lr_scale, c.lr_scale, 0.f);
+    } else if (i < 3 * n) {
+        g = i - 2 * n; row = g; P = p_q; G = g_q; M = m_q; V = v_q;
+        lr = make_float4(c.lr_rot, c.lr_rot, c.lr_rot, c.lr_rot);
+    } else {
+        row = i - 3 * n; g = row / 12; P = p_sh; G = g_sh; M = m_sh; V = v_sh;
+        lr = (row % 12 == 0) ? make_float4(c.lr_sh_dc, c.lr_sh_dc, c.lr_sh_dc, c.lr_sh_rest)
+                             : make_float4(c.lr_sh_rest, c.lr_sh_rest, c.lr_sh_rest, c.lr_sh_rest);
+    }
+    if (!visible[g]) return;
+    float4 p = P[row], gr = G[row], m = M[row], v = V[row];
+    float* pp = &p.x;
+    float* gg = &gr.x;
+    float* mm = &m.x;
+    float* vv = &v.x;
+    const float* ll = &lr.x;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        mm[k] = c.beta1 * mm[k] + (1.f - c.beta1) * gg[k];
+        vv[k] = c.beta2 * vv[k] + (1.f - c.beta2) * gg[k] * gg[k];
+        pp[k] -= ll[k] * (mm[k] / bc1) / (sqrtf(vv[k] / bc2) + c.eps);
+    }
+    P[row] = p;
+    M[row] = m;
+    V[row] = v;
+}
+
+// One thread per view: Adam on the 6-vector, then T_cw <- exp(delta^) T_cw.
+__global__ void k_pose_step(gs_camera* cams, int nv, const float* __restrict__ grad, float* m, float* v, float lr_t,
+                            float lr_r, float b1, float b2, float eps, float bc1, float bc2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    float d[6];
+    for (int k = 0; k < 6; k++) {
+        const float g = grad[6 * i + k];
+        const float mk = b1 * m[6 * i + k] + (1.f - b1) * g;
+        const float vk = b2 * v[6 * i + k] + (1.f - b2) * g * g;
+        m[6 * i + k] = mk;
+        v[6 * i + k] = vk;
+        d[k] = -(k < 3 ? lr_t : lr_r) * (mk / bc1) / (sqrtf(vk / bc2) + eps);
+    }
+    // exp of (rho, phi): R = I + A K + B K^2, t = (I + B K + C K^2) rho with
+    // A = sin(th)/th, B = (1 - cos th)/th^2, C = (th - sin th)/th^3
+    const float wx = d[3], wy = d[4], wz = d[5];
+    const float th2 = wx * wx + wy * wy + wz * wz;
+    const float th = sqrtf(th2);
+    float A, B, C;
+    if (th < 1e-4f) {
+        A = 1.f - th2 / 6.f;
+        B = 0.5f - th2 / 24.f;
+        C = 1.f / 6.f - th2 / 120.f;
+    } else {
+        A = sinf(th) / th;
+        B = (1.f - cosf(th)) / th2;
+        C = (th - sinf(th)) / (th2 * th);
+    }
+    const float K[9] = {0.f, -wz, wy, wz, 0.f, -wx, -wy, wx, 0.f};
+    float K2[9];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) K2[3 * r + c] = K[3 * r] * K[c] + K[3 * r + 1] * K[3 + c] + K[3 * r + 2] * K[6 + c];
+    float dR[9], Vm[9];
+    for (int k = 0; k < 9; k++) {
+        const float I = (k % 4 == 0) ? 1.f : 0.f;
+        dR[k] = I + A * K[k] + B * K2[k];
+        Vm[k] = I + B * K[k] + C * K2[k];
+    }
+    gs_camera& cam = cams[i];
+    float R[9], t[3];
+    for (int k = 0; k < 9; k++) R[k] = cam.R[k];
+    for (int k = 0; k < 3; k++) t[k] = cam.t[k];
+    for (int r = 0; r < 3; r++) {
+        for (int c = 0; c < 3; c++) cam.R[3 * r + c] = dR[3 * r] * R[c] + dR[3 * r + 1] * R[3 + c] + dR[3 * r + 2] * R[6 + c];
+        cam.t[r] = dR[3 * r] * t[0] + dR[3 * r + 1] * t[1] + dR[3 * r + 2] * t[2] + Vm[3 * r] * d[0] +
+                   Vm[3 * r + 1] * d[1] + Vm[3 * r + 2] * d[2];
+    }
+}
+
+constexpr int kLossThreads = 256;
+constexpr int kLossMaxBlocks = 4096;
+
+__global__ void __launch_bounds__(kLossThreads) k_l1(const float4* __restrict__ c4, const float4* __restrict__ t4,
+                                                     float4* __restrict__ g4, int64_t n4, const float* __restrict__ c,
+                                                     const float* __restrict__ t, float* __restrict__ gd, int64_t n,
+                                                     float inv_n, float* __restrict__ partial) {
+    __shared__ float s[kLossThreads / 32];
+    float acc = 0.f;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
+        const float4 a = c4[i], b = t4[i];
+        const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+        acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
+        auto sg = [](float x) { return x > 0.f ? 1.f : (x < 0.f ? -1.f : 0.f); };
+        g4[i] = make_float4(sg(d0) * inv_n, sg(d1) * inv_n, sg(d2) * inv_n, sg(d3) * inv_n);
+    }
+    // scalar tail
+    for (int64_t i = 4 * n4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float d = c[i] - t[i];
+        acc += fabsf(d);
+        gd[i] = (d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f)) * inv_n;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.f;
+        for (int k = 0; k < kLossThreads / 32; k++) b += s[k];
+        partial[blockIdx.x] = b;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_l1_final(const float* __restrict__ partial, int nb, float inv_n,
+                                                   float* __restrict__ loss) {
+    __shared__ float s[1024];
+    float a = 0.f;
+    for (int k = threadIdx.x; k < nb; k += 1024) a += partial[k];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int h = 512; h > 0; h >>= 1) {
+        if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = s[0] * inv_n;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" int gs_adam_step(const gs_gaussians* params, const gs_grads* grads, const gs_gaussians* m,
+                            const gs_gaussians* v, const gs_adam_config* cfg, int32_t step, void* stream) {
+    if (!params || !grads || !m || !v || !cfg || step < 1 || params->n < 0) return GS_ERR_INVALID_ARG;
+    if (m->n != params->n || v->n != params->n || !grads->visible) return GS_ERR_INVALID_ARG;
+    const int64_t n = params->n;
+    if (n == 0) return GS_OK;
+    const float bc1 = (float)(1.0 - pow((double)cfg->beta1, step));
+    const float bc2 = (float)(1.0 - pow((double)cfg->beta2, step));
+    k_adam<<<(unsigned)ceil_div(15 * n, 256), 256, 0, (cudaStream_t)stream>>>(
+        (float4*)params->mean_opa, (float4*)params->scale, (float4*)params->quat, (float4*)params->sh,
+        (const float4*)grads->mean_opa, (const float4*)grads->scale, (const float4*)grads->quat,
+        (const float4*)grads->sh, (float4*)m->mean_opa, (float4*)m->scale, (float4*)m->quat, (float4*)m->sh,
+        (float4*)v->mean_opa, (float4*)v->scale, (float4*)v->quat, (float4*)v->sh, grads->visible, n, *cfg, bc1, bc2);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
+extern "C" int gs_pose_step(gs_camera* cams, int32_t n_views, const float* dL_dpose, float* m, float* v, float lr_t,
+                            float lr_r, float beta1, float beta2, float eps, int32_t step, void* stream) {
+    if (!cams || !dL_dpose || !m || !v || n_views < 1 || n_views > GS_MAX_VIEWS || step < 1) return GS_ERR_INVALID_ARG;
+    const float bc1 = (float)(1.0 - pow((double)beta1, step));
+    const float bc2 = (float)(1.0 - pow((double)beta2, step));
+    k_pose_step<<<1, 64, 0, (cudaStream_t)stream>>>(cams, n_views, dL_dpose, m, v, lr_t, lr_r, beta1, beta2, eps, bc1,
+                                                    bc2);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
+extern "C" int gs_l1_loss(const float* color, const float* target, int64_t count, float* dL_dcolor, float* loss,
+                          void* ws, size_t ws_bytes, void* stream) {
+    if (!color || !target || !dL_dcolor || !loss || count < 1 || !ws || ws_bytes < 4 * kLossMaxBlocks)
+        return GS_ERR_INVALID_ARG;
+    const bool vec = (((uintptr_t)color | (uintptr_t)target | (uintptr_t)dL_dcolor) & 15) == 0;
+    const int64_t n4 = vec ? count / 4 : 0;
+    int64_t nb = ceil_div(count, kLossThreads * 8);
+    if (nb > kLossMaxBlocks) nb = kLossMaxBlocks;
+    const float inv_n = (float)(1.0 / (double)count);
+    cudaStream_t s = (cudaStream_t)stream;
+    k_l1<<<(unsigned)nb, kLossThreads, 0, s>>>((const float4*)color, (const float4*)target, (float4*)dL_dcolor, n4,
+                                                color, target, dL_dcolor, count, inv_n, (float*)ws);
+    count_launch();
+    k_l1_final<<<1, 1024, 0, s>>>((const float*)ws, (int)nb, inv_n, loss);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}

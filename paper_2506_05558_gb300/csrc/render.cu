@@ -1,0 +1,313 @@
+// Front-to-back alpha compositing (K5) and its adjoint (K6).
+//
+// One CTA of 256 threads per 16x16 tile, one pixel per thread; each warp owns
+// an 8x4 block of pixels so a small splat touches few warps. Each tile's
+// depth-ordered list is walked in batches staged in shared memory (128-bit
+// loads of the projected rows). The forward stops a CTA when every pixel's
+// transmittance has terminated (barrier count); the adjoint recomputes the
+// blending state back to front from T_final and n_contrib, reduces each
+// Gaussian's 9 partial derivatives across the warp with a transposing
+// butterfly (12 shuffles for 9 values), sums the 8 warps in a fixed order and
+// writes ONE partial per (tile, Gaussian) pair to the pair's emission slot. No
+// atomics touch gradients, so results are bit-reproducible.
+#include "common.cuh"
+
+namespace gs {
+
+constexpr int kTile = 16;
+constexpr int kThreads = 256;
+constexpr int kFwdBatch = 256;
+constexpr int kBwdBatch = 128;
+constexpr int kWarps = kThreads / 32;
+
+// Pixel of this thread inside the tile: warp w covers an 8x4 block.
+__device__ __forceinline__ void tile_pixel(int tid, int& lx, int& ly) {
+    const int lane = tid & 31, w = tid >> 5;
+    lx = (w & 1) * 8 + (lane & 7);
+    ly = (w >> 1) * 4 + (lane >> 3);
+}
+
+struct TileInfo {
+    int view, px, py, W, H;
+    bool inside;
+    int64_t pix;        // pixel index within all views
+    int64_t plane;      // H*W of the view
+    int64_t color_base; // 3 * pix_base[view]
+};
+
+__device__ __forceinline__ TileInfo tile_info(const gs_frame& f, int tile) {
+    TileInfo t;
+    t.view = view_of_tile(f, tile);
+    const int local = tile - f.tile_base[t.view];
+    const int tx = local % f.tiles_x[t.view], ty = local / f.tiles_x[t.view];
+    int lx, ly;
+    tile_pixel(threadIdx.x, lx, ly);
+    t.px = tx * kTile + lx;
+    t.py = ty * kTile + ly;
+    t.W = f.width[t.view];
+    t.H = f.height[t.view];
+    t.inside = t.px < t.W && t.py < t.H;
+    t.plane = (int64_t)t.W * t.H;
+    t.pix = f.pix_base[t.view] + (int64_t)t.py * t.W + t.px;
+    t.color_base = 3 * f.pix_base[t.view] + (int64_t)t.py * t.W + t.px;
+    return t;
+}
+
+// Staged form of a projected Gaussian: exponent coefficients in base 2,
+// e = A dx^2 + B dx dy + C dy^2 = -(a dx^2 + 2 b dx dy + c dy^2)/2 * log2(e).
+__device__ __forceinline__ void stage(const float2* __restrict__ mean2d, const float4* __restrict__ conic_opa,
+                                      const float4* __restrict__ rgb_depth, uint32_t idx, float2& xy, float4& abco,
+                                      float4& rgb) {
+    xy = mean2d[idx];
+    const float4 co = conic_opa[idx];
+    abco = make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, co.w);
+    rgb = rgb_depth[idx];
+}
+
+// Exponent (base 2) of the Gaussian at offset (dx, dy). The same rounding
+// sequence is used forward and backward so both take identical decisions.
+__device__ __forceinline__ float exponent2(const float4& abco, float dx, float dy) {
+    return __fmaf_rn(__fmul_rn(abco.x, dx), dx,
+                     __fmaf_rn(__fmul_rn(abco.z, dy), dy, __fmul_rn(__fmul_rn(abco.y, dx), dy)));
+}
+
+__global__ void __launch_bounds__(kThreads) k_render_fwd(gs_frame f, gs_config cfg, const uint32_t* __restrict__ range,
+                                                         const uint32_t* __restrict__ src,
+                                                         const float2* __restrict__ mean2d,
+                                                         const float4* __restrict__ conic_opa,
+                                                         const float4* __restrict__ rgb_depth,
+                                                         float* __restrict__ color, float* __restrict__ t_final,
+                                                         int32_t* __restrict__ n_contrib) {
+    __shared__ float2 s_xy[kFwdBatch];
+    __shared__ float4 s_abco[kFwdBatch];
+    __shared__ float4 s_rgb[kFwdBatch];
+    const int tile = blockIdx.x;
+    const TileInfo ti = tile_info(f, tile);
+    const float px = ti.px + 0.5f, py = ti.py + 0.5f;
+    const uint32_t start = range[2 * tile], end = range[2 * tile + 1];
+    float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
+    int last = 0;
+    bool done = !ti.inside;
+    for (uint32_t b0 = start; b0 < end; b0 += kFwdBatch) {
+        if (__syncthreads_count(done) == kThreads) break;
+        const uint32_t j = b0 + threadIdx.x;
+        if (j < end) stage(mean2d, conic_opa, rgb_depth, src[j], s_xy[threadIdx.x], s_abco[threadIdx.x],
+                           s_rgb[threadIdx.x]);
+        __syncthreads();
+        const int cnt = min((uint32_t)kFwdBatch, end - b0);
+        for (int k = 0; k < cnt && !done; k++) {
+            const float2 xy = s_xy[k];
+            const float4 abco = s_abco[k];
+            const float e = exponent2(abco, px - xy.x, py - xy.y);
+            if (e > 0.f) continue;
+            const float og = __fmul_rn(abco.w, fast_exp2(e));
+            const float alpha = fminf(cfg.alpha_max, og);
+            if (alpha < cfg.alpha_min) continue;
+            const float nT = __fmul_rn(T, 1.f - alpha);
+            if (nT < cfg.t_min) { done = true; break; }
+            const float4 c = s_rgb[k];
+            const float w = alpha * T;
+            cr += w * c.x; cg += w * c.y; cb += w * c.z;
+            T = nT;
+            last = (int)(b0 - start) + k + 1;
+        }
+    }
+    if (ti.inside) {
+        color[ti.color_base] = cr + T * cfg.bg[0];
+        color[ti.color_base + ti.plane] = cg + T * cfg.bg[1];
+        color[ti.color_base + 2 * ti.plane] = cb + T * cfg.bg[2];
+        t_final[ti.pix] = T;
+        n_contrib[ti.pix] = last;
+    }
+}
+
+// Warp-wide sum of 9 values by a transposing butterfly: after 5 exchange rounds
+// (5+3+2+1+1 shuffles) even lane L holds the full sum of value kOwner[L>>1].
+__device__ __constant__ int8_t kOwner[16] = {0, 1, 2, -1, 3, 4, -1, -1, 5, 6, 7, -1, 8, -1, -1, -1};
+
+__device__ __forceinline__ float warp_reduce9(const float (&v)[9], int lane) {
+    const unsigned F = 0xffffffffu;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float s[5];
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        const float lo = v[k];
+        const float hi = k < 4 ? v[5 + k] : 0.f;
+        const float send = b4 ? lo : hi;
+        const float keep = b4 ? hi : lo;
+        s[k] = keep + __shfl_xor_sync(F, send, 16);
+    }
+    float t[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float lo = s[k];
+        const float hi = k < 2 ? s[3 + k] : 0.f;
+        t[k] = (b3 ? hi : lo) + __shfl_xor_sync(F, b3 ? lo : hi, 8);
+    }
+    float u[2];
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const float lo = t[k];
+        const float hi = k < 1 ? t[2] : 0.f;
+        u[k] = (b2 ? hi : lo) + __shfl_xor_sync(F, b2 ? lo : hi, 4);
+    }
+    float w = (b1 ? u[1] : u[0]) + __shfl_xor_sync(F, b1 ? u[0] : u[1], 2);
+    w += __shfl_xor_sync(F, w, 1);
+    return w;
+}
+
+__global__ void __launch_bounds__(kThreads) k_render_bwd(gs_frame f, gs_config cfg, const uint32_t* __restrict__ range,
+                                                         const uint32_t* __restrict__ src,
+                                                         const uint32_t* __restrict__ emit,
+                                                         const float2* __restrict__ mean2d,
+                                                         const float4* __restrict__ conic_opa,
+                                                         const float4* __restrict__ rgb_depth,
+                                                         const float* __restrict__ t_final,
+                                                         const int32_t* __restrict__ n_contrib,
+                                                         const float* __restrict__ dL_dcolor,
+                                                         float4* __restrict__ part0, float4* __restrict__ part1,
+                                                         float* __restrict__ part2, int64_t capacity) {
+    __shared__ float2 s_xy[kBwdBatch];
+    __shared__ float4 s_abco[kBwdBatch];
+    __shared__ float4 s_rgb[kBwdBatch];
+    __shared__ uint32_t s_emit[kBwdBatch];
+    __shared__ float s_part[kWarps][kBwdBatch][9];
+    __shared__ int s_max;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int tile = blockIdx.x;
+    const TileInfo ti = tile_info(f, tile);
+    const float px = ti.px + 0.5f, py = ti.py + 0.5f;
+    const uint32_t start = range[2 * tile];
+    float Tf = 1.f, gr = 0.f, gg = 0.f, gb = 0.f;
+    int nc = 0;
+    if (ti.inside) {
+        Tf = t_final[ti.pix];
+        nc = n_contrib[ti.pix];
+        gr = dL_dcolor[ti.color_base];
+        gg = dL_dcolor[ti.color_base + ti.plane];
+        gb = dL_dcolor[ti.color_base + 2 * ti.plane];
+    }
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    atomicMax(&s_max, nc);
+    __syncthreads();
+    const int n_list = s_max;
+    // background seen through the final transmittance, folded into the "behind" term
+    const float bgr = Tf * cfg.bg[0], bgg = Tf * cfg.bg[1], bgb = Tf * cfg.bg[2];
+    float T = Tf, Sr = 0.f, Sg = 0.f, Sb = 0.f;
+    const int8_t owner = (lane & 1) ? (int8_t)-1 : kOwner[lane >> 1];
+    const float inv_log2e = 1.f / kLog2e;
+    for (int bend = n_list; bend > 0; bend -= kBwdBatch) {
+        const int b0 = max(0, bend - kBwdBatch);
+        const int cnt = bend - b0;
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            const uint32_t p = start + b0 + threadIdx.x;
+            stage(mean2d, conic_opa, rgb_depth, src[p], s_xy[threadIdx.x], s_abco[threadIdx.x], s_rgb[threadIdx.x]);
+            s_emit[threadIdx.x] = emit[p];
+        }
+        __syncthreads();
+        for (int k = cnt - 1; k >= 0; k--) {
+            float g[9];
+#pragma unroll
+            for (int c = 0; c < 9; c++) g[c] = 0.f;
+            bool contrib = false;
+            if (b0 + k < nc) {
+                const float2 xy = s_xy[k];
+                const float4 abco = s_abco[k];
+                const float dx = px - xy.x, dy = py - xy.y;
+                const float e = exponent2(abco, dx, dy);
+                if (!(e > 0.f)) {
+                    const float G = fast_exp2(e);
+                    const float og = __fmul_rn(abco.w, G);
+                    const float alpha = fminf(cfg.alpha_max, og);
+                    if (alpha >= cfg.alpha_min) {
+                        contrib = true;
+                        const float one_m = 1.f - alpha;
+                        T = T / one_m;  // transmittance in front of this Gaussian
+                        const float4 c = s_rgb[k];
+                        const float wgt = alpha * T;
+                        g[6] = wgt * gr; g[7] = wgt * gg; g[8] = wgt * gb;
+                        const float inv = 1.f / one_m;
+                        const float dalpha = gr * (T * c.x - (Sr + bgr) * inv) + gg * (T * c.y - (Sg + bgg) * inv) +
+                                             gb * (T * c.z - (Sb + bgb) * inv);
+                        Sr += wgt * c.x; Sg += wgt * c.y; Sb += wgt * c.z;
+                        if (og < cfg.alpha_max) {
+                            const float dpow = dalpha * og;  // d alpha / d(natural exponent) = o g
+                            const float q = -dpow * inv_log2e;  // (a dx + b dy) = -(2A dx + B dy)/log2(e)
+                            g[0] = q * (2.f * abco.x * dx + abco.y * dy);
+                            g[1] = q * (abco.y * dx + 2.f * abco.z * dy);
+                            g[2] = -0.5f * dpow * dx * dx;
+                            g[3] = -dpow * dx * dy;
+                            g[4] = -0.5f * dpow * dy * dy;
+                            g[5] = dalpha * G;
+                        }
+                    }
+                }
+            }
+            if (__any_sync(0xffffffffu, contrib)) {
+                const float r = warp_reduce9(g, lane);
+                if (owner >= 0) s_part[w][k][owner] = r;
+            } else if (lane < 9) {
+                s_part[w][k][lane] = 0.f;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < cnt) {
+            float a[9];
+#pragma unroll
+            for (int c = 0; c < 9; c++) a[c] = s_part[0][threadIdx.x][c];
+#pragma unroll
+            for (int ww = 1; ww < kWarps; ww++)
+#pragma unroll
+                for (int c = 0; c < 9; c++) a[c] += s_part[ww][threadIdx.x][c];
+            const uint32_t e = s_emit[threadIdx.x];
+            if ((int64_t)e < capacity) {
+                part0[e] = make_float4(a[0], a[1], a[2], a[3]);
+                part1[e] = make_float4(a[4], a[5], a[6], a[7]);
+                part2[e] = a[8];
+            }
+        }
+    }
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" size_t gs_render_workspace_size(const gs_frame* f) {
+    (void)f;
+    return 0;
+}
+
+extern "C" int gs_render_fwd(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
+                             const gs_image* out, void* ws, size_t ws_bytes, void* stream) {
+    (void)ws;
+    (void)ws_bytes;
+    if (!p || !pairs || !f || !cfg || !out || !out->color || !out->t_final || !out->n_contrib) return GS_ERR_INVALID_ARG;
+    if (f->tile != kTile || cfg->tile != kTile || f->n_views < 1 || f->n_views > GS_MAX_VIEWS) return GS_ERR_INVALID_ARG;
+    const int n_tiles = f->tile_base[f->n_views];
+    if (n_tiles == 0) return GS_OK;
+    k_render_fwd<<<n_tiles, kThreads, 0, (cudaStream_t)stream>>>(
+        *f, *cfg, pairs->range, pairs->src, (const float2*)p->mean2d, (const float4*)p->conic_opa,
+        (const float4*)p->rgb_depth, out->color, out->t_final, out->n_contrib);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
+namespace gs {
+int launch_render_bwd(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
+                      const gs_image* fwd, const float* dL_dcolor, float4* part0, float4* part1, float* part2,
+                      cudaStream_t s) {
+    const int n_tiles = f->tile_base[f->n_views];
+    if (n_tiles == 0) return GS_OK;
+    k_render_bwd<<<n_tiles, kThreads, 0, s>>>(*f, *cfg, pairs->range, pairs->src, pairs->emit,
+                                              (const float2*)p->mean2d, (const float4*)p->conic_opa,
+                                              (const float4*)p->rgb_depth, fwd->t_final, fwd->n_contrib, dL_dcolor,
+                                              part0, part1, part2, pairs->capacity);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+}  // namespace gs

@@ -1,0 +1,382 @@
+"""Thin Python binding of libgs (include/gs.h): argument marshalling only.
+
+Every step of the hot path runs in the library's sm_103a kernels. PyTorch
+supplies device memory and the current CUDA stream; the structures below mirror
+the C structs byte for byte. If the compiled library is missing, `lib()`
+raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libgs.so")
+
+GS_OK = 0
+GS_ERR_INVALID_ARG = -1
+GS_ERR_CAPACITY = -2
+GS_ERR_CUDA = -3
+GS_ERR_TIMEOUT = -4
+GS_MAX_VIEWS = 64
+
+# Every entry point declared in include/gs.h.
+EXPORTS = [
+    "gs_config_default", "gs_frame_init", "gs_project", "gs_sort_workspace_size", "gs_sort",
+    "gs_render_workspace_size", "gs_render_fwd", "gs_backward_workspace_size", "gs_render_bwd",
+    "gs_adam_step", "gs_pose_step", "gs_l1_loss", "gs_composite_bwd", "gs_project_bwd", "gs_launch_count",
+]
+
+
+class gs_camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class gs_config(C.Structure):
+    _fields_ = [("tile", C.c_int32), ("sh_degree", C.c_int32), ("near_z", C.c_float), ("dilation", C.c_float),
+                ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float), ("bg", C.c_float * 3),
+                ("pose_grad_through_sh", C.c_int32), ("schedule", C.c_int32), ("accumulate", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class gs_frame(C.Structure):
+    _fields_ = [("n_views", C.c_int32), ("tile", C.c_int32), ("width", C.c_int32 * GS_MAX_VIEWS),
+                ("height", C.c_int32 * GS_MAX_VIEWS), ("tiles_x", C.c_int32 * GS_MAX_VIEWS),
+                ("tiles_y", C.c_int32 * GS_MAX_VIEWS), ("tile_base", C.c_int32 * (GS_MAX_VIEWS + 1)),
+                ("pix_base", C.c_int64 * (GS_MAX_VIEWS + 1))]
+
+
+class gs_gaussians(C.Structure):
+    _fields_ = [("mean_opa", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("sh", C.c_void_p),
+                ("n", C.c_int64)]
+
+
+class gs_projected(C.Structure):
+    _fields_ = [("mean2d", C.c_void_p), ("conic_opa", C.c_void_p), ("rgb_depth", C.c_void_p), ("rect", C.c_void_p),
+                ("n_tiles", C.c_void_p)]
+
+
+class gs_pairs(C.Structure):
+    _fields_ = [("src", C.c_void_p), ("emit", C.c_void_p), ("offset", C.c_void_p), ("range", C.c_void_p),
+                ("capacity", C.c_int64), ("count", C.c_void_p), ("status", C.c_void_p)]
+
+
+class gs_image(C.Structure):
+    _fields_ = [("color", C.c_void_p), ("t_final", C.c_void_p), ("n_contrib", C.c_void_p)]
+
+
+class gs_grads(C.Structure):
+    _fields_ = [("mean_opa", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("sh", C.c_void_p),
+                ("visible", C.c_void_p)]
+
+
+class gs_adam_config(C.Structure):
+    _fields_ = [("lr_mean", C.c_float), ("lr_opacity", C.c_float), ("lr_scale", C.c_float), ("lr_rot", C.c_float),
+                ("lr_sh_dc", C.c_float), ("lr_sh_rest", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
+                ("eps", C.c_float)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libgs.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libgs.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        sig = {
+            "gs_config_default": (None, [C.POINTER(gs_config)]),
+            "gs_frame_init": (C.c_int, [C.POINTER(gs_frame), C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                        C.c_int32]),
+            "gs_project": (C.c_int, [C.POINTER(gs_gaussians), P, C.POINTER(gs_frame), C.POINTER(gs_config),
+                                     C.POINTER(gs_projected), P]),
+            "gs_sort_workspace_size": (C.c_size_t, [C.c_int64, C.POINTER(gs_frame), C.c_int64]),
+            "gs_sort": (C.c_int, [C.POINTER(gs_projected), C.c_int64, C.POINTER(gs_frame), C.POINTER(gs_pairs), P,
+                                  C.c_size_t, P]),
+            "gs_render_workspace_size": (C.c_size_t, [C.POINTER(gs_frame)]),
+            "gs_render_fwd": (C.c_int, [C.POINTER(gs_projected), C.POINTER(gs_pairs), C.POINTER(gs_frame),
+                                        C.POINTER(gs_config), C.POINTER(gs_image), P, C.c_size_t, P]),
+            "gs_backward_workspace_size": (C.c_size_t, [C.c_int64, C.POINTER(gs_frame), C.c_int64]),
+            "gs_render_bwd": (C.c_int, [C.POINTER(gs_gaussians), P, C.POINTER(gs_projected), C.POINTER(gs_pairs),
+                                        C.POINTER(gs_frame), C.POINTER(gs_config), C.POINTER(gs_image), P,
+                                        C.POINTER(gs_grads), P, P, P, C.c_size_t, P]),
+            "gs_adam_step": (C.c_int, [C.POINTER(gs_gaussians), C.POINTER(gs_grads), C.POINTER(gs_gaussians),
+                                       C.POINTER(gs_gaussians), C.POINTER(gs_adam_config), C.c_int32, P]),
+            "gs_pose_step": (C.c_int, [P, C.c_int32, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
+                                       C.c_int32, P]),
+            "gs_l1_loss": (C.c_int, [P, P, C.c_int64, P, P, P, C.c_size_t, P]),
+            "gs_composite_bwd": (C.c_int, [C.POINTER(gs_projected), C.POINTER(gs_pairs), C.POINTER(gs_frame),
+                                           C.POINTER(gs_config), C.POINTER(gs_image), P, C.c_int64, P, C.c_size_t,
+                                           P]),
+            "gs_project_bwd": (C.c_int, [C.POINTER(gs_gaussians), P, C.POINTER(gs_projected), C.POINTER(gs_pairs),
+                                         C.POINTER(gs_frame), C.POINTER(gs_config), C.POINTER(gs_grads), P, P, P,
+                                         C.c_size_t, P]),
+            "gs_launch_count": (C.c_int64, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, name: str):
+    if rc != GS_OK:
+        raise RuntimeError(f"{name} returned {rc}")
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+# ---------------------------------------------------------------------------
+# Host structures
+# ---------------------------------------------------------------------------
+
+def config(**kw) -> gs_config:
+    c = gs_config()
+    lib().gs_config_default(C.byref(c))
+    for k, v in kw.items():
+        if k == "bg":
+            c.bg[:] = list(v)
+        else:
+            setattr(c, k, v)
+    return c
+
+
+def frame(sizes, tile: int = 16) -> gs_frame:
+    """sizes: list of (width, height) per view."""
+    f = gs_frame()
+    n = len(sizes)
+    w = (C.c_int32 * n)(*[int(s[0]) for s in sizes])
+    h = (C.c_int32 * n)(*[int(s[1]) for s in sizes])
+    _check(lib().gs_frame_init(C.byref(f), n, w, h, tile), "gs_frame_init")
+    return f
+
+
+def cameras_tensor(cams, device="cuda") -> torch.Tensor:
+    """Packs camera dicts (R, t, fx, fy, cx, cy, width, height) into the device
+    array of gs_camera structs (a uint8 tensor of n * 72 bytes)."""
+    arr = (gs_camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i].R[:] = [float(x) for x in np.asarray(c["R"], np.float64).reshape(9)]
+        arr[i].t[:] = [float(x) for x in np.asarray(c["t"], np.float64).reshape(3)]
+        arr[i].fx, arr[i].fy, arr[i].cx, arr[i].cy = c["fx"], c["fy"], c["cx"], c["cy"]
+        arr[i].width, arr[i].height = c["width"], c["height"]
+    raw = np.frombuffer(bytes(arr), np.uint8).copy()
+    return torch.from_numpy(raw).to(device)
+
+
+def cameras_from_tensor(t: torch.Tensor):
+    raw = t.detach().cpu().numpy().tobytes()
+    arr = (gs_camera * (len(raw) // C.sizeof(gs_camera))).from_buffer_copy(raw)
+    return [dict(R=np.array(a.R[:], np.float32).reshape(3, 3), t=np.array(a.t[:], np.float32), fx=a.fx, fy=a.fy,
+                 cx=a.cx, cy=a.cy, width=a.width, height=a.height) for a in arr]
+
+
+# ---------------------------------------------------------------------------
+# Device buffers (torch tensors) and their C views
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Gaussians:
+    mean_opa: torch.Tensor  # [n, 4]
+    scale: torch.Tensor     # [n, 4]
+    quat: torch.Tensor      # [n, 4]
+    sh: torch.Tensor        # [n, 48]
+
+    @property
+    def n(self) -> int:
+        return int(self.mean_opa.shape[0])
+
+    @staticmethod
+    def from_scene(sc, device="cuda") -> "Gaussians":
+        f = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
+        return Gaussians(f(sc.mean_opa), f(sc.scale), f(sc.quat), f(sc.sh))
+
+    @staticmethod
+    def zeros(n, device="cuda") -> "Gaussians":
+        z = lambda k: torch.zeros((n, k), dtype=torch.float32, device=device)
+        return Gaussians(z(4), z(4), z(4), z(48))
+
+    def c(self) -> gs_gaussians:
+        return gs_gaussians(_ptr(self.mean_opa), _ptr(self.scale), _ptr(self.quat), _ptr(self.sh), self.n)
+
+
+@dataclass
+class Projected:
+    mean2d: torch.Tensor
+    conic_opa: torch.Tensor
+    rgb_depth: torch.Tensor
+    rect: torch.Tensor
+    n_tiles: torch.Tensor
+
+    @staticmethod
+    def alloc(items, device="cuda") -> "Projected":
+        return Projected(torch.zeros((items, 2), dtype=torch.float32, device=device),
+                         torch.zeros((items, 4), dtype=torch.float32, device=device),
+                         torch.zeros((items, 4), dtype=torch.float32, device=device),
+                         torch.zeros((items, 4), dtype=torch.int16, device=device),
+                         torch.zeros((items,), dtype=torch.int32, device=device))
+
+    def c(self) -> gs_projected:
+        return gs_projected(_ptr(self.mean2d), _ptr(self.conic_opa), _ptr(self.rgb_depth), _ptr(self.rect),
+                            _ptr(self.n_tiles))
+
+
+@dataclass
+class Pairs:
+    src: torch.Tensor
+    emit: torch.Tensor
+    offset: torch.Tensor
+    range: torch.Tensor
+    count: torch.Tensor
+    status: torch.Tensor
+
+    @property
+    def capacity(self) -> int:
+        return int(self.src.shape[0])
+
+    @staticmethod
+    def alloc(items, n_tiles_total, capacity, device="cuda") -> "Pairs":
+        u32 = lambda k: torch.zeros((k,), dtype=torch.int32, device=device)
+        return Pairs(u32(max(capacity, 1)), u32(max(capacity, 1)), u32(max(items, 1)), u32(2 * n_tiles_total),
+                     torch.zeros((1,), dtype=torch.int64, device=device),
+                     torch.zeros((1,), dtype=torch.int32, device=device))
+
+    def c(self) -> gs_pairs:
+        return gs_pairs(_ptr(self.src), _ptr(self.emit), _ptr(self.offset), _ptr(self.range), self.capacity,
+                        _ptr(self.count), _ptr(self.status))
+
+
+@dataclass
+class Image:
+    color: torch.Tensor
+    t_final: torch.Tensor
+    n_contrib: torch.Tensor
+
+    @staticmethod
+    def alloc(n_pix, device="cuda") -> "Image":
+        return Image(torch.zeros((3 * n_pix,), dtype=torch.float32, device=device),
+                     torch.zeros((n_pix,), dtype=torch.float32, device=device),
+                     torch.zeros((n_pix,), dtype=torch.int32, device=device))
+
+    def c(self) -> gs_image:
+        return gs_image(_ptr(self.color), _ptr(self.t_final), _ptr(self.n_contrib))
+
+
+@dataclass
+class Grads:
+    mean_opa: torch.Tensor
+    scale: torch.Tensor
+    quat: torch.Tensor
+    sh: torch.Tensor
+    visible: torch.Tensor
+
+    @staticmethod
+    def alloc(n, device="cuda") -> "Grads":
+        z = lambda k: torch.zeros((n, k), dtype=torch.float32, device=device)
+        return Grads(z(4), z(4), z(4), z(48), torch.zeros((n,), dtype=torch.uint8, device=device))
+
+    def c(self) -> gs_grads:
+        return gs_grads(_ptr(self.mean_opa), _ptr(self.scale), _ptr(self.quat), _ptr(self.sh), _ptr(self.visible))
+
+
+def workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    """Caller-owned scratch; torch's allocator returns 512-byte aligned blocks."""
+    return torch.empty((max(int(nbytes), 256),), dtype=torch.uint8, device=device)
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def gs_project(g: Gaussians, cams: torch.Tensor, f: gs_frame, cfg: gs_config, out: Projected, stream=None):
+    gc, pc = g.c(), out.c()
+    _check(lib().gs_project(C.byref(gc), _ptr(cams), C.byref(f), C.byref(cfg), C.byref(pc), _stream(stream)),
+           "gs_project")
+
+
+def gs_sort_workspace_size(n: int, f: gs_frame, capacity: int) -> int:
+    return int(lib().gs_sort_workspace_size(n, C.byref(f), capacity))
+
+
+def gs_sort(p: Projected, n: int, f: gs_frame, out: Pairs, ws: torch.Tensor, stream=None):
+    pc, oc = p.c(), out.c()
+    _check(lib().gs_sort(C.byref(pc), n, C.byref(f), C.byref(oc), _ptr(ws), ws.numel(), _stream(stream)), "gs_sort")
+
+
+def gs_render_fwd(p: Projected, pairs: Pairs, f: gs_frame, cfg: gs_config, out: Image, ws=None, stream=None):
+    pc, qc, oc = p.c(), pairs.c(), out.c()
+    _check(lib().gs_render_fwd(C.byref(pc), C.byref(qc), C.byref(f), C.byref(cfg), C.byref(oc), _ptr(ws),
+                               0 if ws is None else ws.numel(), _stream(stream)), "gs_render_fwd")
+
+
+def gs_backward_workspace_size(n: int, f: gs_frame, capacity: int) -> int:
+    return int(lib().gs_backward_workspace_size(n, C.byref(f), capacity))
+
+
+def gs_render_bwd(g: Gaussians, cams: torch.Tensor, p: Projected, pairs: Pairs, f: gs_frame, cfg: gs_config,
+                  fwd: Image, dL_dcolor: torch.Tensor, grads: Grads, dL_dpose: torch.Tensor, ws: torch.Tensor,
+                  d_proj: torch.Tensor | None = None, stream=None):
+    gc, pc, qc, ic, rc = g.c(), p.c(), pairs.c(), fwd.c(), grads.c()
+    _check(lib().gs_render_bwd(C.byref(gc), _ptr(cams), C.byref(pc), C.byref(qc), C.byref(f), C.byref(cfg),
+                               C.byref(ic), _ptr(dL_dcolor), C.byref(rc), _ptr(dL_dpose), _ptr(d_proj), _ptr(ws),
+                               ws.numel(), _stream(stream)), "gs_render_bwd")
+
+
+def gs_composite_bwd(p: Projected, pairs: Pairs, f: gs_frame, cfg: gs_config, fwd: Image, dL_dcolor: torch.Tensor,
+                     n: int, ws: torch.Tensor, stream=None):
+    pc, qc, ic = p.c(), pairs.c(), fwd.c()
+    _check(lib().gs_composite_bwd(C.byref(pc), C.byref(qc), C.byref(f), C.byref(cfg), C.byref(ic), _ptr(dL_dcolor),
+                                  n, _ptr(ws), ws.numel(), _stream(stream)), "gs_composite_bwd")
+
+
+def gs_project_bwd(g: Gaussians, cams: torch.Tensor, p: Projected, pairs: Pairs, f: gs_frame, cfg: gs_config,
+                   grads: Grads, dL_dpose: torch.Tensor, ws: torch.Tensor, d_proj=None, stream=None):
+    gc, pc, qc, rc = g.c(), p.c(), pairs.c(), grads.c()
+    _check(lib().gs_project_bwd(C.byref(gc), _ptr(cams), C.byref(pc), C.byref(qc), C.byref(f), C.byref(cfg),
+                                C.byref(rc), _ptr(dL_dpose), _ptr(d_proj), _ptr(ws), ws.numel(), _stream(stream)),
+           "gs_project_bwd")
+
+
+def gs_launch_count() -> int:
+    return int(lib().gs_launch_count())
+
+
+def adam_config(lr_mean=1.6e-4, lr_opacity=0.05, lr_scale=5e-3, lr_rot=1e-3, lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4,
+                beta1=0.9, beta2=0.999, eps=1e-15) -> gs_adam_config:
+    return gs_adam_config(lr_mean, lr_opacity, lr_scale, lr_rot, lr_sh_dc, lr_sh_rest, beta1, beta2, eps)
+
+
+def gs_adam_step(params: Gaussians, grads: Grads, m: Gaussians, v: Gaussians, cfg: gs_adam_config, step: int,
+                 stream=None):
+    a, b, c, d = params.c(), grads.c(), m.c(), v.c()
+    _check(lib().gs_adam_step(C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(cfg), step, _stream(stream)),
+           "gs_adam_step")
+
+
+def gs_pose_step(cams: torch.Tensor, n_views: int, dL_dpose: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
+                 lr_t: float, lr_r: float, step: int, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+    _check(lib().gs_pose_step(_ptr(cams), n_views, _ptr(dL_dpose), _ptr(m), _ptr(v), lr_t, lr_r, beta1, beta2, eps,
+                              step, _stream(stream)), "gs_pose_step")
+
+
+def gs_l1_loss(color: torch.Tensor, target: torch.Tensor, dL_dcolor: torch.Tensor, loss: torch.Tensor,
+               ws: torch.Tensor, stream=None):
+    _check(lib().gs_l1_loss(_ptr(color), _ptr(target), color.numel(), _ptr(dL_dcolor), _ptr(loss), _ptr(ws),
+                            ws.numel(), _stream(stream)), "gs_l1_loss")

@@ -1,0 +1,42 @@
+"""Shared test helpers: tolerance checks and oracle/GPU plumbing."""
+from __future__ import annotations
+
+import numpy as np
+
+
+def assert_close(got, ref, rtol, mask=None, what=""):
+    """Per-tensor check |x_gpu - x_ref| <= rtol * (|x_ref| + rms(x_ref)),
+    elementwise, over the entries selected by mask."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if mask is not None:
+        got = got[mask]
+        ref = ref[mask]
+    if ref.size == 0:
+        return
+    rms = float(np.sqrt(np.mean(ref * ref)))
+    err = np.abs(got - ref)
+    lim = rtol * (np.abs(ref) + rms)
+    bad = ~(err <= lim)
+    if bad.any():
+        i = np.argmax(np.where(bad, err / np.maximum(lim, 1e-300), 0))
+        raise AssertionError(f"{what}: {int(bad.sum())} of {ref.size} entries exceed rtol={rtol} "
+                             f"(worst got={got.flat[i]!r} ref={ref.flat[i]!r}, rms={rms:.3e})")
+
+
+def excluded_gaussians(view: dict, bad_tiles: np.ndarray) -> np.ndarray:
+    """Gaussians listed in any flagged tile, plus those with an ambiguous
+    geometric or gradient-path decision."""
+    n = view["proj"]["mean2d"].shape[0]
+    out = np.zeros(n, bool)
+    start, ids = view["start"], view["ids"]
+    for t in np.nonzero(bad_tiles.reshape(-1))[0]:
+        out[ids[start[t]:start[t + 1]]] = True
+    out |= view["proj"]["amb"] > 0
+    return out
+
+
+def tile_pixel_mask(bad_tiles: np.ndarray, width: int, height: int, tile: int) -> np.ndarray:
+    """Pixel mask [H, W] of the pixels lying in flagged tiles."""
+    m = np.repeat(np.repeat(bad_tiles, tile, 0), tile, 1)
+    return m[:height, :width]

@@ -1,0 +1,395 @@
+"""GPU path (libgs, sm_103a) against the FP64 oracle, element by element, on
+the same seeded inputs. Image tolerance 1e-4, gradient tolerance 1e-3
+(relative, per-tensor semantics of helpers.assert_close); tile lists, sort
+orders and integer outputs bit-exact. Decisions the oracle flags as within
+the FP32 margin are excluded and counted."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import assert_close, excluded_gaussians, tile_pixel_mask
+from oracle import oracle as O
+from paper_2506_05558_gb300 import gs, synth
+from paper_2506_05558_gb300.raster import Rasterizer
+
+pytestmark = pytest.mark.gpu
+
+IMG_RTOL = 1e-4
+GRAD_RTOL = 1e-3
+MARGINS = dict(margin_alpha=1e-4, margin_T=1e-4, margin_rect_px=2e-3, margin_geo=1e-5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2506_05558_gb300 import build
+    from oracle import build as ob
+    build.build()
+    ob.build()
+    assert torch.cuda.is_available()
+
+
+def t32(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+def projected_from_items(items_per_view):
+    """Concatenate per-view synthetic projected items into device buffers."""
+    cat = lambda k: np.concatenate([it[k] for it in items_per_view], 0)
+    p = gs.Projected(t32(cat("mean2d")), t32(cat("conic_opa")), t32(cat("rgb_depth")),
+                     torch.from_numpy(cat("rect").astype(np.int16)).cuda(),
+                     torch.from_numpy(cat("n_tiles").astype(np.int32)).cuda())
+    return p
+
+
+def oracle_proj(it):
+    return dict(mean2d=it["mean2d"].astype(np.float64), conic=it["conic_opa"][:, :3].astype(np.float64),
+                opacity=it["conic_opa"][:, 3].astype(np.float64), rgb=it["rgb_depth"][:, :3].astype(np.float64),
+                depth_key=it["rgb_depth"][:, 3].astype(np.float32), rect=it["rect"])
+
+
+def sort_items(items_per_view, sizes, n, capacity=None):
+    f = gs.frame(sizes)
+    p = projected_from_items(items_per_view)
+    total = int(sum(int(it["n_tiles"].sum()) for it in items_per_view))
+    cap = total if capacity is None else capacity
+    pairs = gs.Pairs.alloc(n * len(sizes), int(f.tile_base[len(sizes)]), cap)
+    ws = gs.workspace(gs.gs_sort_workspace_size(n, f, cap))
+    gs.gs_sort(p, n, f, pairs, ws)
+    torch.cuda.synchronize()
+    return f, p, pairs, total
+
+
+# ---------------------------------------------------------------------------
+# Sort: bit-exact tile lists
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("depth_levels", [None, 3])
+def test_sort_matches_oracle_lists(depth_levels):
+    rng = np.random.default_rng(7)
+    sizes = [(200, 120), (77, 50), (160, 160)]
+    n = 3000
+    items = [synth.projected_items(rng, n, (w + 15) // 16, (h + 15) // 16, 16, max_rect=5, depth_levels=depth_levels)
+             for w, h in sizes]
+    f, p, pairs, total = sort_items(items, sizes, n)
+    assert int(pairs.count.item()) == total and int(pairs.status.item()) == gs.GS_OK
+    src = pairs.src.cpu().numpy().view(np.uint32)[:total].astype(np.int64)
+    emit = pairs.emit.cpu().numpy().view(np.uint32)[:total].astype(np.int64)
+    rng_ = pairs.range.cpu().numpy().view(np.uint32).astype(np.int64)
+    offset = pairs.offset.cpu().numpy().view(np.uint32).astype(np.int64)
+    for v, ((w, h), it) in enumerate(zip(sizes, items)):
+        tx, ty = (w + 15) // 16, (h + 15) // 16
+        start, ids = O.tile_lists(it["rect"], it["rgb_depth"][:, 3], tx, ty)
+        for t in range(tx * ty):
+            gt = int(f.tile_base[v]) + t
+            got = src[rng_[2 * gt]:rng_[2 * gt + 1]]
+            want = ids[start[t]:start[t + 1]] + v * n
+            assert np.array_equal(got, want), (v, t)
+    # emission slots: a permutation of [0, total), each inside its item's block
+    assert np.array_equal(np.sort(emit), np.arange(total))
+    nt = np.concatenate([it["n_tiles"] for it in items])
+    assert np.all(emit >= offset[src]) and np.all(emit < offset[src] + nt[src])
+
+
+def test_sort_capacity_overflow_reports_status():
+    rng = np.random.default_rng(8)
+    sizes = [(128, 128)]
+    n = 2000
+    items = [synth.projected_items(rng, n, 8, 8, 16, max_rect=4)]
+    total = int(items[0]["n_tiles"].sum())
+    f, p, pairs, _ = sort_items(items, sizes, n, capacity=total // 3)
+    assert int(pairs.count.item()) == total
+    assert int(pairs.status.item()) == gs.GS_ERR_CAPACITY
+
+
+def test_sort_empty_and_all_culled():
+    sizes = [(64, 64)]
+    for n in (0, 500):
+        it = dict(mean2d=np.zeros((n, 2), np.float32), conic_opa=np.ones((n, 4), np.float32),
+                  rgb_depth=np.ones((n, 4), np.float32), rect=np.zeros((n, 4), np.int32),
+                  n_tiles=np.zeros(n, np.int32))
+        f, p, pairs, total = sort_items([it], sizes, n, capacity=16)
+        assert int(pairs.count.item()) == 0 and int(pairs.status.item()) == gs.GS_OK
+        assert int(pairs.range.abs().sum().item()) == 0
+
+
+# ---------------------------------------------------------------------------
+# Compositing forward / adjoint on synthetic projected splats
+# ---------------------------------------------------------------------------
+
+def _render_items(sizes, n, seed, max_rect=4, bg=(0.0, 0.0, 0.0)):
+    rng = np.random.default_rng(seed)
+    items = [synth.projected_items(rng, n, (w + 15) // 16, (h + 15) // 16, 16, max_rect=max_rect) for w, h in sizes]
+    f, p, pairs, total = sort_items(items, sizes, n)
+    cfg = gs.config(bg=bg)
+    img = gs.Image.alloc(int(f.pix_base[len(sizes)]))
+    gs.gs_render_fwd(p, pairs, f, cfg, img)
+    torch.cuda.synchronize()
+    return rng, items, f, p, pairs, cfg, img
+
+
+@pytest.mark.parametrize("bg", [(0.0, 0.0, 0.0), (0.3, 0.6, 0.1)])
+def test_render_fwd_matches_oracle(bg):
+    sizes = [(150, 100), (64, 48)]
+    rng, items, f, p, pairs, cfg, img = _render_items(sizes, 4000, 11, bg=bg)
+    ocfg = O.Config(bg=bg, **MARGINS)
+    n_amb = 0
+    for v, ((w, h), it) in enumerate(zip(sizes, items)):
+        cam = dict(width=w, height=h)
+        start, ids = O.tile_lists(it["rect"], it["rgb_depth"][:, 3], (w + 15) // 16, (h + 15) // 16)
+        ref = O.render_fwd(oracle_proj(it), start, ids, cam, ocfg)
+        b = int(f.pix_base[v])
+        color = img.color[3 * b:3 * (b + w * h)].view(3, h, w).cpu().numpy()
+        T = img.t_final[b:b + w * h].view(h, w).cpu().numpy()
+        nc = img.n_contrib[b:b + w * h].view(h, w).cpu().numpy()
+        ok = ref["amb"] == 0
+        n_amb += int((~ok).sum())
+        assert_close(color, ref["color"], IMG_RTOL, np.broadcast_to(ok, color.shape), "color")
+        assert_close(T, ref["t_final"], IMG_RTOL, ok, "t_final")
+        assert np.array_equal(nc[ok], ref["n_contrib"][ok])
+    assert n_amb <= 1e-3 * sum(w * h for w, h in sizes) + 2
+
+
+def test_render_bwd_2d_adjoint_matches_oracle():
+    """d_proj (dL/d(u, v, conic, opacity, rgb) per item) against the oracle's
+    compositing adjoint on the same projected splats and lists."""
+    sizes = [(120, 90)]
+    n = 2500
+    rng, items, f, p, pairs, cfg, img = _render_items(sizes, n, 12, bg=(0.1, 0.2, 0.3))
+    w, h = sizes[0]
+    dL = rng.standard_normal((3, h, w)).astype(np.float32)
+    dummy = gs.Gaussians.zeros(n)
+    dummy.quat[:, 0] = 1.0
+    cams = gs.cameras_tensor([synth.camera(np.eye(3), np.zeros(3), 100.0, w, h)])
+    grads = gs.Grads.alloc(n)
+    dpose = torch.zeros((1, 6), device="cuda")
+    ws = gs.workspace(gs.gs_backward_workspace_size(n, f, pairs.capacity))
+    d_proj = torch.zeros((n, 9), device="cuda")
+    gs.gs_render_bwd(dummy, cams, p, pairs, f, cfg, img, t32(dL.reshape(-1)), grads, dpose, ws, d_proj)
+    torch.cuda.synchronize()
+    it = items[0]
+    ocfg = O.Config(bg=(0.1, 0.2, 0.3), **MARGINS)
+    cam = dict(width=w, height=h)
+    start, ids = O.tile_lists(it["rect"], it["rgb_depth"][:, 3], (w + 15) // 16, (h + 15) // 16)
+    oproj = oracle_proj(it)
+    ref = O.render_bwd(oproj, start, ids, cam, ocfg, dL.astype(np.float64))
+    fwd = O.render_fwd(oproj, start, ids, cam, ocfg)
+    oproj.update(amb=np.zeros(n, np.uint8), depth=it["rgb_depth"][:, 3].astype(np.float64))
+    view = dict(proj=oproj, start=start, ids=ids, amb=fwd["amb"])
+    ex = excluded_gaussians(view, O.ambiguous_tiles(view, cam, ocfg))
+    got = d_proj.cpu().numpy()
+    keep = ~ex
+    assert keep.sum() > 0.9 * n
+    for c, name in enumerate(["du", "dv", "da", "db", "dc", "dopa", "dr", "dg", "db_"]):
+        assert_close(got[:, c], ref[:, c], GRAD_RTOL, keep, name)
+
+
+def test_render_bwd_deterministic():
+    sizes = [(96, 96)]
+    n = 2000
+    rng, items, f, p, pairs, cfg, img = _render_items(sizes, n, 13)
+    dL = t32(rng.standard_normal(3 * 96 * 96))
+    dummy = gs.Gaussians.zeros(n)
+    dummy.quat[:, 0] = 1.0
+    cams = gs.cameras_tensor([synth.camera(np.eye(3), np.zeros(3), 100.0, 96, 96)])
+    ws = gs.workspace(gs.gs_backward_workspace_size(n, f, pairs.capacity))
+    outs = []
+    for _ in range(2):
+        grads = gs.Grads.alloc(n)
+        d_proj = torch.zeros((n, 9), device="cuda")
+        gs.gs_render_bwd(dummy, cams, p, pairs, f, cfg, img, dL, grads, torch.zeros((1, 6), device="cuda"), ws,
+                         d_proj)
+        torch.cuda.synchronize()
+        outs.append(d_proj.cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+# ---------------------------------------------------------------------------
+# End to end: project -> sort -> render -> adjoint with pose gradients
+# ---------------------------------------------------------------------------
+
+def run_views(sc, cams, sh_degree, dLs=None, seed=0, pose_through_sh=0, bg=(0.0, 0.0, 0.0)):
+    sizes = [(c["width"], c["height"]) for c in cams]
+    cfg = gs.config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg)
+    g = gs.Gaussians.from_scene(sc)
+    camt = gs.cameras_tensor(cams)
+    r = Rasterizer(sc.n, sizes, capacity=1024, cfg=cfg)
+    r.fit_capacity(g, camt)
+    r.forward(g, camt)
+    rng = np.random.default_rng(seed)
+    if dLs is None:
+        dLs = [rng.standard_normal((3, h, w)) for w, h in sizes]
+    flat = t32(np.concatenate([d.reshape(-1) for d in dLs]))
+    d_proj = torch.zeros((sc.n * len(cams), 9), device="cuda")
+    r.backward(g, camt, flat, d_proj)
+    torch.cuda.synchronize()
+    assert r.status() == gs.GS_OK
+    return r, dLs, d_proj.cpu().numpy()
+
+
+def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), max_amb_frac=2e-3):
+    r, dLs, d_proj = run_views(sc, cams, sh_degree, pose_through_sh=pose_through_sh, bg=bg)
+    ocfg = O.Config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg, **MARGINS)
+    n = sc.n
+    views = []
+    excl = np.zeros(n, bool)
+    n_amb_px = 0
+    for v, cam in enumerate(cams):
+        w, h = cam["width"], cam["height"]
+        view = O.render_view(sc, cam, ocfg)
+        views.append(view)
+        proj = view["proj"]
+        # projection outputs
+        vis = proj["n_tiles"] > 0
+        pg = r.proj
+        sl = slice(v * n, (v + 1) * n)
+        nt = pg.n_tiles[sl].cpu().numpy()
+        geo_ok = (proj["amb"] & 1) == 0
+        assert np.array_equal(nt[geo_ok], proj["n_tiles"][geo_ok]), "n_tiles"
+        rect = pg.rect[sl].cpu().numpy().astype(np.int32) & 0xFFFF
+        both = geo_ok & vis
+        assert np.array_equal(rect[both], proj["rect"][both]), "rect"
+        assert_close(pg.mean2d[sl].cpu().numpy()[both], proj["mean2d"][both], 1e-5, what="mean2d")
+        co = pg.conic_opa[sl].cpu().numpy()[both]
+        assert_close(co[:, :3], proj["conic"][both], 1e-4, what="conic")
+        assert_close(co[:, 3], proj["opacity"][both], 1e-5, what="opacity")
+        rd = pg.rgb_depth[sl].cpu().numpy()[both]
+        assert_close(rd[:, :3], proj["rgb"][both], 1e-5, what="rgb")
+        assert_close(rd[:, 3], proj["depth"][both], 1e-6, what="depth")
+        # image
+        bad = O.ambiguous_tiles(view, cam, ocfg)
+        pm = ~tile_pixel_mask(bad, w, h, 16)
+        n_amb_px += int((~pm).sum())
+        color = r.view_color(v).cpu().numpy()
+        assert_close(color, view["color"], IMG_RTOL, np.broadcast_to(pm, color.shape), f"color view {v}")
+        nc = r.view_pixels(r.img.n_contrib, v).cpu().numpy()
+        assert np.array_equal(nc[pm], view["n_contrib"][pm])
+        excl |= excluded_gaussians(view, bad)
+        # 2D adjoint per item
+        g2d = O.render_bwd(proj, view["start"], view["ids"], cam, ocfg, dLs[v])
+        ok = vis & ~excluded_gaussians(view, bad)
+        for c in range(9):
+            assert_close(d_proj[sl][:, c], g2d[:, c], GRAD_RTOL, ok, f"d_proj[{c}] view {v}")
+    ref = O.backward_views(sc, cams, ocfg, views, dLs)
+    keep = ~excl
+    gr = r.grads
+    mo = gr.mean_opa.cpu().numpy()
+    assert_close(mo[:, :3], ref["mean"], GRAD_RTOL, keep, "d mean")
+    assert_close(mo[:, 3], ref["logit"], GRAD_RTOL, keep, "d opacity logit")
+    assert_close(gr.scale.cpu().numpy()[:, :3], ref["log_scale"], GRAD_RTOL, keep, "d log-scale")
+    assert_close(gr.quat.cpu().numpy(), ref["quat"], GRAD_RTOL, keep, "d quat")
+    ncoef = 3 * (sh_degree + 1) ** 2
+    assert_close(gr.sh.cpu().numpy()[:, :ncoef], ref["sh"][:, :ncoef], GRAD_RTOL, keep, "d sh")
+    vis_any = np.zeros(n, bool)
+    for view in views:
+        vis_any |= view["proj"]["n_tiles"] > 0
+    assert np.array_equal(gr.visible.cpu().numpy().astype(bool)[keep], vis_any[keep])
+    total_px = sum(c["width"] * c["height"] for c in cams)
+    assert n_amb_px <= max_amb_frac * total_px + 256, n_amb_px
+    # pose: the sum runs over every Gaussian, so excluded ones enter it too;
+    # compare only when no Gaussian was excluded, else at a looser bound
+    pose = r.dpose.cpu().numpy()
+    rt = GRAD_RTOL if excl.sum() == 0 else 2e-2
+    for v in range(len(cams)):
+        assert_close(pose[v], ref["pose"][v], rt, what=f"pose view {v}")
+    return r, excl.sum()
+
+
+def test_tiny_scene_sh0_end_to_end():
+    """64x64 view, 1,000 Gaussians, SH degree 0, pose gradient (seeded)."""
+    sc, cam, _ = synth.tiny_scene()
+    compare_views(sc, [cam], 0, bg=(0.2, 0.1, 0.0))
+
+
+@pytest.mark.parametrize("through_sh", [0, 1])
+def test_multiview_sh3_end_to_end(through_sh):
+    """Three views of different sizes (ragged edge tiles), SH degree 3."""
+    sc, cams, _ = synth.multiview_scene(seed=5, n=20000, n_views=3, sizes=[(200, 120), (131, 77), (96, 160)])
+    compare_views(sc, cams, 3, pose_through_sh=through_sh)
+
+
+def test_720p_200k_end_to_end():
+    """1280x720, 200k Gaussians, SH3, 16x16 tiles (full size)."""
+    sc, cam, _ = synth.view_720p_scene()
+    compare_views(sc, [cam], 3)
+
+
+def test_nonfinite_gaussians_are_culled():
+    sc, cam, _ = synth.tiny_scene(n=200)
+    sc.mean_opa[3, 0] = np.nan
+    sc.scale[5, 1] = np.inf
+    sc.quat[7, :] = 0.0
+    sc.sh[9, 0] = np.nan
+    r, _, _ = run_views(sc, [cam], 0)
+    nt = r.proj.n_tiles.cpu().numpy()
+    assert nt[3] == 0 and nt[5] == 0 and nt[7] == 0 and nt[9] == 0
+    assert np.isfinite(r.img.color.cpu().numpy()).all()
+    for t in (r.grads.mean_opa, r.grads.scale, r.grads.sh, r.dpose):
+        assert np.isfinite(t.cpu().numpy()).all()
+
+
+# ---------------------------------------------------------------------------
+# Loss and optimiser
+# ---------------------------------------------------------------------------
+
+def test_l1_loss_matches_oracle():
+    rng = np.random.default_rng(3)
+    for n in (1, 1001, 3 * 64 * 64):
+        c = rng.random(n).astype(np.float32)
+        t = rng.random(n).astype(np.float32)
+        t[: n // 7] = c[: n // 7]
+        dL = torch.zeros(n, device="cuda")
+        loss = torch.zeros(1, device="cuda")
+        gs.gs_l1_loss(t32(c), t32(t), dL, loss, gs.workspace(4 * 4096))
+        ref_l, ref_g = O.l1_loss_grad(c, t)
+        assert abs(loss.item() - ref_l) <= 1e-6 * abs(ref_l) + 1e-7
+        assert np.array_equal(dL.cpu().numpy(), ref_g.astype(np.float32))
+
+
+def test_adam_matches_oracle():
+    rng = np.random.default_rng(4)
+    n = 3000
+    params = {k: rng.standard_normal((n, w)).astype(np.float32) for k, w in
+              (("mean_opa", 4), ("scale", 4), ("quat", 4), ("sh", 48))}
+    params["scale"][:, 3] = 0
+    P = gs.Gaussians(*[t32(params[k]) for k in ("mean_opa", "scale", "quat", "sh")])
+    M, V = gs.Gaussians.zeros(n), gs.Gaussians.zeros(n)
+    vis = rng.random(n) < 0.7
+    cfg = gs.adam_config(lr_mean=0.01, lr_opacity=0.05, lr_scale=0.005, lr_rot=0.001, lr_sh_dc=0.0025,
+                         lr_sh_rest=0.000125)
+    ref = {k: (params[k].astype(np.float64), np.zeros_like(params[k], np.float64),
+               np.zeros_like(params[k], np.float64)) for k in params}
+    lrs = {"mean_opa": [0.01] * 3 + [0.05], "scale": [0.005] * 3 + [0.0], "quat": [0.001] * 4,
+           "sh": [0.0025] * 3 + [0.000125] * 45}
+    for step in (1, 2, 3):
+        grads = {k: rng.standard_normal(params[k].shape).astype(np.float32) for k in params}
+        grads["scale"][:, 3] = 0
+        G = gs.Grads(*[t32(grads[k]) for k in ("mean_opa", "scale", "quat", "sh")],
+                     torch.from_numpy(vis.astype(np.uint8)).cuda())
+        gs.gs_adam_step(P, G, M, V, cfg, step)
+        for k in params:
+            p, m, v = ref[k]
+            lr = np.array(lrs[k])
+            out = [O.adam_step(p[:, j], grads[k][:, j], m[:, j], v[:, j], step, lr[j], eps=1e-15, mask=vis)
+                   for j in range(p.shape[1])]
+            ref[k] = tuple(np.stack([o[i] for o in out], 1) for i in range(3))
+    torch.cuda.synchronize()
+    for k, t in (("mean_opa", P.mean_opa), ("scale", P.scale), ("quat", P.quat), ("sh", P.sh)):
+        assert_close(t.cpu().numpy(), ref[k][0], 1e-5, what=k)
+
+
+def test_pose_step_matches_oracle_retraction():
+    rng = np.random.default_rng(5)
+    cams = [synth.camera(*O.retract_pose(np.eye(3), rng.normal(0, 1, 3), rng.normal(0, 0.3, 6)), 500.0, 64, 64)
+            for _ in range(3)]
+    camt = gs.cameras_tensor(cams)
+    grad = rng.standard_normal((3, 6)).astype(np.float32)
+    m = torch.zeros((3, 6), device="cuda")
+    v = torch.zeros((3, 6), device="cuda")
+    gs.gs_pose_step(camt, 3, t32(grad), m, v, 0.01, 0.02, 1)
+    out = gs.cameras_from_tensor(camt)
+    for i in range(3):
+        lr = np.array([0.01] * 3 + [0.02] * 3)
+        step = -lr * np.sign(grad[i])  # Adam's first step
+        R, t = O.retract_pose(cams[i]["R"], cams[i]["t"], step)
+        assert np.abs(out[i]["R"] - R).max() < 2e-6
+        assert np.abs(out[i]["t"] - t).max() < 2e-5 * max(1.0, np.abs(t).max())
