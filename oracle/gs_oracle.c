@@ -29,10 +29,12 @@
  * cam[18] = R(9, row-major world->camera), t(3), fx, fy, cx, cy, width, height
  * cfg[16] = tile, sh_degree, near, dilation, alpha_min, alpha_max, t_min,
  *           bg(3), pose_grad_through_sh, margin_geo, margin_alpha, margin_T,
- *           margin_rect_px, (1 unused)
+ *           margin_rect_px, margin_depth
  * margin_geo is relative (near plane, determinant, radius, guard band, colour
  * clamp); margin_rect_px is the distance in pixels of a tile-rect edge from a
- * tile boundary; margin_alpha and margin_T are relative.
+ * tile boundary; margin_alpha and margin_T are relative; margin_depth flags a
+ * pixel whose composited Gaussians include two with depths equal to within
+ * that relative margin (their fp32 sort order may differ).
  */
 #include <math.h>
 #include <stdint.h>
@@ -48,7 +50,7 @@ typedef struct {
 
 typedef struct {
     int tile, sh_degree, pose_through_sh;
-    double near_z, dil, a_min, a_max, t_min, bg[3], m_geo, m_alpha, m_T, m_rect;
+    double near_z, dil, a_min, a_max, t_min, bg[3], m_geo, m_alpha, m_T, m_rect, m_depth;
 } Cfg;
 
 static Cam read_cam(const double* c) {
@@ -66,7 +68,7 @@ static Cfg read_cfg(const double* c) {
     g.near_z = c[2]; g.dil = c[3]; g.a_min = c[4]; g.a_max = c[5]; g.t_min = c[6];
     g.bg[0] = c[7]; g.bg[1] = c[8]; g.bg[2] = c[9];
     g.pose_through_sh = (int)c[10];
-    g.m_geo = c[11]; g.m_alpha = c[12]; g.m_T = c[13]; g.m_rect = c[14];
+    g.m_geo = c[11]; g.m_alpha = c[12]; g.m_T = c[13]; g.m_rect = c[14]; g.m_depth = c[15];
     return g;
 }
 
@@ -236,16 +238,18 @@ static void project_one(int64_t i, const double* mean_opa, const double* scale, 
     double mid = 0.5 * (A + C);
     double lam = mid + sqrt(fmax(0.1, mid * mid - st->det));
     double q3 = 3.0 * sqrt(lam);
-    if (dist_to_int(q3) < g->m_geo * fmax(1.0, q3)) a |= 1;
+    /* a radius near an integer may round to r or r+1: an edge then moves by 1 px */
+    double r_slack = dist_to_int(q3) < g->m_geo * fmax(1.0, q3) ? 1.0 : 0.0;
     double r = ceil(q3);
     int T = g->tile;
     int tx = (k->W + T - 1) / T, ty = (k->H + T - 1) / T;
     double e[4] = {(u - r) / T, (v - r) / T, (u + r + T - 1) / T, (v + r + T - 1) / T};
     double lim[4] = {tx, ty, tx, ty};
-    /* an edge near a tile boundary inside the grid may round either way in fp32 */
+    /* an edge near a tile boundary inside the grid may round either way in fp32;
+     * bits 4, 8, 16, 32 flag edges x0, y0, x1, y1 */
     for (int c = 0; c < 4; c++) {
-        double k = nearbyint(e[c]);
-        if (k >= 1 && k <= lim[c] && dist_to_int(e[c]) * T < g->m_rect) a |= 1;
+        double kk = nearbyint(e[c]);
+        if (kk >= 1 && kk <= lim[c] && dist_to_int(e[c]) * T < g->m_rect + r_slack) a |= (uint8_t)(4 << c);
     }
     int rc[4];
     for (int c = 0; c < 4; c++) {
@@ -377,13 +381,26 @@ typedef struct {
 } Contrib;
 
 /* Walks the pixel's list; records composited Gaussians into rec (if non-NULL).
- * Returns the number composited; sets *n_contrib, *T_out, color. */
+ * Returns the number composited; sets *n_contrib, *T_out, color. A decision
+ * within the margins sets *amb and, when amb_g is given, flags the Gaussian(s)
+ * it concerns. */
 static int composite_pixel(const Cfg* g, double px, double py, const int32_t* ids, int64_t len,
                            const double* mean2d, const double* conic, const double* opac, const double* rgb,
-                           double* color, double* T_out, int32_t* n_contrib, uint8_t* amb, Contrib* rec) {
+                           const double* depth, double* color, double* T_out, int32_t* n_contrib, uint8_t* amb,
+                           Contrib* rec, uint8_t* amb_g) {
     double T = 1.0, C[3] = {0, 0, 0};
     int nrec = 0;
     int32_t last = 0;
+    double z_prev = -1.0;
+    int32_t id_prev = -1;
+#define FLAG_G(x)                          \
+    do {                                   \
+        *amb = 1;                          \
+        if (amb_g) {                       \
+            _Pragma("omp atomic write")    \
+            amb_g[x] = 1;                  \
+        }                                  \
+    } while (0)
     for (int64_t j = 0; j < len; j++) {
         int32_t id = ids[j];
         double dx = px - mean2d[2 * id], dy = py - mean2d[2 * id + 1];
@@ -392,13 +409,21 @@ static int composite_pixel(const Cfg* g, double px, double py, const int32_t* id
         if (power > 0) continue;
         double G = exp(power);
         double og = opac[id] * G;
-        if (fabs(og - g->a_max) < g->m_alpha * g->a_max) *amb = 1;
+        if (fabs(og - g->a_max) < g->m_alpha * g->a_max) FLAG_G(id);
         double alpha = og < g->a_max ? og : g->a_max;
-        if (fabs(alpha - g->a_min) < g->m_alpha * g->a_min) *amb = 1;
+        if (fabs(alpha - g->a_min) < g->m_alpha * g->a_min) FLAG_G(id);
         if (alpha < g->a_min) continue;
         double testT = T * (1.0 - alpha);
-        if (fabs(testT - g->t_min) < g->m_T * g->t_min) *amb = 1;
+        if (fabs(testT - g->t_min) < g->m_T * g->t_min) FLAG_G(id);
         if (testT < g->t_min) break;
+        if (depth) {
+            if (z_prev >= 0 && fabs(depth[id] - z_prev) <= g->m_depth * fabs(depth[id])) {
+                FLAG_G(id);
+                FLAG_G(id_prev);
+            }
+            z_prev = depth[id];
+            id_prev = id;
+        }
         for (int ch = 0; ch < 3; ch++) C[ch] += alpha * T * rgb[3 * id + ch];
         if (rec) {
             rec[nrec].alpha = alpha; rec[nrec].T = T; rec[nrec].g = G; rec[nrec].og = og;
@@ -412,11 +437,13 @@ static int composite_pixel(const Cfg* g, double px, double py, const int32_t* id
     *T_out = T;
     *n_contrib = last;
     return nrec;
+#undef FLAG_G
 }
 
 void or_render_fwd(const double* cam, const double* cfg, const int64_t* tile_start, const int32_t* ids,
                    const double* mean2d, const double* conic, const double* opac, const double* rgb,
-                   double* color, double* t_final, int32_t* n_contrib, uint8_t* amb_px) {
+                   const double* depth, double* color, double* t_final, int32_t* n_contrib, uint8_t* amb_px,
+                   uint8_t* amb_g) {
     Cam k = read_cam(cam);
     Cfg g = read_cfg(cfg);
     int T = g.tile, tx = (k.W + T - 1) / T;
@@ -429,7 +456,7 @@ void or_render_fwd(const double* cam, const double* cfg, const int64_t* tile_sta
         int32_t nc;
         uint8_t a = 0;
         composite_pixel(&g, x + 0.5, y + 0.5, ids + tile_start[t], tile_start[t + 1] - tile_start[t], mean2d,
-                        conic, opac, rgb, col, &Tf, &nc, &a, NULL);
+                        conic, opac, rgb, depth, col, &Tf, &nc, &a, NULL, amb_g);
         for (int ch = 0; ch < 3; ch++) color[ch * HW + pix] = col[ch];
         t_final[pix] = Tf;
         n_contrib[pix] = nc;
@@ -444,10 +471,14 @@ void or_render_fwd(const double* cam, const double* cfg, const int64_t* tile_sta
  *   dC/dalpha_i = T_i c_i - (sum_{j>i} alpha_j T_j c_j + T_N bg) / (1 - alpha_i).
  * Then alpha = min(a_max, o g), g = exp(power),
  * power = -(a dx^2 + c dy^2)/2 - b dx dy, d = pixel - mean2d.
- * g2d[9*i] = dL/d(u, v, conic a, b, c, opacity, r, g, b) summed over pixels. */
+ * g2d[9*i] = dL/d(u, v, conic a, b, c, opacity, r, g, b) summed over pixels.
+ * amb_g2d (optional, same shape): the sum of |contribution| coming from pixels
+ * flagged ambiguous (by this pass, or in amb_in [H*W] when given), a bound on
+ * how much an FP32 branch flip can move g2d. */
 void or_render_bwd(const double* cam, const double* cfg, const int64_t* tile_start, const int32_t* ids,
                    const double* mean2d, const double* conic, const double* opac, const double* rgb,
-                   const double* dL_dcolor, int64_t n, double* g2d) {
+                   const double* depth, const double* dL_dcolor, int64_t n, double* g2d, double* amb_g2d,
+                   const uint8_t* amb_in) {
     Cam k = read_cam(cam);
     Cfg g = read_cfg(cfg);
     int T = g.tile, tx = (k.W + T - 1) / T, ty = (k.H + T - 1) / T;
@@ -455,6 +486,7 @@ void or_render_bwd(const double* cam, const double* cfg, const int64_t* tile_sta
     int64_t P = tile_start[nt];
     /* one partial per list entry so tiles can run in parallel; summed in list order below */
     double* part = (double*)calloc((size_t)(P > 0 ? P : 1) * 9, sizeof(double));
+    double* part_amb = (double*)calloc((size_t)(P > 0 ? P : 1) * 9, sizeof(double));
 #pragma omp parallel
     {
         int64_t cap = 0;
@@ -470,7 +502,9 @@ void or_render_bwd(const double* cam, const double* cfg, const int64_t* tile_sta
                     double col[3], Tf, px = x + 0.5, py = y + 0.5;
                     int32_t nc;
                     uint8_t a = 0;
-                    int nr = composite_pixel(&g, px, py, ids + b0, len, mean2d, conic, opac, rgb, col, &Tf, &nc, &a, rec);
+                    int nr = composite_pixel(&g, px, py, ids + b0, len, mean2d, conic, opac, rgb, depth, col, &Tf, &nc,
+                                             &a, rec, NULL);
+                    if (amb_in && amb_in[pix]) a = 1;
                     double gC[3] = {dL_dcolor[pix], dL_dcolor[HW + pix], dL_dcolor[2 * HW + pix]};
                     double total[3] = {0, 0, 0};
                     for (int r = 0; r < nr; r++)
@@ -482,6 +516,8 @@ void or_render_bwd(const double* cam, const double* cfg, const int64_t* tile_sta
                         Contrib* c = &rec[r];
                         int32_t id = c->id;
                         double* pp = part + 9 * (b0 + j);
+                        double before[9];
+                        for (int q = 0; q < 9; q++) before[q] = pp[q];
                         double dalpha = 0;
                         for (int ch = 0; ch < 3; ch++) {
                             double ci = rgb[3 * id + ch];
@@ -502,6 +538,8 @@ void or_render_bwd(const double* cam, const double* cfg, const int64_t* tile_sta
                             pp[4] += dpower * (-0.5 * dy * dy);
                             pp[5] += dalpha * c->g;
                         }
+                        if (a)
+                            for (int q = 0; q < 9; q++) part_amb[9 * (b0 + j) + q] += fabs(pp[q] - before[q]);
                         r++;
                     }
                 }
@@ -509,9 +547,15 @@ void or_render_bwd(const double* cam, const double* cfg, const int64_t* tile_sta
         free(rec);
     }
     for (int64_t i = 0; i < 9 * n; i++) g2d[i] = 0;
+    if (amb_g2d)
+        for (int64_t i = 0; i < 9 * n; i++) amb_g2d[i] = 0;
     for (int64_t j = 0; j < P; j++)
-        for (int c = 0; c < 9; c++) g2d[9 * (int64_t)ids[j] + c] += part[9 * j + c];
+        for (int c = 0; c < 9; c++) {
+            g2d[9 * (int64_t)ids[j] + c] += part[9 * j + c];
+            if (amb_g2d) amb_g2d[9 * (int64_t)ids[j] + c] += part_amb[9 * j + c];
+        }
     free(part);
+    free(part_amb);
 }
 
 /* ---------------------------------------------------------------------------

@@ -38,9 +38,11 @@ def lib():
         _lib.or_tile_lists.restype = C.c_int64
         _lib.or_tile_lists.argtypes = [C.c_int64, i32, f32, C.c_int, C.c_int, i64, i32, C.c_int64]
         _lib.or_render_fwd.restype = None
-        _lib.or_render_fwd.argtypes = [d, d, i64, i32, d, d, d, d, d, d, i32, u8]
+        dn = np.ctypeslib.ndpointer(np.float64, flags="C")
+        opt = C.c_void_p  # optional double array
+        _lib.or_render_fwd.argtypes = [d, d, i64, i32, d, d, d, d, opt, d, d, i32, u8, u8]
         _lib.or_render_bwd.restype = None
-        _lib.or_render_bwd.argtypes = [d, d, i64, i32, d, d, d, d, d, C.c_int64, d]
+        _lib.or_render_bwd.argtypes = [d, d, i64, i32, d, d, d, d, opt, d, C.c_int64, d, opt, opt]
         _lib.or_project_bwd.restype = None
         _lib.or_project_bwd.argtypes = [C.c_int64, d, d, d, d, d, d, d, d, d, d, d, d, d]
         _lib.or_sh_basis.restype = None
@@ -63,11 +65,13 @@ class Config:
     margin_alpha: float = 1e-5
     margin_T: float = 1e-4
     margin_rect_px: float = 2e-3
+    margin_depth: float = 1e-6
 
     def array(self) -> np.ndarray:
         return np.array([self.tile, self.sh_degree, self.near_z, self.dilation, self.alpha_min,
                          self.alpha_max, self.t_min, *self.bg, self.pose_grad_through_sh,
-                         self.margin_geo, self.margin_alpha, self.margin_T, self.margin_rect_px, 0], np.float64)
+                         self.margin_geo, self.margin_alpha, self.margin_T, self.margin_rect_px,
+                         self.margin_depth], np.float64)
 
 
 def cam_array(cam: dict) -> np.ndarray:
@@ -113,26 +117,43 @@ def tile_lists(rect, depth_key, tiles_x, tiles_y):
     return start, ids[:total]
 
 
+def _depth_arg(proj):
+    """Depth array (keeps a reference alive) and its address, or (None, None)."""
+    if proj.get("depth") is None:
+        return None, None
+    z = _c(proj["depth"], np.float64)
+    return z, z.ctypes.data
+
+
 def render_fwd(proj, start, ids, cam, cfg: Config) -> dict:
     H, W = cam["height"], cam["width"]
+    n = proj["mean2d"].shape[0]
     out = dict(color=np.zeros((3, H, W)), t_final=np.zeros((H, W)), n_contrib=np.zeros((H, W), np.int32),
-               amb=np.zeros((H, W), np.uint8))
+               amb=np.zeros((H, W), np.uint8), amb_gauss=np.zeros(max(n, 1), np.uint8))
+    z, zp = _depth_arg(proj)
     lib().or_render_fwd(cam_array(cam), cfg.array(), _c(start, np.int64), _c(ids, np.int32),
                         _c(proj["mean2d"], np.float64), _c(proj["conic"], np.float64),
-                        _c(proj["opacity"], np.float64), _c(proj["rgb"], np.float64),
-                        out["color"], out["t_final"], out["n_contrib"], out["amb"])
+                        _c(proj["opacity"], np.float64), _c(proj["rgb"], np.float64), zp,
+                        out["color"], out["t_final"], out["n_contrib"], out["amb"], out["amb_gauss"])
+    out["amb_gauss"] = out["amb_gauss"][:n]
     return out
 
 
-def render_bwd(proj, start, ids, cam, cfg: Config, dL_dcolor) -> np.ndarray:
-    """Returns g2d [n, 9] = dL/d(u, v, conic a, b, c, opacity, r, g, b)."""
+def render_bwd(proj, start, ids, cam, cfg: Config, dL_dcolor, with_amb=False, amb_pixels=None):
+    """Returns g2d [n, 9] = dL/d(u, v, conic a, b, c, opacity, r, g, b); with
+    with_amb also the [n, 9] bound on contributions from ambiguous pixels
+    (those the oracle flags, plus amb_pixels [H, W] when given)."""
     n = proj["mean2d"].shape[0]
     g2d = np.zeros((n, 9))
+    amb = np.zeros((n, 9))
+    z, zp = _depth_arg(proj)
+    extra = None if amb_pixels is None else _c(amb_pixels, np.uint8)
     lib().or_render_bwd(cam_array(cam), cfg.array(), _c(start, np.int64), _c(ids, np.int32),
                         _c(proj["mean2d"], np.float64), _c(proj["conic"], np.float64),
-                        _c(proj["opacity"], np.float64), _c(proj["rgb"], np.float64),
-                        _c(dL_dcolor, np.float64), n, g2d)
-    return g2d
+                        _c(proj["opacity"], np.float64), _c(proj["rgb"], np.float64), zp,
+                        _c(dL_dcolor, np.float64), n, g2d, amb.ctypes.data if with_amb else None,
+                        None if extra is None else extra.ctypes.data)
+    return (g2d, amb) if with_amb else g2d
 
 
 def project_bwd(scene, cam, cfg: Config, g2d) -> dict:
@@ -189,38 +210,67 @@ def backward_views(scene, cams, cfg, views, dL_dcolors) -> dict:
     return tot
 
 
+def _alpha_on(proj, i, xs, ys):
+    """alpha of item i on the pixel grid xs x ys (pixel centres at +0.5)."""
+    u, v = proj["mean2d"][i]
+    a, b, c = proj["conic"][i]
+    dx = (xs[None, :] + 0.5) - u
+    dy = (ys[:, None] + 0.5) - v
+    power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy
+    return np.where(power > 0, 0.0, proj["opacity"][i] * np.exp(np.minimum(power, 0.0)))
+
+
 def ambiguous_tiles(view: dict, cam, cfg: Config) -> np.ndarray:
-    """Tiles whose list or pixels the FP32 path may legitimately compute
-    differently: tiles holding an ambiguous pixel, tiles within one tile of an
-    ambiguous Gaussian's rect, and tiles whose list holds two consecutive
-    Gaussians with depths equal to within margin_geo (relative)."""
+    """Tiles whose list the FP32 path may legitimately build differently.
+    Ambiguity bits of or_project: 1 = near plane / determinant (the Gaussian
+    may vanish: its whole rect plus one tile), 4/8/16/32 = rect edge x0/y0/x1/y1
+    near a tile boundary: the tile column (row) just inside or outside that
+    edge may or may not list the Gaussian; a tile of it is flagged only if the
+    Gaussian reaches alpha_min there (a Gaussian below alpha_min everywhere in
+    the tile composites to nothing either way)."""
     tx, ty = tiles_xy(cam, cfg)
     T = cfg.tile
+    W, H = cam["width"], cam["height"]
     bad = np.zeros((ty, tx), bool)
-    H, W = cam["height"], cam["width"]
-    amb_px = view["amb"]
-    pad = np.zeros((ty * T, tx * T), bool)
-    pad[:H, :W] = amb_px > 0
-    bad |= pad.reshape(ty, T, tx, T).any(axis=(1, 3))
     proj = view["proj"]
-    for i in np.nonzero(proj["amb"] & 1)[0]:
-        r = proj["rect"][i]
-        if r[2] > r[0] and r[3] > r[1]:
-            bad[max(r[1] - 1, 0):r[3] + 1, max(r[0] - 1, 0):r[2] + 1] = True
-        else:
-            # culled here but may survive in FP32: mark the neighbourhood of its centre
+    amb = proj["amb"]
+    thr = cfg.alpha_min * (1 - 10 * cfg.margin_alpha)
+    for i in np.nonzero(amb & (1 | 4 | 8 | 16 | 32))[0]:
+        x0, y0, x1, y1 = (int(c) for c in proj["rect"][i])
+        a = int(amb[i])
+        if x1 <= x0 or y1 <= y0 or (a & 1):
+            # may vanish or appear: its (possible) rect plus a margin
             u, v = proj["mean2d"][i]
-            if np.isfinite(u) and np.isfinite(v) and proj["depth"][i] > 0:
+            if x1 > x0 and y1 > y0:
+                bad[max(y0 - 1, 0):y1 + 1, max(x0 - 1, 0):x1 + 1] = True
+            elif np.isfinite(u) and np.isfinite(v):
                 cx, cy = int(np.clip(u // T, 0, tx - 1)), int(np.clip(v // T, 0, ty - 1))
                 bad[max(cy - 2, 0):cy + 3, max(cx - 2, 0):cx + 3] = True
-    start, ids = view["start"], view["ids"]
-    z = proj["depth"]
-    for t in range(tx * ty):
-        seg = ids[start[t]:start[t + 1]]
-        if len(seg) > 1:
-            zz = z[seg]
-            if np.any(np.abs(np.diff(zz)) <= cfg.margin_geo * np.abs(zz[1:])):
-                bad[t // tx, t % tx] = True
+            continue
+        u, v = proj["mean2d"][i]
+        r_lo, r_hi = max(y0 - 1, 0), min(y1 + 1, ty)
+        c_lo, c_hi = max(x0 - 1, 0), min(x1 + 1, tx)
+        cols, rows = [], []
+        if a & 4:
+            cols += [x0 - 1, x0]
+        if a & 16:
+            cols += [x1 - 1, x1]
+        if a & 8:
+            rows += [y0 - 1, y0]
+        if a & 32:
+            rows += [y1 - 1, y1]
+        cand = set()
+        for cx in cols:
+            if 0 <= cx < tx:
+                cand |= {(ry, cx) for ry in range(r_lo, r_hi)}
+        for ry in rows:
+            if 0 <= ry < ty:
+                cand |= {(ry, cx) for cx in range(c_lo, c_hi)}
+        for ry, cx in cand:
+            xs = np.arange(cx * T, min(cx * T + T, W), dtype=np.float64)
+            ys = np.arange(ry * T, min(ry * T + T, H), dtype=np.float64)
+            if xs.size and ys.size and _alpha_on(proj, i, xs, ys).max() >= thr:
+                bad[ry, cx] = True
     return bad
 
 

@@ -32,7 +32,7 @@ def excluded_gaussians(view: dict, bad_tiles: np.ndarray) -> np.ndarray:
     start, ids = view["start"], view["ids"]
     for t in np.nonzero(bad_tiles.reshape(-1))[0]:
         out[ids[start[t]:start[t + 1]]] = True
-    out |= view["proj"]["amb"] > 0
+    out |= (view["proj"]["amb"] & (1 | 2)) > 0
     return out
 
 
@@ -40,3 +40,12 @@ def tile_pixel_mask(bad_tiles: np.ndarray, width: int, height: int, tile: int) -
     """Pixel mask [H, W] of the pixels lying in flagged tiles."""
     m = np.repeat(np.repeat(bad_tiles, tile, 0), tile, 1)
     return m[:height, :width]
+
+
+def amb_heavy(g2d, amb, rtol, share=0.3):
+    """Items whose 2D adjoint draws more than `share` of the tolerance from
+    pixels the oracle flagged as ambiguous (a flip there could move it)."""
+    g2d = np.asarray(g2d)
+    amb = np.asarray(amb)
+    rms = np.sqrt(np.mean(g2d * g2d, axis=0, keepdims=True)) + 1e-300
+    return np.any(amb > share * rtol * (np.abs(g2d) + rms), axis=1)
