@@ -12,28 +12,21 @@
 
 namespace gs {
 
-constexpr int kPBThreads = 128;
+constexpr int kPBGauss = 32;                   // Gaussians per CTA, one per lane
+constexpr int kPBWarps = 8;                    // views processed at once, one per warp
+constexpr int kPBThreads = kPBGauss * kPBWarps;
+constexpr int kSlots = 64;                     // 4 mean/logit + 4 scale + 4 quat + 48 SH + visible + pad
+constexpr int kSlotVis = 60;
+constexpr int kSlotPitch = kPBGauss + 1;       // +1 word: conflict-free column access
+constexpr size_t kPBSmem = sizeof(float) * kPBWarps * kSlots * kSlotPitch;
 
-__device__ __forceinline__ void block_sum6(float (&x)[6], float* s_red /* [kPBThreads/32][6] */, float* out6) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int c = 0; c < 6; c++) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x[c] += __shfl_xor_sync(0xffffffffu, x[c], o);
-    }
-    if (lane == 0)
-#pragma unroll
-        for (int c = 0; c < 6; c++) s_red[w * 6 + c] = x[c];
-    __syncthreads();
-    if (threadIdx.x < 6) {
-        float s = 0.f;
-        for (int k = 0; k < kPBThreads / 32; k++) s += s_red[k * 6 + threadIdx.x];
-        out6[threadIdx.x] = s;
-    }
-    __syncthreads();
-}
+// Gradient of one (view, Gaussian) item, written to this warp's slot column.
+struct ItemOut {
+    float* col;  // s_slot[w][*][lane]
+    __device__ __forceinline__ void put(int c, float v) const { col[c * kSlotPitch] = v; }
+};
 
-__global__ void __launch_bounds__(kPBThreads) k_project_bwd(
+__global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
     const float4* __restrict__ mean_opa, const float4* __restrict__ scale, const float4* __restrict__ quat,
     const float4* __restrict__ sh, int64_t n, const gs_camera* __restrict__ cams, gs_frame f, gs_config cfg,
     const int32_t* __restrict__ n_tiles, const uint32_t* __restrict__ offset, const float4* __restrict__ part0,
@@ -41,19 +34,26 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
     float4* __restrict__ g_mean_opa, float4* __restrict__ g_scale, float4* __restrict__ g_quat,
     float4* __restrict__ g_sh, uint8_t* __restrict__ visible, float* __restrict__ d_proj,
     float* __restrict__ pose_part) {
+    extern __shared__ float s_slot[];  // [kPBWarps][kSlots][kSlotPitch]
     __shared__ gs_camera s_cam[GS_MAX_VIEWS];
-    __shared__ float s_red[(kPBThreads / 32) * 6];
+    const unsigned FULL = 0xffffffffu;
     const int nv = f.n_views;
     for (int i = threadIdx.x; i < nv * (int)(sizeof(gs_camera) / 4); i += kPBThreads)
         reinterpret_cast<float*>(s_cam)[i] = reinterpret_cast<const float*>(cams)[i];
-    __syncthreads();
-    const int64_t g = (int64_t)blockIdx.x * kPBThreads + threadIdx.x;
-    const bool valid = g < n;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    // With fewer than 8 views the CTA takes several groups of 32 Gaussians:
+    // warp w handles group w / nvw and, each round, view round * nvw + w % nvw.
+    const int nvw = nv < kPBWarps ? nv : kPBWarps;
+    const int G = kPBWarps / nvw;
+    const int group = w / nvw, vw = w % nvw;
+    const int64_t gi = (int64_t)blockIdx.x * G + group;  // global group index
+    const int64_t n_groups = ceil_div(n, kPBGauss);
+    const int64_t g = gi * kPBGauss + lane;
+    const bool valid = group < G && g < n;
     float4 mo = make_float4(0.f, 0.f, 0.f, 0.f), s4 = mo, q4 = make_float4(1.f, 0.f, 0.f, 0.f);
     if (valid) { mo = mean_opa[g]; s4 = scale[g]; q4 = quat[g]; }
     // parameter-space quantities shared by all views
-    const float qn2 = q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w;
-    const float qi = rsqrtf(qn2);
+    const float qi = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
     const float qw = q4.x * qi, qx = q4.y * qi, qy = q4.z * qi, qz = q4.w * qi;
     float Rq[9];
     Rq[0] = 1.f - 2.f * (qy * qy + qz * qz); Rq[1] = 2.f * (qx * qy - qw * qz); Rq[2] = 2.f * (qx * qz + qw * qy);
@@ -62,23 +62,24 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
     const float sv[3] = {expf(s4.x), expf(s4.y), expf(s4.z)};
     const float opa = 1.f / (1.f + expf(-mo.w));
     const int ncoef = (cfg.sh_degree + 1) * (cfg.sh_degree + 1);
-
-    float gm[3] = {0.f, 0.f, 0.f}, glogit = 0.f, gls[3] = {0.f, 0.f, 0.f}, gRq[9];
+    const ItemOut out{s_slot + (w * kSlots) * kSlotPitch + lane};
+    // reducer: thread t owns slot values idx = t + 256 i (slot idx / 32, Gaussian idx % 32)
+    float acc[kSlots * kPBGauss / kPBThreads];
 #pragma unroll
-    for (int c = 0; c < 9; c++) gRq[c] = 0.f;
-    float gsh[48];
-#pragma unroll
-    for (int c = 0; c < 48; c++) gsh[c] = 0.f;
-    bool any_vis = false;
+    for (int i = 0; i < kSlots * kPBGauss / kPBThreads; i++) acc[i] = 0.f;
+    __syncthreads();
 
-    for (int v = 0; v < nv; v++) {
-        float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int v0 = 0; v0 < nv; v0 += nvw) {
+        const int v = v0 + vw;
         const int64_t item = (int64_t)v * n + g;
-        const int nt = valid ? n_tiles[item] : 0;
-        if (nt > 0) {
-            any_vis = true;
+        const int nt = (valid && v < nv) ? n_tiles[item] : 0;
+        float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (nt <= 0) {
+#pragma unroll 4
+            for (int c = 0; c < kSlots; c++) out.put(c, 0.f);
+        } else {
             const gs_camera& c = s_cam[v];
-            // 1. sum this item's pair partials
+            // 1. sum this item's pair partials (contiguous emission slots)
             const uint32_t off = offset[item];
             float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
             float a2 = 0.f;
@@ -100,17 +101,12 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
             const float x = c.R[0] * mo.x + c.R[1] * mo.y + c.R[2] * mo.z + c.t[0];
             const float y = c.R[3] * mo.x + c.R[4] * mo.y + c.R[5] * mo.z + c.t[1];
             const float z = c.R[6] * mo.x + c.R[7] * mo.y + c.R[8] * mo.z + c.t[2];
-            float RRq[9];  // R_cam * Rq
+            float T[9];  // R_cam Rq diag(s)
 #pragma unroll
             for (int r = 0; r < 3; r++)
 #pragma unroll
                 for (int k = 0; k < 3; k++)
-                    RRq[3 * r + k] = c.R[3 * r] * Rq[k] + c.R[3 * r + 1] * Rq[3 + k] + c.R[3 * r + 2] * Rq[6 + k];
-            float T[9];
-#pragma unroll
-            for (int r = 0; r < 3; r++)
-#pragma unroll
-                for (int k = 0; k < 3; k++) T[3 * r + k] = RRq[3 * r + k] * sv[k];
+                    T[3 * r + k] = (c.R[3 * r] * Rq[k] + c.R[3 * r + 1] * Rq[3 + k] + c.R[3 * r + 2] * Rq[6 + k]) * sv[k];
             const float limx = 1.3f * 0.5f * (float)c.width / c.fx;
             const float limy = 1.3f * 0.5f * (float)c.height / c.fy;
             const float iz = 1.f / z;
@@ -130,10 +126,7 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
             const float idet = 1.f / (Sa * Sc - Sb * Sb);
             const float Qa = Sc * idet, Qb = -Sb * idet, Qc = Sa * idet;
 
-            // 3. opacity
-            glogit += dop * opa * (1.f - opa);
-
-            // 4. colour: rgb = max(0.5 + sum_k Y_k(d) sh_k, 0), d = (mu - centre)/|mu - centre|
+            // 3. colour: rgb = max(0.5 + sum_k Y_k(d) sh_k, 0), d = (mu - centre)/|mu - centre|
             const float ccx = -(c.R[0] * c.t[0] + c.R[3] * c.t[1] + c.R[6] * c.t[2]);
             const float ccy = -(c.R[1] * c.t[0] + c.R[4] * c.t[1] + c.R[7] * c.t[2]);
             const float ccz = -(c.R[2] * c.t[0] + c.R[5] * c.t[1] + c.R[8] * c.t[2]);
@@ -143,64 +136,73 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
             float Y[16];
             sh_eval_basis(cfg.sh_degree, ddx, ddy, ddz, Y);
             const float4* shg = sh + 12 * g;
-            float cf[48];
+            float raw0 = 0.5f, raw1 = 0.5f, raw2 = 0.5f;
 #pragma unroll
             for (int r = 0; r < 12; r++) {
                 if (4 * r < 3 * ncoef) {
                     const float4 q = shg[r];
-                    cf[4 * r] = q.x; cf[4 * r + 1] = q.y; cf[4 * r + 2] = q.z; cf[4 * r + 3] = q.w;
-                } else {
-                    cf[4 * r] = cf[4 * r + 1] = cf[4 * r + 2] = cf[4 * r + 3] = 0.f;
+                    const float cq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int idx = 4 * r + u, k = idx / 3, ch = idx % 3;
+                        if (k < ncoef) {
+                            if (ch == 0) raw0 += Y[k] * cq[u];
+                            else if (ch == 1) raw1 += Y[k] * cq[u];
+                            else raw2 += Y[k] * cq[u];
+                        }
+                    }
                 }
             }
-            float raw0 = 0.5f, raw1 = 0.5f, raw2 = 0.5f;
+            const float gc[3] = {raw0 > 0.f ? dr : 0.f, raw1 > 0.f ? dg : 0.f, raw2 > 0.f ? db : 0.f};
 #pragma unroll
             for (int k = 0; k < 16; k++)
-                if (k < ncoef) {
-                    raw0 += Y[k] * cf[3 * k]; raw1 += Y[k] * cf[3 * k + 1]; raw2 += Y[k] * cf[3 * k + 2];
-                }
-            const float g0 = raw0 > 0.f ? dr : 0.f, g1 = raw1 > 0.f ? dg : 0.f, g2 = raw2 > 0.f ? db : 0.f;
 #pragma unroll
-            for (int k = 0; k < 16; k++)
-                if (k < ncoef) {
-                    gsh[3 * k] += g0 * Y[k]; gsh[3 * k + 1] += g1 * Y[k]; gsh[3 * k + 2] += g2 * Y[k];
-                }
+                for (int ch = 0; ch < 3; ch++) out.put(12 + 3 * k + ch, k < ncoef ? gc[ch] * Y[k] : 0.f);
+            float gmx = 0.f, gmy = 0.f, gmz = 0.f;
             if (cfg.sh_degree > 0) {
                 float3 dY[16];
                 sh_basis_grad(cfg.sh_degree, ddx, ddy, ddz, dY);
                 float gdx = 0.f, gdy = 0.f, gdz = 0.f;
 #pragma unroll
-                for (int k = 1; k < 16; k++)
-                    if (k < ncoef) {
-                        const float s = g0 * cf[3 * k] + g1 * cf[3 * k + 1] + g2 * cf[3 * k + 2];
-                        gdx += s * dY[k].x; gdy += s * dY[k].y; gdz += s * dY[k].z;
+                for (int r = 0; r < 12; r++) {
+                    if (4 * r < 3 * ncoef) {
+                        const float4 q = shg[r];
+                        const float cq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int idx = 4 * r + u, k = idx / 3, ch = idx % 3;
+                            if (k >= 1 && k < ncoef) {
+                                const float s = gc[ch] * cq[u];
+                                gdx += s * dY[k].x; gdy += s * dY[k].y; gdz += s * dY[k].z;
+                            }
+                        }
                     }
+                }
                 const float dd = gdx * ddx + gdy * ddy + gdz * ddz;
-                const float gx = (gdx - ddx * dd) * il, gy = (gdy - ddy * dd) * il, gz = (gdz - ddz * dd) * il;
-                gm[0] += gx; gm[1] += gy; gm[2] += gz;
+                gmx = (gdx - ddx * dd) * il; gmy = (gdy - ddy * dd) * il; gmz = (gdz - ddz * dd) * il;
                 if (cfg.pose_grad_through_sh) {
                     // centre = -R^T t moves by -R^T rho under exp(xi^): dL/drho += R dL/ddir
-                    pose[0] += c.R[0] * gx + c.R[1] * gy + c.R[2] * gz;
-                    pose[1] += c.R[3] * gx + c.R[4] * gy + c.R[5] * gz;
-                    pose[2] += c.R[6] * gx + c.R[7] * gy + c.R[8] * gz;
+                    pose[0] += c.R[0] * gmx + c.R[1] * gmy + c.R[2] * gmz;
+                    pose[1] += c.R[3] * gmx + c.R[4] * gmy + c.R[5] * gmz;
+                    pose[2] += c.R[6] * gmx + c.R[7] * gmy + c.R[8] * gmz;
                 }
             }
 
-            // 5. conic = S^-1: dL/dS = -Q dL/dQ Q, dL/dQ = [[dA, dB/2], [dB/2, dC]]
+            // 4. conic = S^-1: dL/dS = -Q dL/dQ Q, dL/dQ = [[dA, dB/2], [dB/2, dC]]
             const float hB = 0.5f * dB;
             const float t00 = Qa * dA + Qb * hB, t01 = Qa * hB + Qb * dC;
             const float t10 = Qb * dA + Qc * hB, t11 = Qb * hB + Qc * dC;
             const float GS00 = -(t00 * Qa + t01 * Qb);
             const float GS01 = -(t00 * Qb + t01 * Qc);
             const float GS11 = -(t10 * Qb + t11 * Qc);
-            // 6. S = M M^T + dil I: dL/dM = 2 GS M
+            // 5. S = M M^T + dil I: dL/dM = 2 GS M
             float GM0[3], GM1[3];
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 GM0[k] = 2.f * (GS00 * M0[k] + GS01 * M1[k]);
                 GM1[k] = 2.f * (GS01 * M0[k] + GS11 * M1[k]);
             }
-            // 7. M = J T: dL/dJ = GM T^T (entries J00, J02, J11, J12), dL/dT = J^T GM
+            // 6. M = J T: dL/dJ = GM T^T (entries J00, J02, J11, J12), dL/dT = J^T GM
             const float GJ00 = GM0[0] * T[0] + GM0[1] * T[1] + GM0[2] * T[2];
             const float GJ02 = GM0[0] * T[6] + GM0[1] * T[7] + GM0[2] * T[8];
             const float GJ11 = GM1[0] * T[3] + GM1[1] * T[4] + GM1[2] * T[5];
@@ -212,19 +214,35 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
                 GT[3 + k] = J11 * GM1[k];
                 GT[6 + k] = J02 * GM0[k] + J12 * GM1[k];
             }
-            // 8. T = R Rq diag(s): dL/d(Rq diag s) = R^T GT
+            // 7. T = R Rq diag(s): dL/d(Rq diag s) = R^T GT -> log-scale and rotation matrix
+            float gRq[9];
 #pragma unroll
             for (int k = 0; k < 3; k++) {
                 float gsk = 0.f;
 #pragma unroll
                 for (int r = 0; r < 3; r++) {
-                    const float h = c.R[r] * GT[k] + c.R[3 + r] * GT[3 + k] + c.R[6 + r] * GT[6 + k];  // (R^T GT)[r][k]
+                    const float h = c.R[r] * GT[k] + c.R[3 + r] * GT[3 + k] + c.R[6 + r] * GT[6 + k];
                     gsk += h * Rq[3 * r + k];
-                    gRq[3 * r + k] += h * sv[k];
+                    gRq[3 * r + k] = h * sv[k];
                 }
-                gls[k] += gsk * sv[k];
+                out.put(4 + k, gsk * sv[k]);
             }
-            // 9. p = (x, y, z): through the 2D mean and J
+            out.put(7, 0.f);
+            // rotation matrix -> normalised quaternion -> raw quaternion
+            float gq[4];
+            gq[0] = 2.f * (-qz * gRq[1] + qy * gRq[2] + qz * gRq[3] - qx * gRq[5] - qy * gRq[6] + qx * gRq[7]);
+            gq[1] = 2.f * (qy * gRq[1] + qz * gRq[2] + qy * gRq[3] - 2.f * qx * gRq[4] - qw * gRq[5] + qz * gRq[6] +
+                           qw * gRq[7] - 2.f * qx * gRq[8]);
+            gq[2] = 2.f * (-2.f * qy * gRq[0] + qx * gRq[1] + qw * gRq[2] + qx * gRq[3] + qz * gRq[5] - qw * gRq[6] +
+                           qz * gRq[7] - 2.f * qy * gRq[8]);
+            gq[3] = 2.f * (-2.f * qz * gRq[0] - qw * gRq[1] + qx * gRq[2] + qw * gRq[3] - 2.f * qz * gRq[4] +
+                           qy * gRq[5] + qx * gRq[6] + qy * gRq[7]);
+            const float qd = gq[0] * qw + gq[1] * qx + gq[2] * qy + gq[3] * qz;
+            out.put(8, (gq[0] - qw * qd) * qi);
+            out.put(9, (gq[1] - qx * qd) * qi);
+            out.put(10, (gq[2] - qy * qd) * qi);
+            out.put(11, (gq[3] - qz * qd) * qi);
+            // 8. p = (x, y, z): through the 2D mean and J
             float gpx = du * c.fx * iz, gpy = dv * c.fy * iz;
             float gpz = -(du * c.fx * x + dv * c.fy * y) * iz * iz;
             gpz += -(GJ00 * c.fx + GJ11 * c.fy) * iz * iz;
@@ -240,11 +258,15 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
                 gpy += -GJ12 * c.fy * iz * iz;
                 gpz += 2.f * GJ12 * c.fy * y * iz * iz * iz;
             }
-            // mean: p = R mu + t
-            gm[0] += c.R[0] * gpx + c.R[3] * gpy + c.R[6] * gpz;
-            gm[1] += c.R[1] * gpx + c.R[4] * gpy + c.R[7] * gpz;
-            gm[2] += c.R[2] * gpx + c.R[5] * gpy + c.R[8] * gpz;
-            // 10. pose, left perturbation: dp = rho + phi x p, dT = phi^ T
+            // mean: p = R mu + t (plus the SH view-direction term)
+            out.put(0, gmx + c.R[0] * gpx + c.R[3] * gpy + c.R[6] * gpz);
+            out.put(1, gmy + c.R[1] * gpx + c.R[4] * gpy + c.R[7] * gpz);
+            out.put(2, gmz + c.R[2] * gpx + c.R[5] * gpy + c.R[8] * gpz);
+            out.put(3, dop * opa * (1.f - opa));
+            out.put(kSlotVis, 1.f);
+#pragma unroll
+            for (int cc = kSlotVis + 1; cc < kSlots; cc++) out.put(cc, 0.f);
+            // 9. pose, left perturbation: dp = rho + phi x p, dT = phi^ T
             pose[0] += gpx; pose[1] += gpy; pose[2] += gpz;
             pose[3] += y * gpz - z * gpy;
             pose[4] += z * gpx - x * gpz;
@@ -261,44 +283,83 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
             pose[4] += N20 - N02;
             pose[5] += N01 - N10;
         }
-        float out6[6];
-        block_sum6(pose, s_red, out6);
-        if (threadIdx.x < 6) pose_part[((int64_t)v * gridDim.x + blockIdx.x) * 6 + threadIdx.x] = out6[threadIdx.x];
-    }
-    if (!valid) return;
-    // quaternion: rotation-matrix gradient -> normalised quaternion -> raw quaternion
-    float gq[4];
-    gq[0] = 2.f * (-qz * gRq[1] + qy * gRq[2] + qz * gRq[3] - qx * gRq[5] - qy * gRq[6] + qx * gRq[7]);
-    gq[1] = 2.f * (qy * gRq[1] + qz * gRq[2] + qy * gRq[3] - 2.f * qx * gRq[4] - qw * gRq[5] + qz * gRq[6] +
-                   qw * gRq[7] - 2.f * qx * gRq[8]);
-    gq[2] = 2.f * (-2.f * qy * gRq[0] + qx * gRq[1] + qw * gRq[2] + qx * gRq[3] + qz * gRq[5] - qw * gRq[6] +
-                   qz * gRq[7] - 2.f * qy * gRq[8]);
-    gq[3] = 2.f * (-2.f * qz * gRq[0] - qw * gRq[1] + qx * gRq[2] + qw * gRq[3] - 2.f * qz * gRq[4] + qy * gRq[5] +
-                   qx * gRq[6] + qy * gRq[7]);
-    const float qd = gq[0] * qw + gq[1] * qx + gq[2] * qy + gq[3] * qz;
-    float4 o_mo = make_float4(gm[0], gm[1], gm[2], glogit);
-    float4 o_sc = make_float4(gls[0], gls[1], gls[2], 0.f);
-    float4 o_q = make_float4((gq[0] - qw * qd) * qi, (gq[1] - qx * qd) * qi, (gq[2] - qy * qd) * qi,
-                             (gq[3] - qz * qd) * qi);
-    float4* gs_row = g_sh + 12 * g;
-    if (cfg.accumulate) {
-        const float4 a = g_mean_opa[g], b = g_scale[g], c = g_quat[g];
-        o_mo.x += a.x; o_mo.y += a.y; o_mo.z += a.z; o_mo.w += a.w;
-        o_sc.x += b.x; o_sc.y += b.y; o_sc.z += b.z;
-        o_q.x += c.x; o_q.y += c.y; o_q.z += c.z; o_q.w += c.w;
+        // this view's pose partial over the CTA's 32 Gaussians (fixed xor tree)
 #pragma unroll
-        for (int r = 0; r < 12; r++) {
-            const float4 h = gs_row[r];
-            gsh[4 * r] += h.x; gsh[4 * r + 1] += h.y; gsh[4 * r + 2] += h.z; gsh[4 * r + 3] += h.w;
+        for (int c = 0; c < 6; c++)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) pose[c] += __shfl_xor_sync(FULL, pose[c], o);
+        if (group < G && gi < n_groups && v < nv && lane < 6) {
+            float pv = pose[0];
+#pragma unroll
+            for (int c = 1; c < 6; c++) pv = (lane == c) ? pose[c] : pv;
+            pose_part[((int64_t)v * n_groups + gi) * 6 + lane] = pv;
         }
-        any_vis = any_vis || visible[g];
-    }
-    g_mean_opa[g] = o_mo;
-    g_scale[g] = o_sc;
-    g_quat[g] = o_q;
+        __syncthreads();
+        // sum each group's warps (its views of this round) in a fixed order
+        if (G == 1) {  // possibly several rounds: accumulate in registers
 #pragma unroll
-    for (int r = 0; r < 12; r++) gs_row[r] = make_float4(gsh[4 * r], gsh[4 * r + 1], gsh[4 * r + 2], gsh[4 * r + 3]);
-    visible[g] = any_vis ? 1 : 0;
+            for (int i = 0; i < kSlots * kPBGauss / kPBThreads; i++) {
+                const int idx = threadIdx.x + kPBThreads * i;
+                const int cs = idx >> 5, gl = idx & 31;
+                float sacc = 0.f;
+                for (int ww = 0; ww < nvw; ww++) sacc += s_slot[(ww * kSlots + cs) * kSlotPitch + gl];
+                acc[i] += sacc;
+            }
+        } else {  // a single round: fold into the group's first warp's slots
+            for (int e = threadIdx.x; e < G * kSlots * kPBGauss; e += kPBThreads) {
+                const int grp = e / (kSlots * kPBGauss), rem = e % (kSlots * kPBGauss);
+                const int cs = rem >> 5, gl = rem & 31;
+                const int base = grp * nvw;
+                float sacc = 0.f;
+                for (int ww = 0; ww < nvw; ww++) sacc += s_slot[((base + ww) * kSlots + cs) * kSlotPitch + gl];
+                s_slot[(base * kSlots + cs) * kSlotPitch + gl] = sacc;
+            }
+        }
+        __syncthreads();
+    }
+    if (G == 1) {  // stage the totals in warp 0's slots
+#pragma unroll
+        for (int i = 0; i < kSlots * kPBGauss / kPBThreads; i++) {
+            const int idx = threadIdx.x + kPBThreads * i;
+            s_slot[(idx >> 5) * kSlotPitch + (idx & 31)] = acc[i];
+        }
+        __syncthreads();
+    }
+    // write rows, coalesced across each group's 32 Gaussians
+    for (int ri = threadIdx.x; ri < G * 15 * kPBGauss; ri += kPBThreads) {
+        const int grp = ri / (15 * kPBGauss), rr = ri % (15 * kPBGauss);
+        const float* src = s_slot + (grp * nvw * kSlots) * kSlotPitch;
+        const int64_t g0 = ((int64_t)blockIdx.x * G + grp) * kPBGauss;
+        int gl, c0;
+        float4* dst;
+        if (rr < 3 * kPBGauss) {
+            gl = rr % kPBGauss;
+            const int arr = rr / kPBGauss;
+            c0 = 4 * arr;
+            dst = (arr == 0 ? g_mean_opa : arr == 1 ? g_scale : g_quat) + (g0 + gl);
+        } else {
+            const int r = rr - 3 * kPBGauss;
+            gl = r / 12;
+            c0 = 12 + 4 * (r % 12);
+            dst = g_sh + (g0 + gl) * 12 + (r % 12);
+        }
+        if (g0 + gl >= n) continue;
+        float4 val = make_float4(src[c0 * kSlotPitch + gl], src[(c0 + 1) * kSlotPitch + gl],
+                                 src[(c0 + 2) * kSlotPitch + gl], src[(c0 + 3) * kSlotPitch + gl]);
+        if (cfg.accumulate) {
+            const float4 old = *dst;
+            val.x += old.x; val.y += old.y; val.z += old.z; val.w += old.w;
+        }
+        *dst = val;
+    }
+    for (int t = threadIdx.x; t < G * kPBGauss; t += kPBThreads) {
+        const int grp = t / kPBGauss, gl = t % kPBGauss;
+        const int64_t gg = ((int64_t)blockIdx.x * G + grp) * kPBGauss + gl;
+        if (gg >= n) continue;
+        const bool vis = s_slot[((grp * nvw * kSlots) + kSlotVis) * kSlotPitch + gl] > 0.f;
+        uint8_t* vd = visible + gg;
+        *vd = (vis || (cfg.accumulate && *vd)) ? 1 : 0;
+    }
 }
 
 // dL/dxi of view v = sum over CTAs of pose_part[v][b][6], fixed tree order.
@@ -337,7 +398,7 @@ static BwdWs carve_bwd(char* base, size_t cap, int64_t n, int n_views, int64_t c
     w.part0 = c.take<float4>(capacity);
     w.part1 = c.take<float4>(capacity);
     w.part2 = c.take<float>(capacity);
-    w.pose_part = c.take<float>((size_t)n_views * ceil_div(n, kPBThreads) * 6);
+    w.pose_part = c.take<float>((size_t)n_views * ceil_div(n, kPBGauss) * 6);
     *used = c.used;
     return w;
 }
@@ -386,8 +447,15 @@ extern "C" int gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, cons
         GS_CUDA_CHECK_LAUNCH();
         return GS_OK;
     }
-    const int64_t nb = ceil_div(g->n, kPBThreads);
-    k_project_bwd<<<(unsigned)nb, kPBThreads, 0, s>>>(
+    const int64_t nb = ceil_div(g->n, kPBGauss);  // groups of 32 Gaussians (pose partials per view)
+    const int nvw = f->n_views < kPBWarps ? f->n_views : kPBWarps;
+    const int64_t grid = ceil_div(nb, kPBWarps / nvw);
+    static bool attr_set = false;  // the smem opt-in is per function and device-independent here
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_project_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPBSmem);
+        attr_set = true;
+    }
+    k_project_bwd<<<(unsigned)grid, kPBThreads, kPBSmem, s>>>(
         (const float4*)g->mean_opa, (const float4*)g->scale, (const float4*)g->quat, (const float4*)g->sh, g->n, cams,
         *f, *cfg, p->n_tiles, pairs->offset, w.part0, w.part1, w.part2, pairs->capacity, (float4*)grads->mean_opa,
         (float4*)grads->scale, (float4*)grads->quat, (float4*)grads->sh, grads->visible, d_proj, w.pose_part);

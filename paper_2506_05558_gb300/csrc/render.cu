@@ -3,8 +3,12 @@
 // One CTA of 256 threads per 16x16 tile, one pixel per thread; each warp owns
 // an 8x4 block of pixels so a small splat touches few warps. Each tile's
 // depth-ordered list is walked in batches staged in shared memory (128-bit
-// loads of the projected rows). The forward stops a CTA when every pixel's
-// transmittance has terminated (barrier count); the adjoint recomputes the
+// loads of the projected rows). While staging, each Gaussian gets the bounding
+// box of the region where its alpha can reach alpha_min; a warp tests 32
+// staged boxes against its 8x4 block with one ballot and evaluates only the
+// hits, so Gaussians that cannot touch any of its pixels cost nothing. The
+// forward stops a CTA when every pixel's transmittance has terminated; the
+// adjoint recomputes the
 // blending state back to front from T_final and n_contrib, reduces each
 // Gaussian's 9 partial derivatives across the warp with a transposing
 // butterfly (12 shuffles for 9 values), sums the 8 warps in a fixed order and
@@ -54,14 +58,45 @@ __device__ __forceinline__ TileInfo tile_info(const gs_frame& f, int tile) {
 }
 
 // Staged form of a projected Gaussian: exponent coefficients in base 2,
-// e = A dx^2 + B dx dy + C dy^2 = -(a dx^2 + 2 b dx dy + c dy^2)/2 * log2(e).
+// e = A dx^2 + B dx dy + C dy^2 = -(a dx^2 + 2 b dx dy + c dy^2)/2 * log2(e),
+// and the bounding box (x0, y0, x1, y1) of the ellipse where o exp(-q/2) can
+// reach alpha_min (q = d^T conic d <= 2 ln(o / alpha_min)); the box is widened
+// by 0.1% + 0.01 px so that FP32 evaluation never finds a hit outside it.
 __device__ __forceinline__ void stage(const float2* __restrict__ mean2d, const float4* __restrict__ conic_opa,
-                                      const float4* __restrict__ rgb_depth, uint32_t idx, float2& xy, float4& abco,
-                                      float4& rgb) {
+                                      const float4* __restrict__ rgb_depth, uint32_t idx, float alpha_min, float2& xy,
+                                      float4& abco, float4& rgb, float4& box) {
     xy = mean2d[idx];
     const float4 co = conic_opa[idx];
     abco = make_float4(-0.5f * kLog2e * co.x, -kLog2e * co.y, -0.5f * kLog2e * co.z, co.w);
     rgb = rgb_depth[idx];
+    const float det = co.x * co.z - co.y * co.y;
+    if (!(co.w >= alpha_min)) {
+        box = make_float4(1e30f, 1e30f, -1e30f, -1e30f);  // can never reach alpha_min
+    } else if (!(det > 0.f)) {
+        box = make_float4(-1e30f, -1e30f, 1e30f, 1e30f);  // degenerate conic: never skip
+    } else {
+        const float t = 2.f * logf(co.w / alpha_min);
+        const float hx = sqrtf(fmaxf(t * co.z / det, 0.f)) * 1.001f + 0.01f;
+        const float hy = sqrtf(fmaxf(t * co.x / det, 0.f)) * 1.001f + 0.01f;
+        box = make_float4(xy.x - hx, xy.y - hy, xy.x + hx, xy.y + hy);
+    }
+}
+
+struct WarpBlock {
+    float x0, y0, x1, y1;  // pixel-centre extent of this warp's 8x4 block
+    __device__ __forceinline__ bool hits(const float4& b) const {
+        return b.x <= x1 && b.z >= x0 && b.y <= y1 && b.w >= y0;
+    }
+};
+
+__device__ __forceinline__ WarpBlock warp_block(const TileInfo& ti) {
+    const int lane = threadIdx.x & 31;
+    WarpBlock wb;
+    wb.x0 = (float)(ti.px - (lane & 7)) + 0.5f;
+    wb.y0 = (float)(ti.py - (lane >> 3)) + 0.5f;
+    wb.x1 = wb.x0 + 7.f;
+    wb.y1 = wb.y0 + 3.f;
+    return wb;
 }
 
 // Exponent (base 2) of the Gaussian at offset (dx, dy). The same rounding
@@ -81,8 +116,12 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(gs_frame f, gs_config c
     __shared__ float2 s_xy[kFwdBatch];
     __shared__ float4 s_abco[kFwdBatch];
     __shared__ float4 s_rgb[kFwdBatch];
+    __shared__ float4 s_box[kFwdBatch];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int tile = blockIdx.x;
     const TileInfo ti = tile_info(f, tile);
+    const WarpBlock wb = warp_block(ti);
     const float px = ti.px + 0.5f, py = ti.py + 0.5f;
     const uint32_t start = range[2 * tile], end = range[2 * tile + 1];
     float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
@@ -91,25 +130,34 @@ __global__ void __launch_bounds__(kThreads) k_render_fwd(gs_frame f, gs_config c
     for (uint32_t b0 = start; b0 < end; b0 += kFwdBatch) {
         if (__syncthreads_count(done) == kThreads) break;
         const uint32_t j = b0 + threadIdx.x;
-        if (j < end) stage(mean2d, conic_opa, rgb_depth, src[j], s_xy[threadIdx.x], s_abco[threadIdx.x],
-                           s_rgb[threadIdx.x]);
+        if (j < end)
+            stage(mean2d, conic_opa, rgb_depth, src[j], cfg.alpha_min, s_xy[threadIdx.x], s_abco[threadIdx.x],
+                  s_rgb[threadIdx.x], s_box[threadIdx.x]);
         __syncthreads();
         const int cnt = min((uint32_t)kFwdBatch, end - b0);
-        for (int k = 0; k < cnt && !done; k++) {
-            const float2 xy = s_xy[k];
-            const float4 abco = s_abco[k];
-            const float e = exponent2(abco, px - xy.x, py - xy.y);
-            if (e > 0.f) continue;
-            const float og = __fmul_rn(abco.w, fast_exp2(e));
-            const float alpha = fminf(cfg.alpha_max, og);
-            if (alpha < cfg.alpha_min) continue;
-            const float nT = __fmul_rn(T, 1.f - alpha);
-            if (nT < cfg.t_min) { done = true; break; }
-            const float4 c = s_rgb[k];
-            const float w = alpha * T;
-            cr += w * c.x; cg += w * c.y; cb += w * c.z;
-            T = nT;
-            last = (int)(b0 - start) + k + 1;
+        for (int k0 = 0; k0 < cnt; k0 += 32) {
+            if (__all_sync(FULL, done)) break;
+            const int kk = k0 + lane;
+            unsigned m = __ballot_sync(FULL, kk < cnt && wb.hits(s_box[kk < cnt ? kk : 0]));
+            while (m) {
+                const int k = k0 + __ffs(m) - 1;
+                m &= m - 1;
+                if (done) continue;
+                const float2 xy = s_xy[k];
+                const float4 abco = s_abco[k];
+                const float e = exponent2(abco, px - xy.x, py - xy.y);
+                if (e > 0.f) continue;
+                const float og = __fmul_rn(abco.w, fast_exp2(e));
+                const float alpha = fminf(cfg.alpha_max, og);
+                if (alpha < cfg.alpha_min) continue;
+                const float nT = __fmul_rn(T, 1.f - alpha);
+                if (nT < cfg.t_min) { done = true; continue; }
+                const float4 c = s_rgb[k];
+                const float w = alpha * T;
+                cr += w * c.x; cg += w * c.y; cb += w * c.z;
+                T = nT;
+                last = (int)(b0 - start) + k + 1;
+            }
         }
     }
     if (ti.inside) {
@@ -170,12 +218,16 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(gs_frame f, gs_config c
     __shared__ float2 s_xy[kBwdBatch];
     __shared__ float4 s_abco[kBwdBatch];
     __shared__ float4 s_rgb[kBwdBatch];
+    __shared__ float4 s_box[kBwdBatch];
     __shared__ uint32_t s_emit[kBwdBatch];
     __shared__ float s_part[kWarps][kBwdBatch][9];
+    __shared__ uint32_t s_hit[kWarps][kBwdBatch / 32];  // which Gaussians each warp wrote
     __shared__ int s_max;
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int tile = blockIdx.x;
     const TileInfo ti = tile_info(f, tile);
+    const WarpBlock wb = warp_block(ti);
     const float px = ti.px + 0.5f, py = ti.py + 0.5f;
     const uint32_t start = range[2 * tile];
     float Tf = 1.f, gr = 0.f, gg = 0.f, gb = 0.f;
@@ -189,7 +241,8 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(gs_frame f, gs_config c
     }
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
-    atomicMax(&s_max, nc);
+    const int warp_nc = __reduce_max_sync(FULL, (unsigned)nc);
+    if (lane == 0) atomicMax(&s_max, warp_nc);
     __syncthreads();
     const int n_list = s_max;
     // background seen through the final transmittance, folded into the "behind" term
@@ -203,64 +256,79 @@ __global__ void __launch_bounds__(kThreads) k_render_bwd(gs_frame f, gs_config c
         __syncthreads();
         if (threadIdx.x < cnt) {
             const uint32_t p = start + b0 + threadIdx.x;
-            stage(mean2d, conic_opa, rgb_depth, src[p], s_xy[threadIdx.x], s_abco[threadIdx.x], s_rgb[threadIdx.x]);
+            stage(mean2d, conic_opa, rgb_depth, src[p], cfg.alpha_min, s_xy[threadIdx.x], s_abco[threadIdx.x],
+                  s_rgb[threadIdx.x], s_box[threadIdx.x]);
             s_emit[threadIdx.x] = emit[p];
         }
         __syncthreads();
-        for (int k = cnt - 1; k >= 0; k--) {
-            float g[9];
+        for (int ch = (cnt - 1) >> 5; ch >= 0; ch--) {
+            const int k0 = ch * 32;
+            const int kk = k0 + lane;
+            const bool cand = kk < cnt && b0 + kk < warp_nc;
+            unsigned m = __ballot_sync(FULL, cand && wb.hits(s_box[cand ? kk : 0]));
+            unsigned written = 0;
+            while (m) {  // back to front inside the chunk
+                const int jb = 31 - __clz(m);
+                m &= ~(1u << jb);
+                const int k = k0 + jb;
+                float g[9];
 #pragma unroll
-            for (int c = 0; c < 9; c++) g[c] = 0.f;
-            bool contrib = false;
-            if (b0 + k < nc) {
-                const float2 xy = s_xy[k];
-                const float4 abco = s_abco[k];
-                const float dx = px - xy.x, dy = py - xy.y;
-                const float e = exponent2(abco, dx, dy);
-                if (!(e > 0.f)) {
-                    const float G = fast_exp2(e);
-                    const float og = __fmul_rn(abco.w, G);
-                    const float alpha = fminf(cfg.alpha_max, og);
-                    if (alpha >= cfg.alpha_min) {
-                        contrib = true;
-                        const float one_m = 1.f - alpha;
-                        T = T / one_m;  // transmittance in front of this Gaussian
-                        const float4 c = s_rgb[k];
-                        const float wgt = alpha * T;
-                        g[6] = wgt * gr; g[7] = wgt * gg; g[8] = wgt * gb;
-                        const float inv = 1.f / one_m;
-                        const float dalpha = gr * (T * c.x - (Sr + bgr) * inv) + gg * (T * c.y - (Sg + bgg) * inv) +
-                                             gb * (T * c.z - (Sb + bgb) * inv);
-                        Sr += wgt * c.x; Sg += wgt * c.y; Sb += wgt * c.z;
-                        if (og < cfg.alpha_max) {
-                            const float dpow = dalpha * og;  // d alpha / d(natural exponent) = o g
-                            const float q = -dpow * inv_log2e;  // (a dx + b dy) = -(2A dx + B dy)/log2(e)
-                            g[0] = q * (2.f * abco.x * dx + abco.y * dy);
-                            g[1] = q * (abco.y * dx + 2.f * abco.z * dy);
-                            g[2] = -0.5f * dpow * dx * dx;
-                            g[3] = -dpow * dx * dy;
-                            g[4] = -0.5f * dpow * dy * dy;
-                            g[5] = dalpha * G;
+                for (int c = 0; c < 9; c++) g[c] = 0.f;
+                bool contrib = false;
+                if (b0 + k < nc) {
+                    const float2 xy = s_xy[k];
+                    const float4 abco = s_abco[k];
+                    const float dx = px - xy.x, dy = py - xy.y;
+                    const float e = exponent2(abco, dx, dy);
+                    if (!(e > 0.f)) {
+                        const float G = fast_exp2(e);
+                        const float og = __fmul_rn(abco.w, G);
+                        const float alpha = fminf(cfg.alpha_max, og);
+                        if (alpha >= cfg.alpha_min) {
+                            contrib = true;
+                            const float one_m = 1.f - alpha;
+                            T = T / one_m;  // transmittance in front of this Gaussian
+                            const float4 c = s_rgb[k];
+                            const float wgt = alpha * T;
+                            g[6] = wgt * gr; g[7] = wgt * gg; g[8] = wgt * gb;
+                            const float inv = 1.f / one_m;
+                            const float dalpha = gr * (T * c.x - (Sr + bgr) * inv) +
+                                                 gg * (T * c.y - (Sg + bgg) * inv) +
+                                                 gb * (T * c.z - (Sb + bgb) * inv);
+                            Sr += wgt * c.x; Sg += wgt * c.y; Sb += wgt * c.z;
+                            if (og < cfg.alpha_max) {
+                                const float dpow = dalpha * og;  // d alpha / d(natural exponent) = o g
+                                const float q = -dpow * inv_log2e;  // (a dx + b dy) = -(2A dx + B dy)/log2(e)
+                                g[0] = q * (2.f * abco.x * dx + abco.y * dy);
+                                g[1] = q * (abco.y * dx + 2.f * abco.z * dy);
+                                g[2] = -0.5f * dpow * dx * dx;
+                                g[3] = -dpow * dx * dy;
+                                g[4] = -0.5f * dpow * dy * dy;
+                                g[5] = dalpha * G;
+                            }
                         }
                     }
                 }
+                if (__any_sync(FULL, contrib)) {
+                    const float r = warp_reduce9(g, lane);
+                    if (owner >= 0) s_part[w][k][owner] = r;
+                    written |= 1u << jb;
+                }
             }
-            if (__any_sync(0xffffffffu, contrib)) {
-                const float r = warp_reduce9(g, lane);
-                if (owner >= 0) s_part[w][k][owner] = r;
-            } else if (lane < 9) {
-                s_part[w][k][lane] = 0.f;
-            }
+            if (lane == 0) s_hit[w][ch] = written;
         }
         __syncthreads();
         if (threadIdx.x < cnt) {
+            const int ch = threadIdx.x >> 5;
+            const uint32_t bit = 1u << (threadIdx.x & 31);
             float a[9];
 #pragma unroll
-            for (int c = 0; c < 9; c++) a[c] = s_part[0][threadIdx.x][c];
+            for (int c = 0; c < 9; c++) a[c] = 0.f;
 #pragma unroll
-            for (int ww = 1; ww < kWarps; ww++)
+            for (int ww = 0; ww < kWarps; ww++)
+                if (s_hit[ww][ch] & bit)
 #pragma unroll
-                for (int c = 0; c < 9; c++) a[c] += s_part[ww][threadIdx.x][c];
+                    for (int c = 0; c < 9; c++) a[c] += s_part[ww][threadIdx.x][c];
             const uint32_t e = s_emit[threadIdx.x];
             if ((int64_t)e < capacity) {
                 part0[e] = make_float4(a[0], a[1], a[2], a[3]);
