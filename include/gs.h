@@ -238,6 +238,53 @@ int gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, const gs_projec
  * counter; diagnostics for benchmarks). */
 int64_t gs_launch_count(void);
 
+/* Direct spawn sampling settings (Sec. 4.2). sigma: standard deviation in
+ * pixels of the Gaussian n_sigma of the LoG operator (the paper leaves it
+ * unspecified; 1.0 here), 0.3 <= sigma <= 8/3. The mask draws
+ * u = Philox4x32-10(counter = (pixel index, frame, 0, 0), key = seed) and a
+ * pixel spawns iff u < P_s and its depth is positive and finite. */
+typedef struct gs_spawn_config {
+    float sigma;
+    uint32_t frame;
+    uint64_t seed;
+} gs_spawn_config;
+
+/* Spawned Gaussians, compacted in pixel order, in the gs_gaussians row layout
+ * (mean + opacity logit 0, log-scale x3, identity quaternion, SH DC from the
+ * pixel colour with the higher bands 0), plus the source pixel index (optional,
+ * may be NULL). count / status are device words as in gs_pairs. p_l, p_pen, p_s:
+ * optional [H*W] maps of Eq. 1, 2, 3 (NULL to skip). */
+typedef struct gs_spawn_out {
+    float* mean_opa;
+    float* scale;
+    float* quat;
+    float* sh;
+    int32_t* pixel;
+    int64_t capacity;
+    int64_t* count;
+    int32_t* status;
+    float* p_l;
+    float* p_pen;
+    float* p_s;
+} gs_spawn_out;
+
+size_t gs_spawn_workspace_size(int32_t width, int32_t height);
+
+/* Spawn proposal for a new frame (Sec. 4.2, Eq. 1-3 and the scale from the
+ * expected nearest-neighbour distance of a 2-D Poisson process of intensity
+ * P_L: s' = 1/(2 sqrt(P_L)) px, s = z s' / fx).
+ *   image   [3][height][width] in [0, 1], the new frame
+ *   render  [3][height][width] the current Gaussians rendered from the frame's
+ *           pose, or NULL when nothing has been reconstructed yet (P~ = 0)
+ *   depth   [height][width] depth per pixel (camera z) used for the new means
+ *   cam     device camera of the frame (world -> camera)
+ * The LoG kernel is the Laplacian of n_sigma sampled at integer offsets up to
+ * radius ceil(3 sigma), shifted to zero sum; borders replicate; the norm is
+ * over the three colour responses. */
+int gs_spawn_propose(const float* image, const float* render, const float* depth, int32_t width, int32_t height,
+                     const gs_camera* cam, const gs_spawn_config* sc, const gs_spawn_out* out, void* ws,
+                     size_t ws_bytes, void* stream);
+
 /* Learning rates of the parameter groups and the Adam constants. */
 typedef struct gs_adam_config {
     float lr_mean, lr_opacity, lr_scale, lr_rot, lr_sh_dc, lr_sh_rest;

@@ -707,3 +707,97 @@ void or_project_bwd(int64_t n, const double* mean_opa, const double* scale, cons
     }
     for (int c = 0; c < 6; c++) g_pose[c] = pose[c];
 }
+
+/* ---------------------------------------------------------------------------
+ * Direct spawn sampling (Sec. 4.2).
+ *
+ * P_L = min(|| LoG_sigma * I ||, 1)      (Eq. 1, norm over the RGB responses)
+ * P~  = min(|| LoG_sigma * I~ ||, 1)     (Eq. 2, I~ the render from the new pose)
+ * P_s = max(P_L - P~, 0)                 (Eq. 3)
+ * The LoG kernel is the continuous Laplacian of the Gaussian n_sigma sampled at
+ * integer offsets up to radius ceil(3 sigma), shifted to zero sum (so constant
+ * regions respond 0); borders replicate. Computed here as a direct 2-D
+ * convolution. The mask draws u = Philox4x32-10(counter = (pixel, frame, 0, 0),
+ * key = seed) -> top 24 bits of word 0 / 2^24 and spawns iff u < P_s.
+ * ------------------------------------------------------------------------- */
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two 32x32->64
+ * multiplications by M0, M1 with the key bumped by the Weyl constants W0, W1. */
+void or_philox4x32_10(const uint32_t* ctr_in, const uint32_t* key_in, uint32_t* out) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int r = 0; r < 10; r++) {
+        uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += W0; k1 += W1;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static double log_kernel_value(double x, double y, double s) {
+    double r2 = x * x + y * y, s2 = s * s;
+    return (r2 - 2 * s2) / (s2 * s2) * exp(-r2 / (2 * s2)) / (2 * PI_D * s2);
+}
+
+/* Fills the (2R+1)^2 zero-sum sampled LoG kernel; returns R. */
+int or_log_kernel(double sigma, double* k /* (2R+1)^2, R <= 12 */) {
+    int R = (int)ceil(3 * sigma);
+    int n = 2 * R + 1;
+    double sum = 0;
+    for (int j = -R; j <= R; j++)
+        for (int i = -R; i <= R; i++) sum += (k[(j + R) * n + (i + R)] = log_kernel_value(i, j, sigma));
+    for (int t = 0; t < n * n; t++) k[t] -= sum / (n * n);
+    return R;
+}
+
+static void log_norm_map(const double* img, int W, int H, const double* k, int R, double* out) {
+    int n = 2 * R + 1;
+    int64_t HW = (int64_t)W * H;
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < HW; p++) {
+        int x = (int)(p % W), y = (int)(p / W);
+        double acc2 = 0;
+        for (int ch = 0; ch < 3; ch++) {
+            double a = 0;
+            for (int j = -R; j <= R; j++) {
+                int yy = y + j < 0 ? 0 : (y + j >= H ? H - 1 : y + j);
+                for (int i = -R; i <= R; i++) {
+                    int xx = x + i < 0 ? 0 : (x + i >= W ? W - 1 : x + i);
+                    a += k[(j + R) * n + (i + R)] * img[ch * HW + (int64_t)yy * W + xx];
+                }
+            }
+            acc2 += a * a;
+        }
+        double v = sqrt(acc2);
+        out[p] = v < 1 ? v : 1;
+    }
+}
+
+/* image, render: [3][H][W] in [0, 1] (render may be NULL: nothing rendered yet,
+ * P~ = 0). Outputs per pixel: p_l, p_pen, p_s, u (the uniform draw), mask, and
+ * amb = 1 where |u - P_s| is within margin (the FP32 path may decide either way). */
+void or_spawn_maps(const double* image, const double* render, int W, int H, double sigma, uint64_t seed,
+                   uint32_t frame, double margin, double* p_l, double* p_pen, double* p_s, double* u, uint8_t* mask,
+                   uint8_t* amb) {
+    double k[25 * 25];
+    int R = or_log_kernel(sigma, k);
+    int64_t HW = (int64_t)W * H;
+    log_norm_map(image, W, H, k, R, p_l);
+    if (render) log_norm_map(render, W, H, k, R, p_pen);
+    else for (int64_t p = 0; p < HW; p++) p_pen[p] = 0;
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < HW; p++) {
+        double d = p_l[p] - p_pen[p];
+        p_s[p] = d > 0 ? d : 0;
+        uint32_t ctr[4] = {(uint32_t)p, frame, 0u, 0u}, o[4];
+        or_philox4x32_10(ctr, key, o);
+        u[p] = (double)(o[0] >> 8) / 16777216.0;
+        mask[p] = u[p] < p_s[p];
+        amb[p] = fabs(u[p] - p_s[p]) < margin;
+    }
+}

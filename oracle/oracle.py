@@ -47,6 +47,14 @@ def lib():
         _lib.or_project_bwd.argtypes = [C.c_int64, d, d, d, d, d, d, d, d, d, d, d, d, d]
         _lib.or_sh_basis.restype = None
         _lib.or_sh_basis.argtypes = [C.c_int, d, d, d]
+        u32 = np.ctypeslib.ndpointer(np.uint32, flags="C")
+        _lib.or_philox4x32_10.restype = None
+        _lib.or_philox4x32_10.argtypes = [u32, u32, u32]
+        _lib.or_log_kernel.restype = C.c_int
+        _lib.or_log_kernel.argtypes = [C.c_double, d]
+        _lib.or_spawn_maps.restype = None
+        _lib.or_spawn_maps.argtypes = [d, opt, C.c_int, C.c_int, C.c_double, C.c_uint64, C.c_uint32, C.c_double,
+                                       d, d, d, d, u8, u8]
     return _lib
 
 
@@ -272,6 +280,64 @@ def ambiguous_tiles(view: dict, cam, cfg: Config) -> np.ndarray:
             if xs.size and ys.size and _alpha_on(proj, i, xs, ys).max() >= thr:
                 bad[ry, cx] = True
     return bad
+
+
+# ---------------------------------------------------------------------------
+# Direct spawn sampling (Sec. 4.2, Eq. 1-3 and the expected-NN scale)
+# ---------------------------------------------------------------------------
+
+def philox4x32_10(ctr, key):
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def log_kernel(sigma):
+    k = np.zeros(25 * 25)
+    R = lib().or_log_kernel(sigma, k)
+    n = 2 * R + 1
+    return k[:n * n].reshape(n, n)
+
+
+def spawn_maps(image, render, sigma, seed, frame, margin=1e-5):
+    """P_L (Eq. 1), P~ (Eq. 2), P_s (Eq. 3), the uniform draws and the mask."""
+    image = _c(image, np.float64)
+    _, H, W = image.shape
+    out = {k: np.zeros((H, W)) for k in ("p_l", "p_pen", "p_s", "u")}
+    out["mask"] = np.zeros((H, W), np.uint8)
+    out["amb"] = np.zeros((H, W), np.uint8)
+    r = None if render is None else _c(render, np.float64)
+    lib().or_spawn_maps(image, None if r is None else r.ctypes.data, W, H, sigma, int(seed), int(frame), margin,
+                        out["p_l"], out["p_pen"], out["p_s"], out["u"], out["mask"], out["amb"])
+    return out
+
+
+def spawn(image, render, depth, cam, sigma, seed, frame, margin=1e-5):
+    """Spawned Gaussians, in pixel order: a pixel spawns iff its draw u < P_s
+    and its depth z is positive and finite. Each gets the mean back-projected
+    from the pixel centre at depth z, isotropic scale s = z s' / f with
+    s' = 1 / (2 sqrt(P_L)) (expected nearest-neighbour distance of a 2-D
+    Poisson process of intensity P_L), identity rotation, opacity 0.5 and the
+    pixel's colour as its SH DC term (higher bands 0)."""
+    m = spawn_maps(image, render, sigma, seed, frame, margin)
+    depth = np.asarray(depth, np.float64)
+    ok = (m["mask"] > 0) & np.isfinite(depth) & (depth > 0)
+    ys, xs = np.nonzero(ok)  # row-major = pixel order
+    z = depth[ys, xs]
+    pl = m["p_l"][ys, xs]
+    s_px = 1.0 / (2.0 * np.sqrt(pl))
+    s = z * s_px / cam["fx"]
+    pc = np.stack([(xs + 0.5 - cam["cx"]) * z / cam["fx"], (ys + 0.5 - cam["cy"]) * z / cam["fy"], z], 1)
+    R = np.asarray(cam["R"], np.float64)
+    t = np.asarray(cam["t"], np.float64)
+    mu = (pc - t) @ R  # R^T (p - t), row vectors
+    c0 = 0.5 / math.sqrt(math.pi)
+    rgb = np.asarray(image, np.float64)[:, ys, xs].T
+    n = len(xs)
+    out = dict(pixel=ys * image.shape[2] + xs, mean=mu, log_scale=np.repeat(np.log(s)[:, None], 3, 1),
+               quat=np.tile([1.0, 0, 0, 0], (n, 1)), opacity_logit=np.zeros(n), sh_dc=(rgb - 0.5) / c0,
+               scale_px=s_px, maps=m)
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -68,6 +68,9 @@ struct Carve {
 // Scratch bytes of the device-wide scan for up to n_max inputs.
 size_t scan_workspace_bytes(int64_t n_max);
 
+// Device-wide exclusive scan of n uint32 values; total (device) gets the sum.
+void scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, void* ws, cudaStream_t s);
+
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits
 // [0, bits), 8 bits per pass. The pair count is min(n_max, *n_dev). Buffers
 // (ka, va) hold the input; (kb, vb) are the alternates. Returns true when the

@@ -139,6 +139,10 @@ static void scan_exclusive(Load load, uint32_t* out, int64_t n_max, const uint32
     count_launch();
 }
 
+void scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, void* ws, cudaStream_t s) {
+    scan_exclusive(LoadU32{in}, out, n, nullptr, total, ws, s);
+}
+
 // ---------------------------------------------------------------------------
 // LSD radix sort, 8-bit digits, stable.
 // ---------------------------------------------------------------------------

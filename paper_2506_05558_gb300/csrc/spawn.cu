@@ -1,0 +1,211 @@
+// Direct spawn sampling (Sec. 4.2): per-pixel spawn probability from the norm
+// of the Laplacian-of-Gaussian response of the input image (Eq. 1), the same
+// quantity on the current render as a penalty (Eq. 2), their clamped
+// difference (Eq. 3), a Bernoulli mask drawn with a counter-based generator,
+// and, for every spawning pixel, a new Gaussian at the supplied depth with the
+// expected nearest-neighbour scale s = z / (2 f sqrt(P_L)).
+//
+// k_spawn_maps: one CTA per 16x16 pixel tile; the image and render tiles with
+// their halo are staged in shared memory and the (2R+1)^2 LoG taps (host-built,
+// passed by value) are applied directly. The mask is compacted in pixel order
+// with the device-wide scan, then k_spawn_emit writes the spawned rows.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace gs {
+
+constexpr int kSpT = 16;
+constexpr int kSpMaxR = 8;
+constexpr int kSpMaxTaps = (2 * kSpMaxR + 1) * (2 * kSpMaxR + 1);
+
+struct LogTaps {
+    int R;
+    float w[kSpMaxTaps];
+};
+
+// Philox4x32-10 (Salmon et al., SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += W0;
+        k.y += W1;
+    }
+    return c;
+}
+
+__device__ __forceinline__ void stage_tile(const float* __restrict__ img, int W, int H, int x0, int y0, int R,
+                                           float* s /* [3][S][S] */) {
+    const int S = kSpT + 2 * R;
+    const int64_t plane = (int64_t)W * H;
+    for (int i = threadIdx.x; i < 3 * S * S; i += blockDim.x) {
+        const int ch = i / (S * S), r = i % (S * S);
+        const int yy = min(max(y0 - R + r / S, 0), H - 1);
+        const int xx = min(max(x0 - R + r % S, 0), W - 1);
+        s[i] = img[ch * plane + (int64_t)yy * W + xx];
+    }
+}
+
+__device__ __forceinline__ float log_norm(const float* s, const LogTaps& k, int lx, int ly) {
+    const int R = k.R, S = kSpT + 2 * R, n = 2 * R + 1;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i < n; i++) {
+            const float w = k.w[j * n + i];
+            const int o = (ly + j) * S + (lx + i);
+            a0 += w * s[o];
+            a1 += w * s[S * S + o];
+            a2 += w * s[2 * S * S + o];
+        }
+    return fminf(sqrtf(a0 * a0 + a1 * a1 + a2 * a2), 1.f);
+}
+
+__global__ void __launch_bounds__(256) k_spawn_maps(const float* __restrict__ image, const float* __restrict__ render,
+                                                    const float* __restrict__ depth, int W, int H, LogTaps taps,
+                                                    uint2 key, uint32_t frame, float* __restrict__ p_l,
+                                                    float* __restrict__ p_pen, float* __restrict__ p_s,
+                                                    uint32_t* __restrict__ flag) {
+    extern __shared__ float s_tile[];  // image tile, then render tile
+    const int R = taps.R, S = kSpT + 2 * R;
+    const int x0 = blockIdx.x * kSpT, y0 = blockIdx.y * kSpT;
+    stage_tile(image, W, H, x0, y0, R, s_tile);
+    if (render) stage_tile(render, W, H, x0, y0, R, s_tile + 3 * S * S);
+    __syncthreads();
+    const int lx = threadIdx.x % kSpT, ly = threadIdx.x / kSpT;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x >= W || y >= H) return;
+    const int64_t p = (int64_t)y * W + x;
+    const float pl = log_norm(s_tile, taps, lx, ly);
+    const float pp = render ? log_norm(s_tile + 3 * S * S, taps, lx, ly) : 0.f;
+    const float ps = fmaxf(pl - pp, 0.f);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)p, frame, 0u, 0u), key);
+    const float u = (float)(r.x >> 8) * (1.f / 16777216.f);
+    const float z = depth[p];
+    flag[p] = (u < ps && z > 0.f && isfinite(z)) ? 1u : 0u;
+    if (p_l) p_l[p] = pl;
+    if (p_pen) p_pen[p] = pp;
+    if (p_s) p_s[p] = ps;
+}
+
+__global__ void __launch_bounds__(256) k_spawn_emit(const float* __restrict__ image, const float* __restrict__ depth,
+                                                    int W, int H, LogTaps taps, const uint32_t* __restrict__ flag,
+                                                    const uint32_t* __restrict__ pos, const gs_camera* __restrict__ cam,
+                                                    int64_t capacity, float4* __restrict__ mean_opa,
+                                                    float4* __restrict__ scale, float4* __restrict__ quat,
+                                                    float4* __restrict__ sh, int32_t* __restrict__ pixel) {
+    extern __shared__ float s_tile[];
+    const int R = taps.R;
+    const int x0 = blockIdx.x * kSpT, y0 = blockIdx.y * kSpT;
+    // P_L is recomputed from the image tile so the maps need not be stored
+    stage_tile(image, W, H, x0, y0, R, s_tile);
+    __syncthreads();
+    const int lx = threadIdx.x % kSpT, ly = threadIdx.x / kSpT;
+    const int x = x0 + lx, y = y0 + ly;
+    if (x >= W || y >= H) return;
+    const int64_t p = (int64_t)y * W + x;
+    if (!flag[p]) return;
+    const int64_t o = pos[p];
+    if (o >= capacity) return;
+    const float pl = log_norm(s_tile, taps, lx, ly);
+    const float z = depth[p];
+    const gs_camera& c = *cam;
+    const float s_px = 0.5f / sqrtf(pl);
+    const float s = z * s_px / c.fx;
+    const float xc = (x + 0.5f - c.cx) * z / c.fx, yc = (y + 0.5f - c.cy) * z / c.fy;
+    const float qx = xc - c.t[0], qy = yc - c.t[1], qz = z - c.t[2];
+    const float mx = c.R[0] * qx + c.R[3] * qy + c.R[6] * qz;  // R^T (p_cam - t)
+    const float my = c.R[1] * qx + c.R[4] * qy + c.R[7] * qz;
+    const float mz = c.R[2] * qx + c.R[5] * qy + c.R[8] * qz;
+    mean_opa[o] = make_float4(mx, my, mz, 0.f);  // opacity 0.5
+    const float ls = logf(s);
+    scale[o] = make_float4(ls, ls, ls, 0.f);
+    quat[o] = make_float4(1.f, 0.f, 0.f, 0.f);
+    const int64_t plane = (int64_t)W * H;
+    const float inv_c0 = 3.5449077018110318f;  // 1 / SH band-0 constant = 2 sqrt(pi)
+    float4* row = sh + 12 * o;
+    row[0] = make_float4((image[p] - 0.5f) * inv_c0, (image[plane + p] - 0.5f) * inv_c0,
+                         (image[2 * plane + p] - 0.5f) * inv_c0, 0.f);
+#pragma unroll
+    for (int r = 1; r < 12; r++) row[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pixel) pixel[o] = (int32_t)p;
+}
+
+__global__ void k_spawn_count(const uint32_t* total, int64_t capacity, int64_t* count, int32_t* status) {
+    *count = *total;
+    *status = (int64_t)*total > capacity ? GS_ERR_CAPACITY : GS_OK;
+}
+
+static bool make_taps(float sigma, LogTaps* t) {
+    if (!(sigma >= 0.3f) || !(sigma <= kSpMaxR / 3.f)) return false;
+    const int R = (int)std::ceil(3.0 * sigma);
+    const int n = 2 * R + 1;
+    const double s2 = (double)sigma * sigma;
+    double w[kSpMaxTaps], sum = 0;
+    for (int j = -R; j <= R; j++)
+        for (int i = -R; i <= R; i++) {
+            const double r2 = i * i + j * j;
+            const double v = (r2 - 2 * s2) / (s2 * s2) * std::exp(-r2 / (2 * s2)) / (2 * 3.14159265358979323846 * s2);
+            w[(j + R) * n + (i + R)] = v;
+            sum += v;
+        }
+    t->R = R;
+    for (int k = 0; k < n * n; k++) t->w[k] = (float)(w[k] - sum / (n * n));
+    return true;
+}
+
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" size_t gs_spawn_workspace_size(int32_t width, int32_t height) {
+    if (width <= 0 || height <= 0) return 0;
+    const int64_t hw = (int64_t)width * height;
+    Carve c{nullptr, 0, 0};
+    c.take<uint32_t>(hw);
+    c.take<uint32_t>(hw);
+    c.take<uint32_t>(4);
+    c.take<char>(scan_workspace_bytes(hw));
+    return c.used;
+}
+
+extern "C" int gs_spawn_propose(const float* image, const float* render, const float* depth, int32_t width,
+                                int32_t height, const gs_camera* cam, const gs_spawn_config* sc,
+                                const gs_spawn_out* out, void* ws, size_t ws_bytes, void* stream) {
+    if (!image || !depth || !cam || !sc || !out || width <= 0 || height <= 0) return GS_ERR_INVALID_ARG;
+    if (!out->count || !out->status || out->capacity < 0 ||
+        (out->capacity > 0 && (!out->mean_opa || !out->scale || !out->quat || !out->sh)))
+        return GS_ERR_INVALID_ARG;
+    const int64_t hw = (int64_t)width * height;
+    if (hw > (int64_t)UINT32_MAX) return GS_ERR_INVALID_ARG;
+    LogTaps taps;
+    if (!make_taps(sc->sigma, &taps)) return GS_ERR_INVALID_ARG;
+    Carve c{(char*)ws, 0, ws_bytes};
+    uint32_t* flag = c.take<uint32_t>(hw);
+    uint32_t* pos = c.take<uint32_t>(hw);
+    uint32_t* total = c.take<uint32_t>(4);
+    void* scan_ws = c.take<char>(scan_workspace_bytes(hw));
+    if (!ws || !c.ok() || ((uintptr_t)ws & 255)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int S = kSpT + 2 * taps.R;
+    const size_t smem = sizeof(float) * 3 * S * S * (render ? 2 : 1);
+    dim3 grid((unsigned)ceil_div(width, kSpT), (unsigned)ceil_div(height, kSpT));
+    const uint2 key = make_uint2((uint32_t)sc->seed, (uint32_t)(sc->seed >> 32));
+    k_spawn_maps<<<grid, 256, smem, s>>>(image, render, depth, width, height, taps, key, sc->frame, out->p_l,
+                                          out->p_pen, out->p_s, flag);
+    count_launch();
+    scan_exclusive_u32(flag, pos, hw, total, scan_ws, s);
+    k_spawn_count<<<1, 1, 0, s>>>(total, out->capacity, out->count, out->status);
+    count_launch();
+    if (out->capacity > 0) {
+        k_spawn_emit<<<grid, 256, sizeof(float) * 3 * S * S, s>>>(
+            image, depth, width, height, taps, flag, pos, cam, out->capacity, (float4*)out->mean_opa,
+            (float4*)out->scale, (float4*)out->quat, (float4*)out->sh, out->pixel);
+        count_launch();
+    }
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}

@@ -29,6 +29,7 @@ EXPORTS = [
     "gs_config_default", "gs_frame_init", "gs_project", "gs_sort_workspace_size", "gs_sort",
     "gs_render_workspace_size", "gs_render_fwd", "gs_backward_workspace_size", "gs_render_bwd",
     "gs_adam_step", "gs_pose_step", "gs_l1_loss", "gs_composite_bwd", "gs_project_bwd", "gs_launch_count",
+    "gs_spawn_workspace_size", "gs_spawn_propose",
 ]
 
 
@@ -81,6 +82,16 @@ class gs_adam_config(C.Structure):
                 ("eps", C.c_float)]
 
 
+class gs_spawn_config(C.Structure):
+    _fields_ = [("sigma", C.c_float), ("frame", C.c_uint32), ("seed", C.c_uint64)]
+
+
+class gs_spawn_out(C.Structure):
+    _fields_ = [("mean_opa", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("sh", C.c_void_p),
+                ("pixel", C.c_void_p), ("capacity", C.c_int64), ("count", C.c_void_p), ("status", C.c_void_p),
+                ("p_l", C.c_void_p), ("p_pen", C.c_void_p), ("p_s", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -120,6 +131,9 @@ def lib():
                                          C.POINTER(gs_frame), C.POINTER(gs_config), C.POINTER(gs_grads), P, P, P,
                                          C.c_size_t, P]),
             "gs_launch_count": (C.c_int64, []),
+            "gs_spawn_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
+            "gs_spawn_propose": (C.c_int, [P, P, P, C.c_int32, C.c_int32, P, C.POINTER(gs_spawn_config),
+                                           C.POINTER(gs_spawn_out), P, C.c_size_t, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -356,6 +370,43 @@ def gs_project_bwd(g: Gaussians, cams: torch.Tensor, p: Projected, pairs: Pairs,
 
 def gs_launch_count() -> int:
     return int(lib().gs_launch_count())
+
+
+@dataclass
+class Spawned:
+    """Spawned Gaussians (rows as in Gaussians) plus per-pixel maps."""
+    g: Gaussians
+    pixel: torch.Tensor
+    count: torch.Tensor
+    status: torch.Tensor
+    p_l: torch.Tensor | None = None
+    p_pen: torch.Tensor | None = None
+    p_s: torch.Tensor | None = None
+
+    @staticmethod
+    def alloc(capacity, hw=None, device="cuda") -> "Spawned":
+        maps = [torch.zeros((hw,), dtype=torch.float32, device=device) if hw else None for _ in range(3)]
+        return Spawned(Gaussians.zeros(max(capacity, 1), device), torch.zeros((max(capacity, 1),), dtype=torch.int32,
+                                                                                 device=device),
+                       torch.zeros((1,), dtype=torch.int64, device=device),
+                       torch.zeros((1,), dtype=torch.int32, device=device), *maps)
+
+    def c(self, capacity) -> gs_spawn_out:
+        return gs_spawn_out(_ptr(self.g.mean_opa), _ptr(self.g.scale), _ptr(self.g.quat), _ptr(self.g.sh),
+                            _ptr(self.pixel), capacity, _ptr(self.count), _ptr(self.status), _ptr(self.p_l),
+                            _ptr(self.p_pen), _ptr(self.p_s))
+
+
+def gs_spawn_workspace_size(width: int, height: int) -> int:
+    return int(lib().gs_spawn_workspace_size(width, height))
+
+
+def gs_spawn_propose(image: torch.Tensor, render, depth: torch.Tensor, width: int, height: int, cam: torch.Tensor,
+                     sigma: float, seed: int, frame: int, out: Spawned, ws: torch.Tensor, capacity=None, stream=None):
+    sc = gs_spawn_config(sigma, frame, seed)
+    oc = out.c(out.g.n if capacity is None else capacity)
+    _check(lib().gs_spawn_propose(_ptr(image), _ptr(render), _ptr(depth), width, height, _ptr(cam), C.byref(sc),
+                                  C.byref(oc), _ptr(ws), ws.numel(), _stream(stream)), "gs_spawn_propose")
 
 
 def adam_config(lr_mean=1.6e-4, lr_opacity=0.05, lr_scale=5e-3, lr_rot=1e-3, lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4,
