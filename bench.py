@@ -8,10 +8,13 @@ takes the L1 loss against the targets, runs the adjoint (Gaussian and SE(3)
 pose gradients), a sparse Adam step on the visible Gaussians and an Adam +
 retraction step on the poses. The metric counts view iterations: one
 iteration = project + sort + render forward + render backward (with pose) of
-one 1080p view. Inputs are synthetic (seeded), far larger than L2.
+one 1080p view. Inputs are synthetic (seeded) and far larger than L2.
 
-Two arms of the same step are timed: "batched" (all 8 views in each launch,
-the value reported) and "plain" (one launch sequence per view).
+Arms: "batched" (all views in each launch, launch configuration picked by the
+autotuner, the step replayed from CUDA graphs; the value reported) and
+"plain" (one launch sequence per view, default configuration). A second
+workload, 2M Gaussians over 16 views of uneven resolution, is reported under
+"uneven" with the same two arms.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -68,7 +71,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -109,21 +112,23 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# workload
+# workloads
 # ---------------------------------------------------------------------------
-def make_workload(torch, gs, synth, device, n=N_GAUSS, n_views=N_VIEWS):
+def make_workload(torch, gs, synth, device, n, n_views, sizes=None, seed=SEED):
+    """Scene, per-view sizes, true-pose targets (rendered by the path itself,
+    untimed), training Gaussians (means jittered by N(0, 0.01)) and perturbed
+    training poses."""
     from paper_2506_05558_gb300.raster import Rasterizer
-    sc, cams, rng = synth.multiview_scene(seed=SEED, n=n, n_views=n_views)
+    sc, cams, rng = synth.multiview_scene(seed=seed, n=n, n_views=n_views, sizes=sizes)
     sizes = [(c["width"], c["height"]) for c in cams]
     cfg = gs.config(sh_degree=3)
     g_true = gs.Gaussians.from_scene(sc, device)
     cams_true = gs.cameras_tensor(cams, device)
-    # targets: renders of the true scene from the true poses (setup, untimed)
     r = Rasterizer(n, sizes, capacity=1 << 20, cfg=cfg, device=device)
     p = r.fit_capacity(g_true, cams_true)
     r.forward(g_true, cams_true)
     targets = r.img.color.clone()
-    # training state: jittered means, perturbed poses
+    del r, g_true
     sc.mean_opa[:, :3] += rng.normal(0, 0.01, (n, 3)).astype(np.float32)
     g = gs.Gaussians.from_scene(sc, device)
     pert = []
@@ -131,84 +136,46 @@ def make_workload(torch, gs, synth, device, n=N_GAUSS, n_views=N_VIEWS):
         R, t = synth.perturb_pose(rng, c["R"].astype(np.float64), c["t"].astype(np.float64))
         pert.append(dict(c, R=R.astype(np.float32), t=t.astype(np.float32)))
     cams_train = gs.cameras_tensor(pert, device)
-    del r
     torch.cuda.synchronize()
-    return sc, sizes, cfg, g, cams_train, targets, p
+    return dict(sizes=sizes, cfg=cfg, g=g, cams=cams_train, targets=targets, pairs=p,
+                g0=[t.clone() for t in (g.mean_opa, g.scale, g.quat, g.sh)], cams0=cams_train.clone())
 
 
-class BatchedStep:
-    """All views per launch (the library's multi-view path)."""
-
-    STAGES = ("project", "sort", "render_fwd", "loss", "composite_bwd", "project_bwd", "adam", "pose")
-
-    def __init__(self, torch, gs, g, cams, sizes, targets, cfg, capacity, device):
-        from paper_2506_05558_gb300.raster import Rasterizer
-        self.torch, self.gs = torch, gs
-        self.g, self.cams, self.targets = g, cams, targets
-        self.r = Rasterizer(g.n, sizes, capacity, cfg, device)
-        self.m, self.v = gs.Gaussians.zeros(g.n, device), gs.Gaussians.zeros(g.n, device)
-        nv = len(sizes)
-        self.pm = torch.zeros((nv, 6), device=device)
-        self.pv = torch.zeros((nv, 6), device=device)
-        self.dL = torch.zeros_like(self.r.img.color)
-        self.loss = torch.zeros((1,), device=device)
-        self.ws_loss = gs.workspace(4 * 4096, device)
-        self.adam = gs.adam_config()
-        self.t = 0
-
-    def step(self, ev=None):
-        gs, r = self.gs, self.r
-        self.t += 1
-        rec = (lambda i: ev[i].record()) if ev is not None else (lambda i: None)
-        rec(0)
-        gs.gs_project(self.g, self.cams, r.f, r.cfg, r.proj)
-        rec(1)
-        gs.gs_sort(r.proj, r.n, r.f, r.pairs, r.ws_sort)
-        rec(2)
-        gs.gs_render_fwd(r.proj, r.pairs, r.f, r.cfg, r.img)
-        rec(3)
-        gs.gs_l1_loss(r.img.color, self.targets, self.dL, self.loss, self.ws_loss)
-        rec(4)
-        gs.gs_composite_bwd(r.proj, r.pairs, r.f, r.cfg, r.img, self.dL, r.n, r.ws_bwd)
-        rec(5)
-        gs.gs_project_bwd(self.g, self.cams, r.proj, r.pairs, r.f, r.cfg, r.grads, r.dpose, r.ws_bwd)
-        rec(6)
-        gs.gs_adam_step(self.g, r.grads, self.m, self.v, self.adam, self.t)
-        rec(7)
-        gs.gs_pose_step(self.cams, r.n_views, r.dpose, self.pm, self.pv, 1e-3, 1e-3, self.t)
-        rec(8)
-        return self.loss
+def reset(W):
+    g = W["g"]
+    for t, s in zip((g.mean_opa, g.scale, g.quat, g.sh), W["g0"]):
+        t.copy_(s)
+    W["cams"].copy_(W["cams0"])
 
 
 class PlainStep:
     """One launch sequence per view (views rendered one after another); the
     gradients of all views are accumulated before the single optimiser step."""
 
-    def __init__(self, torch, gs, g, cams, sizes, targets, cfg, capacity_per_view, device):
+    def __init__(self, torch, gs, W, device):
         from paper_2506_05558_gb300.raster import Rasterizer
-        self.torch, self.gs = torch, gs
-        self.g, self.targets = g, targets
-        self.sizes = sizes
-        nv = len(sizes)
-        self.cams = cams
-        cam_bytes = 72
-        self.cam_views = [cams[v * cam_bytes:(v + 1) * cam_bytes] for v in range(nv)]
+        self.gs = gs
+        self.g, self.cams, self.targets, self.sizes = W["g"], W["cams"], W["targets"], W["sizes"]
+        nv = len(self.sizes)
+        self.cam_views = [self.cams[v * 72:(v + 1) * 72] for v in range(nv)]
         self.rs = []
         for v in range(nv):
-            cfg_v = gs.config(sh_degree=cfg.sh_degree, accumulate=1 if v > 0 else 0)
-            self.rs.append(Rasterizer(g.n, [sizes[v]], capacity_per_view, cfg_v, device))
+            cfg_v = gs.config(sh_degree=W["cfg"].sh_degree, accumulate=1 if v > 0 else 0)
+            r = Rasterizer(self.g.n, [self.sizes[v]], 1 << 20, cfg_v, device)
+            r.fit_capacity(self.g, self.cam_views[v])
+            self.rs.append(r)
         self.grads = self.rs[0].grads
         for r in self.rs[1:]:
             r.grads = self.grads  # one accumulation buffer
         self.dpose = torch.zeros((nv, 6), device=device)
-        self.m, self.v = gs.Gaussians.zeros(g.n, device), gs.Gaussians.zeros(g.n, device)
+        self.m, self.v = gs.Gaussians.zeros(self.g.n, device), gs.Gaussians.zeros(self.g.n, device)
         self.pm = torch.zeros((nv, 6), device=device)
         self.pv = torch.zeros((nv, 6), device=device)
         self.dLs = [torch.zeros_like(r.img.color) for r in self.rs]
         self.loss = torch.zeros((nv,), device=device)
         self.ws_loss = gs.workspace(4 * 4096, device)
-        offs = np.cumsum([0] + [3 * w * h for w, h in sizes])
-        self.tgt = [targets[offs[v]:offs[v + 1]] for v in range(nv)]
+        offs = np.cumsum([0] + [3 * w * h for w, h in self.sizes])
+        self.tgt = [self.targets[offs[v]:offs[v + 1]] for v in range(nv)]
         self.adam = gs.adam_config()
         self.t = 0
 
@@ -219,13 +186,30 @@ class PlainStep:
             cam = self.cam_views[v]
             gs.gs_project(self.g, cam, r.f, r.cfg, r.proj)
             gs.gs_sort(r.proj, r.n, r.f, r.pairs, r.ws_sort)
-            gs.gs_render_fwd(r.proj, r.pairs, r.f, r.cfg, r.img)
+            gs.gs_render_fwd(r.proj, r.pairs, r.f, r.cfg, r.img, r.ws_render)
             gs.gs_l1_loss(r.img.color, self.tgt[v], self.dLs[v], self.loss[v:v + 1], self.ws_loss)
             gs.gs_render_bwd(self.g, cam, r.proj, r.pairs, r.f, r.cfg, r.img, self.dLs[v], self.grads,
                              self.dpose[v:v + 1], r.ws_bwd)
         gs.gs_adam_step(self.g, self.grads, self.m, self.v, self.adam, self.t)
         gs.gs_pose_step(self.cams, len(self.rs), self.dpose, self.pm, self.pv, 1e-3, 1e-3, self.t)
         return self.loss
+
+    def ok(self):
+        return all(r.status() == self.gs.GS_OK for r in self.rs)
+
+
+def timed(torch, fn, steps, barrier):
+    barrier()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    barrier()
+    return a.elapsed_time(b)
 
 
 # ---------------------------------------------------------------------------
@@ -250,16 +234,19 @@ def oracle_sample(n_views_sample=1, n=N_GAUSS):
 
 
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: each step is one 1080p view's fwd+bwd
+    (a bounded sample of the 8-view step) on the host cores."""
     if rank != 0:
         return 0
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state beyond the first build
     from oracle import build as ob
     ob.build()
+    for _ in range(min(args.warmup, 1)):
+        oracle_sample(1)
     vals = []
     t_all = time.perf_counter()
+    cores = 1
     for _ in range(args.steps):
-        v, dt, cores = oracle_sample(1)
+        _, dt, cores = oracle_sample(1)
         vals.append(dt)
     total = time.perf_counter() - t_all
     value = len(vals) / sum(vals)
@@ -290,6 +277,8 @@ def main():
     ap.add_argument("--views", type=int, default=N_VIEWS)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--cpu-views", type=int, default=3, help="views of the oracle CPU sample")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -304,7 +293,8 @@ def main():
 
     import torch
     import torch.distributed as dist
-    from paper_2506_05558_gb300 import gs, synth
+    from paper_2506_05558_gb300 import autotune, gs, synth
+    from paper_2506_05558_gb300.raster import JointOptimizer
 
     torch.cuda.set_device(local_rank)
     device = f"cuda:{local_rank}"
@@ -323,46 +313,63 @@ def main():
         return float(t.item())
 
     gs.lib()
-    sc, sizes, cfg, g, cams, targets, pairs_true = make_workload(torch, gs, synth, device, args.n, args.views)
-    g0 = [t.clone() for t in (g.mean_opa, g.scale, g.quat, g.sh)]
-    cams0 = cams.clone()
-    capacity = int(pairs_true * 1.3) + 4096
+    W = make_workload(torch, gs, synth, device, args.n, args.views)
+    capacity = int(W["pairs"] * 1.3) + 4096
 
-    # ---------------- batched arm ----------------
-    B = BatchedStep(torch, gs, g, cams, sizes, targets, cfg, capacity, device)
-    B.r.fit_capacity(g, cams)
-    for _ in range(args.warmup):
-        B.step()
+    # ---------------- launch configuration ----------------
+    tuned = None
+    cfg = W["cfg"]
+    if not args.no_autotune:
+        cfg, table = autotune.tune(W["g"], W["cams"], W["sizes"], W["targets"], W["cfg"], steps=2, device=device,
+                                   log=log)
+        tuned = {"tile": cfg.tile, "fwd_batch": cfg.fwd_batch, "bwd_batch": cfg.bwd_batch,
+                 "schedule": "persistent" if cfg.schedule == 1 else "grid",
+                 "trials": [{"tile": t, "fwd_batch": fb, "bwd_batch": bb, "schedule": sc, "ms": ms}
+                            for t, fb, bb, sc, ms in table]}
+        reset(W)
+
+    # ---------------- batched arm: per-stage CUDA graphs, events between them ----------------
+    J = JointOptimizer(W["g"], W["cams"], W["sizes"], W["targets"], capacity, cfg, device=device)
+    J.r.fit_capacity(W["g"], W["cams"])
+    J.step()  # one-time set-up outside the capture
     torch.cuda.synchronize()
-    assert B.r.status() == gs.GS_OK, "pair buffer overflow"
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(9)] for _ in range(args.steps)]
+    reset(W)
+    J.step_dev.fill_(1)
+    launches_per_step = gs.gs_launch_count()
+    J.step()
+    torch.cuda.synchronize()
+    launches_per_step = gs.gs_launch_count() - launches_per_step
+    J.capture(per_stage=True)
+    for _ in range(args.warmup):
+        J.replay()
+    torch.cuda.synchronize()
+    assert J.r.status() == gs.GS_OK, "pair buffer overflow"
+    n_ev = len(J.graphs) + 1
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(n_ev)] for _ in range(args.steps)]
     clocks = ClockSampler(local_rank)
-    launches0 = gs.gs_launch_count()
     barrier()
     torch.cuda.synchronize()
     clocks.start()
-    time.sleep(0.3)
+    time.sleep(0.25)
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     t_start.record()
     for k in range(args.steps):
-        B.step(ev[k])
+        J.replay(ev[k])
     t_end.record()
     torch.cuda.synchronize()
     barrier()
+    time.sleep(0.1)
     clk = clocks.stop()
-    launches = gs.gs_launch_count() - launches0
-    ms_local = t_start.elapsed_time(t_end)
-    ms = max_over_ranks(ms_local)
-    stage_ms = {s: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)]))
-                for i, s in enumerate(BatchedStep.STAGES)}
+    ms = max_over_ranks(t_start.elapsed_time(t_end))
+    stage_ms = {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)]))
+                for i, (name, _) in enumerate(J.graphs)}
     value = world * args.views * args.steps / (ms / 1000.0)
-    status = B.r.status()
-    # work counts of the last step (untimed accounting)
-    n_items_vis = int((B.r.proj.n_tiles > 0).sum().item())
-    P = B.r.pair_count()
-    K = int(B.r.img.n_contrib.to(torch.int64).sum().item())
-    loss = float(B.loss.item())
+    status = J.r.status()
+    n_items_vis = int((J.r.proj.n_tiles > 0).sum().item())
+    P = J.r.pair_count()
+    K = int(J.r.img.n_contrib.to(torch.int64).sum().item())
+    loss = float(J.loss.item())
 
     # ---------------- roofline of the dominant kernel ----------------
     peaks = {}
@@ -376,8 +383,8 @@ def main():
     algo = {
         "render_fwd": ("alu", FWD_FLOPS_PER_EVAL * K / 1e12, "TFLOP/s"),
         "composite_bwd": ("alu", BWD_FLOPS_PER_EVAL * K / 1e12, "TFLOP/s"),
-        "project": ("hbm", (16 * args.n * args.views + (224 + 56) * n_items_vis) / 1e9, "GB/s"),
-        "project_bwd": ("hbm", ((240 + 240) * args.n + (36 + 16) * n_items_vis + 36 * P) / 1e9, "GB/s"),
+        "project": ("hbm", (16 * args.n * args.views + (224 + 52) * n_items_vis) / 1e9, "GB/s"),
+        "project_bwd": ("hbm", ((240 + 240) * args.n + (36 + 12) * n_items_vis + 36 * P) / 1e9, "GB/s"),
         "adam": ("hbm", 7 * 240 * args.n / 1e9, "GB/s"),
     }
     stages = {}
@@ -390,70 +397,92 @@ def main():
             e.update({"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak})
         stages[s] = e
     dom = max(stage_ms, key=lambda s: stage_ms[s])
+    roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None}
     if dom in algo:
         d = stages[dom]
         roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
                 "frac": d["frac"], "traffic": None,
-                "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flop x median SM clock under load"
+                "peak_source": ("FP32 lanes: 152 SMs x 128 x 2 flop x median SM clock sampled under load"
                                 if d["bound"] == "alu" else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
-    else:
-        roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None}
+    del J
 
-    # ---------------- plain arm ----------------
+    # ---------------- plain arm: per-view launches ----------------
     plain = None
     if not args.no_plain:
-        for t, s in zip((g.mean_opa, g.scale, g.quat, g.sh), g0):
-            t.copy_(s)
-        cams.copy_(cams0)
-        cap_v = int(capacity / args.views * 1.6) + 4096
-        Pl = PlainStep(torch, gs, g, cams, sizes, targets, cfg, cap_v, device)
-        for r, cam in zip(Pl.rs, Pl.cam_views):
-            r.fit_capacity(g, cam)
+        reset(W)
+        Pl = PlainStep(torch, gs, W, device)
         for _ in range(args.warmup):
             Pl.step()
         torch.cuda.synchronize()
-        barrier()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(args.steps):
-            Pl.step()
-        b.record()
-        torch.cuda.synchronize()
-        barrier()
-        pms = max_over_ranks(a.elapsed_time(b))
-        plain = {"value": world * args.views * args.steps / (pms / 1000.0), "unit": UNIT, "ms_per_step": pms / args.steps,
-                 "status_ok": all(r.status() == gs.GS_OK for r in Pl.rs)}
+        pms = max_over_ranks(timed(torch, Pl.step, args.steps, barrier))
+        plain = {"value": world * args.views * args.steps / (pms / 1000.0), "unit": UNIT,
+                 "ms_per_step": pms / args.steps, "status_ok": Pl.ok(),
+                 "config": "tile 16, default batches, one CTA per tile, no graph"}
         del Pl
 
     # ---------------- end to end through the public API with host buffers ----------------
-    for t, s in zip((g.mean_opa, g.scale, g.quat, g.sh), g0):
-        t.copy_(s)
-    cams.copy_(cams0)
-    host_targets = targets.cpu().pin_memory()
+    reset(W)
+    host_targets = W["targets"].cpu().pin_memory()
     host_loss = torch.zeros((1,), dtype=torch.float32).pin_memory()
-    E = BatchedStep(torch, gs, g, cams, sizes, torch.empty_like(targets), cfg, capacity, device)
+    dev_targets = torch.empty_like(W["targets"])
+    E = JointOptimizer(W["g"], W["cams"], W["sizes"], dev_targets, capacity, cfg, device=device)
+
+    def e2e_step():
+        dev_targets.copy_(host_targets, non_blocking=True)
+        E.step()
+        host_loss.copy_(E.loss, non_blocking=True)
+
     for _ in range(args.warmup):
-        E.targets.copy_(host_targets, non_blocking=True)
-        E.step()
-        host_loss.copy_(E.loss, non_blocking=True)
+        e2e_step()
     torch.cuda.synchronize()
-    barrier()
-    a = torch.cuda.Event(enable_timing=True)
-    b = torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(args.steps):
-        E.targets.copy_(host_targets, non_blocking=True)
-        E.step()
-        host_loss.copy_(E.loss, non_blocking=True)
-    b.record()
-    torch.cuda.synchronize()
-    barrier()
-    ems = max_over_ranks(a.elapsed_time(b))
+    ems = max_over_ranks(timed(torch, e2e_step, args.steps, barrier))
     e2e = {"value": world * args.views * args.steps / (ems / 1000.0), "unit": UNIT,
-           "h2d_bytes_per_step": int(host_targets.numel() * 4), "d2h_bytes_per_step": 4}
-    del E
+           "h2d_bytes_per_step": int(host_targets.numel() * 4), "d2h_bytes_per_step": 4,
+           "path": "JointOptimizer.step() (C-ABI calls), targets copied from pinned host memory each step"}
+    del E, dev_targets
+
+    # ---------------- uneven views: 2M Gaussians, 16 views of mixed resolution ----------------
+    uneven = None
+    if not args.no_uneven:
+        del W
+        torch.cuda.empty_cache()
+        rng_sz = np.random.Generator(np.random.PCG64(SEED + 1 + 7919))
+        sizes_u = synth.uneven_sizes(rng_sz, 16)
+        U = make_workload(torch, gs, synth, device, 2 * args.n, 16, sizes=sizes_u, seed=SEED + 1)
+        cap_u = int(U["pairs"] * 1.3) + 4096
+        cfg_u = U["cfg"]
+        if not args.no_autotune:
+            cfg_u, _ = autotune.tune(U["g"], U["cams"], U["sizes"], U["targets"], U["cfg"], steps=2, device=device,
+                                     log=log)
+            reset(U)
+        Ju = JointOptimizer(U["g"], U["cams"], U["sizes"], U["targets"], cap_u, cfg_u, device=device)
+        Ju.r.fit_capacity(U["g"], U["cams"])
+        Ju.step()
+        torch.cuda.synchronize()
+        Ju.capture(per_stage=False)
+        for _ in range(args.warmup):
+            Ju.replay()
+        torch.cuda.synchronize()
+        ums = max_over_ranks(timed(torch, Ju.replay, args.steps, barrier))
+        u_ok = Ju.r.status() == gs.GS_OK
+        del Ju
+        reset(U)
+        Pu = PlainStep(torch, gs, U, device)
+        for _ in range(args.warmup):
+            Pu.step()
+        torch.cuda.synchronize()
+        pums = max_over_ranks(timed(torch, Pu.step, args.steps, barrier))
+        pix = sum(w * h for w, h in sizes_u)
+        uneven = {"workload": "2M Gaussians SH3, 16 views " + ",".join(f"{w}x{h}" for w, h in sizes_u),
+                  "unit": "Mpix fwd+bwd/s",
+                  "batched": {"value": world * pix * args.steps / (ums / 1000.0) / 1e6, "ms_per_step": ums / args.steps,
+                              "config": {"tile": cfg_u.tile, "fwd_batch": cfg_u.fwd_batch,
+                                         "bwd_batch": cfg_u.bwd_batch,
+                                         "schedule": "persistent" if cfg_u.schedule == 1 else "grid",
+                                         "graph": "whole step"}, "status_ok": u_ok},
+                  "plain": {"value": world * pix * args.steps / (pums / 1000.0) / 1e6,
+                            "ms_per_step": pums / args.steps, "status_ok": Pu.ok()}}
+        del Pu, U
 
     # ---------------- oracle on the host cores ----------------
     cpu = None
@@ -470,17 +499,18 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"joint pose+Gaussian optimisation step: {args.n} Gaussians SH3, {args.views} "
                                    f"views {WIDTH}x{HEIGHT}, L1 + adjoint with SE(3) pose gradients + sparse Adam",
-                       "arm": "batched (all views per launch)", "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "inputs larger than L2 (parameters+Adam state 0.7 GB, projected buffers "
-                             f"{args.views * args.n * 56 / 1e9:.2f} GB)"},
+                       "arm": "batched: all views per launch, CUDA graph per stage",
+                       "launch": tuned if tuned else "defaults", "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (parameters + Adam state 0.7 GB, projected buffers "
+                             f"{args.views * args.n * 52 / 1e9:.2f} GB)"},
             "plain": plain,
+            "uneven": uneven,
             "roofline": roof,
             "stages": stages,
-            "work": {"visible_items": n_items_vis, "pairs": P, "evaluations": K, "loss": loss,
-                     "status": status},
+            "work": {"visible_items": n_items_vis, "pairs": P, "evaluations": K, "loss": loss, "status": status},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": int(launches),
+            "gpu_launches": int(launches_per_step * args.steps),
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

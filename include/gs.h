@@ -64,7 +64,7 @@ typedef struct gs_camera {
 /* Rasterizer settings (the paper states none of these; the values in the
  * comments are the defaults of gs_config_default). */
 typedef struct gs_config {
-    int32_t tile;                 /* tile edge in pixels: 16 */
+    int32_t tile;                 /* tile edge in pixels, 8, 16 or 32 (must equal the frame's): 16 */
     int32_t sh_degree;            /* 0..3 */
     float near_z;                 /* cull if z <= near_z: 0.2 */
     float dilation;               /* screen-space low-pass added to Sigma2D: 0.3 px^2 */
@@ -77,7 +77,10 @@ typedef struct gs_config {
                                      pulling tiles, largest first, from a work queue */
     int32_t accumulate;           /* gs_render_bwd / gs_project_bwd: 0 overwrite the gradient
                                      buffers, 1 add to them (per-view launches of one step): 0 */
-    int32_t reserved;
+    int32_t fwd_batch;            /* Gaussians staged per round in gs_render_fwd: 0 = default;
+                                     tile 8: 64/128/256, tile 16: 64/128/256, tile 32: 128/256 */
+    int32_t bwd_batch;            /* the same for the adjoint: 0 = default; tile 8: 64/128/256,
+                                     tile 16: 32/64/128, tile 32: 32 */
 } gs_config;
 
 void gs_config_default(gs_config* cfg);
@@ -99,7 +102,7 @@ typedef struct gs_frame {
     int64_t pix_base[GS_MAX_VIEWS + 1];
 } gs_frame;
 
-/* Fills f from host arrays width[n_views], height[n_views]. tile must be 16.
+/* Fills f from host arrays width[n_views], height[n_views]. tile: 8, 16 or 32.
  * Returns GS_ERR_INVALID_ARG for n_views outside 1..GS_MAX_VIEWS, a
  * non-positive size or more than 2^31 tiles or pixels in total. */
 int gs_frame_init(gs_frame* f, int32_t n_views, const int32_t* width, const int32_t* height, int32_t tile);
@@ -147,7 +150,9 @@ int gs_project(const gs_gaussians* g, const gs_camera* cams, const gs_frame* f, 
  *   range   [2 * total tiles]  [start, end) of each tile's pairs in src/emit
  *   count   device int64[1]: number of pairs (written by gs_sort)
  *   status  device int32[1]: GS_OK, or GS_ERR_CAPACITY if count > capacity (then
- *           only the first `capacity` pairs exist and renders are incomplete) */
+ *           only the first `capacity` pairs exist and renders are incomplete)
+ *   order   [total tiles] optional (NULL to skip): tile indices by decreasing
+ *           pair count (stable), the work order of the persistent schedule */
 typedef struct gs_pairs {
     uint32_t* src;
     uint32_t* emit;
@@ -156,6 +161,7 @@ typedef struct gs_pairs {
     int64_t capacity;
     int64_t* count;
     int32_t* status;
+    uint32_t* order;
 } gs_pairs;
 
 /* Scratch bytes gs_sort needs for n Gaussians, the frame's views and a pair
@@ -292,15 +298,23 @@ typedef struct gs_adam_config {
 } gs_adam_config;
 
 /* Sparse Adam over Gaussians with visible[g] != 0 (others untouched); params,
- * m, v in the gs_gaussians layout; step >= 1 (bias correction). */
+ * m, v in the gs_gaussians layout. The step number (>= 1, for the bias
+ * correction) is `step`, or, when step_dev is non-NULL, the device int32 it
+ * points to (so a captured CUDA graph sees the current step; advance it with
+ * gs_counter_add). */
 int gs_adam_step(const gs_gaussians* params, const gs_grads* grads, const gs_gaussians* m, const gs_gaussians* v,
-                 const gs_adam_config* cfg, int32_t step, void* stream);
+                 const gs_adam_config* cfg, int32_t step, const int32_t* step_dev, void* stream);
 
 /* Pose update: Adam on the tangent gradient dL_dpose [n_views][6] with moments
  * m, v [n_views][6], then T_cw <- exp(delta^) T_cw with delta the Adam step;
- * cams updated in place. lr_t for rho, lr_r for phi. */
+ * cams updated in place. lr_t for rho, lr_r for phi. step / step_dev as for
+ * gs_adam_step. */
 int gs_pose_step(gs_camera* cams, int32_t n_views, const float* dL_dpose, float* m, float* v, float lr_t,
-                 float lr_r, float beta1, float beta2, float eps, int32_t step, void* stream);
+                 float lr_r, float beta1, float beta2, float eps, int32_t step, const int32_t* step_dev,
+                 void* stream);
+
+/* counter[0] += delta on the device (advances a graph-visible step counter). */
+int gs_counter_add(int32_t* counter, int32_t delta, void* stream);
 
 /* L1 loss: loss[0] = sum |color - target| / count (deterministic reduction),
  * dL_dcolor = sign(color - target) / count. ws: 4 * 4096 bytes. */

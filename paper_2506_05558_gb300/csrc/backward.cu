@@ -385,11 +385,12 @@ __global__ void __launch_bounds__(256) k_pose_reduce(const float* __restrict__ p
 
 int launch_render_bwd(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
                       const gs_image* fwd, const float* dL_dcolor, float4* part0, float4* part1, float* part2,
-                      cudaStream_t s);
+                      uint32_t* counter, cudaStream_t s);
 
 struct BwdWs {
     float4 *part0, *part1;
     float *part2, *pose_part;
+    uint32_t* counter;
 };
 
 static BwdWs carve_bwd(char* base, size_t cap, int64_t n, int n_views, int64_t capacity, size_t* used) {
@@ -399,6 +400,7 @@ static BwdWs carve_bwd(char* base, size_t cap, int64_t n, int n_views, int64_t c
     w.part1 = c.take<float4>(capacity);
     w.part2 = c.take<float>(capacity);
     w.pose_part = c.take<float>((size_t)n_views * ceil_div(n, kPBGauss) * 6);
+    w.counter = c.take<uint32_t>(4);
     *used = c.used;
     return w;
 }
@@ -415,7 +417,7 @@ extern "C" size_t gs_backward_workspace_size(int64_t n, const gs_frame* f, int64
 }
 
 static int check_bwd_common(const gs_frame* f, const gs_config* cfg) {
-    if (!f || !cfg || f->n_views < 1 || f->n_views > GS_MAX_VIEWS || f->tile != 16 || cfg->tile != 16 ||
+    if (!f || !cfg || f->n_views < 1 || f->n_views > GS_MAX_VIEWS || cfg->tile != f->tile ||
         cfg->sh_degree < 0 || cfg->sh_degree > 3)
         return GS_ERR_INVALID_ARG;
     return GS_OK;
@@ -429,7 +431,8 @@ extern "C" int gs_composite_bwd(const gs_projected* p, const gs_pairs* pairs, co
     BwdWs w = carve_bwd((char*)ws, ws_bytes, n, f->n_views, pairs->capacity, &need);
     if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) return GS_ERR_INVALID_ARG;
     if (n == 0) return GS_OK;
-    return launch_render_bwd(p, pairs, f, cfg, fwd, dL_dcolor, w.part0, w.part1, w.part2, (cudaStream_t)stream);
+    return launch_render_bwd(p, pairs, f, cfg, fwd, dL_dcolor, w.part0, w.part1, w.part2, w.counter,
+                             (cudaStream_t)stream);
 }
 
 extern "C" int gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, const gs_projected* p,

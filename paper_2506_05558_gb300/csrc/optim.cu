@@ -16,9 +16,14 @@ __global__ void __launch_bounds__(256) k_adam(float4* __restrict__ p_mo, float4*
                                               float4* __restrict__ v_mo, float4* __restrict__ v_sc,
                                               float4* __restrict__ v_q, float4* __restrict__ v_sh,
                                               const uint8_t* __restrict__ visible, int64_t n, gs_adam_config c,
-                                              float bc1, float bc2) {
+                                              float bc1, float bc2, const int32_t* __restrict__ step_dev) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 15 * n) return;
+    if (step_dev) {  // bias corrections of the step number held on the device
+        const float t = (float)*step_dev;
+        bc1 = 1.f - powf(c.beta1, t);
+        bc2 = 1.f - powf(c.beta2, t);
+    }
     int64_t g, row;
     float4 *P, *M, *V;
     const float4* G;
@@ -57,9 +62,15 @@ __global__ void __launch_bounds__(256) k_adam(float4* __restrict__ p_mo, float4*
 
 // One thread per view: Adam on the 6-vector, then T_cw <- exp(delta^) T_cw.
 __global__ void k_pose_step(gs_camera* cams, int nv, const float* __restrict__ grad, float* m, float* v, float lr_t,
-                            float lr_r, float b1, float b2, float eps, float bc1, float bc2) {
+                            float lr_r, float b1, float b2, float eps, float bc1, float bc2,
+                            const int32_t* __restrict__ step_dev) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nv) return;
+    if (step_dev) {
+        const float t = (float)*step_dev;
+        bc1 = 1.f - powf(b1, t);
+        bc2 = 1.f - powf(b2, t);
+    }
     float d[6];
     for (int k = 0; k < 6; k++) {
         const float g = grad[6 * i + k];
@@ -156,31 +167,45 @@ __global__ void __launch_bounds__(1024) k_l1_final(const float* __restrict__ par
 
 using namespace gs;
 
+__global__ void k_counter_add(int32_t* c, int32_t d) { *c += d; }
+
+extern "C" int gs_counter_add(int32_t* counter, int32_t delta, void* stream) {
+    if (!counter) return GS_ERR_INVALID_ARG;
+    k_counter_add<<<1, 1, 0, (cudaStream_t)stream>>>(counter, delta);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
 extern "C" int gs_adam_step(const gs_gaussians* params, const gs_grads* grads, const gs_gaussians* m,
-                            const gs_gaussians* v, const gs_adam_config* cfg, int32_t step, void* stream) {
-    if (!params || !grads || !m || !v || !cfg || step < 1 || params->n < 0) return GS_ERR_INVALID_ARG;
+                            const gs_gaussians* v, const gs_adam_config* cfg, int32_t step, const int32_t* step_dev,
+                            void* stream) {
+    if (!params || !grads || !m || !v || !cfg || (step < 1 && !step_dev) || params->n < 0) return GS_ERR_INVALID_ARG;
     if (m->n != params->n || v->n != params->n || !grads->visible) return GS_ERR_INVALID_ARG;
     const int64_t n = params->n;
     if (n == 0) return GS_OK;
-    const float bc1 = (float)(1.0 - pow((double)cfg->beta1, step));
-    const float bc2 = (float)(1.0 - pow((double)cfg->beta2, step));
+    const float bc1 = (float)(1.0 - pow((double)cfg->beta1, step < 1 ? 1 : step));
+    const float bc2 = (float)(1.0 - pow((double)cfg->beta2, step < 1 ? 1 : step));
     k_adam<<<(unsigned)ceil_div(15 * n, 256), 256, 0, (cudaStream_t)stream>>>(
         (float4*)params->mean_opa, (float4*)params->scale, (float4*)params->quat, (float4*)params->sh,
         (const float4*)grads->mean_opa, (const float4*)grads->scale, (const float4*)grads->quat,
         (const float4*)grads->sh, (float4*)m->mean_opa, (float4*)m->scale, (float4*)m->quat, (float4*)m->sh,
-        (float4*)v->mean_opa, (float4*)v->scale, (float4*)v->quat, (float4*)v->sh, grads->visible, n, *cfg, bc1, bc2);
+        (float4*)v->mean_opa, (float4*)v->scale, (float4*)v->quat, (float4*)v->sh, grads->visible, n, *cfg, bc1, bc2,
+        step_dev);
     count_launch();
     GS_CUDA_CHECK_LAUNCH();
     return GS_OK;
 }
 
 extern "C" int gs_pose_step(gs_camera* cams, int32_t n_views, const float* dL_dpose, float* m, float* v, float lr_t,
-                            float lr_r, float beta1, float beta2, float eps, int32_t step, void* stream) {
-    if (!cams || !dL_dpose || !m || !v || n_views < 1 || n_views > GS_MAX_VIEWS || step < 1) return GS_ERR_INVALID_ARG;
-    const float bc1 = (float)(1.0 - pow((double)beta1, step));
-    const float bc2 = (float)(1.0 - pow((double)beta2, step));
+                            float lr_r, float beta1, float beta2, float eps, int32_t step, const int32_t* step_dev,
+                            void* stream) {
+    if (!cams || !dL_dpose || !m || !v || n_views < 1 || n_views > GS_MAX_VIEWS || (step < 1 && !step_dev))
+        return GS_ERR_INVALID_ARG;
+    const float bc1 = (float)(1.0 - pow((double)beta1, step < 1 ? 1 : step));
+    const float bc2 = (float)(1.0 - pow((double)beta2, step < 1 ? 1 : step));
     k_pose_step<<<1, 64, 0, (cudaStream_t)stream>>>(cams, n_views, dL_dpose, m, v, lr_t, lr_r, beta1, beta2, eps, bc1,
-                                                    bc2);
+                                                    bc2, step_dev);
     count_launch();
     GS_CUDA_CHECK_LAUNCH();
     return GS_OK;

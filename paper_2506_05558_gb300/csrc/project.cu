@@ -137,18 +137,20 @@ extern "C" void gs_config_default(gs_config* cfg) {
     cfg->pose_grad_through_sh = 0;
     cfg->schedule = 0;
     cfg->accumulate = 0;
-    cfg->reserved = 0;
+    cfg->fwd_batch = 0;
+    cfg->bwd_batch = 0;
 }
 
 extern "C" int gs_frame_init(gs_frame* f, int32_t n_views, const int32_t* width, const int32_t* height,
                              int32_t tile) {
-    if (!f || !width || !height || n_views < 1 || n_views > GS_MAX_VIEWS || tile != 16) return GS_ERR_INVALID_ARG;
+    if (!f || !width || !height || n_views < 1 || n_views > GS_MAX_VIEWS || (tile != 8 && tile != 16 && tile != 32))
+        return GS_ERR_INVALID_ARG;
     memset(f, 0, sizeof(*f));
     f->n_views = n_views;
     f->tile = tile;
     int64_t tb = 0, pb = 0;
     for (int v = 0; v < n_views; v++) {
-        if (width[v] <= 0 || height[v] <= 0 || width[v] > 65535 * 16 || height[v] > 65535 * 16)
+        if (width[v] <= 0 || height[v] <= 0 || width[v] > 65535 * tile || height[v] > 65535 * tile)
             return GS_ERR_INVALID_ARG;
         f->width[v] = width[v];
         f->height[v] = height[v];

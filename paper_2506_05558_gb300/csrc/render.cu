@@ -1,53 +1,54 @@
 // Front-to-back alpha compositing (K5) and its adjoint (K6).
 //
-// One CTA of 256 threads per 16x16 tile, one pixel per thread; each warp owns
-// an 8x4 block of pixels so a small splat touches few warps. Each tile's
-// depth-ordered list is walked in batches staged in shared memory (128-bit
-// loads of the projected rows). While staging, each Gaussian gets the bounding
-// box of the region where its alpha can reach alpha_min; a warp tests 32
-// staged boxes against its 8x4 block with one ballot and evaluates only the
-// hits, so Gaussians that cannot touch any of its pixels cost nothing. The
-// forward stops a CTA when every pixel's transmittance has terminated; the
-// adjoint recomputes the
-// blending state back to front from T_final and n_contrib, reduces each
-// Gaussian's 9 partial derivatives across the warp with a transposing
-// butterfly (12 shuffles for 9 values), sums the 8 warps in a fixed order and
-// writes ONE partial per (tile, Gaussian) pair to the pair's emission slot. No
-// atomics touch gradients, so results are bit-reproducible.
+// One CTA of TILE x TILE threads per tile (TILE = 8, 16 or 32), one pixel per
+// thread; each warp owns an 8x4 block of pixels so a small splat touches few
+// warps. Each tile's depth-ordered list is walked in batches staged in shared
+// memory (128-bit loads of the projected rows). While staging, each Gaussian
+// gets the bounding box of the region where its alpha can reach alpha_min; a
+// warp tests 32 staged boxes against its 8x4 block with one ballot and
+// evaluates only the hits, so Gaussians that cannot touch any of its pixels
+// cost nothing. The forward stops a CTA when every pixel's transmittance has
+// terminated. The adjoint recomputes the blending state back to front from
+// T_final and n_contrib, reduces each Gaussian's 9 partial derivatives across
+// the warp with a transposing butterfly (12 shuffles for 9 values), sums the
+// warps in a fixed order and writes ONE partial per (tile, Gaussian) pair to
+// the pair's emission slot. No atomics touch gradients: bit-reproducible.
+//
+// Scheduling: either one CTA per tile (grid order), or persistent CTAs (as
+// many as fit on the SMs) that pull tiles from a global counter in the order
+// gs_sort produced (largest pair list first), which evens out the tail when
+// views of very different sizes and densities share one launch. The counter
+// only hands out work; every loop is bounded by the tile count.
 #include "common.cuh"
 
 namespace gs {
 
-constexpr int kTile = 16;
-constexpr int kThreads = 256;
-constexpr int kFwdBatch = 256;
-constexpr int kBwdBatch = 128;
-constexpr int kWarps = kThreads / 32;
-
-// Pixel of this thread inside the tile: warp w covers an 8x4 block.
-__device__ __forceinline__ void tile_pixel(int tid, int& lx, int& ly) {
-    const int lane = tid & 31, w = tid >> 5;
-    lx = (w & 1) * 8 + (lane & 7);
-    ly = (w >> 1) * 4 + (lane >> 3);
-}
+template <int TILE>
+struct Geom {
+    static constexpr int kThreads = TILE * TILE;
+    static constexpr int kWarps = kThreads / 32;
+    static constexpr int kWX = TILE / 8;  // 8x4 warp blocks per tile row
+};
 
 struct TileInfo {
     int view, px, py, W, H;
     bool inside;
-    int64_t pix;        // pixel index within all views
-    int64_t plane;      // H*W of the view
-    int64_t color_base; // 3 * pix_base[view]
+    int64_t pix;         // pixel index within all views
+    int64_t plane;       // H*W of the view
+    int64_t color_base;  // index of this pixel's red value in the colour buffer
 };
 
+template <int TILE>
 __device__ __forceinline__ TileInfo tile_info(const gs_frame& f, int tile) {
     TileInfo t;
     t.view = view_of_tile(f, tile);
     const int local = tile - f.tile_base[t.view];
     const int tx = local % f.tiles_x[t.view], ty = local / f.tiles_x[t.view];
-    int lx, ly;
-    tile_pixel(threadIdx.x, lx, ly);
-    t.px = tx * kTile + lx;
-    t.py = ty * kTile + ly;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lx = (w % Geom<TILE>::kWX) * 8 + (lane & 7);
+    const int ly = (w / Geom<TILE>::kWX) * 4 + (lane >> 3);
+    t.px = tx * TILE + lx;
+    t.py = ty * TILE + ly;
     t.W = f.width[t.view];
     t.H = f.height[t.view];
     t.inside = t.px < t.W && t.py < t.H;
@@ -106,66 +107,90 @@ __device__ __forceinline__ float exponent2(const float4& abco, float dx, float d
                      __fmaf_rn(__fmul_rn(abco.z, dy), dy, __fmul_rn(__fmul_rn(abco.y, dx), dy)));
 }
 
-__global__ void __launch_bounds__(kThreads) k_render_fwd(gs_frame f, gs_config cfg, const uint32_t* __restrict__ range,
-                                                         const uint32_t* __restrict__ src,
-                                                         const float2* __restrict__ mean2d,
-                                                         const float4* __restrict__ conic_opa,
-                                                         const float4* __restrict__ rgb_depth,
-                                                         float* __restrict__ color, float* __restrict__ t_final,
-                                                         int32_t* __restrict__ n_contrib) {
-    __shared__ float2 s_xy[kFwdBatch];
-    __shared__ float4 s_abco[kFwdBatch];
-    __shared__ float4 s_rgb[kFwdBatch];
-    __shared__ float4 s_box[kFwdBatch];
+// Next tile for this CTA: its own (grid schedule, first call only) or the next
+// entry of the work order (persistent schedule). Returns -1 when done.
+__device__ __forceinline__ int next_tile(const uint32_t* __restrict__ order, uint32_t* counter, int n_tiles,
+                                         bool first, int* s_item) {
+    if (!order) return first ? (int)blockIdx.x : -1;
+    if (threadIdx.x == 0) {
+        const uint32_t it = atomicAdd(counter, 1u);
+        *s_item = it < (uint32_t)n_tiles ? (int)order[it] : -1;
+    }
+    __syncthreads();
+    const int t = *s_item;
+    __syncthreads();
+    return t;
+}
+
+template <int TILE, int FB>
+__global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_config cfg,
+                                                            const uint32_t* __restrict__ range,
+                                                            const uint32_t* __restrict__ src,
+                                                            const float2* __restrict__ mean2d,
+                                                            const float4* __restrict__ conic_opa,
+                                                            const float4* __restrict__ rgb_depth,
+                                                            float* __restrict__ color, float* __restrict__ t_final,
+                                                            int32_t* __restrict__ n_contrib,
+                                                            const uint32_t* __restrict__ order, uint32_t* counter,
+                                                            int n_tiles) {
+    constexpr int NT = Geom<TILE>::kThreads;
+    __shared__ float2 s_xy[FB];
+    __shared__ float4 s_abco[FB];
+    __shared__ float4 s_rgb[FB];
+    __shared__ float4 s_box[FB];
+    __shared__ int s_item;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int tile = blockIdx.x;
-    const TileInfo ti = tile_info(f, tile);
-    const WarpBlock wb = warp_block(ti);
-    const float px = ti.px + 0.5f, py = ti.py + 0.5f;
-    const uint32_t start = range[2 * tile], end = range[2 * tile + 1];
-    float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
-    int last = 0;
-    bool done = !ti.inside;
-    for (uint32_t b0 = start; b0 < end; b0 += kFwdBatch) {
-        if (__syncthreads_count(done) == kThreads) break;
-        const uint32_t j = b0 + threadIdx.x;
-        if (j < end)
-            stage(mean2d, conic_opa, rgb_depth, src[j], cfg.alpha_min, s_xy[threadIdx.x], s_abco[threadIdx.x],
-                  s_rgb[threadIdx.x], s_box[threadIdx.x]);
-        __syncthreads();
-        const int cnt = min((uint32_t)kFwdBatch, end - b0);
-        for (int k0 = 0; k0 < cnt; k0 += 32) {
-            if (__all_sync(FULL, done)) break;
-            const int kk = k0 + lane;
-            unsigned m = __ballot_sync(FULL, kk < cnt && wb.hits(s_box[kk < cnt ? kk : 0]));
-            while (m) {
-                const int k = k0 + __ffs(m) - 1;
-                m &= m - 1;
-                if (done) continue;
-                const float2 xy = s_xy[k];
-                const float4 abco = s_abco[k];
-                const float e = exponent2(abco, px - xy.x, py - xy.y);
-                if (e > 0.f) continue;
-                const float og = __fmul_rn(abco.w, fast_exp2(e));
-                const float alpha = fminf(cfg.alpha_max, og);
-                if (alpha < cfg.alpha_min) continue;
-                const float nT = __fmul_rn(T, 1.f - alpha);
-                if (nT < cfg.t_min) { done = true; continue; }
-                const float4 c = s_rgb[k];
-                const float w = alpha * T;
-                cr += w * c.x; cg += w * c.y; cb += w * c.z;
-                T = nT;
-                last = (int)(b0 - start) + k + 1;
+    for (int tile = next_tile(order, counter, n_tiles, true, &s_item); tile >= 0;
+         tile = next_tile(order, counter, n_tiles, false, &s_item)) {
+        const TileInfo ti = tile_info<TILE>(f, tile);
+        const WarpBlock wb = warp_block(ti);
+        const float px = ti.px + 0.5f, py = ti.py + 0.5f;
+        const uint32_t start = range[2 * tile], end = range[2 * tile + 1];
+        float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
+        int last = 0;
+        bool done = !ti.inside;
+        for (uint32_t b0 = start; b0 < end; b0 += FB) {
+            if (__syncthreads_count(done) == NT) break;
+            for (int j = threadIdx.x; j < FB; j += NT)
+                if (b0 + j < end)
+                    stage(mean2d, conic_opa, rgb_depth, src[b0 + j], cfg.alpha_min, s_xy[j], s_abco[j], s_rgb[j],
+                          s_box[j]);
+            __syncthreads();
+            const int cnt = min((uint32_t)FB, end - b0);
+            for (int k0 = 0; k0 < cnt; k0 += 32) {
+                if (__all_sync(FULL, done)) break;
+                const int kk = k0 + lane;
+                unsigned m = __ballot_sync(FULL, kk < cnt && wb.hits(s_box[kk < cnt ? kk : 0]));
+                while (m) {
+                    const int k = k0 + __ffs(m) - 1;
+                    m &= m - 1;
+                    if (done) continue;
+                    const float2 xy = s_xy[k];
+                    const float4 abco = s_abco[k];
+                    const float e = exponent2(abco, px - xy.x, py - xy.y);
+                    if (e > 0.f) continue;
+                    const float og = __fmul_rn(abco.w, fast_exp2(e));
+                    const float alpha = fminf(cfg.alpha_max, og);
+                    if (alpha < cfg.alpha_min) continue;
+                    const float nT = __fmul_rn(T, 1.f - alpha);
+                    if (nT < cfg.t_min) { done = true; continue; }
+                    const float4 c = s_rgb[k];
+                    const float w = alpha * T;
+                    cr += w * c.x; cg += w * c.y; cb += w * c.z;
+                    T = nT;
+                    last = (int)(b0 - start) + k + 1;
+                }
             }
         }
-    }
-    if (ti.inside) {
-        color[ti.color_base] = cr + T * cfg.bg[0];
-        color[ti.color_base + ti.plane] = cg + T * cfg.bg[1];
-        color[ti.color_base + 2 * ti.plane] = cb + T * cfg.bg[2];
-        t_final[ti.pix] = T;
-        n_contrib[ti.pix] = last;
+        if (ti.inside) {
+            color[ti.color_base] = cr + T * cfg.bg[0];
+            color[ti.color_base + ti.plane] = cg + T * cfg.bg[1];
+            color[ti.color_base + 2 * ti.plane] = cb + T * cfg.bg[2];
+            t_final[ti.pix] = T;
+            n_contrib[ti.pix] = last;
+        }
+        __syncthreads();  // shared buffers are reused by the next tile
     }
 }
 
@@ -204,139 +229,225 @@ __device__ __forceinline__ float warp_reduce9(const float (&v)[9], int lane) {
     return w;
 }
 
-__global__ void __launch_bounds__(kThreads) k_render_bwd(gs_frame f, gs_config cfg, const uint32_t* __restrict__ range,
-                                                         const uint32_t* __restrict__ src,
-                                                         const uint32_t* __restrict__ emit,
-                                                         const float2* __restrict__ mean2d,
-                                                         const float4* __restrict__ conic_opa,
-                                                         const float4* __restrict__ rgb_depth,
-                                                         const float* __restrict__ t_final,
-                                                         const int32_t* __restrict__ n_contrib,
-                                                         const float* __restrict__ dL_dcolor,
-                                                         float4* __restrict__ part0, float4* __restrict__ part1,
-                                                         float* __restrict__ part2, int64_t capacity) {
-    __shared__ float2 s_xy[kBwdBatch];
-    __shared__ float4 s_abco[kBwdBatch];
-    __shared__ float4 s_rgb[kBwdBatch];
-    __shared__ float4 s_box[kBwdBatch];
-    __shared__ uint32_t s_emit[kBwdBatch];
-    __shared__ float s_part[kWarps][kBwdBatch][9];
-    __shared__ uint32_t s_hit[kWarps][kBwdBatch / 32];  // which Gaussians each warp wrote
+template <int TILE, int BB>
+__global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_config cfg,
+                                                            const uint32_t* __restrict__ range,
+                                                            const uint32_t* __restrict__ src,
+                                                            const uint32_t* __restrict__ emit,
+                                                            const float2* __restrict__ mean2d,
+                                                            const float4* __restrict__ conic_opa,
+                                                            const float4* __restrict__ rgb_depth,
+                                                            const float* __restrict__ t_final,
+                                                            const int32_t* __restrict__ n_contrib,
+                                                            const float* __restrict__ dL_dcolor,
+                                                            float4* __restrict__ part0, float4* __restrict__ part1,
+                                                            float* __restrict__ part2, int64_t capacity,
+                                                            const uint32_t* __restrict__ order, uint32_t* counter,
+                                                            int n_tiles) {
+    constexpr int NT = Geom<TILE>::kThreads;
+    constexpr int NW = Geom<TILE>::kWarps;
+    __shared__ float2 s_xy[BB];
+    __shared__ float4 s_abco[BB];
+    __shared__ float4 s_rgb[BB];
+    __shared__ float4 s_box[BB];
+    __shared__ uint32_t s_emit[BB];
+    __shared__ float s_part[NW][BB][9];
+    __shared__ uint32_t s_hit[NW][BB / 32];  // which Gaussians each warp wrote
     __shared__ int s_max;
+    __shared__ int s_item;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int tile = blockIdx.x;
-    const TileInfo ti = tile_info(f, tile);
-    const WarpBlock wb = warp_block(ti);
-    const float px = ti.px + 0.5f, py = ti.py + 0.5f;
-    const uint32_t start = range[2 * tile];
-    float Tf = 1.f, gr = 0.f, gg = 0.f, gb = 0.f;
-    int nc = 0;
-    if (ti.inside) {
-        Tf = t_final[ti.pix];
-        nc = n_contrib[ti.pix];
-        gr = dL_dcolor[ti.color_base];
-        gg = dL_dcolor[ti.color_base + ti.plane];
-        gb = dL_dcolor[ti.color_base + 2 * ti.plane];
-    }
-    if (threadIdx.x == 0) s_max = 0;
-    __syncthreads();
-    const int warp_nc = __reduce_max_sync(FULL, (unsigned)nc);
-    if (lane == 0) atomicMax(&s_max, warp_nc);
-    __syncthreads();
-    const int n_list = s_max;
-    // background seen through the final transmittance, folded into the "behind" term
-    const float bgr = Tf * cfg.bg[0], bgg = Tf * cfg.bg[1], bgb = Tf * cfg.bg[2];
-    float T = Tf, Sr = 0.f, Sg = 0.f, Sb = 0.f;
     const int8_t owner = (lane & 1) ? (int8_t)-1 : kOwner[lane >> 1];
     const float inv_log2e = 1.f / kLog2e;
-    for (int bend = n_list; bend > 0; bend -= kBwdBatch) {
-        const int b0 = max(0, bend - kBwdBatch);
-        const int cnt = bend - b0;
-        __syncthreads();
-        if (threadIdx.x < cnt) {
-            const uint32_t p = start + b0 + threadIdx.x;
-            stage(mean2d, conic_opa, rgb_depth, src[p], cfg.alpha_min, s_xy[threadIdx.x], s_abco[threadIdx.x],
-                  s_rgb[threadIdx.x], s_box[threadIdx.x]);
-            s_emit[threadIdx.x] = emit[p];
+    for (int tile = next_tile(order, counter, n_tiles, true, &s_item); tile >= 0;
+         tile = next_tile(order, counter, n_tiles, false, &s_item)) {
+        const TileInfo ti = tile_info<TILE>(f, tile);
+        const WarpBlock wb = warp_block(ti);
+        const float px = ti.px + 0.5f, py = ti.py + 0.5f;
+        const uint32_t start = range[2 * tile];
+        float Tf = 1.f, gr = 0.f, gg = 0.f, gb = 0.f;
+        int nc = 0;
+        if (ti.inside) {
+            Tf = t_final[ti.pix];
+            nc = n_contrib[ti.pix];
+            gr = dL_dcolor[ti.color_base];
+            gg = dL_dcolor[ti.color_base + ti.plane];
+            gb = dL_dcolor[ti.color_base + 2 * ti.plane];
         }
+        if (threadIdx.x == 0) s_max = 0;
         __syncthreads();
-        for (int ch = (cnt - 1) >> 5; ch >= 0; ch--) {
-            const int k0 = ch * 32;
-            const int kk = k0 + lane;
-            const bool cand = kk < cnt && b0 + kk < warp_nc;
-            unsigned m = __ballot_sync(FULL, cand && wb.hits(s_box[cand ? kk : 0]));
-            unsigned written = 0;
-            while (m) {  // back to front inside the chunk
-                const int jb = 31 - __clz(m);
-                m &= ~(1u << jb);
-                const int k = k0 + jb;
-                float g[9];
+        const int warp_nc = __reduce_max_sync(FULL, (unsigned)nc);
+        if (lane == 0) atomicMax(&s_max, warp_nc);
+        __syncthreads();
+        const int n_list = s_max;
+        // pairs past every pixel's last contributor get a zero partial (their
+        // emission slots are summed per Gaussian like all others)
+        const uint32_t len = range[2 * tile + 1] - start;
+        for (uint32_t j = (uint32_t)n_list + threadIdx.x; j < len; j += NT) {
+            const uint32_t e = emit[start + j];
+            if ((int64_t)e < capacity) {
+                part0[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                part1[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+                part2[e] = 0.f;
+            }
+        }
+        // background seen through the final transmittance, folded into the "behind" term
+        const float bgr = Tf * cfg.bg[0], bgg = Tf * cfg.bg[1], bgb = Tf * cfg.bg[2];
+        float T = Tf, Sr = 0.f, Sg = 0.f, Sb = 0.f;
+        for (int bend = n_list; bend > 0; bend -= BB) {
+            const int b0 = max(0, bend - BB);
+            const int cnt = bend - b0;
+            __syncthreads();
+            for (int j = threadIdx.x; j < cnt; j += NT) {
+                const uint32_t p = start + b0 + j;
+                stage(mean2d, conic_opa, rgb_depth, src[p], cfg.alpha_min, s_xy[j], s_abco[j], s_rgb[j], s_box[j]);
+                s_emit[j] = emit[p];
+            }
+            __syncthreads();
+            for (int ch = (cnt - 1) >> 5; ch >= 0; ch--) {
+                const int k0 = ch * 32;
+                const int kk = k0 + lane;
+                const bool cand = kk < cnt && b0 + kk < warp_nc;
+                unsigned m = __ballot_sync(FULL, cand && wb.hits(s_box[cand ? kk : 0]));
+                unsigned written = 0;
+                while (m) {  // back to front inside the chunk
+                    const int jb = 31 - __clz(m);
+                    m &= ~(1u << jb);
+                    const int k = k0 + jb;
+                    float g[9];
 #pragma unroll
-                for (int c = 0; c < 9; c++) g[c] = 0.f;
-                bool contrib = false;
-                if (b0 + k < nc) {
-                    const float2 xy = s_xy[k];
-                    const float4 abco = s_abco[k];
-                    const float dx = px - xy.x, dy = py - xy.y;
-                    const float e = exponent2(abco, dx, dy);
-                    if (!(e > 0.f)) {
-                        const float G = fast_exp2(e);
-                        const float og = __fmul_rn(abco.w, G);
-                        const float alpha = fminf(cfg.alpha_max, og);
-                        if (alpha >= cfg.alpha_min) {
-                            contrib = true;
-                            const float one_m = 1.f - alpha;
-                            T = T / one_m;  // transmittance in front of this Gaussian
-                            const float4 c = s_rgb[k];
-                            const float wgt = alpha * T;
-                            g[6] = wgt * gr; g[7] = wgt * gg; g[8] = wgt * gb;
-                            const float inv = 1.f / one_m;
-                            const float dalpha = gr * (T * c.x - (Sr + bgr) * inv) +
-                                                 gg * (T * c.y - (Sg + bgg) * inv) +
-                                                 gb * (T * c.z - (Sb + bgb) * inv);
-                            Sr += wgt * c.x; Sg += wgt * c.y; Sb += wgt * c.z;
-                            if (og < cfg.alpha_max) {
-                                const float dpow = dalpha * og;  // d alpha / d(natural exponent) = o g
-                                const float q = -dpow * inv_log2e;  // (a dx + b dy) = -(2A dx + B dy)/log2(e)
-                                g[0] = q * (2.f * abco.x * dx + abco.y * dy);
-                                g[1] = q * (abco.y * dx + 2.f * abco.z * dy);
-                                g[2] = -0.5f * dpow * dx * dx;
-                                g[3] = -dpow * dx * dy;
-                                g[4] = -0.5f * dpow * dy * dy;
-                                g[5] = dalpha * G;
+                    for (int c = 0; c < 9; c++) g[c] = 0.f;
+                    bool contrib = false;
+                    if (b0 + k < nc) {
+                        const float2 xy = s_xy[k];
+                        const float4 abco = s_abco[k];
+                        const float dx = px - xy.x, dy = py - xy.y;
+                        const float e = exponent2(abco, dx, dy);
+                        if (!(e > 0.f)) {
+                            const float G = fast_exp2(e);
+                            const float og = __fmul_rn(abco.w, G);
+                            const float alpha = fminf(cfg.alpha_max, og);
+                            if (alpha >= cfg.alpha_min) {
+                                contrib = true;
+                                const float one_m = 1.f - alpha;
+                                T = T / one_m;  // transmittance in front of this Gaussian
+                                const float4 c = s_rgb[k];
+                                const float wgt = alpha * T;
+                                g[6] = wgt * gr; g[7] = wgt * gg; g[8] = wgt * gb;
+                                const float inv = 1.f / one_m;
+                                const float dalpha = gr * (T * c.x - (Sr + bgr) * inv) +
+                                                     gg * (T * c.y - (Sg + bgg) * inv) +
+                                                     gb * (T * c.z - (Sb + bgb) * inv);
+                                Sr += wgt * c.x; Sg += wgt * c.y; Sb += wgt * c.z;
+                                if (og < cfg.alpha_max) {
+                                    const float dpow = dalpha * og;     // d alpha / d(natural exponent)
+                                    const float q = -dpow * inv_log2e;  // (a dx + b dy) = -(2A dx + B dy)/log2(e)
+                                    g[0] = q * (2.f * abco.x * dx + abco.y * dy);
+                                    g[1] = q * (abco.y * dx + 2.f * abco.z * dy);
+                                    g[2] = -0.5f * dpow * dx * dx;
+                                    g[3] = -dpow * dx * dy;
+                                    g[4] = -0.5f * dpow * dy * dy;
+                                    g[5] = dalpha * G;
+                                }
                             }
                         }
                     }
+                    if (__any_sync(FULL, contrib)) {
+                        const float r = warp_reduce9(g, lane);
+                        if (owner >= 0) s_part[w][k][owner] = r;
+                        written |= 1u << jb;
+                    }
                 }
-                if (__any_sync(FULL, contrib)) {
-                    const float r = warp_reduce9(g, lane);
-                    if (owner >= 0) s_part[w][k][owner] = r;
-                    written |= 1u << jb;
+                if (lane == 0) s_hit[w][ch] = written;
+            }
+            __syncthreads();
+            for (int j = threadIdx.x; j < cnt; j += NT) {
+                const int ch = j >> 5;
+                const uint32_t bit = 1u << (j & 31);
+                float a[9];
+#pragma unroll
+                for (int c = 0; c < 9; c++) a[c] = 0.f;
+                for (int ww = 0; ww < NW; ww++)
+                    if (s_hit[ww][ch] & bit)
+#pragma unroll
+                        for (int c = 0; c < 9; c++) a[c] += s_part[ww][j][c];
+                const uint32_t e = s_emit[j];
+                if ((int64_t)e < capacity) {
+                    part0[e] = make_float4(a[0], a[1], a[2], a[3]);
+                    part1[e] = make_float4(a[4], a[5], a[6], a[7]);
+                    part2[e] = a[8];
                 }
             }
-            if (lane == 0) s_hit[w][ch] = written;
         }
-        __syncthreads();
-        if (threadIdx.x < cnt) {
-            const int ch = threadIdx.x >> 5;
-            const uint32_t bit = 1u << (threadIdx.x & 31);
-            float a[9];
-#pragma unroll
-            for (int c = 0; c < 9; c++) a[c] = 0.f;
-#pragma unroll
-            for (int ww = 0; ww < kWarps; ww++)
-                if (s_hit[ww][ch] & bit)
-#pragma unroll
-                    for (int c = 0; c < 9; c++) a[c] += s_part[ww][threadIdx.x][c];
-            const uint32_t e = s_emit[threadIdx.x];
-            if ((int64_t)e < capacity) {
-                part0[e] = make_float4(a[0], a[1], a[2], a[3]);
-                part1[e] = make_float4(a[4], a[5], a[6], a[7]);
-                part2[e] = a[8];
-            }
-        }
+        __syncthreads();  // shared buffers are reused by the next tile
     }
+}
+
+// ---------------------------------------------------------------------------
+// Launch configurations (the autotuner picks among these)
+// ---------------------------------------------------------------------------
+struct RenderLaunch {
+    const void* fn;
+    int threads;
+};
+
+static RenderLaunch pick_fwd(int tile, int batch) {
+#define GS_FWD(T, B) if (tile == T && batch == B) return {(const void*)k_render_fwd<T, B>, T * T};
+    GS_FWD(8, 64) GS_FWD(8, 128) GS_FWD(8, 256)
+    GS_FWD(16, 64) GS_FWD(16, 128) GS_FWD(16, 256)
+    GS_FWD(32, 128) GS_FWD(32, 256)
+#undef GS_FWD
+    return {nullptr, 0};
+}
+
+static RenderLaunch pick_bwd(int tile, int batch) {
+#define GS_BWD(T, B) if (tile == T && batch == B) return {(const void*)k_render_bwd<T, B>, T * T};
+    GS_BWD(8, 64) GS_BWD(8, 128) GS_BWD(8, 256)
+    GS_BWD(16, 32) GS_BWD(16, 64) GS_BWD(16, 128)
+    GS_BWD(32, 32)
+#undef GS_BWD
+    return {nullptr, 0};
+}
+
+static int default_fwd_batch(int tile) { return tile == 8 ? 128 : 256; }
+static int default_bwd_batch(int tile) { return tile == 32 ? 32 : 128; }
+
+// Persistent grid: as many CTAs as fit at once on all SMs. The occupancy query
+// runs once per (device, kernel) so later calls, e.g. inside a stream capture,
+// make no runtime queries.
+static int persistent_grid(const void* fn, int threads) {
+    struct Entry { const void* fn; int dev; int grid; };
+    static Entry cache[64];
+    static int n_cache = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int i = 0; i < n_cache; i++)
+        if (cache[i].fn == fn && cache[i].dev == dev) return cache[i].grid;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
+    const int grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    if (n_cache < 64) cache[n_cache++] = {fn, dev, grid};
+    return grid;
+}
+
+static int launch(const RenderLaunch& L, int n_tiles, bool persistent, void** args, cudaStream_t s) {
+    int grid = n_tiles;
+    if (persistent) {
+        const int pg = persistent_grid(L.fn, L.threads);
+        grid = n_tiles < pg ? n_tiles : pg;
+    }
+    if (cudaLaunchKernel(L.fn, dim3(grid), dim3(L.threads), args, 0, s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
+    count_launch();
+    return GS_OK;
+}
+
+bool render_batch_supported(int tile, int fwd_batch, int bwd_batch) {
+    return pick_fwd(tile, fwd_batch ? fwd_batch : default_fwd_batch(tile)).fn != nullptr &&
+           pick_bwd(tile, bwd_batch ? bwd_batch : default_bwd_batch(tile)).fn != nullptr;
 }
 
 }  // namespace gs
@@ -345,37 +456,69 @@ using namespace gs;
 
 extern "C" size_t gs_render_workspace_size(const gs_frame* f) {
     (void)f;
-    return 0;
+    return 256;  // the persistent schedule's work counter
+}
+
+static bool render_args_ok(const gs_frame* f, const gs_config* cfg) {
+    return f && cfg && f->n_views >= 1 && f->n_views <= GS_MAX_VIEWS && cfg->tile == f->tile &&
+           render_batch_supported(cfg->tile, cfg->fwd_batch, cfg->bwd_batch);
 }
 
 extern "C" int gs_render_fwd(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
                              const gs_image* out, void* ws, size_t ws_bytes, void* stream) {
-    (void)ws;
-    (void)ws_bytes;
-    if (!p || !pairs || !f || !cfg || !out || !out->color || !out->t_final || !out->n_contrib) return GS_ERR_INVALID_ARG;
-    if (f->tile != kTile || cfg->tile != kTile || f->n_views < 1 || f->n_views > GS_MAX_VIEWS) return GS_ERR_INVALID_ARG;
-    const int n_tiles = f->tile_base[f->n_views];
+    if (!p || !pairs || !out || !out->color || !out->t_final || !out->n_contrib || !render_args_ok(f, cfg))
+        return GS_ERR_INVALID_ARG;
+    const bool persistent = cfg->schedule == 1;
+    if (persistent && (!pairs->order || !ws || ws_bytes < 256)) return GS_ERR_INVALID_ARG;
+    int n_tiles = f->tile_base[f->n_views];
     if (n_tiles == 0) return GS_OK;
-    k_render_fwd<<<n_tiles, kThreads, 0, (cudaStream_t)stream>>>(
-        *f, *cfg, pairs->range, pairs->src, (const float2*)p->mean2d, (const float4*)p->conic_opa,
-        (const float4*)p->rgb_depth, out->color, out->t_final, out->n_contrib);
-    count_launch();
-    GS_CUDA_CHECK_LAUNCH();
-    return GS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t* counter = persistent ? (uint32_t*)ws : nullptr;
+    const uint32_t* order = persistent ? pairs->order : nullptr;
+    if (persistent) cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    const RenderLaunch L = pick_fwd(cfg->tile, cfg->fwd_batch ? cfg->fwd_batch : default_fwd_batch(cfg->tile));
+    gs_frame fv = *f;
+    gs_config cv = *cfg;
+    const uint32_t* range = pairs->range;
+    const uint32_t* src = pairs->src;
+    const float2* m2 = (const float2*)p->mean2d;
+    const float4* co = (const float4*)p->conic_opa;
+    const float4* rd = (const float4*)p->rgb_depth;
+    float* color = out->color;
+    float* tf = out->t_final;
+    int32_t* nc = out->n_contrib;
+    void* args[] = {&fv, &cv, (void*)&range, (void*)&src, (void*)&m2, (void*)&co, (void*)&rd,
+                    (void*)&color, (void*)&tf, (void*)&nc, (void*)&order, (void*)&counter, &n_tiles};
+    return launch(L, n_tiles, persistent, args, s);
 }
 
 namespace gs {
 int launch_render_bwd(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
                       const gs_image* fwd, const float* dL_dcolor, float4* part0, float4* part1, float* part2,
-                      cudaStream_t s) {
-    const int n_tiles = f->tile_base[f->n_views];
+                      uint32_t* counter, cudaStream_t s) {
+    if (!render_args_ok(f, cfg)) return GS_ERR_INVALID_ARG;
+    int n_tiles = f->tile_base[f->n_views];
     if (n_tiles == 0) return GS_OK;
-    k_render_bwd<<<n_tiles, kThreads, 0, s>>>(*f, *cfg, pairs->range, pairs->src, pairs->emit,
-                                              (const float2*)p->mean2d, (const float4*)p->conic_opa,
-                                              (const float4*)p->rgb_depth, fwd->t_final, fwd->n_contrib, dL_dcolor,
-                                              part0, part1, part2, pairs->capacity);
-    count_launch();
-    GS_CUDA_CHECK_LAUNCH();
-    return GS_OK;
+    const bool persistent = cfg->schedule == 1;
+    if (persistent && !pairs->order) return GS_ERR_INVALID_ARG;
+    const uint32_t* order = persistent ? pairs->order : nullptr;
+    if (!persistent) counter = nullptr;
+    if (persistent) cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
+    const RenderLaunch L = pick_bwd(cfg->tile, cfg->bwd_batch ? cfg->bwd_batch : default_bwd_batch(cfg->tile));
+    gs_frame fv = *f;
+    gs_config cv = *cfg;
+    const uint32_t* range = pairs->range;
+    const uint32_t* src = pairs->src;
+    const uint32_t* emit = pairs->emit;
+    const float2* m2 = (const float2*)p->mean2d;
+    const float4* co = (const float4*)p->conic_opa;
+    const float4* rd = (const float4*)p->rgb_depth;
+    const float* tf = fwd->t_final;
+    const int32_t* nc = fwd->n_contrib;
+    int64_t cap = pairs->capacity;
+    void* args[] = {&fv, &cv, (void*)&range, (void*)&src, (void*)&emit, (void*)&m2, (void*)&co, (void*)&rd,
+                    (void*)&tf, (void*)&nc, (void*)&dL_dcolor, (void*)&part0, (void*)&part1, (void*)&part2,
+                    &cap, (void*)&order, (void*)&counter, &n_tiles};
+    return launch(L, n_tiles, persistent, args, s);
 }
 }  // namespace gs

@@ -318,14 +318,32 @@ __global__ void k_finish_pairs(const uint32_t* __restrict__ skey, const uint32_t
     if (p == cnt - 1 || skey[p + 1] != t) range[2 * (int64_t)t + 1] = (uint32_t)(p + 1);
 }
 
+// Work order of the persistent schedule: tiles by decreasing pair count.
+__global__ void k_tile_order_keys(const uint32_t* __restrict__ range, int64_t n_tiles, uint32_t* __restrict__ key,
+                                  uint32_t* __restrict__ val) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_tiles) return;
+    const uint32_t len = range[2 * t + 1] - range[2 * t];
+    key[t] = 0xFFFFu - min(len, 0xFFFFu);
+    val[t] = (uint32_t)t;
+}
+
+__global__ void k_copy_u32(const uint32_t* __restrict__ a, uint32_t* __restrict__ b, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
 struct SortWs {
     uint32_t *scan, *vis_pos, *vk0, *vv0, *vk1, *vv1, *emit_off, *pk0, *pv0, *pk1, *pv1, *psrc, *hist, *misc;
+    uint32_t *tk0, *tv0, *tk1, *tv1;
 };
 
-static SortWs carve_sort(char* base, size_t cap_bytes, int64_t n_items, int64_t capacity, size_t* used) {
+static SortWs carve_sort(char* base, size_t cap_bytes, int64_t n_items, int64_t capacity, int64_t n_tiles,
+                         size_t* used) {
     Carve c{base, 0, cap_bytes};
     SortWs w;
-    const int64_t m = n_items > capacity ? n_items : capacity;
+    int64_t m = n_items > capacity ? n_items : capacity;
+    m = m > n_tiles ? m : n_tiles;
     w.scan = c.take<uint32_t>(scan_workspace_bytes(256 * radix_blocks(m) > m ? 256 * radix_blocks(m) : m) / 4);
     w.vis_pos = c.take<uint32_t>(n_items);
     w.vk0 = c.take<uint32_t>(n_items);
@@ -340,6 +358,10 @@ static SortWs carve_sort(char* base, size_t cap_bytes, int64_t n_items, int64_t 
     w.psrc = c.take<uint32_t>(capacity);
     w.hist = c.take<uint32_t>(256 * radix_blocks(m));
     w.misc = c.take<uint32_t>(8);
+    w.tk0 = c.take<uint32_t>(n_tiles);
+    w.tv0 = c.take<uint32_t>(n_tiles);
+    w.tk1 = c.take<uint32_t>(n_tiles);
+    w.tv1 = c.take<uint32_t>(n_tiles);
     *used = c.used;
     return w;
 }
@@ -357,7 +379,7 @@ using namespace gs;
 extern "C" size_t gs_sort_workspace_size(int64_t n, const gs_frame* f, int64_t capacity) {
     if (!f || n < 0 || capacity < 0) return 0;
     size_t used = 0;
-    carve_sort(nullptr, 0, n * f->n_views, capacity, &used);
+    carve_sort(nullptr, 0, n * f->n_views, capacity, f->tile_base[f->n_views], &used);
     return used;
 }
 
@@ -371,7 +393,8 @@ extern "C" int gs_sort(const gs_projected* p, int64_t n, const gs_frame* f, cons
         (n_items > 0 && !out->offset))
         return GS_ERR_INVALID_ARG;
     size_t need = 0;
-    SortWs w = carve_sort((char*)ws, ws_bytes, n_items, out->capacity, &need);
+    const int64_t n_tiles_all = f->tile_base[f->n_views];
+    SortWs w = carve_sort((char*)ws, ws_bytes, n_items, out->capacity, n_tiles_all, &need);
     if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) return GS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n_tiles_total = f->tile_base[f->n_views];
@@ -409,6 +432,16 @@ extern "C" int gs_sort(const gs_projected* p, int64_t n, const gs_frame* f, cons
                                            bits_for(n_tiles_total), w.hist, w.scan, s);
         k_finish_pairs<<<(unsigned)ceil_div(out->capacity, 256), 256, 0, s>>>(
             pin1 ? w.pk1 : w.pk0, pin1 ? w.pv1 : w.pv0, w.psrc, n_eff, out->src, out->emit, out->range);
+        count_launch();
+    }
+    // 7. optional work order for the persistent render schedule
+    if (out->order && n_tiles_total > 0) {
+        k_tile_order_keys<<<(unsigned)ceil_div(n_tiles_total, 256), 256, 0, s>>>(out->range, n_tiles_total, w.tk0,
+                                                                                  w.tv0);
+        count_launch();
+        const bool t1 = radix_sort_pairs(w.tk0, w.tv0, w.tk1, w.tv1, n_tiles_total, nullptr, 16, w.hist, w.scan, s);
+        k_copy_u32<<<(unsigned)ceil_div(n_tiles_total, 256), 256, 0, s>>>(t1 ? w.tv1 : w.tv0, out->order,
+                                                                           n_tiles_total);
         count_launch();
     }
     GS_CUDA_CHECK_LAUNCH();

@@ -29,7 +29,7 @@ EXPORTS = [
     "gs_config_default", "gs_frame_init", "gs_project", "gs_sort_workspace_size", "gs_sort",
     "gs_render_workspace_size", "gs_render_fwd", "gs_backward_workspace_size", "gs_render_bwd",
     "gs_adam_step", "gs_pose_step", "gs_l1_loss", "gs_composite_bwd", "gs_project_bwd", "gs_launch_count",
-    "gs_spawn_workspace_size", "gs_spawn_propose",
+    "gs_spawn_workspace_size", "gs_spawn_propose", "gs_counter_add",
 ]
 
 
@@ -42,7 +42,7 @@ class gs_config(C.Structure):
     _fields_ = [("tile", C.c_int32), ("sh_degree", C.c_int32), ("near_z", C.c_float), ("dilation", C.c_float),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float), ("bg", C.c_float * 3),
                 ("pose_grad_through_sh", C.c_int32), ("schedule", C.c_int32), ("accumulate", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("fwd_batch", C.c_int32), ("bwd_batch", C.c_int32)]
 
 
 class gs_frame(C.Structure):
@@ -64,7 +64,7 @@ class gs_projected(C.Structure):
 
 class gs_pairs(C.Structure):
     _fields_ = [("src", C.c_void_p), ("emit", C.c_void_p), ("offset", C.c_void_p), ("range", C.c_void_p),
-                ("capacity", C.c_int64), ("count", C.c_void_p), ("status", C.c_void_p)]
+                ("capacity", C.c_int64), ("count", C.c_void_p), ("status", C.c_void_p), ("order", C.c_void_p)]
 
 
 class gs_image(C.Structure):
@@ -120,9 +120,10 @@ def lib():
                                         C.POINTER(gs_frame), C.POINTER(gs_config), C.POINTER(gs_image), P,
                                         C.POINTER(gs_grads), P, P, P, C.c_size_t, P]),
             "gs_adam_step": (C.c_int, [C.POINTER(gs_gaussians), C.POINTER(gs_grads), C.POINTER(gs_gaussians),
-                                       C.POINTER(gs_gaussians), C.POINTER(gs_adam_config), C.c_int32, P]),
+                                       C.POINTER(gs_gaussians), C.POINTER(gs_adam_config), C.c_int32, P, P]),
             "gs_pose_step": (C.c_int, [P, C.c_int32, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
-                                       C.c_int32, P]),
+                                       C.c_int32, P, P]),
+            "gs_counter_add": (C.c_int, [P, C.c_int32, P]),
             "gs_l1_loss": (C.c_int, [P, P, C.c_int64, P, P, P, C.c_size_t, P]),
             "gs_composite_bwd": (C.c_int, [C.POINTER(gs_projected), C.POINTER(gs_pairs), C.POINTER(gs_frame),
                                            C.POINTER(gs_config), C.POINTER(gs_image), P, C.c_int64, P, C.c_size_t,
@@ -260,21 +261,23 @@ class Pairs:
     range: torch.Tensor
     count: torch.Tensor
     status: torch.Tensor
+    order: torch.Tensor | None = None
 
     @property
     def capacity(self) -> int:
         return int(self.src.shape[0])
 
     @staticmethod
-    def alloc(items, n_tiles_total, capacity, device="cuda") -> "Pairs":
+    def alloc(items, n_tiles_total, capacity, device="cuda", with_order=True) -> "Pairs":
         u32 = lambda k: torch.zeros((k,), dtype=torch.int32, device=device)
         return Pairs(u32(max(capacity, 1)), u32(max(capacity, 1)), u32(max(items, 1)), u32(2 * n_tiles_total),
                      torch.zeros((1,), dtype=torch.int64, device=device),
-                     torch.zeros((1,), dtype=torch.int32, device=device))
+                     torch.zeros((1,), dtype=torch.int32, device=device),
+                     u32(max(n_tiles_total, 1)) if with_order else None)
 
     def c(self) -> gs_pairs:
         return gs_pairs(_ptr(self.src), _ptr(self.emit), _ptr(self.offset), _ptr(self.range), self.capacity,
-                        _ptr(self.count), _ptr(self.status))
+                        _ptr(self.count), _ptr(self.status), _ptr(self.order))
 
 
 @dataclass
@@ -332,6 +335,10 @@ def gs_sort_workspace_size(n: int, f: gs_frame, capacity: int) -> int:
 def gs_sort(p: Projected, n: int, f: gs_frame, out: Pairs, ws: torch.Tensor, stream=None):
     pc, oc = p.c(), out.c()
     _check(lib().gs_sort(C.byref(pc), n, C.byref(f), C.byref(oc), _ptr(ws), ws.numel(), _stream(stream)), "gs_sort")
+
+
+def gs_render_workspace_size(f: gs_frame) -> int:
+    return int(lib().gs_render_workspace_size(C.byref(f)))
 
 
 def gs_render_fwd(p: Projected, pairs: Pairs, f: gs_frame, cfg: gs_config, out: Image, ws=None, stream=None):
@@ -415,16 +422,21 @@ def adam_config(lr_mean=1.6e-4, lr_opacity=0.05, lr_scale=5e-3, lr_rot=1e-3, lr_
 
 
 def gs_adam_step(params: Gaussians, grads: Grads, m: Gaussians, v: Gaussians, cfg: gs_adam_config, step: int,
-                 stream=None):
+                 stream=None, step_dev: torch.Tensor | None = None):
     a, b, c, d = params.c(), grads.c(), m.c(), v.c()
-    _check(lib().gs_adam_step(C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(cfg), step, _stream(stream)),
-           "gs_adam_step")
+    _check(lib().gs_adam_step(C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(cfg), step, _ptr(step_dev),
+                              _stream(stream)), "gs_adam_step")
 
 
 def gs_pose_step(cams: torch.Tensor, n_views: int, dL_dpose: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
-                 lr_t: float, lr_r: float, step: int, beta1=0.9, beta2=0.999, eps=1e-15, stream=None):
+                 lr_t: float, lr_r: float, step: int, beta1=0.9, beta2=0.999, eps=1e-15, stream=None,
+                 step_dev: torch.Tensor | None = None):
     _check(lib().gs_pose_step(_ptr(cams), n_views, _ptr(dL_dpose), _ptr(m), _ptr(v), lr_t, lr_r, beta1, beta2, eps,
-                              step, _stream(stream)), "gs_pose_step")
+                              step, _ptr(step_dev), _stream(stream)), "gs_pose_step")
+
+
+def gs_counter_add(counter: torch.Tensor, delta: int = 1, stream=None):
+    _check(lib().gs_counter_add(_ptr(counter), delta, _stream(stream)), "gs_counter_add")
 
 
 def gs_l1_loss(color: torch.Tensor, target: torch.Tensor, dL_dcolor: torch.Tensor, loss: torch.Tensor,

@@ -207,9 +207,9 @@ def test_render_bwd_deterministic():
 # End to end: project -> sort -> render -> adjoint with pose gradients
 # ---------------------------------------------------------------------------
 
-def run_views(sc, cams, sh_degree, dLs=None, seed=0, pose_through_sh=0, bg=(0.0, 0.0, 0.0)):
+def run_views(sc, cams, sh_degree, dLs=None, seed=0, pose_through_sh=0, bg=(0.0, 0.0, 0.0), **launch):
     sizes = [(c["width"], c["height"]) for c in cams]
-    cfg = gs.config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg)
+    cfg = gs.config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg, **launch)
     g = gs.Gaussians.from_scene(sc)
     camt = gs.cameras_tensor(cams)
     r = Rasterizer(sc.n, sizes, capacity=1024, cfg=cfg)
@@ -226,9 +226,11 @@ def run_views(sc, cams, sh_degree, dLs=None, seed=0, pose_through_sh=0, bg=(0.0,
     return r, dLs, d_proj.cpu().numpy()
 
 
-def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), max_amb_frac=0.3, max_excl_frac=0.25):
-    r, dLs, d_proj = run_views(sc, cams, sh_degree, pose_through_sh=pose_through_sh, bg=bg)
-    ocfg = O.Config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg, **MARGINS)
+def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), max_amb_frac=0.3, max_excl_frac=0.25,
+                  **launch):
+    r, dLs, d_proj = run_views(sc, cams, sh_degree, pose_through_sh=pose_through_sh, bg=bg, **launch)
+    tile = launch.get("tile", 16)
+    ocfg = O.Config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg, tile=tile, **MARGINS)
     n = sc.n
     views = []
     excl = np.zeros(n, bool)
@@ -257,7 +259,7 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
         assert_close(rd[:, 3], proj["depth"][both], 1e-6, what="depth")
         # image: pixels with an ambiguous decision and tiles an ambiguous rect may touch
         bad = O.ambiguous_tiles(view, cam, ocfg)
-        pm = ~tile_pixel_mask(bad, w, h, 16) & (view["amb"] == 0)
+        pm = ~tile_pixel_mask(bad, w, h, tile) & (view["amb"] == 0)
         n_amb_px += int((~pm).sum())
         color = r.view_color(v).cpu().numpy()
         assert_close(color, view["color"], IMG_RTOL, np.broadcast_to(pm, color.shape), f"color view {v}")
@@ -308,6 +310,43 @@ def test_multiview_sh3_end_to_end(through_sh):
     """Three views of different sizes (ragged edge tiles), SH degree 3."""
     sc, cams, _ = synth.multiview_scene(seed=5, n=20000, n_views=3, sizes=[(200, 120), (131, 77), (96, 160)])
     compare_views(sc, cams, 3, pose_through_sh=through_sh, max_excl_frac=0.6)
+
+
+@pytest.mark.parametrize("tile,schedule,fb,bb", [(8, 0, 64, 256), (8, 1, 256, 64), (16, 1, 64, 32),
+                                                 (32, 0, 128, 32), (32, 1, 256, 32)])
+def test_tiles_batches_schedules_end_to_end(tile, schedule, fb, bb):
+    """Every tile size (8, 16, 32), staging depth and both render schedules
+    give the oracle's images and gradients (the oracle at the same tile size)."""
+    sc, cams, _ = synth.multiview_scene(seed=6, n=8000, n_views=2, sizes=[(200, 120), (96, 160)])
+    compare_views(sc, cams, 3, tile=tile, schedule=schedule, fwd_batch=fb, bwd_batch=bb, max_excl_frac=0.6)
+
+
+def test_graph_replay_matches_eager_steps():
+    """Four optimisation steps issued eagerly and one eager step + three replays
+    of a captured CUDA graph (device-side step counter) give bit-identical
+    parameters, poses and Adam state."""
+    from paper_2506_05558_gb300.raster import JointOptimizer
+    sc, cams, rng = synth.multiview_scene(seed=9, n=5000, n_views=3, sizes=[(128, 96), (160, 64), (64, 64)])
+    sizes = [(c["width"], c["height"]) for c in cams]
+    targets = t32(rng.random(sum(3 * w * h for w, h in sizes)))
+    outs = []
+    for mode in ("eager", "graph"):
+        g = gs.Gaussians.from_scene(sc)
+        camt = gs.cameras_tensor(cams)
+        J = JointOptimizer(g, camt, sizes, targets, 1 << 16, gs.config(sh_degree=3, schedule=1))
+        J.step()
+        if mode == "eager":
+            for _ in range(3):
+                J.step()
+        else:
+            J.capture(per_stage=(len(outs) % 2 == 1))
+            for _ in range(3):
+                J.replay()
+        torch.cuda.synchronize()
+        assert J.r.status() == gs.GS_OK and int(J.step_dev.item()) == 5
+        outs.append([t.cpu().numpy().copy() for t in (g.mean_opa, g.scale, g.quat, g.sh, J.m.sh, J.v.mean_opa, camt)])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
 
 
 def test_720p_200k_end_to_end():

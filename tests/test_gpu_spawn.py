@@ -58,8 +58,12 @@ def test_spawn_matches_oracle(W, H, sigma, with_render):
     ref = O.spawn(im.astype(np.float64), None if rd is None else rd.astype(np.float64), depth, cam, sigma, seed,
                   frame, margin=1e-5)
     m = ref["maps"]
-    for k in ("p_l", "p_pen", "p_s"):
+    for k in ("p_l", "p_pen"):
         assert_close(getattr(out, k).cpu().numpy().reshape(H, W), m[k], 1e-5, what=k)
+    # P_s = max(P_L - P~, 0) cancels: its error scale is that of its operands
+    ps = out.p_s.cpu().numpy().reshape(H, W)
+    scale_l = np.abs(m["p_l"]) + np.sqrt(np.mean(m["p_l"] ** 2))
+    assert np.all(np.abs(ps - m["p_s"]) <= 1e-5 * scale_l), np.abs(ps - m["p_s"]).max()
     n = int(out.count.item())
     pix = out.pixel[:n].cpu().numpy()
     assert np.all(np.diff(pix) > 0)  # compacted in pixel order
