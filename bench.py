@@ -55,6 +55,31 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+PROFILE_OF_STAGE = {"composite_bwd": "render_bwd_1M_2x1080p.md", "render_fwd": "render_fwd_1M_2x1080p.md"}
+
+
+def profiled_traffic(stage, n_views):
+    """DRAM bytes per launch from the committed ncu summary of the stage's
+    kernel (measured on 2 views, scaled by views: traffic grows with the views
+    rendered), or None when no summary exists or the kernel source changed
+    since the counters were taken."""
+    import hashlib
+    import re
+    name = PROFILE_OF_STAGE.get(stage)
+    if not name:
+        return None
+    try:
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+        src = open(os.path.join(ROOT, "paper_2506_05558_gb300", "csrc", "render.cu"), "rb").read()
+    except OSError:
+        return None
+    m_sha = re.search(r"source_sha256: ([0-9a-f]+)", text)
+    m_tb = re.search(r"traffic_bytes_per_view \| ([0-9.e+]+)", text)
+    if not m_sha or not m_tb or not hashlib.sha256(src).hexdigest().startswith(m_sha.group(1)):
+        return None
+    return float(m_tb.group(1)) * n_views
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -401,7 +426,7 @@ def main():
     if dom in algo:
         d = stages[dom]
         roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-                "frac": d["frac"], "traffic": None,
+                "frac": d["frac"], "traffic": profiled_traffic(dom, args.views),
                 "peak_source": ("FP32 lanes: 152 SMs x 128 x 2 flop x median SM clock sampled under load"
                                 if d["bound"] == "alu" else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
     del J
