@@ -291,6 +291,29 @@ int gs_spawn_propose(const float* image, const float* render, const float* depth
                      const gs_camera* cam, const gs_spawn_config* sc, const gs_spawn_out* out, void* ws,
                      size_t ws_bytes, void* stream);
 
+/* gs_spawn_propose for callers that cannot allocate device memory: the paper
+ * has no counterpart; this is a deployment convenience. Callers such as a host
+ * application that owns the allocator, or a process that reserved its memory
+ * up front, can pass only their inputs and outputs: the scratch gs_spawn_propose
+ * takes as `ws` is instead a file-scope device array inside the library, sized
+ * for frames of at most 2,097,152 pixels (1920x1080 fits); about 16.8 MB that
+ * every GPU which loads the library holds until the process exits. Arguments
+ * and outputs are those of gs_spawn_propose; no workspace argument.
+ *  - Returns GS_ERR_INVALID_ARG for width * height > 2,097,152 (use
+ *    gs_spawn_propose for larger frames) and for the checks gs_spawn_propose
+ *    makes; GS_ERR_CUDA if the array's device address cannot be obtained.
+ *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ *  - The first call on each device looks up the array's device address with
+ *    that device current (cudaGetSymbolAddress); make that first call before
+ *    any stream capture.
+ *  - Every call shares the one array, which keeps the previous call's
+ *    contents; nothing in it needs to start at zero (each pass writes what it
+ *    reads). Calls whose kernels overlap on a GPU race on the array: issue them
+ *    on one stream or otherwise order them. */
+int gs_spawn_propose_noalloc(const float* image, const float* render, const float* depth, int32_t width,
+                             int32_t height, const gs_camera* cam, const gs_spawn_config* sc, const gs_spawn_out* out,
+                             void* stream);
+
 /* Learning rates of the parameter groups and the Adam constants. */
 typedef struct gs_adam_config {
     float lr_mean, lr_opacity, lr_scale, lr_rot, lr_sh_dc, lr_sh_rest;

@@ -10,6 +10,7 @@
 // passed by value) are applied directly. The mask is compacted in pixel order
 // with the device-wide scan, then k_spawn_emit writes the spawned rows.
 #include <cmath>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -189,6 +190,89 @@ extern "C" int gs_spawn_propose(const float* image, const float* render, const f
     uint32_t* total = c.take<uint32_t>(4);
     void* scan_ws = c.take<char>(scan_workspace_bytes(hw));
     if (!ws || !c.ok() || ((uintptr_t)ws & 255)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int S = kSpT + 2 * taps.R;
+    const size_t smem = sizeof(float) * 3 * S * S * (render ? 2 : 1);
+    dim3 grid((unsigned)ceil_div(width, kSpT), (unsigned)ceil_div(height, kSpT));
+    const uint2 key = make_uint2((uint32_t)sc->seed, (uint32_t)(sc->seed >> 32));
+    k_spawn_maps<<<grid, 256, smem, s>>>(image, render, depth, width, height, taps, key, sc->frame, out->p_l,
+                                          out->p_pen, out->p_s, flag);
+    count_launch();
+    scan_exclusive_u32(flag, pos, hw, total, scan_ws, s);
+    k_spawn_count<<<1, 1, 0, s>>>(total, out->capacity, out->count, out->status);
+    count_launch();
+    if (out->capacity > 0) {
+        k_spawn_emit<<<grid, 256, sizeof(float) * 3 * S * S, s>>>(
+            image, depth, width, height, taps, flag, pos, cam, out->capacity, (float4*)out->mean_opa,
+            (float4*)out->scale, (float4*)out->quat, (float4*)out->sh, out->pixel);
+        count_launch();
+    }
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Spawn proposal without caller-provided scratch.
+//
+// Some callers cannot allocate device memory at the point where they need a
+// spawn proposal: code running under an allocator that is frozen or owned by
+// another runtime (a host application that hands us only its input and output
+// buffers), or a process that has reserved all its memory up front. For them
+// the scratch (per-pixel spawn flags, their exclusive scan and the scan's
+// block sums) lives in this file-scope device array instead of a workspace.
+// It is sized for at most kNoAllocMaxPixels pixels; every GPU that loads the
+// library holds it until the process exits.
+// ---------------------------------------------------------------------------
+namespace gs {
+
+constexpr int64_t kNoAllocMaxPixels = int64_t(1) << 21;  // 2,097,152 px: covers 1920x1080
+constexpr int64_t kNoAllocScanWords = kNoAllocMaxPixels / 2048 + 256;  // the scan's block sums
+constexpr int kNoAllocMaxDevices = 64;
+constexpr int64_t kNoAllocWords = 2 * kNoAllocMaxPixels + 64 + kNoAllocScanWords;
+
+static __device__ __align__(256) uint32_t g_spawn_scratch[kNoAllocWords];  // ~16.8 MB
+
+// Device address of g_spawn_scratch, looked up once per device with that
+// device current (the host-side name of the array is not a device address).
+static uint32_t* noalloc_scratch_for_current_device() {
+    static std::mutex mu;
+    static uint32_t* ptr[kNoAllocMaxDevices] = {};
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_spawn_scratch) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        ptr[dev] = (uint32_t*)p;
+    }
+    return ptr[dev];
+}
+
+}  // namespace gs
+
+extern "C" int gs_spawn_propose_noalloc(const float* image, const float* render, const float* depth,
+                                        int32_t width, int32_t height, const gs_camera* cam,
+                                        const gs_spawn_config* sc, const gs_spawn_out* out, void* stream) {
+    if (!image || !depth || !cam || !sc || !out || width <= 0 || height <= 0) return GS_ERR_INVALID_ARG;
+    if (!out->count || !out->status || out->capacity < 0 ||
+        (out->capacity > 0 && (!out->mean_opa || !out->scale || !out->quat || !out->sh)))
+        return GS_ERR_INVALID_ARG;
+    const int64_t hw = (int64_t)width * height;
+    if (hw > kNoAllocMaxPixels) return GS_ERR_INVALID_ARG;  // larger frames need gs_spawn_propose
+    LogTaps taps;
+    if (!make_taps(sc->sigma, &taps)) return GS_ERR_INVALID_ARG;
+    uint32_t* base = noalloc_scratch_for_current_device();
+    if (!base) return GS_ERR_CUDA;
+    // Layout inside the static array. Nothing in it needs to start at zero:
+    // every pass writes each word it later reads (flags and positions for all
+    // hw pixels, the scan's block sums and total).
+    uint32_t* flag = base;
+    uint32_t* pos = base + kNoAllocMaxPixels;
+    uint32_t* total = base + 2 * kNoAllocMaxPixels;
+    void* scan_ws = base + 2 * kNoAllocMaxPixels + 64;
     cudaStream_t s = (cudaStream_t)stream;
     const int S = kSpT + 2 * taps.R;
     const size_t smem = sizeof(float) * 3 * S * S * (render ? 2 : 1);

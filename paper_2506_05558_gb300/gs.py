@@ -29,7 +29,7 @@ EXPORTS = [
     "gs_config_default", "gs_frame_init", "gs_project", "gs_sort_workspace_size", "gs_sort",
     "gs_render_workspace_size", "gs_render_fwd", "gs_backward_workspace_size", "gs_render_bwd",
     "gs_adam_step", "gs_pose_step", "gs_l1_loss", "gs_composite_bwd", "gs_project_bwd", "gs_launch_count",
-    "gs_spawn_workspace_size", "gs_spawn_propose", "gs_counter_add",
+    "gs_spawn_workspace_size", "gs_spawn_propose", "gs_counter_add", "gs_spawn_propose_noalloc",
 ]
 
 
@@ -133,6 +133,8 @@ def lib():
                                          C.c_size_t, P]),
             "gs_launch_count": (C.c_int64, []),
             "gs_spawn_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
+            "gs_spawn_propose_noalloc": (C.c_int, [P, P, P, C.c_int32, C.c_int32, P, C.POINTER(gs_spawn_config),
+                                                   C.POINTER(gs_spawn_out), P]),
             "gs_spawn_propose": (C.c_int, [P, P, P, C.c_int32, C.c_int32, P, C.POINTER(gs_spawn_config),
                                            C.POINTER(gs_spawn_out), P, C.c_size_t, P]),
         }
@@ -414,6 +416,19 @@ def gs_spawn_propose(image: torch.Tensor, render, depth: torch.Tensor, width: in
     oc = out.c(out.g.n if capacity is None else capacity)
     _check(lib().gs_spawn_propose(_ptr(image), _ptr(render), _ptr(depth), width, height, _ptr(cam), C.byref(sc),
                                   C.byref(oc), _ptr(ws), ws.numel(), _stream(stream)), "gs_spawn_propose")
+
+
+def gs_spawn_propose_noalloc(image: torch.Tensor, render, depth: torch.Tensor, width: int, height: int,
+                             cam: torch.Tensor, sigma: float, seed: int, frame: int, out: Spawned, capacity=None,
+                             stream=None):
+    """gs_spawn_propose without a workspace, for callers that cannot allocate
+    device memory (the scratch is a fixed array inside the library; frames of
+    at most 2,097,152 pixels). Returns the C status code instead of raising so
+    callers can react to an oversized frame."""
+    sc = gs_spawn_config(sigma, frame, seed)
+    oc = out.c(out.g.n if capacity is None else capacity)
+    return int(lib().gs_spawn_propose_noalloc(_ptr(image), _ptr(render), _ptr(depth), width, height, _ptr(cam),
+                                              C.byref(sc), C.byref(oc), _stream(stream)))
 
 
 def adam_config(lr_mean=1.6e-4, lr_opacity=0.05, lr_scale=5e-3, lr_rot=1e-3, lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4,
