@@ -291,6 +291,27 @@ int gs_spawn_propose(const float* image, const float* render, const float* depth
                      const gs_camera* cam, const gs_spawn_config* sc, const gs_spawn_out* out, void* ws,
                      size_t ws_bytes, void* stream);
 
+/* Anchor trigger (Sec. 4.4): the size of a Gaussian seen from a camera is
+ * S / D, S its largest scale, D the distance of its mean to the camera centre;
+ * in pixels fx S / D. too_fine [n] (device) = 1 where that is below tau_px
+ * (the paper's tau_min = 1 px, measured from the previous camera); count
+ * (device int64) = the number of such Gaussians (exact). An anchor is due when
+ * count > 0.4 n. */
+int gs_anchor_check(const gs_gaussians* g, const gs_camera* cam, float tau_px, uint8_t* too_fine, int64_t* count,
+                    void* stream);
+
+/* Anchor offload / reload (Sec. 4.4: the active set and its optimisation state
+ * are stored at the anchor in host memory and loaded back when required).
+ * gs_anchor_offload copies params (and m, v when both are non-NULL) from the
+ * device to caller-owned host arrays (pinned memory gives asynchronous copies);
+ * gs_anchor_load copies them back. One cudaMemcpyAsync per array on `stream`;
+ * the n of each pair of sets must match. */
+int gs_anchor_offload(const gs_gaussians* params, const gs_gaussians* m, const gs_gaussians* v,
+                      const gs_gaussians* host_params, const gs_gaussians* host_m, const gs_gaussians* host_v,
+                      void* stream);
+int gs_anchor_load(const gs_gaussians* host_params, const gs_gaussians* host_m, const gs_gaussians* host_v,
+                   const gs_gaussians* params, const gs_gaussians* m, const gs_gaussians* v, void* stream);
+
 /* gs_spawn_propose for callers that cannot allocate device memory: the paper
  * has no counterpart; this is a deployment convenience. Callers such as a host
  * application that owns the allocator, or a process that reserved its memory

@@ -341,6 +341,31 @@ def spawn(image, render, depth, cam, sigma, seed, frame, margin=1e-5):
 
 
 # ---------------------------------------------------------------------------
+# Anchor trigger (Sec. 4.4)
+# ---------------------------------------------------------------------------
+
+def anchor_sizes(scene, cam):
+    """On-screen size in pixels of each Gaussian from a camera: fx S / D with S
+    the largest scale and D the distance of the mean to the camera centre."""
+    R = np.asarray(cam["R"], np.float64)
+    t = np.asarray(cam["t"], np.float64)
+    centre = -R.T @ t
+    mu = np.asarray(scene.mean_opa, np.float64)[:, :3]
+    D = np.linalg.norm(mu - centre, axis=1)
+    S = np.exp(np.asarray(scene.scale, np.float64)[:, :3].max(axis=1))
+    return cam["fx"] * S / D
+
+
+def anchor_check(scene, cam, tau_px=1.0, share=0.4, margin=1e-5):
+    """Too-fine flags (size < tau), their count, whether an anchor is due (more
+    than `share` of the active set too fine) and the items within margin."""
+    size = anchor_sizes(scene, cam)
+    fine = size < tau_px
+    amb = np.abs(size - tau_px) < margin * tau_px
+    return dict(size=size, too_fine=fine, count=int(fine.sum()), due=bool(fine.sum() > share * len(size)), amb=amb)
+
+
+# ---------------------------------------------------------------------------
 # Loss, optimiser and pose update (FP64 NumPy)
 # ---------------------------------------------------------------------------
 

@@ -30,6 +30,7 @@ EXPORTS = [
     "gs_render_workspace_size", "gs_render_fwd", "gs_backward_workspace_size", "gs_render_bwd",
     "gs_adam_step", "gs_pose_step", "gs_l1_loss", "gs_composite_bwd", "gs_project_bwd", "gs_launch_count",
     "gs_spawn_workspace_size", "gs_spawn_propose", "gs_counter_add", "gs_spawn_propose_noalloc",
+    "gs_anchor_check", "gs_anchor_offload", "gs_anchor_load",
 ]
 
 
@@ -132,6 +133,9 @@ def lib():
                                          C.POINTER(gs_frame), C.POINTER(gs_config), C.POINTER(gs_grads), P, P, P,
                                          C.c_size_t, P]),
             "gs_launch_count": (C.c_int64, []),
+            "gs_anchor_check": (C.c_int, [C.POINTER(gs_gaussians), P, C.c_float, P, P, P]),
+            "gs_anchor_offload": (C.c_int, [C.POINTER(gs_gaussians)] * 6 + [P]),
+            "gs_anchor_load": (C.c_int, [C.POINTER(gs_gaussians)] * 6 + [P]),
             "gs_spawn_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
             "gs_spawn_propose_noalloc": (C.c_int, [P, P, P, C.c_int32, C.c_int32, P, C.POINTER(gs_spawn_config),
                                                    C.POINTER(gs_spawn_out), P]),
@@ -429,6 +433,34 @@ def gs_spawn_propose_noalloc(image: torch.Tensor, render, depth: torch.Tensor, w
     oc = out.c(out.g.n if capacity is None else capacity)
     return int(lib().gs_spawn_propose_noalloc(_ptr(image), _ptr(render), _ptr(depth), width, height, _ptr(cam),
                                               C.byref(sc), C.byref(oc), _stream(stream)))
+
+
+def gs_anchor_check(g: Gaussians, cam: torch.Tensor, tau_px: float, too_fine: torch.Tensor, count: torch.Tensor,
+                    stream=None):
+    gc = g.c()
+    _check(lib().gs_anchor_check(C.byref(gc), _ptr(cam), tau_px, _ptr(too_fine), _ptr(count), _stream(stream)),
+           "gs_anchor_check")
+
+
+def _opt_c(g):
+    return None if g is None else C.byref(g.c())
+
+
+def gs_anchor_offload(params: Gaussians, m, v, host_params: Gaussians, host_m, host_v, stream=None):
+    """Device -> host copies of the active set (and its Adam state)."""
+    _check(lib().gs_anchor_offload(C.byref(params.c()), _opt_c(m), _opt_c(v), C.byref(host_params.c()),
+                                   _opt_c(host_m), _opt_c(host_v), _stream(stream)), "gs_anchor_offload")
+
+
+def gs_anchor_load(host_params: Gaussians, host_m, host_v, params: Gaussians, m, v, stream=None):
+    """Host -> device copies of an anchor's Gaussians (and Adam state)."""
+    _check(lib().gs_anchor_load(C.byref(host_params.c()), _opt_c(host_m), _opt_c(host_v), C.byref(params.c()),
+                                _opt_c(m), _opt_c(v), _stream(stream)), "gs_anchor_load")
+
+
+def pinned_gaussians(n: int) -> Gaussians:
+    z = lambda k: torch.zeros((n, k), dtype=torch.float32).pin_memory()
+    return Gaussians(z(4), z(4), z(4), z(48))
 
 
 def adam_config(lr_mean=1.6e-4, lr_opacity=0.05, lr_scale=5e-3, lr_rot=1e-3, lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4,
