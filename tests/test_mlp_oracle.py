@@ -1,0 +1,94 @@
+"""Pins of the learned-proposal MLP oracle (CPU): bfloat16 rounding against
+torch's bfloat16 conversion, GELU against torch, the whole-network gradient
+against central finite differences of the loss (with the rounding turned off),
+the patch layout against a direct loop, and Adam's first step."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import mlp as M
+
+
+def test_bf16_rounding_matches_torch():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(10000) * 10 ** rng.uniform(-8, 8, 10000),
+                        [0.0, -0.0, 1.0, 1.00390625, 1.0039063, 3.0e38]])
+    want = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(M.bf16(x), want)
+
+
+def test_gelu_matches_torch():
+    z = np.linspace(-8, 8, 2001)
+    t = torch.tensor(z, dtype=torch.float64, requires_grad=True)
+    y = torch.nn.functional.gelu(t)
+    y.sum().backward()
+    np.testing.assert_allclose(M.gelu(z), y.detach().numpy(), rtol=1e-13, atol=1e-15)
+    np.testing.assert_allclose(M.gelu_grad(z), t.grad.numpy(), rtol=1e-12, atol=1e-14)
+
+
+def test_patch_features_layout():
+    rng = np.random.default_rng(1)
+    im = rng.random((3, 16, 24))
+    X = M.patch_features(im)
+    assert X.shape == (6, 194)
+    for py in range(2):
+        for px in range(3):
+            row = X[py * 3 + px]
+            for c in range(3):
+                for dy in range(8):
+                    for dx in range(8):
+                        assert row[c * 64 + dy * 8 + dx] == im[c, 8 * py + dy, 8 * px + dx]
+            assert row[192] == (px + 0.5) / 3 * 2 - 1 and row[193] == (py + 0.5) / 2 * 2 - 1
+
+
+def test_gradients_match_central_differences(monkeypatch):
+    """With the bfloat16 rounding disabled the network is smooth: every
+    parameter's gradient equals the central difference of the loss."""
+    monkeypatch.setattr(M, "bf16", lambda x: np.asarray(x, np.float64))
+    rng = np.random.default_rng(2)
+    params = M.init_params(rng)
+    X = rng.standard_normal((20, M.IN))
+    t = rng.random(20)
+    zt, st = rng.normal(5, 1, 20), rng.normal(-3, 0.5, 20)
+    mask = (rng.random(20) < 0.7).astype(float)
+    Y, cache = M.forward(params, X)
+    # keep L1 terms away from their kinks
+    zt += np.sign(Y[:, 1] - zt) * 0.1
+    st += np.sign(Y[:, 2] - st) * 0.1
+    L, dY = M.loss(Y, t, zt, st, mask)
+    grads = M.backward(params, cache, dY)
+    h = 1e-6
+    for l in range(4):
+        for which in (0, 1):
+            arr = params[l][which]
+            flat = arr.reshape(-1)
+            for idx in rng.choice(flat.size, 6, replace=False):
+                old = flat[idx]
+                flat[idx] = old + h
+                lp = M.loss(M.forward(params, X)[0], t, zt, st, mask)[0]
+                flat[idx] = old - h
+                lm = M.loss(M.forward(params, X)[0], t, zt, st, mask)[0]
+                flat[idx] = old
+                fd = (lp - lm) / (2 * h)
+                an = grads[l][which].reshape(-1)[idx]
+                assert abs(fd - an) <= 1e-5 * max(1e-3, abs(fd)), (l, which, idx, fd, an)
+
+
+def test_loss_closed_form():
+    Y = np.array([[0.0, 2.0, -1.0], [2.0, 1.0, 0.5]])
+    L, dY = M.loss(Y, np.array([0.5, 1.0]), np.array([1.0, 1.0]), np.array([0.0, 0.0]), np.array([1.0, 0.0]))
+    want = (math.log(2) - 0 + math.log(1 + math.e ** 2) - 2) / 2 + (1.0 + 1.0) / 2
+    assert abs(L - want) < 1e-14
+    assert abs(dY[0, 0] - 0.0) < 1e-15 and abs(dY[1, 0] - (1 / (1 + math.e ** -2) - 1) / 2) < 1e-15
+
+
+def test_adam_first_step_is_sign():
+    rng = np.random.default_rng(3)
+    params = M.init_params(rng)
+    grads = [(rng.standard_normal(W.shape), rng.standard_normal(b.shape)) for W, b in params]
+    z = M.zeros_like_params(params)
+    p2, _, _ = M.adam(params, grads, z, z, 1, 1e-3, eps=1e-12)
+    for (W, b), (W2, b2), (dW, db) in zip(params, p2, grads):
+        np.testing.assert_allclose(W2, W - 1e-3 * np.sign(dW), rtol=0, atol=1e-9)
