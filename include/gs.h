@@ -335,6 +335,58 @@ int gs_spawn_propose_noalloc(const float* image, const float* render, const floa
                              int32_t height, const gs_camera* cam, const gs_spawn_config* sc, const gs_spawn_out* out,
                              void* stream);
 
+/* Learned spawn proposal (not in the paper; the workload's per-patch MLP):
+ * for each 8x8 patch of a frame, x = (its 192 pixel values, channel-major then
+ * row-major, and the patch centre in [-1, 1]^2) -> 3 x (Linear 128 + GELU) ->
+ * Linear 3 = (spawn logit, depth, log-scale). Weights and activations are
+ * bfloat16 in the matrix products, accumulation and everything else FP32.
+ * Parameters (device, FP32 masters, nn.Linear layout): w1 [128][194], b1 [128],
+ * w2 [128][128], b2, w3 [128][128], b3, w4 [3][128], b4 [3]. */
+typedef struct gs_mlp_params {
+    float *w1, *b1, *w2, *b2, *w3, *b3, *w4, *b4;
+} gs_mlp_params;
+
+typedef struct gs_mlp_config {
+    int32_t tensor_path; /* 0: mma.sync bf16 tiles; 1: tcgen05.mma with the accumulator in tensor memory */
+    float w_depth;       /* weight of the L1 depth term */
+    float w_scale;       /* weight of the L1 log-scale term */
+    float lr, beta1, beta2, eps; /* Adam */
+} gs_mlp_config;
+
+/* Patches of a width x height frame (both multiples of 8), -1 otherwise. */
+int64_t gs_mlp_patches(int32_t width, int32_t height);
+/* Number of parameters (58,243): the layout of `grads` below. */
+int64_t gs_mlp_param_count(void);
+size_t gs_mlp_workspace_size(int64_t n_patches);
+
+/* Inference: out [n_patches][3] = (spawn logit, depth, log-scale) per patch in
+ * row-major patch order. image [3][height][width]. */
+int gs_mlp_forward(const gs_mlp_params* p, const float* image, int32_t width, int32_t height, float* out,
+                   const gs_mlp_config* cfg, void* ws, size_t ws_bytes, void* stream);
+
+/* One training step on a frame. targets [n_patches][4] = (fraction of the
+ * patch's pixels whose direct-sampling spawn was kept, their mean depth, mean
+ * log-scale, 1 if any was kept else 0). Loss (device float) = mean over
+ * patches of BCE(sigmoid(logit), fraction) + w_depth |depth - target| mask +
+ * w_scale |log-scale - target| mask. grads (optional, device [param_count])
+ * receives dL/d(w1, b1, w2, b2, w3, b3, w4, b4) flattened in that order; when
+ * m and v are given (Adam moments, same layout as p) p is updated by Adam with
+ * step `step` (>= 1) or *step_dev. out (optional) as in gs_mlp_forward. */
+int gs_mlp_train_step(const gs_mlp_params* p, const gs_mlp_params* m, const gs_mlp_params* v, const float* image,
+                      int32_t width, int32_t height, const float* targets, const gs_mlp_config* cfg, int32_t step,
+                      const int32_t* step_dev, float* loss, float* out, float* grads, void* ws, size_t ws_bytes,
+                      void* stream);
+
+/* The MLP's matrix product on its own, for testing the two tensor-core paths:
+ * C [M][N] (ldc) = A [M][K] (lda) . B [N][K]^T (ldb); A, B bfloat16 (uint16
+ * bit patterns), K-major; K, N multiples of 16, lda, ldb multiples of 8. */
+int gs_mlp_gemm_bf16(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc,
+                     int32_t M, int32_t N, int32_t K, int32_t tensor_path, void* stream);
+
+/* Error code recorded by a tensor-memory GEMM whose completion wait timed out
+ * (0 = none). Synchronous; for tests. */
+int gs_mlp_tc_error(int32_t* out);
+
 /* Learning rates of the parameter groups and the Adam constants. */
 typedef struct gs_adam_config {
     float lr_mean, lr_opacity, lr_scale, lr_rot, lr_sh_dc, lr_sh_rest;

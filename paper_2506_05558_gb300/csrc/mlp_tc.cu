@@ -1,0 +1,212 @@
+// Tensor-core path (sm_100-family tcgen05) of the MLP's "TN" GEMM:
+// C[m][n] = sum_k A[m][k] B[n][k], bf16 operands (K-major), FP32 accumulator
+// in tensor memory.
+//
+// One CTA (4 warps) computes a 128 x Nt tile (Nt = N rounded up to 16, at most
+// 256) of one K split. Per 64-wide K stage all threads copy the A (128 x 64)
+// and B (Nt x 64) tiles into shared memory in the canonical no-swizzle K-major
+// layout (8-row x 16-byte core matrices, K-adjacent cores 128 B apart, 8-row
+// groups 1024 B apart), fence the async proxy, and one elected thread issues
+// four tcgen05.mma (K = 16 each) into the TMEM accumulator and commits them to
+// an mbarrier. The epilogue reads the accumulator back with tcgen05.ld (each
+// warp its 32 TMEM lanes) and stores FP32 rows. Every wait on the mbarrier is
+// bounded; on timeout the kernel records an error code, frees its TMEM and
+// returns.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace gs {
+
+constexpr int kTcM = 128;
+constexpr int kTcBK = 64;
+constexpr int kTcMaxN = 256;
+constexpr uint32_t kTcSpinLimit = 1u << 22;
+
+__device__ int g_tc_error;  // 0 = ok, otherwise the line of the failing wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading (K) and
+// stride (M/N) byte offsets in 16-byte units, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, N, M.
+__host__ __device__ constexpr uint32_t instr_desc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(128) k_gemm_tn_tc(const __nv_bfloat16* __restrict__ A, int64_t lda,
+                                                    const __nv_bfloat16* __restrict__ B, int64_t ldb,
+                                                    float* __restrict__ C, int64_t ldc, int64_t M, int N, int Nt,
+                                                    int64_t K, int64_t k_per_split, int64_t c_split_stride,
+                                                    uint32_t tmem_cols) {
+    extern __shared__ __align__(1024) uint8_t smem[];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    uint8_t* sA = smem;                        // 128 x 64 bf16 = 16 KB
+    uint8_t* sB = smem + kTcM * kTcBK * 2;     // Nt x 64 bf16
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t m0 = (int64_t)blockIdx.x * kTcM;
+    const int64_t kb = (int64_t)blockIdx.z * k_per_split;
+    const int64_t ke = min(K, kb + k_per_split);
+    const uint32_t bar = smem_u32(&s_bar);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_fail = 0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const uint32_t idesc = instr_desc_bf16(kTcM, Nt);
+    uint32_t phase = 0;
+    bool first = true;
+
+    for (int64_t k0 = kb; k0 < ke; k0 += kTcBK) {
+        // stage A (128 rows) and B (Nt rows) as 8x8 core matrices, zero-filled outside
+        const int rows_total = kTcM + Nt;
+        for (int i = tid; i < rows_total * (kTcBK / 8); i += 128) {
+            const int r = i / (kTcBK / 8), kc = i % (kTcBK / 8);
+            const bool isA = r < kTcM;
+            const int rr = isA ? r : r - kTcM;
+            const int64_t grow = isA ? m0 + rr : rr;
+            const int64_t gk = k0 + kc * 8;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            const bool row_ok = isA ? grow < M : grow < N;
+            if (row_ok && gk + 8 <= ke) {
+                const __nv_bfloat16* src = (isA ? A + grow * lda : B + grow * ldb) + gk;
+                v = *reinterpret_cast<const uint4*>(src);
+            } else if (row_ok) {
+                __nv_bfloat16 tmp[8];
+                const __nv_bfloat16* src = (isA ? A + grow * lda : B + grow * ldb);
+                for (int e = 0; e < 8; e++) tmp[e] = (gk + e < ke) ? src[gk + e] : __float2bfloat16_rn(0.f);
+                v = *reinterpret_cast<uint4*>(tmp);
+            }
+            uint8_t* base = isA ? sA : sB;
+            const uint32_t off = (uint32_t)(((rr >> 3) * (kTcBK / 8) + kc) * 128 + (rr & 7) * 16);
+            *reinterpret_cast<uint4*>(base + off) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+            for (int s = 0; s < kTcBK / 16; s++) {
+                const uint64_t ad = smem_desc(a0 + s * 256, 128, 1024);
+                const uint64_t bd = smem_desc(b0 + s * 256, 128, 1024);
+                const uint32_t acc = (first && s == 0) ? 0u : 1u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                    : "memory");
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+                         : "memory");
+            uint32_t spins = 0;
+            while (!mbar_try_wait(bar, phase)) {
+                if (++spins > kTcSpinLimit) {
+                    s_fail = 1;
+                    break;
+                }
+            }
+        }
+        first = false;
+        phase ^= 1u;
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        if (s_fail) break;
+    }
+
+    if (!s_fail && !first) {
+        // epilogue: warp w reads TMEM lanes 32w..32w+31 (rows of the tile), 16 columns at a time
+        const int64_t row = m0 + 32 * warp + lane;
+        float* Cz = C + (int64_t)blockIdx.z * c_split_stride;
+        for (int c0 = 0; c0 < Nt; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 16; j++)
+                    if (c0 + j < N) Cz[row * ldc + c0 + j] = __uint_as_float(r[j]);
+            }
+        }
+    } else if (s_fail && tid == 0) {
+        atomicCAS(&g_tc_error, 0, __LINE__);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
+int gemm_tn_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int64_t ldb, float* C, int64_t ldc,
+               int64_t M, int N, int64_t K, int64_t k_per_split, int64_t c_split_stride, cudaStream_t s) {
+    const int Nt = (int)ceil_div(N, 16) * 16;
+    if (Nt > kTcMaxN || M <= 0 || K <= 0) return GS_ERR_INVALID_ARG;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)Nt) cols <<= 1;
+    const size_t smem = (size_t)(kTcM + Nt) * kTcBK * 2;
+    static bool attr_set = false;
+    if (!attr_set) {
+        // at most ~115 KB of the SM's shared memory per CTA so that at most two
+        // CTAs (2 x 256 TMEM columns) share an SM
+        cudaFuncSetAttribute(k_gemm_tn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        attr_set = true;
+    }
+    const size_t smem_launch = smem < 80 * 1024 ? 80 * 1024 : smem;
+    const int64_t splits = ceil_div(K, k_per_split);
+    dim3 grid((unsigned)ceil_div(M, kTcM), 1, (unsigned)splits);
+    k_gemm_tn_tc<<<grid, 128, smem_launch, s>>>(A, lda, B, ldb, C, ldc, M, N, Nt, K, k_per_split, c_split_stride,
+                                                 cols);
+    count_launch();
+    return GS_OK;
+}
+
+}  // namespace gs
+
+extern "C" int gs_mlp_tc_error(int32_t* out) {
+    if (!out) return GS_ERR_INVALID_ARG;
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, gs::g_tc_error, sizeof(int)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
+    *out = v;
+    return GS_OK;
+}

@@ -31,6 +31,8 @@ EXPORTS = [
     "gs_adam_step", "gs_pose_step", "gs_l1_loss", "gs_composite_bwd", "gs_project_bwd", "gs_launch_count",
     "gs_spawn_workspace_size", "gs_spawn_propose", "gs_counter_add", "gs_spawn_propose_noalloc",
     "gs_anchor_check", "gs_anchor_offload", "gs_anchor_load",
+    "gs_mlp_patches", "gs_mlp_param_count", "gs_mlp_workspace_size", "gs_mlp_forward", "gs_mlp_train_step",
+    "gs_mlp_gemm_bf16", "gs_mlp_tc_error",
 ]
 
 
@@ -93,6 +95,15 @@ class gs_spawn_out(C.Structure):
                 ("p_l", C.c_void_p), ("p_pen", C.c_void_p), ("p_s", C.c_void_p)]
 
 
+class gs_mlp_params(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in ("w1", "b1", "w2", "b2", "w3", "b3", "w4", "b4")]
+
+
+class gs_mlp_config(C.Structure):
+    _fields_ = [("tensor_path", C.c_int32), ("w_depth", C.c_float), ("w_scale", C.c_float), ("lr", C.c_float),
+                ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float)]
+
+
 _lib = None
 
 
@@ -134,6 +145,17 @@ def lib():
                                          C.c_size_t, P]),
             "gs_launch_count": (C.c_int64, []),
             "gs_anchor_check": (C.c_int, [C.POINTER(gs_gaussians), P, C.c_float, P, P, P]),
+            "gs_mlp_patches": (C.c_int64, [C.c_int32, C.c_int32]),
+            "gs_mlp_param_count": (C.c_int64, []),
+            "gs_mlp_workspace_size": (C.c_size_t, [C.c_int64]),
+            "gs_mlp_forward": (C.c_int, [C.POINTER(gs_mlp_params), P, C.c_int32, C.c_int32, P,
+                                         C.POINTER(gs_mlp_config), P, C.c_size_t, P]),
+            "gs_mlp_train_step": (C.c_int, [C.POINTER(gs_mlp_params), C.POINTER(gs_mlp_params),
+                                            C.POINTER(gs_mlp_params), P, C.c_int32, C.c_int32, P,
+                                            C.POINTER(gs_mlp_config), C.c_int32, P, P, P, P, P, C.c_size_t, P]),
+            "gs_mlp_gemm_bf16": (C.c_int, [P, C.c_int64, P, C.c_int64, P, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                                           C.c_int32, P]),
+            "gs_mlp_tc_error": (C.c_int, [C.POINTER(C.c_int32)]),
             "gs_anchor_offload": (C.c_int, [C.POINTER(gs_gaussians)] * 6 + [P]),
             "gs_anchor_load": (C.c_int, [C.POINTER(gs_gaussians)] * 6 + [P]),
             "gs_spawn_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
@@ -461,6 +483,83 @@ def gs_anchor_load(host_params: Gaussians, host_m, host_v, params: Gaussians, m,
 def pinned_gaussians(n: int) -> Gaussians:
     z = lambda k: torch.zeros((n, k), dtype=torch.float32).pin_memory()
     return Gaussians(z(4), z(4), z(4), z(48))
+
+
+MLP_SHAPES = [("w1", (128, 194)), ("b1", (128,)), ("w2", (128, 128)), ("b2", (128,)), ("w3", (128, 128)),
+              ("b3", (128,)), ("w4", (3, 128)), ("b4", (3,))]
+
+
+@dataclass
+class MlpParams:
+    """FP32 master parameters of the learned spawn proposal (device tensors)."""
+    t: dict
+
+    @staticmethod
+    def from_numpy(layers, device="cuda") -> "MlpParams":
+        """layers: [(W1, b1), ..., (W4, b4)] in nn.Linear layout."""
+        t = {}
+        for l, (W, b) in enumerate(layers):
+            t[f"w{l + 1}"] = torch.tensor(np.asarray(W, np.float32), device=device)
+            t[f"b{l + 1}"] = torch.tensor(np.asarray(b, np.float32), device=device)
+        return MlpParams(t)
+
+    @staticmethod
+    def zeros(device="cuda") -> "MlpParams":
+        return MlpParams({k: torch.zeros(shape, dtype=torch.float32, device=device) for k, shape in MLP_SHAPES})
+
+    def c(self) -> gs_mlp_params:
+        return gs_mlp_params(*[_ptr(self.t[k]) for k, _ in MLP_SHAPES])
+
+    def numpy(self):
+        return [(self.t[f"w{l}"].cpu().numpy(), self.t[f"b{l}"].cpu().numpy()) for l in range(1, 5)]
+
+
+def mlp_config(tensor_path=0, w_depth=1.0, w_scale=1.0, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8) -> gs_mlp_config:
+    return gs_mlp_config(tensor_path, w_depth, w_scale, lr, beta1, beta2, eps)
+
+
+def gs_mlp_patches(width: int, height: int) -> int:
+    return int(lib().gs_mlp_patches(width, height))
+
+
+def gs_mlp_param_count() -> int:
+    return int(lib().gs_mlp_param_count())
+
+
+def gs_mlp_workspace_size(n_patches: int) -> int:
+    return int(lib().gs_mlp_workspace_size(n_patches))
+
+
+def gs_mlp_forward(p: MlpParams, image: torch.Tensor, width: int, height: int, out: torch.Tensor,
+                   cfg: gs_mlp_config, ws: torch.Tensor, stream=None):
+    pc = p.c()
+    _check(lib().gs_mlp_forward(C.byref(pc), _ptr(image), width, height, _ptr(out), C.byref(cfg), _ptr(ws),
+                                ws.numel(), _stream(stream)), "gs_mlp_forward")
+
+
+def gs_mlp_train_step(p: MlpParams, m, v, image: torch.Tensor, width: int, height: int, targets: torch.Tensor,
+                      cfg: gs_mlp_config, step: int, loss: torch.Tensor, ws: torch.Tensor, out=None, grads=None,
+                      step_dev=None, stream=None):
+    pc = p.c()
+    mc = None if m is None else C.byref(m.c())
+    vc = None if v is None else C.byref(v.c())
+    _check(lib().gs_mlp_train_step(C.byref(pc), mc, vc, _ptr(image), width, height, _ptr(targets), C.byref(cfg), step,
+                                   _ptr(step_dev), _ptr(loss), _ptr(out), _ptr(grads), _ptr(ws), ws.numel(),
+                                   _stream(stream)), "gs_mlp_train_step")
+
+
+def gs_mlp_gemm_bf16(A: torch.Tensor, B: torch.Tensor, C_out: torch.Tensor, tensor_path: int, stream=None):
+    """A [M][K], B [N][K] bfloat16 tensors; C_out [M][N] float32."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(lib().gs_mlp_gemm_bf16(_ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C_out), C_out.stride(0), M, N, K,
+                                  tensor_path, _stream(stream)), "gs_mlp_gemm_bf16")
+
+
+def gs_mlp_tc_error() -> int:
+    v = C.c_int32(0)
+    _check(lib().gs_mlp_tc_error(C.byref(v)), "gs_mlp_tc_error")
+    return int(v.value)
 
 
 def adam_config(lr_mean=1.6e-4, lr_opacity=0.05, lr_scale=5e-3, lr_rot=1e-3, lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4,

@@ -1,0 +1,122 @@
+"""Learned spawn proposal on the GPU against the FP64 oracle (oracle/mlp.py),
+for both tensor-core paths (0: mma.sync tiles, 1: tcgen05.mma with the
+accumulator in tensor memory): the bf16 GEMM against NumPy, the forward pass
+at 1e-3, the training step's loss at 1e-3 and weight gradients at 1e-2, one
+Adam step."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import assert_close
+from oracle import mlp as OM
+from paper_2506_05558_gb300 import gs
+
+pytestmark = pytest.mark.gpu
+PATHS = [0, 1]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2506_05558_gb300 import build
+    build.build()
+
+
+def bf16_pair(rng, M, N, K):
+    A = torch.tensor(rng.standard_normal((M, K)), dtype=torch.float32).to(torch.bfloat16)
+    B = torch.tensor(rng.standard_normal((N, K)), dtype=torch.float32).to(torch.bfloat16)
+    ref = A.double() @ B.double().T
+    return A.cuda(), B.cuda(), ref.numpy()
+
+
+@pytest.mark.parametrize("PATH", PATHS)
+@pytest.mark.parametrize("M,N,K", [(300, 128, 208), (100, 16, 128), (128, 208, 4096), (1000, 128, 16), (7, 32, 32)])
+def test_gemm_matches_numpy(M, N, K, PATH):
+    rng = np.random.default_rng(M + N + K)
+    A, B, ref = bf16_pair(rng, M, N, K)
+    C = torch.full((M, N), float("nan"), device="cuda")
+    gs.gs_mlp_gemm_bf16(A, B, C, PATH)
+    torch.cuda.synchronize()
+    assert_close(C.cpu().numpy(), ref, 1e-5, what=f"gemm path {PATH}")
+    if PATH == 1:
+        assert gs.gs_mlp_tc_error() == 0
+
+
+def mlp_case(seed, W=96, H=64):
+    rng = np.random.default_rng(seed)
+    layers = OM.init_params(rng)
+    image = rng.random((3, H, W))
+    n = (W // 8) * (H // 8)
+    targets = np.stack([rng.random(n), rng.uniform(2, 10, n), rng.normal(-4, 0.5, n),
+                        (rng.random(n) < 0.6).astype(float)], 1)
+    return rng, layers, image, targets
+
+
+def run_train(layers, image, targets, path, with_adam=False, lr=1e-3):
+    H, W = image.shape[1:]
+    n = gs.gs_mlp_patches(W, H)
+    p = gs.MlpParams.from_numpy(layers)
+    m = gs.MlpParams.zeros() if with_adam else None
+    v = gs.MlpParams.zeros() if with_adam else None
+    ws = gs.workspace(gs.gs_mlp_workspace_size(n))
+    loss = torch.zeros(1, device="cuda")
+    out = torch.zeros((n, 3), device="cuda")
+    grads = torch.zeros(gs.gs_mlp_param_count(), device="cuda")
+    img = torch.tensor(image, dtype=torch.float32, device="cuda")
+    tg = torch.tensor(targets, dtype=torch.float32, device="cuda")
+    cfg = gs.mlp_config(tensor_path=path, lr=lr)
+    gs.gs_mlp_train_step(p, m, v, img, W, H, tg, cfg, 1, loss, ws, out=out, grads=grads)
+    torch.cuda.synchronize()
+    return p, loss.item(), out.cpu().numpy(), grads.cpu().numpy()
+
+
+def oracle_train(layers, image, targets):
+    X = OM.patch_features(image)
+    Y, cache = OM.forward(layers, X)
+    L, dY = OM.loss(Y, targets[:, 0], targets[:, 1], targets[:, 2], targets[:, 3])
+    grads = OM.backward(layers, cache, dY)
+    flat = np.concatenate([np.concatenate([dW.reshape(-1), db]) for dW, db in grads])
+    return Y, L, grads, flat
+
+
+@pytest.mark.parametrize("PATH", PATHS)
+def test_forward_matches_oracle(PATH):
+    rng, layers, image, targets = mlp_case(1)
+    H, W = image.shape[1:]
+    n = gs.gs_mlp_patches(W, H)
+    out = torch.zeros((n, 3), device="cuda")
+    ws = gs.workspace(gs.gs_mlp_workspace_size(n))
+    gs.gs_mlp_forward(gs.MlpParams.from_numpy(layers), torch.tensor(image, dtype=torch.float32, device="cuda"), W, H,
+                      out, gs.mlp_config(tensor_path=PATH), ws)
+    torch.cuda.synchronize()
+    Y, _, _, _ = oracle_train(layers, image, targets)
+    assert_close(out.cpu().numpy(), Y, 1e-3, what="mlp forward")
+
+
+@pytest.mark.parametrize("PATH", PATHS)
+def test_train_step_loss_and_gradients_match_oracle(PATH):
+    rng, layers, image, targets = mlp_case(2)
+    _, loss, out, grads = run_train(layers, image, targets, PATH)
+    Y, L, g, flat = oracle_train(layers, image, targets)
+    assert_close(out, Y, 1e-3, what="outputs")
+    assert abs(loss - L) <= 1e-3 * abs(L)
+    off = 0
+    for l, (dW, db) in enumerate(g):
+        for name, ref in ((f"dW{l + 1}", dW), (f"db{l + 1}", db)):
+            got = grads[off:off + ref.size].reshape(ref.shape)
+            assert_close(got, ref, 1e-2, what=name)
+            off += ref.size
+
+
+@pytest.mark.parametrize("PATH", PATHS)
+def test_adam_step_matches_oracle(PATH):
+    rng, layers, image, targets = mlp_case(3)
+    p, _, _, grads = run_train(layers, image, targets, PATH, with_adam=True, lr=1e-3)
+    # Adam's first step from zero moments moves each parameter by lr * sign(g)
+    got = p.numpy()
+    off = 0
+    for (W, b), (W2, b2) in zip(layers, got):
+        for ref, new in ((W, W2), (b, b2)):
+            g = grads[off:off + ref.size].reshape(ref.shape)
+            off += ref.size
+            want = ref - 1e-3 * g / (np.abs(g) + 1e-8)
+            assert_close(new, want, 1e-5, what="adam")
