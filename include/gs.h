@@ -383,6 +383,25 @@ int gs_mlp_train_step(const gs_mlp_params* p, const gs_mlp_params* m, const gs_m
 int gs_mlp_gemm_bf16(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc,
                      int32_t M, int32_t N, int32_t K, int32_t tensor_path, void* stream);
 
+/* Training targets of the learned proposal from direct sampling: for spawned
+ * Gaussians i (pixel index, camera depth, log-scale) with kept[i] != 0 (still
+ * present after the frame's optimisation), targets [n_patches][4] = (kept
+ * count / 64, their mean depth, mean log-scale, 1 if any kept else 0) per 8x8
+ * patch. ws: gs_mlp_targets_workspace_size bytes. */
+size_t gs_mlp_targets_workspace_size(int32_t width, int32_t height);
+int gs_mlp_targets(const int32_t* pixel, const float* depth, const float* log_scale, const uint8_t* kept,
+                   int64_t n_spawn, int32_t width, int32_t height, float* targets, void* ws, size_t ws_bytes,
+                   void* stream);
+
+/* Spawning from the learned proposal's outputs mlp_out [n_patches][3]: pixel p
+ * of patch m spawns iff u < sigmoid(logit_m) (u = Philox4x32-10 of counter
+ * (p, frame, 1, 0) and key seed) and the predicted depth is positive; the new
+ * Gaussian sits at the pixel centre at the patch's predicted depth with its
+ * predicted log-scale on all axes (other attributes as gs_spawn_propose).
+ * Output, workspace size and status as for gs_spawn_propose. */
+int gs_spawn_learned(const float* image, const float* mlp_out, int32_t width, int32_t height, const gs_camera* cam,
+                     const gs_spawn_config* sc, const gs_spawn_out* out, void* ws, size_t ws_bytes, void* stream);
+
 /* Error code recorded by a tensor-memory GEMM whose completion wait timed out
  * (0 = none). Synchronous; for tests. */
 int gs_mlp_tc_error(int32_t* out);

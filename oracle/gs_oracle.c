@@ -801,3 +801,15 @@ void or_spawn_maps(const double* image, const double* render, int W, int H, doub
         amb[p] = fabs(u[p] - p_s[p]) < margin;
     }
 }
+
+/* u[p] = (word 0 of Philox4x32-10(counter (p, c1, c2, 0), key seed)) >> 8, / 2^24,
+ * for p = 0 .. n-1: the uniform draws of the spawn masks. */
+void or_philox_uniforms(int64_t n, uint32_t c1, uint32_t c2, uint64_t seed, double* u) {
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < n; p++) {
+        uint32_t ctr[4] = {(uint32_t)p, c1, c2, 0u}, o[4];
+        or_philox4x32_10(ctr, key, o);
+        u[p] = (double)(o[0] >> 8) / 16777216.0;
+    }
+}

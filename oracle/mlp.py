@@ -134,3 +134,58 @@ def adam(params, grads, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 def zeros_like_params(params):
     return [(np.zeros_like(W), np.zeros_like(b)) for W, b in params]
+
+
+# ---------------------------------------------------------------------------
+# Targets from direct sampling and spawning from the network's predictions
+# ---------------------------------------------------------------------------
+
+def targets_from_spawns(pixel, depth, log_scale, kept, W, H):
+    """Per 8x8 patch: (kept count / 64, mean depth, mean log-scale, any kept)
+    over the spawned Gaussians that were kept after the frame's optimisation."""
+    nx, ny = W // PATCH, H // PATCH
+    out = np.zeros((nx * ny, 4))
+    pixel = np.asarray(pixel)
+    keep = np.asarray(kept, bool)
+    for p, z, s in zip(pixel[keep], np.asarray(depth)[keep], np.asarray(log_scale)[keep]):
+        m = (p // W // PATCH) * nx + (p % W) // PATCH
+        out[m, 0] += 1
+        out[m, 1] += z
+        out[m, 2] += s
+    has = out[:, 0] > 0
+    out[has, 1] /= out[has, 0]
+    out[has, 2] /= out[has, 0]
+    out[:, 3] = has
+    out[:, 0] /= PATCH * PATCH
+    return out
+
+
+def spawn_learned(image, mlp_out, cam, seed, frame, margin=1e-6):
+    """Pixel p of patch m spawns iff u < sigmoid(logit_m) and the predicted depth
+    is positive, u the Philox draw of counter (p, frame, 1, 0). The Gaussian sits
+    at the pixel centre at the patch's predicted depth, with its predicted
+    log-scale on all axes, identity rotation, opacity 0.5 and the pixel colour
+    as SH DC. Returns the spawns in pixel order and the ambiguous pixels."""
+    from . import oracle as O
+    image = np.asarray(image, np.float64)
+    _, H, W = image.shape
+    nx = W // PATCH
+    u = O.philox_uniforms(W * H, frame, 1, seed)
+    p = np.arange(W * H)
+    x, y = p % W, p // W
+    m = (y // PATCH) * nx + x // PATCH
+    out = np.asarray(mlp_out, np.float64)
+    prob = 1.0 / (1.0 + np.exp(-out[m, 0]))
+    z = out[m, 1]
+    spawn = (u < prob) & (z > 0)
+    amb = np.abs(u - prob) < margin
+    idx = np.nonzero(spawn)[0]
+    zi = z[idx]
+    pc = np.stack([(x[idx] + 0.5 - cam["cx"]) * zi / cam["fx"], (y[idx] + 0.5 - cam["cy"]) * zi / cam["fy"], zi], 1)
+    R = np.asarray(cam["R"], np.float64)
+    t = np.asarray(cam["t"], np.float64)
+    mu = (pc - t) @ R
+    c0 = 0.5 / math.sqrt(math.pi)
+    rgb = image.reshape(3, -1)[:, idx].T
+    return dict(pixel=idx, mean=mu, log_scale=np.repeat(out[m[idx], 2][:, None], 3, 1), sh_dc=(rgb - 0.5) / c0,
+                amb=amb)

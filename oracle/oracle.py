@@ -50,6 +50,8 @@ def lib():
         u32 = np.ctypeslib.ndpointer(np.uint32, flags="C")
         _lib.or_philox4x32_10.restype = None
         _lib.or_philox4x32_10.argtypes = [u32, u32, u32]
+        _lib.or_philox_uniforms.restype = None
+        _lib.or_philox_uniforms.argtypes = [C.c_int64, C.c_uint32, C.c_uint32, C.c_uint64, d]
         _lib.or_log_kernel.restype = C.c_int
         _lib.or_log_kernel.argtypes = [C.c_double, d]
         _lib.or_spawn_maps.restype = None
@@ -290,6 +292,12 @@ def philox4x32_10(ctr, key):
     out = np.zeros(4, np.uint32)
     lib().or_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
     return out
+
+
+def philox_uniforms(n, c1, c2, seed):
+    u = np.zeros(n)
+    lib().or_philox_uniforms(n, c1, c2, int(seed), u)
+    return u
 
 
 def log_kernel(sigma):

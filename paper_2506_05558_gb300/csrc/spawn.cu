@@ -293,3 +293,149 @@ extern "C" int gs_spawn_propose_noalloc(const float* image, const float* render,
     GS_CUDA_CHECK_LAUNCH();
     return GS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Learned spawn proposal: training targets and spawning from its predictions.
+// ---------------------------------------------------------------------------
+namespace gs {
+
+// Scatter the kept spawns into per-pixel slots (each pixel spawns at most once).
+__global__ void k_kept_scatter(const int32_t* __restrict__ pixel, const float* __restrict__ depth,
+                               const float* __restrict__ log_scale, const uint8_t* __restrict__ kept, int64_t n,
+                               int64_t hw, float4* __restrict__ pix_slot) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !kept[i]) return;
+    const int32_t p = pixel[i];
+    if (p < 0 || (int64_t)p >= hw) return;
+    pix_slot[p] = make_float4(1.f, depth[i], log_scale[i], 0.f);
+}
+
+// One thread per 8x8 patch: kept fraction, mean depth and log-scale, any-kept.
+__global__ void k_patch_targets(const float4* __restrict__ pix_slot, int W, int H, float* __restrict__ targets) {
+    const int nx = W / 8, ny = H / 8;
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= (int64_t)nx * ny) return;
+    const int px = (int)(m % nx), py = (int)(m / nx);
+    float cnt = 0.f, zs = 0.f, ss = 0.f;
+    for (int dy = 0; dy < 8; dy++)
+        for (int dx = 0; dx < 8; dx++) {
+            const float4 v = pix_slot[(int64_t)(py * 8 + dy) * W + px * 8 + dx];
+            if (v.x > 0.f) {
+                cnt += 1.f;
+                zs += v.y;
+                ss += v.z;
+            }
+        }
+    targets[m * 4 + 0] = cnt / 64.f;
+    targets[m * 4 + 1] = cnt > 0.f ? zs / cnt : 0.f;
+    targets[m * 4 + 2] = cnt > 0.f ? ss / cnt : 0.f;
+    targets[m * 4 + 3] = cnt > 0.f ? 1.f : 0.f;
+}
+
+// Spawn flags from the MLP: pixel p of patch m spawns iff u < sigmoid(logit_m)
+// and the predicted depth is positive; u = Philox(counter (p, frame, 1, 0)).
+__global__ void k_learned_flags(const float* __restrict__ mlp_out, int W, int H, uint2 key, uint32_t frame,
+                                uint32_t* __restrict__ flag) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)W * H) return;
+    const int x = (int)(p % W), y = (int)(p / W);
+    const int64_t m = (int64_t)(y / 8) * (W / 8) + x / 8;
+    const float logit = mlp_out[m * 3 + 0], z = mlp_out[m * 3 + 1];
+    const float prob = 1.f / (1.f + expf(-logit));
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)p, frame, 1u, 0u), key);
+    const float u = (float)(r.x >> 8) * (1.f / 16777216.f);
+    flag[p] = (u < prob && z > 0.f && isfinite(z)) ? 1u : 0u;
+}
+
+__global__ void k_learned_emit(const float* __restrict__ image, const float* __restrict__ mlp_out, int W, int H,
+                               const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                               const gs_camera* __restrict__ cam, int64_t capacity, float4* __restrict__ mean_opa,
+                               float4* __restrict__ scale, float4* __restrict__ quat, float4* __restrict__ sh,
+                               int32_t* __restrict__ pixel) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int64_t)W * H || !flag[p]) return;
+    const int64_t o = pos[p];
+    if (o >= capacity) return;
+    const int x = (int)(p % W), y = (int)(p / W);
+    const int64_t m = (int64_t)(y / 8) * (W / 8) + x / 8;
+    const float z = mlp_out[m * 3 + 1], ls = mlp_out[m * 3 + 2];
+    const gs_camera& c = *cam;
+    const float xc = (x + 0.5f - c.cx) * z / c.fx, yc = (y + 0.5f - c.cy) * z / c.fy;
+    const float qx = xc - c.t[0], qy = yc - c.t[1], qz = z - c.t[2];
+    mean_opa[o] = make_float4(c.R[0] * qx + c.R[3] * qy + c.R[6] * qz, c.R[1] * qx + c.R[4] * qy + c.R[7] * qz,
+                              c.R[2] * qx + c.R[5] * qy + c.R[8] * qz, 0.f);
+    scale[o] = make_float4(ls, ls, ls, 0.f);
+    quat[o] = make_float4(1.f, 0.f, 0.f, 0.f);
+    const int64_t plane = (int64_t)W * H;
+    const float inv_c0 = 3.5449077018110318f;  // 1 / SH band-0 constant = 2 sqrt(pi)
+    float4* row = sh + 12 * o;
+    row[0] = make_float4((image[p] - 0.5f) * inv_c0, (image[plane + p] - 0.5f) * inv_c0,
+                         (image[2 * plane + p] - 0.5f) * inv_c0, 0.f);
+#pragma unroll
+    for (int r = 1; r < 12; r++) row[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (pixel) pixel[o] = (int32_t)p;
+}
+
+}  // namespace gs
+
+extern "C" size_t gs_mlp_targets_workspace_size(int32_t width, int32_t height) {
+    if (width <= 0 || height <= 0) return 0;
+    return align256(sizeof(float4) * (size_t)width * height);
+}
+
+extern "C" int gs_mlp_targets(const int32_t* pixel, const float* depth, const float* log_scale, const uint8_t* kept,
+                              int64_t n_spawn, int32_t width, int32_t height, float* targets, void* ws,
+                              size_t ws_bytes, void* stream) {
+    if (!targets || width <= 0 || height <= 0 || width % 8 || height % 8 || n_spawn < 0 ||
+        (n_spawn > 0 && (!pixel || !depth || !log_scale || !kept)))
+        return GS_ERR_INVALID_ARG;
+    const int64_t hw = (int64_t)width * height;
+    if (!ws || ws_bytes < gs_mlp_targets_workspace_size(width, height) || ((uintptr_t)ws & 255))
+        return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    float4* slot = (float4*)ws;
+    cudaMemsetAsync(slot, 0, sizeof(float4) * hw, s);
+    if (n_spawn > 0) {
+        k_kept_scatter<<<(unsigned)ceil_div(n_spawn, 256), 256, 0, s>>>(pixel, depth, log_scale, kept, n_spawn, hw,
+                                                                         slot);
+        count_launch();
+    }
+    const int64_t np = hw / 64;
+    k_patch_targets<<<(unsigned)ceil_div(np, 256), 256, 0, s>>>(slot, width, height, targets);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
+extern "C" int gs_spawn_learned(const float* image, const float* mlp_out, int32_t width, int32_t height,
+                                const gs_camera* cam, const gs_spawn_config* sc, const gs_spawn_out* out, void* ws,
+                                size_t ws_bytes, void* stream) {
+    if (!image || !mlp_out || !cam || !sc || !out || width <= 0 || height <= 0 || width % 8 || height % 8)
+        return GS_ERR_INVALID_ARG;
+    if (!out->count || !out->status || out->capacity < 0 ||
+        (out->capacity > 0 && (!out->mean_opa || !out->scale || !out->quat || !out->sh)))
+        return GS_ERR_INVALID_ARG;
+    const int64_t hw = (int64_t)width * height;
+    Carve c{(char*)ws, 0, ws_bytes};
+    uint32_t* flag = c.take<uint32_t>(hw);
+    uint32_t* pos = c.take<uint32_t>(hw);
+    uint32_t* total = c.take<uint32_t>(4);
+    void* scan_ws = c.take<char>(scan_workspace_bytes(hw));
+    if (!ws || !c.ok() || ((uintptr_t)ws & 255)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint2 key = make_uint2((uint32_t)sc->seed, (uint32_t)(sc->seed >> 32));
+    k_learned_flags<<<(unsigned)ceil_div(hw, 256), 256, 0, s>>>(mlp_out, width, height, key, sc->frame, flag);
+    count_launch();
+    scan_exclusive_u32(flag, pos, hw, total, scan_ws, s);
+    k_spawn_count<<<1, 1, 0, s>>>(total, out->capacity, out->count, out->status);
+    count_launch();
+    if (out->capacity > 0) {
+        k_learned_emit<<<(unsigned)ceil_div(hw, 256), 256, 0, s>>>(image, mlp_out, width, height, flag, pos, cam,
+                                                                    out->capacity, (float4*)out->mean_opa,
+                                                                    (float4*)out->scale, (float4*)out->quat,
+                                                                    (float4*)out->sh, out->pixel);
+        count_launch();
+    }
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}

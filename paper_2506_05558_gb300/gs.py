@@ -32,7 +32,7 @@ EXPORTS = [
     "gs_spawn_workspace_size", "gs_spawn_propose", "gs_counter_add", "gs_spawn_propose_noalloc",
     "gs_anchor_check", "gs_anchor_offload", "gs_anchor_load",
     "gs_mlp_patches", "gs_mlp_param_count", "gs_mlp_workspace_size", "gs_mlp_forward", "gs_mlp_train_step",
-    "gs_mlp_gemm_bf16", "gs_mlp_tc_error",
+    "gs_mlp_gemm_bf16", "gs_mlp_tc_error", "gs_mlp_targets_workspace_size", "gs_mlp_targets", "gs_spawn_learned",
 ]
 
 
@@ -156,6 +156,10 @@ def lib():
             "gs_mlp_gemm_bf16": (C.c_int, [P, C.c_int64, P, C.c_int64, P, C.c_int64, C.c_int32, C.c_int32, C.c_int32,
                                            C.c_int32, P]),
             "gs_mlp_tc_error": (C.c_int, [C.POINTER(C.c_int32)]),
+            "gs_mlp_targets_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
+            "gs_mlp_targets": (C.c_int, [P, P, P, P, C.c_int64, C.c_int32, C.c_int32, P, P, C.c_size_t, P]),
+            "gs_spawn_learned": (C.c_int, [P, P, C.c_int32, C.c_int32, P, C.POINTER(gs_spawn_config),
+                                           C.POINTER(gs_spawn_out), P, C.c_size_t, P]),
             "gs_anchor_offload": (C.c_int, [C.POINTER(gs_gaussians)] * 6 + [P]),
             "gs_anchor_load": (C.c_int, [C.POINTER(gs_gaussians)] * 6 + [P]),
             "gs_spawn_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
@@ -560,6 +564,24 @@ def gs_mlp_tc_error() -> int:
     v = C.c_int32(0)
     _check(lib().gs_mlp_tc_error(C.byref(v)), "gs_mlp_tc_error")
     return int(v.value)
+
+
+def gs_mlp_targets(pixel, depth, log_scale, kept, n_spawn: int, width: int, height: int, targets: torch.Tensor,
+                   ws: torch.Tensor, stream=None):
+    _check(lib().gs_mlp_targets(_ptr(pixel), _ptr(depth), _ptr(log_scale), _ptr(kept), n_spawn, width, height,
+                                _ptr(targets), _ptr(ws), ws.numel(), _stream(stream)), "gs_mlp_targets")
+
+
+def gs_mlp_targets_workspace_size(width: int, height: int) -> int:
+    return int(lib().gs_mlp_targets_workspace_size(width, height))
+
+
+def gs_spawn_learned(image: torch.Tensor, mlp_out: torch.Tensor, width: int, height: int, cam: torch.Tensor,
+                     seed: int, frame: int, out: Spawned, ws: torch.Tensor, capacity=None, stream=None):
+    sc = gs_spawn_config(1.0, frame, seed)
+    oc = out.c(out.g.n if capacity is None else capacity)
+    _check(lib().gs_spawn_learned(_ptr(image), _ptr(mlp_out), width, height, _ptr(cam), C.byref(sc), C.byref(oc),
+                                  _ptr(ws), ws.numel(), _stream(stream)), "gs_spawn_learned")
 
 
 def adam_config(lr_mean=1.6e-4, lr_opacity=0.05, lr_scale=5e-3, lr_rot=1e-3, lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4,

@@ -120,3 +120,47 @@ def test_adam_step_matches_oracle(PATH):
             off += ref.size
             want = ref - 1e-3 * g / (np.abs(g) + 1e-8)
             assert_close(new, want, 1e-5, what="adam")
+
+
+def test_targets_from_kept_spawns_match_oracle():
+    rng = np.random.default_rng(5)
+    W, H = 120, 64
+    n = 2000
+    pixel = np.sort(rng.choice(W * H, n, replace=False)).astype(np.int32)
+    depth = rng.uniform(1, 20, n).astype(np.float32)
+    ls = rng.normal(-4, 1, n).astype(np.float32)
+    kept = (rng.random(n) < 0.5).astype(np.uint8)
+    tg = torch.zeros(((W // 8) * (H // 8), 4), device="cuda")
+    ws = gs.workspace(gs.gs_mlp_targets_workspace_size(W, H))
+    c = lambda a: torch.from_numpy(a).cuda()
+    gs.gs_mlp_targets(c(pixel), c(depth), c(ls), c(kept), n, W, H, tg, ws)
+    torch.cuda.synchronize()
+    ref = OM.targets_from_spawns(pixel, depth.astype(np.float64), ls.astype(np.float64), kept, W, H)
+    assert_close(tg.cpu().numpy(), ref, 1e-6, what="targets")
+
+
+def test_learned_spawn_matches_oracle():
+    from paper_2506_05558_gb300 import synth
+    from oracle import oracle as O
+    rng = np.random.default_rng(6)
+    W, H = 160, 96
+    n_p = (W // 8) * (H // 8)
+    out = np.stack([rng.normal(-1, 1.5, n_p), rng.uniform(-1, 15, n_p), rng.normal(-4, 0.5, n_p)], 1).astype(np.float32)
+    image = rng.random((3, H, W)).astype(np.float32)
+    R, t = O.retract_pose(np.eye(3), np.zeros(3), [0.2, -0.1, 0.3, 0.1, 0.05, -0.2])
+    cam = synth.camera(R.astype(np.float32), t.astype(np.float32), 120.0, W, H)
+    sp = gs.Spawned.alloc(W * H)
+    ws = gs.workspace(gs.gs_spawn_workspace_size(W, H))
+    gs.gs_spawn_learned(torch.from_numpy(image).cuda(), torch.from_numpy(out).cuda(), W, H, gs.cameras_tensor([cam]),
+                        99, 7, sp, ws)
+    torch.cuda.synchronize()
+    ref = OM.spawn_learned(image, out, cam, 99, 7)
+    k = int(sp.count.item())
+    pix = sp.pixel[:k].cpu().numpy()
+    amb = set(np.nonzero(ref["amb"])[0].tolist())
+    assert (set(pix.tolist()) ^ set(ref["pixel"].tolist())) <= amb
+    common = np.array(sorted(set(pix.tolist()) & set(ref["pixel"].tolist())))
+    gi, oi = np.searchsorted(pix, common), np.searchsorted(ref["pixel"], common)
+    assert_close(sp.g.mean_opa[:k].cpu().numpy()[gi][:, :3], ref["mean"][oi], 1e-5, what="mean")
+    assert_close(sp.g.scale[:k].cpu().numpy()[gi][:, :3], ref["log_scale"][oi], 1e-6, what="log scale")
+    assert_close(sp.g.sh[:k].cpu().numpy()[gi][:, :3], ref["sh_dc"][oi], 1e-5, what="sh dc")
