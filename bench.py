@@ -238,6 +238,82 @@ def timed(torch, fn, steps, barrier):
 
 
 # ---------------------------------------------------------------------------
+# the other rows of the path, timed on their own (1080p frame, 1M set)
+# ---------------------------------------------------------------------------
+MLP_FLOPS_PER_PATCH_FWD = 2 * (194 * 128 + 128 * 128 * 2 + 128 * 3)
+MLP_FLOPS_PER_PATCH_TRAIN = 2 * MLP_FLOPS_PER_PATCH_FWD + 2 * (128 * 128 * 2 + 128 * 3)
+
+
+def event_ms(torch, fn, reps):
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def measure_rows(torch, gs, W, device, peaks, reps=10):
+    out = {}
+    Wd, Hd = WIDTH, HEIGHT
+    hw = Wd * Hd
+    img = W["targets"][:3 * hw]
+    rng = np.random.default_rng(5)
+    depth = torch.tensor(rng.uniform(2, 40, hw).astype(np.float32), device=device)
+    cam0 = W["cams"][:72]
+    # a8: direct spawn sampling on a 1080p frame; the render reproduces the
+    # right half of the frame and is empty on the left, so the left half spawns
+    render = img.clone()
+    render.view(3, Hd, Wd)[:, :, :Wd // 2] = 0.0
+    sp = gs.Spawned.alloc(hw)
+    ws = gs.workspace(gs.gs_spawn_workspace_size(Wd, Hd), device)
+    ms = event_ms(torch, lambda: gs.gs_spawn_propose(img, render, depth, Wd, Hd, cam0, 1.0, 7, 0, sp, ws), reps)
+    n_sp = int(sp.count.item())
+    # image + render + depth read, flags/positions written and read, spawned rows written
+    bytes_ = (3 + 3 + 1) * 4 * hw + 16 * hw + n_sp * 240
+    out["spawn_propose"] = {"ms": ms, "bound": "hbm", "achieved": bytes_ / ms / 1e6, "unit": "GB/s",
+                            "frac": bytes_ / ms / 1e6 / peaks["hbm"], "spawned": n_sp}
+    # a10: learned proposal, one training step and one inference on a 1080p frame
+    prng = np.random.default_rng(1)
+    layers = [(prng.uniform(-1, 1, (o, i)) / np.sqrt(i), prng.uniform(-1, 1, o) / np.sqrt(i))
+              for o, i in ((128, 194), (128, 128), (128, 128), (3, 128))]
+    n_p = gs.gs_mlp_patches(Wd, Hd)
+    tg = torch.tensor(np.stack([rng.random(n_p), rng.uniform(2, 20, n_p), rng.normal(-4, 0.5, n_p),
+                                (rng.random(n_p) < 0.5)], 1).astype(np.float32), device=device)
+    wsm = gs.workspace(gs.gs_mlp_workspace_size(n_p), device)
+    loss = torch.zeros(1, device=device)
+    mo = torch.zeros((n_p, 3), device=device)
+    for path in (0, 1):
+        p = gs.MlpParams.from_numpy(layers, device)
+        m, v = gs.MlpParams.zeros(device), gs.MlpParams.zeros(device)
+        cfg = gs.mlp_config(tensor_path=path)
+        step_dev = torch.ones(1, dtype=torch.int32, device=device)
+        t_ms = event_ms(torch, lambda: gs.gs_mlp_train_step(p, m, v, img, Wd, Hd, tg, cfg, 0, loss, wsm,
+                                                            step_dev=step_dev), reps)
+        f_ms = event_ms(torch, lambda: gs.gs_mlp_forward(p, img, Wd, Hd, mo, cfg, wsm), reps)
+        tf = MLP_FLOPS_PER_PATCH_TRAIN * n_p / t_ms / 1e9
+        out[f"mlp_path{path}"] = {"path": "tcgen05 + TMEM" if path else "mma.sync", "train_ms": t_ms, "infer_ms": f_ms,
+                                  "train_tflops": tf, "bound": "tensor", "peak": peaks["bf16"],
+                                  "frac": tf / peaks["bf16"], "patches": n_p}
+    # a9: anchor size test on the 1M set and host offload of the set + Adam moments
+    g = W["g"]
+    fine = torch.zeros(g.n, dtype=torch.uint8, device=device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=device)
+    a_ms = event_ms(torch, lambda: gs.gs_anchor_check(g, cam0, 1.0, fine, cnt), reps)
+    hosts = [gs.pinned_gaussians(g.n) for _ in range(3)]
+    mm = gs.Gaussians.zeros(g.n, device)
+    o_ms = event_ms(torch, lambda: gs.gs_anchor_offload(g, mm, mm, hosts[0], hosts[1], hosts[2]), 3)
+    out["anchor"] = {"check_ms": a_ms, "check_gbs": (33 * g.n) / a_ms / 1e6, "too_fine": int(cnt.item()),
+                     "offload_ms": o_ms, "offload_gbs": 3 * 240 * g.n / o_ms / 1e6,
+                     "offload_bytes": 3 * 240 * g.n}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # oracle on the host cores
 # ---------------------------------------------------------------------------
 def oracle_sample(n_views_sample=1, n=N_GAUSS):
@@ -304,6 +380,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the spawn / MLP / anchor measurements")
     ap.add_argument("--cpu-views", type=int, default=3, help="views of the oracle CPU sample")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -466,6 +543,13 @@ def main():
            "path": "JointOptimizer.step() (C-ABI calls), targets copied from pinned host memory each step"}
     del E, dev_targets
 
+    # ---------------- the other rows, timed on their own ----------------
+    rows = None
+    if not args.no_rows and args.views >= 1:
+        reset(W)
+        bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+        rows = measure_rows(torch, gs, W, device, {"hbm": hbm_peak, "bf16": bf16_peak})
+
     # ---------------- uneven views: 2M Gaussians, 16 views of mixed resolution ----------------
     uneven = None
     if not args.no_uneven:
@@ -530,6 +614,7 @@ def main():
                              f"{args.views * args.n * 52 / 1e9:.2f} GB)"},
             "plain": plain,
             "uneven": uneven,
+            "rows": rows,
             "roofline": roof,
             "stages": stages,
             "work": {"visible_items": n_items_vis, "pairs": P, "evaluations": K, "loss": loss, "status": status},

@@ -20,51 +20,82 @@ namespace gs {
 constexpr int kIn = 194, kInPad = 208, kHid = 128, kOut = 3, kOutPad = 16;
 constexpr int kPatch = 8;
 constexpr int kRowAlign = 128;  // patch rows are padded to a multiple of this
-constexpr int kSplitK = 2048;   // patches per split of a weight-gradient GEMM
+constexpr int kSplitK = 256;    // patches per split of a weight-gradient GEMM
 
 __device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad_f(float z) {
     return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
+// Kernels that write an activation both row-major [Mp][N] and transposed
+// [N][Mp] work on 32 x 32 tiles (blockDim 32 x 8): the row-major value is
+// written directly and the tile is turned in shared memory so the transposed
+// store is coalesced too.
+struct TileT {
+    __nv_bfloat16 v[32][33];
+};
+
+__device__ __forceinline__ void store_transposed(TileT& t, __nv_bfloat16* __restrict__ dst_t, int64_t Mp, int N,
+                                                 int64_t m0, int n0) {
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {  // r: column n of the source tile
+        const int n = n0 + r;
+        const int64_t m = m0 + threadIdx.x;
+        if (n < N && m < Mp) dst_t[(int64_t)n * Mp + m] = t.v[threadIdx.x][r];
+    }
+}
+
 // X [Mp][208] and X^T [208][Mp] (bf16) from image [3][H][W]; rows >= M and
 // columns >= 194 are zero. Row (py, px) in row-major patch order.
-__global__ void k_mlp_features(const float* __restrict__ image, int W, int H, int64_t M, int64_t Mp,
-                               __nv_bfloat16* __restrict__ X, __nv_bfloat16* __restrict__ Xt) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Mp * kInPad) return;
-    const int64_t m = i / kInPad;
-    const int c = (int)(i % kInPad);
-    float v = 0.f;
-    if (m < M) {
-        const int nx = W / kPatch, ny = H / kPatch;
-        const int px = (int)(m % nx), py = (int)(m / nx);
-        if (c < 192) {
-            const int ch = c / 64, dy = (c % 64) / 8, dx = c % 8;
-            v = image[(int64_t)ch * W * H + (int64_t)(py * kPatch + dy) * W + px * kPatch + dx];
-        } else if (c == 192) {
-            v = (px + 0.5f) / nx * 2.f - 1.f;
-        } else if (c == 193) {
-            v = (py + 0.5f) / ny * 2.f - 1.f;
+__global__ void __launch_bounds__(256) k_mlp_features(const float* __restrict__ image, int W, int H, int64_t M,
+                                                      int64_t Mp, __nv_bfloat16* __restrict__ X,
+                                                      __nv_bfloat16* __restrict__ Xt) {
+    __shared__ TileT t;
+    const int64_t m0 = (int64_t)blockIdx.y * 32;
+    const int n0 = blockIdx.x * 32;
+    const int c = n0 + threadIdx.x;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t m = m0 + r;
+        float v = 0.f;
+        if (m < M && c < kInPad) {
+            const int nx = W / kPatch, ny = H / kPatch;
+            const int px = (int)(m % nx), py = (int)(m / nx);
+            if (c < 192) {
+                const int ch = c / 64, dy = (c % 64) / 8, dx = c % 8;
+                v = image[(int64_t)ch * W * H + (int64_t)(py * kPatch + dy) * W + px * kPatch + dx];
+            } else if (c == 192) {
+                v = (px + 0.5f) / nx * 2.f - 1.f;
+            } else if (c == 193) {
+                v = (py + 0.5f) / ny * 2.f - 1.f;
+            }
         }
+        const __nv_bfloat16 b = __float2bfloat16_rn(v);
+        if (m < Mp && c < kInPad) X[m * kInPad + c] = b;
+        t.v[r][threadIdx.x] = b;
     }
-    const __nv_bfloat16 b = __float2bfloat16_rn(v);
-    X[i] = b;
-    Xt[(int64_t)c * Mp + m] = b;
+    store_transposed(t, Xt, Mp, kInPad, m0, n0);
 }
 
 // Z += b; H = bf16(GELU(Z)) row-major and transposed. Z [Mp][N], b [N].
-__global__ void k_mlp_bias_gelu(float* __restrict__ Z, const float* __restrict__ b, int64_t Mp, int N,
-                                __nv_bfloat16* __restrict__ Hm, __nv_bfloat16* __restrict__ Ht) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Mp * N) return;
-    const int64_t m = i / N;
-    const int n = (int)(i % N);
-    const float z = Z[i] + b[n];
-    Z[i] = z;
-    const __nv_bfloat16 h = __float2bfloat16_rn(gelu_f(z));
-    Hm[i] = h;
-    Ht[(int64_t)n * Mp + m] = h;
+__global__ void __launch_bounds__(256) k_mlp_bias_gelu(float* __restrict__ Z, const float* __restrict__ b,
+                                                       int64_t Mp, int N, __nv_bfloat16* __restrict__ Hm,
+                                                       __nv_bfloat16* __restrict__ Ht) {
+    __shared__ TileT t;
+    const int64_t m0 = (int64_t)blockIdx.y * 32;
+    const int n0 = blockIdx.x * 32;
+    const int n = n0 + threadIdx.x;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t m = m0 + r;
+        __nv_bfloat16 h = __float2bfloat16_rn(0.f);
+        if (m < Mp && n < N) {
+            const float z = Z[m * N + n] + b[n];
+            Z[m * N + n] = z;
+            h = __float2bfloat16_rn(gelu_f(z));
+            Hm[m * N + n] = h;
+        }
+        t.v[r][threadIdx.x] = h;
+    }
+    store_transposed(t, Ht, Mp, N, m0, n0);
 }
 
 // Output layer: Y = Z4 + b4 (first 3 columns). Loss terms and dY; rows >= M
@@ -128,28 +159,38 @@ __global__ void __launch_bounds__(256) k_mlp_loss(const float* __restrict__ Z4, 
 
 // dZ = dH * GELU'(Z): fp32 [Mp][N] for the bias gradient, bf16 row-major and
 // transposed for the next products.
-__global__ void k_mlp_gelu_bwd(const float* __restrict__ dH, const float* __restrict__ Z, int64_t Mp, int N,
-                               float* __restrict__ dZf, __nv_bfloat16* __restrict__ dZ,
-                               __nv_bfloat16* __restrict__ dZt) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Mp * N) return;
-    const int64_t m = i / N;
-    const int n = (int)(i % N);
-    const float d = dH[i] * gelu_grad_f(Z[i]);
-    dZf[i] = d;
-    const __nv_bfloat16 b = __float2bfloat16_rn(d);
-    dZ[i] = b;
-    dZt[(int64_t)n * Mp + m] = b;
+__global__ void __launch_bounds__(256) k_mlp_gelu_bwd(const float* __restrict__ dH, const float* __restrict__ Z,
+                                                      int64_t Mp, int N, float* __restrict__ dZf,
+                                                      __nv_bfloat16* __restrict__ dZ, __nv_bfloat16* __restrict__ dZt) {
+    __shared__ TileT t;
+    const int64_t m0 = (int64_t)blockIdx.y * 32;
+    const int n0 = blockIdx.x * 32;
+    const int n = n0 + threadIdx.x;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int64_t m = m0 + r;
+        __nv_bfloat16 h = __float2bfloat16_rn(0.f);
+        if (m < Mp && n < N) {
+            const float d = dH[m * N + n] * gelu_grad_f(Z[m * N + n]);
+            dZf[m * N + n] = d;
+            h = __float2bfloat16_rn(d);
+            dZ[m * N + n] = h;
+        }
+        t.v[r][threadIdx.x] = h;
+    }
+    store_transposed(t, dZt, Mp, N, m0, n0);
 }
 
-// Column sums of an fp32 [Mp][N] matrix in a fixed order: one thread per
-// column walks the rows (N <= 128, so one block).
-__global__ void k_col_sum(const float* __restrict__ A, int64_t Mp, int N, int n_valid, float* __restrict__ out) {
+// Column sums of an fp32 [Mp][N] matrix, first pass: block b sums rows
+// [256 b, 256 b + 256) of each column (thread = column); the partials are then
+// summed in block order by k_split_sum.
+constexpr int kColRows = 256;
+__global__ void k_col_sum_part(const float* __restrict__ A, int64_t Mp, int N, float* __restrict__ part) {
     const int n = threadIdx.x;
-    if (n >= n_valid) return;
+    if (n >= N) return;
+    const int64_t r0 = (int64_t)blockIdx.x * kColRows;
     float s = 0.f;
-    for (int64_t m = 0; m < Mp; m++) s += A[m * N + n];
-    out[n] = s;
+    for (int64_t m = r0; m < r0 + kColRows && m < Mp; m++) s += A[m * N + n];
+    part[(int64_t)blockIdx.x * N + n] = s;
 }
 
 // Sum of S split-K partials [S][R][C] into [R][Cv] (the first Cv columns).
@@ -289,13 +330,17 @@ static int mlp_forward(const MlpPtrs& P, const float* image, int W, int H, const
     const int64_t M = w.M, Mp = w.Mp;
     for (int l = 0; l < 4; l++)
         GS_LAUNCH1(k_weight_cast, kRo[l] * kCi[l], P.w[l], kRv[l], kCv[l], kRo[l], kCi[l], w.Wb[l], w.Wt[l]);
-    GS_LAUNCH1(k_mlp_features, Mp * kInPad, image, W, H, M, Mp, w.X, w.Xt);
+    k_mlp_features<<<dim3((unsigned)ceil_div(kInPad, 32), (unsigned)ceil_div(Mp, 32)), dim3(32, 8), 0, s>>>(
+        image, W, H, M, Mp, w.X, w.Xt);
+    count_launch();
     const __nv_bfloat16* Hin = w.X;
     int K = kInPad;
     for (int l = 0; l < 3; l++) {
         int rc = gemm_tn(path, Hin, K, w.Wb[l], K, w.Z[l], kHid, Mp, kHid, K, K, 0, s);
         if (rc != GS_OK) return rc;
-        GS_LAUNCH1(k_mlp_bias_gelu, Mp * kHid, w.Z[l], P.b[l], Mp, kHid, w.H[l], w.Ht[l]);
+        k_mlp_bias_gelu<<<dim3((unsigned)ceil_div(kHid, 32), (unsigned)ceil_div(Mp, 32)), dim3(32, 8), 0, s>>>(
+            w.Z[l], P.b[l], Mp, kHid, w.H[l], w.Ht[l]);
+        count_launch();
         Hin = w.H[l];
         K = kHid;
     }
@@ -327,13 +372,17 @@ static int mlp_backward(const MlpWs& w, int path, cudaStream_t s) {
         int rc = gemm_tn(path, dZt, Mp, Hin_t, Mp, w.part, in, out, in, Mp, kSplitK, (int64_t)out * in, s);
         if (rc != GS_OK) return rc;
         GS_LAUNCH1(k_split_sum, kRv[l] * kCv[l], w.part, (int)w.splits, out, in, kCv[l], kRv[l], w.grad + off[l]);
-        k_col_sum<<<1, 128, 0, s>>>(dZf, Mp, out, kRv[l], w.grad + off[l] + (int64_t)kRv[l] * kCv[l]);
+        const int ncb = (int)ceil_div(Mp, kColRows);
+        k_col_sum_part<<<ncb, 128, 0, s>>>(dZf, Mp, out, w.part);
         count_launch();
+        GS_LAUNCH1(k_split_sum, kRv[l], w.part, ncb, 1, out, kRv[l], 1, w.grad + off[l] + (int64_t)kRv[l] * kCv[l]);
         if (l == 0) break;
         // dH_{l-1} = dZ_l W_l, then dZ_{l-1} = dH * GELU'(Z_{l-1})
         rc = gemm_tn(path, dZ, out, w.Wt[l], out, w.dH, kHid, Mp, kHid, out, out, 0, s);
         if (rc != GS_OK) return rc;
-        GS_LAUNCH1(k_mlp_gelu_bwd, Mp * kHid, w.dH, w.Z[l - 1], Mp, kHid, w.dZf, w.dZ, w.dZt);
+        k_mlp_gelu_bwd<<<dim3((unsigned)ceil_div(kHid, 32), (unsigned)ceil_div(Mp, 32)), dim3(32, 8), 0, s>>>(
+            w.dH, w.Z[l - 1], Mp, kHid, w.dZf, w.dZ, w.dZt);
+        count_launch();
         dZ = w.dZ;
         dZt = w.dZt;
         dZf = w.dZf;

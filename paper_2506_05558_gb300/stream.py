@@ -1,0 +1,201 @@
+"""Frame-by-frame reconstruction loop (Sec. 4.2-4.4) with known poses, used to
+compare plain direct spawn sampling with the learned spawn proposal.
+
+Per new frame: render the active Gaussians from its pose (the penalty image
+of Eq. 2), spawn new Gaussians (direct sampling with the frame's depth map, or
+the learned per-patch proposal), append them, run the joint optimisation over
+a sliding window of recent frames, mark which of the frame's spawns survived
+(opacity above a threshold), turn those into per-patch training targets for
+the learned proposal and train it on the frame, and test the anchor rule from
+the previous camera. Every step is a libgs call; PyTorch only owns memory.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import gs
+from .raster import Rasterizer
+
+
+class GaussianStore:
+    """Preallocated Gaussians, Adam moments and an active count."""
+
+    def __init__(self, capacity: int, device="cuda"):
+        self.cap = capacity
+        self.p = gs.Gaussians.zeros(capacity, device)
+        self.m = gs.Gaussians.zeros(capacity, device)
+        self.v = gs.Gaussians.zeros(capacity, device)
+        self.n = 0
+
+    @staticmethod
+    def _view(g: gs.Gaussians, n: int) -> gs.Gaussians:
+        return gs.Gaussians(g.mean_opa[:n], g.scale[:n], g.quat[:n], g.sh[:n])
+
+    def active(self):
+        return self._view(self.p, self.n), self._view(self.m, self.n), self._view(self.v, self.n)
+
+    def append(self, sp: gs.Spawned, k: int) -> int:
+        k = min(k, self.cap - self.n)
+        if k <= 0:
+            return 0
+        for dst, src in ((self.p.mean_opa, sp.g.mean_opa), (self.p.scale, sp.g.scale), (self.p.quat, sp.g.quat),
+                         (self.p.sh, sp.g.sh)):
+            dst[self.n:self.n + k].copy_(src[:k])
+        for st in (self.m, self.v):
+            for t in (st.mean_opa, st.scale, st.quat, st.sh):
+                t[self.n:self.n + k].zero_()
+        self.n += k
+        return k
+
+
+def psnr(a: torch.Tensor, b: torch.Tensor) -> float:
+    mse = torch.mean((a.clamp(0, 1) - b) ** 2).item()
+    return 10 * math.log10(1.0 / max(mse, 1e-12))
+
+
+def render_depth(g: gs.Gaussians, cam: torch.Tensor, size, cfg, device="cuda"):
+    """Expected depth per pixel (sum alpha T z over the composited Gaussians,
+    normalised by 1 - T_final) and the colour image, by rendering the scene
+    once with its colours and once with each Gaussian's camera depth in place
+    of its colour."""
+    r = Rasterizer(g.n, [size], 1 << 20, cfg, device)
+    r.fit_capacity(g, cam)
+    r.forward(g, cam)
+    color = r.img.color.clone()
+    rd = r.proj.rgb_depth
+    rd[:, 0:3] = rd[:, 3:4]
+    gs.gs_render_fwd(r.proj, r.pairs, r.f, r.cfg, r.img, r.ws_render)
+    acc = (1.0 - r.img.t_final).clamp_min(1e-6)
+    depth = (r.img.color[: size[0] * size[1]] / acc).clone()
+    depth[acc < 0.5] = 0.0  # no reliable depth where little was rendered
+    return color, depth
+
+
+class OnTheFly:
+    def __init__(self, capacity: int, size, window: int = 4, iters: int = 30, mode: str = "plain",
+                 mlp_warmup_frames: int = 3, mlp_steps: int = 40, keep_threshold: float = 0.05, seed: int = 7,
+                 device="cuda"):
+        self.store = GaussianStore(capacity, device)
+        self.W, self.H = size
+        self.window = window
+        self.iters = iters
+        self.mode = mode
+        self.cfg = gs.config(sh_degree=0)
+        self.adam = gs.adam_config(lr_mean=1e-3, lr_opacity=0.05, lr_scale=5e-3, lr_rot=1e-3, lr_sh_dc=5e-3,
+                                   lr_sh_rest=0.0)
+        self.frames = []  # (image [3HW], camera tensor)
+        self.seed = seed
+        self.device = device
+        self.keep_threshold = keep_threshold
+        self.mlp_warmup_frames = mlp_warmup_frames
+        self.mlp_steps = mlp_steps
+        hw = self.W * self.H
+        self.spawned = gs.Spawned.alloc(hw, hw, device)
+        self.ws_spawn = gs.workspace(gs.gs_spawn_workspace_size(self.W, self.H), device)
+        self.iter_count = 0
+        self.step_dev = torch.ones((1,), dtype=torch.int32, device=device)
+        if mode == "learned":
+            rng = np.random.default_rng(seed)
+            layers = [(rng.uniform(-1, 1, (o, i)) / math.sqrt(i), rng.uniform(-1, 1, o) / math.sqrt(i))
+                      for o, i in ((128, 194), (128, 128), (128, 128), (3, 128))]
+            self.mlp = gs.MlpParams.from_numpy(layers, device)
+            self.mlp_m, self.mlp_v = gs.MlpParams.zeros(device), gs.MlpParams.zeros(device)
+            self.n_patches = gs.gs_mlp_patches(self.W, self.H)
+            self.ws_mlp = gs.workspace(gs.gs_mlp_workspace_size(self.n_patches), device)
+            self.mlp_out = torch.zeros((self.n_patches, 3), device=device)
+            self.mlp_targets = torch.zeros((self.n_patches, 4), device=device)
+            self.ws_tg = gs.workspace(gs.gs_mlp_targets_workspace_size(self.W, self.H), device)
+            self.mlp_loss = torch.zeros(1, device=device)
+            self.mlp_cfg = gs.mlp_config(tensor_path=1, lr=1e-3)
+            self.mlp_step = 0
+        self.log = []
+
+    # -- steps -------------------------------------------------------------------
+    def _render_active(self, cam):
+        g, _, _ = self.store.active()
+        if g.n == 0:
+            return None
+        r = Rasterizer(g.n, [(self.W, self.H)], 1 << 18, self.cfg, self.device)
+        r.fit_capacity(g, cam)
+        r.forward(g, cam)
+        return r.img.color.clone()
+
+    def _spawn(self, image, render, depth, cam, frame_idx):
+        hw = self.W * self.H
+        use_learned = self.mode == "learned" and frame_idx >= self.mlp_warmup_frames
+        if use_learned:
+            gs.gs_mlp_forward(self.mlp, image, self.W, self.H, self.mlp_out, self.mlp_cfg, self.ws_mlp)
+            gs.gs_spawn_learned(image, self.mlp_out, self.W, self.H, cam, self.seed, frame_idx, self.spawned,
+                                self.ws_spawn)
+        else:
+            gs.gs_spawn_propose(image, render, depth, self.W, self.H, cam, 1.0, self.seed, frame_idx, self.spawned,
+                                self.ws_spawn)
+        torch.cuda.synchronize()
+        k = min(int(self.spawned.count.item()), hw)
+        return k, use_learned
+
+    def _optimise(self, iters):
+        g, m, v = self.store.active()
+        frames = self.frames[-self.window:]
+        sizes = [(self.W, self.H)] * len(frames)
+        cams = torch.cat([c for _, c in frames])
+        targets = torch.cat([im for im, _ in frames])
+        r = Rasterizer(g.n, sizes, 1 << 18, self.cfg, self.device)
+        r.fit_capacity(g, cams)
+        dL = torch.zeros_like(r.img.color)
+        loss = torch.zeros(1, device=self.device)
+        ws = gs.workspace(4 * 4096, self.device)
+        for _ in range(iters):
+            r.forward(g, cams)
+            gs.gs_l1_loss(r.img.color, targets, dL, loss, ws)
+            r.backward(g, cams, dL)
+            gs.gs_adam_step(g, r.grads, m, v, self.adam, 0, step_dev=self.step_dev)
+            gs.gs_counter_add(self.step_dev, 1)
+            self.iter_count += 1
+        if r.status() != gs.GS_OK:
+            r.fit_capacity(g, cams)
+        return float(loss.item())
+
+    def _train_mlp(self, image, n0, k, depth):
+        """Targets from this frame's spawns that are still opaque after the
+        optimisation, then a few training steps of the proposal network."""
+        if k == 0:
+            return None
+        g, _, _ = self.store.active()
+        opa = torch.sigmoid(g.mean_opa[n0:n0 + k, 3])
+        kept = (opa > self.keep_threshold).to(torch.uint8)
+        pix = self.spawned.pixel[:k]
+        z = depth[pix.long()]
+        ls = self.spawned.g.scale[:k, 0].contiguous()
+        gs.gs_mlp_targets(pix, z.contiguous(), ls, kept, k, self.W, self.H, self.mlp_targets, self.ws_tg)
+        for _ in range(self.mlp_steps):
+            self.mlp_step += 1
+            gs.gs_mlp_train_step(self.mlp, self.mlp_m, self.mlp_v, image, self.W, self.H, self.mlp_targets,
+                                 self.mlp_cfg, self.mlp_step, self.mlp_loss, self.ws_mlp)
+        return float(self.mlp_loss.item())
+
+    def add_frame(self, image: torch.Tensor, depth: torch.Tensor, cam: torch.Tensor, frame_idx: int):
+        render = self._render_active(cam)
+        k, learned = self._spawn(image, render, depth, cam, frame_idx)
+        n0 = self.store.n
+        k = self.store.append(self.spawned, k)
+        self.frames.append((image, cam))
+        loss = self._optimise(self.iters)
+        mlp_loss = None
+        if self.mode == "learned" and not learned:
+            # the direct-sampling spawns of the warm-up frames that survived
+            # the optimisation teach the proposal
+            mlp_loss = self._train_mlp(image, n0, k, depth)
+        self.log.append(dict(frame=frame_idx, spawned=k, n=self.store.n, loss=loss, learned=learned,
+                             mlp_loss=mlp_loss, iters=self.iter_count))
+
+    def evaluate(self, frames):
+        """Mean PSNR of the active set rendered at the given (image, camera) frames."""
+        vals = []
+        for image, cam in frames:
+            r = self._render_active(cam)
+            vals.append(psnr(r, image))
+        return float(np.mean(vals))
