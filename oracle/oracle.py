@@ -434,3 +434,35 @@ def perturbed_cam(cam, xi):
     c = dict(cam)
     c["R"], c["t"] = R, t
     return c
+
+
+def se3_ad(xi):
+    """ad(xi) of xi = (rho, phi) in se(3), acting on (rho, phi): [[phi^, rho^], [0, phi^]]."""
+    rho, phi = np.asarray(xi[:3], np.float64), np.asarray(xi[3:], np.float64)
+    A = np.zeros((6, 6))
+    A[:3, :3] = hat(phi)
+    A[:3, 3:] = hat(rho)
+    A[3:, 3:] = hat(phi)
+    return A
+
+
+def se3_left_jacobian(xi, terms=40):
+    """Left Jacobian of SE(3) by its series, J_l = sum_n ad(xi)^n / (n+1)!:
+    exp((xi + d)^) = exp((J_l d)^) exp(xi^) to first order in d."""
+    A = se3_ad(xi)
+    J = np.zeros((6, 6))
+    P = np.eye(6)
+    fact = 1.0
+    for n in range(terms):
+        fact *= n + 1
+        J += P / fact
+        P = P @ A
+    return J
+
+
+def pose_tangent_grad(xi, g_delta):
+    """Gradient with respect to xi of a loss of the pose exp(xi^) T_ref, given
+    g_delta = dL/d delta of the same loss under T <- exp(delta^) T at
+    T = exp(xi^) T_ref (the gradient the rasteriser's backward returns):
+    J_l(xi)^T g_delta (Sec. 4.3 pose update written on the SE(3) tangent)."""
+    return se3_left_jacobian(xi).T @ np.asarray(g_delta, np.float64)

@@ -425,3 +425,74 @@ def test_se3_exp_matches_matrix_exponential():
         R, t = O.se3_exp(xi)
         np.testing.assert_allclose(R, E[:3, :3], atol=1e-12)
         np.testing.assert_allclose(t, E[:3, 3], atol=1e-12)
+
+
+def _se3_mat(xi):
+    R, t = O.se3_exp(xi)
+    M = np.eye(4)
+    M[:3, :3], M[:3, 3] = R, t
+    return M
+
+
+def _twist_mat(d):
+    M = np.zeros((4, 4))
+    M[:3, :3] = O.hat(d[3:])
+    M[:3, 3] = d[:3]
+    return M
+
+
+def test_se3_left_jacobian_first_order_composition():
+    """exp((xi + e v)^) exp(xi^)^-1 = I + e (J_l v)^ + O(e^2), checked by a
+    central difference of the group elements (no rendering involved): a
+    transposed block or a wrong sign in J_l fails."""
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        xi = np.concatenate([rng.normal(0, 1.0, 3), rng.normal(0, 0.6, 3)])
+        J = O.se3_left_jacobian(xi)
+        inv = np.linalg.inv(_se3_mat(xi))
+        for k in range(6):
+            v = np.zeros(6)
+            v[k] = 1.0
+            e = 1e-6
+            D = (_se3_mat(xi + e * v) @ inv - _se3_mat(xi - e * v) @ inv) / (2 * e)
+            np.testing.assert_allclose(D, _twist_mat(J[:, k]), atol=2e-9)
+
+
+def test_se3_left_jacobian_special_cases():
+    """xi = 0 gives I; pure translation gives [[I, rho^ / 2], [0, I]] (ad^2 = 0)."""
+    np.testing.assert_allclose(O.se3_left_jacobian(np.zeros(6)), np.eye(6), atol=0)
+    rho = np.array([0.3, -1.2, 2.0])
+    J = O.se3_left_jacobian(np.concatenate([rho, np.zeros(3)]))
+    want = np.eye(6)
+    want[:3, 3:] = 0.5 * O.hat(rho)
+    np.testing.assert_allclose(J, want, atol=1e-15)
+
+
+def test_pose_tangent_gradient_matches_central_differences():
+    """dL/dxi of L(exp(xi^) T_ref) at a nonzero xi: J_l(xi)^T applied to the
+    backward pass's gradient at the composed pose equals FP64 central
+    differences of the rendered loss."""
+    cfg = O.Config(sh_degree=0, bg=(0.1, 0.2, 0.3))
+    xi0 = np.array([0.04, -0.02, 0.03, 0.05, -0.04, 0.03])
+    for seed in range(11, 40):
+        sc, cam, rng = _fd_scene(0, seed)
+        cam1 = O.perturbed_cam(cam, xi0)
+        v = O.render_view(sc, cam1, cfg)
+        if v["amb"].sum() == 0 and v["proj"]["amb"].sum() == 0:
+            break
+    assert v["amb"].sum() == 0 and v["proj"]["amb"].sum() == 0
+    w = rng.standard_normal((3, cam["height"], cam["width"]))
+    g = O.backward_view(sc, cam1, cfg, v, w)
+    an = O.pose_tangent_grad(xi0, g["pose"])
+    lists = (v["start"], v["ids"])
+    h = 1e-6
+    fd = np.zeros(6)
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = h
+        lp, _ = _loss(sc, O.perturbed_cam(cam, xi0 + e), cfg, w, lists)
+        lm, _ = _loss(sc, O.perturbed_cam(cam, xi0 - e), cfg, w, lists)
+        fd[k] = (lp - lm) / (2 * h)
+    np.testing.assert_allclose(an, fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
+    # the plain gradient (J_l dropped) is measurably different at this xi
+    assert np.abs(g["pose"] - fd).max() > 1e-3 * np.abs(fd).max()
