@@ -428,6 +428,19 @@ int gs_pose_step(gs_camera* cams, int32_t n_views, const float* dL_dpose, float*
                  float lr_r, float beta1, float beta2, float eps, int32_t step, const int32_t* step_dev,
                  void* stream);
 
+/* Pose of a differentiable render (Sec. 4.3 poses optimised jointly with the
+ * Gaussians, written on the SE(3) tangent): cams_out[i] = exp(xi_i^) cams_ref[i]
+ * for xi [n_views][6] = (rho, phi) on the device. The exponential is evaluated
+ * in FP64 and rounded once into the FP32 camera. cams_out may equal cams_ref.
+ * Intrinsics and sizes are copied. */
+int gs_pose_apply(const gs_camera* cams_ref, const float* xi, int32_t n_views, gs_camera* cams_out, void* stream);
+
+/* Gradient with respect to xi of a loss of exp(xi^) T_ref, from the tangent
+ * gradient dL_ddelta that gs_render_bwd returns at T = exp(xi^) T_ref:
+ * dL_dxi = J_l(xi)^T dL_ddelta, J_l the left Jacobian of SE(3) (closed form,
+ * FP64). All arrays [n_views][6] on the device; dL_dxi may equal dL_ddelta. */
+int gs_pose_tangent_grad(const float* xi, const float* dL_ddelta, int32_t n_views, float* dL_dxi, void* stream);
+
 /* counter[0] += delta on the device (advances a graph-visible step counter). */
 int gs_counter_add(int32_t* counter, int32_t delta, void* stream);
 

@@ -211,6 +211,130 @@ extern "C" int gs_pose_step(gs_camera* cams, int32_t n_views, const float* dL_dp
     return GS_OK;
 }
 
+// SE(3) exponential and left Jacobian in FP64. With K = phi^, th = |phi|:
+// exp: R = I + a K + b K^2, t = V rho, V = I + b K + c K^2, and the left
+// Jacobian [[V, Q], [0, V]] with
+// Q = rho^/2 + c (K P + P K + K P K) + d (K K P + P K K - 3 K P K)
+//     + e (K P K K + K K P K),  P = rho^,
+// a = sin th / th, b = (1 - cos th) / th^2, c = (th - sin th) / th^3,
+// d = (th^2 + 2 cos th - 2) / (2 th^4), e = (2 th - 3 sin th + th cos th) / (2 th^5)
+// (Taylor series below th = 1e-3).
+struct Se3Coef {
+    double a, b, c, d, e;
+};
+
+__device__ Se3Coef se3_coef(double th) {
+    const double t2 = th * th;
+    Se3Coef k;
+    if (th < 1e-3) {
+        k.a = 1.0 - t2 / 6.0;
+        k.b = 0.5 - t2 / 24.0;
+        k.c = 1.0 / 6.0 - t2 / 120.0;
+        k.d = 1.0 / 24.0 - t2 / 720.0;
+        k.e = 1.0 / 120.0 - t2 / 2520.0;
+    } else {
+        const double s = sin(th), co = cos(th);
+        k.a = s / th;
+        k.b = (1.0 - co) / t2;
+        k.c = (th - s) / (t2 * th);
+        k.d = (t2 + 2.0 * co - 2.0) / (2.0 * t2 * t2);
+        k.e = (2.0 * th - 3.0 * s + th * co) / (2.0 * t2 * t2 * th);
+    }
+    return k;
+}
+
+__device__ void hat3(const double* w, double* K) {
+    K[0] = 0.0, K[1] = -w[2], K[2] = w[1];
+    K[3] = w[2], K[4] = 0.0, K[5] = -w[0];
+    K[6] = -w[1], K[7] = w[0], K[8] = 0.0;
+}
+
+__device__ void mul3(const double* A, const double* B, double* C) {
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) C[3 * r + c] = A[3 * r] * B[c] + A[3 * r + 1] * B[3 + c] + A[3 * r + 2] * B[6 + c];
+}
+
+__global__ void k_pose_apply(const gs_camera* __restrict__ ref, const float* __restrict__ xi, int nv,
+                             gs_camera* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    double rho[3], phi[3];
+    for (int k = 0; k < 3; k++) rho[k] = xi[6 * i + k], phi[k] = xi[6 * i + 3 + k];
+    const Se3Coef c = se3_coef(sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]));
+    double K[9], K2[9];
+    hat3(phi, K);
+    mul3(K, K, K2);
+    gs_camera cam = ref[i];
+    double R[9], t[3];
+    for (int k = 0; k < 9; k++) R[k] = cam.R[k];
+    for (int k = 0; k < 3; k++) t[k] = cam.t[k];
+    double dR[9], V[9];
+    for (int k = 0; k < 9; k++) {
+        const double I = (k % 4 == 0) ? 1.0 : 0.0;
+        dR[k] = I + c.a * K[k] + c.b * K2[k];
+        V[k] = I + c.b * K[k] + c.c * K2[k];
+    }
+    for (int r = 0; r < 3; r++) {
+        for (int q = 0; q < 3; q++)
+            cam.R[3 * r + q] = (float)(dR[3 * r] * R[q] + dR[3 * r + 1] * R[3 + q] + dR[3 * r + 2] * R[6 + q]);
+        cam.t[r] = (float)(dR[3 * r] * t[0] + dR[3 * r + 1] * t[1] + dR[3 * r + 2] * t[2] + V[3 * r] * rho[0] +
+                           V[3 * r + 1] * rho[1] + V[3 * r + 2] * rho[2]);
+    }
+    out[i] = cam;
+}
+
+__global__ void k_pose_tangent_grad(const float* __restrict__ xi, const float* g_delta, int nv, float* g_xi) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    double rho[3], phi[3], g[6];
+    for (int k = 0; k < 3; k++) rho[k] = xi[6 * i + k], phi[k] = xi[6 * i + 3 + k];
+    for (int k = 0; k < 6; k++) g[k] = g_delta[6 * i + k];
+    const Se3Coef c = se3_coef(sqrt(phi[0] * phi[0] + phi[1] * phi[1] + phi[2] * phi[2]));
+    double K[9], P[9], K2[9], KP[9], PK[9], KPK[9], KKP[9], PKK[9], KPKK[9], KKPK[9];
+    hat3(phi, K);
+    hat3(rho, P);
+    mul3(K, K, K2);
+    mul3(K, P, KP);
+    mul3(P, K, PK);
+    mul3(KP, K, KPK);
+    mul3(K2, P, KKP);
+    mul3(P, K2, PKK);
+    mul3(KPK, K, KPKK);
+    mul3(K, KPK, KKPK);
+    double V[9], Q[9];
+    for (int k = 0; k < 9; k++) {
+        const double I = (k % 4 == 0) ? 1.0 : 0.0;
+        V[k] = I + c.b * K[k] + c.c * K2[k];
+        Q[k] = 0.5 * P[k] + c.c * (KP[k] + PK[k] + KPK[k]) + c.d * (KKP[k] + PKK[k] - 3.0 * KPK[k]) +
+               c.e * (KPKK[k] + KKPK[k]);
+    }
+    // [g_rho; g_phi] <- [[V^T, 0], [Q^T, V^T]] [g_rho; g_phi]
+    double o[6];
+    for (int q = 0; q < 3; q++) {
+        o[q] = V[q] * g[0] + V[3 + q] * g[1] + V[6 + q] * g[2];
+        o[3 + q] = Q[q] * g[0] + Q[3 + q] * g[1] + Q[6 + q] * g[2] + V[q] * g[3] + V[3 + q] * g[4] + V[6 + q] * g[5];
+    }
+    for (int k = 0; k < 6; k++) g_xi[6 * i + k] = (float)o[k];
+}
+
+extern "C" int gs_pose_apply(const gs_camera* cams_ref, const float* xi, int32_t n_views, gs_camera* cams_out,
+                             void* stream) {
+    if (!cams_ref || !xi || !cams_out || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_INVALID_ARG;
+    k_pose_apply<<<1, 64, 0, (cudaStream_t)stream>>>(cams_ref, xi, n_views, cams_out);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
+extern "C" int gs_pose_tangent_grad(const float* xi, const float* dL_ddelta, int32_t n_views, float* dL_dxi,
+                                    void* stream) {
+    if (!xi || !dL_ddelta || !dL_dxi || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_INVALID_ARG;
+    k_pose_tangent_grad<<<1, 64, 0, (cudaStream_t)stream>>>(xi, dL_ddelta, n_views, dL_dxi);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
 extern "C" int gs_l1_loss(const float* color, const float* target, int64_t count, float* dL_dcolor, float* loss,
                           void* ws, size_t ws_bytes, void* stream) {
     if (!color || !target || !dL_dcolor || !loss || count < 1 || !ws || ws_bytes < 4 * kLossMaxBlocks)

@@ -33,6 +33,7 @@ EXPORTS = [
     "gs_anchor_check", "gs_anchor_offload", "gs_anchor_load",
     "gs_mlp_patches", "gs_mlp_param_count", "gs_mlp_workspace_size", "gs_mlp_forward", "gs_mlp_train_step",
     "gs_mlp_gemm_bf16", "gs_mlp_tc_error", "gs_mlp_targets_workspace_size", "gs_mlp_targets", "gs_spawn_learned",
+    "gs_pose_apply", "gs_pose_tangent_grad",
 ]
 
 
@@ -136,6 +137,8 @@ def lib():
             "gs_pose_step": (C.c_int, [P, C.c_int32, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
                                        C.c_int32, P, P]),
             "gs_counter_add": (C.c_int, [P, C.c_int32, P]),
+            "gs_pose_apply": (C.c_int, [P, P, C.c_int32, P, P]),
+            "gs_pose_tangent_grad": (C.c_int, [P, P, C.c_int32, P, P]),
             "gs_l1_loss": (C.c_int, [P, P, C.c_int64, P, P, P, C.c_size_t, P]),
             "gs_composite_bwd": (C.c_int, [C.POINTER(gs_projected), C.POINTER(gs_pairs), C.POINTER(gs_frame),
                                            C.POINTER(gs_config), C.POINTER(gs_image), P, C.c_int64, P, C.c_size_t,
@@ -601,6 +604,15 @@ def gs_pose_step(cams: torch.Tensor, n_views: int, dL_dpose: torch.Tensor, m: to
                  step_dev: torch.Tensor | None = None):
     _check(lib().gs_pose_step(_ptr(cams), n_views, _ptr(dL_dpose), _ptr(m), _ptr(v), lr_t, lr_r, beta1, beta2, eps,
                               step, _ptr(step_dev), _stream(stream)), "gs_pose_step")
+
+
+def gs_pose_apply(cams_ref: torch.Tensor, xi: torch.Tensor, n_views: int, cams_out: torch.Tensor, stream=None):
+    _check(lib().gs_pose_apply(_ptr(cams_ref), _ptr(xi), n_views, _ptr(cams_out), _stream(stream)), "gs_pose_apply")
+
+
+def gs_pose_tangent_grad(xi: torch.Tensor, dL_ddelta: torch.Tensor, n_views: int, dL_dxi: torch.Tensor, stream=None):
+    _check(lib().gs_pose_tangent_grad(_ptr(xi), _ptr(dL_ddelta), n_views, _ptr(dL_dxi), _stream(stream)),
+           "gs_pose_tangent_grad")
 
 
 def gs_counter_add(counter: torch.Tensor, delta: int = 1, stream=None):

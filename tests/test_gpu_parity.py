@@ -227,8 +227,8 @@ def run_views(sc, cams, sh_degree, dLs=None, seed=0, pose_through_sh=0, bg=(0.0,
 
 
 def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), max_amb_frac=0.3, max_excl_frac=0.25,
-                  **launch):
-    r, dLs, d_proj = run_views(sc, cams, sh_degree, pose_through_sh=pose_through_sh, bg=bg, **launch)
+                  dLs=None, **launch):
+    r, dLs, d_proj = run_views(sc, cams, sh_degree, dLs=dLs, pose_through_sh=pose_through_sh, bg=bg, **launch)
     tile = launch.get("tile", 16)
     ocfg = O.Config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg, tile=tile, **MARGINS)
     n = sc.n
