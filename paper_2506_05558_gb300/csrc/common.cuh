@@ -73,10 +73,13 @@ void scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
 
 // Stable LSD radix sort of (uint32 key, uint32 value) pairs on key bits
 // [0, bits), 8 bits per pass. The pair count is min(n_max, *n_dev). Buffers
-// (ka, va) hold the input; (kb, vb) are the alternates. Returns true when the
-// sorted result ends in (kb, vb). hist: 256 * radix_blocks(n_max) uint32.
+// (ka, va) hold the input; (kb, vb) are the alternates. With va_is_position
+// the input values are taken to be 0, 1, 2, ... and va is not read (it is
+// still needed as the alternate buffer). Returns true when the sorted result
+// ends in (kb, vb). hist: 256 * radix_blocks(n_max) uint32.
 int64_t radix_blocks(int64_t n_max);
 bool radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, int64_t n_max,
-                      const uint32_t* n_dev, int bits, uint32_t* hist, void* scan_ws, cudaStream_t s);
+                      const uint32_t* n_dev, int bits, uint32_t* hist, void* scan_ws, cudaStream_t s,
+                      bool va_is_position);
 
 }  // namespace gs

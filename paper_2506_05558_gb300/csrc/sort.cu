@@ -145,6 +145,14 @@ void scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
 
 // ---------------------------------------------------------------------------
 // LSD radix sort, 8-bit digits, stable.
+//
+// Each CTA owns 4096 consecutive keys. The histogram pass counts digits with
+// shared-memory atomics into per-warp sub-histograms. The scatter pass ranks
+// keys within each warp (peers by __match_any_sync, running per-warp digit
+// counts in shared memory), turns warp counts into block-local digit offsets,
+// places keys and values in shared memory in sorted order and then writes
+// each digit's run to its global offset with consecutive threads on
+// consecutive addresses.
 // ---------------------------------------------------------------------------
 constexpr int kRadixThreads = 256;
 constexpr int kRadixWarps = kRadixThreads / 32;
@@ -159,88 +167,111 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const uint32_t* __
                                                               const uint32_t* n_dev, int shift, uint32_t* hist,
                                                               int64_t nb) {
     __shared__ uint32_t h[kRadixWarps][256];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int w = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kRadixWarps * 256; i += kRadixThreads) (&h[0][0])[i] = 0;
     __syncthreads();
     const int64_t n = valid_count(n_max, n_dev);
-    const int64_t base = (int64_t)blockIdx.x * kRadixTile + (int64_t)w * kRadixWarpSpan;
-    for (int it = 0; it < kRadixIters; it++) {
-        const int64_t idx = base + it * 32 + lane;
-        const bool valid = idx < n;
-        const unsigned d = valid ? (keys[idx] >> shift) & 255u : 256u;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
-        if (valid && (peers & lanemask_lt()) == 0) h[w][d] += __popc(peers);
-        __syncwarp();
+    const int64_t b0 = (int64_t)blockIdx.x * kRadixTile;
+    if (b0 < n) {
+        uint32_t k[kRadixIters];
+#pragma unroll
+        for (int it = 0; it < kRadixIters; it++) {
+            const int64_t idx = b0 + it * kRadixThreads + threadIdx.x;
+            k[it] = idx < n ? keys[idx] : 0u;
+        }
+#pragma unroll
+        for (int it = 0; it < kRadixIters; it++)
+            if (b0 + it * kRadixThreads + threadIdx.x < n) atomicAdd(&h[w][(k[it] >> shift) & 255u], 1u);
     }
     __syncthreads();
     uint32_t s = 0;
 #pragma unroll
-    for (int k = 0; k < kRadixWarps; k++) s += h[k][threadIdx.x];
+    for (int q = 0; q < kRadixWarps; q++) s += h[q][threadIdx.x];
     hist[(int64_t)threadIdx.x * nb + blockIdx.x] = s;
 }
 
+// vin == nullptr: the values are the keys' input positions (0, 1, 2, ...).
 __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
                                                                  const uint32_t* __restrict__ vin,
                                                                  uint32_t* __restrict__ kout,
                                                                  uint32_t* __restrict__ vout, int64_t n_max,
                                                                  const uint32_t* n_dev, int shift,
                                                                  const uint32_t* __restrict__ hist, int64_t nb) {
-    __shared__ uint32_t cnt[kRadixWarps][256];
-    __shared__ uint32_t goff[256];
+    __shared__ uint32_t cnt[kRadixWarps][256];  // per-warp digit counts, then each warp's offset within the digit
+    __shared__ uint32_t goff[256];              // global offset of this CTA's run of each digit
+    __shared__ uint32_t dstart[256];            // block-local start of each digit
+    __shared__ uint32_t s_k[kRadixTile];
+    __shared__ uint32_t s_v[kRadixTile];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t n = valid_count(n_max, n_dev);
+    const int64_t b0 = (int64_t)blockIdx.x * kRadixTile;
+    if (b0 >= n) return;  // uniform over the CTA
     for (int i = threadIdx.x; i < kRadixWarps * 256; i += kRadixThreads) (&cnt[0][0])[i] = 0;
     goff[threadIdx.x] = hist[(int64_t)threadIdx.x * nb + blockIdx.x];
     __syncthreads();
-    const int64_t n = valid_count(n_max, n_dev);
-    const int64_t base = (int64_t)blockIdx.x * kRadixTile + (int64_t)w * kRadixWarpSpan;
+    const int64_t base = b0 + (int64_t)w * kRadixWarpSpan;
     uint32_t kk[kRadixIters], vv[kRadixIters], rank[kRadixIters];
-    unsigned dig[kRadixIters];
 #pragma unroll
     for (int it = 0; it < kRadixIters; it++) {
         const int64_t idx = base + it * 32 + lane;
         const bool valid = idx < n;
         kk[it] = valid ? kin[idx] : 0u;
-        vv[it] = valid ? vin[idx] : 0u;
+        vv[it] = valid ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kRadixIters; it++) {
+        const bool valid = base + it * 32 + lane < n;
         const unsigned d = valid ? (kk[it] >> shift) & 255u : 256u;
-        dig[it] = d;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
-        const unsigned before = valid ? cnt[w][d] : 0u;
+        const unsigned lower = peers & lanemask_lt();
+        const uint32_t before = valid ? cnt[w][d] : 0u;
         __syncwarp();
-        if (valid && (peers & lanemask_lt()) == 0) cnt[w][d] = before + __popc(peers);
+        if (valid && lower == 0) cnt[w][d] = before + __popc(peers);
         __syncwarp();
-        rank[it] = before + __popc(peers & lanemask_lt());
+        rank[it] = valid ? before + __popc(lower) : 0xFFFFFFFFu;
     }
     __syncthreads();
-    {  // exclusive prefix over warps for each digit
-        uint32_t run = 0;
+    uint32_t tot = 0;  // thread t handles digit t
 #pragma unroll
-        for (int k = 0; k < kRadixWarps; k++) {
-            const uint32_t c = cnt[k][threadIdx.x];
-            cnt[k][threadIdx.x] = run;
-            run += c;
-        }
+    for (int q = 0; q < kRadixWarps; q++) {
+        const uint32_t c = cnt[q][threadIdx.x];
+        cnt[q][threadIdx.x] = tot;
+        tot += c;
     }
+    uint32_t ex;
+    block_exclusive_scan<kRadixThreads>(tot, ex);
+    dstart[threadIdx.x] = ex;
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kRadixIters; it++) {
-        if (dig[it] < 256u) {
-            const uint32_t dest = goff[dig[it]] + cnt[w][dig[it]] + rank[it];
-            if ((int64_t)dest < n) {  // always true for a consistent histogram; guards the scatter
-                kout[dest] = kk[it];
-                vout[dest] = vv[it];
-            }
+        if (rank[it] != 0xFFFFFFFFu) {
+            const unsigned d = (kk[it] >> shift) & 255u;
+            const uint32_t pos = dstart[d] + cnt[w][d] + rank[it];
+            s_k[pos] = kk[it];
+            s_v[pos] = vv[it];
+        }
+    }
+    __syncthreads();
+    const int cnt_block = (int)min((int64_t)kRadixTile, n - b0);
+    for (int i = threadIdx.x; i < cnt_block; i += kRadixThreads) {
+        const uint32_t k = s_k[i];
+        const unsigned d = (k >> shift) & 255u;
+        const uint32_t dest = goff[d] + (uint32_t)i - dstart[d];
+        if ((int64_t)dest < n) {  // always true for a consistent histogram; guards the scatter
+            kout[dest] = k;
+            vout[dest] = s_v[i];
         }
     }
 }
 
 bool radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, int64_t n_max, const uint32_t* n_dev,
-                      int bits, uint32_t* hist, void* scan_ws, cudaStream_t s) {
+                      int bits, uint32_t* hist, void* scan_ws, cudaStream_t s, bool va_is_position) {
     const int64_t nb = radix_blocks(n_max);
     bool in_b = false;
     if (nb == 0) return false;
     for (int shift = 0; shift < bits; shift += 8) {
         uint32_t* ki = in_b ? kb : ka;
-        uint32_t* vi = in_b ? vb : va;
+        const uint32_t* vi = in_b ? vb : (va_is_position && shift == 0 ? nullptr : va);
         uint32_t* ko = in_b ? ka : kb;
         uint32_t* vo = in_b ? va : vb;
         k_radix_hist<<<(unsigned)nb, kRadixThreads, 0, s>>>(ki, n_max, n_dev, shift, hist, nb);
@@ -275,33 +306,70 @@ __global__ void k_pair_count(const uint32_t* total, int64_t capacity, int64_t* c
     *status = (int64_t)t > capacity ? GS_ERR_CAPACITY : GS_OK;
 }
 
-__global__ void k_duplicate(const uint32_t* __restrict__ sorted_item, const uint32_t* __restrict__ emit_off,
-                            const uint32_t* n_vis, const ushort4* __restrict__ rect, int64_t n, gs_frame f,
-                            int64_t capacity, uint32_t* __restrict__ offset, uint32_t* __restrict__ pkey,
-                            uint32_t* __restrict__ pval, uint32_t* __restrict__ psrc) {
+// One (tile, emission slot) pair per tile of each visible item's rect, the
+// items taken in depth order. A warp owns 32 consecutive sorted items, whose
+// pairs occupy consecutive slots, and writes them together: pair j of the
+// warp's run finds its item by a binary search over the lanes' prefix counts,
+// so consecutive lanes write consecutive slots whatever the rect sizes.
+__global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ sorted_item,
+                                                   const uint32_t* __restrict__ emit_off, const uint32_t* n_vis,
+                                                   const ushort4* __restrict__ rect, int64_t n, gs_frame f,
+                                                   int64_t capacity, uint32_t* __restrict__ offset,
+                                                   uint32_t* __restrict__ pkey, uint32_t* __restrict__ psrc) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= (int64_t)*n_vis) return;
-    const uint32_t item = sorted_item[s];
-    const uint32_t off = emit_off[s];
-    offset[item] = off;
-    const int v = (int)(item / (uint64_t)n);
-    const ushort4 r = rect[item];
-    const uint32_t tb = (uint32_t)f.tile_base[v];
-    const uint32_t tx = (uint32_t)f.tiles_x[v];
-    const uint32_t ty = (uint32_t)f.tiles_y[v];
-    int64_t e = off;
-    // rect is clamped to the view's grid by gs_project; re-clamp so foreign input cannot index past it
-    const uint32_t x0 = min((uint32_t)r.x, tx), x1 = min((uint32_t)r.z, tx);
-    const uint32_t y0 = min((uint32_t)r.y, ty), y1 = min((uint32_t)r.w, ty);
-    for (uint32_t y = y0; y < y1; y++)
-        for (uint32_t x = x0; x < x1; x++) {
-            if (e < capacity) {
-                pkey[e] = tb + y * tx + x;
-                pval[e] = (uint32_t)e;
-                psrc[e] = item;
-            }
-            e++;
+    const int64_t nv = *n_vis;
+    if (s - lane >= nv) return;  // uniform over the warp
+    uint32_t item = 0, off = 0, x0 = 0, y0 = 0, wx = 1, cnt = 0, tb = 0, tx = 0;
+    if (s < nv) {
+        item = sorted_item[s];
+        off = emit_off[s];
+        offset[item] = off;
+        const int v = (int)(item / (uint64_t)n);
+        const ushort4 r = rect[item];
+        tb = (uint32_t)f.tile_base[v];
+        tx = (uint32_t)f.tiles_x[v];
+        const uint32_t ty = (uint32_t)f.tiles_y[v];
+        // rect is clamped to the view's grid by gs_project; re-clamp so foreign input cannot index past it
+        x0 = min((uint32_t)r.x, tx);
+        const uint32_t x1 = max(min((uint32_t)r.z, tx), x0);
+        y0 = min((uint32_t)r.y, ty);
+        const uint32_t y1 = max(min((uint32_t)r.w, ty), y0);
+        wx = max(x1 - x0, 1u);
+        cnt = (x1 - x0) * (y1 - y0);
+    }
+    uint32_t start = cnt;  // inclusive, then exclusive prefix of cnt over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, start, o);
+        if (lane >= o) start += t;
+    }
+    const uint32_t total = __shfl_sync(FULL, start, 31);
+    start -= cnt;
+    for (uint32_t b = 0; b < total; b += 32) {
+        const uint32_t j = b + lane;
+        int L = 0;  // highest lane whose prefix start is <= j
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const uint32_t st = __shfl_sync(FULL, start, L + step);
+            if (L + step < 32 && st <= j) L += step;
         }
+        const uint32_t st = __shfl_sync(FULL, start, L);
+        const uint32_t o = __shfl_sync(FULL, off, L);
+        const uint32_t it = __shfl_sync(FULL, item, L);
+        const uint32_t ax = __shfl_sync(FULL, x0, L), ay = __shfl_sync(FULL, y0, L);
+        const uint32_t aw = __shfl_sync(FULL, wx, L), atb = __shfl_sync(FULL, tb, L), atx = __shfl_sync(FULL, tx, L);
+        if (j < total) {
+            const uint32_t local = j - st;
+            const uint32_t yy = local / aw, xx = local - yy * aw;
+            const int64_t e = (int64_t)o + local;
+            if (e < capacity) {
+                pkey[e] = atb + (ay + yy) * atx + ax + xx;
+                psrc[e] = it;
+            }
+        }
+    }
 }
 
 __global__ void k_finish_pairs(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sval,
@@ -415,7 +483,7 @@ extern "C" int gs_sort(const gs_projected* p, int64_t n, const gs_frame* f, cons
                                                                        w.vis_pos, n_items, w.vk0, w.vv0);
     count_launch();
     // 2. stable sort of visible items by depth bits
-    const bool in1 = radix_sort_pairs(w.vk0, w.vv0, w.vk1, w.vv1, n_items, n_vis, 32, w.hist, w.scan, s);
+    const bool in1 = radix_sort_pairs(w.vk0, w.vv0, w.vk1, w.vv1, n_items, n_vis, 32, w.hist, w.scan, s, false);
     const uint32_t* sorted_item = in1 ? w.vv1 : w.vv0;
     // 3. emission offsets in depth order; pair count
     scan_exclusive(LoadGatherTiles{p->n_tiles, sorted_item}, w.emit_off, n_items, n_vis, p_total, w.scan, s);
@@ -424,12 +492,13 @@ extern "C" int gs_sort(const gs_projected* p, int64_t n, const gs_frame* f, cons
     // 4. duplicate: one (tile, emission slot) pair per tile of each visible item's rect
     k_duplicate<<<(unsigned)ceil_div(n_items, 256), 256, 0, s>>>(sorted_item, w.emit_off, n_vis,
                                                                  (const ushort4*)p->rect, n, *f, out->capacity,
-                                                                 out->offset, w.pk0, w.pv0, w.psrc);
+                                                                 out->offset, w.pk0, w.psrc);
     count_launch();
     // 5. stable sort by global tile index; 6. gather sources, tile ranges
     if (out->capacity > 0) {
+        // the pairs' values are their emission slots, i.e. their positions before the sort
         const bool pin1 = radix_sort_pairs(w.pk0, w.pv0, w.pk1, w.pv1, out->capacity, n_eff,
-                                           bits_for(n_tiles_total), w.hist, w.scan, s);
+                                           bits_for(n_tiles_total), w.hist, w.scan, s, true);
         k_finish_pairs<<<(unsigned)ceil_div(out->capacity, 256), 256, 0, s>>>(
             pin1 ? w.pk1 : w.pk0, pin1 ? w.pv1 : w.pv0, w.psrc, n_eff, out->src, out->emit, out->range);
         count_launch();
@@ -439,7 +508,8 @@ extern "C" int gs_sort(const gs_projected* p, int64_t n, const gs_frame* f, cons
         k_tile_order_keys<<<(unsigned)ceil_div(n_tiles_total, 256), 256, 0, s>>>(out->range, n_tiles_total, w.tk0,
                                                                                   w.tv0);
         count_launch();
-        const bool t1 = radix_sort_pairs(w.tk0, w.tv0, w.tk1, w.tv1, n_tiles_total, nullptr, 16, w.hist, w.scan, s);
+        const bool t1 = radix_sort_pairs(w.tk0, w.tv0, w.tk1, w.tv1, n_tiles_total, nullptr, 16, w.hist, w.scan, s,
+                                         false);
         k_copy_u32<<<(unsigned)ceil_div(n_tiles_total, 256), 256, 0, s>>>(t1 ? w.tv1 : w.tv0, out->order,
                                                                            n_tiles_total);
         count_launch();

@@ -152,5 +152,5 @@ def test_config1_l1_dssim_loss_gradients():
         loss = (img - tgt).abs().mean() + 0.2 * (1.0 - ssim(img, tgt))
         loss.backward()
         opt.step()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     assert losses[-1] < losses[0], losses
