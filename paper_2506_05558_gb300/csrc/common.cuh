@@ -38,6 +38,13 @@ __device__ __forceinline__ float fast_exp2(float x) {
     return y;
 }
 
+// Hardware reciprocal approximation (MUFU), for x away from 0 and infinity.
+__device__ __forceinline__ float fast_rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

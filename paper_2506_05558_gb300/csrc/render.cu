@@ -165,21 +165,23 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                 while (m) {
                     const int k = k0 + __ffs(m) - 1;
                     m &= m - 1;
-                    if (done) continue;
+                    // predicated: every lane runs the same instructions, the
+                    // pixel's state changes only where the Gaussian composites
                     const float2 xy = s_xy[k];
                     const float4 abco = s_abco[k];
                     const float e = exponent2(abco, px - xy.x, py - xy.y);
-                    if (e > 0.f) continue;
                     const float og = __fmul_rn(abco.w, fast_exp2(e));
                     const float alpha = fminf(cfg.alpha_max, og);
-                    if (alpha < cfg.alpha_min) continue;
+                    const bool ok = !done && !(e > 0.f) && alpha >= cfg.alpha_min;
                     const float nT = __fmul_rn(T, 1.f - alpha);
-                    if (nT < cfg.t_min) { done = true; continue; }
+                    const bool term = ok && nT < cfg.t_min;
+                    const bool acc = ok && !term;
+                    done = done || term;
                     const float4 c = s_rgb[k];
-                    const float w = alpha * T;
+                    const float w = acc ? alpha * T : 0.f;
                     cr += w * c.x; cg += w * c.y; cb += w * c.z;
-                    T = nT;
-                    last = (int)(b0 - start) + k + 1;
+                    T = acc ? nT : T;
+                    last = acc ? (int)(b0 - start) + k + 1 : last;
                 }
             }
         }
@@ -314,45 +316,40 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
                     const int jb = 31 - __clz(m);
                     m &= ~(1u << jb);
                     const int k = k0 + jb;
-                    float g[9];
-#pragma unroll
-                    for (int c = 0; c < 9; c++) g[c] = 0.f;
-                    bool contrib = false;
-                    if (b0 + k < nc) {
-                        const float2 xy = s_xy[k];
-                        const float4 abco = s_abco[k];
-                        const float dx = px - xy.x, dy = py - xy.y;
-                        const float e = exponent2(abco, dx, dy);
-                        if (!(e > 0.f)) {
-                            const float G = fast_exp2(e);
-                            const float og = __fmul_rn(abco.w, G);
-                            const float alpha = fminf(cfg.alpha_max, og);
-                            if (alpha >= cfg.alpha_min) {
-                                contrib = true;
-                                const float one_m = 1.f - alpha;
-                                T = T / one_m;  // transmittance in front of this Gaussian
-                                const float4 c = s_rgb[k];
-                                const float wgt = alpha * T;
-                                g[6] = wgt * gr; g[7] = wgt * gg; g[8] = wgt * gb;
-                                const float inv = 1.f / one_m;
-                                const float dalpha = gr * (T * c.x - (Sr + bgr) * inv) +
-                                                     gg * (T * c.y - (Sg + bgg) * inv) +
-                                                     gb * (T * c.z - (Sb + bgb) * inv);
-                                Sr += wgt * c.x; Sg += wgt * c.y; Sb += wgt * c.z;
-                                if (og < cfg.alpha_max) {
-                                    const float dpow = dalpha * og;     // d alpha / d(natural exponent)
-                                    const float q = -dpow * inv_log2e;  // (a dx + b dy) = -(2A dx + B dy)/log2(e)
-                                    g[0] = q * (2.f * abco.x * dx + abco.y * dy);
-                                    g[1] = q * (abco.y * dx + 2.f * abco.z * dy);
-                                    g[2] = -0.5f * dpow * dx * dx;
-                                    g[3] = -dpow * dx * dy;
-                                    g[4] = -0.5f * dpow * dy * dy;
-                                    g[5] = dalpha * G;
-                                }
-                            }
-                        }
-                    }
+                    const float2 xy = s_xy[k];
+                    const float4 abco = s_abco[k];
+                    const float dx = px - xy.x, dy = py - xy.y;
+                    const float e = exponent2(abco, dx, dy);
+                    const float G = fast_exp2(e);
+                    const float og = __fmul_rn(abco.w, G);
+                    const float alpha = fminf(cfg.alpha_max, og);
+                    // same decisions as the forward pass: listed before this pixel's
+                    // last contributor, exponent <= 0, alpha >= alpha_min
+                    const bool contrib = b0 + k < nc && !(e > 0.f) && alpha >= cfg.alpha_min;
                     if (__any_sync(FULL, contrib)) {
+                        // predicated adjoint: non-contributing lanes keep their
+                        // state and add zeros
+                        const float inv = fast_rcp(1.f - alpha);
+                        T = contrib ? T * inv : T;  // transmittance in front of this Gaussian
+                        const float4 c = s_rgb[k];
+                        const float wgt = contrib ? alpha * T : 0.f;
+                        const float dalpha = gr * (T * c.x - (Sr + bgr) * inv) + gg * (T * c.y - (Sg + bgg) * inv) +
+                                             gb * (T * c.z - (Sb + bgb) * inv);
+                        Sr += wgt * c.x; Sg += wgt * c.y; Sb += wgt * c.z;
+                        // alpha clamped at alpha_max passes no gradient to the exponent or
+                        // opacity; selects (not products with 0) keep a non-finite og or G
+                        // of a lane outside the Gaussian out of the sums
+                        const bool pass = contrib && og < cfg.alpha_max;
+                        const float dpow = pass ? dalpha * og : 0.f;  // d alpha / d(natural exponent)
+                        const float q = -dpow * inv_log2e;  // (a dx + b dy) = -(2A dx + B dy)/log2(e)
+                        float g[9];
+                        g[0] = q * (2.f * abco.x * dx + abco.y * dy);
+                        g[1] = q * (abco.y * dx + 2.f * abco.z * dy);
+                        g[2] = -0.5f * dpow * dx * dx;
+                        g[3] = -dpow * dx * dy;
+                        g[4] = -0.5f * dpow * dy * dy;
+                        g[5] = pass ? dalpha * G : 0.f;
+                        g[6] = wgt * gr; g[7] = wgt * gg; g[8] = wgt * gb;
                         const float r = warp_reduce9(g, lane);
                         if (owner >= 0) s_part[w][k][owner] = r;
                         written |= 1u << jb;
