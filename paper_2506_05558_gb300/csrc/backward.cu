@@ -83,13 +83,29 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
             const uint32_t off = offset[item];
             float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
             float a2 = 0.f;
-            for (int k = 0; k < nt; k++) {
-                const int64_t e = (int64_t)off + k;
-                if (e >= capacity) break;
-                const float4 p0 = part0[e], p1 = part1[e];
+            // slots past the pair buffer's capacity were never written (overflowed sort)
+            const int run = (int)max((int64_t)0, min((int64_t)nt, capacity - (int64_t)off));
+            const float4* q0 = part0 + off;
+            const float4* q1 = part1 + off;
+            const float* q2 = part2 + off;
+            int k = 0;
+            for (; k + 4 <= run; k += 4) {  // four pairs' loads in flight, summed in slot order
+                float4 p0[4], p1[4];
+                float p2[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) { p0[u] = q0[k + u]; p1[u] = q1[k + u]; p2[u] = q2[k + u]; }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    a0.x += p0[u].x; a0.y += p0[u].y; a0.z += p0[u].z; a0.w += p0[u].w;
+                    a1.x += p1[u].x; a1.y += p1[u].y; a1.z += p1[u].z; a1.w += p1[u].w;
+                    a2 += p2[u];
+                }
+            }
+            for (; k < run; k++) {
+                const float4 p0 = q0[k], p1 = q1[k];
                 a0.x += p0.x; a0.y += p0.y; a0.z += p0.z; a0.w += p0.w;
                 a1.x += p1.x; a1.y += p1.y; a1.z += p1.z; a1.w += p1.w;
-                a2 += part2[e];
+                a2 += q2[k];
             }
             const float du = a0.x, dv = a0.y, dA = a0.z, dB = a0.w, dC = a1.x, dop = a1.y;
             const float dr = a1.z, dg = a1.w, db = a2;
