@@ -1,30 +1,48 @@
 // Adjoint of the projection (K7) and the per-view pose reduction.
 //
-// One thread per Gaussian walks all views in a fixed order: it sums the
-// Gaussian's per-pair partials (contiguous emission slots, written by the
-// compositing adjoint), recomputes the projection for that view, applies the
-// chain rule to every parameter and accumulates over views in registers, so
-// each gradient row is written once, without atomics. Each view's pose
-// gradient is reduced per CTA in a fixed order and then across CTAs by
-// k_pose_reduce: the whole backward pass is deterministic.
+// A CTA holds 32 Gaussians (one per lane) and up to 8 views (one per warp).
+// Each warp sums its (view, Gaussian) items' pair partials (contiguous
+// emission slots written by the compositing adjoint), recomputes the
+// projection, applies the chain rule and leaves per item in shared memory the
+// 12 geometry gradients, a visibility mark, the clamp-masked colour gradient
+// (3) and the 16 SH basis values. The views are then summed in a fixed order;
+// the SH coefficient gradients are formed there as sum_v gc_v[ch] Y_v[k], so
+// the per-item record is 32 values instead of 64. Each gradient row is
+// written once, without atomics. Each view's pose gradient is reduced per CTA
+// in a fixed order and then across CTAs by k_pose_reduce: the whole backward
+// pass is deterministic.
 #include "common.cuh"
 #include "sh.cuh"
 
 namespace gs {
 
-constexpr int kPBGauss = 32;                   // Gaussians per CTA, one per lane
+constexpr int kPBGauss = 32;                   // Gaussians per CTA group, one per lane
 constexpr int kPBWarps = 8;                    // views processed at once, one per warp
 constexpr int kPBThreads = kPBGauss * kPBWarps;
-constexpr int kSlots = 64;                     // 4 mean/logit + 4 scale + 4 quat + 48 SH + visible + pad
-constexpr int kSlotVis = 60;
+// per-item record: 0-3 mean xyz + opacity logit, 4-7 log-scale xyz + 0, 8-11
+// quaternion, 12 visible, 13-15 clamp-masked colour gradient, 16-31 SH basis
+constexpr int kSlots = 32;
+constexpr int kSlotVis = 12, kSlotGc = 13, kSlotY = 16;
 constexpr int kSlotPitch = kPBGauss + 1;       // +1 word: conflict-free column access
+// output values per Gaussian: 12 geometry, visible, 48 SH coefficient gradients
+constexpr int kOut = 61;
+constexpr int kAcc = (kOut * kPBGauss + kPBThreads - 1) / kPBThreads;
 constexpr size_t kPBSmem = sizeof(float) * kPBWarps * kSlots * kSlotPitch;
 
-// Gradient of one (view, Gaussian) item, written to this warp's slot column.
-struct ItemOut {
-    float* col;  // s_slot[w][*][lane]
-    __device__ __forceinline__ void put(int c, float v) const { col[c * kSlotPitch] = v; }
-};
+// Output value o (0..60) of lane gl, summed over warps w0 .. w0 + nw - 1 of the
+// slot array in a fixed order.
+__device__ __forceinline__ float out_value(const float* s_slot, int w0, int nw, int o, int gl) {
+    float a = 0.f;
+    if (o <= kSlotVis) {
+        for (int w = w0; w < w0 + nw; w++) a += s_slot[(w * kSlots + o) * kSlotPitch + gl];
+    } else {
+        const int c = o - (kSlotVis + 1), k = c / 3, ch = c - 3 * k;
+        for (int w = w0; w < w0 + nw; w++)
+            a += s_slot[(w * kSlots + kSlotGc + ch) * kSlotPitch + gl] *
+                 s_slot[(w * kSlots + kSlotY + k) * kSlotPitch + gl];
+    }
+    return a;
+}
 
 __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
     const float4* __restrict__ mean_opa, const float4* __restrict__ scale, const float4* __restrict__ quat,
@@ -62,11 +80,12 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
     const float sv[3] = {expf(s4.x), expf(s4.y), expf(s4.z)};
     const float opa = 1.f / (1.f + expf(-mo.w));
     const int ncoef = (cfg.sh_degree + 1) * (cfg.sh_degree + 1);
-    const ItemOut out{s_slot + (w * kSlots) * kSlotPitch + lane};
-    // reducer: thread t owns slot values idx = t + 256 i (slot idx / 32, Gaussian idx % 32)
-    float acc[kSlots * kPBGauss / kPBThreads];
+    float* col = s_slot + (w * kSlots) * kSlotPitch + lane;  // this item's record
+    auto put = [&](int c, float v) { col[c * kSlotPitch] = v; };
+    // G == 1 (8 views or more): thread t accumulates output values t + 256 i over rounds
+    float acc[kAcc];
 #pragma unroll
-    for (int i = 0; i < kSlots * kPBGauss / kPBThreads; i++) acc[i] = 0.f;
+    for (int i = 0; i < kAcc; i++) acc[i] = 0.f;
     __syncthreads();
 
     for (int v0 = 0; v0 < nv; v0 += nvw) {
@@ -76,7 +95,7 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
         float pose[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (nt <= 0) {
 #pragma unroll 4
-            for (int c = 0; c < kSlots; c++) out.put(c, 0.f);
+            for (int c = 0; c < kSlots; c++) put(c, 0.f);  // all of it: 0 x stale data could be NaN
         } else {
             const gs_camera& c = s_cam[v];
             // 1. sum this item's pair partials (contiguous emission slots)
@@ -113,7 +132,75 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
                 float* o = d_proj + 9 * item;
                 o[0] = du; o[1] = dv; o[2] = dA; o[3] = dB; o[4] = dC; o[5] = dop; o[6] = dr; o[7] = dg; o[8] = db;
             }
-            // 2. recompute the projection
+
+            // 2. colour: rgb = max(0.5 + sum_k Y_k(d) sh_k, 0), d = (mu - centre)/|mu - centre|
+            const float ccx = -(c.R[0] * c.t[0] + c.R[3] * c.t[1] + c.R[6] * c.t[2]);
+            const float ccy = -(c.R[1] * c.t[0] + c.R[4] * c.t[1] + c.R[7] * c.t[2]);
+            const float ccz = -(c.R[2] * c.t[0] + c.R[5] * c.t[1] + c.R[8] * c.t[2]);
+            float ddx = mo.x - ccx, ddy = mo.y - ccy, ddz = mo.z - ccz;
+            const float il = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+            ddx *= il; ddy *= il; ddz *= il;
+            const float4* shg = sh + 12 * g;
+            float gc[3];
+            {
+                float Y[16];
+                sh_eval_basis(cfg.sh_degree, ddx, ddy, ddz, Y);
+                float raw0 = 0.5f, raw1 = 0.5f, raw2 = 0.5f;
+#pragma unroll
+                for (int r = 0; r < 12; r++) {
+                    if (4 * r < 3 * ncoef) {
+                        const float4 q = shg[r];
+                        const float cq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int idx = 4 * r + u, kk = idx / 3, ch = idx % 3;
+                            if (kk < ncoef) {
+                                if (ch == 0) raw0 += Y[kk] * cq[u];
+                                else if (ch == 1) raw1 += Y[kk] * cq[u];
+                                else raw2 += Y[kk] * cq[u];
+                            }
+                        }
+                    }
+                }
+                gc[0] = raw0 > 0.f ? dr : 0.f;
+                gc[1] = raw1 > 0.f ? dg : 0.f;
+                gc[2] = raw2 > 0.f ? db : 0.f;
+#pragma unroll
+                for (int kk = 0; kk < 16; kk++) put(kSlotY + kk, kk < ncoef ? Y[kk] : 0.f);
+            }
+            put(kSlotGc, gc[0]);
+            put(kSlotGc + 1, gc[1]);
+            put(kSlotGc + 2, gc[2]);
+            float gmx = 0.f, gmy = 0.f, gmz = 0.f;
+            if (cfg.sh_degree > 0) {
+                // direction gradient of sum_k w_k Y_k(d), w_k = sum_ch gc[ch] sh[k][ch]
+                float wk[16];
+#pragma unroll
+                for (int kk = 0; kk < 16; kk++) wk[kk] = 0.f;
+#pragma unroll
+                for (int r = 0; r < 12; r++) {
+                    if (4 * r < 3 * ncoef) {
+                        const float4 q = shg[r];
+                        const float cq[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int idx = 4 * r + u, kk = idx / 3, ch = idx % 3;
+                            if (kk >= 1 && kk < ncoef) wk[kk] += gc[ch] * cq[u];
+                        }
+                    }
+                }
+                const float3 gd = sh_weighted_grad(cfg.sh_degree, ddx, ddy, ddz, wk);
+                const float dd = gd.x * ddx + gd.y * ddy + gd.z * ddz;
+                gmx = (gd.x - ddx * dd) * il; gmy = (gd.y - ddy * dd) * il; gmz = (gd.z - ddz * dd) * il;
+                if (cfg.pose_grad_through_sh) {
+                    // centre = -R^T t moves by -R^T rho under exp(xi^): dL/drho += R dL/ddir
+                    pose[0] += c.R[0] * gmx + c.R[1] * gmy + c.R[2] * gmz;
+                    pose[1] += c.R[3] * gmx + c.R[4] * gmy + c.R[5] * gmz;
+                    pose[2] += c.R[6] * gmx + c.R[7] * gmy + c.R[8] * gmz;
+                }
+            }
+
+            // 3. recompute the projection
             const float x = c.R[0] * mo.x + c.R[1] * mo.y + c.R[2] * mo.z + c.t[0];
             const float y = c.R[3] * mo.x + c.R[4] * mo.y + c.R[5] * mo.z + c.t[1];
             const float z = c.R[6] * mo.x + c.R[7] * mo.y + c.R[8] * mo.z + c.t[2];
@@ -121,8 +208,9 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
 #pragma unroll
             for (int r = 0; r < 3; r++)
 #pragma unroll
-                for (int k = 0; k < 3; k++)
-                    T[3 * r + k] = (c.R[3 * r] * Rq[k] + c.R[3 * r + 1] * Rq[3 + k] + c.R[3 * r + 2] * Rq[6 + k]) * sv[k];
+                for (int kk = 0; kk < 3; kk++)
+                    T[3 * r + kk] =
+                        (c.R[3 * r] * Rq[kk] + c.R[3 * r + 1] * Rq[3 + kk] + c.R[3 * r + 2] * Rq[6 + kk]) * sv[kk];
             const float limx = 1.3f * 0.5f * (float)c.width / c.fx;
             const float limy = 1.3f * 0.5f * (float)c.height / c.fy;
             const float iz = 1.f / z;
@@ -132,77 +220,15 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
             const float J00 = c.fx * iz, J02 = -c.fx * txz * iz, J11 = c.fy * iz, J12 = -c.fy * tyz * iz;
             float M0[3], M1[3];  // rows of M = J T
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                M0[k] = J00 * T[k] + J02 * T[6 + k];
-                M1[k] = J11 * T[3 + k] + J12 * T[6 + k];
+            for (int kk = 0; kk < 3; kk++) {
+                M0[kk] = J00 * T[kk] + J02 * T[6 + kk];
+                M1[kk] = J11 * T[3 + kk] + J12 * T[6 + kk];
             }
             const float Sa = M0[0] * M0[0] + M0[1] * M0[1] + M0[2] * M0[2] + cfg.dilation;
             const float Sb = M0[0] * M1[0] + M0[1] * M1[1] + M0[2] * M1[2];
             const float Sc = M1[0] * M1[0] + M1[1] * M1[1] + M1[2] * M1[2] + cfg.dilation;
             const float idet = 1.f / (Sa * Sc - Sb * Sb);
             const float Qa = Sc * idet, Qb = -Sb * idet, Qc = Sa * idet;
-
-            // 3. colour: rgb = max(0.5 + sum_k Y_k(d) sh_k, 0), d = (mu - centre)/|mu - centre|
-            const float ccx = -(c.R[0] * c.t[0] + c.R[3] * c.t[1] + c.R[6] * c.t[2]);
-            const float ccy = -(c.R[1] * c.t[0] + c.R[4] * c.t[1] + c.R[7] * c.t[2]);
-            const float ccz = -(c.R[2] * c.t[0] + c.R[5] * c.t[1] + c.R[8] * c.t[2]);
-            float ddx = mo.x - ccx, ddy = mo.y - ccy, ddz = mo.z - ccz;
-            const float il = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
-            ddx *= il; ddy *= il; ddz *= il;
-            float Y[16];
-            sh_eval_basis(cfg.sh_degree, ddx, ddy, ddz, Y);
-            const float4* shg = sh + 12 * g;
-            float raw0 = 0.5f, raw1 = 0.5f, raw2 = 0.5f;
-#pragma unroll
-            for (int r = 0; r < 12; r++) {
-                if (4 * r < 3 * ncoef) {
-                    const float4 q = shg[r];
-                    const float cq[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                    for (int u = 0; u < 4; u++) {
-                        const int idx = 4 * r + u, k = idx / 3, ch = idx % 3;
-                        if (k < ncoef) {
-                            if (ch == 0) raw0 += Y[k] * cq[u];
-                            else if (ch == 1) raw1 += Y[k] * cq[u];
-                            else raw2 += Y[k] * cq[u];
-                        }
-                    }
-                }
-            }
-            const float gc[3] = {raw0 > 0.f ? dr : 0.f, raw1 > 0.f ? dg : 0.f, raw2 > 0.f ? db : 0.f};
-#pragma unroll
-            for (int k = 0; k < 16; k++)
-#pragma unroll
-                for (int ch = 0; ch < 3; ch++) out.put(12 + 3 * k + ch, k < ncoef ? gc[ch] * Y[k] : 0.f);
-            float gmx = 0.f, gmy = 0.f, gmz = 0.f;
-            if (cfg.sh_degree > 0) {
-                float3 dY[16];
-                sh_basis_grad(cfg.sh_degree, ddx, ddy, ddz, dY);
-                float gdx = 0.f, gdy = 0.f, gdz = 0.f;
-#pragma unroll
-                for (int r = 0; r < 12; r++) {
-                    if (4 * r < 3 * ncoef) {
-                        const float4 q = shg[r];
-                        const float cq[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-                        for (int u = 0; u < 4; u++) {
-                            const int idx = 4 * r + u, k = idx / 3, ch = idx % 3;
-                            if (k >= 1 && k < ncoef) {
-                                const float s = gc[ch] * cq[u];
-                                gdx += s * dY[k].x; gdy += s * dY[k].y; gdz += s * dY[k].z;
-                            }
-                        }
-                    }
-                }
-                const float dd = gdx * ddx + gdy * ddy + gdz * ddz;
-                gmx = (gdx - ddx * dd) * il; gmy = (gdy - ddy * dd) * il; gmz = (gdz - ddz * dd) * il;
-                if (cfg.pose_grad_through_sh) {
-                    // centre = -R^T t moves by -R^T rho under exp(xi^): dL/drho += R dL/ddir
-                    pose[0] += c.R[0] * gmx + c.R[1] * gmy + c.R[2] * gmz;
-                    pose[1] += c.R[3] * gmx + c.R[4] * gmy + c.R[5] * gmz;
-                    pose[2] += c.R[6] * gmx + c.R[7] * gmy + c.R[8] * gmz;
-                }
-            }
 
             // 4. conic = S^-1: dL/dS = -Q dL/dQ Q, dL/dQ = [[dA, dB/2], [dB/2, dC]]
             const float hB = 0.5f * dB;
@@ -214,9 +240,9 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
             // 5. S = M M^T + dil I: dL/dM = 2 GS M
             float GM0[3], GM1[3];
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                GM0[k] = 2.f * (GS00 * M0[k] + GS01 * M1[k]);
-                GM1[k] = 2.f * (GS01 * M0[k] + GS11 * M1[k]);
+            for (int kk = 0; kk < 3; kk++) {
+                GM0[kk] = 2.f * (GS00 * M0[kk] + GS01 * M1[kk]);
+                GM1[kk] = 2.f * (GS01 * M0[kk] + GS11 * M1[kk]);
             }
             // 6. M = J T: dL/dJ = GM T^T (entries J00, J02, J11, J12), dL/dT = J^T GM
             const float GJ00 = GM0[0] * T[0] + GM0[1] * T[1] + GM0[2] * T[2];
@@ -225,25 +251,25 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
             const float GJ12 = GM1[0] * T[6] + GM1[1] * T[7] + GM1[2] * T[8];
             float GT[9];
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                GT[k] = J00 * GM0[k];
-                GT[3 + k] = J11 * GM1[k];
-                GT[6 + k] = J02 * GM0[k] + J12 * GM1[k];
+            for (int kk = 0; kk < 3; kk++) {
+                GT[kk] = J00 * GM0[kk];
+                GT[3 + kk] = J11 * GM1[kk];
+                GT[6 + kk] = J02 * GM0[kk] + J12 * GM1[kk];
             }
             // 7. T = R Rq diag(s): dL/d(Rq diag s) = R^T GT -> log-scale and rotation matrix
             float gRq[9];
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
+            for (int kk = 0; kk < 3; kk++) {
                 float gsk = 0.f;
 #pragma unroll
                 for (int r = 0; r < 3; r++) {
-                    const float h = c.R[r] * GT[k] + c.R[3 + r] * GT[3 + k] + c.R[6 + r] * GT[6 + k];
-                    gsk += h * Rq[3 * r + k];
-                    gRq[3 * r + k] = h * sv[k];
+                    const float h = c.R[r] * GT[kk] + c.R[3 + r] * GT[3 + kk] + c.R[6 + r] * GT[6 + kk];
+                    gsk += h * Rq[3 * r + kk];
+                    gRq[3 * r + kk] = h * sv[kk];
                 }
-                out.put(4 + k, gsk * sv[k]);
+                put(4 + kk, gsk * sv[kk]);
             }
-            out.put(7, 0.f);
+            put(7, 0.f);
             // rotation matrix -> normalised quaternion -> raw quaternion
             float gq[4];
             gq[0] = 2.f * (-qz * gRq[1] + qy * gRq[2] + qz * gRq[3] - qx * gRq[5] - qy * gRq[6] + qx * gRq[7]);
@@ -254,10 +280,10 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
             gq[3] = 2.f * (-2.f * qz * gRq[0] - qw * gRq[1] + qx * gRq[2] + qw * gRq[3] - 2.f * qz * gRq[4] +
                            qy * gRq[5] + qx * gRq[6] + qy * gRq[7]);
             const float qd = gq[0] * qw + gq[1] * qx + gq[2] * qy + gq[3] * qz;
-            out.put(8, (gq[0] - qw * qd) * qi);
-            out.put(9, (gq[1] - qx * qd) * qi);
-            out.put(10, (gq[2] - qy * qd) * qi);
-            out.put(11, (gq[3] - qz * qd) * qi);
+            put(8, (gq[0] - qw * qd) * qi);
+            put(9, (gq[1] - qx * qd) * qi);
+            put(10, (gq[2] - qy * qd) * qi);
+            put(11, (gq[3] - qz * qd) * qi);
             // 8. p = (x, y, z): through the 2D mean and J
             float gpx = du * c.fx * iz, gpy = dv * c.fy * iz;
             float gpz = -(du * c.fx * x + dv * c.fy * y) * iz * iz;
@@ -275,13 +301,11 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
                 gpz += 2.f * GJ12 * c.fy * y * iz * iz * iz;
             }
             // mean: p = R mu + t (plus the SH view-direction term)
-            out.put(0, gmx + c.R[0] * gpx + c.R[3] * gpy + c.R[6] * gpz);
-            out.put(1, gmy + c.R[1] * gpx + c.R[4] * gpy + c.R[7] * gpz);
-            out.put(2, gmz + c.R[2] * gpx + c.R[5] * gpy + c.R[8] * gpz);
-            out.put(3, dop * opa * (1.f - opa));
-            out.put(kSlotVis, 1.f);
-#pragma unroll
-            for (int cc = kSlotVis + 1; cc < kSlots; cc++) out.put(cc, 0.f);
+            put(0, gmx + c.R[0] * gpx + c.R[3] * gpy + c.R[6] * gpz);
+            put(1, gmy + c.R[1] * gpx + c.R[4] * gpy + c.R[7] * gpz);
+            put(2, gmz + c.R[2] * gpx + c.R[5] * gpy + c.R[8] * gpz);
+            put(3, dop * opa * (1.f - opa));
+            put(kSlotVis, 1.f);
             // 9. pose, left perturbation: dp = rho + phi x p, dT = phi^ T
             pose[0] += gpx; pose[1] += gpy; pose[2] += gpz;
             pose[3] += y * gpz - z * gpy;
@@ -290,10 +314,10 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
             // tr(T GT^T phi^): N = T GT^T, dphi = (N12 - N21, N20 - N02, N01 - N10)
             float N01 = 0.f, N10 = 0.f, N02 = 0.f, N20 = 0.f, N12 = 0.f, N21 = 0.f;
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                N01 += T[k] * GT[3 + k]; N10 += T[3 + k] * GT[k];
-                N02 += T[k] * GT[6 + k]; N20 += T[6 + k] * GT[k];
-                N12 += T[3 + k] * GT[6 + k]; N21 += T[6 + k] * GT[3 + k];
+            for (int kk = 0; kk < 3; kk++) {
+                N01 += T[kk] * GT[3 + kk]; N10 += T[3 + kk] * GT[kk];
+                N02 += T[kk] * GT[6 + kk]; N20 += T[6 + kk] * GT[kk];
+                N12 += T[3 + kk] * GT[6 + kk]; N21 += T[6 + kk] * GT[3 + kk];
             }
             pose[3] += N12 - N21;
             pose[4] += N20 - N02;
@@ -311,57 +335,49 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
             pose_part[((int64_t)v * n_groups + gi) * 6 + lane] = pv;
         }
         __syncthreads();
-        // sum each group's warps (its views of this round) in a fixed order
-        if (G == 1) {  // possibly several rounds: accumulate in registers
+        if (G == 1) {  // possibly several rounds: accumulate this round's views in registers
 #pragma unroll
-            for (int i = 0; i < kSlots * kPBGauss / kPBThreads; i++) {
+            for (int i = 0; i < kAcc; i++) {
                 const int idx = threadIdx.x + kPBThreads * i;
-                const int cs = idx >> 5, gl = idx & 31;
-                float sacc = 0.f;
-                for (int ww = 0; ww < nvw; ww++) sacc += s_slot[(ww * kSlots + cs) * kSlotPitch + gl];
-                acc[i] += sacc;
+                if (idx < kOut * kPBGauss) acc[i] += out_value(s_slot, 0, nvw, idx >> 5, idx & 31);
             }
-        } else {  // a single round: fold into the group's first warp's slots
-            for (int e = threadIdx.x; e < G * kSlots * kPBGauss; e += kPBThreads) {
-                const int grp = e / (kSlots * kPBGauss), rem = e % (kSlots * kPBGauss);
-                const int cs = rem >> 5, gl = rem & 31;
-                const int base = grp * nvw;
-                float sacc = 0.f;
-                for (int ww = 0; ww < nvw; ww++) sacc += s_slot[((base + ww) * kSlots + cs) * kSlotPitch + gl];
-                s_slot[(base * kSlots + cs) * kSlotPitch + gl] = sacc;
-            }
+            __syncthreads();
         }
-        __syncthreads();
     }
-    if (G == 1) {  // stage the totals in warp 0's slots
+    if (G == 1) {  // stage the totals as [kOut][kSlotPitch] at the start of the slot array
 #pragma unroll
-        for (int i = 0; i < kSlots * kPBGauss / kPBThreads; i++) {
+        for (int i = 0; i < kAcc; i++) {
             const int idx = threadIdx.x + kPBThreads * i;
-            s_slot[(idx >> 5) * kSlotPitch + (idx & 31)] = acc[i];
+            if (idx < kOut * kPBGauss) s_slot[(idx >> 5) * kSlotPitch + (idx & 31)] = acc[i];
         }
         __syncthreads();
     }
-    // write rows, coalesced across each group's 32 Gaussians
+    // output value o of group grp's lane gl: the staged total (G == 1) or the
+    // sum over the group's warps (G > 1, a single round)
+    auto total = [&](int grp, int o, int gl) -> float {
+        return G == 1 ? s_slot[o * kSlotPitch + gl] : out_value(s_slot, grp * nvw, nvw, o, gl);
+    };
+    // write rows, coalesced across each group's 32 Gaussians: 3 geometry rows and
+    // 12 SH rows (output value 13 + c holds SH element c = 3 k + ch)
     for (int ri = threadIdx.x; ri < G * 15 * kPBGauss; ri += kPBThreads) {
         const int grp = ri / (15 * kPBGauss), rr = ri % (15 * kPBGauss);
-        const float* src = s_slot + (grp * nvw * kSlots) * kSlotPitch;
         const int64_t g0 = ((int64_t)blockIdx.x * G + grp) * kPBGauss;
-        int gl, c0;
+        int gl, o0;
         float4* dst;
         if (rr < 3 * kPBGauss) {
             gl = rr % kPBGauss;
             const int arr = rr / kPBGauss;
-            c0 = 4 * arr;
+            o0 = 4 * arr;
             dst = (arr == 0 ? g_mean_opa : arr == 1 ? g_scale : g_quat) + (g0 + gl);
         } else {
             const int r = rr - 3 * kPBGauss;
             gl = r / 12;
-            c0 = 12 + 4 * (r % 12);
+            o0 = kSlotVis + 1 + 4 * (r % 12);
             dst = g_sh + (g0 + gl) * 12 + (r % 12);
         }
         if (g0 + gl >= n) continue;
-        float4 val = make_float4(src[c0 * kSlotPitch + gl], src[(c0 + 1) * kSlotPitch + gl],
-                                 src[(c0 + 2) * kSlotPitch + gl], src[(c0 + 3) * kSlotPitch + gl]);
+        float4 val = make_float4(total(grp, o0, gl), total(grp, o0 + 1, gl), total(grp, o0 + 2, gl),
+                                 total(grp, o0 + 3, gl));
         if (cfg.accumulate) {
             const float4 old = *dst;
             val.x += old.x; val.y += old.y; val.z += old.z; val.w += old.w;
@@ -372,7 +388,7 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
         const int grp = t / kPBGauss, gl = t % kPBGauss;
         const int64_t gg = ((int64_t)blockIdx.x * G + grp) * kPBGauss + gl;
         if (gg >= n) continue;
-        const bool vis = s_slot[((grp * nvw * kSlots) + kSlotVis) * kSlotPitch + gl] > 0.f;
+        const bool vis = total(grp, kSlotVis, gl) > 0.f;
         uint8_t* vd = visible + gg;
         *vd = (vis || (cfg.accumulate && *vd)) ? 1 : 0;
     }

@@ -41,28 +41,49 @@ __device__ __forceinline__ void sh_eval_basis(int deg, float x, float y, float z
     Y[15] = -kSH3a * x * (xx - 3.f * yy);
 }
 
-// Gradient of each basis polynomial w.r.t. (x, y, z): dY[k] = (d/dx, d/dy, d/dz).
-__device__ __forceinline__ void sh_basis_grad(int deg, float x, float y, float z, float3* dY) {
-    dY[0] = make_float3(0.f, 0.f, 0.f);
-    if (deg < 1) return;
-    dY[1] = make_float3(0.f, -kSH1, 0.f);
-    dY[2] = make_float3(0.f, 0.f, kSH1);
-    dY[3] = make_float3(-kSH1, 0.f, 0.f);
-    if (deg < 2) return;
+// Gradient of f = sum_k w_k Y_k with respect to the direction components
+// (x, y, z) of the basis polynomials, accumulated term by term (w_0 unused:
+// Y_0 is constant).
+__device__ __forceinline__ float3 sh_weighted_grad(int deg, float x, float y, float z, const float* w) {
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    if (deg < 1) return make_float3(gx, gy, gz);
+    gy -= kSH1 * w[1];
+    gz += kSH1 * w[2];
+    gx -= kSH1 * w[3];
+    if (deg < 2) return make_float3(gx, gy, gz);
+    gx += kSH2a * w[4] * y;  // Y4 = a x y
+    gy += kSH2a * w[4] * x;
+    gy -= kSH2a * w[5] * z;  // Y5 = -a y z
+    gz -= kSH2a * w[5] * y;
+    gx -= 2.f * kSH2b * w[6] * x;  // Y6 = b (2 zz - xx - yy)
+    gy -= 2.f * kSH2b * w[6] * y;
+    gz += 4.f * kSH2b * w[6] * z;
+    gx -= kSH2a * w[7] * z;  // Y7 = -a x z
+    gz -= kSH2a * w[7] * x;
+    gx += 2.f * kSH2c * w[8] * x;  // Y8 = c (xx - yy)
+    gy -= 2.f * kSH2c * w[8] * y;
+    if (deg < 3) return make_float3(gx, gy, gz);
     const float xx = x * x, yy = y * y, zz = z * z;
-    dY[4] = make_float3(kSH2a * y, kSH2a * x, 0.f);
-    dY[5] = make_float3(0.f, -kSH2a * z, -kSH2a * y);
-    dY[6] = make_float3(-2.f * kSH2b * x, -2.f * kSH2b * y, 4.f * kSH2b * z);
-    dY[7] = make_float3(-kSH2a * z, 0.f, -kSH2a * x);
-    dY[8] = make_float3(2.f * kSH2c * x, -2.f * kSH2c * y, 0.f);
-    if (deg < 3) return;
-    dY[9] = make_float3(-kSH3a * 6.f * x * y, -kSH3a * (3.f * xx - 3.f * yy), 0.f);
-    dY[10] = make_float3(kSH3b * y * z, kSH3b * x * z, kSH3b * x * y);
-    dY[11] = make_float3(kSH3c * 2.f * x * y, -kSH3c * (4.f * zz - xx - 3.f * yy), -kSH3c * 8.f * y * z);
-    dY[12] = make_float3(-kSH3d * 6.f * x * z, -kSH3d * 6.f * y * z, kSH3d * (6.f * zz - 3.f * xx - 3.f * yy));
-    dY[13] = make_float3(-kSH3c * (4.f * zz - 3.f * xx - yy), kSH3c * 2.f * x * y, -kSH3c * 8.f * x * z);
-    dY[14] = make_float3(kSH3e * 2.f * x * z, -kSH3e * 2.f * y * z, kSH3e * (xx - yy));
-    dY[15] = make_float3(-kSH3a * (3.f * xx - 3.f * yy), kSH3a * 6.f * x * y, 0.f);
+    gx -= kSH3a * w[9] * 6.f * x * y;  // Y9 = -a y (3 xx - yy)
+    gy -= kSH3a * w[9] * (3.f * xx - 3.f * yy);
+    gx += kSH3b * w[10] * y * z;  // Y10 = b x y z
+    gy += kSH3b * w[10] * x * z;
+    gz += kSH3b * w[10] * x * y;
+    gx += kSH3c * w[11] * 2.f * x * y;  // Y11 = -c y (4 zz - xx - yy)
+    gy -= kSH3c * w[11] * (4.f * zz - xx - 3.f * yy);
+    gz -= kSH3c * w[11] * 8.f * y * z;
+    gx -= kSH3d * w[12] * 6.f * x * z;  // Y12 = d z (2 zz - 3 xx - 3 yy)
+    gy -= kSH3d * w[12] * 6.f * y * z;
+    gz += kSH3d * w[12] * (6.f * zz - 3.f * xx - 3.f * yy);
+    gx -= kSH3c * w[13] * (4.f * zz - 3.f * xx - yy);  // Y13 = -c x (4 zz - xx - yy)
+    gy += kSH3c * w[13] * 2.f * x * y;
+    gz -= kSH3c * w[13] * 8.f * x * z;
+    gx += kSH3e * w[14] * 2.f * x * z;  // Y14 = e z (xx - yy)
+    gy -= kSH3e * w[14] * 2.f * y * z;
+    gz += kSH3e * w[14] * (xx - yy);
+    gx -= kSH3a * w[15] * (3.f * xx - 3.f * yy);  // Y15 = -a x (xx - 3 yy)
+    gy += kSH3a * w[15] * 6.f * x * y;
+    return make_float3(gx, gy, gz);
 }
 
 // Unclamped colour 0.5 + sum_k Y_k sh_k for one Gaussian (sh: its 12 float4 rows).
