@@ -98,6 +98,13 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
             for (int c = 0; c < kSlots; c++) put(c, 0.f);  // all of it: 0 x stale data could be NaN
         } else {
             const gs_camera& c = s_cam[v];
+            // the SH rows are needed after the partial sums: start fetching them into L2 now
+            const float4* shg = sh + 12 * g;
+            if (ncoef > 1) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(shg));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(shg + 6));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(shg + 11));
+            }
             // 1. sum this item's pair partials (contiguous emission slots)
             const uint32_t off = offset[item];
             float4 a0 = make_float4(0.f, 0.f, 0.f, 0.f), a1 = a0;
@@ -140,7 +147,6 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
             float ddx = mo.x - ccx, ddy = mo.y - ccy, ddz = mo.z - ccz;
             const float il = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
             ddx *= il; ddy *= il; ddz *= il;
-            const float4* shg = sh + 12 * g;
             float gc[3];
             {
                 float Y[16];

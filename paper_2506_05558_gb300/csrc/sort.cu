@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_hist(const uint32_t* __
 }
 
 // vin == nullptr: the values are the keys' input positions (0, 1, 2, ...).
-__global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
+__global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const uint32_t* __restrict__ kin,
                                                                  const uint32_t* __restrict__ vin,
                                                                  uint32_t* __restrict__ kout,
                                                                  uint32_t* __restrict__ vout, int64_t n_max,
@@ -210,17 +210,15 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const uint32_t*
     goff[threadIdx.x] = hist[(int64_t)threadIdx.x * nb + blockIdx.x];
     __syncthreads();
     const int64_t base = b0 + (int64_t)w * kRadixWarpSpan;
-    uint32_t kk[kRadixIters], vv[kRadixIters], rank[kRadixIters];
+    // this lane's keys are kin[base + lane + 32 it] for 32 it < rem
+    const int64_t rem = n - base - lane;
+    const uint32_t* kp = kin + base + lane;
+    uint32_t kk[kRadixIters], rank[kRadixIters];  // values are loaded after ranking (fewer registers)
+#pragma unroll
+    for (int it = 0; it < kRadixIters; it++) kk[it] = 32 * it < rem ? kp[32 * it] : 0u;
 #pragma unroll
     for (int it = 0; it < kRadixIters; it++) {
-        const int64_t idx = base + it * 32 + lane;
-        const bool valid = idx < n;
-        kk[it] = valid ? kin[idx] : 0u;
-        vv[it] = valid ? (vin ? vin[idx] : (uint32_t)idx) : 0u;
-    }
-#pragma unroll
-    for (int it = 0; it < kRadixIters; it++) {
-        const bool valid = base + it * 32 + lane < n;
+        const bool valid = 32 * it < rem;
         const unsigned d = valid ? (kk[it] >> shift) & 255u : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const unsigned lower = peers & lanemask_lt();
@@ -242,6 +240,11 @@ __global__ void __launch_bounds__(kRadixThreads) k_radix_scatter(const uint32_t*
     block_exclusive_scan<kRadixThreads>(tot, ex);
     dstart[threadIdx.x] = ex;
     __syncthreads();
+    uint32_t vv[kRadixIters];
+    const uint32_t* vp = vin ? vin + base + lane : nullptr;
+#pragma unroll
+    for (int it = 0; it < kRadixIters; it++)
+        vv[it] = 32 * it < rem ? (vp ? vp[32 * it] : (uint32_t)(base + lane + 32 * it)) : 0u;
 #pragma unroll
     for (int it = 0; it < kRadixIters; it++) {
         if (rank[it] != 0xFFFFFFFFu) {
