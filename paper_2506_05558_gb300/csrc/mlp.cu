@@ -301,6 +301,9 @@ static MlpWs carve_mlp(char* base, size_t cap, int64_t M, size_t* used) {
     return w;
 }
 
+int mlp_forward_fused(const float* const* w, const float* const* b, const float* image, int W, int H, float* out,
+                      cudaStream_t s);
+
 struct MlpPtrs {
     float* w[4];
     float* b[4];
@@ -424,8 +427,13 @@ extern "C" int gs_mlp_forward(const gs_mlp_params* p, const float* image, int32_
     MlpWs w;
     int rc = mlp_setup(p, width, height, ws, ws_bytes, cfg, &w);
     if (rc != GS_OK || !image || !out) return rc != GS_OK ? rc : GS_ERR_INVALID_ARG;
-    rc = mlp_forward(ptrs(p), image, width, height, w, cfg->tensor_path, nullptr, 0.f, 0.f, out,
-                     (cudaStream_t)stream);
+    const MlpPtrs P = ptrs(p);
+    if (cfg->tensor_path == 1 && ((uintptr_t)image & 15) == 0) {
+        // the whole network in one persistent tcgen05 kernel (weights resident in shared memory)
+        rc = mlp_forward_fused(P.w, P.b, image, width, height, out, (cudaStream_t)stream);
+    } else {
+        rc = mlp_forward(P, image, width, height, w, cfg->tensor_path, nullptr, 0.f, 0.f, out, (cudaStream_t)stream);
+    }
     if (rc != GS_OK) return rc;
     GS_CUDA_CHECK_LAUNCH();
     return GS_OK;

@@ -210,3 +210,249 @@ extern "C" int gs_mlp_tc_error(int32_t* out) {
     *out = v;
     return GS_OK;
 }
+
+namespace gs {
+
+// ---------------------------------------------------------------------------
+// Fused inference of the whole MLP on tensor cores (tcgen05).
+//
+// Persistent CTAs of 256 threads, one per SM (about 206 KB of shared memory):
+// each converts the four weight matrices to bfloat16 once, in the canonical
+// no-swizzle K-major layout (K-adjacent 8x16-byte core matrices 128 B apart,
+// 8-row groups (K/8) * 128 B apart), then walks 128-patch tiles. Per tile the
+// threads gather the patch features straight from the image into the same
+// layout (X, 128 x 208), and for each layer one elected thread issues the
+// K/16 tcgen05.mma (M = 128 patches, N = 128 or 16, bf16 in, FP32 in a
+// 128-column TMEM accumulator) and commits them to an mbarrier; the eight
+// warps then read the accumulator back (warps w and w + 4 share TMEM lane
+// quarter w % 4 and split the columns), add the bias, apply GELU and write the
+// bf16 activations over the previous layer's buffer (that product has
+// completed) as the next layer's A operand. The last layer writes (logit,
+// depth, log-scale) in FP32. Every mbarrier wait is bounded; on timeout the
+// kernel records the failing line in g_tc_error, frees its TMEM and returns.
+// ---------------------------------------------------------------------------
+constexpr int kFM = 128, kFIn = 194, kFInPad = 208, kFHid = 128, kFOut = 3, kFOutPad = 16;
+constexpr int kFThreads = 256;
+constexpr uint32_t kFOffW1 = 0;
+constexpr uint32_t kFOffW2 = kFOffW1 + kFHid * kFInPad * 2;     // 53248
+constexpr uint32_t kFOffW3 = kFOffW2 + kFHid * kFHid * 2;       // 86016
+constexpr uint32_t kFOffW4 = kFOffW3 + kFHid * kFHid * 2;       // 118784
+constexpr uint32_t kFOffX = kFOffW4 + kFOutPad * kFHid * 2;     // 122880
+constexpr uint32_t kFOffH = kFOffX + kFM * kFInPad * 2;         // 176128
+constexpr uint32_t kFOffB = kFOffH + kFM * kFHid * 2;           // 208896: biases, FP32
+constexpr uint32_t kFSmem = kFOffB + (3 * kFHid + kFOutPad) * 4;
+
+// Byte offset of element (r, k) of a K-major [rows][K] bf16 matrix, K % 8 == 0.
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k, int K) {
+    return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ uint4 pack8_bf16(const float* v) {
+    uint4 u;
+    uint32_t* w = reinterpret_cast<uint32_t*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+        w[i] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    return u;
+}
+
+__device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
+
+// W [rows_valid][cols_valid] FP32 (nn.Linear layout) -> bf16 [rows][K] K-major at dst, zero padded.
+__device__ void stage_weight(const float* __restrict__ Wm, int rows_valid, int cols_valid, int rows, int K,
+                             uint8_t* dst) {
+    const int chunks = rows * (K >> 3);
+    for (int q = threadIdx.x; q < chunks; q += blockDim.x) {
+        const int r = q / (K >> 3), kc = q % (K >> 3);
+        float v[8];
+#pragma unroll
+        for (int e = 0; e < 8; e++) {
+            const int k = kc * 8 + e;
+            v[e] = (r < rows_valid && k < cols_valid) ? Wm[(int64_t)r * cols_valid + k] : 0.f;
+        }
+        *reinterpret_cast<uint4*>(dst + kmajor_off(r, kc * 8, K)) = pack8_bf16(v);
+    }
+}
+
+__global__ void __launch_bounds__(kFThreads, 1) k_mlp_forward_tc(
+    const float* __restrict__ image, int W, int H, const float* __restrict__ w1, const float* __restrict__ b1,
+    const float* __restrict__ w2, const float* __restrict__ b2, const float* __restrict__ w3,
+    const float* __restrict__ b3, const float* __restrict__ w4, const float* __restrict__ b4,
+    float* __restrict__ out) {
+    extern __shared__ __align__(1024) uint8_t sm[];
+    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nx = W >> 3, ny = H >> 3;
+    const int64_t M = (int64_t)nx * ny;
+    const int64_t n_tiles = (M + kFM - 1) / kFM;
+    const uint32_t bar = smem_u32(&s_bar);
+    float* s_b = reinterpret_cast<float*>(sm + kFOffB);  // b1 | b2 | b3 | b4 (padded to 16)
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&s_tmem)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_fail = 0;
+    }
+    stage_weight(w1, kFHid, kFIn, kFHid, kFInPad, sm + kFOffW1);
+    stage_weight(w2, kFHid, kFHid, kFHid, kFHid, sm + kFOffW2);
+    stage_weight(w3, kFHid, kFHid, kFHid, kFHid, sm + kFOffW3);
+    stage_weight(w4, kFOut, kFHid, kFOutPad, kFHid, sm + kFOffW4);
+    for (int i = tid; i < 3 * kFHid + kFOutPad; i += kFThreads) {
+        const int l = i / kFHid, j = i % kFHid;
+        s_b[i] = l == 0 ? b1[j] : l == 1 ? b2[j] : l == 2 ? b3[j] : (j < kFOut ? b4[j] : 0.f);
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const uint32_t sbase = smem_u32(sm);
+    uint32_t phase = 0;
+
+    for (int64_t tile = blockIdx.x; tile < n_tiles && !s_fail; tile += gridDim.x) {
+        // 1. features: chunk q = (row r, 8-column group kc); a warp covers 32 patches of one group
+        const int64_t p0 = tile * kFM;
+        for (int q = tid; q < kFM * (kFInPad >> 3); q += kFThreads) {
+            const int r = q % kFM, kc = q / kFM;
+            const int64_t p = p0 + r;
+            float v[8];
+            if (p < M) {
+                const int py = (int)(p / nx), px = (int)(p % nx);
+                if (kc < 24) {  // 3 channels x 8 rows of 8 pixels
+                    const int c = kc >> 3, dy = kc & 7;
+                    const float4* src =
+                        reinterpret_cast<const float4*>(image + ((int64_t)c * H + 8 * py + dy) * W + 8 * px);
+                    const float4 a = src[0], b = src[1];
+                    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; e++) v[e] = 0.f;
+                    if (kc == 24) {  // patch centre in [-1, 1]^2, x first
+                        v[0] = (px + 0.5f) / nx * 2.f - 1.f;
+                        v[1] = (py + 0.5f) / ny * 2.f - 1.f;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; e++) v[e] = 0.f;
+            }
+            *reinterpret_cast<uint4*>(sm + kFOffX + kmajor_off(r, kc * 8, kFInPad)) = pack8_bf16(v);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+
+        for (int l = 0; l < 4; l++) {
+            const int K = l == 0 ? kFInPad : kFHid;
+            const int N = l == 3 ? kFOutPad : kFHid;
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t a0 = sbase + (l == 0 ? kFOffX : kFOffH);
+                const uint32_t b0 = sbase + (l == 0 ? kFOffW1 : l == 1 ? kFOffW2 : l == 2 ? kFOffW3 : kFOffW4);
+                const uint32_t sbo = (uint32_t)(K >> 3) * 128u;
+                const uint32_t idesc = instr_desc_bf16(kFM, N);
+                for (int s = 0; s < K / 16; s++) {
+                    const uint64_t ad = smem_desc(a0 + s * 256, 128, sbo);
+                    const uint64_t bd = smem_desc(b0 + s * 256, 128, sbo);
+                    const uint32_t acc = s > 0 ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                        : "memory");
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                                 bar)
+                             : "memory");
+                uint32_t spins = 0;
+                while (!mbar_try_wait(bar, phase)) {
+                    if (++spins > kTcSpinLimit) {
+                        s_fail = __LINE__;
+                        break;
+                    }
+                }
+            }
+            phase ^= 1u;
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            if (s_fail) break;
+            // 2. epilogue: row r of the tile = TMEM lane 32 (warp % 4) + lane
+            const int quarter = warp & 3, half = warp >> 2;
+            const int r = 32 * quarter + lane;
+            const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+            if (l < 3) {
+                for (int c0 = 64 * half; c0 < 64 * half + 64; c0 += 16) {
+                    uint32_t u[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15}, [%16];\n"
+                        : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+                          "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]),
+                          "=r"(u[14]), "=r"(u[15])
+                        : "r"(trow + (uint32_t)c0));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; j++) v[j] = gelu_erf(__uint_as_float(u[j]) + s_b[l * kFHid + c0 + j]);
+                    *reinterpret_cast<uint4*>(sm + kFOffH + kmajor_off(r, c0, kFHid)) = pack8_bf16(v);
+                    *reinterpret_cast<uint4*>(sm + kFOffH + kmajor_off(r, c0 + 8, kFHid)) = pack8_bf16(v + 8);
+                }
+            } else if (half == 0) {
+                uint32_t u[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                    "%15}, [%16];\n"
+                    : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]),
+                      "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]),
+                      "=r"(u[15])
+                    : "r"(trow));
+                asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                const int64_t p = p0 + r;
+                if (p < M) {
+#pragma unroll
+                    for (int j = 0; j < kFOut; j++) out[p * kFOut + j] = __uint_as_float(u[j]) + s_b[3 * kFHid + j];
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();
+        }
+    }
+    if (s_fail && tid == 0) atomicCAS(&g_tc_error, 0, s_fail);
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(128) : "memory");
+    }
+}
+
+int mlp_forward_fused(const float* const* w, const float* const* b, const float* image, int W, int H, float* out,
+                      cudaStream_t s) {
+    static int n_sm = 0;
+    static bool attr_set = false;
+    if (!attr_set) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFSmem);
+        attr_set = true;
+    }
+    const int64_t M = (int64_t)(W / 8) * (H / 8);
+    const int64_t n_tiles = (M + kFM - 1) / kFM;
+    if (n_tiles == 0) return GS_OK;
+    const int grid = (int)(n_tiles < n_sm ? n_tiles : n_sm);
+    k_mlp_forward_tc<<<grid, kFThreads, kFSmem, s>>>(image, W, H, w[0], b[0], w[1], b[1], w[2], b[2], w[3], b[3], out);
+    count_launch();
+    return GS_OK;
+}
+
+}  // namespace gs

@@ -93,6 +93,24 @@ def test_forward_matches_oracle(PATH):
 
 
 @pytest.mark.parametrize("PATH", PATHS)
+def test_forward_full_frame_matches_oracle(PATH):
+    """A 1920x1080 frame: 32,400 patches = 253 tiles of 128 with a ragged last
+    tile, more tiles than SMs (the tcgen05 path runs the fused persistent
+    kernel, so CTAs take several tiles)."""
+    rng, layers, image, targets = mlp_case(5, W=1920, H=1080)
+    n = gs.gs_mlp_patches(1920, 1080)
+    assert n == 32400
+    out = torch.zeros((n, 3), device="cuda")
+    ws = gs.workspace(gs.gs_mlp_workspace_size(n))
+    gs.gs_mlp_forward(gs.MlpParams.from_numpy(layers), torch.tensor(image, dtype=torch.float32, device="cuda"), 1920,
+                      1080, out, gs.mlp_config(tensor_path=PATH), ws)
+    torch.cuda.synchronize()
+    assert gs.gs_mlp_tc_error() == 0
+    Y, _ = OM.forward(layers, OM.patch_features(image))
+    assert_close(out.cpu().numpy(), Y, 1e-3, what="mlp forward 1080p")
+
+
+@pytest.mark.parametrize("PATH", PATHS)
 def test_train_step_loss_and_gradients_match_oracle(PATH):
     rng, layers, image, targets = mlp_case(2)
     _, loss, out, grads = run_train(layers, image, targets, PATH)
