@@ -160,12 +160,14 @@ def targets_from_spawns(pixel, depth, log_scale, kept, W, H):
     return out
 
 
-def spawn_learned(image, mlp_out, cam, seed, frame, margin=1e-6):
-    """Pixel p of patch m spawns iff u < sigmoid(logit_m) and the predicted depth
-    is positive, u the Philox draw of counter (p, frame, 1, 0). The Gaussian sits
-    at the pixel centre at the patch's predicted depth, with its predicted
-    log-scale on all axes, identity rotation, opacity 0.5 and the pixel colour
-    as SH DC. Returns the spawns in pixel order and the ambiguous pixels."""
+def spawn_learned(image, mlp_out, cam, seed, frame, margin=1e-6, depth=None):
+    """Pixel p of patch m spawns iff u < sigmoid(logit_m) and its depth is
+    positive, u the Philox draw of counter (p, frame, 1, 0). The depth is the
+    depth map's value at p where a map is given and that value is positive and
+    finite, else the patch's predicted depth. The Gaussian sits at the pixel
+    centre at that depth, with the patch's predicted log-scale on all axes,
+    identity rotation, opacity 0.5 and the pixel colour as SH DC. Returns the
+    spawns in pixel order and the ambiguous pixels."""
     from . import oracle as O
     image = np.asarray(image, np.float64)
     _, H, W = image.shape
@@ -177,6 +179,10 @@ def spawn_learned(image, mlp_out, cam, seed, frame, margin=1e-6):
     out = np.asarray(mlp_out, np.float64)
     prob = 1.0 / (1.0 + np.exp(-out[m, 0]))
     z = out[m, 1]
+    if depth is not None:
+        d = np.asarray(depth, np.float64).reshape(-1)
+        use = np.isfinite(d) & (d > 0)
+        z = np.where(use, d, z)
     spawn = (u < prob) & (z > 0)
     amb = np.abs(u - prob) < margin
     idx = np.nonzero(spawn)[0]

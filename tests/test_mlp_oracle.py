@@ -92,3 +92,69 @@ def test_adam_first_step_is_sign():
     p2, _, _ = M.adam(params, grads, z, z, 1, 1e-3, eps=1e-12)
     for (W, b), (W2, b2), (dW, db) in zip(params, p2, grads):
         np.testing.assert_allclose(W2, W - 1e-3 * np.sign(dW), rtol=0, atol=1e-9)
+
+
+def test_targets_from_spawns_hand_case():
+    """Two 8x8 patches of a 16x8 frame; values written out by hand."""
+    W, H = 16, 8
+    # pixels: (x, y) -> p = y W + x; patch 0 = x < 8, patch 1 = x >= 8
+    pixel = np.array([0 * W + 1, 3 * W + 7, 5 * W + 2, 2 * W + 9, 7 * W + 15])
+    depth = np.array([2.0, 4.0, 100.0, 6.0, 8.0])
+    ls = np.array([-3.0, -5.0, 7.0, -2.0, -4.0])
+    kept = np.array([1, 1, 0, 0, 1])
+    t = M.targets_from_spawns(pixel, depth, ls, kept, W, H)
+    np.testing.assert_array_equal(t, [[2 / 64, 3.0, -4.0, 1.0], [1 / 64, 8.0, -4.0, 1.0]])
+    t0 = M.targets_from_spawns(pixel, depth, ls, np.zeros(5), W, H)
+    np.testing.assert_array_equal(t0, np.zeros((2, 4)))
+
+
+def _pin_cam(W, H):
+    from oracle import oracle as O
+    from paper_2506_05558_gb300 import synth
+    R, t = O.retract_pose(np.eye(3), np.zeros(3), [0.3, -0.2, 0.1, 0.05, -0.1, 0.2])
+    return synth.camera(R, t, 50.0, W, H, dtype=np.float64)
+
+
+def test_spawn_learned_certain_and_impossible_spawns():
+    """logit +40: every pixel with a positive depth spawns; logit -40: none.
+    Means reproject to their pixel centres at the chosen depth (projection
+    written here independently); the depth map wins where valid; SH DC gives
+    back the pixel colour."""
+    rng = np.random.default_rng(0)
+    W, H = 24, 16
+    n_p = (W // 8) * (H // 8)
+    cam = _pin_cam(W, H)
+    image = rng.random((3, H, W))
+    out = np.stack([np.full(n_p, 40.0), rng.uniform(1, 9, n_p), np.full(n_p, -4.0)], 1)
+    out[1, 1] = -2.0  # a patch with a negative predicted depth
+    depth = rng.uniform(2, 12, (H, W))
+    depth[rng.random((H, W)) < 0.3] = 0.0  # holes fall back to the prediction
+    for dmap in (None, depth):
+        r = M.spawn_learned(image, out, cam, 5, 3, depth=dmap)
+        p = np.arange(W * H)
+        x, y = p % W, p // W
+        m = (y // 8) * (W // 8) + x // 8
+        z = out[m, 1] if dmap is None else np.where(depth.reshape(-1) > 0, depth.reshape(-1), out[m, 1])
+        np.testing.assert_array_equal(r["pixel"], p[z > 0])
+        q = r["mean"] @ np.asarray(cam["R"]).T + np.asarray(cam["t"])
+        np.testing.assert_allclose(q[:, 2], z[z > 0], rtol=1e-12)
+        np.testing.assert_allclose(cam["fx"] * q[:, 0] / q[:, 2] + cam["cx"], x[z > 0] + 0.5, atol=1e-9)
+        np.testing.assert_allclose(cam["fy"] * q[:, 1] / q[:, 2] + cam["cy"], y[z > 0] + 0.5, atol=1e-9)
+        np.testing.assert_allclose(r["sh_dc"] * (0.5 / math.sqrt(math.pi)) + 0.5, image.reshape(3, -1)[:, z > 0].T,
+                                   atol=1e-12)
+        np.testing.assert_array_equal(r["log_scale"], np.full((int((z > 0).sum()), 3), -4.0))
+    out[:, 0] = -40.0
+    assert M.spawn_learned(image, out, cam, 5, 3)["pixel"].size == 0
+
+
+def test_spawn_learned_rate_follows_the_logit():
+    """Logit 0 and log 3: spawn fractions 1/2 and 3/4 within 4 sigma over
+    64k pixels (independent Philox draws per pixel)."""
+    W, H = 256, 256
+    cam = _pin_cam(W, H)
+    n_p = (W // 8) * (H // 8)
+    image = np.zeros((3, H, W))
+    for logit, want in ((0.0, 0.5), (math.log(3.0), 0.75)):
+        out = np.stack([np.full(n_p, logit), np.full(n_p, 5.0), np.zeros(n_p)], 1)
+        frac = M.spawn_learned(image, out, cam, 11, 2)["pixel"].size / (W * H)
+        assert abs(frac - want) < 4 * math.sqrt(want * (1 - want) / (W * H)), (logit, frac)
