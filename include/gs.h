@@ -395,12 +395,15 @@ int gs_mlp_targets(const int32_t* pixel, const float* depth, const float* log_sc
 
 /* Spawning from the learned proposal's outputs mlp_out [n_patches][3]: pixel p
  * of patch m spawns iff u < sigmoid(logit_m) (u = Philox4x32-10 of counter
- * (p, frame, 1, 0) and key seed) and the predicted depth is positive; the new
- * Gaussian sits at the pixel centre at the patch's predicted depth with its
- * predicted log-scale on all axes (other attributes as gs_spawn_propose).
- * Output, workspace size and status as for gs_spawn_propose. */
-int gs_spawn_learned(const float* image, const float* mlp_out, int32_t width, int32_t height, const gs_camera* cam,
-                     const gs_spawn_config* sc, const gs_spawn_out* out, void* ws, size_t ws_bytes, void* stream);
+ * (p, frame, 1, 0) and key seed) and its depth is positive. The depth is
+ * depth[p] (the per-pixel map gs_spawn_propose takes; may be NULL) where that
+ * is positive and finite, else the patch's predicted depth. The new Gaussian
+ * sits at the pixel centre at that depth with the patch's predicted log-scale
+ * on all axes (other attributes as gs_spawn_propose). Output, workspace size
+ * and status as for gs_spawn_propose. */
+int gs_spawn_learned(const float* image, const float* mlp_out, const float* depth, int32_t width, int32_t height,
+                     const gs_camera* cam, const gs_spawn_config* sc, const gs_spawn_out* out, void* ws,
+                     size_t ws_bytes, void* stream);
 
 /* Error code recorded by a tensor-memory GEMM whose completion wait timed out
  * (0 = none). Synchronous; for tests. */

@@ -334,20 +334,29 @@ __global__ void k_patch_targets(const float4* __restrict__ pix_slot, int W, int 
 
 // Spawn flags from the MLP: pixel p of patch m spawns iff u < sigmoid(logit_m)
 // and the predicted depth is positive; u = Philox(counter (p, frame, 1, 0)).
-__global__ void k_learned_flags(const float* __restrict__ mlp_out, int W, int H, uint2 key, uint32_t frame,
-                                uint32_t* __restrict__ flag) {
+// Depth of a learned spawn at pixel p: the depth map's value where it is
+// positive and finite, else the patch's predicted depth.
+__device__ __forceinline__ float learned_depth(const float* __restrict__ depth, const float* __restrict__ mlp_out,
+                                               int64_t p, int64_t m) {
+    const float d = depth ? depth[p] : 0.f;
+    return (d > 0.f && isfinite(d)) ? d : mlp_out[m * 3 + 1];
+}
+
+__global__ void k_learned_flags(const float* __restrict__ mlp_out, const float* __restrict__ depth, int W, int H,
+                                uint2 key, uint32_t frame, uint32_t* __restrict__ flag) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= (int64_t)W * H) return;
     const int x = (int)(p % W), y = (int)(p / W);
     const int64_t m = (int64_t)(y / 8) * (W / 8) + x / 8;
-    const float logit = mlp_out[m * 3 + 0], z = mlp_out[m * 3 + 1];
+    const float logit = mlp_out[m * 3 + 0], z = learned_depth(depth, mlp_out, p, m);
     const float prob = 1.f / (1.f + expf(-logit));
     const uint4 r = philox4x32_10(make_uint4((uint32_t)p, frame, 1u, 0u), key);
     const float u = (float)(r.x >> 8) * (1.f / 16777216.f);
     flag[p] = (u < prob && z > 0.f && isfinite(z)) ? 1u : 0u;
 }
 
-__global__ void k_learned_emit(const float* __restrict__ image, const float* __restrict__ mlp_out, int W, int H,
+__global__ void k_learned_emit(const float* __restrict__ image, const float* __restrict__ mlp_out,
+                               const float* __restrict__ depth, int W, int H,
                                const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
                                const gs_camera* __restrict__ cam, int64_t capacity, float4* __restrict__ mean_opa,
                                float4* __restrict__ scale, float4* __restrict__ quat, float4* __restrict__ sh,
@@ -358,7 +367,7 @@ __global__ void k_learned_emit(const float* __restrict__ image, const float* __r
     if (o >= capacity) return;
     const int x = (int)(p % W), y = (int)(p / W);
     const int64_t m = (int64_t)(y / 8) * (W / 8) + x / 8;
-    const float z = mlp_out[m * 3 + 1], ls = mlp_out[m * 3 + 2];
+    const float z = learned_depth(depth, mlp_out, p, m), ls = mlp_out[m * 3 + 2];
     const gs_camera& c = *cam;
     const float xc = (x + 0.5f - c.cx) * z / c.fx, yc = (y + 0.5f - c.cy) * z / c.fy;
     const float qx = xc - c.t[0], qy = yc - c.t[1], qz = z - c.t[2];
@@ -407,7 +416,8 @@ extern "C" int gs_mlp_targets(const int32_t* pixel, const float* depth, const fl
     return GS_OK;
 }
 
-extern "C" int gs_spawn_learned(const float* image, const float* mlp_out, int32_t width, int32_t height,
+extern "C" int gs_spawn_learned(const float* image, const float* mlp_out, const float* depth, int32_t width,
+                                int32_t height,
                                 const gs_camera* cam, const gs_spawn_config* sc, const gs_spawn_out* out, void* ws,
                                 size_t ws_bytes, void* stream) {
     if (!image || !mlp_out || !cam || !sc || !out || width <= 0 || height <= 0 || width % 8 || height % 8)
@@ -424,13 +434,14 @@ extern "C" int gs_spawn_learned(const float* image, const float* mlp_out, int32_
     if (!ws || !c.ok() || ((uintptr_t)ws & 255)) return GS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const uint2 key = make_uint2((uint32_t)sc->seed, (uint32_t)(sc->seed >> 32));
-    k_learned_flags<<<(unsigned)ceil_div(hw, 256), 256, 0, s>>>(mlp_out, width, height, key, sc->frame, flag);
+    k_learned_flags<<<(unsigned)ceil_div(hw, 256), 256, 0, s>>>(mlp_out, depth, width, height, key, sc->frame,
+                                                                 flag);
     count_launch();
     scan_exclusive_u32(flag, pos, hw, total, scan_ws, s);
     k_spawn_count<<<1, 1, 0, s>>>(total, out->capacity, out->count, out->status);
     count_launch();
     if (out->capacity > 0) {
-        k_learned_emit<<<(unsigned)ceil_div(hw, 256), 256, 0, s>>>(image, mlp_out, width, height, flag, pos, cam,
+        k_learned_emit<<<(unsigned)ceil_div(hw, 256), 256, 0, s>>>(image, mlp_out, depth, width, height, flag, pos, cam,
                                                                     out->capacity, (float4*)out->mean_opa,
                                                                     (float4*)out->scale, (float4*)out->quat,
                                                                     (float4*)out->sh, out->pixel);

@@ -129,7 +129,7 @@ class OnTheFly:
         if use_learned:
             gs.gs_mlp_forward(self.mlp, image, self.W, self.H, self.mlp_out, self.mlp_cfg, self.ws_mlp)
             gs.gs_spawn_learned(image, self.mlp_out, self.W, self.H, cam, self.seed, frame_idx, self.spawned,
-                                self.ws_spawn)
+                                self.ws_spawn, depth=depth)
         else:
             gs.gs_spawn_propose(image, render, depth, self.W, self.H, cam, 1.0, self.seed, frame_idx, self.spawned,
                                 self.ws_spawn)
@@ -159,18 +159,23 @@ class OnTheFly:
             r.fit_capacity(g, cams)
         return float(loss.item())
 
-    def _train_mlp(self, image, n0, k, depth):
+    def _train_mlp(self, image, n0, k, cam):
         """Targets from this frame's spawns that are still opaque after the
-        optimisation, then a few training steps of the proposal network."""
+        optimisation: their optimised camera depth and mean log-scale, so the
+        network learns where spawns survive and what they converge to; then a
+        few training steps of the proposal network."""
         if k == 0:
             return None
         g, _, _ = self.store.active()
         opa = torch.sigmoid(g.mean_opa[n0:n0 + k, 3])
         kept = (opa > self.keep_threshold).to(torch.uint8)
         pix = self.spawned.pixel[:k]
-        z = depth[pix.long()]
-        ls = self.spawned.g.scale[:k, 0].contiguous()
-        gs.gs_mlp_targets(pix, z.contiguous(), ls, kept, k, self.W, self.H, self.mlp_targets, self.ws_tg)
+        c = gs.cameras_from_tensor(cam)[0]
+        R = torch.tensor(c["R"], dtype=torch.float32, device=self.device)
+        t = torch.tensor(c["t"], dtype=torch.float32, device=self.device)
+        z = (g.mean_opa[n0:n0 + k, :3] @ R[2] + t[2]).contiguous()
+        ls = g.scale[n0:n0 + k, :3].mean(1).contiguous()
+        gs.gs_mlp_targets(pix, z, ls, kept, k, self.W, self.H, self.mlp_targets, self.ws_tg)
         for _ in range(self.mlp_steps):
             self.mlp_step += 1
             gs.gs_mlp_train_step(self.mlp, self.mlp_m, self.mlp_v, image, self.W, self.H, self.mlp_targets,
@@ -188,7 +193,7 @@ class OnTheFly:
         if self.mode == "learned" and not learned:
             # the direct-sampling spawns of the warm-up frames that survived
             # the optimisation teach the proposal
-            mlp_loss = self._train_mlp(image, n0, k, depth)
+            mlp_loss = self._train_mlp(image, n0, k, cam)
         self.log.append(dict(frame=frame_idx, spawned=k, n=self.store.n, loss=loss, learned=learned,
                              mlp_loss=mlp_loss, iters=self.iter_count))
 

@@ -157,7 +157,10 @@ def test_targets_from_kept_spawns_match_oracle():
     assert_close(tg.cpu().numpy(), ref, 1e-6, what="targets")
 
 
-def test_learned_spawn_matches_oracle():
+@pytest.mark.parametrize("with_depth", [False, True])
+def test_learned_spawn_matches_oracle(with_depth):
+    """Spawns from the network's outputs; with a depth map (holes: zero,
+    negative, NaN) its values replace the predicted depth where valid."""
     from paper_2506_05558_gb300 import synth
     from oracle import oracle as O
     rng = np.random.default_rng(6)
@@ -165,14 +168,21 @@ def test_learned_spawn_matches_oracle():
     n_p = (W // 8) * (H // 8)
     out = np.stack([rng.normal(-1, 1.5, n_p), rng.uniform(-1, 15, n_p), rng.normal(-4, 0.5, n_p)], 1).astype(np.float32)
     image = rng.random((3, H, W)).astype(np.float32)
+    depth = None
+    if with_depth:
+        depth = rng.uniform(1, 20, (H, W)).astype(np.float32)
+        holes = rng.random((H, W))
+        depth[holes < 0.2] = 0.0
+        depth[(holes >= 0.2) & (holes < 0.25)] = -3.0
+        depth[(holes >= 0.25) & (holes < 0.3)] = np.nan
     R, t = O.retract_pose(np.eye(3), np.zeros(3), [0.2, -0.1, 0.3, 0.1, 0.05, -0.2])
     cam = synth.camera(R.astype(np.float32), t.astype(np.float32), 120.0, W, H)
     sp = gs.Spawned.alloc(W * H)
     ws = gs.workspace(gs.gs_spawn_workspace_size(W, H))
     gs.gs_spawn_learned(torch.from_numpy(image).cuda(), torch.from_numpy(out).cuda(), W, H, gs.cameras_tensor([cam]),
-                        99, 7, sp, ws)
+                        99, 7, sp, ws, depth=None if depth is None else torch.from_numpy(depth).cuda())
     torch.cuda.synchronize()
-    ref = OM.spawn_learned(image, out, cam, 99, 7)
+    ref = OM.spawn_learned(image, out, cam, 99, 7, depth=depth)
     k = int(sp.count.item())
     pix = sp.pixel[:k].cpu().numpy()
     amb = set(np.nonzero(ref["amb"])[0].tolist())

@@ -45,15 +45,20 @@ def run(mode, frames, size, iters=20):
 
 
 def test_learned_vs_plain_spawning():
+    """Both modes at 10, 20 and 30 iterations per frame; the report records
+    PSNR and set size per budget."""
     size = (256, 144)
     frames = make_stream(size=size)
     empty = 10 * np.log10(1.0 / torch.mean(frames[-1][0] ** 2).item())
-    p_plain, a = run("plain", frames, size)
-    p_learn, b = run("learned", frames, size)
-    report = {"psnr_plain": p_plain, "psnr_learned": p_learn, "gaussians_plain": a.store.n,
-              "gaussians_learned": b.store.n, "iterations": a.iter_count, "empty_render_psnr": empty,
-              "log_learned": b.log}
+    report = {"empty_render_psnr": empty, "frames": len(frames), "size": size, "budgets": {}}
+    for iters in (10, 20, 30):
+        p_plain, a = run("plain", frames, size, iters)
+        p_learn, b = run("learned", frames, size, iters)
+        report["budgets"][iters] = {"psnr_plain": p_plain, "psnr_learned": p_learn, "gaussians_plain": a.store.n,
+                                    "gaussians_learned": b.store.n, "iterations": a.iter_count,
+                                    "spawned_learned": [e["spawned"] for e in b.log],
+                                    "spawned_plain": [e["spawned"] for e in a.log]}
+        assert p_plain > empty + 5 and p_learn > empty + 3, report
     os.makedirs("gpurun_out", exist_ok=True)
     with open("gpurun_out/stream_report.json", "w") as f:
         json.dump(report, f, indent=1)
-    assert p_plain > empty + 5 and p_learn > empty + 3, report
