@@ -160,31 +160,49 @@ def targets_from_spawns(pixel, depth, log_scale, kept, W, H):
     return out
 
 
-def spawn_learned(image, mlp_out, cam, seed, frame, margin=1e-6, depth=None):
-    """Pixel p of patch m spawns iff u < sigmoid(logit_m) and its depth is
-    positive, u the Philox draw of counter (p, frame, 1, 0). The depth is the
-    depth map's value at p where a map is given and that value is positive and
-    finite, else the patch's predicted depth. The Gaussian sits at the pixel
-    centre at that depth, with the patch's predicted log-scale on all axes,
-    identity rotation, opacity 0.5 and the pixel colour as SH DC. Returns the
-    spawns in pixel order and the ambiguous pixels."""
+PATCH_FLOOR = 64 * 1e-3  # lower bound of a patch's P_s sum in the placement ratio
+
+
+def spawn_learned(image, mlp_out, cam, seed, frame, depth=None, render=None, sigma=1.0):
+    """Spawning from the network's per-patch outputs with direct sampling's
+    placement: pixel p of patch m spawns with probability
+    min(1, sigmoid(logit_m) * 64 * P_s(p) / max(sum_{q in m} P_s(q), 0.064)),
+    P_s the spawn probability of Eq. 3 (render penalty included), so the patch
+    receives on average the network's predicted number of kept spawns where
+    direct sampling would have placed them. The draw u is the Philox output of
+    counter (p, frame, 1, 0); the pixel spawns iff u < probability and its depth
+    is positive. The depth is the map's value where a map is given and that
+    value is positive and finite, else the patch's predicted depth. The
+    Gaussian sits at the pixel centre at that depth, with the patch's predicted
+    log-scale on all axes, identity rotation, opacity 0.5 and the pixel colour
+    as SH DC. Returns the spawns in pixel order and, as `amb`, the pixels whose
+    decision an FP32 evaluation may take the other way (|u - probability|
+    within a bound of the FP32 errors of P_s and of the patch sum)."""
     from . import oracle as O
     image = np.asarray(image, np.float64)
     _, H, W = image.shape
     nx = W // PATCH
+    maps = O.spawn_maps(image, render, sigma, seed, frame)
+    ps = maps["p_s"].reshape(-1)
     u = O.philox_uniforms(W * H, frame, 1, seed)
     p = np.arange(W * H)
     x, y = p % W, p // W
     m = (y // PATCH) * nx + x // PATCH
+    S = np.bincount(m, weights=ps, minlength=nx * (H // PATCH))
+    Sf = np.maximum(S, PATCH_FLOOR)[m]
     out = np.asarray(mlp_out, np.float64)
-    prob = 1.0 / (1.0 + np.exp(-out[m, 0]))
+    sig = 1.0 / (1.0 + np.exp(-out[m, 0]))
+    prob = np.minimum(1.0, sig * 64.0 * ps / Sf)
     z = out[m, 1]
     if depth is not None:
         d = np.asarray(depth, np.float64).reshape(-1)
         use = np.isfinite(d) & (d > 0)
         z = np.where(use, d, z)
     spawn = (u < prob) & (z > 0)
-    amb = np.abs(u - prob) < margin
+    # FP32 P_s is within ~2e-6 of the FP64 value (P_L <= 1) and the patch sum
+    # within 64 times that; propagate through the ratio
+    err = sig * 64.0 / Sf * (2e-6 + 128e-6 * ps / Sf) + 2e-6
+    amb = np.abs(u - prob) < err
     idx = np.nonzero(spawn)[0]
     zi = z[idx]
     pc = np.stack([(x[idx] + 0.5 - cam["cx"]) * zi / cam["fx"], (y[idx] + 0.5 - cam["cy"]) * zi / cam["fy"], zi], 1)
@@ -194,4 +212,4 @@ def spawn_learned(image, mlp_out, cam, seed, frame, margin=1e-6, depth=None):
     c0 = 0.5 / math.sqrt(math.pi)
     rgb = image.reshape(3, -1)[:, idx].T
     return dict(pixel=idx, mean=mu, log_scale=np.repeat(out[m[idx], 2][:, None], 3, 1), sh_dc=(rgb - 0.5) / c0,
-                amb=amb)
+                amb=amb, prob=prob)

@@ -115,46 +115,76 @@ def _pin_cam(W, H):
     return synth.camera(R, t, 50.0, W, H, dtype=np.float64)
 
 
-def test_spawn_learned_certain_and_impossible_spawns():
-    """logit +40: every pixel with a positive depth spawns; logit -40: none.
-    Means reproject to their pixel centres at the chosen depth (projection
-    written here independently); the depth map wins where valid; SH DC gives
-    back the pixel colour."""
+def _textured(rng, W, H):
+    """An image with detail everywhere (sum of random sinusoids + noise), so
+    every 8x8 patch has a positive LoG response."""
+    yy, xx = np.mgrid[0:H, 0:W]
+    img = np.zeros((3, H, W))
+    for c in range(3):
+        for _ in range(4):
+            f = rng.uniform(0.2, 1.2, 2)
+            img[c] += 0.1 * np.sin(f[0] * xx + f[1] * yy + rng.uniform(0, 6))
+    return np.clip(0.5 + img + rng.normal(0, 0.02, img.shape), 0, 1)
+
+
+def test_spawn_learned_expected_count_and_placement():
+    """Without saturation the probabilities of a patch sum to 64 sigmoid(logit)
+    (the predicted count) and are proportional to P_s (Eq. 3) inside the patch;
+    a render equal to the image (P_s = 0) spawns nothing; logit -40 spawns
+    nothing. Spawned means reproject to their pixel centres at the chosen depth
+    (projection written here independently), the depth map wins where valid,
+    and SH DC gives back the pixel colour."""
+    from oracle import oracle as O
     rng = np.random.default_rng(0)
-    W, H = 24, 16
+    W, H = 32, 24
     n_p = (W // 8) * (H // 8)
     cam = _pin_cam(W, H)
-    image = rng.random((3, H, W))
-    out = np.stack([np.full(n_p, 40.0), rng.uniform(1, 9, n_p), np.full(n_p, -4.0)], 1)
+    image = _textured(rng, W, H)
+    out = np.stack([rng.uniform(-4, -2, n_p), rng.uniform(1, 9, n_p), np.full(n_p, -4.0)], 1)
     out[1, 1] = -2.0  # a patch with a negative predicted depth
     depth = rng.uniform(2, 12, (H, W))
     depth[rng.random((H, W)) < 0.3] = 0.0  # holes fall back to the prediction
+    ps = O.spawn_maps(image, None, 1.0, 5, 3)["p_s"]
     for dmap in (None, depth):
         r = M.spawn_learned(image, out, cam, 5, 3, depth=dmap)
+        prob = r["prob"].reshape(H // 8, 8, W // 8, 8).transpose(0, 2, 1, 3).reshape(n_p, 64)
+        psp = ps.reshape(H // 8, 8, W // 8, 8).transpose(0, 2, 1, 3).reshape(n_p, 64)
+        sig = 1 / (1 + np.exp(-out[:, 0]))
+        assert (psp.sum(1) > M.PATCH_FLOOR).all() and (prob < 1).all()
+        np.testing.assert_allclose(prob.sum(1), 64 * sig, rtol=1e-12)
+        np.testing.assert_allclose(prob / psp, np.repeat((prob.sum(1) / psp.sum(1))[:, None], 64, 1), rtol=1e-12)
         p = np.arange(W * H)
         x, y = p % W, p // W
         m = (y // 8) * (W // 8) + x // 8
         z = out[m, 1] if dmap is None else np.where(depth.reshape(-1) > 0, depth.reshape(-1), out[m, 1])
-        np.testing.assert_array_equal(r["pixel"], p[z > 0])
+        u = O.philox_uniforms(W * H, 3, 1, 5)
+        want = p[(u < r["prob"]) & (z > 0)]
+        np.testing.assert_array_equal(r["pixel"], want)
+        zi = z[want]
         q = r["mean"] @ np.asarray(cam["R"]).T + np.asarray(cam["t"])
-        np.testing.assert_allclose(q[:, 2], z[z > 0], rtol=1e-12)
-        np.testing.assert_allclose(cam["fx"] * q[:, 0] / q[:, 2] + cam["cx"], x[z > 0] + 0.5, atol=1e-9)
-        np.testing.assert_allclose(cam["fy"] * q[:, 1] / q[:, 2] + cam["cy"], y[z > 0] + 0.5, atol=1e-9)
-        np.testing.assert_allclose(r["sh_dc"] * (0.5 / math.sqrt(math.pi)) + 0.5, image.reshape(3, -1)[:, z > 0].T,
+        np.testing.assert_allclose(q[:, 2], zi, rtol=1e-12)
+        np.testing.assert_allclose(cam["fx"] * q[:, 0] / q[:, 2] + cam["cx"], x[want] + 0.5, atol=1e-9)
+        np.testing.assert_allclose(cam["fy"] * q[:, 1] / q[:, 2] + cam["cy"], y[want] + 0.5, atol=1e-9)
+        np.testing.assert_allclose(r["sh_dc"] * (0.5 / math.sqrt(math.pi)) + 0.5, image.reshape(3, -1)[:, want].T,
                                    atol=1e-12)
-        np.testing.assert_array_equal(r["log_scale"], np.full((int((z > 0).sum()), 3), -4.0))
+        np.testing.assert_array_equal(r["log_scale"], np.full((want.size, 3), -4.0))
+    assert M.spawn_learned(image, out, cam, 5, 3, render=image)["pixel"].size == 0
     out[:, 0] = -40.0
     assert M.spawn_learned(image, out, cam, 5, 3)["pixel"].size == 0
 
 
-def test_spawn_learned_rate_follows_the_logit():
-    """Logit 0 and log 3: spawn fractions 1/2 and 3/4 within 4 sigma over
-    64k pixels (independent Philox draws per pixel)."""
+def test_spawn_learned_count_follows_the_logit():
+    """Over a 256x256 textured frame the number of spawns matches the sum of
+    the probabilities (= 64 sigmoid(logit) per unsaturated patch) within 4
+    standard deviations of the Poisson-binomial count."""
+    rng = np.random.default_rng(1)
     W, H = 256, 256
     cam = _pin_cam(W, H)
     n_p = (W // 8) * (H // 8)
-    image = np.zeros((3, H, W))
-    for logit, want in ((0.0, 0.5), (math.log(3.0), 0.75)):
+    image = _textured(rng, W, H)
+    for logit in (-3.0, -2.0):
         out = np.stack([np.full(n_p, logit), np.full(n_p, 5.0), np.zeros(n_p)], 1)
-        frac = M.spawn_learned(image, out, cam, 11, 2)["pixel"].size / (W * H)
-        assert abs(frac - want) < 4 * math.sqrt(want * (1 - want) / (W * H)), (logit, frac)
+        r = M.spawn_learned(image, out, cam, 11, 2)
+        mean, var = r["prob"].sum(), (r["prob"] * (1 - r["prob"])).sum()
+        assert abs(r["pixel"].size - mean) < 4 * math.sqrt(var), (logit, r["pixel"].size, mean)
+        assert abs(mean - 64 * n_p / (1 + math.exp(-logit))) < 0.02 * mean
