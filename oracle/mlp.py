@@ -1,7 +1,7 @@
 """FP64 oracle of the learned spawn proposal: a per-patch MLP over 8x8 image
 patches (192 pixel values + 2 patch coordinates -> 3 x (Linear 128 + GELU) ->
-Linear 3: spawn logit, depth, log-scale), its loss against the spawns that
-plain direct sampling (Sec. 4.2) produced and kept, the backward pass and
+Linear 3: spawn logit, depth, log-scale offset), its loss against the spawns
+that plain direct sampling (Sec. 4.2) produced and kept, the backward pass and
 Adam.
 
 TEST INFRASTRUCTURE ONLY (tests, smoke check, benchmark CPU baseline).
@@ -141,8 +141,10 @@ def zeros_like_params(params):
 # ---------------------------------------------------------------------------
 
 def targets_from_spawns(pixel, depth, log_scale, kept, W, H):
-    """Per 8x8 patch: (kept count / 64, mean depth, mean log-scale, any kept)
-    over the spawned Gaussians that were kept after the frame's optimisation."""
+    """Per 8x8 patch: (kept count / 64, mean depth, mean log_scale value, any
+    kept) over the spawned Gaussians that were kept after the frame's
+    optimisation (log_scale: whatever per-spawn scale quantity the network is
+    to predict, e.g. the change the optimisation made to the log-scale)."""
     nx, ny = W // PATCH, H // PATCH
     out = np.zeros((nx * ny, 4))
     pixel = np.asarray(pixel)
@@ -173,9 +175,10 @@ def spawn_learned(image, mlp_out, cam, seed, frame, depth=None, render=None, sig
     counter (p, frame, 1, 0); the pixel spawns iff u < probability and its depth
     is positive. The depth is the map's value where a map is given and that
     value is positive and finite, else the patch's predicted depth. The
-    Gaussian sits at the pixel centre at that depth, with the patch's predicted
-    log-scale on all axes, identity rotation, opacity 0.5 and the pixel colour
-    as SH DC. Returns the spawns in pixel order and, as `amb`, the pixels whose
+    Gaussian sits at the pixel centre at that depth z with, on all axes, direct
+    sampling's log-scale log(z / (2 fx sqrt(P_L(p)))) plus the patch's predicted
+    log-scale offset, identity rotation, opacity 0.5 and the pixel colour as SH
+    DC. Returns the spawns in pixel order and, as `amb`, the pixels whose
     decision an FP32 evaluation may take the other way (|u - probability|
     within a bound of the FP32 errors of P_s and of the patch sum)."""
     from . import oracle as O
@@ -211,5 +214,7 @@ def spawn_learned(image, mlp_out, cam, seed, frame, depth=None, render=None, sig
     mu = (pc - t) @ R
     c0 = 0.5 / math.sqrt(math.pi)
     rgb = image.reshape(3, -1)[:, idx].T
-    return dict(pixel=idx, mean=mu, log_scale=np.repeat(out[m[idx], 2][:, None], 3, 1), sh_dc=(rgb - 0.5) / c0,
-                amb=amb, prob=prob)
+    pl = maps["p_l"].reshape(-1)[idx]
+    ls = np.log(zi / (2.0 * np.sqrt(pl)) / cam["fx"]) + out[m[idx], 2]
+    return dict(pixel=idx, mean=mu, log_scale=np.repeat(ls[:, None], 3, 1), sh_dc=(rgb - 0.5) / c0, amb=amb,
+                prob=prob)

@@ -141,7 +141,7 @@ def test_spawn_learned_expected_count_and_placement():
     cam = _pin_cam(W, H)
     image = _textured(rng, W, H)
     out = np.stack([rng.uniform(-4, -2, n_p), rng.uniform(1, 9, n_p), np.full(n_p, -4.0)], 1)
-    out[1, 1] = -2.0  # a patch with a negative predicted depth
+    out[1, 1] = -2.0  # a patch with a negative predicted depth (log-scale offset -4 everywhere)
     depth = rng.uniform(2, 12, (H, W))
     depth[rng.random((H, W)) < 0.3] = 0.0  # holes fall back to the prediction
     ps = O.spawn_maps(image, None, 1.0, 5, 3)["p_s"]
@@ -167,7 +167,16 @@ def test_spawn_learned_expected_count_and_placement():
         np.testing.assert_allclose(cam["fy"] * q[:, 1] / q[:, 2] + cam["cy"], y[want] + 0.5, atol=1e-9)
         np.testing.assert_allclose(r["sh_dc"] * (0.5 / math.sqrt(math.pi)) + 0.5, image.reshape(3, -1)[:, want].T,
                                    atol=1e-12)
-        np.testing.assert_array_equal(r["log_scale"], np.full((want.size, 3), -4.0))
+        # direct sampling's scale at the same pixel and depth (the plain oracle, whose draws
+        # differ: pool its spawns over several frames), times exp(offset)
+        plain_ls = {}
+        for fr in range(12):
+            pl = O.spawn(image, None, z.reshape(H, W), cam, 1.0, 5, fr)
+            plain_ls.update(zip(pl["pixel"].tolist(), pl["log_scale"][:, 0].tolist()))
+        both = [i for i, px in enumerate(want.tolist()) if px in plain_ls]
+        assert len(both) > 0.5 * want.size
+        np.testing.assert_allclose(r["log_scale"][both, 0], np.array([plain_ls[want[i]] for i in both]) - 4.0,
+                                   rtol=1e-12)
     assert M.spawn_learned(image, out, cam, 5, 3, render=image)["pixel"].size == 0
     out[:, 0] = -40.0
     assert M.spawn_learned(image, out, cam, 5, 3)["pixel"].size == 0
