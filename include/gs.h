@@ -340,6 +340,8 @@ int gs_spawn_propose_noalloc(const float* image, const float* render, const floa
  * row-major, and the patch centre in [-1, 1]^2) -> 3 x (Linear 128 + GELU) ->
  * Linear 3 = (spawn logit, depth, log-scale). Weights and activations are
  * bfloat16 in the matrix products, accumulation and everything else FP32.
+ * The log-scale output is an offset to direct sampling's scale (see
+ * gs_spawn_learned).
  * Parameters (device, FP32 masters, nn.Linear layout): w1 [128][194], b1 [128],
  * w2 [128][128], b2, w3 [128][128], b3, w4 [3][128], b4 [3]. */
 typedef struct gs_mlp_params {
@@ -384,26 +386,34 @@ int gs_mlp_gemm_bf16(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t 
                      int32_t M, int32_t N, int32_t K, int32_t tensor_path, void* stream);
 
 /* Training targets of the learned proposal from direct sampling: for spawned
- * Gaussians i (pixel index, camera depth, log-scale) with kept[i] != 0 (still
- * present after the frame's optimisation), targets [n_patches][4] = (kept
- * count / 64, their mean depth, mean log-scale, 1 if any kept else 0) per 8x8
- * patch. ws: gs_mlp_targets_workspace_size bytes. */
+ * Gaussians i (pixel index, camera depth, log-scale value) with kept[i] != 0
+ * (still present after the frame's optimisation), targets [n_patches][4] =
+ * (kept count / 64, their mean depth, mean log-scale value, 1 if any kept
+ * else 0) per 8x8 patch. The log-scale value is the quantity the network's
+ * third output learns: the offset to direct sampling's log-scale, e.g. the
+ * change the optimisation made to it. ws: gs_mlp_targets_workspace_size bytes. */
 size_t gs_mlp_targets_workspace_size(int32_t width, int32_t height);
 int gs_mlp_targets(const int32_t* pixel, const float* depth, const float* log_scale, const uint8_t* kept,
                    int64_t n_spawn, int32_t width, int32_t height, float* targets, void* ws, size_t ws_bytes,
                    void* stream);
 
-/* Spawning from the learned proposal's outputs mlp_out [n_patches][3]: pixel p
- * of patch m spawns iff u < sigmoid(logit_m) (u = Philox4x32-10 of counter
- * (p, frame, 1, 0) and key seed) and its depth is positive. The depth is
- * depth[p] (the per-pixel map gs_spawn_propose takes; may be NULL) where that
- * is positive and finite, else the patch's predicted depth. The new Gaussian
- * sits at the pixel centre at that depth with the patch's predicted log-scale
- * on all axes (other attributes as gs_spawn_propose). Output, workspace size
- * and status as for gs_spawn_propose. */
-int gs_spawn_learned(const float* image, const float* mlp_out, const float* depth, int32_t width, int32_t height,
-                     const gs_camera* cam, const gs_spawn_config* sc, const gs_spawn_out* out, void* ws,
-                     size_t ws_bytes, void* stream);
+/* Spawning from the learned proposal's outputs mlp_out [n_patches][3]: the
+ * network gives each 8x8 patch m its expected number of kept spawns
+ * 64 sigmoid(logit_m); they are placed where direct sampling would place them.
+ * Pixel p spawns iff u < min(1, sigmoid(logit_m) 64 P_s(p) / S_m) and its
+ * depth is positive, with P_s the spawn probability of Eq. 1-3 (render
+ * penalty included; render may be NULL), S_m = max(sum of P_s over the patch,
+ * 0.064) and u = Philox4x32-10 of counter (p, frame, 1, 0) and key seed
+ * (LoG sigma from sc). The depth is depth[p] (the per-pixel map
+ * gs_spawn_propose takes; may be NULL) where that is positive and finite,
+ * else the patch's predicted depth. The new Gaussian sits at the pixel
+ * centre at that depth z with, on all axes, direct sampling's log-scale
+ * log(z / (2 fx sqrt(P_L(p)))) plus the patch's predicted log-scale offset
+ * (other attributes as gs_spawn_propose). Output (p_l, p_pen, p_s maps
+ * optional), workspace size and status as for gs_spawn_propose. */
+int gs_spawn_learned(const float* image, const float* mlp_out, const float* render, const float* depth,
+                     int32_t width, int32_t height, const gs_camera* cam, const gs_spawn_config* sc,
+                     const gs_spawn_out* out, void* ws, size_t ws_bytes, void* stream);
 
 /* Error code recorded by a tensor-memory GEMM whose completion wait timed out
  * (0 = none). Synchronous; for tests. */

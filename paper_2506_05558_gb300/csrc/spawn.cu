@@ -83,10 +83,12 @@ __global__ void __launch_bounds__(256) k_spawn_maps(const float* __restrict__ im
     const float pl = log_norm(s_tile, taps, lx, ly);
     const float pp = render ? log_norm(s_tile + 3 * S * S, taps, lx, ly) : 0.f;
     const float ps = fmaxf(pl - pp, 0.f);
-    const uint4 r = philox4x32_10(make_uint4((uint32_t)p, frame, 0u, 0u), key);
-    const float u = (float)(r.x >> 8) * (1.f / 16777216.f);
-    const float z = depth[p];
-    flag[p] = (u < ps && z > 0.f && isfinite(z)) ? 1u : 0u;
+    if (flag) {  // the direct-sampling mask (the learned proposal only needs the maps)
+        const uint4 r = philox4x32_10(make_uint4((uint32_t)p, frame, 0u, 0u), key);
+        const float u = (float)(r.x >> 8) * (1.f / 16777216.f);
+        const float z = depth[p];
+        flag[p] = (u < ps && z > 0.f && isfinite(z)) ? 1u : 0u;
+    }
     if (p_l) p_l[p] = pl;
     if (p_pen) p_pen[p] = pp;
     if (p_s) p_s[p] = ps;
@@ -170,6 +172,9 @@ extern "C" size_t gs_spawn_workspace_size(int32_t width, int32_t height) {
     c.take<uint32_t>(hw);
     c.take<uint32_t>(4);
     c.take<char>(scan_workspace_bytes(hw));
+    c.take<float>(hw);       // gs_spawn_learned: P_s
+    c.take<float>(hw / 64);  // gs_spawn_learned: patch sums
+    c.take<float>(hw);       // gs_spawn_learned: P_L
     return c.used;
 }
 
@@ -332,8 +337,6 @@ __global__ void k_patch_targets(const float4* __restrict__ pix_slot, int W, int 
     targets[m * 4 + 3] = cnt > 0.f ? 1.f : 0.f;
 }
 
-// Spawn flags from the MLP: pixel p of patch m spawns iff u < sigmoid(logit_m)
-// and the predicted depth is positive; u = Philox(counter (p, frame, 1, 0)).
 // Depth of a learned spawn at pixel p: the depth map's value where it is
 // positive and finite, else the patch's predicted depth.
 __device__ __forceinline__ float learned_depth(const float* __restrict__ depth, const float* __restrict__ mlp_out,
@@ -342,21 +345,43 @@ __device__ __forceinline__ float learned_depth(const float* __restrict__ depth, 
     return (d > 0.f && isfinite(d)) ? d : mlp_out[m * 3 + 1];
 }
 
-__global__ void k_learned_flags(const float* __restrict__ mlp_out, const float* __restrict__ depth, int W, int H,
+// Lower bound of a patch's P_s sum in the placement ratio (keeps the ratio
+// well conditioned where the render already explains the patch).
+constexpr float kPatchFloor = 64.f * 1e-3f;
+
+// One thread per 8x8 patch: sum of P_s in row-major order, floored.
+__global__ void k_patch_ps_sum(const float* __restrict__ ps, int W, int H, float* __restrict__ sums) {
+    const int nx = W / 8, ny = H / 8;
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= (int64_t)nx * ny) return;
+    const int px = (int)(m % nx), py = (int)(m / nx);
+    float a = 0.f;
+    for (int dy = 0; dy < 8; dy++)
+        for (int dx = 0; dx < 8; dx++) a += ps[(int64_t)(py * 8 + dy) * W + px * 8 + dx];
+    sums[m] = fmaxf(a, kPatchFloor);
+}
+
+// Spawn flags from the MLP: pixel p of patch m spawns with probability
+// min(1, sigmoid(logit_m) 64 P_s(p) / patch sum) (the predicted count placed
+// where direct sampling would place it) and a positive depth; the draw is
+// Philox(counter (p, frame, 1, 0)).
+__global__ void k_learned_flags(const float* __restrict__ mlp_out, const float* __restrict__ depth,
+                                const float* __restrict__ ps, const float* __restrict__ sums, int W, int H,
                                 uint2 key, uint32_t frame, uint32_t* __restrict__ flag) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= (int64_t)W * H) return;
     const int x = (int)(p % W), y = (int)(p / W);
     const int64_t m = (int64_t)(y / 8) * (W / 8) + x / 8;
     const float logit = mlp_out[m * 3 + 0], z = learned_depth(depth, mlp_out, p, m);
-    const float prob = 1.f / (1.f + expf(-logit));
+    const float sig = 1.f / (1.f + expf(-logit));
+    const float prob = fminf(1.f, sig * 64.f * ps[p] / sums[m]);
     const uint4 r = philox4x32_10(make_uint4((uint32_t)p, frame, 1u, 0u), key);
     const float u = (float)(r.x >> 8) * (1.f / 16777216.f);
     flag[p] = (u < prob && z > 0.f && isfinite(z)) ? 1u : 0u;
 }
 
 __global__ void k_learned_emit(const float* __restrict__ image, const float* __restrict__ mlp_out,
-                               const float* __restrict__ depth, int W, int H,
+                               const float* __restrict__ depth, const float* __restrict__ p_l, int W, int H,
                                const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
                                const gs_camera* __restrict__ cam, int64_t capacity, float4* __restrict__ mean_opa,
                                float4* __restrict__ scale, float4* __restrict__ quat, float4* __restrict__ sh,
@@ -367,7 +392,9 @@ __global__ void k_learned_emit(const float* __restrict__ image, const float* __r
     if (o >= capacity) return;
     const int x = (int)(p % W), y = (int)(p / W);
     const int64_t m = (int64_t)(y / 8) * (W / 8) + x / 8;
-    const float z = learned_depth(depth, mlp_out, p, m), ls = mlp_out[m * 3 + 2];
+    const float z = learned_depth(depth, mlp_out, p, m);
+    // direct sampling's scale z / (2 fx sqrt(P_L)) times the patch's predicted factor exp(offset)
+    const float ls = logf(z * (0.5f / sqrtf(p_l[p])) / cam->fx) + mlp_out[m * 3 + 2];
     const gs_camera& c = *cam;
     const float xc = (x + 0.5f - c.cx) * z / c.fx, yc = (y + 0.5f - c.cy) * z / c.fy;
     const float qx = xc - c.t[0], qy = yc - c.t[1], qz = z - c.t[2];
@@ -416,32 +443,49 @@ extern "C" int gs_mlp_targets(const int32_t* pixel, const float* depth, const fl
     return GS_OK;
 }
 
-extern "C" int gs_spawn_learned(const float* image, const float* mlp_out, const float* depth, int32_t width,
-                                int32_t height,
-                                const gs_camera* cam, const gs_spawn_config* sc, const gs_spawn_out* out, void* ws,
-                                size_t ws_bytes, void* stream) {
+extern "C" int gs_spawn_learned(const float* image, const float* mlp_out, const float* render, const float* depth,
+                                int32_t width, int32_t height, const gs_camera* cam, const gs_spawn_config* sc,
+                                const gs_spawn_out* out, void* ws, size_t ws_bytes, void* stream) {
     if (!image || !mlp_out || !cam || !sc || !out || width <= 0 || height <= 0 || width % 8 || height % 8)
         return GS_ERR_INVALID_ARG;
     if (!out->count || !out->status || out->capacity < 0 ||
         (out->capacity > 0 && (!out->mean_opa || !out->scale || !out->quat || !out->sh)))
         return GS_ERR_INVALID_ARG;
     const int64_t hw = (int64_t)width * height;
+    if (hw > (int64_t)UINT32_MAX) return GS_ERR_INVALID_ARG;
+    LogTaps taps;
+    if (!make_taps(sc->sigma, &taps)) return GS_ERR_INVALID_ARG;
     Carve c{(char*)ws, 0, ws_bytes};
     uint32_t* flag = c.take<uint32_t>(hw);
     uint32_t* pos = c.take<uint32_t>(hw);
     uint32_t* total = c.take<uint32_t>(4);
     void* scan_ws = c.take<char>(scan_workspace_bytes(hw));
+    float* ps = c.take<float>(hw);
+    float* sums = c.take<float>(hw / 64);
+    float* pl = c.take<float>(hw);
     if (!ws || !c.ok() || ((uintptr_t)ws & 255)) return GS_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const uint2 key = make_uint2((uint32_t)sc->seed, (uint32_t)(sc->seed >> 32));
-    k_learned_flags<<<(unsigned)ceil_div(hw, 256), 256, 0, s>>>(mlp_out, depth, width, height, key, sc->frame,
-                                                                 flag);
+    // P_s (Eq. 1-3) of the frame, then its patch sums
+    const int S = kSpT + 2 * taps.R;
+    const size_t smem = sizeof(float) * 3 * S * S * (render ? 2 : 1);
+    dim3 grid((unsigned)ceil_div(width, kSpT), (unsigned)ceil_div(height, kSpT));
+    float* psb = out->p_s ? out->p_s : ps;  // the caller's maps when it asks for them
+    float* plb = out->p_l ? out->p_l : pl;
+    k_spawn_maps<<<grid, 256, smem, s>>>(image, render, nullptr, width, height, taps, key, sc->frame, plb,
+                                          out->p_pen, psb, nullptr);
+    count_launch();
+    k_patch_ps_sum<<<(unsigned)ceil_div(hw / 64, 256), 256, 0, s>>>(psb, width, height, sums);
+    count_launch();
+    k_learned_flags<<<(unsigned)ceil_div(hw, 256), 256, 0, s>>>(mlp_out, depth, psb, sums, width, height, key,
+                                                                 sc->frame, flag);
     count_launch();
     scan_exclusive_u32(flag, pos, hw, total, scan_ws, s);
     k_spawn_count<<<1, 1, 0, s>>>(total, out->capacity, out->count, out->status);
     count_launch();
     if (out->capacity > 0) {
-        k_learned_emit<<<(unsigned)ceil_div(hw, 256), 256, 0, s>>>(image, mlp_out, depth, width, height, flag, pos, cam,
+        k_learned_emit<<<(unsigned)ceil_div(hw, 256), 256, 0, s>>>(image, mlp_out, depth, plb, width, height, flag,
+                                                                    pos, cam,
                                                                     out->capacity, (float4*)out->mean_opa,
                                                                     (float4*)out->scale, (float4*)out->quat,
                                                                     (float4*)out->sh, out->pixel);

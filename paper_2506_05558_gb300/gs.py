@@ -161,7 +161,7 @@ def lib():
             "gs_mlp_tc_error": (C.c_int, [C.POINTER(C.c_int32)]),
             "gs_mlp_targets_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
             "gs_mlp_targets": (C.c_int, [P, P, P, P, C.c_int64, C.c_int32, C.c_int32, P, P, C.c_size_t, P]),
-            "gs_spawn_learned": (C.c_int, [P, P, P, C.c_int32, C.c_int32, P, C.POINTER(gs_spawn_config),
+            "gs_spawn_learned": (C.c_int, [P, P, P, P, C.c_int32, C.c_int32, P, C.POINTER(gs_spawn_config),
                                            C.POINTER(gs_spawn_out), P, C.c_size_t, P]),
             "gs_anchor_offload": (C.c_int, [C.POINTER(gs_gaussians)] * 6 + [P]),
             "gs_anchor_load": (C.c_int, [C.POINTER(gs_gaussians)] * 6 + [P]),
@@ -580,11 +580,13 @@ def gs_mlp_targets_workspace_size(width: int, height: int) -> int:
 
 
 def gs_spawn_learned(image: torch.Tensor, mlp_out: torch.Tensor, width: int, height: int, cam: torch.Tensor,
-                     seed: int, frame: int, out: Spawned, ws: torch.Tensor, capacity=None, stream=None, depth=None):
-    sc = gs_spawn_config(1.0, frame, seed)
+                     seed: int, frame: int, out: Spawned, ws: torch.Tensor, capacity=None, stream=None, depth=None,
+                     render=None, sigma: float = 1.0):
+    sc = gs_spawn_config(sigma, frame, seed)
     oc = out.c(out.g.n if capacity is None else capacity)
-    _check(lib().gs_spawn_learned(_ptr(image), _ptr(mlp_out), _ptr(depth), width, height, _ptr(cam), C.byref(sc),
-                                  C.byref(oc), _ptr(ws), ws.numel(), _stream(stream)), "gs_spawn_learned")
+    _check(lib().gs_spawn_learned(_ptr(image), _ptr(mlp_out), _ptr(render), _ptr(depth), width, height, _ptr(cam),
+                                  C.byref(sc), C.byref(oc), _ptr(ws), ws.numel(), _stream(stream)),
+           "gs_spawn_learned")
 
 
 def adam_config(lr_mean=1.6e-4, lr_opacity=0.05, lr_scale=5e-3, lr_rot=1e-3, lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4,

@@ -129,7 +129,7 @@ class OnTheFly:
         if use_learned:
             gs.gs_mlp_forward(self.mlp, image, self.W, self.H, self.mlp_out, self.mlp_cfg, self.ws_mlp)
             gs.gs_spawn_learned(image, self.mlp_out, self.W, self.H, cam, self.seed, frame_idx, self.spawned,
-                                self.ws_spawn, depth=depth)
+                                self.ws_spawn, depth=depth, render=render)
         else:
             gs.gs_spawn_propose(image, render, depth, self.W, self.H, cam, 1.0, self.seed, frame_idx, self.spawned,
                                 self.ws_spawn)
@@ -161,9 +161,9 @@ class OnTheFly:
 
     def _train_mlp(self, image, n0, k, cam):
         """Targets from this frame's spawns that are still opaque after the
-        optimisation: their optimised camera depth and mean log-scale, so the
-        network learns where spawns survive and what they converge to; then a
-        few training steps of the proposal network."""
+        optimisation: their optimised camera depth and the change of their mean
+        log-scale, so the network learns where spawns survive and how their
+        scale converges; then a few training steps of the proposal network."""
         if k == 0:
             return None
         g, _, _ = self.store.active()
@@ -174,7 +174,8 @@ class OnTheFly:
         R = torch.tensor(c["R"], dtype=torch.float32, device=self.device)
         t = torch.tensor(c["t"], dtype=torch.float32, device=self.device)
         z = (g.mean_opa[n0:n0 + k, :3] @ R[2] + t[2]).contiguous()
-        ls = g.scale[n0:n0 + k, :3].mean(1).contiguous()
+        # the network predicts the change the optimisation made to the spawn's log-scale
+        ls = (g.scale[n0:n0 + k, :3].mean(1) - self.spawned.g.scale[:k, 0]).contiguous()
         gs.gs_mlp_targets(pix, z, ls, kept, k, self.W, self.H, self.mlp_targets, self.ws_tg)
         for _ in range(self.mlp_steps):
             self.mlp_step += 1

@@ -157,17 +157,22 @@ def test_targets_from_kept_spawns_match_oracle():
     assert_close(tg.cpu().numpy(), ref, 1e-6, what="targets")
 
 
-@pytest.mark.parametrize("with_depth", [False, True])
-def test_learned_spawn_matches_oracle(with_depth):
-    """Spawns from the network's outputs; with a depth map (holes: zero,
-    negative, NaN) its values replace the predicted depth where valid."""
+@pytest.mark.parametrize("with_depth,with_render", [(False, False), (True, False), (True, True)])
+def test_learned_spawn_matches_oracle(with_depth, with_render):
+    """Spawns from the network's outputs placed by P_s; with a depth map (holes:
+    zero, negative, NaN) its values replace the predicted depth where valid;
+    with a render the penalty of Eq. 2 enters P_s."""
     from paper_2506_05558_gb300 import synth
     from oracle import oracle as O
     rng = np.random.default_rng(6)
     W, H = 160, 96
     n_p = (W // 8) * (H // 8)
-    out = np.stack([rng.normal(-1, 1.5, n_p), rng.uniform(-1, 15, n_p), rng.normal(-4, 0.5, n_p)], 1).astype(np.float32)
+    out = np.stack([rng.normal(-2, 1.5, n_p), rng.uniform(-1, 15, n_p), rng.normal(-4, 0.5, n_p)], 1).astype(np.float32)
     image = rng.random((3, H, W)).astype(np.float32)
+    render = None
+    if with_render:
+        render = np.clip(image + rng.normal(0, 0.05, image.shape), 0, 1).astype(np.float32)
+        render[:, :, :40] = image[:, :, :40]  # a fully explained strip: P_s = 0 there
     depth = None
     if with_depth:
         depth = rng.uniform(1, 20, (H, W)).astype(np.float32)
@@ -179,13 +184,16 @@ def test_learned_spawn_matches_oracle(with_depth):
     cam = synth.camera(R.astype(np.float32), t.astype(np.float32), 120.0, W, H)
     sp = gs.Spawned.alloc(W * H)
     ws = gs.workspace(gs.gs_spawn_workspace_size(W, H))
-    gs.gs_spawn_learned(torch.from_numpy(image).cuda(), torch.from_numpy(out).cuda(), W, H, gs.cameras_tensor([cam]),
-                        99, 7, sp, ws, depth=None if depth is None else torch.from_numpy(depth).cuda())
+    dev = lambda a: None if a is None else torch.from_numpy(a).cuda()
+    gs.gs_spawn_learned(dev(image), dev(out), W, H, gs.cameras_tensor([cam]), 99, 7, sp, ws, depth=dev(depth),
+                        render=dev(render))
     torch.cuda.synchronize()
-    ref = OM.spawn_learned(image, out, cam, 99, 7, depth=depth)
+    ref = OM.spawn_learned(image, out, cam, 99, 7, depth=depth, render=render)
     k = int(sp.count.item())
+    assert k > 100
     pix = sp.pixel[:k].cpu().numpy()
     amb = set(np.nonzero(ref["amb"])[0].tolist())
+    assert len(amb) <= 0.01 * W * H
     assert (set(pix.tolist()) ^ set(ref["pixel"].tolist())) <= amb
     common = np.array(sorted(set(pix.tolist()) & set(ref["pixel"].tolist())))
     gi, oi = np.searchsorted(pix, common), np.searchsorted(ref["pixel"], common)
