@@ -149,6 +149,17 @@ def render_fwd(proj, start, ids, cam, cfg: Config) -> dict:
     return out
 
 
+def render_depth(proj, start, ids, cam, cfg: Config) -> np.ndarray:
+    """Depth integral per pixel, sum_i alpha_i T_i z_i over the composited
+    Gaussians (expected depth times 1 - T_final): the compositing of render_fwd
+    with every Gaussian's colour replaced by its camera depth and a black
+    background (the weights alpha_i T_i do not depend on the colours)."""
+    import dataclasses
+    p2 = dict(proj)
+    p2["rgb"] = np.repeat(np.asarray(proj["depth"], np.float64)[:, None], 3, 1)
+    return render_fwd(p2, start, ids, cam, dataclasses.replace(cfg, bg=(0.0, 0.0, 0.0)))["color"][0]
+
+
 def render_bwd(proj, start, ids, cam, cfg: Config, dL_dcolor, with_amb=False, amb_pixels=None):
     """Returns g2d [n, 9] = dL/d(u, v, conic a, b, c, opacity, r, g, b); with
     with_amb also the [n, 9] bound on contributions from ambiguous pixels

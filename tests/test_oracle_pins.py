@@ -496,3 +496,26 @@ def test_pose_tangent_gradient_matches_central_differences():
     np.testing.assert_allclose(an, fd, rtol=1e-5, atol=1e-6 * np.abs(fd).max())
     # the plain gradient (J_l dropped) is measurably different at this xi
     assert np.abs(g["pose"] - fd).max() > 1e-3 * np.abs(fd).max()
+
+
+def test_depth_integral_closed_forms():
+    """Depth integral sum_i alpha_i T_i z_i: one Gaussian at a pixel centre
+    gives o z; two on the same pixel give o1 z1 + (1 - o1) o2 z2 in either
+    input order; a background colour does not enter it; away from all splats 0."""
+    cam = _cam_px()
+    o = 0.7
+    sc = one_gaussian(_at_pixel(cam, 10, 12, 3.0), np.log([0.05] * 3), [1, 0, 0, 0], math.log(o / (1 - o)))
+    cfg = O.Config(sh_degree=0, bg=(0.3, 0.3, 0.3))
+    v = O.render_view(sc, cam, cfg)
+    d = O.render_depth(v["proj"], v["start"], v["ids"], cam, cfg)
+    assert abs(d[12, 10] - o * 3.0) < 1e-12
+    assert d[0, 0] == 0.0
+    o1, o2 = 1 / (1 + math.exp(-0.4)), 1 / (1 + math.exp(0.2))
+    near, far = (_at_pixel(cam, 7, 9, 2.0), 0.4), (_at_pixel(cam, 7, 9, 5.0), -0.2)
+    for order in ((near, far), (far, near)):
+        mo = np.array([[*g[0], g[1]] for g in order])
+        sc2 = synth.Scene(mo, np.tile(np.log([0.05, 0.05, 0.05, 1.0]), (2, 1)), np.tile([1.0, 0, 0, 0], (2, 1)),
+                          np.zeros((2, 48)), 0)
+        v2 = O.render_view(sc2, cam, cfg)
+        d2 = O.render_depth(v2["proj"], v2["start"], v2["ids"], cam, cfg)
+        assert abs(d2[9, 7] - (o1 * 2.0 + (1 - o1) * o2 * 5.0)) < 1e-12
