@@ -384,6 +384,108 @@ def anchor_check(scene, cam, tau_px=1.0, share=0.4, margin=1e-5):
     return dict(size=size, too_fine=fine, count=int(fine.sum()), due=bool(fine.sum() > share * len(size)), amb=amb)
 
 
+def quat_to_rot(q):
+    """Rotation matrix of a (not necessarily unit) quaternion (w, x, y, z)."""
+    w, x, y, z = np.asarray(q, np.float64) / np.linalg.norm(q)
+    return np.array([[1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)],
+                     [2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)],
+                     [2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)]])
+
+
+def covariance(log_scale, quat):
+    """Sigma = R diag(exp(2 s)) R^T."""
+    R = quat_to_rot(quat)
+    return R @ np.diag(np.exp(2.0 * np.asarray(log_scale, np.float64)[:3])) @ R.T
+
+
+def merge_group(mean_opa, scale, quat, sh):
+    """Moment-matching merge of a group of Gaussians (rows of the inputs) into
+    one (Sec. 4.4, following the hierarchical merge): weights w_i = o_i a_i with
+    a_i the product of the two largest scales (the area of the Gaussian's
+    largest cross-section up to pi); mean and covariance are the w-weighted mean
+    and second moment about it, SH the w-weighted mean, and the opacity keeps
+    the total o a: o = min(0.99, sum_i w_i / a) with a the product of the merged
+    Gaussian's two largest scales. Returns (mean, covariance, opacity, sh)."""
+    mo = np.asarray(mean_opa, np.float64)
+    o = 1.0 / (1.0 + np.exp(-mo[:, 3]))
+    s = np.exp(np.asarray(scale, np.float64)[:, :3])
+    ss = np.sort(s, axis=1)
+    w = o * ss[:, 1] * ss[:, 2]
+    W = w.sum()
+    mu = (w[:, None] * mo[:, :3]).sum(0) / W
+    cov = np.zeros((3, 3))
+    for i in range(len(w)):
+        d = mo[i, :3] - mu
+        cov += w[i] * (covariance(scale[i], quat[i]) + np.outer(d, d))
+    cov /= W
+    lam = np.sort(np.linalg.eigvalsh(cov))
+    a = math.sqrt(lam[1] * lam[2])
+    return mu, cov, min(0.99, W / a), (w[:, None] * np.asarray(sh, np.float64)).sum(0) / W
+
+
+def anchor_merge(scene, too_fine, seed, radius, k=3, margin=1e-5):
+    """Merging at an anchor (Sec. 4.4). Gaussian i is selected iff it is too
+    fine and u_i < 1/(k+1), u_i the Philox draw of counter (i, 0, 2, 0). Every
+    selected Gaussian proposes the k nearest (Euclidean distance of the means,
+    ties by index, at most `radius` away) too-fine Gaussians that are not
+    selected; a Gaussian proposed by several goes to the lowest selected index.
+    Each selected Gaussian and the candidates it claimed merge (merge_group);
+    claimed Gaussians leave the set; all others are kept unchanged. The output
+    keeps index order (a merged Gaussian takes its selected Gaussian's place).
+    Returns dict(kind = per output row 0 kept / 1 merged, src = input index,
+    mean, cov, opacity, sh for merged rows, selected, claim, amb = selected
+    Gaussians whose neighbour decision lies within margin (relative) of the
+    radius or of the k-th/(k+1)-th distance tie)."""
+    mo = np.asarray(scene.mean_opa, np.float64)
+    n = mo.shape[0]
+    fine = np.asarray(too_fine, bool)
+    u = philox_uniforms(n, 0, 2, seed)
+    sel = fine & (u < 1.0 / (k + 1))
+    cand = np.nonzero(fine & ~sel)[0]
+    claim = np.full(n, -1, np.int64)
+    props = {}
+    amb = np.zeros(n, bool)
+    P = mo[cand, :3]
+    for s_ in np.nonzero(sel)[0]:
+        d = np.sqrt(((P - mo[s_, :3]) ** 2).sum(1)) if cand.size else np.zeros(0)
+        inside = d <= radius
+        order = np.lexsort((cand[inside], d[inside]))
+        chosen = cand[inside][order][:k]
+        props[s_] = chosen
+        near = np.abs(d - radius) < margin * radius
+        ds = np.sort(d[inside])
+        if near.any() or (ds.size > k and ds[k] - ds[k - 1] < margin * max(ds[k], 1e-30)):
+            amb[s_] = True
+        for c in chosen:
+            if claim[c] < 0 or s_ < claim[c]:
+                claim[c] = s_
+    kind, src, means, covs, opas, shs = [], [], [], [], [], []
+    for i in range(n):
+        if claim[i] >= 0:
+            continue
+        src.append(i)
+        if sel[i]:
+            grp = [i] + [c for c in props[i] if claim[c] == i]
+            mu, cov, op, sh = merge_group(mo[grp], np.asarray(scene.scale)[grp], np.asarray(scene.quat)[grp],
+                                          np.asarray(scene.sh)[grp])
+            kind.append(1)
+            means.append(mu); covs.append(cov); opas.append(op); shs.append(sh)
+        else:
+            kind.append(0)
+            means.append(mo[i, :3]); covs.append(covariance(scene.scale[i], scene.quat[i]))
+            opas.append(1.0 / (1.0 + math.exp(-mo[i, 3]))); shs.append(np.asarray(scene.sh[i], np.float64))
+    return dict(kind=np.array(kind), src=np.array(src), mean=np.array(means).reshape(-1, 3),
+                cov=np.array(covs).reshape(-1, 3, 3), opacity=np.array(opas), sh=np.array(shs).reshape(-1, 48),
+                selected=sel, claim=claim, amb=amb)
+
+
+def anchor_blend_weight(d1, d2, overlap=0.1):
+    """Blending weight of the closest anchor (Sec. 4.4): r = d1 / d2 (d1 <= d2);
+    1 for r < 1 - o, else 1 - (r - (1 - o)) * 0.5 / o (0.5 at r = 1)."""
+    r = d1 / d2
+    return 1.0 if r < 1.0 - overlap else 1.0 - (r - (1.0 - overlap)) * 0.5 / overlap
+
+
 # ---------------------------------------------------------------------------
 # Loss, optimiser and pose update (FP64 NumPy)
 # ---------------------------------------------------------------------------

@@ -64,3 +64,102 @@ def test_anchor_check_and_offload_on_gpu():
     torch.cuda.synchronize()
     for a, b in zip((g.mean_opa, g.scale, g.quat, g.sh, m.sh), want):
         assert torch.equal(a.cpu(), b)
+
+
+# ---------------------------------------------------------------------------
+# Merging at an anchor and the blending weight (oracle pins, CPU)
+# ---------------------------------------------------------------------------
+
+def _rot_quat(rng):
+    q = rng.standard_normal(4)
+    return q / np.linalg.norm(q)
+
+
+def test_merge_group_single_and_duplicate():
+    rng = np.random.default_rng(2)
+    mo = np.array([[0.3, -1.0, 4.0, 0.2]])
+    sc = np.array([[-3.0, -2.5, -3.4, 0.0]])
+    q = np.array([_rot_quat(rng)])
+    sh = rng.standard_normal((1, 48))
+    mu, cov, op, shm = O.merge_group(mo, sc, q, sh)
+    o = 1 / (1 + math.exp(-0.2))
+    np.testing.assert_allclose(mu, mo[0, :3], rtol=1e-14)
+    np.testing.assert_allclose(cov, O.covariance(sc[0], q[0]), rtol=1e-12, atol=1e-18)
+    assert abs(op - o) < 1e-12
+    np.testing.assert_allclose(shm, sh[0], rtol=1e-14)
+    # two copies: same geometry and colour, opacity doubled (total o * area kept)
+    mu2, cov2, op2, _ = O.merge_group(np.repeat(mo, 2, 0), np.repeat(sc, 2, 0), np.repeat(q, 2, 0),
+                                      np.repeat(sh, 2, 0))
+    np.testing.assert_allclose(cov2, cov, rtol=1e-12, atol=1e-18)
+    assert abs(op2 - min(0.99, 2 * o)) < 1e-12
+
+
+def test_merge_group_symmetric_pair_closed_form():
+    """Two equal isotropic Gaussians at +-d on x: mean 0, covariance
+    sigma^2 I + diag(d^2, 0, 0)."""
+    sig, d = 0.05, 0.2
+    mo = np.array([[d, 0, 5, 0.0], [-d, 0, 5, 0.0]])
+    sc = np.log(np.array([[sig, sig, sig, 1.0]] * 2))
+    q = np.array([[1.0, 0, 0, 0]] * 2)
+    mu, cov, op, _ = O.merge_group(mo, sc, q, np.zeros((2, 48)))
+    np.testing.assert_allclose(mu, [0, 0, 5], atol=1e-15)
+    np.testing.assert_allclose(cov, np.diag([sig ** 2 + d ** 2, sig ** 2, sig ** 2]), rtol=1e-12)
+    # opacity keeps sum o a: 2 * 0.5 * sig^2 = o * sig * sqrt(sig^2 + d^2)
+    assert abs(op - min(0.99, sig / math.sqrt(sig ** 2 + d ** 2))) < 1e-12
+
+
+def test_merge_group_matches_the_mixture_moments():
+    """Monte Carlo: samples of the w-weighted mixture of the group's Gaussians
+    have the merged mean and covariance (law of total covariance)."""
+    rng = np.random.default_rng(3)
+    g = 4
+    mo = np.concatenate([rng.normal(0, 0.3, (g, 3)), rng.normal(0, 1, (g, 1))], 1)
+    sc = np.concatenate([rng.normal(-2.5, 0.4, (g, 3)), np.zeros((g, 1))], 1)
+    q = np.array([_rot_quat(rng) for _ in range(g)])
+    mu, cov, _, _ = O.merge_group(mo, sc, q, np.zeros((g, 48)))
+    o = 1 / (1 + np.exp(-mo[:, 3]))
+    ss = np.sort(np.exp(sc[:, :3]), 1)
+    w = o * ss[:, 1] * ss[:, 2]
+    counts = np.round(400_000 * w / w.sum()).astype(int)
+    pts = np.concatenate([rng.multivariate_normal(mo[i, :3], O.covariance(sc[i], q[i]), counts[i])
+                          for i in range(g)])
+    np.testing.assert_allclose(pts.mean(0), mu, atol=4e-3)
+    np.testing.assert_allclose(np.cov(pts.T), cov, atol=0.02 * np.abs(cov).max())
+
+
+def test_anchor_merge_neighbours_claims_and_counts():
+    """Proposals are the k nearest non-selected too-fine Gaussians within the
+    radius (checked with scipy's k-d tree); each claimed Gaussian goes to the
+    lowest selected index; the output drops exactly the claimed ones."""
+    spatial = pytest.importorskip("scipy.spatial")
+    rng = np.random.default_rng(5)
+    n = 3000
+    sc, _, _ = synth.multiview_scene(seed=9, n=n, n_views=1, sizes=[(64, 48)])
+    fine = rng.random(n) < 0.6
+    radius = 1.5
+    r = O.anchor_merge(sc, fine, seed=17, radius=radius, k=3)
+    sel = r["selected"]
+    assert 0.15 < sel.sum() / fine.sum() < 0.35
+    cand = np.nonzero(fine & ~sel)[0]
+    tree = spatial.cKDTree(np.asarray(sc.mean_opa)[cand, :3])
+    claim_ref = np.full(n, -1)
+    for s in np.nonzero(sel)[0]:
+        d, j = tree.query(np.asarray(sc.mean_opa)[s, :3], k=3, distance_upper_bound=radius)
+        for dd, jj in zip(d, j):
+            if np.isfinite(dd):
+                c = cand[jj]
+                if claim_ref[c] < 0:
+                    claim_ref[c] = s  # selected Gaussians are visited in increasing index
+    np.testing.assert_array_equal(r["claim"], claim_ref)
+    assert len(r["src"]) == n - (claim_ref >= 0).sum()
+    np.testing.assert_array_equal(r["src"], np.nonzero(claim_ref < 0)[0])
+    np.testing.assert_array_equal(r["kind"], sel[r["src"]].astype(int))
+
+
+def test_anchor_blend_weight():
+    """w = 1 for r < 1 - o, 0.5 at r = 1, continuous at r = 1 - o, linear between."""
+    o = 0.1
+    assert O.anchor_blend_weight(1.0, 2.0, o) == 1.0
+    assert abs(O.anchor_blend_weight(0.9, 1.0, o) - 1.0) < 1e-12
+    assert abs(O.anchor_blend_weight(1.0, 1.0, o) - 0.5) < 1e-12
+    assert abs(O.anchor_blend_weight(0.95, 1.0, o) - 0.75) < 1e-12
