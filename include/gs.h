@@ -178,13 +178,18 @@ int gs_sort(const gs_projected* p, int64_t n, const gs_frame* f, const gs_pairs*
 
 /* Forward image and the per-pixel state the adjoint needs.
  *   color     [sum_v 3 * H_v * W_v]  planar RGB per view
- *   t_final   [sum_v H_v * W_v]      final transmittance
+ *   t_final   [sum_v H_v * W_v]      final transmittance (alpha = 1 - t_final)
  *   n_contrib [sum_v H_v * W_v]      1 + list position of the last composited
- *                                     Gaussian (0 if none) */
+ *                                     Gaussian (0 if none)
+ *   depth     [sum_v H_v * W_v]      optional (NULL: not written): depth
+ *                                     integral sum_i alpha_i T_i z_i, i.e. the
+ *                                     expected camera depth times 1 - t_final
+ *                                     (Sec. 4.4 anchors; no gradient) */
 typedef struct gs_image {
     float* color;
     float* t_final;
     int32_t* n_contrib;
+    float* depth;
 } gs_image;
 
 /* Scratch bytes gs_render_fwd / gs_render_bwd need (work queue of the
@@ -311,6 +316,43 @@ int gs_anchor_offload(const gs_gaussians* params, const gs_gaussians* m, const g
                       void* stream);
 int gs_anchor_load(const gs_gaussians* host_params, const gs_gaussians* host_m, const gs_gaussians* host_v,
                    const gs_gaussians* params, const gs_gaussians* m, const gs_gaussians* v, void* stream);
+
+/* Merging at an anchor (Sec. 4.4): a random 1/(k+1) of the too-fine
+ * Gaussians each absorb up to k nearest too-fine neighbours, giving a coarser
+ * active set.
+ *  - Gaussian i is selected iff too_fine[i] and u_i < 1/(k+1), u_i the top 24
+ *    bits of Philox4x32-10(counter (i, 0, 2, 0), key seed) / 2^24.
+ *  - A selected Gaussian proposes the k nearest (Euclidean distance of the
+ *    means, ties by index) Gaussians that are too fine and not selected, at
+ *    most `radius` away; a Gaussian proposed by several selected ones is
+ *    claimed by the lowest index.
+ *  - Each selected Gaussian and the ones it claimed are replaced by their
+ *    moment-matching merge: weights w_i = o_i a_i (opacity times the product
+ *    of the two largest scales), mean and covariance the w-weighted mean and
+ *    second moment about it (scales and rotation from its eigen-decomposition),
+ *    SH the w-weighted mean, opacity min(0.99, sum_i w_i / a) with a the merged
+ *    product of the two largest scales.
+ *  - Claimed Gaussians leave the set; all others are copied unchanged. The
+ *    output keeps index order; *n_out (device int64) = its size (<= in->n).
+ * out (and m_out, v_out) need in->n rows. m_in, v_in, m_out, v_out: the Adam
+ * moments (all four or none); merged rows get zero moments. radius > 0,
+ * 1 <= k <= 8. ws: gs_anchor_merge_workspace_size(in->n, k) bytes. */
+size_t gs_anchor_merge_workspace_size(int64_t n, int32_t k);
+int gs_anchor_merge(const gs_gaussians* in, const gs_gaussians* m_in, const gs_gaussians* v_in,
+                    const uint8_t* too_fine, float radius, int32_t k, uint64_t seed, const gs_gaussians* out,
+                    const gs_gaussians* m_out, const gs_gaussians* v_out, int64_t* n_out, void* ws, size_t ws_bytes,
+                    void* stream);
+
+/* Anchor blending for novel views (Sec. 4.4, Eq. of w(r)): with d1 <= d2 the
+ * distances of the camera to the two closest anchors, r = d1 / d2 and overlap
+ * o in (0, 0.5): weight of the closest anchor = 1 for r < 1 - o, else
+ * 1 - (r - (1 - o)) 0.5 / o. Host function; returns NaN for invalid input. */
+float gs_anchor_blend_weight(float d1, float d2, float overlap);
+
+/* Scales the opacities of n Gaussians by w in [0, 1] in place (opacity logit
+ * l -> logit(w sigmoid(l))): the two anchors' sets are blended by rendering
+ * their union with weights w and 1 - w. */
+int gs_scale_opacity(float* mean_opa, int64_t n, float w, void* stream);
 
 /* gs_spawn_propose for callers that cannot allocate device memory: the paper
  * has no counterpart; this is a deployment convenience. Callers such as a host

@@ -122,7 +122,8 @@ __device__ __forceinline__ int next_tile(const uint32_t* __restrict__ order, uin
     return t;
 }
 
-template <int TILE, int FB>
+// DEPTH: also accumulate the depth integral sum_i alpha_i T_i z_i per pixel.
+template <int TILE, int FB, bool DEPTH>
 __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_config cfg,
                                                             const uint32_t* __restrict__ range,
                                                             const uint32_t* __restrict__ src,
@@ -131,6 +132,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                                                             const float4* __restrict__ rgb_depth,
                                                             float* __restrict__ color, float* __restrict__ t_final,
                                                             int32_t* __restrict__ n_contrib,
+                                                            float* __restrict__ depth_out,
                                                             const uint32_t* __restrict__ order, uint32_t* counter,
                                                             int n_tiles) {
     constexpr int NT = Geom<TILE>::kThreads;
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
         const WarpBlock wb = warp_block(ti);
         const float px = ti.px + 0.5f, py = ti.py + 0.5f;
         const uint32_t start = range[2 * tile], end = range[2 * tile + 1];
-        float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f;
+        float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, cz = 0.f;
         int last = 0;
         bool done = !ti.inside;
         for (uint32_t b0 = start; b0 < end; b0 += FB) {
@@ -180,6 +182,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                     const float4 c = s_rgb[k];
                     const float w = acc ? alpha * T : 0.f;
                     cr += w * c.x; cg += w * c.y; cb += w * c.z;
+                    if (DEPTH) cz += w * c.w;
                     T = acc ? nT : T;
                     last = acc ? (int)(b0 - start) + k + 1 : last;
                 }
@@ -191,6 +194,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
             color[ti.color_base + 2 * ti.plane] = cb + T * cfg.bg[2];
             t_final[ti.pix] = T;
             n_contrib[ti.pix] = last;
+            if (DEPTH) depth_out[ti.pix] = cz;
         }
         __syncthreads();  // shared buffers are reused by the next tile
     }
@@ -388,8 +392,10 @@ struct RenderLaunch {
     int threads;
 };
 
-static RenderLaunch pick_fwd(int tile, int batch) {
-#define GS_FWD(T, B) if (tile == T && batch == B) return {(const void*)k_render_fwd<T, B>, T * T};
+static RenderLaunch pick_fwd(int tile, int batch, bool depth = false) {
+#define GS_FWD(T, B)                                                                     \
+    if (tile == T && batch == B)                                                         \
+        return {depth ? (const void*)k_render_fwd<T, B, true> : (const void*)k_render_fwd<T, B, false>, T * T};
     GS_FWD(8, 64) GS_FWD(8, 128) GS_FWD(8, 256)
     GS_FWD(16, 64) GS_FWD(16, 128) GS_FWD(16, 256)
     GS_FWD(32, 128) GS_FWD(32, 256)
@@ -473,7 +479,8 @@ extern "C" int gs_render_fwd(const gs_projected* p, const gs_pairs* pairs, const
     uint32_t* counter = persistent ? (uint32_t*)ws : nullptr;
     const uint32_t* order = persistent ? pairs->order : nullptr;
     if (persistent) cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
-    const RenderLaunch L = pick_fwd(cfg->tile, cfg->fwd_batch ? cfg->fwd_batch : default_fwd_batch(cfg->tile));
+    const RenderLaunch L =
+        pick_fwd(cfg->tile, cfg->fwd_batch ? cfg->fwd_batch : default_fwd_batch(cfg->tile), out->depth != nullptr);
     gs_frame fv = *f;
     gs_config cv = *cfg;
     const uint32_t* range = pairs->range;
@@ -484,8 +491,9 @@ extern "C" int gs_render_fwd(const gs_projected* p, const gs_pairs* pairs, const
     float* color = out->color;
     float* tf = out->t_final;
     int32_t* nc = out->n_contrib;
+    float* dz = out->depth;
     void* args[] = {&fv, &cv, (void*)&range, (void*)&src, (void*)&m2, (void*)&co, (void*)&rd,
-                    (void*)&color, (void*)&tf, (void*)&nc, (void*)&order, (void*)&counter, &n_tiles};
+                    (void*)&color, (void*)&tf, (void*)&nc, (void*)&dz, (void*)&order, (void*)&counter, &n_tiles};
     return launch(L, n_tiles, persistent, args, s);
 }
 

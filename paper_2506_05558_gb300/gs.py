@@ -33,7 +33,8 @@ EXPORTS = [
     "gs_anchor_check", "gs_anchor_offload", "gs_anchor_load",
     "gs_mlp_patches", "gs_mlp_param_count", "gs_mlp_workspace_size", "gs_mlp_forward", "gs_mlp_train_step",
     "gs_mlp_gemm_bf16", "gs_mlp_tc_error", "gs_mlp_targets_workspace_size", "gs_mlp_targets", "gs_spawn_learned",
-    "gs_pose_apply", "gs_pose_tangent_grad",
+    "gs_pose_apply", "gs_pose_tangent_grad", "gs_anchor_merge_workspace_size", "gs_anchor_merge",
+    "gs_anchor_blend_weight", "gs_scale_opacity",
 ]
 
 
@@ -72,7 +73,7 @@ class gs_pairs(C.Structure):
 
 
 class gs_image(C.Structure):
-    _fields_ = [("color", C.c_void_p), ("t_final", C.c_void_p), ("n_contrib", C.c_void_p)]
+    _fields_ = [("color", C.c_void_p), ("t_final", C.c_void_p), ("n_contrib", C.c_void_p), ("depth", C.c_void_p)]
 
 
 class gs_grads(C.Structure):
@@ -138,6 +139,11 @@ def lib():
                                        C.c_int32, P, P]),
             "gs_counter_add": (C.c_int, [P, C.c_int32, P]),
             "gs_pose_apply": (C.c_int, [P, P, C.c_int32, P, P]),
+            "gs_anchor_merge_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32]),
+            "gs_anchor_merge": (C.c_int, [C.POINTER(gs_gaussians)] * 3 + [P, C.c_float, C.c_int32, C.c_uint64] +
+                                [C.POINTER(gs_gaussians)] * 3 + [P, P, C.c_size_t, P]),
+            "gs_anchor_blend_weight": (C.c_float, [C.c_float, C.c_float, C.c_float]),
+            "gs_scale_opacity": (C.c_int, [P, C.c_int64, C.c_float, P]),
             "gs_pose_tangent_grad": (C.c_int, [P, P, C.c_int32, P, P]),
             "gs_l1_loss": (C.c_int, [P, P, C.c_int64, P, P, P, C.c_size_t, P]),
             "gs_composite_bwd": (C.c_int, [C.POINTER(gs_projected), C.POINTER(gs_pairs), C.POINTER(gs_frame),
@@ -320,15 +326,17 @@ class Image:
     color: torch.Tensor
     t_final: torch.Tensor
     n_contrib: torch.Tensor
+    depth: torch.Tensor | None = None  # depth integral, written only when present
 
     @staticmethod
-    def alloc(n_pix, device="cuda") -> "Image":
+    def alloc(n_pix, device="cuda", with_depth=False) -> "Image":
         return Image(torch.zeros((3 * n_pix,), dtype=torch.float32, device=device),
                      torch.zeros((n_pix,), dtype=torch.float32, device=device),
-                     torch.zeros((n_pix,), dtype=torch.int32, device=device))
+                     torch.zeros((n_pix,), dtype=torch.int32, device=device),
+                     torch.zeros((n_pix,), dtype=torch.float32, device=device) if with_depth else None)
 
     def c(self) -> gs_image:
-        return gs_image(_ptr(self.color), _ptr(self.t_final), _ptr(self.n_contrib))
+        return gs_image(_ptr(self.color), _ptr(self.t_final), _ptr(self.n_contrib), _ptr(self.depth))
 
 
 @dataclass
@@ -485,6 +493,29 @@ def gs_anchor_load(host_params: Gaussians, host_m, host_v, params: Gaussians, m,
     """Host -> device copies of an anchor's Gaussians (and Adam state)."""
     _check(lib().gs_anchor_load(C.byref(host_params.c()), _opt_c(host_m), _opt_c(host_v), C.byref(params.c()),
                                 _opt_c(m), _opt_c(v), _stream(stream)), "gs_anchor_load")
+
+
+def gs_anchor_merge_workspace_size(n: int, k: int = 3) -> int:
+    return int(lib().gs_anchor_merge_workspace_size(n, k))
+
+
+def gs_anchor_merge(g: Gaussians, too_fine: torch.Tensor, radius: float, seed: int, out: Gaussians,
+                    n_out: torch.Tensor, ws: torch.Tensor, k: int = 3, m=None, v=None, m_out=None, v_out=None,
+                    stream=None):
+    """Merges a random 1/(k+1) of the too-fine Gaussians with their k nearest
+    too-fine neighbours into out (n_out: device int64 row count)."""
+    a, o = g.c(), out.c()
+    cs = [None if t is None else C.byref(t.c()) for t in (m, v, m_out, v_out)]
+    _check(lib().gs_anchor_merge(C.byref(a), cs[0], cs[1], _ptr(too_fine), radius, k, seed, C.byref(o), cs[2], cs[3],
+                                 _ptr(n_out), _ptr(ws), ws.numel(), _stream(stream)), "gs_anchor_merge")
+
+
+def gs_anchor_blend_weight(d1: float, d2: float, overlap: float = 0.1) -> float:
+    return float(lib().gs_anchor_blend_weight(d1, d2, overlap))
+
+
+def gs_scale_opacity(mean_opa: torch.Tensor, w: float, stream=None):
+    _check(lib().gs_scale_opacity(_ptr(mean_opa), mean_opa.shape[0], w, _stream(stream)), "gs_scale_opacity")
 
 
 def pinned_gaussians(n: int) -> Gaussians:

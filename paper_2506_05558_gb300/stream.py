@@ -57,21 +57,17 @@ def psnr(a: torch.Tensor, b: torch.Tensor) -> float:
 
 
 def render_depth(g: gs.Gaussians, cam: torch.Tensor, size, cfg, device="cuda"):
-    """Expected depth per pixel (sum alpha T z over the composited Gaussians,
-    normalised by 1 - T_final) and the colour image, by rendering the scene
-    once with its colours and once with each Gaussian's camera depth in place
-    of its colour."""
+    """Colour image and expected depth per pixel (the depth integral of the
+    forward pass normalised by 1 - T_final; 0 where less than half the pixel is
+    covered)."""
     r = Rasterizer(g.n, [size], 1 << 20, cfg, device)
+    r.img.depth = torch.zeros_like(r.img.t_final)
     r.fit_capacity(g, cam)
     r.forward(g, cam)
-    color = r.img.color.clone()
-    rd = r.proj.rgb_depth
-    rd[:, 0:3] = rd[:, 3:4]
-    gs.gs_render_fwd(r.proj, r.pairs, r.f, r.cfg, r.img, r.ws_render)
     acc = (1.0 - r.img.t_final).clamp_min(1e-6)
-    depth = (r.img.color[: size[0] * size[1]] / acc).clone()
+    depth = r.img.depth / acc
     depth[acc < 0.5] = 0.0  # no reliable depth where little was rendered
-    return color, depth
+    return r.img.color.clone(), depth
 
 
 class OnTheFly:

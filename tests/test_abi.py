@@ -15,7 +15,7 @@ def declared_functions():
         if h.endswith(".h"):
             src = open(os.path.join(ROOT, "include", h)).read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:int|void|size_t|int64_t)\s+\**\s*(gs_\w+)\s*\(", src, flags=re.M))
+            names |= set(re.findall(r"^\s*(?:int|void|size_t|int64_t|float)\s+\**\s*(gs_\w+)\s*\(", src, flags=re.M))
     return sorted(names)
 
 

@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 import torch
 
+from helpers import assert_close
 from oracle import oracle as O
 from paper_2506_05558_gb300 import gs, synth
 
@@ -163,3 +164,70 @@ def test_anchor_blend_weight():
     assert abs(O.anchor_blend_weight(0.9, 1.0, o) - 1.0) < 1e-12
     assert abs(O.anchor_blend_weight(1.0, 1.0, o) - 0.5) < 1e-12
     assert abs(O.anchor_blend_weight(0.95, 1.0, o) - 0.75) < 1e-12
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("with_moments", [False, True])
+def test_anchor_merge_matches_oracle(with_moments):
+    """GPU merge against the oracle on 20k Gaussians (60% too fine): the output
+    count and the kept rows bit-exact (with their Adam moments), merged rows'
+    mean, covariance, opacity and SH within tolerance, merged moments zero."""
+    from paper_2506_05558_gb300 import build
+    build.build()
+    rng = np.random.default_rng(8)
+    n, radius, seed = 20000, 1.2, 4243  # a seed with no neighbour decision within the FP32 margin
+    sc, _, _ = synth.multiview_scene(seed=12, n=n, n_views=1, sizes=[(64, 48)])
+    sc.mean_opa[:, 3] = rng.normal(0, 1, n)
+    fine = (rng.random(n) < 0.6)
+    ref = O.anchor_merge(sc, fine, seed=seed, radius=radius, k=3)
+    assert ref["amb"].sum() == 0
+    g = gs.Gaussians.from_scene(sc)
+    out = gs.Gaussians.zeros(n)
+    n_out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws = gs.workspace(gs.gs_anchor_merge_workspace_size(n, 3))
+    kw = {}
+    if with_moments:
+        m = gs.Gaussians(*[t.clone().normal_() for t in (g.mean_opa, g.scale, g.quat, g.sh)])
+        v = gs.Gaussians(*[t.clone().uniform_() for t in (g.mean_opa, g.scale, g.quat, g.sh)])
+        kw = dict(m=m, v=v, m_out=gs.Gaussians.zeros(n), v_out=gs.Gaussians.zeros(n))
+    gs.gs_anchor_merge(g, torch.tensor(fine.astype(np.uint8), device="cuda"), radius, seed, out, n_out, ws, **kw)
+    torch.cuda.synchronize()
+    k = int(n_out.item())
+    assert k == len(ref["src"]) and k < n
+    kept = ref["kind"] == 0
+    src = ref["src"]
+    for name in ("mean_opa", "scale", "quat", "sh"):
+        got = getattr(out, name)[:k].cpu().numpy()
+        want = getattr(g, name).cpu().numpy()[src]
+        assert np.array_equal(got[kept], want[kept]), name
+        if with_moments:
+            for st, so in ((kw["m"], kw["m_out"]), (kw["v"], kw["v_out"])):
+                mo_ = getattr(so, name)[:k].cpu().numpy()
+                assert np.array_equal(mo_[kept], getattr(st, name).cpu().numpy()[src][kept])
+                assert not mo_[~kept].any()
+    mrg = ~kept
+    assert mrg.sum() > 500
+    mo = out.mean_opa[:k].cpu().numpy()[mrg]
+    assert_close(mo[:, :3], ref["mean"][mrg], 1e-5, what="merged mean")
+    assert_close(1 / (1 + np.exp(-mo[:, 3].astype(np.float64))), ref["opacity"][mrg], 1e-4, what="merged opacity")
+    ls = out.scale[:k].cpu().numpy()[mrg]
+    q = out.quat[:k].cpu().numpy()[mrg]
+    cov = np.array([O.covariance(ls[i], q[i]) for i in range(len(ls))])
+    for i in range(len(ls)):
+        assert_close(cov[i], ref["cov"][mrg][i], 1e-3, what=f"merged covariance {i}")
+    assert_close(out.sh[:k].cpu().numpy()[mrg], ref["sh"][mrg], 1e-4, what="merged SH")
+
+
+@pytest.mark.gpu
+def test_anchor_blend_weight_and_opacity_scaling():
+    from paper_2506_05558_gb300 import build
+    build.build()
+    for d1, d2 in ((1.0, 2.0), (0.95, 1.0), (1.0, 1.0), (0.9, 1.0)):
+        assert abs(gs.gs_anchor_blend_weight(d1, d2, 0.1) - O.anchor_blend_weight(d1, d2, 0.1)) < 1e-6
+    assert math.isnan(gs.gs_anchor_blend_weight(2.0, 1.0, 0.1))
+    logit = torch.tensor([[0, 0, 0, 1.5], [0, 0, 0, -2.0], [0, 0, 0, 0.0]], device="cuda")
+    o = 1 / (1 + np.exp(-logit[:, 3].cpu().numpy().astype(np.float64)))
+    gs.gs_scale_opacity(logit, 0.25)
+    torch.cuda.synchronize()
+    got = 1 / (1 + np.exp(-logit[:, 3].cpu().numpy().astype(np.float64)))
+    np.testing.assert_allclose(got, 0.25 * o, rtol=1e-5)

@@ -355,6 +355,36 @@ def test_720p_200k_end_to_end():
     compare_views(sc, [cam], 3)
 
 
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_depth_channel_matches_oracle(schedule):
+    """The optional depth-integral output of the forward pass against the
+    oracle (three views of different sizes, SH3), with colour and transmittance
+    unchanged by requesting it."""
+    sc, cams, _ = synth.multiview_scene(seed=31, n=3000, n_views=3, sizes=[(96, 64), (80, 48), (72, 72)])
+    sizes = [(c["width"], c["height"]) for c in cams]
+    cfg = gs.config(sh_degree=3, schedule=schedule)
+    g = gs.Gaussians.from_scene(sc)
+    camt = gs.cameras_tensor(cams)
+    r = Rasterizer(sc.n, sizes, capacity=1024, cfg=cfg)
+    r.fit_capacity(g, camt)
+    r.forward(g, camt)
+    color0 = r.img.color.clone()
+    r.img.depth = torch.zeros_like(r.img.t_final)
+    r.forward(g, camt)
+    torch.cuda.synchronize()
+    assert torch.equal(color0, r.img.color)
+    ocfg = O.Config(sh_degree=3, **MARGINS)
+    for v, cam in enumerate(cams):
+        w, h = cam["width"], cam["height"]
+        view = O.render_view(sc, cam, ocfg)
+        bad = O.ambiguous_tiles(view, cam, ocfg)
+        pm = ~tile_pixel_mask(bad, w, h, 16) & (view["amb"] == 0)
+        ref = O.render_depth(view["proj"], view["start"], view["ids"], cam, ocfg)
+        got = r.view_pixels(r.img.depth, v).cpu().numpy()
+        assert_close(got, ref, IMG_RTOL, pm, f"depth view {v}")
+        assert (ref[pm] > 0).mean() > 0.3
+
+
 def test_nonfinite_gaussians_are_culled():
     sc, cam, _ = synth.tiny_scene(n=200)
     sc.mean_opa[3, 0] = np.nan
