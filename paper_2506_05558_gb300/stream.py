@@ -1,5 +1,10 @@
 """Frame-by-frame reconstruction loop (Sec. 4.2-4.4) with known poses, used to
-compare plain direct spawn sampling with the learned spawn proposal.
+compare plain direct spawn sampling with the learned spawn proposal, with
+anchors (Sec. 4.4): when more than 40% of the active Gaussians are below one
+pixel from the previous camera, the active set and its Adam state are copied
+to pinned host memory as an anchor at that camera's centre and the set is
+coarsened by merging; novel views render the closest anchor, blending the two
+closest when their distances are similar.
 
 Per new frame: render the active Gaussians from its pose (the penalty image
 of Eq. 2), spawn new Gaussians (direct sampling with the frame's depth map, or
@@ -18,6 +23,29 @@ import torch
 
 from . import gs
 from .raster import Rasterizer
+
+
+class Anchor:
+    """An anchor: its location (camera centre) and the active set stored there
+    (pinned host copies of the Gaussians and their Adam moments)."""
+
+    def __init__(self, location, store: "GaussianStore"):
+        n = store.n
+        self.location = np.asarray(location, np.float64)
+        self.n = n
+        self.p, self.m, self.v = gs.pinned_gaussians(n), gs.pinned_gaussians(n), gs.pinned_gaussians(n)
+        g, m, v = store.active()
+        gs.gs_anchor_offload(g, m, v, self.p, self.m, self.v)
+
+    def load(self, device="cuda") -> gs.Gaussians:
+        g = gs.Gaussians.zeros(self.n, device)
+        gs.gs_anchor_load(self.p, None, None, g, None, None)
+        return g
+
+
+def camera_centre(cam: torch.Tensor):
+    c = gs.cameras_from_tensor(cam)[0]
+    return -np.asarray(c["R"], np.float64).T @ np.asarray(c["t"], np.float64)
 
 
 class GaussianStore:
@@ -73,7 +101,7 @@ def render_depth(g: gs.Gaussians, cam: torch.Tensor, size, cfg, device="cuda"):
 class OnTheFly:
     def __init__(self, capacity: int, size, window: int = 4, iters: int = 30, mode: str = "plain",
                  mlp_warmup_frames: int = 3, mlp_steps: int = 40, keep_threshold: float = 0.05, seed: int = 7,
-                 device="cuda"):
+                 anchor_tau: float = 1.0, anchor_share: float = 0.4, merge_radius: float = 0.5, device="cuda"):
         self.store = GaussianStore(capacity, device)
         self.W, self.H = size
         self.window = window
@@ -108,6 +136,63 @@ class OnTheFly:
             self.mlp_cfg = gs.mlp_config(tensor_path=1, lr=1e-3)
             self.mlp_step = 0
         self.log = []
+        self.anchors: list[Anchor] = []
+        self.prev_cam = None
+        self.anchor_tau = anchor_tau
+        self.anchor_share = anchor_share
+        self.merge_radius = merge_radius
+        self.too_fine = torch.zeros((capacity,), dtype=torch.uint8, device=device)
+        self.count = torch.zeros((1,), dtype=torch.int64, device=device)
+
+    # -- anchors -------------------------------------------------------------------
+    def _maybe_anchor(self, frame_idx):
+        """Anchor rule from the previous camera; on trigger, store the active set
+        at an anchor and merge the too-fine Gaussians. Returns the merge log."""
+        if self.prev_cam is None or self.store.n == 0 or self.anchor_tau <= 0:
+            return None
+        g, m, v = self.store.active()
+        fine = self.too_fine[:g.n]
+        gs.gs_anchor_check(g, self.prev_cam, self.anchor_tau, fine, self.count)
+        cnt = int(self.count.item())
+        if cnt <= self.anchor_share * g.n:
+            return None
+        self.anchors.append(Anchor(camera_centre(self.prev_cam), self.store))
+        out = GaussianStore(self.store.cap, self.device)
+        n_out = torch.zeros((1,), dtype=torch.int64, device=self.device)
+        ws = gs.workspace(gs.gs_anchor_merge_workspace_size(g.n, 3), self.device)
+        go, mo, vo = out.p, out.m, out.v
+        gs.gs_anchor_merge(g, fine, self.merge_radius, self.seed * 7919 + frame_idx, go, n_out, ws, m=m, v=v,
+                           m_out=mo, v_out=vo)
+        out.n = int(n_out.item())
+        before = g.n
+        self.store = out
+        return dict(frame=frame_idx, too_fine=cnt, before=before, after=out.n)
+
+    def finish(self, cam):
+        """The active set at the end of the path is stored in a last anchor."""
+        self.anchors.append(Anchor(camera_centre(cam), self.store))
+
+    def render_anchors(self, cam, overlap=0.1):
+        """Novel view from the anchors (Sec. 4.4): the closest anchor's
+        Gaussians, or the two closest blended by opacity weights w, 1 - w."""
+        c = camera_centre(cam)
+        d = sorted((float(np.linalg.norm(a.location - c)), i) for i, a in enumerate(self.anchors))
+        if len(d) == 1 or d[1][0] <= 0.0:
+            parts = [(self.anchors[d[0][1]], 1.0)]
+        else:
+            w = gs.gs_anchor_blend_weight(d[0][0], d[1][0], overlap)
+            parts = [(self.anchors[d[0][1]], w)] + ([(self.anchors[d[1][1]], 1.0 - w)] if w < 1.0 else [])
+        sets = []
+        for a, w in parts:
+            g = a.load(self.device)
+            if w < 1.0:
+                gs.gs_scale_opacity(g.mean_opa, w)
+            sets.append(g)
+        g = gs.Gaussians(*[torch.cat([getattr(x, f) for x in sets]) for f in ("mean_opa", "scale", "quat", "sh")])
+        r = Rasterizer(g.n, [(self.W, self.H)], 1 << 18, self.cfg, self.device)
+        r.fit_capacity(g, cam)
+        r.forward(g, cam)
+        return r.img.color.clone()
 
     # -- steps -------------------------------------------------------------------
     def _render_active(self, cam):
@@ -180,6 +265,7 @@ class OnTheFly:
         return float(self.mlp_loss.item())
 
     def add_frame(self, image: torch.Tensor, depth: torch.Tensor, cam: torch.Tensor, frame_idx: int):
+        anchor = self._maybe_anchor(frame_idx)
         render = self._render_active(cam)
         k, learned = self._spawn(image, render, depth, cam, frame_idx)
         n0 = self.store.n
@@ -192,7 +278,8 @@ class OnTheFly:
             # the optimisation teach the proposal
             mlp_loss = self._train_mlp(image, n0, k, cam)
         self.log.append(dict(frame=frame_idx, spawned=k, n=self.store.n, loss=loss, learned=learned,
-                             mlp_loss=mlp_loss, iters=self.iter_count))
+                             mlp_loss=mlp_loss, iters=self.iter_count, anchor=anchor))
+        self.prev_cam = cam
 
     def evaluate(self, frames):
         """Mean PSNR of the active set rendered at the given (image, camera) frames."""

@@ -37,7 +37,8 @@ def make_stream(n_gt=60_000, n_frames=10, size=(256, 144), seed=21):
 
 
 def run(mode, frames, size, iters=20):
-    otf = OnTheFly(2_000_000, size, window=3, iters=iters, mode=mode, mlp_warmup_frames=3, mlp_steps=30)
+    otf = OnTheFly(2_000_000, size, window=3, iters=iters, mode=mode, mlp_warmup_frames=3, mlp_steps=30,
+                   anchor_tau=0.0)  # spawning comparison without anchors
     for i, (img, depth, cam) in enumerate(frames):
         otf.add_frame(img, depth, cam, i)
     ev = [(img, cam) for img, _, cam in frames[-3:]]
@@ -62,3 +63,32 @@ def test_learned_vs_plain_spawning():
     os.makedirs("gpurun_out", exist_ok=True)
     with open("gpurun_out/stream_report.json", "w") as f:
         json.dump(report, f, indent=1)
+
+
+def test_anchors_in_the_stream():
+    """With a 50-pixel size threshold anchors trigger: each stores the active set
+    on the host and the merge shrinks it; the final set is stored in a last
+    anchor and a training view rendered from the anchors (closest or blended)
+    still reconstructs the frame."""
+    size = (256, 144)
+    frames = make_stream(size=size)
+    empty = 10 * np.log10(1.0 / torch.mean(frames[-1][0] ** 2).item())
+    otf = OnTheFly(2_000_000, size, window=3, iters=20, mode="plain", anchor_tau=50.0, merge_radius=0.5)
+    for i, (img, depth, cam) in enumerate(frames):
+        otf.add_frame(img, depth, cam, i)
+    merges = [e["anchor"] for e in otf.log if e["anchor"]]
+    assert merges, otf.log
+    for a in merges:
+        assert a["after"] < a["before"] and a["too_fine"] > 0.4 * a["before"]
+    otf.finish(frames[-1][2])
+    assert len(otf.anchors) == len(merges) + 1
+    from paper_2506_05558_gb300.stream import psnr
+    img, _, cam = frames[-1]
+    p_active = otf.evaluate([(img, cam)])
+    p_anchor = psnr(otf.render_anchors(cam), img)
+    report = {"merges": merges, "psnr_active": p_active, "psnr_from_anchors": p_anchor, "empty": empty,
+              "anchors": [dict(location=a.location.tolist(), n=a.n) for a in otf.anchors]}
+    os.makedirs("gpurun_out", exist_ok=True)
+    with open("gpurun_out/stream_anchor_report.json", "w") as f:
+        json.dump(report, f, indent=1)
+    assert p_active > empty + 3 and p_anchor > empty + 3, report
