@@ -27,9 +27,13 @@
  * them: FP32 arithmetic on the GPU may legitimately take the other branch.
  *
  * cam[18] = R(9, row-major world->camera), t(3), fx, fy, cx, cy, width, height
- * cfg[16] = tile, sh_degree, near, dilation, alpha_min, alpha_max, t_min,
+ * cfg[17] = tile, sh_degree, near, dilation, alpha_min, alpha_max, t_min,
  *           bg(3), pose_grad_through_sh, margin_geo, margin_alpha, margin_T,
- *           margin_rect_px, margin_depth
+ *           margin_rect_px, margin_depth, mip_filter
+ * mip_filter = 1: the dilation acts as a 2-D low-pass filter that keeps the
+ * splat's integral (the multi-scale filtering of Sec. 4.3): the opacity is
+ * multiplied by sqrt(rho), rho = det(Sigma2D) / det(Sigma2D + dil I), with rho
+ * floored at 1e-6 (a degenerate splat keeps a tiny, gradient-free weight).
  * margin_geo is relative (near plane, determinant, radius, guard band, colour
  * clamp); margin_rect_px is the distance in pixels of a tile-rect edge from a
  * tile boundary; margin_alpha and margin_T are relative; margin_depth flags a
@@ -49,7 +53,7 @@ typedef struct {
 } Cam;
 
 typedef struct {
-    int tile, sh_degree, pose_through_sh;
+    int tile, sh_degree, pose_through_sh, mip;
     double near_z, dil, a_min, a_max, t_min, bg[3], m_geo, m_alpha, m_T, m_rect, m_depth;
 } Cfg;
 
@@ -69,6 +73,7 @@ static Cfg read_cfg(const double* c) {
     g.bg[0] = c[7]; g.bg[1] = c[8]; g.bg[2] = c[9];
     g.pose_through_sh = (int)c[10];
     g.m_geo = c[11]; g.m_alpha = c[12]; g.m_T = c[13]; g.m_rect = c[14]; g.m_depth = c[15];
+    g.mip = (int)c[16];
     return g;
 }
 
@@ -172,6 +177,8 @@ typedef struct {
     double p[3], qn[4], qlen, Rq[9], s[3], Sig[9], Sc[9], J[6], S2[4], det;
     int clamp_x, clamp_y;
     double dir[3], dlen, d[3], Y[16], dY[48], raw[3];
+    double o, rho, fmip; /* opacity before the filter factor; rho and sqrt(rho) (1 without the filter) */
+    int rho_floor;       /* rho below its floor: no gradient through it */
 } ProjState;
 
 static void project_one(int64_t i, const double* mean_opa, const double* scale, const double* quat,
@@ -227,11 +234,22 @@ static void project_one(int64_t i, const double* mean_opa, const double* scale, 
     for (int r = 0; r < 2; r++)
         for (int c = 0; c < 2; c++)
             st->S2[2 * r + c] = JS[3 * r] * J[3 * c] + JS[3 * r + 1] * J[3 * c + 1] + JS[3 * r + 2] * J[3 * c + 2];
+    /* filter factor: rho = det(Sigma2D) / det(Sigma2D + dil I), before the dilation */
+    double det0 = st->S2[0] * st->S2[3] - st->S2[1] * st->S2[1];
+    double a0 = st->S2[0], c0 = st->S2[3];
     st->S2[0] += g->dil;
     st->S2[3] += g->dil;
     double A = st->S2[0], Bc = st->S2[1], C = st->S2[3];
     st->det = A * C - Bc * Bc;
     if (fabs(st->det) < g->m_geo * A * C) a |= 1;
+    st->rho = 1.0; st->fmip = 1.0; st->rho_floor = 0;
+    if (g->mip) {
+        st->rho = det0 / st->det;
+        /* det0 cancels for thin splats: FP32 may then disagree in every digit */
+        if (fabs(det0) < 1e3 * g->m_geo * a0 * c0 || fabs(st->rho - 1e-6) < g->m_geo * 1e-6) a |= 1;
+        st->rho_floor = !(st->rho > 1e-6);
+        st->fmip = sqrt(st->rho_floor ? 1e-6 : st->rho);
+    }
     if (amb) amb[i] = a;
     if (!(st->det > 0)) return;
     double u = k->fx * x / z + k->cx, v = k->fy * y / z + k->cy;
@@ -281,6 +299,8 @@ static void project_one(int64_t i, const double* mean_opa, const double* scale, 
         if (s < 0) cm |= (uint8_t)(1 << ch);
     }
     double o = 1.0 / (1.0 + exp(-logit));
+    st->o = o;
+    o *= st->fmip;
     if (!isfinite(st->raw[0]) || !isfinite(st->raw[1]) || !isfinite(st->raw[2]) || !isfinite(o)) return;
 
     st->culled = 0;
@@ -588,8 +608,9 @@ void or_project_bwd(int64_t n, const double* mean_opa, const double* scale, cons
         const double* G = g2d + 9 * i;
         double x = st.p[0], y = st.p[1], z = st.p[2];
 
-        /* opacity */
-        g_logit[i] = G[5] * op * (1 - op);
+        /* opacity o f, o = sigmoid(logit), f = sqrt(rho) with the filter (else 1) */
+        g_logit[i] = G[5] * st.fmip * st.o * (1 - st.o);
+        double g_rho = (g.mip && !st.rho_floor) ? G[5] * st.o / (2.0 * st.fmip) : 0.0;
 
         /* colour: rgb = max(SH(d) + 0.5, 0) */
         double graw[3];
@@ -620,6 +641,14 @@ void or_project_bwd(int64_t n, const double* mean_opa, const double* scale, cons
             for (int c = 0; c < 2; c++) t4[2 * r + c] = Q[2 * r] * GQ[c] + Q[2 * r + 1] * GQ[2 + c];
         for (int r = 0; r < 2; r++)
             for (int c = 0; c < 2; c++) GS[2 * r + c] = -(t4[2 * r] * Q[c] + t4[2 * r + 1] * Q[2 + c]);
+        if (g_rho != 0.0) {
+            /* rho = ((A - dil)(C - dil) - B^2) / (A C - B^2) with S2 = [[A, B], [B, C]] */
+            double A = st.S2[0], B = st.S2[1], C = st.S2[3], rho = st.rho;
+            GS[0] += g_rho * ((C - g.dil) - rho * C) / st.det;
+            GS[3] += g_rho * ((A - g.dil) - rho * A) / st.det;
+            GS[1] += -g_rho * B * (1.0 - rho) / st.det; /* half of d rho / dB on each symmetric entry */
+            GS[2] += -g_rho * B * (1.0 - rho) / st.det;
+        }
 
         /* S2 = J Sc J^T + dil I: dL/dSc = J^T GS J, dL/dJ = 2 GS J Sc */
         const double* J = st.J;

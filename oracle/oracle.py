@@ -76,12 +76,13 @@ class Config:
     margin_T: float = 1e-4
     margin_rect_px: float = 2e-3
     margin_depth: float = 1e-6
+    mip_filter: int = 0
 
     def array(self) -> np.ndarray:
         return np.array([self.tile, self.sh_degree, self.near_z, self.dilation, self.alpha_min,
                          self.alpha_max, self.t_min, *self.bg, self.pose_grad_through_sh,
                          self.margin_geo, self.margin_alpha, self.margin_T, self.margin_rect_px,
-                         self.margin_depth], np.float64)
+                         self.margin_depth, self.mip_filter], np.float64)
 
 
 def cam_array(cam: dict) -> np.ndarray:

@@ -311,9 +311,10 @@ def _fd_scene(sh_degree, seed):
     return sc, cam, rng
 
 
-@pytest.mark.parametrize("sh_degree,through_sh", [(0, 0), (3, 1), (3, 0)])
-def test_gradients_match_central_differences(sh_degree, through_sh):
-    cfg = O.Config(sh_degree=sh_degree, pose_grad_through_sh=through_sh, bg=(0.1, 0.2, 0.3))
+@pytest.mark.parametrize("sh_degree,through_sh,mip", [(0, 0, 0), (3, 1, 0), (3, 0, 0), (0, 0, 1), (3, 0, 1)])
+def test_gradients_match_central_differences(sh_degree, through_sh, mip):
+    cfg = O.Config(sh_degree=sh_degree, pose_grad_through_sh=through_sh, bg=(0.1, 0.2, 0.3), mip_filter=mip,
+                   dilation=0.1 if mip else 0.3)
     # first seed whose scene has no decision within the ambiguity margins
     for seed in range(11, 40):
         sc, cam, rng = _fd_scene(sh_degree, seed)
@@ -519,3 +520,26 @@ def test_depth_integral_closed_forms():
         v2 = O.render_view(sc2, cam, cfg)
         d2 = O.render_depth(v2["proj"], v2["start"], v2["ids"], cam, cfg)
         assert abs(d2[9, 7] - (o1 * 2.0 + (1 - o1) * o2 * 5.0)) < 1e-12
+
+
+def test_mip_filter_single_gaussian_closed_form():
+    """With the filter, an axis-aligned Gaussian on the optical axis (Sigma2D =
+    diag(sx^2, sy^2), sx = fx Sx / z) composites at its centre to
+    o sqrt(sx^2 sy^2 / ((sx^2 + s)(sy^2 + s))) rgb, s the filter variance; the
+    conic is that of Sigma2D + s I."""
+    cam = synth.camera(np.eye(3), np.zeros(3), 40.0, 33, 33, dtype=np.float64)
+    cam = dict(cam, cx=16.5, cy=16.5)  # the optical axis through the centre of pixel (16, 16)
+    o, z, S = 0.6, 4.0, (0.07, 0.03, 0.05)
+    sc = one_gaussian([0.0, 0.0, z], np.log(S), [1, 0, 0, 0], math.log(o / (1 - o)), (0.4, 0.2, -0.1))
+    s = 0.1
+    cfg = O.Config(sh_degree=0, mip_filter=1, dilation=s)
+    v = O.render_view(sc, cam, cfg)
+    sx2, sy2 = (40.0 * S[0] / z) ** 2, (40.0 * S[1] / z) ** 2
+    f = math.sqrt(sx2 * sy2 / ((sx2 + s) * (sy2 + s)))
+    rgb = v["proj"]["rgb"][0]
+    np.testing.assert_allclose(v["color"][:, 16, 16], o * f * rgb, rtol=1e-12)
+    np.testing.assert_allclose(v["proj"]["opacity"][0], o * f, rtol=1e-12)
+    np.testing.assert_allclose(v["proj"]["conic"][0], [1 / (sx2 + s), 0.0, 1 / (sy2 + s)], rtol=1e-12, atol=1e-15)
+    # without the filter the same dilation leaves the opacity unchanged
+    v0 = O.render_view(sc, cam, O.Config(sh_degree=0, mip_filter=0, dilation=s))
+    np.testing.assert_allclose(v0["proj"]["opacity"][0], o, rtol=1e-12)
