@@ -310,9 +310,16 @@ def measure_rows(torch, gs, W, device, peaks, reps=10):
     hosts = [gs.pinned_gaussians(g.n) for _ in range(3)]
     mm = gs.Gaussians.zeros(g.n, device)
     o_ms = event_ms(torch, lambda: gs.gs_anchor_offload(g, mm, mm, hosts[0], hosts[1], hosts[2]), 3)
+    hosts_dev = [gs.Gaussians.zeros(g.n, device) for _ in range(2)]
+    # f1: merge of the too-fine set (k = 3, 0.5 m search radius) with Adam state
+    mout = gs.Gaussians.zeros(g.n, device)
+    n_out = torch.zeros(1, dtype=torch.int64, device=device)
+    wsa = gs.workspace(gs.gs_anchor_merge_workspace_size(g.n, 3), device)
+    m_ms = event_ms(torch, lambda: gs.gs_anchor_merge(g, fine, 0.5, 7, mout, n_out, wsa, m=mm, v=mm,
+                                                      m_out=hosts_dev[0], v_out=hosts_dev[1]), 3)
     out["anchor"] = {"check_ms": a_ms, "check_gbs": (33 * g.n) / a_ms / 1e6, "too_fine": int(cnt.item()),
                      "offload_ms": o_ms, "offload_gbs": 3 * 240 * g.n / o_ms / 1e6,
-                     "offload_bytes": 3 * 240 * g.n}
+                     "offload_bytes": 3 * 240 * g.n, "merge_ms": m_ms, "merged_rows_out": int(n_out.item())}
     return out
 
 

@@ -81,6 +81,10 @@ typedef struct gs_config {
                                      tile 8: 64/128/256, tile 16: 64/128/256, tile 32: 128/256 */
     int32_t bwd_batch;            /* the same for the adjoint: 0 = default; tile 8: 64/128/256,
                                      tile 16: 32/64/128, tile 32: 32 */
+    int32_t mip_filter;           /* 1: the dilation is a 2-D low-pass filter that keeps the splat's
+                                     integral (multi-scale training, Sec. 4.3): opacity times
+                                     sqrt(rho), rho = det(Sigma2D) / det(Sigma2D + dilation I)
+                                     floored at 1e-6; use dilation 0.1 with it: 0 */
 } gs_config;
 
 void gs_config_default(gs_config* cfg);

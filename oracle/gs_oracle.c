@@ -245,8 +245,8 @@ static void project_one(int64_t i, const double* mean_opa, const double* scale, 
     st->rho = 1.0; st->fmip = 1.0; st->rho_floor = 0;
     if (g->mip) {
         st->rho = det0 / st->det;
-        /* det0 cancels for thin splats: FP32 may then disagree in every digit */
-        if (fabs(det0) < 1e3 * g->m_geo * a0 * c0 || fabs(st->rho - 1e-6) < g->m_geo * 1e-6) a |= 1;
+        /* an FP32 det(Sigma2D) of a very thin splat (det0 << a0 c0) may lose most digits */
+        if (fabs(det0) < 1e-4 * a0 * c0 || fabs(st->rho - 1e-6) < g->m_geo * 1e-6) a |= 1;
         st->rho_floor = !(st->rho > 1e-6);
         st->fmip = sqrt(st->rho_floor ? 1e-6 : st->rho);
     }

@@ -230,19 +230,31 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
                 M0[kk] = J00 * T[kk] + J02 * T[6 + kk];
                 M1[kk] = J11 * T[3 + kk] + J12 * T[6 + kk];
             }
-            const float Sa = M0[0] * M0[0] + M0[1] * M0[1] + M0[2] * M0[2] + cfg.dilation;
+            const float Sa0 = M0[0] * M0[0] + M0[1] * M0[1] + M0[2] * M0[2];
             const float Sb = M0[0] * M1[0] + M0[1] * M1[1] + M0[2] * M1[2];
-            const float Sc = M1[0] * M1[0] + M1[1] * M1[1] + M1[2] * M1[2] + cfg.dilation;
+            const float Sc0 = M1[0] * M1[0] + M1[1] * M1[1] + M1[2] * M1[2];
+            const float Sa = Sa0 + cfg.dilation, Sc = Sc0 + cfg.dilation;
             const float idet = 1.f / (Sa * Sc - Sb * Sb);
             const float Qa = Sc * idet, Qb = -Sb * idet, Qc = Sa * idet;
+            // filter factor f = sqrt(rho), rho = det(Sigma2D) / det(Sigma2D + dil I) (1 without the filter)
+            float fmip = 1.f, g_rho = 0.f, rho = 1.f;
+            if (cfg.mip_filter) {
+                // det Sigma2D = |M0 x M1|^2 (no cancellation for thin splats)
+                const float k0 = M0[1] * M1[2] - M0[2] * M1[1], k1 = M0[2] * M1[0] - M0[0] * M1[2];
+                const float k2 = M0[0] * M1[1] - M0[1] * M1[0];
+                rho = (k0 * k0 + k1 * k1 + k2 * k2) * idet;
+                fmip = sqrtf(rho > 1e-6f ? rho : 1e-6f);
+                if (rho > 1e-6f) g_rho = dop * opa / (2.f * fmip);  // dL/drho through opacity o f
+            }
 
             // 4. conic = S^-1: dL/dS = -Q dL/dQ Q, dL/dQ = [[dA, dB/2], [dB/2, dC]]
             const float hB = 0.5f * dB;
             const float t00 = Qa * dA + Qb * hB, t01 = Qa * hB + Qb * dC;
             const float t10 = Qb * dA + Qc * hB, t11 = Qb * hB + Qc * dC;
-            const float GS00 = -(t00 * Qa + t01 * Qb);
-            const float GS01 = -(t00 * Qb + t01 * Qc);
-            const float GS11 = -(t10 * Qb + t11 * Qc);
+            // plus the filter factor's rho = ((A - dil)(C - dil) - B^2) / (A C - B^2), S = [[A, B], [B, C]]
+            const float GS00 = -(t00 * Qa + t01 * Qb) + g_rho * (Sc0 - rho * Sc) * idet;
+            const float GS01 = -(t00 * Qb + t01 * Qc) - g_rho * Sb * (1.f - rho) * idet;
+            const float GS11 = -(t10 * Qb + t11 * Qc) + g_rho * (Sa0 - rho * Sa) * idet;
             // 5. S = M M^T + dil I: dL/dM = 2 GS M
             float GM0[3], GM1[3];
 #pragma unroll
@@ -310,7 +322,7 @@ __global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
             put(0, gmx + c.R[0] * gpx + c.R[3] * gpy + c.R[6] * gpz);
             put(1, gmy + c.R[1] * gpx + c.R[4] * gpy + c.R[7] * gpz);
             put(2, gmz + c.R[2] * gpx + c.R[5] * gpy + c.R[8] * gpz);
-            put(3, dop * opa * (1.f - opa));
+            put(3, dop * fmip * opa * (1.f - opa));
             put(kSlotVis, 1.f);
             // 9. pose, left perturbation: dp = rho + phi x p, dT = phi^ T
             pose[0] += gpx; pose[1] += gpy; pose[2] += gpz;

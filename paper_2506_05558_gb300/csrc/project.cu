@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean
     const float z = c.R[6] * mo.x + c.R[7] * mo.y + c.R[8] * mo.z + c.t[2];
     bool keep = z > cfg.near_z;  // false for NaN
 
-    float a = 0.f, b = 0.f, cc = 0.f, det = 0.f, u = 0.f, vv = 0.f;
+    float a = 0.f, b = 0.f, cc = 0.f, det = 0.f, u = 0.f, vv = 0.f, fmip = 1.f;
     int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
     if (keep) {
         const float4 q4 = quat[g];
@@ -64,10 +64,19 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean
             A0[k] = c.fx * iz * (T[k] - txz * T[6 + k]);
             A1[k] = c.fy * iz * (T[3 + k] - tyz * T[6 + k]);
         }
-        a = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2] + cfg.dilation;
+        const float a0 = A0[0] * A0[0] + A0[1] * A0[1] + A0[2] * A0[2];
         b = A0[0] * A1[0] + A0[1] * A1[1] + A0[2] * A1[2];
-        cc = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2] + cfg.dilation;
+        const float c0 = A1[0] * A1[0] + A1[1] * A1[1] + A1[2] * A1[2];
+        a = a0 + cfg.dilation;
+        cc = c0 + cfg.dilation;
         det = a * cc - b * b;
+        if (cfg.mip_filter) {  // filter factor sqrt(det Sigma2D / det(Sigma2D + dil I)), rho floored at 1e-6
+            // det Sigma2D = |A0|^2 |A1|^2 - (A0.A1)^2 = |A0 x A1|^2: no cancellation for thin splats
+            const float k0 = A0[1] * A1[2] - A0[2] * A1[1], k1 = A0[2] * A1[0] - A0[0] * A1[2];
+            const float k2 = A0[0] * A1[1] - A0[1] * A1[0];
+            const float rho = (k0 * k0 + k1 * k1 + k2 * k2) / det;
+            fmip = sqrtf(rho > 1e-6f ? rho : 1e-6f);
+        }
         u = c.fx * x * iz + c.cx;
         vv = c.fy * y * iz + c.cy;
         keep = det > 0.f && isfinite(u) && isfinite(vv);
@@ -97,7 +106,7 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean
         float Y[16];
         sh_eval_basis(cfg.sh_degree, dx, dy, dz, Y);
         rgb = sh_color(sh + 12 * g, cfg.sh_degree, Y);
-        opa = 1.f / (1.f + expf(-mo.w));
+        opa = fmip / (1.f + expf(-mo.w));
         keep = isfinite(rgb.x) && isfinite(rgb.y) && isfinite(rgb.z) && isfinite(opa);
         rgb.x = fmaxf(rgb.x, 0.f); rgb.y = fmaxf(rgb.y, 0.f); rgb.z = fmaxf(rgb.z, 0.f);
     }
@@ -133,6 +142,7 @@ extern "C" void gs_config_default(gs_config* cfg) {
     cfg->alpha_min = 1.f / 255.f;
     cfg->alpha_max = 0.99f;
     cfg->t_min = 1e-4f;
+    cfg->mip_filter = 0;
     cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.f;
     cfg->pose_grad_through_sh = 0;
     cfg->schedule = 0;

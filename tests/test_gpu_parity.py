@@ -227,10 +227,13 @@ def run_views(sc, cams, sh_degree, dLs=None, seed=0, pose_through_sh=0, bg=(0.0,
 
 
 def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), max_amb_frac=0.3, max_excl_frac=0.25,
-                  dLs=None, **launch):
-    r, dLs, d_proj = run_views(sc, cams, sh_degree, dLs=dLs, pose_through_sh=pose_through_sh, bg=bg, **launch)
+                  dLs=None, mip=0, **launch):
+    dil = 0.1 if mip else 0.3
+    r, dLs, d_proj = run_views(sc, cams, sh_degree, dLs=dLs, pose_through_sh=pose_through_sh, bg=bg, mip_filter=mip,
+                               dilation=dil, **launch)
     tile = launch.get("tile", 16)
-    ocfg = O.Config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg, tile=tile, **MARGINS)
+    ocfg = O.Config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg, tile=tile, mip_filter=mip,
+                    dilation=dil, **MARGINS)
     n = sc.n
     views = []
     excl = np.zeros(n, bool)
@@ -299,10 +302,12 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
     return r, excl.sum()
 
 
-def test_tiny_scene_sh0_end_to_end():
-    """64x64 view, 1,000 Gaussians, SH degree 0, pose gradient (seeded)."""
+@pytest.mark.parametrize("mip", [0, 1])
+def test_tiny_scene_sh0_end_to_end(mip):
+    """64x64 view, 1,000 Gaussians, SH degree 0, pose gradient (seeded); with
+    and without the integral-keeping 2-D filter."""
     sc, cam, _ = synth.tiny_scene()
-    compare_views(sc, [cam], 0, bg=(0.2, 0.1, 0.0))
+    compare_views(sc, [cam], 0, bg=(0.2, 0.1, 0.0), mip=mip)
 
 
 @pytest.mark.parametrize("through_sh", [0, 1])
@@ -310,6 +315,13 @@ def test_multiview_sh3_end_to_end(through_sh):
     """Three views of different sizes (ragged edge tiles), SH degree 3."""
     sc, cams, _ = synth.multiview_scene(seed=5, n=20000, n_views=3, sizes=[(200, 120), (131, 77), (96, 160)])
     compare_views(sc, cams, 3, pose_through_sh=through_sh, max_excl_frac=0.6)
+
+
+def test_multiview_sh3_mip_filter_end_to_end():
+    """The same three views with the integral-keeping 2-D filter (dilation 0.1):
+    small splats lose opacity, so the filter's gradient path is exercised."""
+    sc, cams, _ = synth.multiview_scene(seed=5, n=20000, n_views=3, sizes=[(200, 120), (131, 77), (96, 160)])
+    compare_views(sc, cams, 3, max_excl_frac=0.6, mip=1)
 
 
 @pytest.mark.parametrize("tile,schedule,fb,bb", [(8, 0, 64, 256), (8, 1, 256, 64), (16, 1, 64, 32),
