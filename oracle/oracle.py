@@ -519,6 +519,17 @@ def adam_step(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-15, mask=None
     return p2, m2, v2
 
 
+def lr_decay(lr_scale, mask, decay):
+    """Per-Gaussian learning-rate multipliers (App. A.3: learning rates are set
+    when a Gaussian is introduced and multiplied by the decay ratio every time
+    the sparse Adam step processes it): the rows in mask are multiplied by decay.
+    adam_step takes lr as the per-row product of the group rate and this
+    multiplier."""
+    s = np.array(lr_scale, np.float64)
+    s[np.asarray(mask, bool)] *= decay
+    return s
+
+
 def hat(w):
     return np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]], np.float64)
 

@@ -543,3 +543,20 @@ def test_mip_filter_single_gaussian_closed_form():
     # without the filter the same dilation leaves the opacity unchanged
     v0 = O.render_view(sc, cam, O.Config(sh_degree=0, mip_filter=0, dilation=s))
     np.testing.assert_allclose(v0["proj"]["opacity"][0], o, rtol=1e-12)
+
+
+def test_per_gaussian_learning_rate_decay():
+    """A Gaussian processed k times since its introduction has multiplier
+    decay^k; the first Adam step it takes moves it by lr * multiplier * sign(g)."""
+    rng = np.random.default_rng(0)
+    n, decay = 50, 0.99
+    s = np.ones(n)
+    seen = np.zeros(n, int)
+    for _ in range(7):
+        mask = rng.random(n) < 0.6
+        s = O.lr_decay(s, mask, decay)
+        seen += mask
+    np.testing.assert_allclose(s, decay ** seen, rtol=1e-14)
+    p, g = rng.standard_normal(n), rng.standard_normal(n)
+    p1, _, _ = O.adam_step(p, g, np.zeros(n), np.zeros(n), 1, 0.01 * s)
+    np.testing.assert_allclose(p1, p - 0.01 * s * np.sign(g), rtol=0, atol=1e-12)
