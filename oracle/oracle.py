@@ -480,6 +480,14 @@ def anchor_merge(scene, too_fine, seed, radius, k=3, margin=1e-5):
                 selected=sel, claim=claim, amb=amb)
 
 
+def cull_opacity(mean_opa, min_opacity, margin=1e-6):
+    """Opacity culling (Sec. 4.3, as in 3DGS): the Gaussians whose opacity
+    sigmoid(logit) is at least min_opacity are kept, in index order. Returns
+    (kept indices, ambiguous: opacity within margin (relative) of the bound)."""
+    o = 1.0 / (1.0 + np.exp(-np.asarray(mean_opa, np.float64)[:, 3]))
+    return np.nonzero(o >= min_opacity)[0], np.abs(o - min_opacity) < margin * min_opacity
+
+
 def anchor_blend_weight(d1, d2, overlap=0.1):
     """Blending weight of the closest anchor (Sec. 4.4): r = d1 / d2 (d1 <= d2);
     1 for r < 1 - o, else 1 - (r - (1 - o)) * 0.5 / o (0.5 at r = 1)."""

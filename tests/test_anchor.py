@@ -231,3 +231,15 @@ def test_anchor_blend_weight_and_opacity_scaling():
     torch.cuda.synchronize()
     got = 1 / (1 + np.exp(-logit[:, 3].cpu().numpy().astype(np.float64)))
     np.testing.assert_allclose(got, 0.25 * o, rtol=1e-5)
+
+
+
+def test_cull_opacity_hand_case():
+    logits = np.array([-6.0, -4.0, 0.0, -5.2933, 3.0, -10.0])  # sigmoid: 0.00247, 0.018, 0.5, 0.00500.., 0.95, 4.5e-5
+    mo = np.zeros((6, 4))
+    mo[:, 3] = logits
+    kept, amb = O.cull_opacity(mo, 0.005)
+    o = 1 / (1 + np.exp(-logits))
+    np.testing.assert_array_equal(kept, [i for i in range(6) if o[i] >= 0.005])
+    np.testing.assert_array_equal(kept, [1, 2, 3, 4])
+    assert not amb.any()
