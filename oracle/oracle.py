@@ -527,6 +527,31 @@ def adam_step(p, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-15, mask=None
     return p2, m2, v2
 
 
+def downsample(image, factor):
+    """Coarse-to-fine training image (Sec. 4.3, 2^l downsampling): output pixel
+    (I, J) of [3][ceil(H/f)][ceil(W/f)] is the mean of the input pixels of the
+    f x f block it covers (a partial block at a ragged edge averages the pixels
+    it has)."""
+    image = np.asarray(image, np.float64)
+    _, H, W = image.shape
+    h, w = -(-H // factor), -(-W // factor)
+    out = np.zeros((3, h, w))
+    for I in range(h):
+        for J in range(w):
+            out[:, I, J] = image[:, I * factor:(I + 1) * factor, J * factor:(J + 1) * factor].mean(axis=(1, 2))
+    return out
+
+
+def downsample_camera(cam, factor):
+    """The camera of a 2^l-downsampled image: intrinsics divided by the factor,
+    size rounded up (pixel centres stay at I + 0.5)."""
+    c = dict(cam)
+    for k in ("fx", "fy", "cx", "cy"):
+        c[k] = cam[k] / factor
+    c["width"], c["height"] = -(-cam["width"] // factor), -(-cam["height"] // factor)
+    return c
+
+
 def lr_decay(lr_scale, mask, decay):
     """Per-Gaussian learning-rate multipliers (App. A.3: learning rates are set
     when a Gaussian is introduced and multiplied by the decay ratio every time

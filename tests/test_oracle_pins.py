@@ -560,3 +560,29 @@ def test_per_gaussian_learning_rate_decay():
     p, g = rng.standard_normal(n), rng.standard_normal(n)
     p1, _, _ = O.adam_step(p, g, np.zeros(n), np.zeros(n), 1, 0.01 * s)
     np.testing.assert_allclose(p1, p - 0.01 * s * np.sign(g), rtol=0, atol=1e-12)
+
+
+def test_downsample_hand_cases():
+    """Factor 1 is the identity; a constant stays constant; a 4x4 ramp gives the
+    block means; a 5x3 frame at factor 2 averages its partial edge blocks."""
+    rng = np.random.default_rng(1)
+    im = rng.random((3, 6, 7))
+    np.testing.assert_array_equal(O.downsample(im, 1), im)
+    np.testing.assert_allclose(O.downsample(np.full((3, 9, 5), 0.25), 4), np.full((3, 3, 2), 0.25))
+    ramp = np.tile(np.arange(16.0).reshape(4, 4), (3, 1, 1))
+    np.testing.assert_allclose(O.downsample(ramp, 2)[0], [[2.5, 4.5], [10.5, 12.5]])
+    r = np.tile(np.arange(15.0).reshape(3, 5), (3, 1, 1))
+    np.testing.assert_allclose(O.downsample(r, 2)[0], [[3.0, 5.0, 6.5], [10.5, 12.5, 14.0]])
+
+
+def test_downsampled_camera_keeps_pixel_centres():
+    """A world point at the centre of full-resolution pixel block (2I.., 2J..)
+    projects to the centre of downsampled pixel (I, J)."""
+    cam = synth.camera(np.eye(3), np.zeros(3), 40.0, 32, 24, dtype=np.float64)
+    c2 = O.downsample_camera(cam, 4)
+    for I, J in ((0, 0), (3, 5), (5, 7)):
+        u, v = 4 * J + 2.0, 4 * I + 2.0  # centre of the block in full-resolution pixel coordinates
+        z = 3.0
+        p = [(u - cam["cx"]) * z / cam["fx"], (v - cam["cy"]) * z / cam["fy"], z]
+        assert abs(c2["fx"] * p[0] / z + c2["cx"] - (J + 0.5)) < 1e-12
+        assert abs(c2["fy"] * p[1] / z + c2["cy"] - (I + 0.5)) < 1e-12
