@@ -339,13 +339,25 @@ int gs_anchor_load(const gs_gaussians* host_params, const gs_gaussians* host_m, 
  *  - Claimed Gaussians leave the set; all others are copied unchanged. The
  *    output keeps index order; *n_out (device int64) = its size (<= in->n).
  * out (and m_out, v_out) need in->n rows. m_in, v_in, m_out, v_out: the Adam
- * moments (all four or none); merged rows get zero moments. radius > 0,
- * 1 <= k <= 8. ws: gs_anchor_merge_workspace_size(in->n, k) bytes. */
+ * moments (all four or none); merged rows get zero moments. lr_in, lr_out:
+ * the per-Gaussian rate multipliers of gs_adam_step (both or none); merged
+ * rows restart at 1. radius > 0, 1 <= k <= 8. ws:
+ * gs_anchor_merge_workspace_size(in->n, k) bytes. */
 size_t gs_anchor_merge_workspace_size(int64_t n, int32_t k);
-int gs_anchor_merge(const gs_gaussians* in, const gs_gaussians* m_in, const gs_gaussians* v_in,
+int gs_anchor_merge(const gs_gaussians* in, const gs_gaussians* m_in, const gs_gaussians* v_in, const float* lr_in,
                     const uint8_t* too_fine, float radius, int32_t k, uint64_t seed, const gs_gaussians* out,
-                    const gs_gaussians* m_out, const gs_gaussians* v_out, int64_t* n_out, void* ws, size_t ws_bytes,
-                    void* stream);
+                    const gs_gaussians* m_out, const gs_gaussians* v_out, float* lr_out, int64_t* n_out, void* ws,
+                    size_t ws_bytes, void* stream);
+
+/* Opacity culling (Sec. 4.3, as in 3DGS): keeps the Gaussians with
+ * sigmoid(logit) >= min_opacity, in index order, with their Adam moments and
+ * rate multipliers when given (m/v: all four or none; lr: both or none);
+ * *n_out (device int64) = the kept count. out needs in->n rows. ws:
+ * gs_cull_opacity_workspace_size(in->n) bytes. */
+size_t gs_cull_opacity_workspace_size(int64_t n);
+int gs_cull_opacity(const gs_gaussians* in, const gs_gaussians* m_in, const gs_gaussians* v_in, const float* lr_in,
+                    float min_opacity, const gs_gaussians* out, const gs_gaussians* m_out, const gs_gaussians* v_out,
+                    float* lr_out, int64_t* n_out, void* ws, size_t ws_bytes, void* stream);
 
 /* Anchor blending for novel views (Sec. 4.4, Eq. of w(r)): with d1 <= d2 the
  * distances of the camera to the two closest anchors, r = d1 / d2 and overlap
@@ -469,15 +481,20 @@ int gs_mlp_tc_error(int32_t* out);
 typedef struct gs_adam_config {
     float lr_mean, lr_opacity, lr_scale, lr_rot, lr_sh_dc, lr_sh_rest;
     float beta1, beta2, eps;
+    float decay; /* per-Gaussian rate decay (App. A.3): with lr_scale, each processed Gaussian's multiplier
+                    is multiplied by decay after its update (1 = none) */
 } gs_adam_config;
 
 /* Sparse Adam over Gaussians with visible[g] != 0 (others untouched); params,
- * m, v in the gs_gaussians layout. The step number (>= 1, for the bias
+ * m, v in the gs_gaussians layout. lr_scale (optional, device float [n]):
+ * per-Gaussian multiplier of every group rate, set to 1 when a Gaussian is
+ * introduced and multiplied by cfg->decay after each step that processes it
+ * (App. A.3). The step number (>= 1, for the bias
  * correction) is `step`, or, when step_dev is non-NULL, the device int32 it
  * points to (so a captured CUDA graph sees the current step; advance it with
  * gs_counter_add). */
 int gs_adam_step(const gs_gaussians* params, const gs_grads* grads, const gs_gaussians* m, const gs_gaussians* v,
-                 const gs_adam_config* cfg, int32_t step, const int32_t* step_dev, void* stream);
+                 const gs_adam_config* cfg, int32_t step, const int32_t* step_dev, float* lr_scale, void* stream);
 
 /* Pose update: Adam on the tangent gradient dL_dpose [n_views][6] with moments
  * m, v [n_views][6], then T_cw <- exp(delta^) T_cw with delta the Adam step;
@@ -499,6 +516,14 @@ int gs_pose_apply(const gs_camera* cams_ref, const float* xi, int32_t n_views, g
  * dL_dxi = J_l(xi)^T dL_ddelta, J_l the left Jacobian of SE(3) (closed form,
  * FP64). All arrays [n_views][6] on the device; dL_dxi may equal dL_ddelta. */
 int gs_pose_tangent_grad(const float* xi, const float* dL_ddelta, int32_t n_views, float* dL_dxi, void* stream);
+
+/* Coarse-to-fine training (Sec. 4.3: a new image is first used with 2^l
+ * downsampling, l decremented every five iterations): out
+ * [3][ceil(height/factor)][ceil(width/factor)] = the mean of each factor x
+ * factor block of image [3][height][width] (partial blocks at ragged edges
+ * average the pixels they have). The matching camera divides fx, fy, cx, cy
+ * by the factor; pixel centres stay at I + 0.5. */
+int gs_downsample(const float* image, int32_t width, int32_t height, int32_t factor, float* out, void* stream);
 
 /* counter[0] += delta on the device (advances a graph-visible step counter). */
 int gs_counter_add(int32_t* counter, int32_t delta, void* stream);

@@ -226,7 +226,8 @@ __global__ void k_merge_write(const float4* __restrict__ mo_in, const float4* __
                               const float4* __restrict__ v_q, const float4* __restrict__ v_sh,
                               const uint32_t* __restrict__ sel, const int32_t* __restrict__ prop,
                               const uint32_t* __restrict__ claim, const uint32_t* __restrict__ keep,
-                              const uint32_t* __restrict__ pos, int64_t n, int k, float4* __restrict__ o_mo,
+                              const uint32_t* __restrict__ pos, int64_t n, int k, const float* __restrict__ lr_in,
+                              float* __restrict__ lr_out, float4* __restrict__ o_mo,
                               float4* __restrict__ o_sc, float4* __restrict__ o_q, float4* __restrict__ o_sh,
                               float4* __restrict__ om_mo, float4* __restrict__ om_sc, float4* __restrict__ om_q,
                               float4* __restrict__ om_sh, float4* __restrict__ ov_mo, float4* __restrict__ ov_sc,
@@ -235,6 +236,7 @@ __global__ void k_merge_write(const float4* __restrict__ mo_in, const float4* __
     if (i >= n || !keep[i]) return;
     const int64_t o = pos[i];
     const bool moments = om_mo != nullptr;
+    if (lr_out) lr_out[o] = sel[i] ? 1.f : lr_in[i];  // a merged Gaussian is a new primitive
     if (!sel[i]) {  // unchanged, with its optimiser state
         o_mo[o] = mo_in[i]; o_sc[o] = sc_in[i]; o_q[o] = q_in[i];
         for (int r = 0; r < 12; r++) o_sh[12 * o + r] = sh_in[12 * i + r];
@@ -306,6 +308,39 @@ __global__ void k_merge_write(const float4* __restrict__ mo_in, const float4* __
 
 __global__ void k_merge_count(const uint32_t* total, int64_t* n_out) { *n_out = *total; }
 
+__global__ void k_cull_keep(const float4* __restrict__ mean_opa, int64_t n, float min_opacity,
+                            uint32_t* __restrict__ keep) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) keep[i] = 1.f / (1.f + expf(-mean_opa[i].w)) >= min_opacity ? 1u : 0u;
+}
+
+// Copies the kept rows (and, when given, their Adam moments and rate
+// multipliers) to their compacted positions.
+__global__ void k_compact_rows(const uint32_t* __restrict__ keep, const uint32_t* __restrict__ pos, int64_t n,
+                               const float4* __restrict__ mo, const float4* __restrict__ sc,
+                               const float4* __restrict__ q, const float4* __restrict__ sh,
+                               const float4* __restrict__ m_mo, const float4* __restrict__ m_sc,
+                               const float4* __restrict__ m_q, const float4* __restrict__ m_sh,
+                               const float4* __restrict__ v_mo, const float4* __restrict__ v_sc,
+                               const float4* __restrict__ v_q, const float4* __restrict__ v_sh,
+                               const float* __restrict__ lr_in, float4* __restrict__ o_mo, float4* __restrict__ o_sc,
+                               float4* __restrict__ o_q, float4* __restrict__ o_sh, float4* __restrict__ om_mo,
+                               float4* __restrict__ om_sc, float4* __restrict__ om_q, float4* __restrict__ om_sh,
+                               float4* __restrict__ ov_mo, float4* __restrict__ ov_sc, float4* __restrict__ ov_q,
+                               float4* __restrict__ ov_sh, float* __restrict__ lr_out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !keep[i]) return;
+    const int64_t o = pos[i];
+    o_mo[o] = mo[i]; o_sc[o] = sc[i]; o_q[o] = q[i];
+    for (int r = 0; r < 12; r++) o_sh[12 * o + r] = sh[12 * i + r];
+    if (om_mo) {
+        om_mo[o] = m_mo[i]; om_sc[o] = m_sc[i]; om_q[o] = m_q[i];
+        ov_mo[o] = v_mo[i]; ov_sc[o] = v_sc[i]; ov_q[o] = v_q[i];
+        for (int r = 0; r < 12; r++) { om_sh[12 * o + r] = m_sh[12 * i + r]; ov_sh[12 * o + r] = v_sh[12 * i + r]; }
+    }
+    if (lr_out) lr_out[o] = lr_in[i];
+}
+
 __global__ void k_scale_opacity(float4* __restrict__ mean_opa, int64_t n, float w) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -361,6 +396,65 @@ extern "C" int gs_scale_opacity(float* mean_opa, int64_t n, float w, void* strea
     return GS_OK;
 }
 
+extern "C" size_t gs_cull_opacity_workspace_size(int64_t n) {
+    if (n < 0) return 0;
+    Carve c{nullptr, 0, 0};
+    c.take<uint32_t>(n);
+    c.take<uint32_t>(n);
+    c.take<uint32_t>(4);
+    c.take<char>(scan_workspace_bytes(n));
+    return c.used;
+}
+
+extern "C" int gs_cull_opacity(const gs_gaussians* in, const gs_gaussians* m_in, const gs_gaussians* v_in,
+                               const float* lr_in, float min_opacity, const gs_gaussians* out,
+                               const gs_gaussians* m_out, const gs_gaussians* v_out, float* lr_out, int64_t* n_out,
+                               void* ws, size_t ws_bytes, void* stream) {
+    auto ok = [](const gs_gaussians* g) { return g && g->mean_opa && g->scale && g->quat && g->sh; };
+    if (!ok(in) || !ok(out) || !n_out || in->n < 0 || out->n < in->n || !(min_opacity >= 0.f) ||
+        in->n > (int64_t)UINT32_MAX || !lr_in != !lr_out)
+        return GS_ERR_INVALID_ARG;
+    const bool moments = m_in || v_in || m_out || v_out;
+    if (moments && !(ok(m_in) && ok(v_in) && ok(m_out) && ok(v_out) && m_in->n == in->n && v_in->n == in->n &&
+                     m_out->n >= in->n && v_out->n >= in->n))
+        return GS_ERR_INVALID_ARG;
+    const int64_t n = in->n;
+    Carve c{(char*)ws, 0, ws_bytes};
+    uint32_t* keep = c.take<uint32_t>(n);
+    uint32_t* pos = c.take<uint32_t>(n);
+    uint32_t* total = c.take<uint32_t>(4);
+    void* scan_ws = c.take<char>(scan_workspace_bytes(n));
+    if (!ws || !c.ok() || ((uintptr_t)ws & 255)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (n == 0) {
+        cudaMemsetAsync(n_out, 0, sizeof(int64_t), s);
+        GS_CUDA_CHECK_LAUNCH();
+        return GS_OK;
+    }
+    const unsigned nb = (unsigned)ceil_div(n, 256);
+    k_cull_keep<<<nb, 256, 0, s>>>((const float4*)in->mean_opa, n, min_opacity, keep);
+    count_launch();
+    scan_exclusive_u32(keep, pos, n, total, scan_ws, s);
+    auto f4 = [](const gs_gaussians* g, int f) -> const float4* {
+        if (!g) return nullptr;
+        return (const float4*)(f == 0 ? g->mean_opa : f == 1 ? g->scale : f == 2 ? g->quat : g->sh);
+    };
+    auto o4 = [](const gs_gaussians* g, int f) -> float4* {
+        if (!g) return nullptr;
+        return (float4*)(f == 0 ? g->mean_opa : f == 1 ? g->scale : f == 2 ? g->quat : g->sh);
+    };
+    k_compact_rows<<<nb, 256, 0, s>>>(keep, pos, n, f4(in, 0), f4(in, 1), f4(in, 2), f4(in, 3), f4(m_in, 0),
+                                      f4(m_in, 1), f4(m_in, 2), f4(m_in, 3), f4(v_in, 0), f4(v_in, 1), f4(v_in, 2),
+                                      f4(v_in, 3), lr_in, o4(out, 0), o4(out, 1), o4(out, 2), o4(out, 3),
+                                      o4(m_out, 0), o4(m_out, 1), o4(m_out, 2), o4(m_out, 3), o4(v_out, 0),
+                                      o4(v_out, 1), o4(v_out, 2), o4(v_out, 3), lr_out);
+    count_launch();
+    k_merge_count<<<1, 1, 0, s>>>(total, n_out);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
 extern "C" size_t gs_anchor_merge_workspace_size(int64_t n, int32_t k) {
     if (n < 0 || k < 1 || k > kMergeMaxK) return 0;
     size_t used = 0;
@@ -371,9 +465,9 @@ extern "C" size_t gs_anchor_merge_workspace_size(int64_t n, int32_t k) {
 static bool set_ok(const gs_gaussians* g) { return g && g->mean_opa && g->scale && g->quat && g->sh; }
 
 extern "C" int gs_anchor_merge(const gs_gaussians* in, const gs_gaussians* m_in, const gs_gaussians* v_in,
-                               const uint8_t* too_fine, float radius, int32_t k, uint64_t seed,
+                               const float* lr_in, const uint8_t* too_fine, float radius, int32_t k, uint64_t seed,
                                const gs_gaussians* out, const gs_gaussians* m_out, const gs_gaussians* v_out,
-                               int64_t* n_out, void* ws, size_t ws_bytes, void* stream) {
+                               float* lr_out, int64_t* n_out, void* ws, size_t ws_bytes, void* stream) {
     if (!set_ok(in) || !set_ok(out) || !too_fine || !n_out || in->n < 0 || out->n < in->n || !(radius > 0.f) ||
         k < 1 || k > kMergeMaxK || in->n > (int64_t)INT32_MAX)
         return GS_ERR_INVALID_ARG;
@@ -381,6 +475,7 @@ extern "C" int gs_anchor_merge(const gs_gaussians* in, const gs_gaussians* m_in,
     if (moments && !(set_ok(m_in) && set_ok(v_in) && set_ok(m_out) && set_ok(v_out) && m_in->n == in->n &&
                      v_in->n == in->n && m_out->n >= in->n && v_out->n >= in->n))
         return GS_ERR_INVALID_ARG;
+    if (!lr_in != !lr_out) return GS_ERR_INVALID_ARG;
     const int64_t n = in->n;
     size_t need = 0;
     MergeWs w = carve_merge((char*)ws, ws_bytes, n, k, &need);
@@ -414,7 +509,7 @@ extern "C" int gs_anchor_merge(const gs_gaussians* in, const gs_gaussians* m_in,
         moments ? f4(m_in->scale) : nullptr, moments ? f4(m_in->quat) : nullptr, moments ? f4(m_in->sh) : nullptr,
         moments ? f4(v_in->mean_opa) : nullptr, moments ? f4(v_in->scale) : nullptr,
         moments ? f4(v_in->quat) : nullptr, moments ? f4(v_in->sh) : nullptr, w.sel, w.prop, w.claim, w.keep, w.pos,
-        n, k, o4(out->mean_opa), o4(out->scale), o4(out->quat), o4(out->sh),
+        n, k, lr_in, lr_out, o4(out->mean_opa), o4(out->scale), o4(out->quat), o4(out->sh),
         moments ? o4(m_out->mean_opa) : nullptr, moments ? o4(m_out->scale) : nullptr,
         moments ? o4(m_out->quat) : nullptr, moments ? o4(m_out->sh) : nullptr,
         moments ? o4(v_out->mean_opa) : nullptr, moments ? o4(v_out->scale) : nullptr,

@@ -16,7 +16,8 @@ __global__ void __launch_bounds__(256) k_adam(float4* __restrict__ p_mo, float4*
                                               float4* __restrict__ v_mo, float4* __restrict__ v_sc,
                                               float4* __restrict__ v_q, float4* __restrict__ v_sh,
                                               const uint8_t* __restrict__ visible, int64_t n, gs_adam_config c,
-                                              float bc1, float bc2, const int32_t* __restrict__ step_dev) {
+                                              float bc1, float bc2, const int32_t* __restrict__ step_dev,
+                                              const float* __restrict__ lr_scale) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 15 * n) return;
     if (step_dev) {  // bias corrections of the step number held on the device
@@ -43,6 +44,10 @@ __global__ void __launch_bounds__(256) k_adam(float4* __restrict__ p_mo, float4*
                              : make_float4(c.lr_sh_rest, c.lr_sh_rest, c.lr_sh_rest, c.lr_sh_rest);
     }
     if (!visible[g]) return;
+    if (lr_scale) {
+        const float ls = lr_scale[g];
+        lr.x *= ls; lr.y *= ls; lr.z *= ls; lr.w *= ls;
+    }
     float4 p = P[row], gr = G[row], m = M[row], v = V[row];
     float* pp = &p.x;
     float* gg = &gr.x;
@@ -177,9 +182,16 @@ extern "C" int gs_counter_add(int32_t* counter, int32_t delta, void* stream) {
     return GS_OK;
 }
 
+// Each processed Gaussian's rate multiplier decays after the update (a
+// separate launch: every parameter row of a Gaussian reads the old value).
+__global__ void k_lr_decay(float* __restrict__ lr_scale, const uint8_t* __restrict__ visible, int64_t n, float d) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && visible[i]) lr_scale[i] *= d;
+}
+
 extern "C" int gs_adam_step(const gs_gaussians* params, const gs_grads* grads, const gs_gaussians* m,
                             const gs_gaussians* v, const gs_adam_config* cfg, int32_t step, const int32_t* step_dev,
-                            void* stream) {
+                            float* lr_scale, void* stream) {
     if (!params || !grads || !m || !v || !cfg || (step < 1 && !step_dev) || params->n < 0) return GS_ERR_INVALID_ARG;
     if (m->n != params->n || v->n != params->n || !grads->visible) return GS_ERR_INVALID_ARG;
     const int64_t n = params->n;
@@ -191,8 +203,13 @@ extern "C" int gs_adam_step(const gs_gaussians* params, const gs_grads* grads, c
         (const float4*)grads->mean_opa, (const float4*)grads->scale, (const float4*)grads->quat,
         (const float4*)grads->sh, (float4*)m->mean_opa, (float4*)m->scale, (float4*)m->quat, (float4*)m->sh,
         (float4*)v->mean_opa, (float4*)v->scale, (float4*)v->quat, (float4*)v->sh, grads->visible, n, *cfg, bc1, bc2,
-        step_dev);
+        step_dev, lr_scale);
     count_launch();
+    if (lr_scale && cfg->decay != 1.f) {
+        k_lr_decay<<<(unsigned)ceil_div(n, 256), 256, 0, (cudaStream_t)stream>>>(lr_scale, grads->visible, n,
+                                                                                 cfg->decay);
+        count_launch();
+    }
     GS_CUDA_CHECK_LAUNCH();
     return GS_OK;
 }
@@ -330,6 +347,35 @@ extern "C" int gs_pose_tangent_grad(const float* xi, const float* dL_ddelta, int
                                     void* stream) {
     if (!xi || !dL_ddelta || !dL_dxi || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_INVALID_ARG;
     k_pose_tangent_grad<<<1, 64, 0, (cudaStream_t)stream>>>(xi, dL_ddelta, n_views, dL_dxi);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
+// Coarse-to-fine training image: out [3][ceil(H/f)][ceil(W/f)], each pixel the
+// mean of the input pixels of its f x f block (partial blocks at ragged edges).
+__global__ void k_downsample(const float* __restrict__ in, int W, int H, int f, int w, int h,
+                             float* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3LL * w * h) return;
+    const int ch = (int)(i / ((int64_t)w * h));
+    const int64_t rem = i % ((int64_t)w * h);
+    const int I = (int)(rem / w), J = (int)(rem % w);
+    const int y1 = min(H, (I + 1) * f), x1 = min(W, (J + 1) * f);
+    const float* src = in + (int64_t)ch * W * H;
+    float acc = 0.f;
+    for (int y = I * f; y < y1; y++)
+        for (int x = J * f; x < x1; x++) acc += src[(int64_t)y * W + x];
+    out[i] = acc / (float)((y1 - I * f) * (x1 - J * f));
+}
+
+extern "C" int gs_downsample(const float* image, int32_t width, int32_t height, int32_t factor, float* out,
+                             void* stream) {
+    if (!image || !out || width < 1 || height < 1 || factor < 1) return GS_ERR_INVALID_ARG;
+    const int w = (width + factor - 1) / factor, h = (height + factor - 1) / factor;
+    const int64_t n = 3LL * w * h;
+    k_downsample<<<(unsigned)ceil_div(n, 256), 256, 0, (cudaStream_t)stream>>>(image, width, height, factor, w, h,
+                                                                               out);
     count_launch();
     GS_CUDA_CHECK_LAUNCH();
     return GS_OK;

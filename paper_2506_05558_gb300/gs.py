@@ -34,7 +34,8 @@ EXPORTS = [
     "gs_mlp_patches", "gs_mlp_param_count", "gs_mlp_workspace_size", "gs_mlp_forward", "gs_mlp_train_step",
     "gs_mlp_gemm_bf16", "gs_mlp_tc_error", "gs_mlp_targets_workspace_size", "gs_mlp_targets", "gs_spawn_learned",
     "gs_pose_apply", "gs_pose_tangent_grad", "gs_anchor_merge_workspace_size", "gs_anchor_merge",
-    "gs_anchor_blend_weight", "gs_scale_opacity",
+    "gs_anchor_blend_weight", "gs_scale_opacity", "gs_cull_opacity_workspace_size", "gs_cull_opacity",
+    "gs_downsample",
 ]
 
 
@@ -84,7 +85,7 @@ class gs_grads(C.Structure):
 class gs_adam_config(C.Structure):
     _fields_ = [("lr_mean", C.c_float), ("lr_opacity", C.c_float), ("lr_scale", C.c_float), ("lr_rot", C.c_float),
                 ("lr_sh_dc", C.c_float), ("lr_sh_rest", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float),
-                ("eps", C.c_float)]
+                ("eps", C.c_float), ("decay", C.c_float)]
 
 
 class gs_spawn_config(C.Structure):
@@ -134,14 +135,18 @@ def lib():
                                         C.POINTER(gs_frame), C.POINTER(gs_config), C.POINTER(gs_image), P,
                                         C.POINTER(gs_grads), P, P, P, C.c_size_t, P]),
             "gs_adam_step": (C.c_int, [C.POINTER(gs_gaussians), C.POINTER(gs_grads), C.POINTER(gs_gaussians),
-                                       C.POINTER(gs_gaussians), C.POINTER(gs_adam_config), C.c_int32, P, P]),
+                                       C.POINTER(gs_gaussians), C.POINTER(gs_adam_config), C.c_int32, P, P, P]),
             "gs_pose_step": (C.c_int, [P, C.c_int32, P, P, P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
                                        C.c_int32, P, P]),
             "gs_counter_add": (C.c_int, [P, C.c_int32, P]),
+            "gs_downsample": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, P, P]),
             "gs_pose_apply": (C.c_int, [P, P, C.c_int32, P, P]),
             "gs_anchor_merge_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32]),
-            "gs_anchor_merge": (C.c_int, [C.POINTER(gs_gaussians)] * 3 + [P, C.c_float, C.c_int32, C.c_uint64] +
-                                [C.POINTER(gs_gaussians)] * 3 + [P, P, C.c_size_t, P]),
+            "gs_anchor_merge": (C.c_int, [C.POINTER(gs_gaussians)] * 3 + [P, P, C.c_float, C.c_int32, C.c_uint64] +
+                                [C.POINTER(gs_gaussians)] * 3 + [P, P, P, C.c_size_t, P]),
+            "gs_cull_opacity_workspace_size": (C.c_size_t, [C.c_int64]),
+            "gs_cull_opacity": (C.c_int, [C.POINTER(gs_gaussians)] * 3 + [P, C.c_float] +
+                                [C.POINTER(gs_gaussians)] * 3 + [P, P, P, C.c_size_t, P]),
             "gs_anchor_blend_weight": (C.c_float, [C.c_float, C.c_float, C.c_float]),
             "gs_scale_opacity": (C.c_int, [P, C.c_int64, C.c_float, P]),
             "gs_pose_tangent_grad": (C.c_int, [P, P, C.c_int32, P, P]),
@@ -501,13 +506,27 @@ def gs_anchor_merge_workspace_size(n: int, k: int = 3) -> int:
 
 def gs_anchor_merge(g: Gaussians, too_fine: torch.Tensor, radius: float, seed: int, out: Gaussians,
                     n_out: torch.Tensor, ws: torch.Tensor, k: int = 3, m=None, v=None, m_out=None, v_out=None,
-                    stream=None):
+                    lr=None, lr_out=None, stream=None):
     """Merges a random 1/(k+1) of the too-fine Gaussians with their k nearest
     too-fine neighbours into out (n_out: device int64 row count)."""
     a, o = g.c(), out.c()
     cs = [None if t is None else C.byref(t.c()) for t in (m, v, m_out, v_out)]
-    _check(lib().gs_anchor_merge(C.byref(a), cs[0], cs[1], _ptr(too_fine), radius, k, seed, C.byref(o), cs[2], cs[3],
-                                 _ptr(n_out), _ptr(ws), ws.numel(), _stream(stream)), "gs_anchor_merge")
+    _check(lib().gs_anchor_merge(C.byref(a), cs[0], cs[1], _ptr(lr), _ptr(too_fine), radius, k, seed, C.byref(o),
+                                 cs[2], cs[3], _ptr(lr_out), _ptr(n_out), _ptr(ws), ws.numel(), _stream(stream)),
+           "gs_anchor_merge")
+
+
+def gs_cull_opacity_workspace_size(n: int) -> int:
+    return int(lib().gs_cull_opacity_workspace_size(n))
+
+
+def gs_cull_opacity(g: Gaussians, min_opacity: float, out: Gaussians, n_out: torch.Tensor, ws: torch.Tensor, m=None,
+                    v=None, m_out=None, v_out=None, lr=None, lr_out=None, stream=None):
+    """Keeps the Gaussians with opacity >= min_opacity (compacted into out)."""
+    a, o = g.c(), out.c()
+    cs = [None if t is None else C.byref(t.c()) for t in (m, v, m_out, v_out)]
+    _check(lib().gs_cull_opacity(C.byref(a), cs[0], cs[1], _ptr(lr), min_opacity, C.byref(o), cs[2], cs[3],
+                                 _ptr(lr_out), _ptr(n_out), _ptr(ws), ws.numel(), _stream(stream)), "gs_cull_opacity")
 
 
 def gs_anchor_blend_weight(d1: float, d2: float, overlap: float = 0.1) -> float:
@@ -621,15 +640,15 @@ def gs_spawn_learned(image: torch.Tensor, mlp_out: torch.Tensor, width: int, hei
 
 
 def adam_config(lr_mean=1.6e-4, lr_opacity=0.05, lr_scale=5e-3, lr_rot=1e-3, lr_sh_dc=2.5e-3, lr_sh_rest=1.25e-4,
-                beta1=0.9, beta2=0.999, eps=1e-15) -> gs_adam_config:
-    return gs_adam_config(lr_mean, lr_opacity, lr_scale, lr_rot, lr_sh_dc, lr_sh_rest, beta1, beta2, eps)
+                beta1=0.9, beta2=0.999, eps=1e-15, decay=1.0) -> gs_adam_config:
+    return gs_adam_config(lr_mean, lr_opacity, lr_scale, lr_rot, lr_sh_dc, lr_sh_rest, beta1, beta2, eps, decay)
 
 
 def gs_adam_step(params: Gaussians, grads: Grads, m: Gaussians, v: Gaussians, cfg: gs_adam_config, step: int,
-                 stream=None, step_dev: torch.Tensor | None = None):
+                 stream=None, step_dev: torch.Tensor | None = None, lr_scale: torch.Tensor | None = None):
     a, b, c, d = params.c(), grads.c(), m.c(), v.c()
     _check(lib().gs_adam_step(C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(cfg), step, _ptr(step_dev),
-                              _stream(stream)), "gs_adam_step")
+                              _ptr(lr_scale), _stream(stream)), "gs_adam_step")
 
 
 def gs_pose_step(cams: torch.Tensor, n_views: int, dL_dpose: torch.Tensor, m: torch.Tensor, v: torch.Tensor,
@@ -646,6 +665,26 @@ def gs_pose_apply(cams_ref: torch.Tensor, xi: torch.Tensor, n_views: int, cams_o
 def gs_pose_tangent_grad(xi: torch.Tensor, dL_ddelta: torch.Tensor, n_views: int, dL_dxi: torch.Tensor, stream=None):
     _check(lib().gs_pose_tangent_grad(_ptr(xi), _ptr(dL_ddelta), n_views, _ptr(dL_dxi), _stream(stream)),
            "gs_pose_tangent_grad")
+
+
+def gs_downsample(image: torch.Tensor, width: int, height: int, factor: int, out: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """Block-mean downsampling of a planar [3][H][W] image by factor."""
+    w, h = -(-width // factor), -(-height // factor)
+    if out is None:
+        out = torch.empty((3 * h * w,), dtype=torch.float32, device=image.device)
+    _check(lib().gs_downsample(_ptr(image), width, height, factor, _ptr(out), _stream(stream)), "gs_downsample")
+    return out
+
+
+def downsample_cameras(cams: torch.Tensor, factor: int) -> torch.Tensor:
+    """Cameras of factor-downsampled images (intrinsics / factor, sizes rounded up)."""
+    cs = cameras_from_tensor(cams)
+    for c in cs:
+        for k in ("fx", "fy", "cx", "cy"):
+            c[k] = c[k] / factor
+        c["width"], c["height"] = -(-c["width"] // factor), -(-c["height"] // factor)
+    return cameras_tensor(cs, cams.device)
 
 
 def gs_counter_add(counter: torch.Tensor, delta: int = 1, stream=None):

@@ -56,6 +56,7 @@ class GaussianStore:
         self.p = gs.Gaussians.zeros(capacity, device)
         self.m = gs.Gaussians.zeros(capacity, device)
         self.v = gs.Gaussians.zeros(capacity, device)
+        self.lr = torch.ones((capacity,), dtype=torch.float32, device=device)  # per-Gaussian rate multipliers
         self.n = 0
 
     @staticmethod
@@ -75,6 +76,7 @@ class GaussianStore:
         for st in (self.m, self.v):
             for t in (st.mean_opa, st.scale, st.quat, st.sh):
                 t[self.n:self.n + k].zero_()
+        self.lr[self.n:self.n + k] = 1.0  # rates start fresh when a Gaussian is introduced
         self.n += k
         return k
 
@@ -101,16 +103,23 @@ def render_depth(g: gs.Gaussians, cam: torch.Tensor, size, cfg, device="cuda"):
 class OnTheFly:
     def __init__(self, capacity: int, size, window: int = 4, iters: int = 30, mode: str = "plain",
                  mlp_warmup_frames: int = 3, mlp_steps: int = 40, keep_threshold: float = 0.05, seed: int = 7,
-                 anchor_tau: float = 1.0, anchor_share: float = 0.4, merge_radius: float = 0.5, device="cuda"):
+                 anchor_tau: float = 1.0, anchor_share: float = 0.4, merge_radius: float = 0.5,
+                 coarse_to_fine: int = 0, mip_filter: bool = False, lr_decay: float = 1.0,
+                 min_opacity: float = 0.0, device="cuda"):
         self.store = GaussianStore(capacity, device)
         self.W, self.H = size
         self.window = window
         self.iters = iters
         self.mode = mode
-        self.cfg = gs.config(sh_degree=0)
-        self.adam = gs.adam_config(lr_mean=1e-3, lr_opacity=0.05, lr_scale=5e-3, lr_rot=1e-3, lr_sh_dc=5e-3,
+        # coarse_to_fine = l: a new frame is first trained at 2^l downsampling, l
+        # decremented every five iterations (Sec. 4.3); mip_filter: the
+        # integral-keeping 2-D filter that makes the multi-scale training consistent
+        self.c2f = coarse_to_fine
+        self.cfg = gs.config(sh_degree=0, mip_filter=1, dilation=0.1) if mip_filter else gs.config(sh_degree=0)
+        self.min_opacity = min_opacity
+        self.adam = gs.adam_config(decay=lr_decay, lr_mean=1e-3, lr_opacity=0.05, lr_scale=5e-3, lr_rot=1e-3, lr_sh_dc=5e-3,
                                    lr_sh_rest=0.0)
-        self.frames = []  # (image [3HW], camera tensor)
+        self.frames = []  # [image [3HW], camera tensor, coarse-to-fine level]
         self.seed = seed
         self.device = device
         self.keep_threshold = keep_threshold
@@ -162,7 +171,7 @@ class OnTheFly:
         ws = gs.workspace(gs.gs_anchor_merge_workspace_size(g.n, 3), self.device)
         go, mo, vo = out.p, out.m, out.v
         gs.gs_anchor_merge(g, fine, self.merge_radius, self.seed * 7919 + frame_idx, go, n_out, ws, m=m, v=v,
-                           m_out=mo, v_out=vo)
+                           m_out=mo, v_out=vo, lr=self.store.lr[:g.n], lr_out=out.lr)
         out.n = int(n_out.item())
         before = g.n
         self.store = out
@@ -219,26 +228,58 @@ class OnTheFly:
         return k, use_learned
 
     def _optimise(self, iters):
+        """iters iterations over the sliding window; each frame renders at its
+        current coarse-to-fine level, lowered every five iterations."""
         g, m, v = self.store.active()
         frames = self.frames[-self.window:]
-        sizes = [(self.W, self.H)] * len(frames)
-        cams = torch.cat([c for _, c in frames])
-        targets = torch.cat([im for im, _ in frames])
-        r = Rasterizer(g.n, sizes, 1 << 18, self.cfg, self.device)
-        r.fit_capacity(g, cams)
-        dL = torch.zeros_like(r.img.color)
         loss = torch.zeros(1, device=self.device)
         ws = gs.workspace(4 * 4096, self.device)
-        for _ in range(iters):
-            r.forward(g, cams)
-            gs.gs_l1_loss(r.img.color, targets, dL, loss, ws)
-            r.backward(g, cams, dL)
-            gs.gs_adam_step(g, r.grads, m, v, self.adam, 0, step_dev=self.step_dev)
-            gs.gs_counter_add(self.step_dev, 1)
-            self.iter_count += 1
-        if r.status() != gs.GS_OK:
+        lr = self.store.lr[:g.n] if self.adam.decay != 1.0 else None
+        done = 0
+        while done < iters:
+            run = min(5, iters - done) if self.c2f else iters
+            sizes, cams, targets = [], [], []
+            for fr in frames:
+                f = 1 << fr[2]
+                if f > 1:
+                    cams.append(gs.downsample_cameras(fr[1], f))
+                    targets.append(gs.gs_downsample(fr[0], self.W, self.H, f))
+                    sizes.append((-(-self.W // f), -(-self.H // f)))
+                else:
+                    cams.append(fr[1])
+                    targets.append(fr[0])
+                    sizes.append((self.W, self.H))
+            cams, targets = torch.cat(cams), torch.cat(targets)
+            r = Rasterizer(g.n, sizes, 1 << 18, self.cfg, self.device)
             r.fit_capacity(g, cams)
+            dL = torch.zeros_like(r.img.color)
+            for _ in range(run):
+                r.forward(g, cams)
+                gs.gs_l1_loss(r.img.color, targets, dL, loss, ws)
+                r.backward(g, cams, dL)
+                gs.gs_adam_step(g, r.grads, m, v, self.adam, 0, step_dev=self.step_dev, lr_scale=lr)
+                gs.gs_counter_add(self.step_dev, 1)
+                self.iter_count += 1
+            done += run
+            for fr in frames:
+                fr[2] = max(0, fr[2] - 1)
         return float(loss.item())
+
+    def _cull(self):
+        """Opacity culling (Sec. 4.3): Gaussians below min_opacity leave the set
+        with their optimiser state."""
+        if self.min_opacity <= 0 or self.store.n == 0:
+            return 0
+        g, m, v = self.store.active()
+        out = GaussianStore(self.store.cap, self.device)
+        n_out = torch.zeros((1,), dtype=torch.int64, device=self.device)
+        ws = gs.workspace(gs.gs_cull_opacity_workspace_size(g.n), self.device)
+        gs.gs_cull_opacity(g, self.min_opacity, out.p, n_out, ws, m=m, v=v, m_out=out.m, v_out=out.v,
+                           lr=self.store.lr[:g.n], lr_out=out.lr)
+        out.n = int(n_out.item())
+        removed = g.n - out.n
+        self.store = out
+        return removed
 
     def _train_mlp(self, image, n0, k, cam):
         """Targets from this frame's spawns that are still opaque after the
@@ -270,15 +311,16 @@ class OnTheFly:
         k, learned = self._spawn(image, render, depth, cam, frame_idx)
         n0 = self.store.n
         k = self.store.append(self.spawned, k)
-        self.frames.append((image, cam))
+        self.frames.append([image, cam, self.c2f])
         loss = self._optimise(self.iters)
         mlp_loss = None
         if self.mode == "learned" and not learned:
             # the direct-sampling spawns of the warm-up frames that survived
-            # the optimisation teach the proposal
+            # the optimisation teach the proposal (before culling moves rows)
             mlp_loss = self._train_mlp(image, n0, k, cam)
+        culled = self._cull()
         self.log.append(dict(frame=frame_idx, spawned=k, n=self.store.n, loss=loss, learned=learned,
-                             mlp_loss=mlp_loss, iters=self.iter_count, anchor=anchor))
+                             mlp_loss=mlp_loss, iters=self.iter_count, anchor=anchor, culled=culled))
         self.prev_cam = cam
 
     def evaluate(self, frames):

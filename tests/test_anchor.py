@@ -189,7 +189,8 @@ def test_anchor_merge_matches_oracle(with_moments):
     if with_moments:
         m = gs.Gaussians(*[t.clone().normal_() for t in (g.mean_opa, g.scale, g.quat, g.sh)])
         v = gs.Gaussians(*[t.clone().uniform_() for t in (g.mean_opa, g.scale, g.quat, g.sh)])
-        kw = dict(m=m, v=v, m_out=gs.Gaussians.zeros(n), v_out=gs.Gaussians.zeros(n))
+        kw = dict(m=m, v=v, m_out=gs.Gaussians.zeros(n), v_out=gs.Gaussians.zeros(n),
+                  lr=torch.rand(n, device="cuda") * 0.5 + 0.25, lr_out=torch.zeros(n, device="cuda"))
     gs.gs_anchor_merge(g, torch.tensor(fine.astype(np.uint8), device="cuda"), radius, seed, out, n_out, ws, **kw)
     torch.cuda.synchronize()
     k = int(n_out.item())
@@ -207,6 +208,9 @@ def test_anchor_merge_matches_oracle(with_moments):
                 assert not mo_[~kept].any()
     mrg = ~kept
     assert mrg.sum() > 500
+    if with_moments:
+        lr_out = kw["lr_out"][:k].cpu().numpy()
+        assert np.array_equal(lr_out[kept], kw["lr"].cpu().numpy()[src][kept]) and (lr_out[mrg] == 1.0).all()
     mo = out.mean_opa[:k].cpu().numpy()[mrg]
     assert_close(mo[:, :3], ref["mean"][mrg], 1e-5, what="merged mean")
     assert_close(1 / (1 + np.exp(-mo[:, 3].astype(np.float64))), ref["opacity"][mrg], 1e-4, what="merged opacity")
@@ -243,3 +247,34 @@ def test_cull_opacity_hand_case():
     np.testing.assert_array_equal(kept, [i for i in range(6) if o[i] >= 0.005])
     np.testing.assert_array_equal(kept, [1, 2, 3, 4])
     assert not amb.any()
+
+
+
+@pytest.mark.gpu
+def test_cull_opacity_matches_oracle():
+    """Kept rows, their order, Adam moments and rate multipliers bit-exact."""
+    from paper_2506_05558_gb300 import build
+    build.build()
+    rng = np.random.default_rng(3)
+    n = 50_000
+    sc, _, _ = synth.multiview_scene(seed=2, n=n, n_views=1, sizes=[(64, 48)])
+    sc.mean_opa[:, 3] = rng.normal(-4, 2, n)
+    kept, amb = O.cull_opacity(sc.mean_opa.astype(np.float32).astype(np.float64), 0.005, margin=1e-5)
+    assert not amb.any()
+    g = gs.Gaussians.from_scene(sc)
+    m = gs.Gaussians(*[t.clone().normal_() for t in (g.mean_opa, g.scale, g.quat, g.sh)])
+    v = gs.Gaussians(*[t.clone().uniform_() for t in (g.mean_opa, g.scale, g.quat, g.sh)])
+    lr = torch.rand(n, device="cuda")
+    out, mo, vo = gs.Gaussians.zeros(n), gs.Gaussians.zeros(n), gs.Gaussians.zeros(n)
+    lr_out = torch.zeros(n, device="cuda")
+    n_out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ws = gs.workspace(gs.gs_cull_opacity_workspace_size(n))
+    gs.gs_cull_opacity(g, 0.005, out, n_out, ws, m=m, v=v, m_out=mo, v_out=vo, lr=lr, lr_out=lr_out)
+    torch.cuda.synchronize()
+    k = int(n_out.item())
+    assert k == len(kept) and 0.2 * n < k < 0.9 * n
+    for src_set, dst_set in ((g, out), (m, mo), (v, vo)):
+        for name in ("mean_opa", "scale", "quat", "sh"):
+            assert np.array_equal(getattr(dst_set, name)[:k].cpu().numpy(),
+                                  getattr(src_set, name).cpu().numpy()[kept]), name
+    assert np.array_equal(lr_out[:k].cpu().numpy(), lr.cpu().numpy()[kept])

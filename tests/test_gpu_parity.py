@@ -429,7 +429,10 @@ def test_l1_loss_matches_oracle():
         assert np.array_equal(dL.cpu().numpy(), ref_g.astype(np.float32))
 
 
-def test_adam_matches_oracle():
+@pytest.mark.parametrize("decay", [None, 0.97])
+def test_adam_matches_oracle(decay):
+    """Three sparse Adam steps; optionally with per-Gaussian rate multipliers
+    that decay each time a Gaussian is processed."""
     rng = np.random.default_rng(4)
     n = 3000
     params = {k: rng.standard_normal((n, w)).astype(np.float32) for k, w in
@@ -439,7 +442,9 @@ def test_adam_matches_oracle():
     M, V = gs.Gaussians.zeros(n), gs.Gaussians.zeros(n)
     vis = rng.random(n) < 0.7
     cfg = gs.adam_config(lr_mean=0.01, lr_opacity=0.05, lr_scale=0.005, lr_rot=0.001, lr_sh_dc=0.0025,
-                         lr_sh_rest=0.000125)
+                         lr_sh_rest=0.000125, decay=decay or 1.0)
+    ls = rng.uniform(0.5, 1.0, n) if decay else np.ones(n)
+    ls_dev = t32(ls) if decay else None
     ref = {k: (params[k].astype(np.float64), np.zeros_like(params[k], np.float64),
                np.zeros_like(params[k], np.float64)) for k in params}
     lrs = {"mean_opa": [0.01] * 3 + [0.05], "scale": [0.005] * 3 + [0.0], "quat": [0.001] * 4,
@@ -449,14 +454,18 @@ def test_adam_matches_oracle():
         grads["scale"][:, 3] = 0
         G = gs.Grads(*[t32(grads[k]) for k in ("mean_opa", "scale", "quat", "sh")],
                      torch.from_numpy(vis.astype(np.uint8)).cuda())
-        gs.gs_adam_step(P, G, M, V, cfg, step)
+        gs.gs_adam_step(P, G, M, V, cfg, step, lr_scale=ls_dev)
         for k in params:
             p, m, v = ref[k]
             lr = np.array(lrs[k])
-            out = [O.adam_step(p[:, j], grads[k][:, j], m[:, j], v[:, j], step, lr[j], eps=1e-15, mask=vis)
+            out = [O.adam_step(p[:, j], grads[k][:, j], m[:, j], v[:, j], step, lr[j] * ls, eps=1e-15, mask=vis)
                    for j in range(p.shape[1])]
             ref[k] = tuple(np.stack([o[i] for o in out], 1) for i in range(3))
+        if decay:
+            ls = O.lr_decay(ls, vis, decay)
     torch.cuda.synchronize()
+    if decay:
+        assert_close(ls_dev.cpu().numpy(), ls, 1e-6, what="rate multipliers")
     for k, t in (("mean_opa", P.mean_opa), ("scale", P.scale), ("quat", P.quat), ("sh", P.sh)):
         assert_close(t.cpu().numpy(), ref[k][0], 1e-5, what=k)
 
@@ -477,3 +486,13 @@ def test_pose_step_matches_oracle_retraction():
         R, t = O.retract_pose(cams[i]["R"], cams[i]["t"], step)
         assert np.abs(out[i]["R"] - R).max() < 2e-6
         assert np.abs(out[i]["t"] - t).max() < 2e-5 * max(1.0, np.abs(t).max())
+
+
+def test_downsample_matches_oracle():
+    rng = np.random.default_rng(9)
+    for W, H, f in ((64, 48, 2), (67, 45, 4), (31, 17, 8), (16, 16, 1)):
+        im = rng.random((3, H, W)).astype(np.float32)
+        out = gs.gs_downsample(t32(im.reshape(-1)), W, H, f)
+        torch.cuda.synchronize()
+        ref = O.downsample(im, f)
+        assert_close(out.cpu().numpy().reshape(ref.shape), ref, 1e-6, what=f"downsample {W}x{H}/{f}")
