@@ -11,8 +11,8 @@ iteration: residual norms e_pf; observations with e > median + 4 MAD (lower
 median, MAD = lower median of |e - median|) are discarded; the rest are
 weighted by Huber with threshold delta (weight 1 inside, delta / e outside;
 cost 0.5 e^2 inside, delta (e - delta / 2) outside). The step solves
-(H + lam diag(H) + eps I) d = -g with H = J^T W J, g = J^T W r and
-eps = 1e-12 mean(diag H) over the parameters
+(H + lam diag(H) + 1e-9 I) d = -g with H = J^T W J and g = J^T W r over the
+parameters
 (pose tangents of frames 1..F-1 as left perturbations T <- exp(d^) T, the
 focal length, the points), written out as the dense normal equations. A step
 is accepted when the robust cost over the same observation set decreases: then
@@ -100,11 +100,11 @@ def lm_iteration(params, lam, obs, cx, cy, delta=2.0, nu=2.0):
     wr = np.repeat(w.reshape(-1), 2)
     H = Jm.T @ (wr[:, None] * Jm)
     g = Jm.T @ (wr * r.reshape(-1))
-    # Marquardt damping plus a floor 1e-12 * mean(diag H) on the diagonal, so a
+    # Marquardt damping plus an absolute floor 1e-9 on the diagonal, so a
     # parameter without any kept observation gets a zero step instead of a
     # singular system
     dg = np.diag(H)
-    A = H + np.diag(lam * dg + 1e-12 * dg.mean())
+    A = H + np.diag(lam * dg + 1e-9)
     d = np.linalg.solve(A, -g)
     trial = apply_step(params, d)
     c0 = robust_cost(e, mask, delta)
