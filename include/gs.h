@@ -525,6 +525,31 @@ int gs_pose_tangent_grad(const float* xi, const float* dL_ddelta, int32_t n_view
  * by the factor; pixel centres stay at I + 0.5. */
 int gs_downsample(const float* image, int32_t width, int32_t height, int32_t factor, float* out, void* stream);
 
+/* Mini bundle adjustment of the initial pose estimation (Sec. 4.1 bootstrapping,
+ * App. A.1): `iterations` Levenberg-Marquardt iterations over the shared focal
+ * length, the poses of frames 1..F-1 (frame 0 fixed) and P points, each point
+ * observed in all F frames (2 <= F <= 8).
+ *   obs     device float [P][F][2]: observed pixel of point p in frame f
+ *   fl      device float [1], in/out: focal length (fx = fy; principal point cx, cy)
+ *   poses   device float [F][12], in/out: world->camera R (row-major) | t
+ *   points  device float [P][4], in/out: x, y, z, unused (16-byte aligned)
+ *   lam     device float [1], in/out: damping (App. A.1 starts at 1e-5)
+ * Residual r = (fl x/z + cx, fl y/z + cy) - obs for (x, y, z) = R X + t. Each
+ * iteration discards observations whose |r| exceeds median + 4 MAD (lower
+ * medians), weights the rest by Huber (threshold huber_delta px), solves
+ * (H + lam diag(H) + 1e-9 I) d = -J^T W r by the Schur complement on the points
+ * (reduced camera system in FP64), applies d (poses: T <- exp(d^) T) and keeps
+ * it iff the robust cost on the same observations decreases (lam /= nu), else
+ * lam *= nu. history (optional, device float [iterations][3]) receives (cost,
+ * trial cost, accepted) per iteration; *failed (device int32) = 1 if a reduced
+ * system was not positive definite (its step is then zero). Everything stays
+ * on the device: the call can be captured into a CUDA graph. ws:
+ * gs_ba_workspace_size(F, P) bytes. */
+size_t gs_ba_workspace_size(int32_t n_frames, int64_t n_points);
+int gs_ba_lm(const float* obs, int32_t n_frames, int64_t n_points, float cx, float cy, float* fl, float* poses,
+             float* points, float* lam, int32_t iterations, float huber_delta, float nu, float* history,
+             int32_t* failed, void* ws, size_t ws_bytes, void* stream);
+
 /* counter[0] += delta on the device (advances a graph-visible step counter). */
 int gs_counter_add(int32_t* counter, int32_t delta, void* stream);
 

@@ -35,7 +35,7 @@ EXPORTS = [
     "gs_mlp_gemm_bf16", "gs_mlp_tc_error", "gs_mlp_targets_workspace_size", "gs_mlp_targets", "gs_spawn_learned",
     "gs_pose_apply", "gs_pose_tangent_grad", "gs_anchor_merge_workspace_size", "gs_anchor_merge",
     "gs_anchor_blend_weight", "gs_scale_opacity", "gs_cull_opacity_workspace_size", "gs_cull_opacity",
-    "gs_downsample",
+    "gs_downsample", "gs_ba_workspace_size", "gs_ba_lm",
 ]
 
 
@@ -140,6 +140,9 @@ def lib():
                                        C.c_int32, P, P]),
             "gs_counter_add": (C.c_int, [P, C.c_int32, P]),
             "gs_downsample": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, P, P]),
+            "gs_ba_workspace_size": (C.c_size_t, [C.c_int32, C.c_int64]),
+            "gs_ba_lm": (C.c_int, [P, C.c_int32, C.c_int64, C.c_float, C.c_float, P, P, P, P, C.c_int32, C.c_float,
+                                   C.c_float, P, P, P, C.c_size_t, P]),
             "gs_pose_apply": (C.c_int, [P, P, C.c_int32, P, P]),
             "gs_anchor_merge_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32]),
             "gs_anchor_merge": (C.c_int, [C.POINTER(gs_gaussians)] * 3 + [P, P, C.c_float, C.c_int32, C.c_uint64] +
@@ -685,6 +688,21 @@ def downsample_cameras(cams: torch.Tensor, factor: int) -> torch.Tensor:
             c[k] = c[k] / factor
         c["width"], c["height"] = -(-c["width"] // factor), -(-c["height"] // factor)
     return cameras_tensor(cs, cams.device)
+
+
+def gs_ba_workspace_size(n_frames: int, n_points: int) -> int:
+    return int(lib().gs_ba_workspace_size(n_frames, n_points))
+
+
+def gs_ba_lm(obs: torch.Tensor, cx: float, cy: float, fl: torch.Tensor, poses: torch.Tensor, points: torch.Tensor,
+             lam: torch.Tensor, iterations: int, ws: torch.Tensor, failed: torch.Tensor, huber_delta: float = 2.0,
+             nu: float = 2.0, history: torch.Tensor | None = None, stream=None):
+    """Levenberg-Marquardt iterations of the mini bundle adjustment (obs
+    [P][F][2], poses [F][12], points [P][4], fl and lam [1], all device)."""
+    P, F = obs.shape[0], obs.shape[1]
+    _check(lib().gs_ba_lm(_ptr(obs), F, P, cx, cy, _ptr(fl), _ptr(poses), _ptr(points), _ptr(lam), iterations,
+                          huber_delta, nu, _ptr(history), _ptr(failed), _ptr(ws), ws.numel(), _stream(stream)),
+           "gs_ba_lm")
 
 
 def gs_counter_add(counter: torch.Tensor, delta: int = 1, stream=None):

@@ -1,0 +1,137 @@
+"""Mini bundle adjustment on the GPU (Sec. 4.1, App. A.1) against the FP64
+oracle: one Levenberg-Marquardt iteration (step, costs, decision), a 30-iteration
+run (final robust cost), determinism and CUDA-graph replay."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import assert_close
+from oracle import mini_ba as B
+from oracle import oracle as O
+from paper_2506_05558_gb300 import gs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2506_05558_gb300 import build
+    build.build()
+
+
+def problem(seed, F=6, P=200):
+    """0.5 px noise, 3% outliers, start 1-3% off the truth; returns oracle state
+    and its FP32 copy (the GPU starts from the same rounded values)."""
+    rng = np.random.default_rng(seed)
+    gt, obs, cx, cy, out = B.synthetic_problem(rng, F=F, P=P, outlier_frac=0.03, noise_px=0.5)
+    params = {"fl": gt["fl"] * 1.03, "R": gt["R"].copy(), "t": gt["t"].copy(),
+              "X": gt["X"] * (1 + rng.normal(0, 0.02, gt["X"].shape))}
+    for f in range(1, F):
+        params["R"][f], params["t"][f] = O.retract_pose(gt["R"][f], gt["t"][f], rng.normal(0, 0.01, 6))
+    r32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    params = {k: r32(v) for k, v in params.items()}
+    params["fl"] = float(params["fl"])
+    return gt, r32(obs), cx, cy, params
+
+
+def to_device(obs, params):
+    P, F = obs.shape[:2]
+    poses = np.concatenate([params["R"].reshape(F, 9), params["t"]], 1)
+    pts = np.concatenate([params["X"], np.zeros((P, 1))], 1)
+    f32 = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda").contiguous()
+    return f32(obs), f32([params["fl"]]), f32(poses), f32(pts)
+
+
+def from_device(fl, poses, pts):
+    pz = poses.cpu().numpy().astype(np.float64)
+    return {"fl": float(fl.item()), "R": pz[:, :9].reshape(-1, 3, 3), "t": pz[:, 9:12],
+            "X": pts.cpu().numpy().astype(np.float64)[:, :3]}
+
+
+def run_gpu(obs, params, iterations, lam0=1e-5):
+    P, F = obs.shape[:2]
+    ob, fl, poses, pts = to_device(obs, params)
+    lam = torch.tensor([lam0], device="cuda")
+    ws = gs.workspace(gs.gs_ba_workspace_size(F, P))
+    hist = torch.zeros((max(iterations, 1), 3), device="cuda")
+    failed = torch.zeros(1, dtype=torch.int32, device="cuda")
+    gs.gs_ba_lm(ob, CX, CY, fl, poses, pts, lam, iterations, ws, failed, history=hist)
+    torch.cuda.synchronize()
+    assert int(failed.item()) == 0
+    return from_device(fl, poses, pts), float(lam.item()), hist.cpu().numpy()
+
+
+CX, CY = 320.0, 240.0
+
+
+def test_one_iteration_matches_oracle():
+    gt, obs, cx, cy, params = problem(11)
+    assert (cx, cy) == (CX, CY)
+    e = np.linalg.norm(B.residuals(params, obs, cx, cy), axis=2)
+    med = B.lower_median(e)
+    thr = med + 4 * B.lower_median(np.abs(e - med))
+    assert np.abs(e - thr).min() > 1e-4 * thr  # no observation within FP32 reach of the rejection boundary
+    ref, lam_ref, info = B.lm_iteration(params, 1e-5, obs, cx, cy)
+    got, lam, hist = run_gpu(obs, params, 1)
+    assert info["accepted"] and hist[0, 2] == 1.0 and abs(lam - lam_ref) < 1e-12
+    assert abs(hist[0, 0] - info["cost"]) < 1e-4 * info["cost"]
+    assert abs(hist[0, 1] - info["trial_cost"]) < 1e-3 * info["trial_cost"]
+    assert abs(got["fl"] - ref["fl"]) < 1e-4 * ref["fl"]
+    assert_close(got["X"], ref["X"], 1e-4, what="points")
+    assert_close(got["R"], ref["R"], 1e-5, what="rotations")
+    assert_close(got["t"], ref["t"], 1e-4, what="translations")
+
+
+def test_thirty_iterations_reach_the_oracle_cost():
+    gt, obs, cx, cy, params = problem(12)
+    ref, lam_ref = params, 1e-5
+    for _ in range(30):
+        ref, lam_ref, info = B.lm_iteration(ref, lam_ref, obs, cx, cy)
+    got, lam, hist = run_gpu(obs, params, 30)
+    accepted = hist[:, 2] > 0
+    assert accepted[:5].all()
+    final = lambda prm: B.robust_cost(np.linalg.norm(B.residuals(prm, obs, cx, cy), axis=2),
+                                      B.inlier_mask(np.linalg.norm(B.residuals(prm, obs, cx, cy), axis=2)), 2.0)
+    c_gpu, c_ref = final(got), final(ref)
+    assert abs(c_gpu - c_ref) < 1e-3 * c_ref, (c_gpu, c_ref)
+    # accepted costs never increase
+    acc_costs = hist[accepted, 1]
+    assert (np.diff(acc_costs) <= 1e-6 * acc_costs[0]).all()
+
+
+def test_deterministic_and_graph_replay():
+    gt, obs, cx, cy, params = problem(13, F=8, P=500)
+    P, F = obs.shape[:2]
+    a, _, ha = run_gpu(obs, params, 10)
+    b, _, hb = run_gpu(obs, params, 10)
+    assert np.array_equal(ha, hb) and np.array_equal(a["X"], b["X"])
+    # the same 10 iterations captured into one CUDA graph
+    ob, fl, poses, pts = to_device(obs, params)
+    lam = torch.tensor([1e-5], device="cuda")
+    ws = gs.workspace(gs.gs_ba_workspace_size(F, P))
+    hist = torch.zeros((10, 3), device="cuda")
+    failed = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        gs.gs_ba_lm(ob, CX, CY, fl, poses, pts, lam, 1, ws, failed, stream=stream)  # warm-up (attributes)
+    torch.cuda.synchronize()
+    ob, fl, poses, pts = to_device(obs, params)
+    lam.fill_(1e-5)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        gs.gs_ba_lm(ob, CX, CY, fl, poses, pts, lam, 10, ws, failed, history=hist, stream=stream)
+    g.replay()
+    torch.cuda.synchronize()
+    c = from_device(fl, poses, pts)
+    assert np.array_equal(hist.cpu().numpy(), ha) and np.array_equal(c["X"], a["X"])
+
+
+def test_invalid_arguments():
+    ob = torch.zeros((10, 9, 2), device="cuda")
+    f = torch.zeros(1, device="cuda")
+    ws = gs.workspace(1024)
+    failed = torch.zeros(1, dtype=torch.int32, device="cuda")
+    with pytest.raises(RuntimeError):
+        gs.gs_ba_lm(ob, 0, 0, f, torch.zeros((9, 12), device="cuda"), torch.zeros((10, 4), device="cuda"), f, 1, ws,
+                    failed)  # 9 frames > 8
+    assert gs.gs_ba_workspace_size(9, 10) == 0
