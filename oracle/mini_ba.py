@@ -16,7 +16,8 @@ parameters
 (pose tangents of frames 1..F-1 as left perturbations T <- exp(d^) T, the
 focal length, the points), written out as the dense normal equations. A step
 is accepted when the robust cost over the same observation set decreases: then
-lam /= nu, else the parameters stay and lam *= nu.
+lam /= nu, else the parameters stay and lam *= nu; lam stays within
+[1e-12, 1e10].
 """
 from __future__ import annotations
 
@@ -110,9 +111,10 @@ def lm_iteration(params, lam, obs, cx, cy, delta=2.0, nu=2.0):
     c0 = robust_cost(e, mask, delta)
     c1 = robust_cost(np.linalg.norm(residuals(trial, obs, cx, cy), axis=2), mask, delta)
     info = dict(cost=c0, trial_cost=c1, step=d, inliers=int(mask.sum()), accepted=c1 < c0)
+    # lam is kept within [1e-12, 1e10] (a converged run rejects every step)
     if c1 < c0:
-        return trial, lam / nu, info
-    return params, lam * nu, info
+        return trial, max(1e-12, lam / nu), info
+    return params, min(1e10, lam * nu), info
 
 
 def bootstrap_init(obs, F, width, cx, cy):
