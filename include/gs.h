@@ -536,16 +536,21 @@ int gs_downsample(const float* image, int32_t width, int32_t height, int32_t fac
  *   lam     device float [1], in/out: damping (App. A.1 starts at 1e-5)
  * Residual r = (fl x/z + cx, fl y/z + cy) - obs for (x, y, z) = R X + t. Each
  * iteration discards observations whose |r| exceeds median + 4 MAD (lower
- * medians), weights the rest by Huber (threshold huber_delta px), solves
+ * medians, selected by one CTA; P F <= 2^26), weights the rest by Huber
+ * (threshold huber_delta px), solves
  * (H + lam diag(H) + 1e-9 I) d = -J^T W r by the Schur complement on the points
  * (reduced camera system in FP64), applies d (poses: T <- exp(d^) T) and keeps
  * it iff the robust cost on the same observations decreases (lam /= nu), else
- * lam *= nu. history (optional, device float [iterations][3]) receives (cost,
+ * lam *= nu; lam is kept within [1e-12, 1e10]. history (optional, device float [iterations][3]) receives (cost,
  * trial cost, accepted) per iteration; *failed (device int32) = 1 if a reduced
  * system was not positive definite (its step is then zero). Everything stays
  * on the device: the call can be captured into a CUDA graph. ws:
  * gs_ba_workspace_size(F, P) bytes. */
 size_t gs_ba_workspace_size(int32_t n_frames, int64_t n_points);
+/* The mini bundle adjustment's camera model: obs [P][F][2] = (fl x/z + cx,
+ * fl y/z + cy) of every point in every frame (same layouts as gs_ba_lm). */
+int gs_ba_project(const float* fl, const float* poses, const float* points, int32_t n_frames, int64_t n_points,
+                  float cx, float cy, float* obs, void* stream);
 int gs_ba_lm(const float* obs, int32_t n_frames, int64_t n_points, float cx, float cy, float* fl, float* poses,
              float* points, float* lam, int32_t iterations, float huber_delta, float nu, float* history,
              int32_t* failed, void* ws, size_t ws_bytes, void* stream);

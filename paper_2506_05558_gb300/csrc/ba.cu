@@ -4,14 +4,16 @@
 // fixed-size layout that makes every block of the problem a fixed-size
 // computation. One iteration:
 //   k_ba_residual   residual norms e of all P F observations
-//   (radix sorts)   lower median of e and of |e - median|: threshold median + 4 MAD
+//   k_ba_median_mad lower median of e and of |e - median| by radix select in one
+//                   CTA: median + 4 MAD
 //   k_ba_normal     per 32-point chunk: each point's Huber-weighted 3x3 block
 //                   (damped), gradient and coupling rows K (Nc x 3) are staged
 //                   in shared memory; threads owning entries of the reduced
 //                   camera system accumulate H_cc - sum_p K H_pp^-1 K^T and its
 //                   right-hand side in FP64, in a fixed order (deterministic)
-//   k_ba_solve      one CTA: sum of the chunk partials, Marquardt damping,
-//                   Cholesky and the two triangular solves in FP64
+//   k_ba_reduce     fixed-order sum of the chunk partials
+//   k_ba_solve      one CTA: Marquardt damping, L D L^T factorisation and the
+//                   two triangular solves in FP64
 //   k_ba_backsub    point steps dp = -H_pp^-1 (g_p + K^T dc) and the trial state
 //   k_ba_trial_cost robust cost of the trial state on the same observation set
 //   k_ba_accept     accept (state <- trial, lam /= nu) or reject (lam *= nu)
@@ -62,15 +64,9 @@ __device__ __forceinline__ double ba_cost(float e, bool keep, float delta) {
     return e <= delta ? 0.5 * (double)e * e : (double)delta * ((double)e - 0.5 * delta);
 }
 
-__device__ __forceinline__ float ba_threshold(const uint32_t* sorted_e, const uint32_t* sorted_d, int64_t n) {
-    const int64_t mid = (n - 1) / 2;
-    return __uint_as_float(sorted_e[mid]) + 4.f * __uint_as_float(sorted_d[mid]);
-}
-
 __global__ void k_ba_residual(const float2* __restrict__ obs, const float* __restrict__ poses,
                               const float4* __restrict__ pts, const float* __restrict__ fl, float cx, float cy,
-                              int F, int64_t P, float* __restrict__ e_out, uint32_t* __restrict__ key,
-                              uint32_t* __restrict__ val) {
+                              int F, int64_t P, float* __restrict__ e_out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P * F) return;
     const int64_t p = i / F;
@@ -78,17 +74,71 @@ __global__ void k_ba_residual(const float2* __restrict__ obs, const float* __res
     BaObs o;
     ba_observe(poses + 12 * f, pts[p], *fl, cx, cy, obs[i], o);
     e_out[i] = o.e;
-    key[i] = __float_as_uint(o.e);  // e >= 0: the bit pattern orders like the value
-    val[i] = (uint32_t)i;
 }
 
-__global__ void k_ba_dev_keys(const float* __restrict__ e, const uint32_t* __restrict__ sorted_e, int64_t n,
-                              uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float med = __uint_as_float(sorted_e[(n - 1) / 2]);
-    key[i] = __float_as_uint(fabsf(e[i] - med));
-    val[i] = (uint32_t)i;
+// Median + 4 MAD threshold in one CTA: radix select (8 bits per pass, most
+// significant first) of the lower median of e, then of |e - median|; the
+// values are re-read from global memory (L1-resident) on every pass, so any
+// P F fits. Non-negative floats order like their bits. The residual norms share
+// a handful of exponents, so the first pass would pile every atomic onto a few
+// bins: each lane counts into its own copy of the histogram (row stride 257,
+// so equal digits of one warp fall into distinct banks).
+constexpr int kBaSelThreads = 1024;
+constexpr int64_t kBaMaxObs = int64_t(1) << 26;  // P F bound: 32-bit indexing everywhere
+constexpr int kBaHistStride = 257;
+
+template <bool kAbsDev>
+__device__ uint32_t select_rank(const float* __restrict__ e, int n, float med, int rank, uint32_t* hist,
+                                uint32_t* s_wsum, uint32_t* s_pref) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t* my = hist + lane * kBaHistStride;
+    uint32_t prefix = 0, mask = 0;
+    int k = rank;
+    for (int shift = 24; shift >= 0; shift -= 8) {
+        for (int i = tid; i < 32 * kBaHistStride; i += blockDim.x) hist[i] = 0;
+        __syncthreads();
+        for (int i = tid; i < n; i += blockDim.x) {
+            const float x = kAbsDev ? fabsf(e[i] - med) : e[i];
+            const uint32_t u = __float_as_uint(x);
+            if ((u & mask) == prefix) atomicAdd(&my[(u >> shift) & 255u], 1u);
+        }
+        __syncthreads();
+        uint32_t c = 0, incl = 0;
+        if (tid < 256) {  // bin tid over the 32 copies, then a block scan of the 256 bins
+            for (int l = 0; l < 32; l++) c += hist[l * kBaHistStride + tid];
+            incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+        }
+        __syncthreads();
+        if (tid < 256) {
+            for (int w = 0; w < warp; w++) incl += s_wsum[w];
+            const uint32_t excl = incl - c;
+            if (excl <= (uint32_t)k && (uint32_t)k < incl) {  // exactly one bin holds rank k
+                s_pref[0] = prefix | ((uint32_t)tid << shift);
+                s_pref[1] = (uint32_t)k - excl;
+            }
+        }
+        __syncthreads();
+        prefix = s_pref[0];
+        k = (int)s_pref[1];
+        mask |= 255u << shift;
+        __syncthreads();
+    }
+    return prefix;
+}
+
+__global__ void __launch_bounds__(kBaSelThreads) k_ba_median_mad(const float* __restrict__ e, int n,
+                                                                 float* __restrict__ thr) {
+    __shared__ uint32_t hist[32 * kBaHistStride];
+    __shared__ uint32_t s_wsum[8];
+    __shared__ uint32_t s_pref[2];
+    const float med = __uint_as_float(select_rank<false>(e, n, 0.f, (n - 1) / 2, hist, s_wsum, s_pref));
+    const float mad = __uint_as_float(select_rank<true>(e, n, med, (n - 1) / 2, hist, s_wsum, s_pref));
+    if (threadIdx.x == 0) *thr = med + 4.f * mad;
 }
 
 // Per-point system: damped H_pp, gradient g_p, coupling rows K (camera
@@ -190,15 +240,14 @@ __global__ void __launch_bounds__(kBaThreads) k_ba_normal(const float2* __restri
                                                           const float4* __restrict__ pts,
                                                           const float* __restrict__ fl_p, float cx, float cy, int F,
                                                           int64_t P, const float* __restrict__ e_cur,
-                                                          const uint32_t* __restrict__ sorted_e,
-                                                          const uint32_t* __restrict__ sorted_d, float delta,
+                                                          const float* __restrict__ thr_p, float delta,
                                                           const float* __restrict__ lam_p,
                                                           double* __restrict__ partial) {
     extern __shared__ float sm[];
     const int nc = ba_nc(F);
     float* s_pose = sm;                                              // [F][12]
     float(*s_K)[kBaMaxNc][3] = (float(*)[kBaMaxNc][3])(s_pose + 12 * kBaMaxF);  // [pts][Nc][3]
-    double(*s_V)[kBaMaxNc][3] = (double(*)[kBaMaxNc][3])(s_K + kBaPts);         // H^-1 K rows
+    float(*s_V)[kBaMaxNc][3] = (float(*)[kBaMaxNc][3])(s_K + kBaPts);           // H^-1 K rows
     double(*s_u)[3] = (double(*)[3])(s_V + kBaPts);                              // H^-1 g
     float(*s_J)[kBaMaxF][2][8] = (float(*)[kBaMaxF][2][8])(s_u + kBaPts);         // camera rows
     float(*s_w)[kBaMaxF] = (float(*)[kBaMaxF])(s_J + kBaPts);
@@ -208,7 +257,7 @@ __global__ void __launch_bounds__(kBaThreads) k_ba_normal(const float2* __restri
     __syncthreads();
     const int64_t p0 = (int64_t)blockIdx.x * kBaPts;
     const int np = (int)min((int64_t)kBaPts, P - p0);
-    const float thr = ba_threshold(sorted_e, sorted_d, P * F);
+    const float thr = *thr_p;
     const float fl = *fl_p, lam = *lam_p;
     if (tid < kBaPts) {
         if (tid < np) {
@@ -218,7 +267,7 @@ __global__ void __launch_bounds__(kBaThreads) k_ba_normal(const float2* __restri
             for (int c = 0; c < nc; c++) {
                 double v[3];
                 sym3_mul(bp.Hinv, s_K[tid][c], v);
-                s_V[tid][c][0] = v[0]; s_V[tid][c][1] = v[1]; s_V[tid][c][2] = v[2];
+                s_V[tid][c][0] = (float)v[0]; s_V[tid][c][1] = (float)v[1]; s_V[tid][c][2] = (float)v[2];
             }
             double u[3];
             sym3_mul(bp.Hinv, bp.g, u);
@@ -241,19 +290,23 @@ __global__ void __launch_bounds__(kBaThreads) k_ba_normal(const float2* __restri
         int fi, ai, fj, aj;
         cam_of(i, fi, ai);
         cam_of(j, fj, aj);
-        double h = 0.0;  // H_cc entry from the observations
-        for (int pt = 0; pt < np; pt++) {
-            for (int f = 0; f < F; f++) {
-                if ((fi >= 0 && fi != f) || (fj >= 0 && fj != f)) continue;
-                const float w = s_w[pt][f];
-                h += (double)w * ((double)s_J[pt][f][0][ai] * s_J[pt][f][0][aj] +
-                                  (double)s_J[pt][f][1][ai] * s_J[pt][f][1][aj]);
+        // H_cc entry from the observations: poses of two different frames share
+        // none; a pose entry involves its own frame only; focal-focal all frames
+        double h = 0.0;
+        if (fi < 0 || fj < 0 || fi == fj) {
+            const int f_lo = fi >= 0 ? fi : (fj >= 0 ? fj : 0);
+            const int f_hi = fi >= 0 ? fi + 1 : (fj >= 0 ? fj + 1 : F);
+            for (int pt = 0; pt < np; pt++) {
+                float hp = 0.f;  // this point's terms in FP32
+                for (int f = f_lo; f < f_hi; f++)
+                    hp += s_w[pt][f] * (s_J[pt][f][0][ai] * s_J[pt][f][0][aj] + s_J[pt][f][1][ai] * s_J[pt][f][1][aj]);
+                h += (double)hp;
             }
         }
-        double sch = 0.0;  // sum_p K_i . H^-1 K_j
+        double sch = 0.0;  // sum_p K_i . H^-1 K_j: each point's dot product in FP32, the sum in FP64
         for (int pt = 0; pt < np; pt++)
-            sch += (double)s_K[pt][i][0] * s_V[pt][j][0] + (double)s_K[pt][i][1] * s_V[pt][j][1] +
-                   (double)s_K[pt][i][2] * s_V[pt][j][2];
+            sch += (double)(s_K[pt][i][0] * s_V[pt][j][0] + s_K[pt][i][1] * s_V[pt][j][1] +
+                            s_K[pt][i][2] * s_V[pt][j][2]);
         out[e] = h - sch;
         if (i == j) out[nup + i] = h;
     }
@@ -280,22 +333,53 @@ __global__ void __launch_bounds__(kBaThreads) k_ba_normal(const float2* __restri
 
 constexpr int kBaSolveThreads = 256;
 
-// One CTA: fixed-order sum of the chunk partials, damping, Cholesky, solves.
-__global__ void __launch_bounds__(kBaSolveThreads) k_ba_solve(const double* __restrict__ partial, int nb, int F,
+// Fixed-order sum of the chunk partials: a block of 32 x 8 threads takes 32
+// values; each of the 8 rows sums a contiguous segment of the chunks, then the
+// 8 segment sums are added in order.
+__global__ void __launch_bounds__(256) k_ba_reduce(const double* __restrict__ partial, int nb, int stride,
+                                                   double* __restrict__ tot) {
+    __shared__ double s[8][33];
+    const int v = blockIdx.x * 32 + threadIdx.x;
+    const int seg = (nb + 7) / 8, b0 = threadIdx.y * seg, b1 = min(nb, b0 + seg);
+    double a = 0.0;
+    if (v < stride)
+        for (int b = b0; b < b1; b++) a += partial[(int64_t)b * stride + v];
+    s[threadIdx.y][threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.y == 0 && v < stride) {
+        double t = 0.0;
+        for (int r = 0; r < 8; r++) t += s[r][threadIdx.x];
+        tot[v] = t;
+    }
+}
+
+// Fixed-order sum of the trial-cost block partials (one CTA).
+__global__ void k_ba_sum(const double* __restrict__ part, int nb, double* __restrict__ out) {
+    __shared__ double s[256];
+    double a = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) a += part[b];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if (threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+// One CTA: damping, L D L^T factorisation and solves (FP64).
+__global__ void __launch_bounds__(kBaSolveThreads) k_ba_solve(const double* __restrict__ tot, int F,
                                                                const float* __restrict__ lam_p,
                                                                double* __restrict__ dc, double* __restrict__ cost_cur,
                                                                int* __restrict__ fail) {
     __shared__ double s_tot[kBaMaxNc * (kBaMaxNc + 1) / 2 + 2 * kBaMaxNc + 1];
     __shared__ double L[kBaMaxNc][kBaMaxNc + 1];
     __shared__ double y[kBaMaxNc];
+    __shared__ double s_dinv[kBaMaxNc];
     __shared__ int s_bad;
     const int nc = ba_nc(F), nup = ba_nup(nc), stride = ba_stride(nc);
     const int tid = threadIdx.x;
-    for (int v = tid; v < stride; v += blockDim.x) {
-        double a = 0.0;
-        for (int b = 0; b < nb; b++) a += partial[(int64_t)b * stride + v];
-        s_tot[v] = a;
-    }
+    for (int v = tid; v < stride; v += blockDim.x) s_tot[v] = tot[v];
     if (tid == 0) s_bad = 0;
     __syncthreads();
     const double lam = *lam_p;
@@ -308,36 +392,44 @@ __global__ void __launch_bounds__(kBaSolveThreads) k_ba_solve(const double* __re
         L[j][i] = v;
     }
     __syncthreads();
-    for (int k = 0; k < nc; k++) {  // right-looking Cholesky, lower triangle
+    // right-looking L D L^T (unit lower L): one reciprocal per column, no square
+    // roots; the trailing update uses the unscaled column, scaled at the end
+    for (int k = 0; k < nc; k++) {
         if (tid == 0) {
             const double d = L[k][k];
             if (!(d > 0.0)) s_bad = 1;
-            L[k][k] = d > 0.0 ? sqrt(d) : 1.0;
+            s_dinv[k] = d > 0.0 ? 1.0 / d : 0.0;
         }
         __syncthreads();
-        for (int i = k + 1 + tid; i < nc; i += blockDim.x) L[i][k] /= L[k][k];
-        __syncthreads();
+        const double dinv = s_dinv[k];
         const int m = nc - k - 1;
         for (int e = tid; e < m * m; e += blockDim.x) {
             const int i = k + 1 + e / m, j = k + 1 + e % m;
-            if (j <= i) L[i][j] -= L[i][k] * L[j][k];
+            if (j <= i) L[i][j] -= L[i][k] * L[j][k] * dinv;
         }
         __syncthreads();
     }
-    if (tid < 32) {  // forward and back substitution by one warp
+    for (int e = tid; e < nc * nc; e += blockDim.x) {
+        const int i = e / nc, k = e % nc;
+        if (i > k) L[i][k] *= s_dinv[k];
+    }
+    __syncthreads();
+    if (tid < 32) {  // L y = rhs, then L^T x = D^-1 y, by one warp
         const int lane = tid;
         for (int i = 0; i < nc; i++) {
-            double s = 0.0;
-            for (int j = lane; j < i; j += 32) s += L[i][j] * y[j];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) y[i] = (s_tot[nup + nc + i] - s) / L[i][i];
+            double a = 0.0;
+            for (int j = lane; j < i; j += 32) a += L[i][j] * y[j];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) y[i] = s_tot[nup + nc + i] - a;
             __syncwarp();
         }
+        for (int i = lane; i < nc; i += 32) y[i] *= s_dinv[i];
+        __syncwarp();
         for (int i = nc - 1; i >= 0; i--) {
-            double s = 0.0;
-            for (int j = i + 1 + lane; j < nc; j += 32) s += L[j][i] * y[j];
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) y[i] = (y[i] - s) / L[i][i];
+            double a = 0.0;
+            for (int j = i + 1 + lane; j < nc; j += 32) a += L[j][i] * y[j];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) y[i] -= a;
             __syncwarp();
         }
     }
@@ -382,8 +474,7 @@ __global__ void __launch_bounds__(kBaThreads) k_ba_backsub(const float2* __restr
                                                            const float4* __restrict__ pts,
                                                            const float* __restrict__ fl_p, float cx, float cy, int F,
                                                            int64_t P, const float* __restrict__ e_cur,
-                                                           const uint32_t* __restrict__ sorted_e,
-                                                           const uint32_t* __restrict__ sorted_d, float delta,
+                                                           const float* __restrict__ thr_p, float delta,
                                                            const float* __restrict__ lam_p,
                                                            const double* __restrict__ dc, float* __restrict__ poses_t,
                                                            float4* __restrict__ pts_t, float* __restrict__ fl_t) {
@@ -404,8 +495,7 @@ __global__ void __launch_bounds__(kBaThreads) k_ba_backsub(const float2* __restr
     if (p >= P) return;
     float K[kBaMaxNc][3];
     BaPoint bp;
-    const float thr = ba_threshold(sorted_e, sorted_d, P * F);
-    ba_point_system(p, F, obs, s_pose, pts, *fl_p, cx, cy, e_cur, thr, delta, *lam_p, K, nullptr, nullptr, bp);
+    ba_point_system(p, F, obs, s_pose, pts, *fl_p, cx, cy, e_cur, *thr_p, delta, *lam_p, K, nullptr, nullptr, bp);
     double rhs[3] = {bp.g[0], bp.g[1], bp.g[2]};
     for (int c = 0; c < nc; c++)
         for (int k = 0; k < 3; k++) rhs[k] += (double)K[c][k] * dc[c];
@@ -422,17 +512,15 @@ __global__ void __launch_bounds__(256) k_ba_trial_cost(const float2* __restrict_
                                                         const float4* __restrict__ pts_t,
                                                         const float* __restrict__ fl_t, float cx, float cy, int F,
                                                         int64_t P, const float* __restrict__ e_cur,
-                                                        const uint32_t* __restrict__ sorted_e,
-                                                        const uint32_t* __restrict__ sorted_d, float delta,
+                                                        const float* __restrict__ thr_p, float delta,
                                                         double* __restrict__ partial) {
     __shared__ double s[256];
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double c = 0.0;
     if (i < P * F) {
-        const float thr = ba_threshold(sorted_e, sorted_d, P * F);
         BaObs o;
         ba_observe(poses_t + 12 * (i % F), pts_t[i / F], *fl_t, cx, cy, obs[i], o);
-        c = ba_cost(o.e, e_cur[i] <= thr, delta);
+        c = ba_cost(o.e, e_cur[i] <= *thr_p, delta);
     }
     s[threadIdx.x] = c;
     __syncthreads();
@@ -443,13 +531,12 @@ __global__ void __launch_bounds__(256) k_ba_trial_cost(const float2* __restrict_
     if (threadIdx.x == 0) partial[blockIdx.x] = s[0];
 }
 
-__global__ void k_ba_accept(const double* __restrict__ trial_partial, int nb, const double* __restrict__ cost_cur,
+__global__ void k_ba_accept(const double* __restrict__ trial_total, const double* __restrict__ cost_cur,
                             int F, int64_t P, const float* __restrict__ poses_t, const float4* __restrict__ pts_t,
                             const float* __restrict__ fl_t, float* __restrict__ poses, float4* __restrict__ pts,
                             float* __restrict__ fl, float* __restrict__ lam, float nu, float* __restrict__ history,
                             int* __restrict__ iter) {
-    double tc = 0.0;  // every thread sums in the same order
-    for (int b = 0; b < nb; b++) tc += trial_partial[b];
+    const double tc = *trial_total;
     const double cur = *cost_cur;
     const bool acc = tc < cur;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -459,7 +546,9 @@ __global__ void k_ba_accept(const double* __restrict__ trial_partial, int nb, co
         if (i == 0) *fl = *fl_t;
     }
     if (i == 0) {
-        *lam = acc ? *lam / nu : *lam * nu;
+        // lam is kept within [1e-12, 1e10]: a converged run rejects every further
+        // step, and unbounded growth would reach infinity
+        *lam = fminf(1e10f, fmaxf(1e-12f, acc ? *lam / nu : *lam * nu));
         if (history) {
             const int it = *iter;
             history[3 * it] = (float)cur;
@@ -470,12 +559,21 @@ __global__ void k_ba_accept(const double* __restrict__ trial_partial, int nb, co
     }
 }
 
+__global__ void k_ba_project(const float* __restrict__ poses, const float4* __restrict__ pts,
+                             const float* __restrict__ fl, float cx, float cy, int F, int64_t P,
+                             float2* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * F) return;
+    BaObs o;
+    ba_observe(poses + 12 * (i % F), pts[i / F], *fl, cx, cy, make_float2(0.f, 0.f), o);
+    out[i] = make_float2(o.r[0], o.r[1]);
+}
+
 struct BaWs {
     float *e, *poses_t, *fl_t;
     float4* pts_t;
-    uint32_t *k0, *v0, *k1, *v1, *d0, *dv0, *d1, *dv1, *hist;
-    void* scan;
-    double *partial, *trial_partial, *dc, *cost_cur;
+    double *partial, *trial_partial, *dc, *cost_cur, *tot, *trial_total;
+    float* thr;
     int *iter, *fail;
 };
 
@@ -489,17 +587,13 @@ static BaWs carve_ba(char* base, size_t cap, int F, int64_t P, size_t* used) {
     w.poses_t = c.take<float>(12 * kBaMaxF);
     w.fl_t = c.take<float>(4);
     w.pts_t = c.take<float4>(P);
-    w.k0 = c.take<uint32_t>(n); w.v0 = c.take<uint32_t>(n);
-    w.k1 = c.take<uint32_t>(n); w.v1 = c.take<uint32_t>(n);
-    w.d0 = c.take<uint32_t>(n); w.dv0 = c.take<uint32_t>(n);
-    w.d1 = c.take<uint32_t>(n); w.dv1 = c.take<uint32_t>(n);
-    w.hist = c.take<uint32_t>(256 * radix_blocks(n));
-    const int64_t sn = 256 * radix_blocks(n) > n ? 256 * radix_blocks(n) : n;
-    w.scan = c.take<char>(scan_workspace_bytes(sn));
     w.partial = c.take<double>(nb * (nc * (nc + 1) / 2 + 2 * nc + 1));
     w.trial_partial = c.take<double>(nt);
     w.dc = c.take<double>(kBaMaxNc);
     w.cost_cur = c.take<double>(1);
+    w.tot = c.take<double>(nc * (nc + 1) / 2 + 2 * nc + 1);
+    w.trial_total = c.take<double>(1);
+    w.thr = c.take<float>(1);
     w.iter = c.take<int>(1);
     w.fail = c.take<int>(1);
     *used = c.used;
@@ -508,7 +602,7 @@ static BaWs carve_ba(char* base, size_t cap, int F, int64_t P, size_t* used) {
 
 static size_t ba_normal_smem() {
     return sizeof(float) * 12 * kBaMaxF + sizeof(float) * kBaPts * kBaMaxNc * 3 +
-           sizeof(double) * kBaPts * kBaMaxNc * 3 + sizeof(double) * kBaPts * 3 +
+           sizeof(float) * kBaPts * kBaMaxNc * 3 + sizeof(double) * kBaPts * 3 +
            sizeof(float) * kBaPts * kBaMaxF * 2 * 8 + sizeof(float) * kBaPts * kBaMaxF + sizeof(double) * kBaPts;
 }
 
@@ -517,7 +611,7 @@ static size_t ba_normal_smem() {
 using namespace gs;
 
 extern "C" size_t gs_ba_workspace_size(int32_t n_frames, int64_t n_points) {
-    if (n_frames < 2 || n_frames > kBaMaxF || n_points < 1) return 0;
+    if (n_frames < 2 || n_frames > kBaMaxF || n_points < 1 || n_points * n_frames > kBaMaxObs) return 0;
     size_t used = 0;
     carve_ba(nullptr, 0, n_frames, n_points, &used);
     return used;
@@ -529,7 +623,7 @@ extern "C" int gs_ba_lm(const float* obs, int32_t n_frames, int64_t n_points, fl
     const int F = n_frames;
     const int64_t P = n_points;
     if (!obs || !fl || !poses || !points || !lam || F < 2 || F > kBaMaxF || P < 1 || iterations < 0 ||
-        !(huber_delta > 0.f) || !(nu > 1.f) || P * F > (int64_t)UINT32_MAX || !failed)
+        !(huber_delta > 0.f) || !(nu > 1.f) || P * F > kBaMaxObs || !failed)
         return GS_ERR_INVALID_ARG;
     size_t need = 0;
     BaWs w = carve_ba((char*)ws, ws_bytes, F, P, &need);
@@ -542,40 +636,55 @@ extern "C" int gs_ba_lm(const float* obs, int32_t n_frames, int64_t n_points, fl
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_ba_normal, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ba_normal_smem());
+        cudaFuncSetAttribute(k_ba_median_mad, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
         attr_set = true;
     }
+    const int stride = nc * (nc + 1) / 2 + 2 * nc + 1;
     const float2* ob = (const float2*)obs;
     float4* pts = (float4*)points;
     cudaMemsetAsync(w.iter, 0, sizeof(int), s);
     cudaMemsetAsync(w.fail, 0, sizeof(int), s);
     for (int it = 0; it < iterations; it++) {
-        k_ba_residual<<<nt, 256, 0, s>>>(ob, poses, pts, fl, cx, cy, F, P, w.e, w.k0, w.v0);
+        k_ba_residual<<<nt, 256, 0, s>>>(ob, poses, pts, fl, cx, cy, F, P, w.e);
         count_launch();
-        const bool e1 = radix_sort_pairs(w.k0, w.v0, w.k1, w.v1, n, nullptr, 32, w.hist, w.scan, s, false);
-        const uint32_t* se = e1 ? w.k1 : w.k0;
-        k_ba_dev_keys<<<nt, 256, 0, s>>>(w.e, se, n, w.d0, w.dv0);
+        k_ba_median_mad<<<1, kBaSelThreads, 0, s>>>(w.e, (int)n, w.thr);
         count_launch();
-        const bool d1 = radix_sort_pairs(w.d0, w.dv0, w.d1, w.dv1, n, nullptr, 32, w.hist, w.scan, s, false);
-        const uint32_t* sd = d1 ? w.d1 : w.d0;
-        k_ba_normal<<<nb, kBaThreads, ba_normal_smem(), s>>>(ob, poses, pts, fl, cx, cy, F, P, w.e, se, sd,
+        k_ba_normal<<<nb, kBaThreads, ba_normal_smem(), s>>>(ob, poses, pts, fl, cx, cy, F, P, w.e, w.thr,
                                                              huber_delta, lam, w.partial);
         count_launch();
-        k_ba_solve<<<1, kBaSolveThreads, 0, s>>>(w.partial, nb, F, lam, w.dc, w.cost_cur, w.fail);
+        k_ba_reduce<<<(unsigned)ceil_div(stride, 32), dim3(32, 8), 0, s>>>(w.partial, nb, stride, w.tot);
+        count_launch();
+        k_ba_solve<<<1, kBaSolveThreads, 0, s>>>(w.tot, F, lam, w.dc, w.cost_cur, w.fail);
         count_launch();
         k_ba_backsub<<<(unsigned)ceil_div(P, kBaThreads), kBaThreads, 0, s>>>(
-            ob, poses, pts, fl, cx, cy, F, P, w.e, se, sd, huber_delta, lam, w.dc, w.poses_t, w.pts_t, w.fl_t);
+            ob, poses, pts, fl, cx, cy, F, P, w.e, w.thr, huber_delta, lam, w.dc, w.poses_t, w.pts_t, w.fl_t);
         count_launch();
-        k_ba_trial_cost<<<nt, 256, 0, s>>>(ob, w.poses_t, w.pts_t, w.fl_t, cx, cy, F, P, w.e, se, sd, huber_delta,
+        k_ba_trial_cost<<<nt, 256, 0, s>>>(ob, w.poses_t, w.pts_t, w.fl_t, cx, cy, F, P, w.e, w.thr, huber_delta,
                                            w.trial_partial);
         count_launch();
+        k_ba_sum<<<1, 256, 0, s>>>(w.trial_partial, nt, w.trial_total);
+        count_launch();
         const int64_t na = P > 12 * F ? P : 12 * F;
-        k_ba_accept<<<(unsigned)ceil_div(na, 256), 256, 0, s>>>(w.trial_partial, nt, w.cost_cur, F, P, w.poses_t,
+        k_ba_accept<<<(unsigned)ceil_div(na, 256), 256, 0, s>>>(w.trial_total, w.cost_cur, F, P, w.poses_t,
                                                                 w.pts_t, w.fl_t, poses, pts, fl, lam, nu, history,
                                                                 w.iter);
         count_launch();
     }
     cudaMemcpyAsync(failed, w.fail, sizeof(int), cudaMemcpyDeviceToDevice, s);
     (void)nc;
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
+extern "C" int gs_ba_project(const float* fl, const float* poses, const float* points, int32_t n_frames,
+                             int64_t n_points, float cx, float cy, float* obs, void* stream) {
+    if (!fl || !poses || !points || !obs || n_frames < 1 || n_frames > kBaMaxF || n_points < 1 ||
+        ((uintptr_t)points & 15) || ((uintptr_t)obs & 7))
+        return GS_ERR_INVALID_ARG;
+    const int64_t n = n_points * n_frames;
+    k_ba_project<<<(unsigned)ceil_div(n, 256), 256, 0, (cudaStream_t)stream>>>(
+        poses, (const float4*)points, fl, cx, cy, n_frames, n_points, (float2*)obs);
+    count_launch();
     GS_CUDA_CHECK_LAUNCH();
     return GS_OK;
 }

@@ -35,7 +35,7 @@ EXPORTS = [
     "gs_mlp_gemm_bf16", "gs_mlp_tc_error", "gs_mlp_targets_workspace_size", "gs_mlp_targets", "gs_spawn_learned",
     "gs_pose_apply", "gs_pose_tangent_grad", "gs_anchor_merge_workspace_size", "gs_anchor_merge",
     "gs_anchor_blend_weight", "gs_scale_opacity", "gs_cull_opacity_workspace_size", "gs_cull_opacity",
-    "gs_downsample", "gs_ba_workspace_size", "gs_ba_lm",
+    "gs_downsample", "gs_ba_workspace_size", "gs_ba_lm", "gs_ba_project",
 ]
 
 
@@ -141,6 +141,7 @@ def lib():
             "gs_counter_add": (C.c_int, [P, C.c_int32, P]),
             "gs_downsample": (C.c_int, [P, C.c_int32, C.c_int32, C.c_int32, P, P]),
             "gs_ba_workspace_size": (C.c_size_t, [C.c_int32, C.c_int64]),
+            "gs_ba_project": (C.c_int, [P, P, P, C.c_int32, C.c_int64, C.c_float, C.c_float, P, P]),
             "gs_ba_lm": (C.c_int, [P, C.c_int32, C.c_int64, C.c_float, C.c_float, P, P, P, P, C.c_int32, C.c_float,
                                    C.c_float, P, P, P, C.c_size_t, P]),
             "gs_pose_apply": (C.c_int, [P, P, C.c_int32, P, P]),
@@ -703,6 +704,13 @@ def gs_ba_lm(obs: torch.Tensor, cx: float, cy: float, fl: torch.Tensor, poses: t
     _check(lib().gs_ba_lm(_ptr(obs), F, P, cx, cy, _ptr(fl), _ptr(poses), _ptr(points), _ptr(lam), iterations,
                           huber_delta, nu, _ptr(history), _ptr(failed), _ptr(ws), ws.numel(), _stream(stream)),
            "gs_ba_lm")
+
+
+def gs_ba_project(fl: torch.Tensor, poses: torch.Tensor, points: torch.Tensor, cx: float, cy: float,
+                  obs: torch.Tensor, stream=None):
+    """obs [P][F][2] = pixels of points [P][4] in the F cameras poses [F][12]."""
+    _check(lib().gs_ba_project(_ptr(fl), _ptr(poses), _ptr(points), poses.shape[0], points.shape[0], cx, cy,
+                               _ptr(obs), _stream(stream)), "gs_ba_project")
 
 
 def gs_counter_add(counter: torch.Tensor, delta: int = 1, stream=None):

@@ -232,3 +232,26 @@ def projected_items(rng, n_items, tiles_x, tiles_y, tile, max_rect=4, depth_leve
     rect[culled] = 0
     n_tiles = ((rect[:, 2] - rect[:, 0]) * (rect[:, 3] - rect[:, 1])).astype(np.int32)
     return dict(mean2d=mean2d, conic_opa=conic_opa, rgb_depth=rgb_depth, rect=rect, n_tiles=n_tiles)
+
+
+def ba_problem(seed=1005, n_frames=8, n_points=6144, width=1920, fl=1500.0, noise_px=0.5, outlier_frac=0.03):
+    """Seeded inputs of a bootstrapping mini bundle adjustment shaped like the
+    paper's (8 initial frames, 6144 keypoints): ground-truth points in a box
+    3-8 m ahead, frame poses as small tangent steps along a forward path
+    (0.1 m and 2 degrees per frame, jittered), per-observation pixel noise and
+    gross-outlier offsets (30-80 px on outlier_frac of the observations), and
+    start-state jitters. Only random draws: the caller builds poses and
+    observations from them."""
+    rng = _rng(seed)
+    P, F = n_points, n_frames
+    X = np.stack([rng.uniform(-2, 2, P), rng.uniform(-1.5, 1.5, P), rng.uniform(3, 8, P)], 1)
+    xi = np.zeros((F, 6))
+    for f in range(1, F):
+        xi[f] = np.concatenate([rng.normal(0, 0.05, 3) + [0.1 * f, 0, 0], rng.normal(0, 0.02, 3) + [0, 0.035 * f, 0]])
+    noise = rng.normal(0, noise_px, (P, F, 2))
+    out = rng.random((P, F)) < outlier_frac
+    ang = rng.uniform(0, 2 * np.pi, (P, F))
+    mag = rng.uniform(30, 80, (P, F))
+    noise[out] += np.stack([np.cos(ang), np.sin(ang)], -1)[out] * mag[out][:, None]
+    return dict(X=X, xi=xi, noise=noise, fl=fl, width=width, start_X_scale=1 + rng.normal(0, 0.02, (P, 3)),
+                start_xi=rng.normal(0, 0.01, (F, 6)), start_fl=1.03)
