@@ -255,3 +255,70 @@ def ba_problem(seed=1005, n_frames=8, n_points=6144, width=1920, fl=1500.0, nois
     noise[out] += np.stack([np.cos(ang), np.sin(ang)], -1)[out] * mag[out][:, None]
     return dict(X=X, xi=xi, noise=noise, fl=fl, width=width, start_X_scale=1 + rng.normal(0, 0.02, (P, 3)),
                 start_xi=rng.normal(0, 0.01, (F, 6)), start_fl=1.03)
+
+
+def to_bf16(x) -> np.ndarray:
+    """bfloat16 bit patterns (uint16) of x, rounded to nearest even from float32."""
+    u = np.ascontiguousarray(np.asarray(x, np.float32)).view(np.uint32).astype(np.uint64)
+    return ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+
+
+def guided_scene(seed=1006, width=1920, height=1080, f=1500.0, n_nb=4, channels=32, period_px=(8.0, 40.0),
+                 mono_sd=0.05, mono_holes=0.01, n_boxes=4):
+    """Multi-view feature maps of a synthetic room, the input of guided depth
+    matching: a reference frame (the newest of a camera path, 0.3 m and 5
+    degrees per frame) and n_nb earlier frames. The room is a ray-cast set of
+    planes (back wall, floor, ceiling, side walls, n_boxes fronto-parallel
+    rectangles 3-6 m ahead); each pixel's feature vector is a smooth random
+    field of the world point it sees (random mixtures of 8 sinusoids whose
+    periods span period_px pixels at 5 m), normalised to unit length and
+    rounded to bfloat16. The monocular depth is the reference's true depth
+    times exp(N(0, mono_sd)), with a fraction mono_holes of pixels set to 0.
+    Returns dict(cams [1 + n_nb] (reference first), feats uint16
+    [1 + n_nb][H][W][C], z_mono float32 [H][W], z_true float32 [H][W])."""
+    rng = _rng(seed)
+    path = camera_path(rng, n_nb + 1)
+    order = [n_nb] + list(range(n_nb))
+    cams = [camera(*world_to_camera(*path[k]), f, width, height) for k in order]
+    planes = [(np.array([0.0, 0.0, 1.0]), 9.0, None), (np.array([0.0, 1.0, 0.0]), 1.6, None),
+              (np.array([0.0, 1.0, 0.0]), -1.8, None), (np.array([1.0, 0.0, 0.0]), -3.5, None),
+              (np.array([1.0, 0.0, 0.0]), 3.5, None)]
+    for _ in range(n_boxes):
+        zc, xc, yc = rng.uniform(3, 6), rng.uniform(-2, 2), rng.uniform(-1, 1)
+        hw, hh = rng.uniform(0.3, 1.0), rng.uniform(0.3, 1.0)
+        planes.append((np.array([0.0, 0.0, 1.0]), zc, (xc - hw, xc + hw, yc - hh, yc + hh)))
+    lo_m, hi_m = (p * 5.0 / f for p in period_px)
+    dirs = rng.normal(size=(8, 3))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    omega = dirs * (2 * np.pi / rng.uniform(lo_m, hi_m, 8))[:, None]
+    phase = rng.uniform(0, 2 * np.pi, 8)
+    mix = rng.normal(size=(8, channels))
+    feats = np.empty((n_nb + 1, height, width, channels), np.uint16)
+    z_true = None
+    v, u = np.mgrid[0:height, 0:width]
+    for k, cam in enumerate(cams):
+        R, t = cam["R"].astype(np.float64), cam["t"].astype(np.float64)
+        ray = np.stack([((u + 0.5 - cam["cx"]) / cam["fx"]).ravel(), ((v + 0.5 - cam["cy"]) / cam["fy"]).ravel(),
+                        np.ones(height * width)], 1)
+        dw = ray @ R  # world directions R^T ray
+        c = -R.T @ t
+        s_best = np.full(height * width, np.inf)
+        for n, off, rect in planes:
+            den = dw @ n
+            with np.errstate(divide="ignore", invalid="ignore"):
+                s = (off - n @ c) / den
+            hit = np.isfinite(s) & (s > 0.05)
+            if rect is not None:
+                p = c + s[:, None] * dw
+                hit &= (p[:, 0] >= rect[0]) & (p[:, 0] <= rect[1]) & (p[:, 1] >= rect[2]) & (p[:, 1] <= rect[3])
+            s_best = np.where(hit & (s < s_best), s, s_best)
+        s_best = np.where(np.isfinite(s_best), s_best, 50.0)
+        X = c + s_best[:, None] * dw
+        fv = np.sin(X @ omega.T + phase) @ mix
+        fv /= np.linalg.norm(fv, axis=1, keepdims=True) + 1e-12
+        feats[k] = to_bf16(fv).reshape(height, width, channels)
+        if k == 0:
+            z_true = s_best.reshape(height, width).astype(np.float32)
+    z_mono = (z_true * np.exp(rng.normal(0, mono_sd, z_true.shape))).astype(np.float32)
+    z_mono[rng.random(z_true.shape) < mono_holes] = 0.0
+    return dict(cams=cams, feats=feats, z_mono=z_mono, z_true=z_true)
