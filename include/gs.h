@@ -555,6 +555,35 @@ int gs_ba_lm(const float* obs, int32_t n_frames, int64_t n_points, float cx, flo
              float* points, float* lam, int32_t iterations, float huber_delta, float nu, float* history,
              int32_t* failed, void* ws, size_t ws_bytes, void* stream);
 
+/* Guided-matching depth refinement (Sec. 4.2 depth for new primitives,
+ * App. A.2). For every pixel of the reference frame: n_cand inverse depths
+ * d_k = d_lo + k (d_hi - d_lo) / (n_cand - 1), d_lo = max(1/Z* - window, 0),
+ * d_hi = 1/Z* + window (the appendix uses window 0.1) around the monocular
+ * depth Z*; among the n_nb neighbours, those for which the whole candidate
+ * segment lies in front of the camera and inside the bilinear domain of its
+ * map (sample coordinates x - 0.5 in [0, W-1] x [0, H-1]) are usable, and the
+ * one whose segment is longest in pixels is chosen (adaptive matching; ties:
+ * lower index); C_k = <F_ref(pixel), bilinear F_j(reprojected candidate k)>
+ * in FP32; k* = the first maximum; when 0 < k* < n_cand - 1 the parabola
+ * through C_{k*-1}, C_{k*}, C_{k*+1} moves d by its vertex offset times the
+ * candidate step; depth = 1 / d.
+ *   feats    device bfloat16 bit patterns [1 + n_nb][H][W][C]: the reference
+ *            frame's map, then the neighbours'; C = channels in {8, 16, 32, 64};
+ *            16-byte aligned
+ *   cams     device gs_camera [1 + n_nb], reference first; intrinsics refer to
+ *            the W x H maps (their width/height fields are not read)
+ *   z_mono   device float [H][W]: monocular depth (z in the reference camera)
+ *   depth    device float [H][W] out: refined depth; pixels with no usable
+ *            neighbour, a monocular depth that is not a positive finite
+ *            number, or a refined inverse depth <= 0 keep z_mono
+ *   nb       device int32 [H][W] out, optional: chosen neighbour (0-based), -1
+ *            where depth kept z_mono
+ *   corr     device float [H][W] out, optional: C_{k*} (0 where nb = -1)
+ * 1 <= n_nb <= 8, W, H >= 2, 3 <= n_cand <= 1024, window > 0. */
+int gs_guided_depth(const uint16_t* feats, const gs_camera* cams, int32_t n_nb, int32_t width, int32_t height,
+                    int32_t channels, const float* z_mono, int32_t n_cand, float window, float* depth, int32_t* nb,
+                    float* corr, void* stream);
+
 /* counter[0] += delta on the device (advances a graph-visible step counter). */
 int gs_counter_add(int32_t* counter, int32_t delta, void* stream);
 

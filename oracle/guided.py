@@ -107,8 +107,9 @@ def fit_peak(cm, c0, cp):
     return np.where(den < 0, (cm - cp) / (2.0 * np.where(den < 0, den, -1.0)), 0.0)
 
 
-def guided_depth(feat_i, feats_nb, cam_i, cams_nb, z_mono, n_cand=32, window=WINDOW, margins=False):
-    """Refined depth of every pixel of frame i.
+def guided_depth(feat_i, feats_nb, cam_i, cams_nb, z_mono, n_cand=32, window=WINDOW, margins=False, pixels=None):
+    """Refined depth of every pixel of frame i (or of the flat pixel indices
+    `pixels`, then every output is 1-D over them).
 
     feat_i [H][W][C] and feats_nb [J][H][W][C]: uint16 bfloat16 patterns;
     z_mono [H][W]. Returns dict(depth [H][W], nb [H][W] int, corr [H][W]) and,
@@ -116,13 +117,17 @@ def guided_depth(feat_i, feats_nb, cam_i, cams_nb, z_mono, n_cand=32, window=WIN
     other way: 'score_gap' (relative gap of the two longest usable segments),
     'edge' (smallest distance in pixels of a segment end to a domain border),
     'front' (smallest Z of a segment end relative to |a|), 'arg_gap' (best
-    minus second-best correlation), 'den' (the parabola's curvature)."""
+    minus second-best correlation), 'den' (the parabola's curvature),
+    'depth_alt', 'den_alt', 'nb_alt' (result, curvature and neighbour output
+    had the runner-up candidate been the maximum), 'cbest' (the largest
+    correlation, also where the refined inverse depth is not positive)."""
     _, _, _, _, _, _, W, H = camera_arrays(cam_i)
-    Fi = bf16_to_f64(feat_i).reshape(H * W, -1)
+    sel = np.arange(H * W) if pixels is None else np.asarray(pixels, np.int64)
+    Fi = bf16_to_f64(np.asarray(feat_i).reshape(H * W, -1)[sel])
     Fn = [bf16_to_f64(f) for f in feats_nb]
-    z = np.asarray(z_mono, np.float64).reshape(-1)
-    npx = H * W
-    r = pixel_rays(cam_i)
+    z = np.asarray(z_mono, np.float64).reshape(-1)[sel]
+    npx = sel.size
+    r = pixel_rays(cam_i)[sel]
     ok = np.isfinite(z) & (z > 0)
     zs = np.where(ok, z, 1.0)
     d = candidates(zs, n_cand, window)
@@ -155,6 +160,10 @@ def guided_depth(feat_i, feats_nb, cam_i, cams_nb, z_mono, n_cand=32, window=WIN
     corr = np.zeros(npx)
     arg_gap = np.full(npx, np.inf)
     den = np.full(npx, -np.inf)
+    depth_alt = depth.copy()
+    den_alt = np.full(npx, -np.inf)
+    nb_alt = nb.copy()
+    cbest = np.zeros(npx)
     for j, cam_j in enumerate(cams_nb):
         idx = np.nonzero(has & (nb == j))[0]
         if idx.size == 0:
@@ -166,26 +175,36 @@ def guided_depth(feat_i, feats_nb, cam_i, cams_nb, z_mono, n_cand=32, window=WIN
         C = np.empty((idx.size, n_cand))
         for k in range(n_cand):
             C[:, k] = np.einsum("pc,pc->p", Fi[idx], bilinear(Fn[j], x[:, k], y[:, k]))
-        ks = np.argmax(C, axis=1)
-        cb = C[np.arange(idx.size), ks]
-        srt = np.sort(C, axis=1)
-        arg_gap[idx] = srt[:, -1] - srt[:, -2]
-        interior = (ks > 0) & (ks < n_cand - 1)
-        km, kp = np.clip(ks - 1, 0, n_cand - 1), np.clip(ks + 1, 0, n_cand - 1)
-        cm, cp = C[np.arange(idx.size), km], C[np.arange(idx.size), kp]
-        delta = np.where(interior, fit_peak(cm, cb, cp), 0.0)
-        den[idx] = np.where(interior, cm - 2 * cb + cp, -np.inf)
         step = (dk[:, -1] - dk[:, 0]) / (n_cand - 1)
-        ds = dk[np.arange(idx.size), ks] + delta * step
+        rows = np.arange(idx.size)
+
+        def refine(ks):
+            cb = C[rows, ks]
+            interior = (ks > 0) & (ks < n_cand - 1)
+            km, kp = np.clip(ks - 1, 0, n_cand - 1), np.clip(ks + 1, 0, n_cand - 1)
+            cm, cp = C[rows, km], C[rows, kp]
+            delta = np.where(interior, fit_peak(cm, cb, cp), 0.0)
+            return cb, dk[rows, ks] + delta * step, np.where(interior, cm - 2 * cb + cp, -np.inf)
+
+        ks = np.argmax(C, axis=1)
+        cb, ds, den[idx] = refine(ks)
+        order = np.argsort(-C, axis=1, kind="stable")
+        arg_gap[idx] = C[rows, order[:, 0]] - C[rows, order[:, 1]]
+        _, ds2, den_alt[idx] = refine(order[:, 1])  # the runner-up as the maximum (a near tie may go either way)
         good = ds > 0
         depth[idx] = np.where(good, 1.0 / np.where(good, ds, 1.0), z[idx])
+        depth_alt[idx] = np.where(ds2 > 0, 1.0 / np.where(ds2 > 0, ds2, 1.0), z[idx])
+        nb_alt[idx] = np.where(ds2 > 0, j, -1)
+        cbest[idx] = cb
         corr[idx] = np.where(good, cb, 0.0)
         nb[idx] = np.where(good, j, -1)
-    out = {"depth": depth.reshape(H, W), "nb": nb.reshape(H, W), "corr": corr.reshape(H, W)}
+    shape = (H, W) if pixels is None else (npx,)
+    out = {"depth": depth.reshape(shape), "nb": nb.reshape(shape), "corr": corr.reshape(shape)}
     if margins:
         with np.errstate(invalid="ignore", divide="ignore"):
             gap = np.where(second_score >= 0, (best_score - second_score) / np.maximum(best_score, 1e-30), np.inf)
-        out.update(score_gap=gap.reshape(H, W), edge=edge.reshape(H, W), front=front.reshape(H, W),
-                   arg_gap=arg_gap.reshape(H, W),
-                   den=den.reshape(H, W), inv_step=((hi - lo) / (n_cand - 1)).reshape(H, W))
+        out.update(score_gap=gap.reshape(shape), edge=edge.reshape(shape), front=front.reshape(shape),
+                   arg_gap=arg_gap.reshape(shape), den=den.reshape(shape), depth_alt=depth_alt.reshape(shape),
+                   den_alt=den_alt.reshape(shape), nb_alt=nb_alt.reshape(shape), cbest=cbest.reshape(shape),
+                   inv_step=((hi - lo) / (n_cand - 1)).reshape(shape))
     return out

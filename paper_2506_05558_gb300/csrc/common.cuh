@@ -106,4 +106,23 @@ bool radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, in
                       const uint32_t* n_dev, int bits, uint32_t* hist, void* scan_ws, cudaStream_t s,
                       bool va_is_position);
 
+// Persistent grid: as many CTAs as fit at once on all SMs. The occupancy query
+// runs once per (device, kernel) so later calls, e.g. inside a stream capture,
+// make no runtime queries.
+inline int persistent_grid(const void* fn, int threads) {
+    struct Entry { const void* fn; int dev; int grid; };
+    static Entry cache[64];
+    static int n_cache = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    for (int i = 0; i < n_cache; i++)
+        if (cache[i].fn == fn && cache[i].dev == dev) return cache[i].grid;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
+    const int grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
+    if (n_cache < 64) cache[n_cache++] = {fn, dev, grid};
+    return grid;
+}
+
 }  // namespace gs

@@ -415,25 +415,6 @@ static RenderLaunch pick_bwd(int tile, int batch) {
 static int default_fwd_batch(int tile) { return tile == 8 ? 128 : 256; }
 static int default_bwd_batch(int tile) { return tile == 32 ? 32 : 128; }
 
-// Persistent grid: as many CTAs as fit at once on all SMs. The occupancy query
-// runs once per (device, kernel) so later calls, e.g. inside a stream capture,
-// make no runtime queries.
-static int persistent_grid(const void* fn, int threads) {
-    struct Entry { const void* fn; int dev; int grid; };
-    static Entry cache[64];
-    static int n_cache = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    for (int i = 0; i < n_cache; i++)
-        if (cache[i].fn == fn && cache[i].dev == dev) return cache[i].grid;
-    int sms = 0, per_sm = 0;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
-    const int grid = (per_sm > 0 ? per_sm : 1) * (sms > 0 ? sms : 1);
-    if (n_cache < 64) cache[n_cache++] = {fn, dev, grid};
-    return grid;
-}
-
 static int launch(const RenderLaunch& L, int n_tiles, bool persistent, void** args, cudaStream_t s) {
     int grid = n_tiles;
     if (persistent) {

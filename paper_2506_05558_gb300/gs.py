@@ -35,7 +35,7 @@ EXPORTS = [
     "gs_mlp_gemm_bf16", "gs_mlp_tc_error", "gs_mlp_targets_workspace_size", "gs_mlp_targets", "gs_spawn_learned",
     "gs_pose_apply", "gs_pose_tangent_grad", "gs_anchor_merge_workspace_size", "gs_anchor_merge",
     "gs_anchor_blend_weight", "gs_scale_opacity", "gs_cull_opacity_workspace_size", "gs_cull_opacity",
-    "gs_downsample", "gs_ba_workspace_size", "gs_ba_lm", "gs_ba_project",
+    "gs_downsample", "gs_ba_workspace_size", "gs_ba_lm", "gs_ba_project", "gs_guided_depth",
 ]
 
 
@@ -145,6 +145,8 @@ def lib():
             "gs_ba_lm": (C.c_int, [P, C.c_int32, C.c_int64, C.c_float, C.c_float, P, P, P, P, C.c_int32, C.c_float,
                                    C.c_float, P, P, P, C.c_size_t, P]),
             "gs_pose_apply": (C.c_int, [P, P, C.c_int32, P, P]),
+            "gs_guided_depth": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, C.c_int32, C.c_float,
+                                          P, P, P, P]),
             "gs_anchor_merge_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32]),
             "gs_anchor_merge": (C.c_int, [C.POINTER(gs_gaussians)] * 3 + [P, P, C.c_float, C.c_int32, C.c_uint64] +
                                 [C.POINTER(gs_gaussians)] * 3 + [P, P, P, C.c_size_t, P]),
@@ -711,6 +713,20 @@ def gs_ba_project(fl: torch.Tensor, poses: torch.Tensor, points: torch.Tensor, c
     """obs [P][F][2] = pixels of points [P][4] in the F cameras poses [F][12]."""
     _check(lib().gs_ba_project(_ptr(fl), _ptr(poses), _ptr(points), poses.shape[0], points.shape[0], cx, cy,
                                _ptr(obs), _stream(stream)), "gs_ba_project")
+
+
+def gs_guided_depth(feats: torch.Tensor, cams: torch.Tensor, z_mono: torch.Tensor, n_cand: int = 32,
+                    window: float = 0.1, depth: torch.Tensor | None = None, nb: torch.Tensor | None = None,
+                    corr: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Refined depth [H][W] of the reference frame from feats [1 + n_nb][H][W][C]
+    (bfloat16 bit patterns as int16/uint16, or a bfloat16 tensor), cams (device
+    gs_camera array, reference first) and z_mono [H][W]."""
+    J1, H, W, Ch = feats.shape
+    if depth is None:
+        depth = torch.empty((H, W), dtype=torch.float32, device=feats.device)
+    _check(lib().gs_guided_depth(_ptr(feats), _ptr(cams), J1 - 1, W, H, Ch, _ptr(z_mono), n_cand, window,
+                                 _ptr(depth), _ptr(nb), _ptr(corr), _stream(stream)), "gs_guided_depth")
+    return depth
 
 
 def gs_counter_add(counter: torch.Tensor, delta: int = 1, stream=None):
