@@ -579,7 +579,7 @@ int gs_ba_lm(const float* obs, int32_t n_frames, int64_t n_points, float cx, flo
  *   nb       device int32 [H][W] out, optional: chosen neighbour (0-based), -1
  *            where depth kept z_mono
  *   corr     device float [H][W] out, optional: C_{k*} (0 where nb = -1)
- * 1 <= n_nb <= 8, W, H >= 2, 3 <= n_cand <= 1024, window > 0. */
+ * 1 <= n_nb <= 8, W, H >= 2, W H C < 2^31, 3 <= n_cand <= 1024, window > 0. */
 int gs_guided_depth(const uint16_t* feats, const gs_camera* cams, int32_t n_nb, int32_t width, int32_t height,
                     int32_t channels, const float* z_mono, int32_t n_cand, float window, float* depth, int32_t* nb,
                     float* corr, void* stream);

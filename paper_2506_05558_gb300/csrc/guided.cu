@@ -11,8 +11,10 @@
 // contiguous, 2C bytes). Four lanes (a quad) own one pixel, each a quarter of
 // the channels, so a warp reads eight pixels' features as contiguous
 // 2C-byte runs per corner; the quad's partial dot products meet in two
-// shuffles. Persistent CTAs walk 16 x 4 pixel tiles; the relative poses are
-// composed once per CTA in FP64.
+// shuffles. The quad's lanes project four candidates at once and broadcast
+// each one's cell and weights, so the scalar work is not repeated per lane.
+// Persistent CTAs walk 16 x 4 pixel tiles; the relative poses are composed
+// once per CTA in FP64.
 #include "common.cuh"
 
 namespace gs {
@@ -147,12 +149,14 @@ __global__ void __launch_bounds__(256) k_guided_depth(const uint16_t* __restrict
         gm_load<C>(feats + p * C + q * (C / 4), fi);
         const uint16_t* Fj = feats + ((int64_t)(1 + (act ? jb : 0)) * H * W) * C + q * (C / 4);
         const float span = hi - lo;
-        float cbest = -INFINITY, cm = 0.f, cp = 0.f, prev = 0.f, kf = 0.f;
+        const int64_t row = (int64_t)W * C;
+        float cbest = -INFINITY, cm = 0.f, cp = 0.f, prev = 0.f;
         int kb = 0;
         bool want_next = false;
-#pragma unroll 2
-        for (int k = 0; k < n_cand; k++, kf += 1.f) {
-            const float d = fmaf(span, kf * inv, lo);
+        const int qbase = (tid & 31) & ~3;
+        for (int k0 = 0; k0 < n_cand; k0 += 4) {
+            // lane q projects candidate k0 + q (the last group may run past n_cand: those are never used)
+            const float d = fmaf(span, (float)(k0 + q) * inv, lo);
             const float iz = fast_rcp(fmaf(d, b2, a2));
             const float sx = fmaf(fxj * fmaf(d, b0, a0), iz, cxj);
             const float sy = fmaf(fyj * fmaf(d, b1, a1), iz, cyj);
@@ -160,23 +164,33 @@ __global__ void __launch_bounds__(256) k_guided_depth(const uint16_t* __restrict
             // inside; rounding may put an interior sample a hair outside)
             const int x0 = min(max(__float2int_rd(sx), 0), W - 2);
             const int y0 = min(max(__float2int_rd(sy), 0), H - 2);
-            const float wx = sx - (float)x0, wy = sy - (float)y0;
-            const uint16_t* r0 = Fj + ((int64_t)y0 * W + x0) * C;
-            const uint16_t* r1 = r0 + (int64_t)W * C;
-            uint32_t w00[C / 8], w01[C / 8], w10[C / 8], w11[C / 8];
-            gm_load<C>(r0, w00);
-            gm_load<C>(r0 + C, w01);
-            gm_load<C>(r1, w10);
-            gm_load<C>(r1 + C, w11);
-            const float c00 = gm_dot<C>(fi, w00), c01 = gm_dot<C>(fi, w01);
-            const float c10 = gm_dot<C>(fi, w10), c11 = gm_dot<C>(fi, w11);
-            float c = (1.f - wx) * (1.f - wy) * c00 + wx * (1.f - wy) * c01 + (1.f - wx) * wy * c10 +
-                      wx * wy * c11;
-            c += __shfl_xor_sync(0xffffffffu, c, 1);
-            c += __shfl_xor_sync(0xffffffffu, c, 2);
-            if (want_next) { cp = c; want_next = false; }
-            if (c > cbest) { cbest = c; kb = k; cm = prev; want_next = true; }
-            prev = c;
+            const float wxo = sx - (float)x0, wyo = sy - (float)y0;
+            const int offo = (y0 * W + x0) * C;
+            const int nk = min(4, n_cand - k0);
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                if (j >= nk) break;  // uniform across the warp
+                const int off = __shfl_sync(0xffffffffu, offo, qbase + j);
+                const float wx = __shfl_sync(0xffffffffu, wxo, qbase + j);
+                const float wy = __shfl_sync(0xffffffffu, wyo, qbase + j);
+                const uint16_t* r0 = Fj + off;
+                const uint16_t* r1 = r0 + row;
+                uint32_t w00[C / 8], w01[C / 8], w10[C / 8], w11[C / 8];
+                gm_load<C>(r0, w00);
+                gm_load<C>(r0 + C, w01);
+                gm_load<C>(r1, w10);
+                gm_load<C>(r1 + C, w11);
+                const float c00 = gm_dot<C>(fi, w00), c01 = gm_dot<C>(fi, w01);
+                const float c10 = gm_dot<C>(fi, w10), c11 = gm_dot<C>(fi, w11);
+                float c = (1.f - wx) * (1.f - wy) * c00 + wx * (1.f - wy) * c01 + (1.f - wx) * wy * c10 +
+                          wx * wy * c11;
+                c += __shfl_xor_sync(0xffffffffu, c, 1);
+                c += __shfl_xor_sync(0xffffffffu, c, 2);
+                const int k = k0 + j;
+                if (want_next) { cp = c; want_next = false; }
+                if (c > cbest) { cbest = c; kb = k; cm = prev; want_next = true; }
+                prev = c;
+            }
         }
         float out_d = zm, out_c = 0.f;
         int out_j = -1;
@@ -206,7 +220,7 @@ extern "C" int gs_guided_depth(const uint16_t* feats, const gs_camera* cams, int
                                float* depth, int32_t* nb, float* corr, void* stream) {
     if (!feats || !cams || !z_mono || !depth || n_nb < 1 || n_nb > kGmMaxNb || width < 2 || height < 2 ||
         n_cand < 3 || n_cand > 1024 || !(window > 0.f) || !(window < 1e30f) || ((uintptr_t)feats & 15) ||
-        (int64_t)width * height > (int64_t(1) << 31) / 4)
+        (int64_t)width * height * channels > INT32_MAX)
         return GS_ERR_INVALID_ARG;
     const void* fn = channels == 8    ? (const void*)k_guided_depth<8>
                      : channels == 16 ? (const void*)k_guided_depth<16>
