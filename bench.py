@@ -501,6 +501,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the spawn / MLP / anchor measurements")
     ap.add_argument("--cpu-views", type=int, default=3, help="views of the oracle CPU sample")
+    ap.add_argument("--row", choices=["mini_ba", "guided_matching"], default=None,
+                    help="measure only this side row and print its numbers (for profiling)")
+    ap.add_argument("--ba-iterations", type=int, default=200)
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up raised to 3 (timing rule)")
@@ -534,6 +537,14 @@ def main():
         return float(t.item())
 
     gs.lib()
+    if args.row is not None:  # one side row alone, rank 0 only
+        if rank == 0:
+            if args.row == "mini_ba":
+                r = measure_ba(torch, gs, device, iterations=args.ba_iterations)
+            else:
+                r = measure_guided(torch, gs, device, SMS * FP32_LANES * 2 * 2070.0 * 1e6 / 1e12)
+            print(json.dumps({"row": args.row, **r}), flush=True)
+        return 0
     W = make_workload(torch, gs, synth, device, args.n, args.views)
     capacity = int(W["pairs"] * 1.3) + 4096
 
