@@ -138,6 +138,15 @@ class JointOptimizer:
                               gs.gs_counter_add(sd, 1, stream))),
         ]
 
+    def set_targets(self, targets: torch.Tensor):
+        """Points the loss stage at another target buffer (same shape, dtype and
+        device). step() reads it at call time; graphs keep the buffer they were
+        captured with."""
+        if targets.shape != self.targets.shape or targets.dtype != self.targets.dtype or \
+                targets.device != self.targets.device:
+            raise ValueError("targets must match the optimiser's target buffer")
+        self.targets = targets
+
     def step(self, stream=None):
         """Enqueues one iteration (the step number advances on the device)."""
         for _, call in self.stage_calls(stream):

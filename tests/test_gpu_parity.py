@@ -361,6 +361,34 @@ def test_graph_replay_matches_eager_steps():
         assert np.array_equal(a, b)
 
 
+def test_set_targets_switches_the_loss_buffer():
+    """Steps alternating between two target buffers with set_targets() equal
+    steps of optimisers built on each buffer (bit for bit), and a buffer of
+    another shape is refused."""
+    from paper_2506_05558_gb300.raster import JointOptimizer
+    sc, cams, rng = synth.multiview_scene(seed=10, n=3000, n_views=2, sizes=[(96, 64), (64, 80)])
+    sizes = [(c["width"], c["height"]) for c in cams]
+    n = sum(3 * w * h for w, h in sizes)
+    ta, tb = t32(rng.random(n)), t32(rng.random(n))
+    runs = []
+    for switch in (True, False):
+        g = gs.Gaussians.from_scene(sc)
+        J = JointOptimizer(g, gs.cameras_tensor(cams), sizes, ta.clone(), 1 << 16, gs.config(sh_degree=3))
+        losses = []
+        for k in range(4):
+            t = ta if k % 2 == 0 else tb
+            if switch:
+                J.set_targets(t)
+            else:
+                J.targets.copy_(t)
+            losses.append(float(J.step().item()))
+        torch.cuda.synchronize()
+        runs.append((losses, g.mean_opa.cpu().numpy().copy()))
+    assert runs[0][0] == runs[1][0] and np.array_equal(runs[0][1], runs[1][1])
+    with pytest.raises(ValueError):
+        J.set_targets(ta[:-3])
+
+
 def test_720p_200k_end_to_end():
     """1280x720, 200k Gaussians, SH3, 16x16 tiles (full size)."""
     sc, cam, _ = synth.view_720p_scene()
