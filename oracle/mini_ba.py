@@ -145,3 +145,65 @@ def synthetic_problem(rng, F=8, P=200, width=640, height=480, fl=500.0, noise_px
     mag = rng.uniform(30, 80, (P, F))
     obs[out] += np.stack([np.cos(ang), np.sin(ang)], -1)[out] * mag[out][:, None]
     return gt, obs, cx, cy, out
+
+
+# ---------------------------------------------------------------------------
+# Pose refinement of a new frame (Sec. 4.1, subsequent frames): the same
+# robust Levenberg-Marquardt iteration over one camera pose only, the 3-D
+# points (triangulated from earlier frames) and the focal length held fixed.
+# ---------------------------------------------------------------------------
+
+def pose_jacobian(fl, R, t, X):
+    """Jacobian [2M][6] of the residuals of points X [M][3] in camera (R, t)
+    with respect to a left perturbation (rho, phi) of the pose: for q = R X + t,
+    d pixel / d q = fl / z [[1, 0, -x/z], [0, 1, -y/z]] and d q / d(rho, phi) =
+    [I, -q^]."""
+    M = X.shape[0]
+    Jm = np.zeros((2 * M, 6))
+    for m in range(M):
+        q = R @ X[m] + t
+        x, y, z = q
+        dq = fl / z * np.array([[1, 0, -x / z], [0, 1, -y / z]])
+        Jm[2 * m:2 * m + 2, :3] = dq
+        Jm[2 * m:2 * m + 2, 3:] = dq @ -O.hat(q)
+    return Jm
+
+
+def pose_lm_iteration(R, t, lam, X, obs, fl, cx, cy, delta=2.0, nu=2.0):
+    """One Levenberg-Marquardt iteration on the pose (R, t) against obs [M][2].
+    Same robust terms, damping, floor and decision as lm_iteration. Returns
+    (R, t, lam, info)."""
+    r = project(fl, cx, cy, R, t, X) - obs
+    e = np.linalg.norm(r, axis=1)
+    mask = inlier_mask(e)
+    w = np.where(mask, np.where(e <= delta, 1.0, delta / np.maximum(e, 1e-300)), 0.0)
+    Jm = pose_jacobian(fl, R, t, X)
+    wr = np.repeat(w, 2)
+    H = Jm.T @ (wr[:, None] * Jm)
+    g = Jm.T @ (wr * r.reshape(-1))
+    A = H + np.diag(lam * np.diag(H) + 1e-9)
+    d = np.linalg.solve(A, -g)
+    R1, t1 = O.retract_pose(R, t, d)
+    c0 = robust_cost(e, mask, delta)
+    c1 = robust_cost(np.linalg.norm(project(fl, cx, cy, R1, t1, X) - obs, axis=1), mask, delta)
+    info = dict(cost=c0, trial_cost=c1, step=d, inliers=int(mask.sum()), accepted=c1 < c0)
+    if c1 < c0:
+        return R1, t1, max(1e-12, lam / nu), info
+    return R, t, min(1e10, lam * nu), info
+
+
+def synthetic_pose_problem(rng, M=500, width=640, height=480, fl=500.0, noise_px=0.0, outlier_frac=0.0):
+    """Seeded 3-D to 2-D problem of a new frame: points in a box 3-8 m ahead of
+    the origin, a true pose 0.3 m and a few degrees from it, observations with
+    optional pixel noise and gross outliers (30-80 px off). Returns (R, t, X,
+    obs, cx, cy, outlier mask)."""
+    cx, cy = width / 2.0, height / 2.0
+    X = np.stack([rng.uniform(-2, 2, M), rng.uniform(-1.5, 1.5, M), rng.uniform(3, 8, M)], 1)
+    xi = np.concatenate([rng.normal(0, 0.05, 3) + [0.3, 0, 0], rng.normal(0, 0.02, 3) + [0, 0.05, 0]])
+    R, t = O.retract_pose(np.eye(3), np.zeros(3), xi)
+    obs = project(fl, cx, cy, R, t, X) + rng.normal(0, noise_px, (M, 2))
+    out = rng.random(M) < outlier_frac
+    ang = rng.uniform(0, 2 * np.pi, M)
+    mag = rng.uniform(30, 80, M)
+    obs[out] += np.stack([np.cos(ang), np.sin(ang)], -1)[out] * mag[out][:, None]
+    return R, t, X, obs, cx, cy, out

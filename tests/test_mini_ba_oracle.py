@@ -88,3 +88,54 @@ def test_rejected_step_keeps_parameters():
     p2, lam, info = B.lm_iteration(gt, 1e-3, obs, cx, cy)
     assert not info["accepted"] and lam == 2e-3
     assert p2 is gt
+
+
+def test_pose_jacobian_matches_central_differences():
+    rng = np.random.default_rng(7)
+    R, t, X, obs, cx, cy, _ = B.synthetic_pose_problem(rng, M=8)
+    R0, t0 = O.retract_pose(R, t, rng.normal(0, 0.05, 6))
+    Jm = B.pose_jacobian(500.0, R0, t0, X)
+    h = 1e-6
+    for j in range(6):
+        d = np.zeros(6)
+        d[j] = h
+        Rp, tp = O.retract_pose(R0, t0, d)
+        Rm, tm = O.retract_pose(R0, t0, -d)
+        fd = (B.project(500.0, cx, cy, Rp, tp, X) - B.project(500.0, cx, cy, Rm, tm, X)).reshape(-1) / (2 * h)
+        np.testing.assert_allclose(Jm[:, j], fd, rtol=1e-5, atol=1e-6 * np.abs(Jm).max())
+    # the pose columns equal the frame's columns of the full bundle adjustment Jacobian
+    params = {"fl": 500.0, "R": np.stack([np.eye(3), R0]), "t": np.stack([np.zeros(3), t0]), "X": X}
+    full = B.jacobian(params, cx, cy)
+    rows = np.concatenate([np.arange(2 * (2 * m + 1), 2 * (2 * m + 1) + 2) for m in range(8)])
+    np.testing.assert_allclose(full[rows, :6], Jm, rtol=1e-12, atol=1e-12)
+
+
+def test_pose_refinement_recovers_the_pose_and_rejects_outliers():
+    """0.5 px noise and 10% gross outliers, start 27 mrad / several cm off:
+    after 20 iterations (the paper's count) the pose is within 1 mrad and 5 mm,
+    every planted outlier is excluded, and the robust cost is at most the true
+    pose's on the same observation set."""
+    rng = np.random.default_rng(5)
+    R, t, X, obs, cx, cy, out = B.synthetic_pose_problem(rng, M=400, noise_px=0.5, outlier_frac=0.1)
+    Rc, tc = O.retract_pose(R, t, rng.normal(0, 0.02, 6))
+    lam = 1e-5
+    for _ in range(20):
+        Rc, tc, lam, info = B.pose_lm_iteration(Rc, tc, lam, X, obs, 500.0, cx, cy)
+    ang = math.acos(min(1.0, max(-1.0, (np.trace(Rc @ R.T) - 1) / 2)))
+    assert ang < 1e-3 and np.linalg.norm(tc - t) < 5e-3
+    e = np.linalg.norm(B.project(500.0, cx, cy, Rc, tc, X) - obs, axis=1)
+    m = B.inlier_mask(e)
+    assert not m[out].any() and m[~out].mean() > 0.98
+    e_gt = np.linalg.norm(B.project(500.0, cx, cy, R, t, X) - obs, axis=1)
+    assert B.robust_cost(e, m, 2.0) <= B.robust_cost(e_gt, m, 2.0)
+
+
+def test_pose_rejected_step_keeps_the_pose():
+    """Noise-free observations at the true pose: no step lowers the cost, so
+    the pose stays and lam grows by nu; lam never exceeds 1e10."""
+    rng = np.random.default_rng(8)
+    R, t, X, obs, cx, cy, _ = B.synthetic_pose_problem(rng, M=30)
+    R2, t2, lam, info = B.pose_lm_iteration(R, t, 1e-3, X, obs, 500.0, cx, cy)
+    assert not info["accepted"] and lam == 2e-3 and R2 is R and t2 is t
+    _, _, lam, _ = B.pose_lm_iteration(R, t, 8e9, X, obs, 500.0, cx, cy)
+    assert lam == 1e10
