@@ -555,6 +555,28 @@ int gs_ba_lm(const float* obs, int32_t n_frames, int64_t n_points, float cx, flo
              float* points, float* lam, int32_t iterations, float huber_delta, float nu, float* history,
              int32_t* failed, void* ws, size_t ws_bytes, void* stream);
 
+/* Pose refinement of a new frame (Sec. 4.1, subsequent frames: 20 iterations
+ * with all inliers after RANSAC): the iteration of gs_ba_lm over one camera
+ * pose only, the M 3-D points and the focal length held fixed. Each
+ * iteration: residual norms, median + 4 MAD rejection (lower medians), Huber
+ * weights (threshold huber_delta px), (H + lam diag(H) + 1e-9 I) d = -J^T W r
+ * for the left perturbation d = (rho, phi) of the pose (6 x 6, FP64), the
+ * retracted trial pose T <- exp(d^) T kept iff the robust cost on the same
+ * observations decreases (lam /= nu), else lam *= nu; lam in [1e-12, 1e10].
+ *   points  device float [M][4]: x, y, z, unused (16-byte aligned)
+ *   obs     device float [M][2]: observed pixel of each point
+ *   fl      device float [1]: focal length (fx = fy; principal point cx, cy)
+ *   pose    device float [12], in/out: world->camera R (row-major) | t
+ *   lam     device float [1], in/out: damping
+ *   history optional device float [iterations][3]: cost, trial cost, accepted
+ *   failed  device int32 [1]: 1 if a damped system was not positive definite
+ * ws: gs_ba_pose_workspace_size(M) bytes (0 for M outside 1..2^26). Nothing
+ * leaves the device: the call can be captured into a CUDA graph. */
+size_t gs_ba_pose_workspace_size(int64_t n_obs);
+int gs_ba_pose_lm(const float* points, const float* obs, int64_t n_obs, const float* fl, float cx, float cy,
+                  float* pose, float* lam, int32_t iterations, float huber_delta, float nu, float* history,
+                  int32_t* failed, void* ws, size_t ws_bytes, void* stream);
+
 /* Guided-matching depth refinement (Sec. 4.2 depth for new primitives,
  * App. A.2). For every pixel of the reference frame: n_cand inverse depths
  * d_k = d_lo + k (d_hi - d_lo) / (n_cand - 1), d_lo = max(1/Z* - window, 0),

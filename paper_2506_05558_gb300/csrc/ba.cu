@@ -600,6 +600,135 @@ static BaWs carve_ba(char* base, size_t cap, int F, int64_t P, size_t* used) {
     return w;
 }
 
+// ---------------------------------------------------------------------------
+// Pose refinement of a new frame (Sec. 4.1, subsequent frames): the same
+// robust iteration over one pose, points and focal length fixed. The 6 x 6
+// normal equations are summed per CTA (FP32 products, FP64 warp and CTA sums
+// in a fixed order); one CTA then damps, factors (L D L^T, FP64) and retracts.
+// The residual, median / MAD, trial-cost and accept kernels are the bundle
+// adjustment's with one frame.
+// ---------------------------------------------------------------------------
+constexpr int kBpThreads = 256;
+constexpr int kBpVals = 28;  // H upper triangle (21) | g (6) | cost
+
+__global__ void __launch_bounds__(kBpThreads) k_bp_normal(const float2* __restrict__ obs,
+                                                           const float* __restrict__ pose,
+                                                           const float4* __restrict__ pts,
+                                                           const float* __restrict__ fl_p, float cx, float cy,
+                                                           int64_t M, const float* __restrict__ e_cur,
+                                                           const float* __restrict__ thr_p, float delta,
+                                                           double* __restrict__ partial) {
+    __shared__ float s_pose[12];
+    __shared__ double s_w[kBpThreads / 32][kBpVals];
+    if (threadIdx.x < 12) s_pose[threadIdx.x] = pose[threadIdx.x];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v[kBpVals];
+#pragma unroll
+    for (int k = 0; k < kBpVals; k++) v[k] = 0.0;
+    if (i < M) {
+        BaObs o;
+        ba_observe(s_pose, pts[i], *fl_p, cx, cy, obs[i], o);
+        const bool keep = e_cur[i] <= *thr_p;
+        const float w = ba_weight(o.e, keep, delta);
+        float J[2][6];
+        const float qx = o.q[0], qy = o.q[1], qz = o.q[2];
+        for (int k = 0; k < 2; k++) {  // rho: jq; phi: jq (-q^), -q^ = [[0, qz, -qy], [-qz, 0, qx], [qy, -qx, 0]]
+            const float a0 = o.jq[k][0], a1 = o.jq[k][1], a2 = o.jq[k][2];
+            J[k][0] = a0; J[k][1] = a1; J[k][2] = a2;
+            J[k][3] = -a1 * qz + a2 * qy;
+            J[k][4] = a0 * qz - a2 * qx;
+            J[k][5] = -a0 * qy + a1 * qx;
+        }
+        int e = 0;
+#pragma unroll
+        for (int a = 0; a < 6; a++)
+#pragma unroll
+            for (int b = a; b < 6; b++) v[e++] = (double)(w * (J[0][a] * J[0][b] + J[1][a] * J[1][b]));
+#pragma unroll
+        for (int a = 0; a < 6; a++) v[21 + a] = (double)(w * (J[0][a] * o.r[0] + J[1][a] * o.r[1]));
+        v[27] = ba_cost(o.e, keep, delta);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < kBpVals; k++) {
+        double a = v[k];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) s_w[warp][k] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < kBpVals) {
+        double a = 0.0;
+        for (int wi = 0; wi < kBpThreads / 32; wi++) a += s_w[wi][threadIdx.x];
+        partial[(int64_t)blockIdx.x * kBpVals + threadIdx.x] = a;
+    }
+}
+
+// One thread: damping (H + lam diag(H) + 1e-9 I), L D L^T of the 6 x 6 system
+// in FP64, the step d = -A^-1 g and the retracted trial pose.
+__global__ void k_bp_solve(const double* __restrict__ tot, const float* __restrict__ pose,
+                           const float* __restrict__ lam_p, float* __restrict__ pose_t,
+                           double* __restrict__ cost_cur, int* __restrict__ fail) {
+    if (threadIdx.x != 0) return;
+    const double lam = *lam_p;
+    double A[6][6], g[6];
+    int e = 0;
+    for (int a = 0; a < 6; a++)
+        for (int b = a; b < 6; b++) { A[a][b] = tot[e]; A[b][a] = tot[e]; e++; }
+    for (int a = 0; a < 6; a++) { A[a][a] += lam * A[a][a] + 1e-9; g[a] = tot[21 + a]; }
+    bool bad = false;
+    double dinv[6];
+    for (int k = 0; k < 6; k++) {  // L D L^T, unit lower L stored below the diagonal
+        const double d = A[k][k];
+        if (!(d > 0.0)) bad = true;
+        dinv[k] = d > 0.0 ? 1.0 / d : 0.0;
+        double col[6];
+        for (int i = k + 1; i < 6; i++) col[i] = A[i][k];  // unscaled column k
+        for (int i = k + 1; i < 6; i++)
+            for (int j = k + 1; j <= i; j++) A[i][j] -= col[i] * col[j] * dinv[k];
+        for (int i = k + 1; i < 6; i++) A[i][k] = col[i] * dinv[k];
+    }
+    double y[6];
+    for (int i = 0; i < 6; i++) {
+        double a = -g[i];
+        for (int j = 0; j < i; j++) a -= A[i][j] * y[j];
+        y[i] = a;
+    }
+    for (int i = 0; i < 6; i++) y[i] *= dinv[i];
+    for (int i = 5; i >= 0; i--)
+        for (int j = i + 1; j < 6; j++) y[i] -= A[j][i] * y[j];
+    if (bad)
+        for (int i = 0; i < 6; i++) y[i] = 0.0;
+    if (bad) *fail = 1;
+    ba_retract(pose, y, pose_t);
+    *cost_cur = tot[27];
+}
+
+struct BpWs {
+    float *e, *pose_t, *fl_t, *thr;
+    double *partial, *tot, *trial_partial, *trial_total, *cost_cur;
+    int *iter, *fail;
+};
+
+static BpWs carve_bp(char* base, size_t cap, int64_t M, size_t* used) {
+    Carve c{base, 0, cap};
+    BpWs w;
+    const int64_t nb = ceil_div(M, kBpThreads), nt = ceil_div(M, 256);
+    w.e = c.take<float>(M);
+    w.pose_t = c.take<float>(12);
+    w.fl_t = c.take<float>(4);
+    w.thr = c.take<float>(1);
+    w.partial = c.take<double>(nb * kBpVals);
+    w.tot = c.take<double>(kBpVals);
+    w.trial_partial = c.take<double>(nt);
+    w.trial_total = c.take<double>(1);
+    w.cost_cur = c.take<double>(1);
+    w.iter = c.take<int>(1);
+    w.fail = c.take<int>(1);
+    *used = c.used;
+    return w;
+}
+
 static size_t ba_normal_smem() {
     return sizeof(float) * 12 * kBaMaxF + sizeof(float) * kBaPts * kBaMaxNc * 3 +
            sizeof(float) * kBaPts * kBaMaxNc * 3 + sizeof(double) * kBaPts * 3 +
@@ -688,3 +817,59 @@ extern "C" int gs_ba_project(const float* fl, const float* poses, const float* p
     GS_CUDA_CHECK_LAUNCH();
     return GS_OK;
 }
+
+extern "C" size_t gs_ba_pose_workspace_size(int64_t n_obs) {
+    if (n_obs < 1 || n_obs > kBaMaxObs) return 0;
+    size_t used = 0;
+    carve_bp(nullptr, 0, n_obs, &used);
+    return used;
+}
+
+extern "C" int gs_ba_pose_lm(const float* points, const float* obs, int64_t n_obs, const float* fl, float cx,
+                             float cy, float* pose, float* lam, int32_t iterations, float huber_delta, float nu,
+                             float* history, int32_t* failed, void* ws, size_t ws_bytes, void* stream) {
+    const int64_t M = n_obs;
+    if (!points || !obs || !fl || !pose || !lam || !failed || M < 1 || M > kBaMaxObs || iterations < 0 ||
+        !(huber_delta > 0.f) || !(nu > 1.f))
+        return GS_ERR_INVALID_ARG;
+    size_t need = 0;
+    BpWs w = carve_bp((char*)ws, ws_bytes, M, &need);
+    if (!ws || ws_bytes < need || ((uintptr_t)ws & 255) || ((uintptr_t)points & 15) || ((uintptr_t)obs & 7))
+        return GS_ERR_INVALID_ARG;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_ba_median_mad, cudaFuncAttributePreferredSharedMemoryCarveout, 25);
+        attr_set = true;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int nb = (int)ceil_div(M, kBpThreads), nt = (int)ceil_div(M, 256);
+    const float2* ob = (const float2*)obs;
+    const float4* pts = (const float4*)points;
+    cudaMemcpyAsync(w.fl_t, fl, sizeof(float), cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(w.iter, 0, sizeof(int), s);
+    cudaMemsetAsync(w.fail, 0, sizeof(int), s);
+    for (int it = 0; it < iterations; it++) {
+        k_ba_residual<<<nt, 256, 0, s>>>(ob, pose, pts, w.fl_t, cx, cy, 1, M, w.e);
+        count_launch();
+        k_ba_median_mad<<<1, kBaSelThreads, 0, s>>>(w.e, (int)M, w.thr);
+        count_launch();
+        k_bp_normal<<<nb, kBpThreads, 0, s>>>(ob, pose, pts, w.fl_t, cx, cy, M, w.e, w.thr, huber_delta, w.partial);
+        count_launch();
+        k_ba_reduce<<<1, dim3(32, 8), 0, s>>>(w.partial, nb, kBpVals, w.tot);
+        count_launch();
+        k_bp_solve<<<1, 32, 0, s>>>(w.tot, pose, lam, w.pose_t, w.cost_cur, w.fail);
+        count_launch();
+        k_ba_trial_cost<<<nt, 256, 0, s>>>(ob, w.pose_t, pts, w.fl_t, cx, cy, 1, M, w.e, w.thr, huber_delta,
+                                           w.trial_partial);
+        count_launch();
+        k_ba_sum<<<1, 256, 0, s>>>(w.trial_partial, nt, w.trial_total);
+        count_launch();
+        k_ba_accept<<<1, 32, 0, s>>>(w.trial_total, w.cost_cur, 1, 0, w.pose_t, nullptr, w.fl_t, pose, nullptr,
+                                     w.fl_t, lam, nu, history, w.iter);
+        count_launch();
+    }
+    cudaMemcpyAsync(failed, w.fail, sizeof(int), cudaMemcpyDeviceToDevice, s);
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+

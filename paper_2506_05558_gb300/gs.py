@@ -36,6 +36,7 @@ EXPORTS = [
     "gs_pose_apply", "gs_pose_tangent_grad", "gs_anchor_merge_workspace_size", "gs_anchor_merge",
     "gs_anchor_blend_weight", "gs_scale_opacity", "gs_cull_opacity_workspace_size", "gs_cull_opacity",
     "gs_downsample", "gs_ba_workspace_size", "gs_ba_lm", "gs_ba_project", "gs_guided_depth",
+    "gs_ba_pose_workspace_size", "gs_ba_pose_lm",
 ]
 
 
@@ -145,6 +146,9 @@ def lib():
             "gs_ba_lm": (C.c_int, [P, C.c_int32, C.c_int64, C.c_float, C.c_float, P, P, P, P, C.c_int32, C.c_float,
                                    C.c_float, P, P, P, C.c_size_t, P]),
             "gs_pose_apply": (C.c_int, [P, P, C.c_int32, P, P]),
+            "gs_ba_pose_workspace_size": (C.c_size_t, [C.c_int64]),
+            "gs_ba_pose_lm": (C.c_int, [P, P, C.c_int64, P, C.c_float, C.c_float, P, P, C.c_int32, C.c_float, C.c_float,
+                                        P, P, P, C.c_size_t, P]),
             "gs_guided_depth": (C.c_int, [P, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P, C.c_int32, C.c_float,
                                           P, P, P, P]),
             "gs_anchor_merge_workspace_size": (C.c_size_t, [C.c_int64, C.c_int32]),
@@ -706,6 +710,20 @@ def gs_ba_lm(obs: torch.Tensor, cx: float, cy: float, fl: torch.Tensor, poses: t
     _check(lib().gs_ba_lm(_ptr(obs), F, P, cx, cy, _ptr(fl), _ptr(poses), _ptr(points), _ptr(lam), iterations,
                           huber_delta, nu, _ptr(history), _ptr(failed), _ptr(ws), ws.numel(), _stream(stream)),
            "gs_ba_lm")
+
+
+def gs_ba_pose_workspace_size(n_obs: int) -> int:
+    return int(lib().gs_ba_pose_workspace_size(n_obs))
+
+
+def gs_ba_pose_lm(points: torch.Tensor, obs: torch.Tensor, fl: torch.Tensor, cx: float, cy: float,
+                  pose: torch.Tensor, lam: torch.Tensor, iterations: int, ws: torch.Tensor, failed: torch.Tensor,
+                  huber_delta: float = 2.0, nu: float = 2.0, history: torch.Tensor | None = None, stream=None):
+    """Levenberg-Marquardt refinement of one pose [12] from points [M][4] and
+    their observations obs [M][2] (all device; points and fl fixed)."""
+    _check(lib().gs_ba_pose_lm(_ptr(points), _ptr(obs), obs.shape[0], _ptr(fl), cx, cy, _ptr(pose), _ptr(lam),
+                               iterations, huber_delta, nu, _ptr(history), _ptr(failed), _ptr(ws), ws.numel(),
+                               _stream(stream)), "gs_ba_pose_lm")
 
 
 def gs_ba_project(fl: torch.Tensor, poses: torch.Tensor, points: torch.Tensor, cx: float, cy: float,

@@ -322,3 +322,22 @@ def guided_scene(seed=1006, width=1920, height=1080, f=1500.0, n_nb=4, channels=
     z_mono = (z_true * np.exp(rng.normal(0, mono_sd, z_true.shape))).astype(np.float32)
     z_mono[rng.random(z_true.shape) < mono_holes] = 0.0
     return dict(cams=cams, feats=feats, z_mono=z_mono, z_true=z_true)
+
+
+def ba_pose_problem(seed=1007, n_obs=6144, width=1920, fl=1500.0, noise_px=0.5, outlier_frac=0.1):
+    """Seeded inputs of a new frame's pose refinement (6144 keypoints matched
+    to triangulated points): points in a box 3-8 m ahead, the true pose as a
+    tangent step (0.3 m and a few degrees, jittered), per-observation pixel
+    noise and gross outliers (30-80 px on outlier_frac of them), and the start
+    pose's tangent offset (about 0.02 rad / 0.02 m, a RANSAC estimate). Only
+    random draws: the caller builds the pose and the observations."""
+    rng = _rng(seed)
+    M = n_obs
+    X = np.stack([rng.uniform(-2, 2, M), rng.uniform(-1.5, 1.5, M), rng.uniform(3, 8, M)], 1)
+    xi = np.concatenate([rng.normal(0, 0.05, 3) + [0.3, 0, 0], rng.normal(0, 0.02, 3) + [0, 0.05, 0]])
+    noise = rng.normal(0, noise_px, (M, 2))
+    out = rng.random(M) < outlier_frac
+    ang = rng.uniform(0, 2 * np.pi, M)
+    mag = rng.uniform(30, 80, M)
+    noise[out] += np.stack([np.cos(ang), np.sin(ang)], -1)[out] * mag[out][:, None]
+    return dict(X=X, xi=xi, noise=noise, fl=fl, width=width, start_xi=rng.normal(0, 0.02, 6))

@@ -158,3 +158,92 @@ def test_large_problem_cost_and_threshold():
     _, _, hist = run_gpu(obs, params, 1)
     assert lo * (1 - 1e-4) <= hist[0, 0] <= hi * (1 + 1e-4)
     assert B.robust_cost(e, e <= thr, 2.0) > 0 and hist[0, 1] > 0
+
+
+# ---------------------------------------------------------------------------
+# pose refinement of a new frame (points and focal length fixed)
+# ---------------------------------------------------------------------------
+
+def pose_problem(seed, M=500):
+    rng = np.random.default_rng(seed)
+    R, t, X, obs, cx, cy, out = B.synthetic_pose_problem(rng, M=M, noise_px=0.5, outlier_frac=0.1)
+    R0, t0 = O.retract_pose(R, t, rng.normal(0, 0.02, 6))
+    r32 = lambda a: np.asarray(a, np.float32).astype(np.float64)
+    return (R, t), r32(X), r32(obs), cx, cy, r32(R0), r32(t0), out
+
+
+def run_pose_gpu(X, obs, R0, t0, iterations, fl=500.0, lam0=1e-5, graph=False):
+    M = X.shape[0]
+    f32 = lambda a: torch.tensor(np.asarray(a, np.float32), device="cuda").contiguous()
+    pts = f32(np.concatenate([X, np.zeros((M, 1))], 1))
+    ob = f32(obs)
+    flt = f32([fl])
+    pose = f32(np.concatenate([R0.reshape(9), t0]))
+    lam = f32([lam0])
+    ws = gs.workspace(gs.gs_ba_pose_workspace_size(M))
+    hist = torch.zeros((max(iterations, 1), 3), device="cuda")
+    failed = torch.zeros(1, dtype=torch.int32, device="cuda")
+    if graph:
+        gs.gs_ba_pose_lm(pts, ob, flt, CX, CY, pose.clone(), lam.clone(), 1, ws, failed)  # set-up outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        with torch.cuda.graph(g, stream=s):
+            gs.gs_ba_pose_lm(pts, ob, flt, CX, CY, pose, lam, iterations, ws, failed, history=hist, stream=s)
+        g.replay()
+    else:
+        gs.gs_ba_pose_lm(pts, ob, flt, CX, CY, pose, lam, iterations, ws, failed, history=hist)
+    torch.cuda.synchronize()
+    assert int(failed.item()) == 0
+    pz = pose.cpu().numpy().astype(np.float64)
+    return pz[:9].reshape(3, 3), pz[9:], float(lam.item()), hist.cpu().numpy()
+
+
+def test_pose_one_iteration_matches_oracle():
+    _, X, obs, cx, cy, R0, t0, _ = pose_problem(21)
+    assert (cx, cy) == (CX, CY)
+    e = np.linalg.norm(B.project(500.0, cx, cy, R0, t0, X) - obs, axis=1)
+    med = B.lower_median(e)
+    thr = med + 4 * B.lower_median(np.abs(e - med))
+    assert np.abs(e - thr).min() > 1e-4 * thr
+    R1, t1, lam_ref, info = B.pose_lm_iteration(R0, t0, 1e-5, X, obs, 500.0, cx, cy)
+    R, t, lam, hist = run_pose_gpu(X, obs, R0, t0, 1)
+    assert info["accepted"] and hist[0, 2] == 1.0 and abs(lam - lam_ref) < 1e-12
+    assert abs(hist[0, 0] - info["cost"]) < 1e-4 * info["cost"]
+    assert abs(hist[0, 1] - info["trial_cost"]) < 1e-3 * info["trial_cost"]
+    assert np.abs(R - R1).max() < 2e-6 and np.abs(t - t1).max() < 2e-6
+
+
+def test_pose_twenty_iterations_recover_the_pose():
+    (Rt, tt), X, obs, cx, cy, R0, t0, _ = pose_problem(22, M=2000)
+    R, t, lam, hist = run_pose_gpu(X, obs, R0, t0, 20)
+    Rr, tr, lr = R0, t0, 1e-5
+    for _ in range(20):
+        Rr, tr, lr, info = B.pose_lm_iteration(Rr, tr, lr, X, obs, 500.0, cx, cy)
+    for Ra, ta in ((R, t), (Rr, tr)):
+        ang = np.arccos(np.clip((np.trace(Ra @ Rt.T) - 1) / 2, -1, 1))
+        assert ang < 1e-3 and np.linalg.norm(ta - tt) < 5e-3
+    assert abs(hist[-1, 0] - info["cost"]) < 1e-2 * info["cost"]
+
+
+def test_pose_graph_replay_is_bit_exact():
+    _, X, obs, cx, cy, R0, t0, _ = pose_problem(23, M=6144)
+    a = run_pose_gpu(X, obs, R0, t0, 20)
+    b = run_pose_gpu(X, obs, R0, t0, 20, graph=True)
+    c = run_pose_gpu(X, obs, R0, t0, 20)
+    for x, y, z in zip(a, b, c):
+        assert np.array_equal(np.asarray(x), np.asarray(y)) and np.array_equal(np.asarray(x), np.asarray(z))
+
+
+def test_pose_invalid_arguments():
+    assert gs.gs_ba_pose_workspace_size(0) == 0 and gs.gs_ba_pose_workspace_size(1 << 27) == 0
+    pts = torch.zeros((10, 4), device="cuda")
+    ob = torch.zeros((10, 2), device="cuda")
+    f = torch.ones(1, device="cuda")
+    pose = torch.zeros(12, device="cuda")
+    failed = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = gs.workspace(gs.gs_ba_pose_workspace_size(10))
+    with pytest.raises(RuntimeError):
+        gs.gs_ba_pose_lm(pts, ob, f, 0, 0, pose, f, 1, ws, failed, nu=1.0)
+    with pytest.raises(RuntimeError):
+        gs.gs_ba_pose_lm(pts, ob, f, 0, 0, pose, f, 1, ws[:16], failed)  # workspace too small
