@@ -9,10 +9,11 @@
 // evaluates only the hits, so Gaussians that cannot touch any of its pixels
 // cost nothing. The forward stops a CTA when every pixel's transmittance has
 // terminated. The adjoint recomputes the blending state back to front from
-// T_final and n_contrib, reduces each Gaussian's 9 partial derivatives across
-// the warp with a transposing butterfly (12 shuffles for 9 values), sums the
-// warps in a fixed order and writes ONE partial per (tile, Gaussian) pair to
-// the pair's emission slot. No atomics touch gradients: bit-reproducible.
+// T_final and n_contrib, records per pixel and Gaussian two scalars in a
+// per-warp table, forms each Gaussian's 9 partial derivatives from the table
+// (sums over the warp's pixels in a fixed order), sums the warps in a fixed
+// order and writes ONE partial per (tile, Gaussian) pair to the pair's
+// emission slot. No atomics touch gradients: bit-reproducible.
 //
 // Scheduling: either one CTA per tile (grid order), or persistent CTAs (as
 // many as fit on the SMs) that pull tiles from a global counter in the order
@@ -200,40 +201,15 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
     }
 }
 
-// Warp-wide sum of 9 values by a transposing butterfly: after 5 exchange rounds
-// (5+3+2+1+1 shuffles) even lane L holds the full sum of value kOwner[L>>1].
-__device__ __constant__ int8_t kOwner[16] = {0, 1, 2, -1, 3, 4, -1, -1, 5, 6, 7, -1, 8, -1, -1, -1};
-
-__device__ __forceinline__ float warp_reduce9(const float (&v)[9], int lane) {
-    const unsigned F = 0xffffffffu;
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
-    float s[5];
-#pragma unroll
-    for (int k = 0; k < 5; k++) {
-        const float lo = v[k];
-        const float hi = k < 4 ? v[5 + k] : 0.f;
-        const float send = b4 ? lo : hi;
-        const float keep = b4 ? hi : lo;
-        s[k] = keep + __shfl_xor_sync(F, send, 16);
-    }
-    float t[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) {
-        const float lo = s[k];
-        const float hi = k < 2 ? s[3 + k] : 0.f;
-        t[k] = (b3 ? hi : lo) + __shfl_xor_sync(F, b3 ? lo : hi, 8);
-    }
-    float u[2];
-#pragma unroll
-    for (int k = 0; k < 2; k++) {
-        const float lo = t[k];
-        const float hi = k < 1 ? t[2] : 0.f;
-        u[k] = (b2 ? hi : lo) + __shfl_xor_sync(F, b2 ? lo : hi, 4);
-    }
-    float w = (b1 ? u[1] : u[0]) + __shfl_xor_sync(F, b1 ? u[0] : u[1], 2);
-    w += __shfl_xor_sync(F, w, 1);
-    return w;
-}
+// Compositing adjoint. Per pixel (one lane) and Gaussian, back to front: the
+// transmittance in front of it, dL/dalpha and from it the two scalars that all
+// nine gradient terms of the (tile, Gaussian) pair are built from - dpow =
+// dL/d(exponent) and the blending weight. Rather than a 9-value warp reduction
+// per Gaussian, each warp keeps the scalars of its last kBwdHits Gaussians in a
+// shared table (row = Gaussian, column = pixel) and, when full, four lanes per
+// Gaussian form sum(dpow), sum(dpow dx), ..., sum(w dL/dc) over eight pixels
+// each and combine in a fixed order: about a third fewer instructions per hit.
+constexpr int kBwdHits = 8;  // hits per table flush (4 lanes per hit, 8 pixels each)
 
 template <int TILE, int BB>
 __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_config cfg,
@@ -259,11 +235,15 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
     __shared__ uint32_t s_emit[BB];
     __shared__ float s_part[NW][BB][9];
     __shared__ uint32_t s_hit[NW][BB / 32];  // which Gaussians each warp wrote
+    // per warp: the last HB hits' per-pixel adjoint scalars (row = hit, column =
+    // pixel) and each pixel's colour gradient
+    __shared__ float s_td[NW][kBwdHits][33];
+    __shared__ float s_tw[NW][kBwdHits][33];
+    __shared__ float4 s_pix[NW][32];
     __shared__ int s_max;
     __shared__ int s_item;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int8_t owner = (lane & 1) ? (int8_t)-1 : kOwner[lane >> 1];
     const float inv_log2e = 1.f / kLog2e;
     for (int tile = next_tile(order, counter, n_tiles, true, &s_item); tile >= 0;
          tile = next_tile(order, counter, n_tiles, false, &s_item)) {
@@ -300,6 +280,56 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
         // background seen through the final transmittance, folded into the "behind" term
         const float bgr = Tf * cfg.bg[0], bgg = Tf * cfg.bg[1], bgb = Tf * cfg.bg[2];
         float T = Tf, Sr = 0.f, Sg = 0.f, Sb = 0.f;
+        s_pix[w][lane] = make_float4(gr, gg, gb, 0.f);
+        int nh = 0;    // hits recorded in this warp's table (warp-uniform)
+        int myk = 0;   // the staged index of hit (lane % HB) of the table
+        // Sums over the warp's 32 pixels of the 9 gradient terms of each recorded
+        // hit: lanes r, r + HB, ... share hit r, each summing 32 / L pixels from the
+        // table, then combine in a fixed order; the first writes the CTA partial.
+        auto flush = [&]() {
+            __syncwarp();
+            const int r = lane % kBwdHits, part = lane / kBwdHits;
+            const bool act = r < nh;
+            float S[9];
+#pragma unroll
+            for (int c = 0; c < 9; c++) S[c] = 0.f;
+            float4 abco = make_float4(0.f, 0.f, 0.f, 1.f);
+            if (act) {
+                const float2 xy = s_xy[myk];
+                abco = s_abco[myk];
+                // pixel p = part * HB + i sits at (x0 + (p & 7), y0 + (p >> 3)): the same
+                // floats as the compositing pass's pixel centres, so dx, dy are identical
+                const float yb = wb.y0 + (float)((part * kBwdHits) >> 3) - xy.y;
+#pragma unroll
+                for (int i = 0; i < kBwdHits; i++) {
+                    const int pp = part * kBwdHits + i;
+                    const float dx = (wb.x0 + (float)(i & 7)) - xy.x;
+                    const float dy = yb + (float)(i >> 3);
+                    const float d = s_td[w][r][pp], wv = s_tw[w][r][pp];
+                    const float4 pc = s_pix[w][pp];
+                    const float t1 = d * dx, t2 = d * dy;
+                    S[0] += d; S[1] += t1; S[2] += t2;
+                    S[3] += t1 * dx; S[4] += t1 * dy; S[5] += t2 * dy;
+                    S[6] += wv * pc.x; S[7] += wv * pc.y; S[8] += wv * pc.z;
+                }
+            }
+#pragma unroll
+            for (int off = kBwdHits; off < 32; off <<= 1)
+#pragma unroll
+                for (int c = 0; c < 9; c++) S[c] += __shfl_xor_sync(FULL, S[c], off);
+            if (act && part == 0) {
+                float* o = s_part[w][myk];
+                o[0] = -inv_log2e * (2.f * abco.x * S[1] + abco.y * S[2]);
+                o[1] = -inv_log2e * (abco.y * S[1] + 2.f * abco.z * S[2]);
+                o[2] = -0.5f * S[3];
+                o[3] = -S[4];
+                o[4] = -0.5f * S[5];
+                o[5] = abco.w > 0.f ? S[0] / abco.w : 0.f;  // sum of dalpha G = sum of dalpha (o G) / o
+                o[6] = S[6]; o[7] = S[7]; o[8] = S[8];
+            }
+            nh = 0;
+            __syncwarp();
+        };
         for (int bend = n_list; bend > 0; bend -= BB) {
             const int b0 = max(0, bend - BB);
             const int cnt = bend - b0;
@@ -345,22 +375,18 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
                         // of a lane outside the Gaussian out of the sums
                         const bool pass = contrib && og < cfg.alpha_max;
                         const float dpow = pass ? dalpha * og : 0.f;  // d alpha / d(natural exponent)
-                        const float q = -dpow * inv_log2e;  // (a dx + b dy) = -(2A dx + B dy)/log2(e)
-                        float g[9];
-                        g[0] = q * (2.f * abco.x * dx + abco.y * dy);
-                        g[1] = q * (abco.y * dx + 2.f * abco.z * dy);
-                        g[2] = -0.5f * dpow * dx * dx;
-                        g[3] = -dpow * dx * dy;
-                        g[4] = -0.5f * dpow * dy * dy;
-                        g[5] = pass ? dalpha * G : 0.f;
-                        g[6] = wgt * gr; g[7] = wgt * gg; g[8] = wgt * gb;
-                        const float r = warp_reduce9(g, lane);
-                        if (owner >= 0) s_part[w][k][owner] = r;
+                        // record this pixel's two scalars; the 9 gradient terms are summed
+                        // over the warp's pixels when the table is full
+                        s_td[w][nh][lane] = dpow;
+                        s_tw[w][nh][lane] = wgt;
+                        if (lane % kBwdHits == nh) myk = k;
                         written |= 1u << jb;
+                        if (++nh == kBwdHits) flush();
                     }
                 }
                 if (lane == 0) s_hit[w][ch] = written;
             }
+            if (nh > 0) flush();
             __syncthreads();
             for (int j = threadIdx.x; j < cnt; j += NT) {
                 const int ch = j >> 5;
@@ -413,7 +439,7 @@ static RenderLaunch pick_bwd(int tile, int batch) {
 }
 
 static int default_fwd_batch(int tile) { return tile == 8 ? 128 : 256; }
-static int default_bwd_batch(int tile) { return tile == 32 ? 32 : 128; }
+static int default_bwd_batch(int tile) { return tile == 32 ? 32 : tile == 16 ? 64 : 128; }
 
 static int launch(const RenderLaunch& L, int n_tiles, bool persistent, void** args, cudaStream_t s) {
     int grid = n_tiles;
