@@ -598,7 +598,7 @@ def main():
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the spawn / MLP / anchor measurements")
-    ap.add_argument("--cpu-views", type=int, default=3, help="views of the oracle CPU sample")
+    ap.add_argument("--cpu-views", type=int, default=6, help="views of the oracle CPU sample")
     ap.add_argument("--row", choices=["mini_ba", "pose_refine", "guided_matching"], default=None,
                     help="measure only this side row and print its numbers (for profiling)")
     ap.add_argument("--ba-iterations", type=int, default=200)
