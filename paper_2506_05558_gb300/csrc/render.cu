@@ -237,8 +237,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
     __shared__ uint32_t s_hit[NW][BB / 32];  // which Gaussians each warp wrote
     // per warp: the last HB hits' per-pixel adjoint scalars (row = hit, column =
     // pixel) and each pixel's colour gradient
-    __shared__ float s_td[NW][kBwdHits][33];
-    __shared__ float s_tw[NW][kBwdHits][33];
+    __shared__ float2 s_tdw[NW][kBwdHits][33];  // (dpow, weight)
     __shared__ float4 s_pix[NW][32];
     __shared__ int s_max;
     __shared__ int s_item;
@@ -305,7 +304,8 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
                     const int pp = part * kBwdHits + i;
                     const float dx = (wb.x0 + (float)(i & 7)) - xy.x;
                     const float dy = yb + (float)(i >> 3);
-                    const float d = s_td[w][r][pp], wv = s_tw[w][r][pp];
+                    const float2 dw = s_tdw[w][r][pp];
+                    const float d = dw.x, wv = dw.y;
                     const float4 pc = s_pix[w][pp];
                     const float t1 = d * dx, t2 = d * dy;
                     S[0] += d; S[1] += t1; S[2] += t2;
@@ -377,8 +377,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
                         const float dpow = pass ? dalpha * og : 0.f;  // d alpha / d(natural exponent)
                         // record this pixel's two scalars; the 9 gradient terms are summed
                         // over the warp's pixels when the table is full
-                        s_td[w][nh][lane] = dpow;
-                        s_tw[w][nh][lane] = wgt;
+                        s_tdw[w][nh][lane] = make_float2(dpow, wgt);
                         if (lane % kBwdHits == nh) myk = k;
                         written |= 1u << jb;
                         if (++nh == kBwdHits) flush();
