@@ -551,6 +551,34 @@ def oracle_sample(n_views_sample=1, n=N_GAUSS):
     return n_views_sample / dt, dt, cores
 
 
+class Ranks:
+    """Rank bookkeeping of a torchrun launch (one process per GPU, replicas):
+    a barrier, the maximum of a per-rank time over all ranks, and the whole-job
+    throughput from it. With one rank every call is local; the tensors of the
+    collective live on `device` (a GPU under NCCL, the host under gloo)."""
+
+    def __init__(self, world: int, rank: int, device, dist=None):
+        self.world, self.rank, self.device, self.dist = world, rank, device, dist
+
+    def barrier(self):
+        if self.world > 1:
+            self.dist.barrier()
+
+    def max(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        import torch
+        t = torch.tensor([x], device=self.device, dtype=torch.float64)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def throughput(self, units_per_rank: float, ms_local: float) -> tuple[float, float]:
+        """(whole-job units per second, slowest rank's ms): every rank processed
+        units_per_rank in its own timed region; the job took the longest one."""
+        ms = self.max(ms_local)
+        return self.world * units_per_rank / (ms / 1000.0), ms
+
+
 def run_reference(args, rank, world):
     """The oracle as the reference arm: each step is one 1080p view's fwd+bwd
     (a bounded sample of the 8-view step) on the host cores."""
@@ -623,16 +651,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device(device))
 
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    ranks = Ranks(world, rank, device, dist)
+    barrier, max_over_ranks = ranks.barrier, ranks.max
 
     gs.lib()
     if args.row is not None:  # one side row alone, rank 0 only
@@ -693,10 +713,9 @@ def main():
     barrier()
     time.sleep(0.1)
     clk = clocks.stop()
-    ms = max_over_ranks(t_start.elapsed_time(t_end))
+    value, ms = ranks.throughput(args.views * args.steps, t_start.elapsed_time(t_end))
     stage_ms = {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)]))
                 for i, (name, _) in enumerate(J.graphs)}
-    value = world * args.views * args.steps / (ms / 1000.0)
     status = J.r.status()
     n_items_vis = int((J.r.proj.n_tiles > 0).sum().item())
     P = J.r.pair_count()
