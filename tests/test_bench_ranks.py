@@ -32,7 +32,7 @@ def _worker(rank, world, port, out):
 
 def test_two_ranks_take_the_slowest_time_and_sum_the_units():
     world, port = 2, 29500 + os.getpid() % 1000
-    out = mp.Manager().dict()
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     for rank in range(world):
         value, ms = out[rank]
