@@ -278,7 +278,9 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
         }
         // background seen through the final transmittance, folded into the "behind" term
         const float bgr = Tf * cfg.bg[0], bgg = Tf * cfg.bg[1], bgb = Tf * cfg.bg[2];
-        float T = Tf, Sr = 0.f, Sg = 0.f, Sb = 0.f;
+        // Sr, Sg, Sb: colour composited behind the current Gaussian plus the background
+        // seen through T_final
+        float T = Tf, Sr = bgr, Sg = bgg, Sb = bgb;
         s_pix[w][lane] = make_float4(gr, gg, gb, 0.f);
         int nh = 0;    // hits recorded in this warp's table (warp-uniform)
         int myk = 0;   // the staged index of hit (lane % HB) of the table
@@ -296,22 +298,25 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
             if (act) {
                 const float2 xy = s_xy[myk];
                 abco = s_abco[myk];
-                // pixel p = part * HB + i sits at (x0 + (p & 7), y0 + (p >> 3)): the same
-                // floats as the compositing pass's pixel centres, so dx, dy are identical
-                const float yb = wb.y0 + (float)((part * kBwdHits) >> 3) - xy.y;
+                // pixel p = 8 part + i sits at (x0 + i, y0 + part): the same floats as the
+                // compositing pass's pixel centres, so dx is identical; dy is constant over
+                // this lane's row, so the dy terms follow from sum(d) and sum(d dx)
+                static_assert(kBwdHits == 8, "one pixel row per lane");
+                const float dy = (wb.y0 + (float)part) - xy.y;
 #pragma unroll
                 for (int i = 0; i < kBwdHits; i++) {
                     const int pp = part * kBwdHits + i;
-                    const float dx = (wb.x0 + (float)(i & 7)) - xy.x;
-                    const float dy = yb + (float)(i >> 3);
+                    const float dx = (wb.x0 + (float)i) - xy.x;
                     const float2 dw = s_tdw[w][r][pp];
                     const float d = dw.x, wv = dw.y;
                     const float4 pc = s_pix[w][pp];
-                    const float t1 = d * dx, t2 = d * dy;
-                    S[0] += d; S[1] += t1; S[2] += t2;
-                    S[3] += t1 * dx; S[4] += t1 * dy; S[5] += t2 * dy;
+                    const float t1 = d * dx;
+                    S[0] += d; S[1] += t1; S[3] += t1 * dx;
                     S[6] += wv * pc.x; S[7] += wv * pc.y; S[8] += wv * pc.z;
                 }
+                S[2] = dy * S[0];
+                S[4] = dy * S[1];
+                S[5] = dy * S[2];
             }
 #pragma unroll
             for (int off = kBwdHits; off < 32; off <<= 1)
@@ -367,8 +372,8 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
                         T = contrib ? T * inv : T;  // transmittance in front of this Gaussian
                         const float4 c = s_rgb[k];
                         const float wgt = contrib ? alpha * T : 0.f;
-                        const float dalpha = gr * (T * c.x - (Sr + bgr) * inv) + gg * (T * c.y - (Sg + bgg) * inv) +
-                                             gb * (T * c.z - (Sb + bgb) * inv);
+                        const float dalpha = gr * (T * c.x - Sr * inv) + gg * (T * c.y - Sg * inv) +
+                                             gb * (T * c.z - Sb * inv);
                         Sr += wgt * c.x; Sg += wgt * c.y; Sb += wgt * c.z;
                         // alpha clamped at alpha_max passes no gradient to the exponent or
                         // opacity; selects (not products with 0) keep a non-finite og or G
