@@ -44,7 +44,7 @@ __device__ __forceinline__ float out_value(const float* s_slot, int w0, int nw, 
     return a;
 }
 
-__global__ void __launch_bounds__(kPBThreads, 2) k_project_bwd(
+__global__ void __launch_bounds__(kPBThreads, 3) k_project_bwd(
     const float4* __restrict__ mean_opa, const float4* __restrict__ scale, const float4* __restrict__ quat,
     const float4* __restrict__ sh, int64_t n, const gs_camera* __restrict__ cams, gs_frame f, gs_config cfg,
     const int32_t* __restrict__ n_tiles, const uint32_t* __restrict__ offset, const float4* __restrict__ part0,
