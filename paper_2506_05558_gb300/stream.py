@@ -105,7 +105,7 @@ class OnTheFly:
                  mlp_warmup_frames: int = 3, mlp_steps: int = 40, keep_threshold: float = 0.05, seed: int = 7,
                  anchor_tau: float = 1.0, anchor_share: float = 0.4, merge_radius: float = 0.5,
                  coarse_to_fine: int = 0, mip_filter: bool = False, lr_decay: float = 1.0,
-                 min_opacity: float = 0.0, device="cuda"):
+                 min_opacity: float = 0.0, guided_neighbours: int = 0, device="cuda"):
         self.store = GaussianStore(capacity, device)
         self.W, self.H = size
         self.window = window
@@ -152,6 +152,10 @@ class OnTheFly:
         self.merge_radius = merge_radius
         self.too_fine = torch.zeros((capacity,), dtype=torch.uint8, device=device)
         self.count = torch.zeros((1,), dtype=torch.int64, device=device)
+        # guided matching (App. A.2): the given depth of a new frame is a monocular
+        # estimate, refined against the feature maps of up to this many earlier frames
+        self.guided_neighbours = guided_neighbours
+        self.feat_frames = []  # (feature map [H][W][C] bf16 bits, camera)
 
     # -- anchors -------------------------------------------------------------------
     def _maybe_anchor(self, frame_idx):
@@ -305,7 +309,27 @@ class OnTheFly:
                                  self.mlp_cfg, self.mlp_step, self.mlp_loss, self.ws_mlp)
         return float(self.mlp_loss.item())
 
-    def add_frame(self, image: torch.Tensor, depth: torch.Tensor, cam: torch.Tensor, frame_idx: int):
+    def _guided_depth(self, depth: torch.Tensor, feats, cam: torch.Tensor):
+        """The frame's monocular depth refined by guided matching against the
+        stored earlier frames (unchanged for the first frame)."""
+        if feats is None:
+            return depth
+        prev = self.feat_frames[-self.guided_neighbours:]
+        self.feat_frames.append((feats, cam))
+        if not prev:
+            return depth
+        stack = torch.stack([feats] + [f for f, _ in prev]).contiguous()
+        cams = torch.cat([cam] + [c for _, c in prev])
+        out = gs.gs_guided_depth(stack, cams, depth.reshape(self.H, self.W).contiguous())
+        return out.reshape(depth.shape)
+
+    def add_frame(self, image: torch.Tensor, depth: torch.Tensor, cam: torch.Tensor, frame_idx: int,
+                  feats: torch.Tensor | None = None):
+        """One new frame: image [3HW], depth [HW] (the spawn depth; with
+        guided_neighbours > 0 and feats [H][W][C] given, a monocular estimate
+        refined by guided matching first), camera tensor."""
+        if self.guided_neighbours > 0:
+            depth = self._guided_depth(depth, feats, cam)
         anchor = self._maybe_anchor(frame_idx)
         render = self._render_active(cam)
         k, learned = self._spawn(image, render, depth, cam, frame_idx)

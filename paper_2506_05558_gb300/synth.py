@@ -341,3 +341,56 @@ def ba_pose_problem(seed=1007, n_obs=6144, width=1920, fl=1500.0, noise_px=0.5, 
     mag = rng.uniform(30, 80, M)
     noise[out] += np.stack([np.cos(ang), np.sin(ang)], -1)[out] * mag[out][:, None]
     return dict(X=X, xi=xi, noise=noise, fl=fl, width=width, start_xi=rng.normal(0, 0.02, 6))
+
+
+def surface_scene(seed=1008, n=120_000, n_views=10, size=(256, 144), f=200.0):
+    """Gaussians on the surfaces of a room (back wall, floor, ceiling, side walls,
+    four fronto-parallel boxes 5.5-7.5 m ahead; every surface stays a few metres
+    from the camera path): small flat discs (in-plane scale
+    3 cm, 3 mm along the normal), nearly opaque (opacity logit 4), random
+    colours - so rendered images and per-Gaussian feature maps are consistent
+    across views, as on real textured surfaces - seen by n_views cameras along
+    the standard path (0.3 m and 5 degrees per frame). Returns (Scene, cameras)."""
+    rng = _rng(seed)
+    # (origin, u axis, v axis): rectangle origin + a u + b v, a, b in [0, 1]
+    rects = [((-4.0, -2.2, 9.0), (8.0, 0, 0), (0, 4.0, 0)),     # back wall z = 9
+             ((-4.0, 1.6, 0.5), (8.0, 0, 0), (0, 0, 8.5)),      # floor y = 1.6
+             ((-4.0, -2.2, 0.5), (8.0, 0, 0), (0, 0, 8.5)),     # ceiling y = -2.2
+             ((-3.5, -2.2, 0.5), (0, 3.8, 0), (0, 0, 8.5)),     # left wall x = -3.5
+             ((3.5, -2.2, 0.5), (0, 3.8, 0), (0, 0, 8.5))]      # right wall x = 3.5
+    for _ in range(4):
+        zc, xc, yc = rng.uniform(5.5, 7.5), rng.uniform(-2, 2), rng.uniform(-1, 1)
+        hw, hh = rng.uniform(0.3, 1.0), rng.uniform(0.3, 1.0)
+        rects.append(((xc - hw, yc - hh, zc), (2 * hw, 0, 0), (0, 2 * hh, 0)))
+    area = np.array([np.linalg.norm(np.cross(u, v)) for _, u, v in rects])
+    which = rng.choice(len(rects), n, p=area / area.sum())
+    ab = rng.random((n, 2))
+    mean = np.empty((n, 3))
+    quat = np.empty((n, 4))
+    for k, (o, u, v) in enumerate(rects):
+        m = which == k
+        o, u, v = np.asarray(o), np.asarray(u, float), np.asarray(v, float)
+        mean[m] = o + ab[m, :1] * u + ab[m, 1:] * v
+        nrm = np.cross(u, v)
+        nrm /= np.linalg.norm(nrm)
+        # rotation taking the z axis to the normal (the disc's thin axis)
+        axis = np.cross([0.0, 0.0, 1.0], nrm)
+        s, c = np.linalg.norm(axis), nrm[2]
+        if s < 1e-9:
+            q = np.array([1.0, 0.0, 0.0, 0.0])
+        else:
+            ang = math.atan2(s, c)
+            axis /= s
+            q = np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * axis])
+        quat[m] = q
+    scale = np.zeros((n, 4))
+    scale[:, 0] = scale[:, 1] = math.log(0.03)
+    scale[:, 2] = math.log(0.003)
+    sh = np.zeros((n, 48))
+    sh[:, :3] = rng.normal(0, DC_STD, (n, 3))
+    mean_opa = np.concatenate([mean, np.full((n, 1), 4.0)], 1)
+    sc = Scene(mean_opa.astype(np.float32), scale.astype(np.float32), quat.astype(np.float32),
+               sh.astype(np.float32), 0)
+    path = camera_path(rng, n_views)
+    cams = [camera(*world_to_camera(R, c), f, size[0], size[1]) for R, c in path]
+    return sc, cams
