@@ -15,6 +15,9 @@ from paper_2506_05558_gb300.stream import OnTheFly, render_depth
 
 pytestmark = pytest.mark.gpu
 
+# where the streaming comparisons write their JSON reports
+REPORT_DIR = os.environ.get("GS_REPORT_DIR", "test_reports")
+
 
 @pytest.fixture(scope="module", autouse=True)
 def built():
@@ -60,8 +63,8 @@ def test_learned_vs_plain_spawning():
                                     "spawned_learned": [e["spawned"] for e in b.log],
                                     "spawned_plain": [e["spawned"] for e in a.log]}
         assert p_plain > empty + 5 and p_learn > empty + 3, report
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open("gpurun_out/stream_report.json", "w") as f:
+    os.makedirs(REPORT_DIR, exist_ok=True)
+    with open(os.path.join(REPORT_DIR, "stream_report.json"), "w") as f:
         json.dump(report, f, indent=1)
 
 
@@ -88,8 +91,8 @@ def test_anchors_in_the_stream():
     p_anchor = psnr(otf.render_anchors(cam), img)
     report = {"merges": merges, "psnr_active": p_active, "psnr_from_anchors": p_anchor, "empty": empty,
               "anchors": [dict(location=a.location.tolist(), n=a.n) for a in otf.anchors]}
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open("gpurun_out/stream_anchor_report.json", "w") as f:
+    os.makedirs(REPORT_DIR, exist_ok=True)
+    with open(os.path.join(REPORT_DIR, "stream_anchor_report.json"), "w") as f:
         json.dump(report, f, indent=1)
     assert p_active > empty + 3 and p_anchor > empty + 3, report
 
@@ -113,8 +116,8 @@ def test_training_schedule_variants():
             otf.add_frame(img, depth, cam, i)
         p = otf.evaluate([(img, cam) for img, _, cam in frames[-3:]])
         report[name] = {"psnr": p, "gaussians": otf.store.n, "culled": sum(e["culled"] for e in otf.log)}
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open("gpurun_out/stream_schedule_report.json", "w") as f:
+    os.makedirs(REPORT_DIR, exist_ok=True)
+    with open(os.path.join(REPORT_DIR, "stream_schedule_report.json"), "w") as f:
         json.dump(report, f, indent=1)
     for name in variants:
         assert report[name]["psnr"] > empty + 5, (name, report)
@@ -211,8 +214,8 @@ def test_guided_matching_refines_the_spawn_depth():
             otf.add_frame(img, d, cts[i], i, feats=feats[i] if name == "guided" else None)
         psnr[name] = otf.evaluate([(img, cts[i]) for i, (img, _) in enumerate(frames)][-3:])
     report.update({f"psnr_{k}": v for k, v in psnr.items()})
-    os.makedirs("gpurun_out", exist_ok=True)
-    with open("gpurun_out/stream_guided_report.json", "w") as f:
+    os.makedirs(REPORT_DIR, exist_ok=True)
+    with open(os.path.join(REPORT_DIR, "stream_guided_report.json"), "w") as f:
         json.dump(report, f, indent=1)
     print(report)
     assert report["guided"] < 0.9 * report["mono"], report
