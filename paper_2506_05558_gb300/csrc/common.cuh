@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "../../include/gs.h"
 
 #define GS_CUDA_CHECK_LAUNCH()                         \
@@ -108,11 +110,13 @@ bool radix_sort_pairs(uint32_t* ka, uint32_t* va, uint32_t* kb, uint32_t* vb, in
 
 // Persistent grid: as many CTAs as fit at once on all SMs. The occupancy query
 // runs once per (device, kernel) so later calls, e.g. inside a stream capture,
-// make no runtime queries.
+// make no runtime queries. The cache is shared by all host threads (locked).
 inline int persistent_grid(const void* fn, int threads) {
     struct Entry { const void* fn; int dev; int grid; };
     static Entry cache[64];
     static int n_cache = 0;
+    static std::mutex lock;
+    std::lock_guard<std::mutex> guard(lock);
     int dev = 0;
     cudaGetDevice(&dev);
     for (int i = 0; i < n_cache; i++)
