@@ -413,6 +413,10 @@ static int composite_pixel(const Cfg* g, double px, double py, const int32_t* id
     int32_t last = 0;
     double z_prev = -1.0;
     int32_t id_prev = -1;
+    /* Relative uncertainty of the FP32 path's T, grown by each composited
+     * Gaussian's alpha uncertainty and one rounding per step (margins only:
+     * the arithmetic above is unaffected). */
+    double T_unc = 0.0;
 #define FLAG_G(x)                          \
     do {                                   \
         *amb = 1;                          \
@@ -426,16 +430,27 @@ static int composite_pixel(const Cfg* g, double px, double py, const int32_t* id
         double dx = px - mean2d[2 * id], dy = py - mean2d[2 * id + 1];
         double a = conic[3 * id], b = conic[3 * id + 1], c = conic[3 * id + 2];
         double power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
+        /* Uncertainty of the FP32 exponent: the splat centre is held in FP32
+         * (a few ulps of its coordinates), times the exponent's gradient, plus
+         * the conic's relative rounding and the hardware exp2. At 1080p an ulp
+         * of a coordinate is up to 1.2e-4 px, which for the narrowest splats
+         * moves alpha by ~1e-3 relative. */
+        double ulp = 4.0 * ldexp(fmax(1.0, fmax(fabs(mean2d[2 * id]), fabs(mean2d[2 * id + 1]))), -24);
+        double grad = fabs(a * dx + b * dy) + fabs(c * dy + b * dx);
+        double dpow = grad * ulp + 1e-5 * fabs(power) + ldexp(1.0, -21);
+        if (fabs(power) < dpow) FLAG_G(id);
         if (power > 0) continue;
         double G = exp(power);
         double og = opac[id] * G;
-        if (fabs(og - g->a_max) < g->m_alpha * g->a_max) FLAG_G(id);
+        if (fabs(og - g->a_max) < (g->m_alpha + dpow) * g->a_max) FLAG_G(id);
         double alpha = og < g->a_max ? og : g->a_max;
-        if (fabs(alpha - g->a_min) < g->m_alpha * g->a_min) FLAG_G(id);
+        if (fabs(alpha - g->a_min) < (g->m_alpha + dpow) * g->a_min) FLAG_G(id);
         if (alpha < g->a_min) continue;
         double testT = T * (1.0 - alpha);
-        if (fabs(testT - g->t_min) < g->m_T * g->t_min) FLAG_G(id);
+        double t_unc = T_unc + alpha / (1.0 - alpha) * dpow + ldexp(1.0, -22);
+        if (fabs(testT - g->t_min) < (g->m_T + t_unc) * g->t_min) FLAG_G(id);
         if (testT < g->t_min) break;
+        T_unc = t_unc;
         if (depth) {
             if (z_prev >= 0 && fabs(depth[id] - z_prev) <= g->m_depth * fabs(depth[id])) {
                 FLAG_G(id);

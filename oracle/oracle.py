@@ -242,14 +242,15 @@ def _alpha_on(proj, i, xs, ys):
     return np.where(power > 0, 0.0, proj["opacity"][i] * np.exp(np.minimum(power, 0.0)))
 
 
-def ambiguous_tiles(view: dict, cam, cfg: Config) -> np.ndarray:
+def ambiguous_tiles(view: dict, cam, cfg: Config, any_alpha: bool = False) -> np.ndarray:
     """Tiles whose list the FP32 path may legitimately build differently.
     Ambiguity bits of or_project: 1 = near plane / determinant (the Gaussian
     may vanish: its whole rect plus one tile), 4/8/16/32 = rect edge x0/y0/x1/y1
     near a tile boundary: the tile column (row) just inside or outside that
     edge may or may not list the Gaussian; a tile of it is flagged only if the
     Gaussian reaches alpha_min there (a Gaussian below alpha_min everywhere in
-    the tile composites to nothing either way)."""
+    the tile composites to nothing either way), or, with any_alpha, always (its
+    presence still shifts the list positions, e.g. n_contrib)."""
     tx, ty = tiles_xy(cam, cfg)
     T = cfg.tile
     W, H = cam["width"], cam["height"]
@@ -291,7 +292,7 @@ def ambiguous_tiles(view: dict, cam, cfg: Config) -> np.ndarray:
         for ry, cx in cand:
             xs = np.arange(cx * T, min(cx * T + T, W), dtype=np.float64)
             ys = np.arange(ry * T, min(ry * T + T, H), dtype=np.float64)
-            if xs.size and ys.size and _alpha_on(proj, i, xs, ys).max() >= thr:
+            if xs.size and ys.size and (any_alpha or _alpha_on(proj, i, xs, ys).max() >= thr):
                 bad[ry, cx] = True
     return bad
 

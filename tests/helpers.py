@@ -49,3 +49,38 @@ def amb_heavy(g2d, amb, rtol, share=0.3):
     amb = np.asarray(amb)
     rms = np.sqrt(np.mean(g2d * g2d, axis=0, keepdims=True)) + 1e-300
     return np.any(amb > share * rtol * (np.abs(g2d) + rms), axis=1)
+
+
+def fp32_adjoint_kappa(n_contrib_max):
+    """Relative FP32 error per contribution of the compositing adjoint: the
+    transmittance in front of a Gaussian is recovered from T_final through up
+    to n_contrib reciprocal-and-multiply steps (about 1.5 ulp each), so a term
+    can be off by about n_contrib x 2^-23 relative (bound taken 2x wider)."""
+    return 3.0 * 2.0 ** -23 * max(1, int(n_contrib_max))
+
+
+def ill_conditioned(g2d, absum, rtol, kappa, share=0.3):
+    """Items whose 2D adjoint is a sum with so much cancellation that its FP32
+    error bound, kappa x the sum of |contributions| (absum, from the oracle),
+    exceeds `share` of the tolerance: the FP32 path cannot be held to the
+    tolerance there, so such items are excluded and counted like flagged ones."""
+    g2d = np.asarray(g2d)
+    rms = np.sqrt(np.mean(g2d * g2d, axis=0, keepdims=True)) + 1e-300
+    return np.any(kappa * np.asarray(absum) > share * rtol * (np.abs(g2d) + rms), axis=1)
+
+
+def assert_close_tail(got, ref, rtol, mask=None, what="", min_frac=0.9999, hard=4.0):
+    """assert_close for full-size sums: at least min_frac of the entries within
+    rtol x (|ref| + rms), every entry within hard x that (FP32 sums over
+    hundreds of composited Gaussians and several views leave a thin tail)."""
+    got = np.asarray(got, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if mask is not None:
+        got = got[mask]
+        ref = ref[mask]
+    if ref.size == 0:
+        return
+    rms = float(np.sqrt(np.mean(ref * ref)))
+    ratio = np.abs(got - ref) / (rtol * (np.abs(ref) + rms) + 1e-300)
+    frac = float(np.mean(ratio <= 1.0))
+    assert frac >= min_frac and ratio.max() <= hard, (what, frac, float(ratio.max()), ref.size)
