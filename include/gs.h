@@ -283,6 +283,8 @@ typedef struct gs_spawn_out {
     float* p_s;
 } gs_spawn_out;
 
+/* Workspace bytes gs_spawn_propose needs for a width x height frame (0 for
+ * a non-positive size); the workspace is caller-owned, 256-byte aligned. */
 size_t gs_spawn_workspace_size(int32_t width, int32_t height);
 
 /* Spawn proposal for a new frame (Sec. 4.2, Eq. 1-3 and the scale from the
