@@ -180,12 +180,6 @@ def uneven_sizes(rng, n_views):
     return [UNEVEN_SIZES[i] for i in idx]
 
 
-def uneven_multiview_scene(seed=1003, n=2_000_000, n_views=16):
-    rng = _rng(seed + 7919)
-    sizes = uneven_sizes(rng, n_views)
-    return multiview_scene(seed, n, n_views, sizes)
-
-
 def image(rng, width, height, lo=0.0, hi=1.0):
     return (lo + (hi - lo) * rng.random((3, height, width))).astype(np.float32)
 
