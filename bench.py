@@ -58,7 +58,7 @@ def log(*a):
 PROFILE_OF_STAGE = {"composite_bwd": "render_bwd_1M_2x1080p.md", "render_fwd": "render_fwd_1M_2x1080p.md"}
 
 
-def profiled_traffic(stage, n_views):
+def profiled_traffic(stage, n_views, root=ROOT):
     """DRAM bytes per launch from the committed ncu summary of the stage's
     kernel (measured on 2 views, scaled by views: traffic grows with the views
     rendered), or None when no summary exists or the kernel source changed
@@ -69,8 +69,8 @@ def profiled_traffic(stage, n_views):
     if not name:
         return None
     try:
-        text = open(os.path.join(ROOT, "profiles", name)).read()
-        src = open(os.path.join(ROOT, "paper_2506_05558_gb300", "csrc", "render.cu"), "rb").read()
+        text = open(os.path.join(root, "profiles", name)).read()
+        src = open(os.path.join(root, "paper_2506_05558_gb300", "csrc", "render.cu"), "rb").read()
     except OSError:
         return None
     m_sha = re.search(r"source_sha256: ([0-9a-f]+)", text)
@@ -116,9 +116,15 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
+        return self.summarise(self.lines)
+
+    @staticmethod
+    def summarise(lines):
+        """Median SM clock, the maximum clock and the throttle reasons seen
+        active, from CSV lines of the query in FIELDS (no header, no units)."""
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
