@@ -148,7 +148,7 @@ void scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* 
 //
 // Each CTA owns 4096 consecutive keys. The histogram pass counts digits with
 // shared-memory atomics into per-warp sub-histograms. The scatter pass ranks
-// keys within each warp (peers by __match_any_sync, running per-warp digit
+// keys within each warp (peers by one ballot per digit bit, running per-warp digit
 // counts in shared memory), turns warp counts into block-local digit offsets,
 // places keys and values in shared memory in sorted order and then writes
 // each digit's run to its global offset with consecutive threads on
@@ -220,7 +220,15 @@ __global__ void __launch_bounds__(kRadixThreads, 3) k_radix_scatter(const uint32
     for (int it = 0; it < kRadixIters; it++) {
         const bool valid = 32 * it < rem;
         const unsigned d = valid ? (kk[it] >> shift) & 255u : 256u;
-        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        // lanes holding the same digit: one ballot per bit of the 9-bit label
+        // (256 marks a missing key), all in registers
+        unsigned peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 9; b++) {
+            const bool bit = (d >> b) & 1u;
+            const unsigned bal = __ballot_sync(0xffffffffu, bit);
+            peers &= bit ? bal : ~bal;
+        }
         const unsigned lower = peers & lanemask_lt();
         const uint32_t before = valid ? cnt[w][d] : 0u;
         __syncwarp();
