@@ -723,7 +723,9 @@ def main():
     stage_ms = {name: float(np.mean([ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps)]))
                 for i, (name, _) in enumerate(J.graphs)}
     status = J.r.status()
-    n_items_vis = int((J.r.proj.n_tiles > 0).sum().item())
+    kept = (J.r.proj.n_tiles[:args.views * args.n] > 0).view(args.views, args.n)
+    n_items_vis = int(kept.sum().item())
+    n_seen = int(kept.any(0).sum().item())  # Gaussians kept in at least one view
     P = J.r.pair_count()
     K = int(J.r.img.n_contrib.to(torch.int64).sum().item())
     loss = float(J.loss.item())
@@ -740,7 +742,10 @@ def main():
     algo = {
         "render_fwd": ("alu", FWD_FLOPS_PER_EVAL * K / 1e12, "TFLOP/s"),
         "composite_bwd": ("alu", BWD_FLOPS_PER_EVAL * K / 1e12, "TFLOP/s"),
-        "project": ("hbm", (16 * args.n * args.views + (224 + 52) * n_items_vis) / 1e9, "GB/s"),
+        # attributes read once per Gaussian (the views of one block share them in L2), 52 B written per
+        # visible item and 12 B (tile count, rect) per culled one
+        "project": ("hbm", (16 * args.n + 224 * n_seen + 52 * n_items_vis
+                            + 12 * (args.n * args.views - n_items_vis)) / 1e9, "GB/s"),
         "project_bwd": ("hbm", ((240 + 240) * args.n + (36 + 12) * n_items_vis + 36 * P) / 1e9, "GB/s"),
         "adam": ("hbm", 7 * 240 * args.n / 1e9, "GB/s"),
     }

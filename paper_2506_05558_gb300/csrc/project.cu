@@ -1,6 +1,9 @@
-// EWA projection + SH colour (K1). One thread per (view, Gaussian); the view is
-// blockIdx.y so every CTA reads one camera. Attributes are read as 128-bit
-// rows; SH coefficients are read only for Gaussians that survive the cull.
+// EWA projection + SH colour (K1). One thread per (view, Gaussian); every CTA
+// reads one camera. The view is the fastest-varying CTA index, so the CTAs of
+// one block of 256 Gaussians in all views run side by side and the attribute
+// rows read from DRAM by the first are L2 hits for the others. Attributes are
+// read as 128-bit rows; SH coefficients are read only for Gaussians that
+// survive the cull.
 #include <atomic>
 #include <cstring>
 
@@ -16,11 +19,12 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean
                                                  float4* __restrict__ conic_opa, float4* __restrict__ rgb_depth,
                                                  ushort4* __restrict__ rect, int32_t* __restrict__ n_tiles) {
     __shared__ gs_camera cam_s;
-    const int v = blockIdx.y;
+    const int v = (int)(blockIdx.x % (unsigned)f.n_views);
+    const int64_t gblock = blockIdx.x / (unsigned)f.n_views;
     if (threadIdx.x < sizeof(gs_camera) / 4)
         reinterpret_cast<float*>(&cam_s)[threadIdx.x] = reinterpret_cast<const float*>(cams + v)[threadIdx.x];
     __syncthreads();
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t g = gblock * blockDim.x + threadIdx.x;
     if (g >= n) return;
     const int64_t item = (int64_t)v * n + g;
     const gs_camera& c = cam_s;
@@ -189,8 +193,8 @@ extern "C" int gs_project(const gs_gaussians* g, const gs_camera* cams, const gs
     if (!aligned16(g->mean_opa) || !aligned16(g->scale) || !aligned16(g->quat) || !aligned16(g->sh) ||
         !aligned16(out->conic_opa) || !aligned16(out->rgb_depth) || !out->mean2d || !out->rect || !out->n_tiles)
         return GS_ERR_INVALID_ARG;
-    dim3 grid((unsigned)ceil_div(g->n, 256), (unsigned)f->n_views);
-    k_project<<<grid, 256, 0, (cudaStream_t)stream>>>(
+    const int64_t blocks = ceil_div(g->n, 256) * f->n_views;  // <= 2^22 * GS_MAX_VIEWS
+    k_project<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
         (const float4*)g->mean_opa, (const float4*)g->scale, (const float4*)g->quat, (const float4*)g->sh, g->n,
         cams, *f, *cfg, (float2*)out->mean2d, (float4*)out->conic_opa, (float4*)out->rgb_depth,
         (ushort4*)out->rect, out->n_tiles);
