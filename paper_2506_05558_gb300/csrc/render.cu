@@ -165,13 +165,9 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                 if (__all_sync(FULL, done)) break;
                 const int kk = k0 + lane;
                 unsigned m = __ballot_sync(FULL, kk < cnt && wb.hits(s_box[kk < cnt ? kk : 0]));
-                while (m) {
-                    const int k = k0 + __ffs(m) - 1;
-                    m &= m - 1;
-                    // predicated: every lane runs the same instructions, the
-                    // pixel's state changes only where the Gaussian composites
-                    const float2 xy = s_xy[k];
-                    const float4 abco = s_abco[k];
+                // predicated: every lane runs the same instructions, the
+                // pixel's state changes only where the Gaussian composites
+                auto composite = [&](int k, const float2 xy, const float4 abco, const float4 c) {
                     const float e = exponent2(abco, px - xy.x, py - xy.y);
                     const float og = __fmul_rn(abco.w, fast_exp2(e));
                     const float alpha = fminf(cfg.alpha_max, og);
@@ -180,12 +176,25 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                     const bool term = ok && nT < cfg.t_min;
                     const bool acc = ok && !term;
                     done = done || term;
-                    const float4 c = s_rgb[k];
                     const float w = acc ? alpha * T : 0.f;
                     cr += w * c.x; cg += w * c.y; cb += w * c.z;
                     if (DEPTH) cz += w * c.w;
                     T = acc ? nT : T;
                     last = acc ? (int)(b0 - start) + k + 1 : last;
+                };
+                // two hits per round (warp-uniform): both Gaussians' shared
+                // loads are issued before the first composites, in order
+                while (m) {
+                    const int ka = k0 + __ffs(m) - 1;
+                    m &= m - 1;
+                    const bool two = m != 0;
+                    const int kb = two ? k0 + __ffs(m) - 1 : ka;
+                    m &= m - 1;
+                    const float2 xya = s_xy[ka], xyb = s_xy[kb];
+                    const float4 aba = s_abco[ka], abb = s_abco[kb];
+                    const float4 ca = s_rgb[ka], cb2 = s_rgb[kb];
+                    composite(ka, xya, aba, ca);
+                    if (two) composite(kb, xyb, abb, cb2);
                 }
             }
         }
