@@ -1,5 +1,5 @@
 """End-to-end streaming check of the learned spawn proposal against plain
-direct sampling (Sec. 4.2 as the fallback and judge): both reconstruct a
+direct sampling (Sec. 4.2, the fallback it is measured against): both reconstruct a
 synthetic scene frame by frame with the same iteration budget; the test
 records the PSNR each reaches and the Gaussians each spawned, and requires both
 to reconstruct (PSNR well above the empty render)."""
