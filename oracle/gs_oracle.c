@@ -184,7 +184,7 @@ typedef struct {
 static void project_one(int64_t i, const double* mean_opa, const double* scale, const double* quat,
                         const double* sh, const Cam* k, const Cfg* g, ProjState* st,
                         double* mean2d, double* conic, double* opac, double* rgb, double* depth,
-                        int32_t* rect, uint8_t* clampm, uint8_t* amb) {
+                        int32_t* rect, uint8_t* clampm, uint8_t* amb, uint8_t* side) {
     memset(st, 0, sizeof *st);
     st->culled = 1;
     double mu[3] = {mean_opa[4 * i], mean_opa[4 * i + 1], mean_opa[4 * i + 2]};
@@ -264,11 +264,20 @@ static void project_one(int64_t i, const double* mean_opa, const double* scale, 
     double e[4] = {(u - r) / T, (v - r) / T, (u + r + T - 1) / T, (v + r + T - 1) / T};
     double lim[4] = {tx, ty, tx, ty};
     /* an edge near a tile boundary inside the grid may round either way in fp32;
-     * bits 4, 8, 16, 32 flag edges x0, y0, x1, y1 */
+     * bits 4, 8, 16, 32 flag edges x0, y0, x1, y1. side (optional) says which
+     * way the other rounding goes: bit c set when the edge lies at or above the
+     * boundary (floor gives the boundary; the other rounding is one less), bit
+     * 4 + c when a radius near an integer may move the edge either way. */
+    uint8_t sd = 0;
     for (int c = 0; c < 4; c++) {
         double kk = nearbyint(e[c]);
-        if (kk >= 1 && kk <= lim[c] && dist_to_int(e[c]) * T < g->m_rect + r_slack) a |= (uint8_t)(4 << c);
+        if (kk >= 1 && kk <= lim[c] && dist_to_int(e[c]) * T < g->m_rect + r_slack) {
+            a |= (uint8_t)(4 << c);
+            if (e[c] >= kk) sd |= (uint8_t)(1 << c);
+            if (r_slack > 0) sd |= (uint8_t)(16 << c);
+        }
     }
+    if (side) side[i] = sd;
     int rc[4];
     for (int c = 0; c < 4; c++) {
         double f = floor(e[c]);
@@ -278,7 +287,10 @@ static void project_one(int64_t i, const double* mean_opa, const double* scale, 
     }
     if (amb) amb[i] = a;
     if (!isfinite(u) || !isfinite(v)) return;
-    if ((rc[2] - rc[0]) * (rc[3] - rc[1]) == 0) return;
+    /* An empty rect lists the item in no tile, so it stays culled; its
+     * projected values and clamped rect are written all the same, because a
+     * rect edge within the margin may make it one tile wide in FP32. */
+    int empty = (rc[2] - rc[0]) * (rc[3] - rc[1]) == 0;
 
     /* colour from SH in the direction camera centre -> mean */
     double cpos[3];
@@ -303,7 +315,7 @@ static void project_one(int64_t i, const double* mean_opa, const double* scale, 
     o *= st->fmip;
     if (!isfinite(st->raw[0]) || !isfinite(st->raw[1]) || !isfinite(st->raw[2]) || !isfinite(o)) return;
 
-    st->culled = 0;
+    st->culled = empty;
     mean2d[2 * i] = u; mean2d[2 * i + 1] = v;
     conic[3 * i] = C / st->det; conic[3 * i + 1] = -Bc / st->det; conic[3 * i + 2] = A / st->det;
     opac[i] = o;
@@ -314,11 +326,13 @@ static void project_one(int64_t i, const double* mean_opa, const double* scale, 
 }
 
 /* Returns the number of visible Gaussians. Outputs are per Gaussian; culled ones
- * get n_tiles = 0 and an all-zero rect. depth_key is the depth rounded to fp32. */
+ * get n_tiles = 0 (an all-zero rect when culled before the rect, else the
+ * empty rect as computed). depth_key is the depth rounded to fp32. side
+ * (optional) as in project_one. */
 int64_t or_project(int64_t n, const double* mean_opa, const double* scale, const double* quat, const double* sh,
                    const double* cam, const double* cfg, double* mean2d, double* conic, double* opac,
                    double* rgb, double* depth, float* depth_key, int32_t* rect, int32_t* n_tiles,
-                   uint8_t* clampm, uint8_t* amb) {
+                   uint8_t* clampm, uint8_t* amb, uint8_t* side) {
     Cam k = read_cam(cam);
     Cfg g = read_cfg(cfg);
     int64_t vis = 0;
@@ -330,7 +344,9 @@ int64_t or_project(int64_t n, const double* mean_opa, const double* scale, const
         opac[i] = 0;
         rgb[3 * i] = rgb[3 * i + 1] = rgb[3 * i + 2] = 0;
         if (clampm) clampm[i] = 0;
-        project_one(i, mean_opa, scale, quat, sh, &k, &g, &st, mean2d, conic, opac, rgb, depth, rect, clampm, amb);
+        if (side) side[i] = 0;
+        project_one(i, mean_opa, scale, quat, sh, &k, &g, &st, mean2d, conic, opac, rgb, depth, rect, clampm, amb,
+                    side);
         depth_key[i] = (float)depth[i];
         n_tiles[i] = (rect[4 * i + 2] - rect[4 * i]) * (rect[4 * i + 3] - rect[4 * i + 1]);
         vis += !st.culled;
@@ -398,21 +414,35 @@ typedef struct {
     double alpha, T, g, og;  /* alpha, transmittance before it, exp(power), o*exp(power) */
     int32_t id;
     int clamped;
+    int64_t j;               /* position in the pixel's list */
+    double dpow;             /* uncertainty of the FP32 exponent (margins only) */
 } Contrib;
+
+/* Decisions of the compositing loop that can be recorded when within their
+ * margin, and forced to the other branch (the tolerance bounds use this). */
+enum { FL_POWER = 1, FL_CLAMP = 2, FL_AMIN = 3, FL_TMIN = 4, FL_DEPTH = 5 };
+typedef struct {
+    int64_t j, j2; /* list position of the decision; FL_DEPTH: also the earlier Gaussian of the near-tie */
+    int kind;
+} Flag;
 
 /* Walks the pixel's list; records composited Gaussians into rec (if non-NULL).
  * Returns the number composited; sets *n_contrib, *T_out, color. A decision
  * within the margins sets *amb and, when amb_g is given, flags the Gaussian(s)
- * it concerns. */
+ * it concerns; when flags is given the decision is also appended there (at
+ * most max_flags, counted in *n_flags). flip (may be NULL) names one decision
+ * (list position and kind, not FL_DEPTH) that is forced to the other branch. */
 static int composite_pixel(const Cfg* g, double px, double py, const int32_t* ids, int64_t len,
                            const double* mean2d, const double* conic, const double* opac, const double* rgb,
                            const double* depth, double* color, double* T_out, int32_t* n_contrib, uint8_t* amb,
-                           Contrib* rec, uint8_t* amb_g) {
+                           Contrib* rec, uint8_t* amb_g, const Flag* flip, Flag* flags, int max_flags,
+                           int* n_flags) {
     double T = 1.0, C[3] = {0, 0, 0};
     int nrec = 0;
     int32_t last = 0;
     double z_prev = -1.0;
     int32_t id_prev = -1;
+    int64_t j_prev = -1;
     /* Relative uncertainty of the FP32 path's T, grown by each composited
      * Gaussian's alpha uncertainty and one rounding per step (margins only:
      * the arithmetic above is unaffected). */
@@ -425,6 +455,15 @@ static int composite_pixel(const Cfg* g, double px, double py, const int32_t* id
             amb_g[x] = 1;                  \
         }                                  \
     } while (0)
+#define RECORD(jj, kk, j2_)                                                   \
+    do {                                                                      \
+        if (flags && *n_flags < max_flags) {                                  \
+            flags[*n_flags].j = (jj); flags[*n_flags].j2 = (j2_);             \
+            flags[*n_flags].kind = (kk); (*n_flags)++;                        \
+        }                                                                     \
+    } while (0)
+#define FORCED(jj, kk) (flip && flip->j == (jj) && flip->kind == (kk))
+    if (n_flags) *n_flags = 0;
     for (int64_t j = 0; j < len; j++) {
         int32_t id = ids[j];
         double dx = px - mean2d[2 * id], dy = py - mean2d[2 * id + 1];
@@ -438,31 +477,35 @@ static int composite_pixel(const Cfg* g, double px, double py, const int32_t* id
         double ulp = 4.0 * ldexp(fmax(1.0, fmax(fabs(mean2d[2 * id]), fabs(mean2d[2 * id + 1]))), -24);
         double grad = fabs(a * dx + b * dy) + fabs(c * dy + b * dx);
         double dpow = grad * ulp + 1e-5 * fabs(power) + ldexp(1.0, -21);
-        if (fabs(power) < dpow) FLAG_G(id);
-        if (power > 0) continue;
+        if (fabs(power) < dpow) { FLAG_G(id); RECORD(j, FL_POWER, -1); }
+        if ((power > 0) != FORCED(j, FL_POWER)) continue;
         double G = exp(power);
         double og = opac[id] * G;
-        if (fabs(og - g->a_max) < (g->m_alpha + dpow) * g->a_max) FLAG_G(id);
-        double alpha = og < g->a_max ? og : g->a_max;
-        if (fabs(alpha - g->a_min) < (g->m_alpha + dpow) * g->a_min) FLAG_G(id);
-        if (alpha < g->a_min) continue;
+        if (fabs(og - g->a_max) < (g->m_alpha + dpow) * g->a_max) { FLAG_G(id); RECORD(j, FL_CLAMP, -1); }
+        int clamped = !(og < g->a_max);
+        if (FORCED(j, FL_CLAMP)) clamped = !clamped;
+        double alpha = clamped ? g->a_max : og;
+        if (fabs(alpha - g->a_min) < (g->m_alpha + dpow) * g->a_min) { FLAG_G(id); RECORD(j, FL_AMIN, -1); }
+        if ((alpha < g->a_min) != FORCED(j, FL_AMIN)) continue;
         double testT = T * (1.0 - alpha);
         double t_unc = T_unc + alpha / (1.0 - alpha) * dpow + ldexp(1.0, -22);
-        if (fabs(testT - g->t_min) < (g->m_T + t_unc) * g->t_min) FLAG_G(id);
-        if (testT < g->t_min) break;
+        if (fabs(testT - g->t_min) < (g->m_T + t_unc) * g->t_min) { FLAG_G(id); RECORD(j, FL_TMIN, -1); }
+        if ((testT < g->t_min) != FORCED(j, FL_TMIN)) break;
         T_unc = t_unc;
         if (depth) {
             if (z_prev >= 0 && fabs(depth[id] - z_prev) <= g->m_depth * fabs(depth[id])) {
                 FLAG_G(id);
                 FLAG_G(id_prev);
+                RECORD(j, FL_DEPTH, j_prev);
             }
             z_prev = depth[id];
             id_prev = id;
+            j_prev = j;
         }
         for (int ch = 0; ch < 3; ch++) C[ch] += alpha * T * rgb[3 * id + ch];
         if (rec) {
             rec[nrec].alpha = alpha; rec[nrec].T = T; rec[nrec].g = G; rec[nrec].og = og;
-            rec[nrec].id = id; rec[nrec].clamped = !(og < g->a_max);
+            rec[nrec].id = id; rec[nrec].clamped = clamped; rec[nrec].j = j; rec[nrec].dpow = dpow;
         }
         nrec++;
         T = testT;
@@ -472,6 +515,8 @@ static int composite_pixel(const Cfg* g, double px, double py, const int32_t* id
     *T_out = T;
     *n_contrib = last;
     return nrec;
+#undef FORCED
+#undef RECORD
 #undef FLAG_G
 }
 
@@ -491,7 +536,7 @@ void or_render_fwd(const double* cam, const double* cfg, const int64_t* tile_sta
         int32_t nc;
         uint8_t a = 0;
         composite_pixel(&g, x + 0.5, y + 0.5, ids + tile_start[t], tile_start[t + 1] - tile_start[t], mean2d,
-                        conic, opac, rgb, depth, col, &Tf, &nc, &a, NULL, amb_g);
+                        conic, opac, rgb, depth, col, &Tf, &nc, &a, NULL, amb_g, NULL, NULL, 0, NULL);
         for (int ch = 0; ch < 3; ch++) color[ch * HW + pix] = col[ch];
         t_final[pix] = Tf;
         n_contrib[pix] = nc;
@@ -499,17 +544,56 @@ void or_render_fwd(const double* cam, const double* cfg, const int64_t* tile_sta
     }
 }
 
-/* Adjoint of the compositing, one view. For each pixel the forward is
- * recomputed front to back with the transmittance before each Gaussian stored;
- * with C = sum_i alpha_i T_i c_i + T_N bg,
+/* Adjoint of one pixel's compositing. rec[0..nr) are the pixel's composited
+ * Gaussians in front-to-back order (from composite_pixel, final transmittance
+ * Tf); with C = sum_i alpha_i T_i c_i + T_N bg,
  *   dC/dc_i     = alpha_i T_i
- *   dC/dalpha_i = T_i c_i - (sum_{j>i} alpha_j T_j c_j + T_N bg) / (1 - alpha_i).
- * Then alpha = min(a_max, o g), g = exp(power),
+ *   dC/dalpha_i = T_i c_i - (sum_{j>i} alpha_j T_j c_j + T_N bg) / (1 - alpha_i),
+ * then alpha = min(a_max, o g), g = exp(power),
  * power = -(a dx^2 + c dy^2)/2 - b dx dy, d = pixel - mean2d.
- * g2d[9*i] = dL/d(u, v, conic a, b, c, opacity, r, g, b) summed over pixels.
- * amb_g2d (optional, same shape): the sum of |contribution| coming from pixels
- * flagged ambiguous (by this pass, or in amb_in [H*W] when given), a bound on
- * how much an FP32 branch flip can move g2d. */
+ * out[9 r + q] = this pixel's share of dL/d(u, v, conic a, b, c, opacity,
+ * r, g, b) of rec[r] for the colour gradient gC; the first six are 0 where
+ * alpha is clamped. */
+static void pixel_contribs(const Cfg* g, double px, double py, const Contrib* rec, int nr, double Tf,
+                           const double* mean2d, const double* conic, const double* rgb, const double* gC,
+                           double* out) {
+    double total[3] = {0, 0, 0};
+    for (int r = 0; r < nr; r++)
+        for (int ch = 0; ch < 3; ch++) total[ch] += rec[r].alpha * rec[r].T * rgb[3 * rec[r].id + ch];
+    double prefix[3] = {0, 0, 0};
+    for (int r = 0; r < nr; r++) {
+        const Contrib* c = &rec[r];
+        int32_t id = c->id;
+        double* o = out + 9 * r;
+        double dalpha = 0;
+        for (int ch = 0; ch < 3; ch++) {
+            double ci = rgb[3 * id + ch];
+            prefix[ch] += c->alpha * c->T * ci;
+            double after = total[ch] - prefix[ch];
+            o[6 + ch] = c->alpha * c->T * gC[ch];
+            dalpha += gC[ch] * (c->T * ci - (after + Tf * g->bg[ch]) / (1.0 - c->alpha));
+        }
+        for (int q = 0; q < 6; q++) o[q] = 0;
+        if (!c->clamped) {
+            double dpower = dalpha * c->og;
+            double dx = px - mean2d[2 * id], dy = py - mean2d[2 * id + 1];
+            double ca = conic[3 * id], cb = conic[3 * id + 1], cc = conic[3 * id + 2];
+            /* dpower/du = a dx + b dy, dpower/dv = b dx + c dy (d = pixel - mean) */
+            o[0] = dpower * (ca * dx + cb * dy);
+            o[1] = dpower * (cb * dx + cc * dy);
+            o[2] = dpower * (-0.5 * dx * dx);
+            o[3] = dpower * (-dx * dy);
+            o[4] = dpower * (-0.5 * dy * dy);
+            o[5] = dalpha * c->g;
+        }
+    }
+}
+
+/* Adjoint of the compositing, one view: the per-pixel adjoint above summed over
+ * the pixels of every tile. g2d[9*i] = dL/d(u, v, conic a, b, c, opacity,
+ * r, g, b) of item i. amb_g2d (optional, same shape): the sum of
+ * |contribution| coming from pixels flagged ambiguous (by this pass, or in
+ * amb_in [H*W] when given). */
 void or_render_bwd(const double* cam, const double* cfg, const int64_t* tile_start, const int32_t* ids,
                    const double* mean2d, const double* conic, const double* opac, const double* rgb,
                    const double* depth, const double* dL_dcolor, int64_t n, double* g2d, double* amb_g2d,
@@ -526,10 +610,15 @@ void or_render_bwd(const double* cam, const double* cfg, const int64_t* tile_sta
     {
         int64_t cap = 0;
         Contrib* rec = NULL;
+        double* cb = NULL;
 #pragma omp for schedule(dynamic, 8)
         for (int64_t t = 0; t < nt; t++) {
             int64_t b0 = tile_start[t], len = tile_start[t + 1] - b0;
-            if (len > cap) { cap = len; rec = (Contrib*)realloc(rec, sizeof(Contrib) * cap); }
+            if (len > cap) {
+                cap = len;
+                rec = (Contrib*)realloc(rec, sizeof(Contrib) * cap);
+                cb = (double*)realloc(cb, sizeof(double) * 9 * cap);
+            }
             int x0 = (int)(t % tx) * T, y0 = (int)(t / tx) * T;
             for (int y = y0; y < y0 + T && y < k.H; y++)
                 for (int x = x0; x < x0 + T && x < k.W; x++) {
@@ -538,48 +627,25 @@ void or_render_bwd(const double* cam, const double* cfg, const int64_t* tile_sta
                     int32_t nc;
                     uint8_t a = 0;
                     int nr = composite_pixel(&g, px, py, ids + b0, len, mean2d, conic, opac, rgb, depth, col, &Tf, &nc,
-                                             &a, rec, NULL);
+                                             &a, rec, NULL, NULL, NULL, 0, NULL);
                     if (amb_in && amb_in[pix]) a = 1;
                     double gC[3] = {dL_dcolor[pix], dL_dcolor[HW + pix], dL_dcolor[2 * HW + pix]};
-                    double total[3] = {0, 0, 0};
-                    for (int r = 0; r < nr; r++)
-                        for (int ch = 0; ch < 3; ch++) total[ch] += rec[r].alpha * rec[r].T * rgb[3 * rec[r].id + ch];
-                    double prefix[3] = {0, 0, 0};
-                    int r = 0;
-                    for (int64_t j = 0; j < len && r < nr; j++) {
-                        if (ids[b0 + j] != rec[r].id) continue;
-                        Contrib* c = &rec[r];
-                        int32_t id = c->id;
-                        double* pp = part + 9 * (b0 + j);
+                    pixel_contribs(&g, px, py, rec, nr, Tf, mean2d, conic, rgb, gC, cb);
+                    for (int r = 0; r < nr; r++) {
+                        double* pp = part + 9 * (b0 + rec[r].j);
+                        const double* o = cb + 9 * r;
                         double before[9];
                         for (int q = 0; q < 9; q++) before[q] = pp[q];
-                        double dalpha = 0;
-                        for (int ch = 0; ch < 3; ch++) {
-                            double ci = rgb[3 * id + ch];
-                            prefix[ch] += c->alpha * c->T * ci;
-                            double after = total[ch] - prefix[ch];
-                            pp[6 + ch] += c->alpha * c->T * gC[ch];
-                            dalpha += gC[ch] * (c->T * ci - (after + Tf * g.bg[ch]) / (1.0 - c->alpha));
-                        }
-                        if (!c->clamped) {
-                            double dpower = dalpha * c->og;
-                            double dx = px - mean2d[2 * id], dy = py - mean2d[2 * id + 1];
-                            double ca = conic[3 * id], cb = conic[3 * id + 1], cc = conic[3 * id + 2];
-                            /* dpower/du = a dx + b dy, dpower/dv = b dx + c dy (d = pixel - mean) */
-                            pp[0] += dpower * (ca * dx + cb * dy);
-                            pp[1] += dpower * (cb * dx + cc * dy);
-                            pp[2] += dpower * (-0.5 * dx * dx);
-                            pp[3] += dpower * (-dx * dy);
-                            pp[4] += dpower * (-0.5 * dy * dy);
-                            pp[5] += dalpha * c->g;
-                        }
+                        for (int q = 6; q < 9; q++) pp[q] += o[q];
+                        if (!rec[r].clamped)
+                            for (int q = 0; q < 6; q++) pp[q] += o[q];
                         if (a)
-                            for (int q = 0; q < 9; q++) part_amb[9 * (b0 + j) + q] += fabs(pp[q] - before[q]);
-                        r++;
+                            for (int q = 0; q < 9; q++) part_amb[9 * (b0 + rec[r].j) + q] += fabs(pp[q] - before[q]);
                     }
                 }
         }
         free(rec);
+        free(cb);
     }
     for (int64_t i = 0; i < 9 * n; i++) g2d[i] = 0;
     if (amb_g2d)
@@ -601,13 +667,156 @@ void or_render_bwd(const double* cam, const double* cfg, const int64_t* tile_sta
  * ------------------------------------------------------------------------- */
 static void sym2_from(double a, double b, double c, double* M) { M[0] = a; M[1] = b; M[2] = b; M[3] = c; }
 
+/* Adjoint of the projection for one visible item (st from project_one): from
+ * its 2D adjoint G[9] to its parameter gradients, overwritten in gm[3],
+ * *glogit, gls[3], gq4[4], gsh[48], and its camera-pose contribution, added to
+ * pose[6]. Linear in G. */
+static void project_bwd_item(const ProjState* pst, const double* G, const double* shrow, const Cam* kp,
+                         const Cfg* gp_, double* gm, double* glogit, double* gls, double* gq4, double* gsh,
+                         double* pose) {
+    const ProjState st = *pst;
+    const Cam k = *kp;
+    const Cfg g = *gp_;
+    int ncoef = (g.sh_degree + 1) * (g.sh_degree + 1);
+    for (int c = 0; c < 3; c++) gm[c] = 0, gls[c] = 0;
+    for (int c = 0; c < 4; c++) gq4[c] = 0;
+    for (int c = 0; c < 48; c++) gsh[c] = 0;
+    *glogit = 0;
+    double x = st.p[0], y = st.p[1], z = st.p[2];
+
+    /* opacity o f, o = sigmoid(logit), f = sqrt(rho) with the filter (else 1) */
+    *glogit = G[5] * st.fmip * st.o * (1 - st.o);
+    double g_rho = (g.mip && !st.rho_floor) ? G[5] * st.o / (2.0 * st.fmip) : 0.0;
+
+    /* colour: rgb = max(SH(d) + 0.5, 0) */
+    double graw[3];
+    for (int ch = 0; ch < 3; ch++) graw[ch] = st.raw[ch] > 0 ? G[6 + ch] : 0;
+    double gd[3] = {0, 0, 0};
+    for (int kk = 0; kk < ncoef; kk++)
+        for (int ch = 0; ch < 3; ch++) {
+            double shv = shrow[3 * kk + ch];
+            gsh[3 * kk + ch] = graw[ch] * st.Y[kk];
+            for (int c = 0; c < 3; c++) gd[c] += graw[ch] * shv * st.dY[3 * kk + c];
+        }
+    /* d = dir/|dir|: dL/ddir = (gd - d (d.gd)) / |dir| */
+    double dd = gd[0] * st.d[0] + gd[1] * st.d[1] + gd[2] * st.d[2];
+    double gdir[3];
+    for (int c = 0; c < 3; c++) gdir[c] = (gd[c] - st.d[c] * dd) / st.dlen;
+    for (int c = 0; c < 3; c++) gm[c] += gdir[c];
+    if (g.pose_through_sh) {
+        /* dir = mu - centre, centre = -R^T t; left perturbation moves the centre by -R^T rho */
+        for (int r = 0; r < 3; r++)
+            pose[r] += k.R[3 * r] * gdir[0] + k.R[3 * r + 1] * gdir[1] + k.R[3 * r + 2] * gdir[2];
+    }
+
+    /* conic = S2^-1: dL/dS2 = -Q dL/dQ Q with the full symmetric dL/dQ */
+    double Q[4], GQ[4], GS[4], t4[4];
+    sym2_from(st.S2[3] / st.det, -st.S2[1] / st.det, st.S2[0] / st.det, Q);
+    sym2_from(G[2], 0.5 * G[3], G[4], GQ);
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 2; c++) t4[2 * r + c] = Q[2 * r] * GQ[c] + Q[2 * r + 1] * GQ[2 + c];
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 2; c++) GS[2 * r + c] = -(t4[2 * r] * Q[c] + t4[2 * r + 1] * Q[2 + c]);
+    if (g_rho != 0.0) {
+        /* rho = ((A - dil)(C - dil) - B^2) / (A C - B^2) with S2 = [[A, B], [B, C]] */
+        double A = st.S2[0], B = st.S2[1], C = st.S2[3], rho = st.rho;
+        GS[0] += g_rho * ((C - g.dil) - rho * C) / st.det;
+        GS[3] += g_rho * ((A - g.dil) - rho * A) / st.det;
+        GS[1] += -g_rho * B * (1.0 - rho) / st.det; /* half of d rho / dB on each symmetric entry */
+        GS[2] += -g_rho * B * (1.0 - rho) / st.det;
+    }
+
+    /* S2 = J Sc J^T + dil I: dL/dSc = J^T GS J, dL/dJ = 2 GS J Sc */
+    const double* J = st.J;
+    double GSc[9], GJ[6], JSc[6];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) {
+            double s = 0;
+            for (int a = 0; a < 2; a++)
+                for (int b = 0; b < 2; b++) s += J[3 * a + r] * GS[2 * a + b] * J[3 * b + c];
+            GSc[3 * r + c] = s;
+        }
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 3; c++)
+            JSc[3 * r + c] = J[3 * r] * st.Sc[c] + J[3 * r + 1] * st.Sc[3 + c] + J[3 * r + 2] * st.Sc[6 + c];
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 3; c++) GJ[3 * r + c] = 2 * (GS[2 * r] * JSc[c] + GS[2 * r + 1] * JSc[3 + c]);
+
+    /* mean2d and J as functions of p = (x, y, z) */
+    double gp[3] = {0, 0, 0};
+    gp[0] += G[0] * k.fx / z;
+    gp[2] += -G[0] * k.fx * x / (z * z);
+    gp[1] += G[1] * k.fy / z;
+    gp[2] += -G[1] * k.fy * y / (z * z);
+    gp[2] += GJ[0] * (-k.fx / (z * z)) + GJ[4] * (-k.fy / (z * z));
+    if (st.clamp_x) {
+        double c = x / z < 0 ? -1.3 * (k.W * 0.5) / k.fx : 1.3 * (k.W * 0.5) / k.fx;
+        gp[2] += GJ[2] * (k.fx * c / (z * z));
+    } else {
+        gp[0] += GJ[2] * (-k.fx / (z * z));
+        gp[2] += GJ[2] * (2 * k.fx * x / (z * z * z));
+    }
+    if (st.clamp_y) {
+        double c = y / z < 0 ? -1.3 * (k.H * 0.5) / k.fy : 1.3 * (k.H * 0.5) / k.fy;
+        gp[2] += GJ[5] * (k.fy * c / (z * z));
+    } else {
+        gp[1] += GJ[5] * (-k.fy / (z * z));
+        gp[2] += GJ[5] * (2 * k.fy * y / (z * z * z));
+    }
+
+    /* Sc = R Sig R^T: dL/dSig = R^T GSc R */
+    double RT[9], t9[9], GSig[9];
+    mat3_T(k.R, RT);
+    mat3_mul(RT, GSc, t9);
+    mat3_mul(t9, k.R, GSig);
+    /* Sig = M M^T, M = Rq diag(s): dL/dM = 2 GSig M */
+    double M[9], GM[9];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) M[3 * r + c] = st.Rq[3 * r + c] * st.s[c];
+    mat3_mul(GSig, M, GM);
+    for (int c = 0; c < 9; c++) GM[c] *= 2;
+    double GRq[9];
+    for (int c = 0; c < 3; c++) {
+        double gs = 0;
+        for (int r = 0; r < 3; r++) {
+            gs += GM[3 * r + c] * st.Rq[3 * r + c];
+            GRq[3 * r + c] = GM[3 * r + c] * st.s[c];
+        }
+        gls[c] = gs * st.s[c];
+    }
+    /* rotation matrix of the normalised quaternion */
+    double w = st.qn[0], qx = st.qn[1], qy = st.qn[2], qz = st.qn[3];
+    double gq[4];
+    gq[0] = 2 * (-qz * GRq[1] + qy * GRq[2] + qz * GRq[3] - qx * GRq[5] - qy * GRq[6] + qx * GRq[7]);
+    gq[1] = 2 * (qy * GRq[1] + qz * GRq[2] + qy * GRq[3] - 2 * qx * GRq[4] - w * GRq[5] + qz * GRq[6] + w * GRq[7] - 2 * qx * GRq[8]);
+    gq[2] = 2 * (-2 * qy * GRq[0] + qx * GRq[1] + w * GRq[2] + qx * GRq[3] + qz * GRq[5] - w * GRq[6] + qz * GRq[7] - 2 * qy * GRq[8]);
+    gq[3] = 2 * (-2 * qz * GRq[0] - w * GRq[1] + qx * GRq[2] + w * GRq[3] - 2 * qz * GRq[4] + qy * GRq[5] + qx * GRq[6] + qy * GRq[7]);
+    double qd = gq[0] * st.qn[0] + gq[1] * st.qn[1] + gq[2] * st.qn[2] + gq[3] * st.qn[3];
+    for (int c = 0; c < 4; c++) gq4[c] = (gq[c] - st.qn[c] * qd) / st.qlen;
+
+    /* p = R mu + t */
+    for (int c = 0; c < 3; c++) gm[c] += RT[3 * c] * gp[0] + RT[3 * c + 1] * gp[1] + RT[3 * c + 2] * gp[2];
+
+    /* pose, left perturbation: dp = rho + phi x p, dSc = phi^ Sc - Sc phi^ */
+    pose[0] += gp[0]; pose[1] += gp[1]; pose[2] += gp[2];
+    pose[3] += st.p[1] * gp[2] - st.p[2] * gp[1];
+    pose[4] += st.p[2] * gp[0] - st.p[0] * gp[2];
+    pose[5] += st.p[0] * gp[1] - st.p[1] * gp[0];
+    double A1[9], A2[9], Mx[9];
+    mat3_mul(st.Sc, GSc, A1);
+    mat3_mul(GSc, st.Sc, A2);
+    for (int c = 0; c < 9; c++) Mx[c] = A1[c] - A2[c];
+    pose[3] += Mx[5] - Mx[7];
+    pose[4] += Mx[6] - Mx[2];
+    pose[5] += Mx[1] - Mx[3];
+}
+
 void or_project_bwd(int64_t n, const double* mean_opa, const double* scale, const double* quat, const double* sh,
                     const double* cam, const double* cfg, const double* g2d, double* g_mean, double* g_logit,
                     double* g_logscale, double* g_quat, double* g_sh, double* g_pose) {
     Cam k = read_cam(cam);
     Cfg g = read_cfg(cfg);
     double pose[6] = {0, 0, 0, 0, 0, 0};
-    int ncoef = (g.sh_degree + 1) * (g.sh_degree + 1);
     for (int64_t i = 0; i < n; i++) {
         ProjState st;
         double m2[2], cn[3], op, col[3], dep;
@@ -618,138 +827,418 @@ void or_project_bwd(int64_t n, const double* mean_opa, const double* scale, cons
         g_logit[i] = 0;
         /* project_one indexes its outputs by i; point it at local storage */
         project_one(0, mean_opa + 4 * i, scale + 4 * i, quat + 4 * i, sh + 48 * i, &k, &g, &st, m2, cn, &op, col,
-                    &dep, rc, NULL, NULL);
+                    &dep, rc, NULL, NULL, NULL);
         if (st.culled) continue;
-        const double* G = g2d + 9 * i;
-        double x = st.p[0], y = st.p[1], z = st.p[2];
-
-        /* opacity o f, o = sigmoid(logit), f = sqrt(rho) with the filter (else 1) */
-        g_logit[i] = G[5] * st.fmip * st.o * (1 - st.o);
-        double g_rho = (g.mip && !st.rho_floor) ? G[5] * st.o / (2.0 * st.fmip) : 0.0;
-
-        /* colour: rgb = max(SH(d) + 0.5, 0) */
-        double graw[3];
-        for (int ch = 0; ch < 3; ch++) graw[ch] = st.raw[ch] > 0 ? G[6 + ch] : 0;
-        double gd[3] = {0, 0, 0};
-        for (int kk = 0; kk < ncoef; kk++)
-            for (int ch = 0; ch < 3; ch++) {
-                double shv = sh[48 * i + 3 * kk + ch];
-                g_sh[48 * i + 3 * kk + ch] = graw[ch] * st.Y[kk];
-                for (int c = 0; c < 3; c++) gd[c] += graw[ch] * shv * st.dY[3 * kk + c];
-            }
-        /* d = dir/|dir|: dL/ddir = (gd - d (d.gd)) / |dir| */
-        double dd = gd[0] * st.d[0] + gd[1] * st.d[1] + gd[2] * st.d[2];
-        double gdir[3];
-        for (int c = 0; c < 3; c++) gdir[c] = (gd[c] - st.d[c] * dd) / st.dlen;
-        for (int c = 0; c < 3; c++) g_mean[3 * i + c] += gdir[c];
-        if (g.pose_through_sh) {
-            /* dir = mu - centre, centre = -R^T t; left perturbation moves the centre by -R^T rho */
-            for (int r = 0; r < 3; r++)
-                pose[r] += k.R[3 * r] * gdir[0] + k.R[3 * r + 1] * gdir[1] + k.R[3 * r + 2] * gdir[2];
-        }
-
-        /* conic = S2^-1: dL/dS2 = -Q dL/dQ Q with the full symmetric dL/dQ */
-        double Q[4], GQ[4], GS[4], t4[4];
-        sym2_from(st.S2[3] / st.det, -st.S2[1] / st.det, st.S2[0] / st.det, Q);
-        sym2_from(G[2], 0.5 * G[3], G[4], GQ);
-        for (int r = 0; r < 2; r++)
-            for (int c = 0; c < 2; c++) t4[2 * r + c] = Q[2 * r] * GQ[c] + Q[2 * r + 1] * GQ[2 + c];
-        for (int r = 0; r < 2; r++)
-            for (int c = 0; c < 2; c++) GS[2 * r + c] = -(t4[2 * r] * Q[c] + t4[2 * r + 1] * Q[2 + c]);
-        if (g_rho != 0.0) {
-            /* rho = ((A - dil)(C - dil) - B^2) / (A C - B^2) with S2 = [[A, B], [B, C]] */
-            double A = st.S2[0], B = st.S2[1], C = st.S2[3], rho = st.rho;
-            GS[0] += g_rho * ((C - g.dil) - rho * C) / st.det;
-            GS[3] += g_rho * ((A - g.dil) - rho * A) / st.det;
-            GS[1] += -g_rho * B * (1.0 - rho) / st.det; /* half of d rho / dB on each symmetric entry */
-            GS[2] += -g_rho * B * (1.0 - rho) / st.det;
-        }
-
-        /* S2 = J Sc J^T + dil I: dL/dSc = J^T GS J, dL/dJ = 2 GS J Sc */
-        const double* J = st.J;
-        double GSc[9], GJ[6], JSc[6];
-        for (int r = 0; r < 3; r++)
-            for (int c = 0; c < 3; c++) {
-                double s = 0;
-                for (int a = 0; a < 2; a++)
-                    for (int b = 0; b < 2; b++) s += J[3 * a + r] * GS[2 * a + b] * J[3 * b + c];
-                GSc[3 * r + c] = s;
-            }
-        for (int r = 0; r < 2; r++)
-            for (int c = 0; c < 3; c++)
-                JSc[3 * r + c] = J[3 * r] * st.Sc[c] + J[3 * r + 1] * st.Sc[3 + c] + J[3 * r + 2] * st.Sc[6 + c];
-        for (int r = 0; r < 2; r++)
-            for (int c = 0; c < 3; c++) GJ[3 * r + c] = 2 * (GS[2 * r] * JSc[c] + GS[2 * r + 1] * JSc[3 + c]);
-
-        /* mean2d and J as functions of p = (x, y, z) */
-        double gp[3] = {0, 0, 0};
-        gp[0] += G[0] * k.fx / z;
-        gp[2] += -G[0] * k.fx * x / (z * z);
-        gp[1] += G[1] * k.fy / z;
-        gp[2] += -G[1] * k.fy * y / (z * z);
-        gp[2] += GJ[0] * (-k.fx / (z * z)) + GJ[4] * (-k.fy / (z * z));
-        if (st.clamp_x) {
-            double c = x / z < 0 ? -1.3 * (k.W * 0.5) / k.fx : 1.3 * (k.W * 0.5) / k.fx;
-            gp[2] += GJ[2] * (k.fx * c / (z * z));
-        } else {
-            gp[0] += GJ[2] * (-k.fx / (z * z));
-            gp[2] += GJ[2] * (2 * k.fx * x / (z * z * z));
-        }
-        if (st.clamp_y) {
-            double c = y / z < 0 ? -1.3 * (k.H * 0.5) / k.fy : 1.3 * (k.H * 0.5) / k.fy;
-            gp[2] += GJ[5] * (k.fy * c / (z * z));
-        } else {
-            gp[1] += GJ[5] * (-k.fy / (z * z));
-            gp[2] += GJ[5] * (2 * k.fy * y / (z * z * z));
-        }
-
-        /* Sc = R Sig R^T: dL/dSig = R^T GSc R */
-        double RT[9], t9[9], GSig[9];
-        mat3_T(k.R, RT);
-        mat3_mul(RT, GSc, t9);
-        mat3_mul(t9, k.R, GSig);
-        /* Sig = M M^T, M = Rq diag(s): dL/dM = 2 GSig M */
-        double M[9], GM[9];
-        for (int r = 0; r < 3; r++)
-            for (int c = 0; c < 3; c++) M[3 * r + c] = st.Rq[3 * r + c] * st.s[c];
-        mat3_mul(GSig, M, GM);
-        for (int c = 0; c < 9; c++) GM[c] *= 2;
-        double GRq[9];
-        for (int c = 0; c < 3; c++) {
-            double gs = 0;
-            for (int r = 0; r < 3; r++) {
-                gs += GM[3 * r + c] * st.Rq[3 * r + c];
-                GRq[3 * r + c] = GM[3 * r + c] * st.s[c];
-            }
-            g_logscale[3 * i + c] = gs * st.s[c];
-        }
-        /* rotation matrix of the normalised quaternion */
-        double w = st.qn[0], qx = st.qn[1], qy = st.qn[2], qz = st.qn[3];
-        double gq[4];
-        gq[0] = 2 * (-qz * GRq[1] + qy * GRq[2] + qz * GRq[3] - qx * GRq[5] - qy * GRq[6] + qx * GRq[7]);
-        gq[1] = 2 * (qy * GRq[1] + qz * GRq[2] + qy * GRq[3] - 2 * qx * GRq[4] - w * GRq[5] + qz * GRq[6] + w * GRq[7] - 2 * qx * GRq[8]);
-        gq[2] = 2 * (-2 * qy * GRq[0] + qx * GRq[1] + w * GRq[2] + qx * GRq[3] + qz * GRq[5] - w * GRq[6] + qz * GRq[7] - 2 * qy * GRq[8]);
-        gq[3] = 2 * (-2 * qz * GRq[0] - w * GRq[1] + qx * GRq[2] + w * GRq[3] - 2 * qz * GRq[4] + qy * GRq[5] + qx * GRq[6] + qy * GRq[7]);
-        double qd = gq[0] * st.qn[0] + gq[1] * st.qn[1] + gq[2] * st.qn[2] + gq[3] * st.qn[3];
-        for (int c = 0; c < 4; c++) g_quat[4 * i + c] = (gq[c] - st.qn[c] * qd) / st.qlen;
-
-        /* p = R mu + t */
-        for (int c = 0; c < 3; c++) g_mean[3 * i + c] += RT[3 * c] * gp[0] + RT[3 * c + 1] * gp[1] + RT[3 * c + 2] * gp[2];
-
-        /* pose, left perturbation: dp = rho + phi x p, dSc = phi^ Sc - Sc phi^ */
-        pose[0] += gp[0]; pose[1] += gp[1]; pose[2] += gp[2];
-        pose[3] += st.p[1] * gp[2] - st.p[2] * gp[1];
-        pose[4] += st.p[2] * gp[0] - st.p[0] * gp[2];
-        pose[5] += st.p[0] * gp[1] - st.p[1] * gp[0];
-        double A1[9], A2[9], Mx[9];
-        mat3_mul(st.Sc, GSc, A1);
-        mat3_mul(GSc, st.Sc, A2);
-        for (int c = 0; c < 9; c++) Mx[c] = A1[c] - A2[c];
-        pose[3] += Mx[5] - Mx[7];
-        pose[4] += Mx[6] - Mx[2];
-        pose[5] += Mx[1] - Mx[3];
+        project_bwd_item(&st, g2d + 9 * i, sh + 48 * i, &k, &g, g_mean + 3 * i, g_logit + i, g_logscale + 3 * i,
+                         g_quat + 4 * i, g_sh + 48 * i, pose);
     }
     for (int c = 0; c < 6; c++) g_pose[c] = pose[c];
+}
+
+/* Bounds carried through the projection adjoint. b2d[9 i + c] >= 0 bounds how
+ * far the 2D adjoint component c of item i may be from the value the oracle
+ * computes. The adjoint is linear in the 2D adjoint, so the most a parameter
+ * gradient can move is sum_c |d param / d g2d_c| b2d_c, and the most the
+ * view's pose gradient can move is the sum of that over the items; each
+ * Jacobian column is the item adjoint of a unit vector. Outputs (overwritten)
+ * have the shapes of or_project_bwd's. With g2d given (may be NULL),
+ * pose_absum[6] receives sum_i |pose contribution of item i| under that
+ * adjoint: the scale of the rounding error of summing the items in any order. */
+void or_project_bwd_abs(int64_t n, const double* mean_opa, const double* scale, const double* quat,
+                        const double* sh, const double* cam, const double* cfg, const double* b2d,
+                        const double* g2d, double* b_mean, double* b_logit, double* b_logscale, double* b_quat,
+                        double* b_sh, double* b_pose, double* pose_absum) {
+    Cam k = read_cam(cam);
+    Cfg g = read_cfg(cfg);
+    double* item_pose = (double*)calloc((size_t)(n > 0 ? n : 1) * 12, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int64_t i = 0; i < n; i++) {
+        ProjState st;
+        double m2[2], cn[3], op, col[3], dep;
+        int32_t rc[4];
+        double gm[3], gl, gls[3], gq[4], gsh[48];
+        for (int c = 0; c < 3; c++) b_mean[3 * i + c] = 0, b_logscale[3 * i + c] = 0;
+        for (int c = 0; c < 4; c++) b_quat[4 * i + c] = 0;
+        for (int c = 0; c < 48; c++) b_sh[48 * i + c] = 0;
+        b_logit[i] = 0;
+        project_one(0, mean_opa + 4 * i, scale + 4 * i, quat + 4 * i, sh + 48 * i, &k, &g, &st, m2, cn, &op, col,
+                    &dep, rc, NULL, NULL, NULL);
+        if (st.culled) continue;
+        for (int q = 0; q < 9; q++) {
+            double bq = b2d[9 * i + q];
+            if (!(bq > 0)) continue;
+            double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            double pz[6] = {0, 0, 0, 0, 0, 0};
+            e[q] = bq;
+            project_bwd_item(&st, e, sh + 48 * i, &k, &g, gm, &gl, gls, gq, gsh, pz);
+            for (int c = 0; c < 3; c++) b_mean[3 * i + c] += fabs(gm[c]), b_logscale[3 * i + c] += fabs(gls[c]);
+            for (int c = 0; c < 4; c++) b_quat[4 * i + c] += fabs(gq[c]);
+            for (int c = 0; c < 48; c++) b_sh[48 * i + c] += fabs(gsh[c]);
+            b_logit[i] += fabs(gl);
+            for (int c = 0; c < 6; c++) item_pose[12 * i + c] += fabs(pz[c]);
+        }
+        if (g2d) {
+            double pz[6] = {0, 0, 0, 0, 0, 0};
+            project_bwd_item(&st, g2d + 9 * i, sh + 48 * i, &k, &g, gm, &gl, gls, gq, gsh, pz);
+            for (int c = 0; c < 6; c++) item_pose[12 * i + 6 + c] = fabs(pz[c]);
+        }
+    }
+    for (int c = 0; c < 6; c++) b_pose[c] = 0, pose_absum[c] = 0;
+    for (int64_t i = 0; i < n; i++)
+        for (int c = 0; c < 6; c++) b_pose[c] += item_pose[12 * i + c], pose_absum[c] += item_pose[12 * i + 6 + c];
+    free(item_pose);
+}
+
+/* Per-item Jacobian of the view's pose gradient with respect to the item's 2D
+ * adjoint: jac[54 i + 9 c + q] = d pose_c / d g2d_q (zeros for culled items).
+ * The projection adjoint is linear in g2d, so column q is the item adjoint of
+ * the unit vector e_q. */
+void or_pose_jacobian(int64_t n, const double* mean_opa, const double* scale, const double* quat,
+                      const double* sh, const double* cam, const double* cfg, double* jac) {
+    Cam k = read_cam(cam);
+    Cfg g = read_cfg(cfg);
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int64_t i = 0; i < n; i++) {
+        ProjState st;
+        double m2[2], cn[3], op, col[3], dep;
+        int32_t rc[4];
+        double gm[3], gl, gls[3], gq[4], gsh[48];
+        for (int c = 0; c < 54; c++) jac[54 * i + c] = 0;
+        project_one(0, mean_opa + 4 * i, scale + 4 * i, quat + 4 * i, sh + 48 * i, &k, &g, &st, m2, cn, &op, col,
+                    &dep, rc, NULL, NULL, NULL);
+        if (st.culled) continue;
+        for (int q = 0; q < 9; q++) {
+            double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+            double pz[6] = {0, 0, 0, 0, 0, 0};
+            e[q] = 1.0;
+            project_bwd_item(&st, e, sh + 48 * i, &k, &g, gm, &gl, gls, gq, gsh, pz);
+            for (int c = 0; c < 6; c++) jac[54 * i + 9 * c + q] = pz[c];
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Tolerance bounds for an FP32 implementation of the compositing adjoint.
+ *
+ * Two effects move an FP32 result away from or_render_bwd's FP64 value by
+ * more than a relative tolerance can express, and both are computed here from
+ * the oracle's own state (nothing from the implementation under test):
+ *
+ * (1) Decisions within their margin (alpha_min, the 0.99 clamp, the exponent
+ *     sign, termination, depth near-ties, and tile-list membership where a
+ *     rect edge lies within the margin of a tile boundary) may go either way.
+ *     Each pixel's decision is forced to its other branch on its own (depth
+ *     near-ties: the two Gaussians swapped), the pixel's adjoint is
+ *     recomputed, and |change| is accumulated per item and component
+ *     (b_flip). A list membership concerns a whole tile, so its change is
+ *     summed over the tile's pixels before the absolute value. With the
+ *     per-item pose Jacobian (or_pose_jacobian), pose_flip[6] accumulates
+ *     |sum over items of J (change)| per flip: the most the view's pose
+ *     gradient can move when any subset of the flagged decisions flips.
+ * (2) FP32 rounding of a back-to-front adjoint: the transmittance in front of
+ *     a Gaussian is recovered from the stored final transmittance through the
+ *     Gaussians behind it, so its relative error grows with each of them by
+ *     alpha/(1-alpha) times the alpha uncertainty plus two roundings, on top
+ *     of the forward's own accumulated error. The first-order error bound e of
+ *     each contribution follows from that, from the exponent's uncertainty and
+ *     from the splat centre's last bits. Summed as |e| these bounds grow with
+ *     the number of pixels while the errors themselves, of varying sign,
+ *     largely cancel; b_fp32 is therefore the root of the sum of e^2 per item
+ *     and component (the scale of a sum of independent errors, as in
+ *     probabilistic rounding-error analysis), and pose_fp32 the same for the
+ *     pose through |J|. Callers multiply it by the confidence factor they
+ *     choose.
+ * amb_in [H*W] (may be NULL) marks pixels whose decisions are not modelled:
+ * there |contribution| itself counts in b_flip.
+ * memb [n_memb][3] = (tile, item, group) triples whose membership is
+ * uncertain, sorted by tile; items absent from the tile's list are inserted in
+ * (depth key, id) order. The memberships of one group change together (the
+ * tiles of one rect edge, or of a Gaussian that may vanish or appear), so
+ * their pose changes are summed with sign before the absolute value. Outputs
+ * are overwritten.
+ * ------------------------------------------------------------------------- */
+#define MAX_FLAGS 64
+typedef struct {
+    int64_t cap;
+    Contrib* rec;
+    Contrib* recf;
+    double *cb, *c0, *cf, *acc;
+    int32_t* lst;
+} BScratch;
+
+static void bs_reserve(BScratch* s, int64_t len) {
+    if (len + 2 <= s->cap) return;
+    s->cap = len + 2;
+    s->rec = (Contrib*)realloc(s->rec, sizeof(Contrib) * s->cap);
+    s->recf = (Contrib*)realloc(s->recf, sizeof(Contrib) * s->cap);
+    s->cb = (double*)realloc(s->cb, sizeof(double) * 9 * s->cap);
+    s->c0 = (double*)realloc(s->c0, sizeof(double) * 9 * s->cap);
+    s->cf = (double*)realloc(s->cf, sizeof(double) * 9 * s->cap);
+    s->acc = (double*)realloc(s->acc, sizeof(double) * 9 * s->cap);
+    s->lst = (int32_t*)realloc(s->lst, sizeof(int32_t) * s->cap);
+}
+
+/* contributions of the pixel under list lst (length len) and optional flip,
+ * scattered by position into out[9 * (len + 1)] after map (position in lst ->
+ * position in the caller's numbering; NULL = identity). Returns the last
+ * position touched + 1 in the caller's numbering. */
+static int64_t pixel_by_position(const Cfg* g, double px, double py, const int32_t* lst, int64_t len,
+                                 const double* mean2d, const double* conic, const double* opac, const double* rgb,
+                                 const double* depth, const double* gC, const Flag* flip, const int64_t* map,
+                                 int64_t out_len, Contrib* rec, double* cb, double* out) {
+    double col[3], Tf;
+    int32_t nc;
+    uint8_t a = 0;
+    int nr = composite_pixel(g, px, py, lst, len, mean2d, conic, opac, rgb, depth, col, &Tf, &nc, &a, rec, NULL,
+                             flip, NULL, 0, NULL);
+    pixel_contribs(g, px, py, rec, nr, Tf, mean2d, conic, rgb, gC, cb);
+    for (int64_t q = 0; q < 9 * out_len; q++) out[q] = 0;
+    int64_t hi = 0;
+    for (int r = 0; r < nr; r++) {
+        int64_t j = map ? map[rec[r].j] : rec[r].j;
+        for (int q = 0; q < 9; q++) out[9 * j + q] = cb[9 * r + q];
+        if (j + 1 > hi) hi = j + 1;
+    }
+    return hi;
+}
+
+static void pose_of(const double* jac, int32_t id, const double* v, double* d) {
+    for (int c = 0; c < 6; c++) {
+        double s = 0;
+        for (int q = 0; q < 9; q++) s += jac[54 * (int64_t)id + 9 * c + q] * v[q];
+        d[c] += s;
+    }
+}
+
+void or_render_bwd_bounds(const double* cam, const double* cfg, const int64_t* tile_start, const int32_t* ids,
+                          const double* mean2d, const double* conic, const double* opac, const double* rgb,
+                          const double* depth, const float* depth_key, const double* dL_dcolor, int64_t n,
+                          const int64_t* memb, int64_t n_memb, const uint8_t* amb_in, const double* jac,
+                          double* b_flip, double* b_fp32, double* pose_flip, double* pose_fp32) {
+    Cam k = read_cam(cam);
+    Cfg g = read_cfg(cfg);
+    int T = g.tile, tx = (k.W + T - 1) / T, ty = (k.H + T - 1) / T;
+    int64_t HW = (int64_t)k.W * k.H, nt = (int64_t)tx * ty;
+    int64_t P = tile_start[nt];
+    const double u = ldexp(1.0, -24);
+    double* pf = (double*)calloc((size_t)(P > 0 ? P : 1) * 9, sizeof(double));
+    double* p32 = (double*)calloc((size_t)(P > 0 ? P : 1) * 9, sizeof(double));
+    double* pm = (double*)calloc((size_t)(n_memb > 0 ? n_memb : 1) * 9, sizeof(double));
+    double* tpose = (double*)calloc((size_t)(nt > 0 ? nt : 1) * 12, sizeof(double));
+    int64_t* mstart = (int64_t*)calloc((size_t)nt + 1, sizeof(int64_t));
+    double* mpose = (double*)calloc((size_t)(n_memb > 0 ? n_memb : 1) * 6, sizeof(double));
+    int64_t n_group = 0;
+    for (int64_t m = 0; m < n_memb; m++) {
+        mstart[memb[3 * m] + 1]++;
+        if (memb[3 * m + 2] + 1 > n_group) n_group = memb[3 * m + 2] + 1;
+    }
+    for (int64_t t = 0; t < nt; t++) mstart[t + 1] += mstart[t];
+#pragma omp parallel
+    {
+        BScratch s = {0, NULL, NULL, NULL, NULL, NULL, NULL, NULL};
+        int64_t* map = NULL;
+        int64_t map_cap = 0;
+        Flag flags[MAX_FLAGS];
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t t = 0; t < nt; t++) {
+            int64_t b0 = tile_start[t], len = tile_start[t + 1] - b0;
+            const int32_t* L = ids + b0;
+            bs_reserve(&s, len);
+            if (len + 2 > map_cap) { map_cap = len + 2; map = (int64_t*)realloc(map, sizeof(int64_t) * map_cap); }
+            double* tp = tpose + 12 * t;
+            int x0 = (int)(t % tx) * T, y0 = (int)(t / tx) * T;
+            /* per-pixel decisions and FP32 rounding */
+            for (int y = y0; y < y0 + T && y < k.H; y++)
+                for (int x = x0; x < x0 + T && x < k.W; x++) {
+                    int64_t pix = (int64_t)y * k.W + x;
+                    double px = x + 0.5, py = y + 0.5, col[3], Tf;
+                    double gC[3] = {dL_dcolor[pix], dL_dcolor[HW + pix], dL_dcolor[2 * HW + pix]};
+                    int32_t nc;
+                    uint8_t a = 0;
+                    int nfl = 0;
+                    int nr = composite_pixel(&g, px, py, L, len, mean2d, conic, opac, rgb, depth, col, &Tf, &nc, &a,
+                                             s.rec, NULL, NULL, flags, MAX_FLAGS, &nfl);
+                    pixel_contribs(&g, px, py, s.rec, nr, Tf, mean2d, conic, rgb, gC, s.cb);
+                    /* (2) FP32 rounding */
+                    double U = 0, dmax = 0;
+                    for (int r = 0; r < nr; r++) {
+                        U += s.rec[r].alpha / (1.0 - s.rec[r].alpha) * s.rec[r].dpow + 2 * u;
+                        if (s.rec[r].dpow > dmax) dmax = s.rec[r].dpow;
+                    }
+                    double total[3] = {0, 0, 0};
+                    for (int r = 0; r < nr; r++)
+                        for (int ch = 0; ch < 3; ch++) total[ch] += s.rec[r].alpha * s.rec[r].T * rgb[3 * s.rec[r].id + ch];
+                    double prefix[3] = {0, 0, 0};
+                    double back = 0;
+                    for (int r = nr - 1; r >= 0; r--) back += s.rec[r].alpha / (1.0 - s.rec[r].alpha) * s.rec[r].dpow + 4 * u;
+                    for (int r = 0; r < nr; r++) {
+                        const Contrib* c = &s.rec[r];
+                        int32_t id = c->id;
+                        /* relative error of the recovered T_r: forward error of T_final plus the
+                         * recovery through every Gaussian from r to the back */
+                        double al = c->alpha, tr = c->T;
+                        double rel = U + back + (1.0 + al / (1.0 - al)) * c->dpow + ldexp(1.0, -20) + 64 * u + (nr - r) * u;
+                        double mag = 0;
+                        for (int ch = 0; ch < 3; ch++) {
+                            double ci = rgb[3 * id + ch];
+                            prefix[ch] += al * tr * ci;
+                            double after = total[ch] - prefix[ch];
+                            mag += fabs(gC[ch]) * (tr * fabs(ci) + (fabs(after) + fabs(Tf * g.bg[ch])) / (1.0 - al));
+                        }
+                        double e_da = mag * rel + dmax * mag;
+                        const double* o = s.cb + 9 * r;
+                        double b[9];
+                        for (int ch = 0; ch < 3; ch++) b[6 + ch] = fabs(o[6 + ch]) * (rel + 4 * u);
+                        for (int q = 0; q < 6; q++) b[q] = 0;
+                        if (!c->clamped) {
+                            double dx = px - mean2d[2 * id], dy = py - mean2d[2 * id + 1];
+                            double ca = conic[3 * id], cbb = conic[3 * id + 1], cc = conic[3 * id + 2];
+                            double ulp = 4.0 * ldexp(fmax(1.0, fmax(fabs(mean2d[2 * id]), fabs(mean2d[2 * id + 1]))), -24);
+                            double f[5] = {ca * dx + cbb * dy, cbb * dx + cc * dy, -0.5 * dx * dx, -dx * dy, -0.5 * dy * dy};
+                            double fe[5] = {(fabs(ca) + fabs(cbb)) * ulp + 1e-5 * (fabs(ca * dx) + fabs(cbb * dy)),
+                                            (fabs(cbb) + fabs(cc)) * ulp + 1e-5 * (fabs(cbb * dx) + fabs(cc * dy)),
+                                            fabs(dx) * ulp, (fabs(dx) + fabs(dy)) * ulp, fabs(dy) * ulp};
+                            /* |dalpha| from the opacity share: o[5] = dalpha g */
+                            double dalpha = c->g > 0 ? fabs(o[5]) / c->g : 0;
+                            double e_dp = e_da * c->og + dalpha * c->og * c->dpow;
+                            double dpw = dalpha * c->og;
+                            for (int q = 0; q < 5; q++) b[q] = e_dp * fabs(f[q]) + dpw * fe[q] + 4 * u * fabs(o[q]);
+                            b[5] = e_da * c->g + dalpha * c->g * c->dpow + 4 * u * fabs(o[5]);
+                        }
+                        for (int q = 0; q < 9; q++) p32[9 * (b0 + c->j) + q] += b[q] * b[q];
+                        if (jac) {
+                            for (int cc6 = 0; cc6 < 6; cc6++) {
+                                double sacc = 0;
+                                for (int q = 0; q < 9; q++) sacc += fabs(jac[54 * (int64_t)id + 9 * cc6 + q]) * b[q];
+                                tp[6 + cc6] += sacc * sacc;
+                            }
+                        }
+                        back -= c->alpha / (1.0 - c->alpha) * c->dpow + 4 * u;
+                    }
+                    /* scatter the pixel's contributions by list position */
+                    for (int64_t q = 0; q < 9 * (len + 1); q++) s.c0[q] = 0;
+                    int64_t hi0 = 0;
+                    for (int r = 0; r < nr; r++) {
+                        for (int q = 0; q < 9; q++) s.c0[9 * s.rec[r].j + q] = s.cb[9 * r + q];
+                        hi0 = s.rec[r].j + 1;
+                    }
+                    if (amb_in && amb_in[pix]) {
+                        double d[6] = {0, 0, 0, 0, 0, 0};
+                        for (int r = 0; r < nr; r++) {
+                            int64_t j = s.rec[r].j;
+                            for (int q = 0; q < 9; q++) pf[9 * (b0 + j) + q] += fabs(s.c0[9 * j + q]);
+                            if (jac)
+                                for (int cc6 = 0; cc6 < 6; cc6++)
+                                    for (int q = 0; q < 9; q++)
+                                        d[cc6] += fabs(jac[54 * (int64_t)L[j] + 9 * cc6 + q] * s.c0[9 * j + q]);
+                        }
+                        for (int cc6 = 0; cc6 < 6; cc6++) tp[cc6] += d[cc6];
+                    }
+                    /* (1) every recorded decision flipped on its own */
+                    for (int f = 0; f < nfl; f++) {
+                        int64_t hi;
+                        if (flags[f].kind == FL_DEPTH) {
+                            int64_t j1 = flags[f].j, j2 = flags[f].j2;
+                            memcpy(s.lst, L, sizeof(int32_t) * (size_t)len);
+                            s.lst[j1] = L[j2];
+                            s.lst[j2] = L[j1];
+                            for (int64_t j = 0; j < len; j++) map[j] = j;
+                            map[j1] = j2;
+                            map[j2] = j1;
+                            hi = pixel_by_position(&g, px, py, s.lst, len, mean2d, conic, opac, rgb, depth, gC, NULL,
+                                                   map, len + 1, s.recf, s.cb, s.cf);
+                        } else {
+                            hi = pixel_by_position(&g, px, py, L, len, mean2d, conic, opac, rgb, depth, gC, &flags[f],
+                                                   NULL, len + 1, s.recf, s.cb, s.cf);
+                        }
+                        if (hi0 > hi) hi = hi0;
+                        double d[6] = {0, 0, 0, 0, 0, 0};
+                        for (int64_t j = 0; j < hi; j++) {
+                            double dv[9];
+                            int nz = 0;
+                            for (int q = 0; q < 9; q++) {
+                                dv[q] = s.cf[9 * j + q] - s.c0[9 * j + q];
+                                nz |= dv[q] != 0;
+                            }
+                            if (!nz) continue;
+                            for (int q = 0; q < 9; q++) pf[9 * (b0 + j) + q] += fabs(dv[q]);
+                            if (jac) pose_of(jac, L[j], dv, d);
+                        }
+                        for (int cc6 = 0; cc6 < 6; cc6++) tp[cc6] += fabs(d[cc6]);
+                    }
+                }
+            /* (1) uncertain list memberships of this tile, one at a time over the whole tile */
+            for (int64_t m = mstart[t]; m < mstart[t + 1]; m++) {
+                int32_t item = (int32_t)memb[3 * m + 1];
+                int64_t jr = -1;
+                for (int64_t j = 0; j < len; j++)
+                    if (L[j] == item) { jr = j; break; }
+                int64_t len2;
+                if (jr >= 0) { /* remove it */
+                    len2 = len - 1;
+                    for (int64_t j = 0, w = 0; j < len; j++)
+                        if (j != jr) { s.lst[w] = L[j]; map[w] = j; w++; }
+                } else { /* insert it in (depth key, id) order */
+                    uint32_t kb;
+                    memcpy(&kb, &depth_key[item], 4);
+                    int64_t ji = 0;
+                    while (ji < len) {
+                        uint32_t kj;
+                        memcpy(&kj, &depth_key[L[ji]], 4);
+                        if (kj > kb || (kj == kb && L[ji] > item)) break;
+                        ji++;
+                    }
+                    len2 = len + 1;
+                    for (int64_t j = 0, w = 0; w < len2; w++) {
+                        if (w == ji) { s.lst[w] = item; map[w] = len; }
+                        else { s.lst[w] = L[j]; map[w] = j; j++; }
+                    }
+                }
+                for (int64_t q = 0; q < 9 * (len + 1); q++) s.acc[q] = 0;
+                for (int y = y0; y < y0 + T && y < k.H; y++)
+                    for (int x = x0; x < x0 + T && x < k.W; x++) {
+                        int64_t pix = (int64_t)y * k.W + x;
+                        double px = x + 0.5, py = y + 0.5;
+                        double gC[3] = {dL_dcolor[pix], dL_dcolor[HW + pix], dL_dcolor[2 * HW + pix]};
+                        pixel_by_position(&g, px, py, L, len, mean2d, conic, opac, rgb, depth, gC, NULL, NULL, len + 1,
+                                          s.rec, s.cb, s.c0);
+                        pixel_by_position(&g, px, py, s.lst, len2, mean2d, conic, opac, rgb, depth, gC, NULL, map,
+                                          len + 1, s.recf, s.cb, s.cf);
+                        for (int64_t q = 0; q < 9 * (len + 1); q++) s.acc[q] += s.cf[q] - s.c0[q];
+                    }
+                double d[6] = {0, 0, 0, 0, 0, 0};
+                for (int64_t j = 0; j < len; j++) {
+                    for (int q = 0; q < 9; q++) pf[9 * (b0 + j) + q] += fabs(s.acc[9 * j + q]);
+                    if (jac) pose_of(jac, L[j], s.acc + 9 * j, d);
+                }
+                for (int q = 0; q < 9; q++) pm[9 * m + q] = fabs(s.acc[9 * len + q]);
+                if (jac && jr < 0) pose_of(jac, item, s.acc + 9 * len, d);
+                for (int cc6 = 0; cc6 < 6; cc6++) mpose[6 * m + cc6] = d[cc6];
+            }
+        }
+        free(s.rec); free(s.recf); free(s.cb); free(s.c0); free(s.cf); free(s.acc); free(s.lst); free(map);
+    }
+    for (int64_t i = 0; i < 9 * n; i++) b_flip[i] = 0, b_fp32[i] = 0;
+    for (int64_t j = 0; j < P; j++)
+        for (int q = 0; q < 9; q++) {
+            b_flip[9 * (int64_t)ids[j] + q] += pf[9 * j + q];
+            b_fp32[9 * (int64_t)ids[j] + q] += p32[9 * j + q];
+        }
+    for (int64_t i = 0; i < 9 * n; i++) b_fp32[i] = sqrt(b_fp32[i]);
+    for (int64_t m = 0; m < n_memb; m++)
+        for (int q = 0; q < 9; q++) b_flip[9 * memb[3 * m + 1] + q] += pm[9 * m + q];
+    for (int c = 0; c < 6; c++) pose_flip[c] = 0, pose_fp32[c] = 0;
+    for (int64_t t = 0; t < nt; t++)
+        for (int c = 0; c < 6; c++) pose_flip[c] += tpose[12 * t + c], pose_fp32[c] += tpose[12 * t + 6 + c];
+    for (int c = 0; c < 6; c++) pose_fp32[c] = sqrt(pose_fp32[c]);
+    double* gpose = (double*)calloc((size_t)(n_group > 0 ? n_group : 1) * 6, sizeof(double));
+    for (int64_t m = 0; m < n_memb; m++)
+        for (int c = 0; c < 6; c++) gpose[6 * memb[3 * m + 2] + c] += mpose[6 * m + c];
+    for (int64_t q = 0; q < n_group; q++)
+        for (int c = 0; c < 6; c++) pose_flip[c] += fabs(gpose[6 * q + c]);
+    free(gpose);
+    free(mpose);
+    free(pf); free(p32); free(pm); free(tpose); free(mstart);
 }
 
 /* ---------------------------------------------------------------------------

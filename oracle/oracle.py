@@ -14,6 +14,7 @@ is silent the reading is the one documented at the top of gs_oracle.c.
 from __future__ import annotations
 
 import ctypes as C
+import dataclasses
 import math
 from dataclasses import dataclass, field
 
@@ -34,7 +35,7 @@ def lib():
                                 np.ctypeslib.ndpointer(np.float32, flags="C"),
                                 np.ctypeslib.ndpointer(np.uint8, flags="C"))
         _lib.or_project.restype = C.c_int64
-        _lib.or_project.argtypes = [C.c_int64, d, d, d, d, d, d, d, d, d, d, d, f32, i32, i32, u8, u8]
+        _lib.or_project.argtypes = [C.c_int64, d, d, d, d, d, d, d, d, d, d, d, f32, i32, i32, u8, u8, u8]
         _lib.or_tile_lists.restype = C.c_int64
         _lib.or_tile_lists.argtypes = [C.c_int64, i32, f32, C.c_int, C.c_int, i64, i32, C.c_int64]
         _lib.or_render_fwd.restype = None
@@ -45,6 +46,13 @@ def lib():
         _lib.or_render_bwd.argtypes = [d, d, i64, i32, d, d, d, d, opt, d, C.c_int64, d, opt, opt]
         _lib.or_project_bwd.restype = None
         _lib.or_project_bwd.argtypes = [C.c_int64, d, d, d, d, d, d, d, d, d, d, d, d, d]
+        _lib.or_project_bwd_abs.restype = None
+        _lib.or_project_bwd_abs.argtypes = [C.c_int64, d, d, d, d, d, d, d, opt, d, d, d, d, d, d, d]
+        _lib.or_pose_jacobian.restype = None
+        _lib.or_pose_jacobian.argtypes = [C.c_int64, d, d, d, d, d, d, d]
+        _lib.or_render_bwd_bounds.restype = None
+        _lib.or_render_bwd_bounds.argtypes = [d, d, i64, i32, d, d, d, d, opt, f32, d, C.c_int64, i64, C.c_int64,
+                                              opt, opt, d, d, d, d]
         _lib.or_sh_basis.restype = None
         _lib.or_sh_basis.argtypes = [C.c_int, d, d, d]
         u32 = np.ctypeslib.ndpointer(np.uint32, flags="C")
@@ -107,11 +115,13 @@ def project(scene, cam, cfg: Config) -> dict:
     n = scene.n
     out = dict(mean2d=np.zeros((n, 2)), conic=np.zeros((n, 3)), opacity=np.zeros(n), rgb=np.zeros((n, 3)),
                depth=np.zeros(n), depth_key=np.zeros(n, np.float32), rect=np.zeros((n, 4), np.int32),
-               n_tiles=np.zeros(n, np.int32), clamp=np.zeros(n, np.uint8), amb=np.zeros(n, np.uint8))
+               n_tiles=np.zeros(n, np.int32), clamp=np.zeros(n, np.uint8), amb=np.zeros(n, np.uint8),
+               edge_side=np.zeros(n, np.uint8))
     vis = lib().or_project(n, _c(scene.mean_opa, np.float64), _c(scene.scale, np.float64),
                            _c(scene.quat, np.float64), _c(scene.sh, np.float64), cam_array(cam), cfg.array(),
                            out["mean2d"], out["conic"], out["opacity"], out["rgb"], out["depth"],
-                           out["depth_key"], out["rect"], out["n_tiles"], out["clamp"], out["amb"])
+                           out["depth_key"], out["rect"], out["n_tiles"], out["clamp"], out["amb"],
+                           out["edge_side"])
     out["n_visible"] = int(vis)
     return out
 
@@ -186,6 +196,171 @@ def project_bwd(scene, cam, cfg: Config, g2d) -> dict:
                          _c(scene.quat, np.float64), _c(scene.sh, np.float64), cam_array(cam), cfg.array(),
                          _c(g2d, np.float64), out["mean"], out["logit"], out["log_scale"], out["quat"],
                          out["sh"], out["pose"])
+    return out
+
+
+def project_bwd_abs(scene, cam, cfg: Config, b2d, g2d=None) -> dict:
+    """Per-item bounds b2d [n, 9] (>= 0) on the 2D adjoint carried through the
+    projection adjoint with absolute Jacobians: the most each parameter
+    gradient (mean, logit, log_scale, quat, sh) and the view's pose gradient
+    can move. With g2d, pose_absum = sum over items of |pose contribution|."""
+    n = scene.n
+    out = dict(mean=np.zeros((n, 3)), logit=np.zeros(n), log_scale=np.zeros((n, 3)), quat=np.zeros((n, 4)),
+               sh=np.zeros((n, 48)), pose=np.zeros(6), pose_absum=np.zeros(6))
+    g = None if g2d is None else _c(g2d, np.float64)
+    lib().or_project_bwd_abs(n, _c(scene.mean_opa, np.float64), _c(scene.scale, np.float64),
+                             _c(scene.quat, np.float64), _c(scene.sh, np.float64), cam_array(cam), cfg.array(),
+                             _c(b2d, np.float64), None if g is None else g.ctypes.data, out["mean"], out["logit"],
+                             out["log_scale"], out["quat"], out["sh"], out["pose"], out["pose_absum"])
+    return out
+
+
+def pose_jacobian(scene, cam, cfg: Config) -> np.ndarray:
+    """[n, 6, 9]: d(pose gradient of the view) / d(2D adjoint of item i)."""
+    n = scene.n
+    jac = np.zeros((n, 6, 9))
+    lib().or_pose_jacobian(n, _c(scene.mean_opa, np.float64), _c(scene.scale, np.float64),
+                           _c(scene.quat, np.float64), _c(scene.sh, np.float64), cam_array(cam), cfg.array(), jac)
+    return jac
+
+
+def _subset(scene, idx):
+    return type(scene)(scene.mean_opa[idx], scene.scale[idx], scene.quat[idx], scene.sh[idx], scene.sh_degree)
+
+
+def ambiguous_memberships(view: dict, cam, cfg: Config, scene=None):
+    """(tile, item, group) triples whose tile-list membership an FP32
+    projection may decide the other way. A rect edge within the margin of a
+    tile boundary (bits 4/8/16/32 of the projection's flags) may round to the
+    other side: the column (row) just outside joins, or the one just inside
+    leaves, whichever the oracle's side of the boundary (edge_side) makes the
+    other rounding; a radius near an integer allows both. Items that may
+    vanish or appear altogether (bit 1): visible ones may leave all their
+    tiles; ones the near plane culled (given the scene) are projected with the
+    plane moved just past them and may join every tile of that rect (their
+    projections are returned in `extra`, item -> (projection, config)); any
+    other such item's neighbourhood is returned as a mask [H, W] of pixels
+    whose every contribution counts as uncertain. An item with an empty rect
+    (culled, but projected) may join the column or row next to a flagged edge.
+    The memberships of one edge (or one vanishing or appearing item) share a
+    group: they change together. Returns (memb int64 [m, 3] sorted by tile,
+    mask uint8 [H, W], extra)."""
+    tx, ty = tiles_xy(cam, cfg)
+    T = cfg.tile
+    W, H = cam["width"], cam["height"]
+    proj = view["proj"]
+    amb = proj["amb"]
+    side = proj.get("edge_side")
+    out = []
+    bad = np.zeros((ty, tx), bool)
+    vis = proj["n_tiles"] > 0
+    extra = {}
+    group = 0
+
+    def add(tiles, i):
+        nonlocal group
+        tiles = sorted(set(tiles))
+        if tiles:
+            out.extend((t, int(i), group) for t in tiles)
+            group += 1
+
+    for i in np.nonzero(amb & (1 | 4 | 8 | 16 | 32))[0]:
+        x0, y0, x1, y1 = (int(c) for c in proj["rect"][i])
+        a = int(amb[i])
+        if a & 1:
+            if vis[i]:
+                # may vanish: it may leave all of its tiles
+                add([ry * tx + cx for ry in range(y0, y1) for cx in range(x0, x1)], i)
+            elif proj["opacity"][i] == 0 and np.all(proj["conic"][i] == 0):
+                z = proj["depth"][i]
+                if scene is not None and np.isfinite(z) and z <= cfg.near_z:
+                    # culled by the near plane within its margin: project it with the plane moved
+                    # just past it; it may join every tile of that rect
+                    cfg2 = dataclasses.replace(cfg, near_z=float(z) - cfg.margin_geo * max(1.0, abs(float(z))))
+                    one = project(_subset(scene, [i]), cam, cfg2)
+                    if one["n_tiles"][0] > 0:
+                        extra[int(i)] = (one, cfg2)
+                        r0, s0, r1, s1 = (int(c) for c in one["rect"][0])
+                        add([ry * tx + cx for ry in range(s0, s1) for cx in range(r0, r1)], i)
+                    continue
+                # culled before its projection otherwise (non-finite): not modelled
+                u, v = proj["mean2d"][i]
+                if np.isfinite(u) and np.isfinite(v):
+                    cx, cy = int(np.clip(u // T, 0, tx - 1)), int(np.clip(v // T, 0, ty - 1))
+                    bad[max(cy - 2, 0):cy + 3, max(cx - 2, 0):cx + 3] = True
+            continue
+        if proj["opacity"][i] == 0 and np.all(proj["conic"][i] == 0):
+            continue
+        sd = 0x0F | 0xF0 if side is None else int(side[i])
+        # edge c: 0 = x0, 1 = y0, 2 = x1, 3 = y1; "down" = the other rounding is one less
+        for c, (lo, hi, n_) in enumerate(((x0, x1, tx), (y0, y1, ty), (x0, x1, tx), (y0, y1, ty))):
+            if not a & (4 << c):
+                continue
+            down = bool(sd & (1 << c))
+            both = bool(sd & (16 << c))
+            lines = []
+            if c < 2:  # a lower edge at e: one less -> line e - 1 joins; one more -> line e leaves
+                if down or both:
+                    lines.append(lo - 1)
+                if not down or both:
+                    lines.append(lo)
+            else:      # an upper edge at e (exclusive): one less -> line e - 1 leaves; one more -> line e joins
+                if down or both:
+                    lines.append(hi - 1)
+                if not down or both:
+                    lines.append(hi)
+            for ln in lines:
+                if not 0 <= ln < n_:
+                    continue
+                if c in (0, 2):
+                    add([ry * tx + ln for ry in range(y0, y1)], i)
+                else:
+                    add([ln * tx + cx for cx in range(x0, x1)], i)
+    memb = np.array(sorted(out), np.int64).reshape(-1, 3)
+    mask = np.repeat(np.repeat(bad, T, 0), T, 1)[:H, :W].astype(np.uint8)
+    return memb, mask, extra
+
+
+def adjoint_bounds(scene, view: dict, cam, cfg: Config, dL_dcolor) -> dict:
+    """render_bwd_bounds for a whole view with every uncertain membership
+    modelled (ambiguous_memberships), the pose Jacobian of the projection
+    adjoint, and the near-plane items that may appear projected as they would
+    be. Adds the count of such items (near_plane) and of masked pixels."""
+    memb, mask, extra = ambiguous_memberships(view, cam, cfg, scene)
+    proj = view["proj"]
+    jac = pose_jacobian(scene, cam, cfg)
+    if extra:
+        proj = {k: (np.array(v, copy=True) if isinstance(v, np.ndarray) else v) for k, v in proj.items()}
+        for i, (one, cfg2) in extra.items():
+            for k in ("mean2d", "conic", "opacity", "rgb", "depth", "depth_key"):
+                proj[k][i] = one[k][0]
+            jac[i] = pose_jacobian(_subset(scene, [i]), cam, cfg2)[0]
+    out = render_bwd_bounds(proj, view["start"], view["ids"], cam, cfg, dL_dcolor, memb, mask, jac)
+    out["near_plane"] = len(extra)
+    out["masked_pixels"] = int(mask.sum())
+    out["memberships"] = int(memb.shape[0])
+    return out
+
+
+def render_bwd_bounds(proj, start, ids, cam, cfg: Config, dL_dcolor, memb=None, amb_pixels=None, jac=None) -> dict:
+    """How far an FP32 compositing adjoint may legitimately be from render_bwd
+    (gs_oracle.c, or_render_bwd_bounds): flip [n, 9] from decisions within
+    their margin and uncertain list memberships, fp32 [n, 9] from the rounding
+    of a back-to-front adjoint; with the pose Jacobian, pose_flip [6] and
+    pose_fp32 [6] for the view's pose gradient."""
+    n = proj["mean2d"].shape[0]
+    out = dict(flip=np.zeros((n, 9)), fp32=np.zeros((n, 9)), pose_flip=np.zeros(6), pose_fp32=np.zeros(6))
+    z, zp = _depth_arg(proj)
+    memb = np.zeros((0, 3), np.int64) if memb is None else _c(memb, np.int64)
+    mask = None if amb_pixels is None else _c(amb_pixels, np.uint8)
+    j = None if jac is None else _c(jac, np.float64)
+    lib().or_render_bwd_bounds(cam_array(cam), cfg.array(), _c(start, np.int64), _c(ids, np.int32),
+                               _c(proj["mean2d"], np.float64), _c(proj["conic"], np.float64),
+                               _c(proj["opacity"], np.float64), _c(proj["rgb"], np.float64), zp,
+                               _c(proj["depth_key"], np.float32), _c(dL_dcolor, np.float64), n,
+                               memb if memb.size else np.zeros((1, 3), np.int64), int(memb.shape[0]),
+                               None if mask is None else mask.ctypes.data, None if j is None else j.ctypes.data,
+                               out["flip"], out["fp32"], out["pose_flip"], out["pose_fp32"])
     return out
 
 

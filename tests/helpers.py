@@ -24,63 +24,48 @@ def assert_close(got, ref, rtol, mask=None, what=""):
                              f"(worst got={got.flat[i]!r} ref={ref.flat[i]!r}, rms={rms:.3e})")
 
 
-def excluded_gaussians(view: dict, bad_tiles: np.ndarray) -> np.ndarray:
-    """Gaussians listed in any flagged tile, plus those with an ambiguous
-    geometric or gradient-path decision."""
-    n = view["proj"]["mean2d"].shape[0]
-    out = np.zeros(n, bool)
-    start, ids = view["start"], view["ids"]
-    for t in np.nonzero(bad_tiles.reshape(-1))[0]:
-        out[ids[start[t]:start[t + 1]]] = True
-    out |= (view["proj"]["amb"] & (1 | 2)) > 0
-    return out
-
-
 def tile_pixel_mask(bad_tiles: np.ndarray, width: int, height: int, tile: int) -> np.ndarray:
     """Pixel mask [H, W] of the pixels lying in flagged tiles."""
     m = np.repeat(np.repeat(bad_tiles, tile, 0), tile, 1)
     return m[:height, :width]
 
 
-def amb_heavy(g2d, amb, rtol, share=0.3):
-    """Items whose 2D adjoint draws more than `share` of the tolerance from
-    pixels the oracle flagged as ambiguous (a flip there could move it)."""
-    g2d = np.asarray(g2d)
-    amb = np.asarray(amb)
-    rms = np.sqrt(np.mean(g2d * g2d, axis=0, keepdims=True)) + 1e-300
-    return np.any(amb > share * rtol * (np.abs(g2d) + rms), axis=1)
-
-
-def fp32_adjoint_kappa(n_contrib_max):
-    """Relative FP32 error per contribution of the compositing adjoint: the
-    transmittance in front of a Gaussian is recovered from T_final through up
-    to n_contrib reciprocal-and-multiply steps (about 1.5 ulp each), so a term
-    can be off by about n_contrib x 2^-23 relative (bound taken 2x wider)."""
-    return 3.0 * 2.0 ** -23 * max(1, int(n_contrib_max))
-
-
-def ill_conditioned(g2d, absum, rtol, kappa, share=0.3):
-    """Items whose 2D adjoint is a sum with so much cancellation that its FP32
-    error bound, kappa x the sum of |contributions| (absum, from the oracle),
-    exceeds `share` of the tolerance: the FP32 path cannot be held to the
-    tolerance there, so such items are excluded and counted like flagged ones."""
-    g2d = np.asarray(g2d)
-    rms = np.sqrt(np.mean(g2d * g2d, axis=0, keepdims=True)) + 1e-300
-    return np.any(kappa * np.asarray(absum) > share * rtol * (np.abs(g2d) + rms), axis=1)
-
-
-def assert_close_tail(got, ref, rtol, mask=None, what="", min_frac=0.9999, hard=4.0):
-    """assert_close for full-size sums: at least min_frac of the entries within
-    rtol x (|ref| + rms), every entry within hard x that (FP32 sums over
-    hundreds of composited Gaussians and several views leave a thin tail)."""
+def assert_within(got, ref, rtol, bound=None, mask=None, what=""):
+    """|x_gpu - x_ref| <= rtol * (|x_ref| + rms(x_ref)) + bound, elementwise over
+    the entries selected by mask (rms over those entries). bound [same shape,
+    >= 0] is the oracle's own estimate of how far an FP32 evaluation may
+    legitimately move the value (decisions within their margin taking the
+    other branch, rounding). Returns (worst ratio of error to allowance,
+    median share of bound / (rtol * (|x_ref| + rms)))."""
     got = np.asarray(got, np.float64)
     ref = np.asarray(ref, np.float64)
+    bound = np.zeros_like(ref) if bound is None else np.broadcast_to(np.asarray(bound, np.float64), ref.shape)
     if mask is not None:
-        got = got[mask]
-        ref = ref[mask]
+        got, ref, bound = got[mask], ref[mask], bound[mask]
     if ref.size == 0:
-        return
+        return 0.0, 0.0
     rms = float(np.sqrt(np.mean(ref * ref)))
-    ratio = np.abs(got - ref) / (rtol * (np.abs(ref) + rms) + 1e-300)
-    frac = float(np.mean(ratio <= 1.0))
-    assert frac >= min_frac and ratio.max() <= hard, (what, frac, float(ratio.max()), ref.size)
+    tol = rtol * (np.abs(ref) + rms)
+    lim = tol + bound
+    err = np.abs(got - ref)
+    bad = ~(err <= lim)
+    if bad.any():
+        i = np.argmax(np.where(bad, err / np.maximum(lim, 1e-300), 0))
+        raise AssertionError(f"{what}: {int(bad.sum())} of {ref.size} entries exceed rtol={rtol} + bound "
+                             f"(worst got={got.flat[i]!r} ref={ref.flat[i]!r} bound={bound.flat[i]!r}, rms={rms:.3e})")
+    return float((err / np.maximum(lim, 1e-300)).max()), float(np.median(bound / np.maximum(tol, 1e-300)))
+
+
+def workload_gradients(oracle, scene, cams, cfg, views, synth, seed=0):
+    """dL/dC of the joint optimisation's L1 loss for each view: the oracle's
+    render at the training pose against a target rendered from the same
+    scene at a pose perturbed by N(0, 0.01) rad / m (the training poses of the
+    benchmark workload are off by that much), sign(C - target) / (3 H W)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for view, cam in zip(views, cams):
+        R, t = synth.perturb_pose(rng, np.asarray(cam["R"], np.float64), np.asarray(cam["t"], np.float64))
+        cam2 = dict(cam, R=R.astype(np.float32), t=t.astype(np.float32))
+        target = oracle.render_view(scene, cam2, cfg)["color"]
+        out.append(np.sign(view["color"] - target) / view["color"].size)
+    return out

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import amb_heavy, assert_close, assert_close_tail, excluded_gaussians, fp32_adjoint_kappa, ill_conditioned, tile_pixel_mask
+from helpers import assert_close, assert_within, tile_pixel_mask, workload_gradients
 from oracle import oracle as O
 from paper_2506_05558_gb300 import gs, synth
 from paper_2506_05558_gb300.raster import Rasterizer
@@ -17,6 +17,10 @@ pytestmark = pytest.mark.gpu
 IMG_RTOL = 1e-4
 GRAD_RTOL = 1e-3
 MARGINS = dict(margin_alpha=1e-4, margin_T=1e-4, margin_rect_px=2e-3, margin_geo=1e-5)
+# confidence factor on the root-sum-square FP32 rounding bound of the adjoint
+FP32_LAMBDA = 1.0
+# with the workload's loss gradient, the pose bound may use at most this share of |ref| + rms
+POSE_SHARE = 1e-2
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -173,14 +177,12 @@ def test_render_bwd_2d_adjoint_matches_oracle():
     start, ids = O.tile_lists(it["rect"], it["rgb_depth"][:, 3], (w + 15) // 16, (h + 15) // 16)
     oproj = oracle_proj(it)
     oproj.update(amb=np.zeros(n, np.uint8), depth=it["rgb_depth"][:, 3].astype(np.float64))
-    ref, amb = O.render_bwd(oproj, start, ids, cam, ocfg, dL.astype(np.float64), with_amb=True)
-    fwd = O.render_fwd(oproj, start, ids, cam, ocfg)
-    ex = amb_heavy(ref, amb, GRAD_RTOL) | (fwd["amb_gauss"] > 0)
+    ref = O.render_bwd(oproj, start, ids, cam, ocfg, dL.astype(np.float64))
+    bb = O.render_bwd_bounds(oproj, start, ids, cam, ocfg, dL.astype(np.float64))
     got = d_proj.cpu().numpy()
-    keep = ~ex
-    assert keep.sum() > 0.9 * n
+    vis = it["n_tiles"] > 0
     for c, name in enumerate(["du", "dv", "da", "db", "dc", "dopa", "dr", "dg", "db_"]):
-        assert_close(got[:, c], ref[:, c], GRAD_RTOL, keep, name)
+        assert_within(got[:, c], ref[:, c], GRAD_RTOL, bb["flip"][:, c] + FP32_LAMBDA * bb["fp32"][:, c], vis, name)
 
 
 def test_render_bwd_deterministic():
@@ -249,34 +251,55 @@ def last_contributor_tied(view, w, h, tile):
     return tied
 
 
-def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), max_amb_frac=0.3, max_excl_frac=0.25,
-                  dLs=None, mip=0, conditioning=False, min_cond_frac=0.3, margins=None, **launch):
+def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), max_amb_frac=0.3, max_excl_frac=0.05,
+                  dLs=None, grad="l1", mip=0, margins=None, lam=FP32_LAMBDA, max_pose_share=POSE_SHARE, **launch):
     """GPU vs oracle on every view: projection, image, n_contrib, the 2D adjoint
-    per item, the parameter and pose gradients, away from flagged decisions.
-    conditioning (full-size workloads, pixels hundreds of Gaussians deep): the
-    2D adjoint's tolerance also admits kappa x sum|contributions| - the FP32
-    error of a sum whose terms carry the transmittance recovered through up to
-    n_contrib steps - and the parameter gradients are compared on the items
-    whose 2D adjoint is well conditioned in every view (at least min_cond_frac
-    of the compared items)."""
+    per item, every visible Gaussian's parameter gradients and the pose
+    gradient of each view.
+
+    The adjoint input dL/dC is the workload's L1 gradient (grad="l1": a render
+    at the training pose against a target from a perturbed pose), standard
+    normal noise (grad="random"), or dLs when given. Gradients are held to
+    1e-3 * (|ref| + rms) plus the oracle's own bound on what an FP32 evaluation
+    may legitimately change: every decision within its margin flipped on its
+    own and every uncertain tile membership toggled, plus lam x the root sum of
+    squares of the first-order FP32 error of each contribution, carried to
+    the parameters and the pose through the projection adjoint. Only items
+    with a flagged projection decision (near plane, determinant, guard band,
+    colour clamp: the adjoint's own path may differ) are left out, and
+    counted. With the workload gradient the pose bound must stay below
+    max_pose_share of |ref| + rms, except in a view where a Gaussian lies
+    within the FP32 uncertainty of the near plane (reported)."""
     dil = 0.1 if mip else 0.3
-    r, dLs, d_proj = run_views(sc, cams, sh_degree, dLs=dLs, pose_through_sh=pose_through_sh, bg=bg, mip_filter=mip,
-                               dilation=dil, **launch)
     tile = launch.get("tile", 16)
     ocfg = O.Config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg, tile=tile, mip_filter=mip,
                     dilation=dil, **(margins or MARGINS))
+    views = [O.render_view(sc, cam, ocfg) for cam in cams]
+    workload = dLs is None and grad == "l1"
+    if dLs is None:
+        if grad == "l1":
+            dLs = workload_gradients(O, sc, cams, ocfg, views, synth)
+        else:
+            rng = np.random.default_rng(0)
+            dLs = [rng.standard_normal((3, c["height"], c["width"])) for c in cams]
+    r, dLs, d_proj = run_views(sc, cams, sh_degree, dLs=dLs, pose_through_sh=pose_through_sh, bg=bg, mip_filter=mip,
+                               dilation=dil, **launch)
     n = sc.n
-    views = []
+    keys = ("mean", "logit", "log_scale", "quat", "sh")
+    ref = {k: 0.0 for k in keys}
+    bnd = {k: 0.0 for k in keys}
     excl = np.zeros(n, bool)
-    ill = np.zeros(n, bool)
+    vis_any = np.zeros(n, bool)
     n_amb_px = 0
+    pose_gpu = r.dpose.cpu().numpy()
+    report = []
     for v, cam in enumerate(cams):
         w, h = cam["width"], cam["height"]
-        view = O.render_view(sc, cam, ocfg)
-        views.append(view)
+        view = views[v]
         proj = view["proj"]
         # projection outputs
         vis = proj["n_tiles"] > 0
+        vis_any |= vis
         pg = r.proj
         sl = slice(v * n, (v + 1) * n)
         nt = pg.n_tiles[sl].cpu().numpy()
@@ -309,56 +332,56 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
         pl &= ~last_contributor_tied(view, w, h, tile)
         nc = r.view_pixels(r.img.n_contrib, v).cpu().numpy()
         assert np.array_equal(nc[pl], view["n_contrib"][pl]), (v, int((nc[pl] != view["n_contrib"][pl]).sum()))
-        # 2D adjoint per item
-        g2d, amb = O.render_bwd(proj, view["start"], view["ids"], cam, ocfg, dLs[v], with_amb=True,
-                                amb_pixels=~pm)
-        ex_v = (proj["amb"] > 0) | (view["amb_gauss"] > 0) | amb_heavy(g2d, amb, GRAD_RTOL)
-        excl |= ex_v
-        ok = vis & ~ex_v
-        if conditioning:
-            # sum of |contributions| per item (every pixel counted as "ambiguous")
-            _, absum = O.render_bwd(proj, view["start"], view["ids"], cam, ocfg, dLs[v], with_amb=True,
-                                    amb_pixels=np.ones((h, w), bool))
-            kappa = fp32_adjoint_kappa(view["n_contrib"].max())
-            ill |= ill_conditioned(g2d, absum, GRAD_RTOL, kappa)
-            for c in range(9):
-                ref = g2d[ok, c]
-                rms = np.sqrt(np.mean(ref * ref)) if ref.size else 0.0
-                err = np.abs(d_proj[sl][ok, c] - ref)
-                lim = GRAD_RTOL * (np.abs(ref) + rms) + kappa * absum[ok, c]
-                assert (err <= lim).all(), (f"d_proj[{c}] view {v}", int((err > lim).sum()), float((err / lim).max()))
-        else:
-            for c in range(9):
-                assert_close(d_proj[sl][:, c], g2d[:, c], GRAD_RTOL, ok, f"d_proj[{c}] view {v}")
-    ref = O.backward_views(sc, cams, ocfg, views, dLs)
-    keep = ~excl
-    if conditioning:
-        assert (keep & ~ill).sum() >= min_cond_frac * keep.sum(), ((keep & ~ill).sum(), keep.sum())
-        keep = keep & ~ill
+        # the oracle's adjoint of this view and its bounds
+        b = O.backward_view(sc, cam, ocfg, view, dLs[v])
+        bb = O.adjoint_bounds(sc, view, cam, ocfg, dLs[v])
+        b2d = bb["flip"] + lam * bb["fp32"]
+        geo = (proj["amb"] & (1 | 2)) > 0
+        excl |= geo
+        ok = vis & ~geo
+        worst2d = 0.0
+        for c in range(9):
+            wr, _ = assert_within(d_proj[sl][:, c], b["g2d"][:, c], GRAD_RTOL, b2d[:, c], ok, f"d_proj[{c}] view {v}")
+            worst2d = max(worst2d, wr)
+        ab = O.project_bwd_abs(sc, cam, ocfg, b2d)
+        for k in keys:
+            ref[k] = ref[k] + b[k]
+            bnd[k] = bnd[k] + ab[k]
+        # pose of this view: its sum runs over every item; the bound covers the flips and rounding
+        pr = b["pose"]
+        pb = bb["pose_flip"] + lam * bb["pose_fp32"]
+        wp, _ = assert_within(pose_gpu[v], pr, GRAD_RTOL, pb, what=f"pose view {v}")
+        share = float((pb / (np.abs(pr) + np.sqrt(np.mean(pr * pr)))).max())
+        report.append(f"view {v}: 2D adjoint worst {worst2d:.3f}, pose worst {wp:.3f}, pose bound share {share:.2e} "
+                      f"({bb['memberships']} uncertain memberships, {bb['near_plane']} near-plane items, "
+                      f"{bb['masked_pixels']} masked pixels)")
+        # a Gaussian within the FP32 uncertainty of the near plane may appear as a splat hundreds of pixels
+        # wide in front of everything: the pose bound of such a view is that large, and is reported
+        if workload and bb["near_plane"] == 0:
+            assert share <= max_pose_share, (v, share)
+    keep = vis_any & ~excl
     gr = r.grads
     mo = gr.mean_opa.cpu().numpy()
-    # full-size sums (conditioning): a thin FP32 tail is admitted, bounded and counted
-    close = assert_close_tail if conditioning else assert_close
-    close(mo[:, :3], ref["mean"], GRAD_RTOL, keep, "d mean")
-    close(mo[:, 3], ref["logit"], GRAD_RTOL, keep, "d opacity logit")
-    close(gr.scale.cpu().numpy()[:, :3], ref["log_scale"], GRAD_RTOL, keep, "d log-scale")
-    close(gr.quat.cpu().numpy(), ref["quat"], GRAD_RTOL, keep, "d quat")
     ncoef = 3 * (sh_degree + 1) ** 2
-    close(gr.sh.cpu().numpy()[:, :ncoef], ref["sh"][:, :ncoef], GRAD_RTOL, keep, "d sh")
-    vis_any = np.zeros(n, bool)
-    for view in views:
-        vis_any |= view["proj"]["n_tiles"] > 0
+    got = dict(mean=mo[:, :3], logit=mo[:, 3], log_scale=gr.scale.cpu().numpy()[:, :3], quat=gr.quat.cpu().numpy(),
+               sh=gr.sh.cpu().numpy()[:, :ncoef])
+    shares = []
+    for k in keys:
+        rk, bk = ref[k], bnd[k]
+        if k == "sh":
+            rk, bk = rk[:, :ncoef], bk[:, :ncoef]
+        wr, med = assert_within(got[k], rk, GRAD_RTOL, bk, keep, f"d {k}")
+        shares.append(f"{k} worst {wr:.3f} median bound/tol {med:.2f}")
     assert np.array_equal(gr.visible.cpu().numpy().astype(bool)[keep], vis_any[keep])
     total_px = sum(c["width"] * c["height"] for c in cams)
     assert n_amb_px <= max_amb_frac * total_px + 256, n_amb_px
-    assert excl.sum() <= max_excl_frac * n + 10, excl.sum()
-    # pose: the sum runs over every pixel, ambiguous ones included; widen the
-    # bound by the ambiguous pixel share
-    pose = r.dpose.cpu().numpy()
-    rt = GRAD_RTOL + 10.0 * n_amb_px / total_px
-    for v in range(len(cams)):
-        assert_close(pose[v], ref["pose"][v], rt, what=f"pose view {v}")
-    return r, excl.sum()
+    n_excl = int(excl[vis_any].sum())
+    assert n_excl <= max_excl_frac * vis_any.sum() + 10, (n_excl, int(vis_any.sum()))
+    print(f"\n[{len(cams)} views, {int(vis_any.sum())} visible Gaussians, {n_excl} excluded "
+          f"({n_excl / max(1, vis_any.sum()):.2e})]")
+    for line in report + shares:
+        print("  " + line)
+    return r, n_excl
 
 
 @pytest.mark.parametrize("mip", [0, 1])
@@ -370,17 +393,20 @@ def test_tiny_scene_sh0_end_to_end(mip):
 
 
 @pytest.mark.parametrize("through_sh", [0, 1])
-def test_multiview_sh3_end_to_end(through_sh):
-    """Three views of different sizes (ragged edge tiles), SH degree 3."""
+@pytest.mark.parametrize("grad", ["l1", "random"])
+def test_multiview_sh3_end_to_end(through_sh, grad):
+    """Three views of different sizes (ragged edge tiles), SH degree 3, with
+    and without the SH view-direction path in the pose gradient; adjoint input
+    the workload's L1 gradient or standard normal noise."""
     sc, cams, _ = synth.multiview_scene(seed=5, n=20000, n_views=3, sizes=[(200, 120), (131, 77), (96, 160)])
-    compare_views(sc, cams, 3, pose_through_sh=through_sh, max_excl_frac=0.6)
+    compare_views(sc, cams, 3, pose_through_sh=through_sh, grad=grad)
 
 
 def test_multiview_sh3_mip_filter_end_to_end():
     """The same three views with the integral-keeping 2-D filter (dilation 0.1):
     small splats lose opacity, so the filter's gradient path is exercised."""
     sc, cams, _ = synth.multiview_scene(seed=5, n=20000, n_views=3, sizes=[(200, 120), (131, 77), (96, 160)])
-    compare_views(sc, cams, 3, max_excl_frac=0.6, mip=1)
+    compare_views(sc, cams, 3, mip=1)
 
 
 @pytest.mark.parametrize("tile,schedule,fb,bb", [(8, 0, 64, 256), (8, 1, 256, 64), (16, 1, 64, 32),
@@ -389,7 +415,7 @@ def test_tiles_batches_schedules_end_to_end(tile, schedule, fb, bb):
     """Every tile size (8, 16, 32), staging depth and both render schedules
     give the oracle's images and gradients (the oracle at the same tile size)."""
     sc, cams, _ = synth.multiview_scene(seed=6, n=8000, n_views=2, sizes=[(200, 120), (96, 160)])
-    compare_views(sc, cams, 3, tile=tile, schedule=schedule, fwd_batch=fb, bwd_batch=bb, max_excl_frac=0.6)
+    compare_views(sc, cams, 3, tile=tile, schedule=schedule, fwd_batch=fb, bwd_batch=bb)
 
 
 def test_graph_replay_matches_eager_steps():
@@ -452,16 +478,23 @@ def test_headline_1m_8x1080p_end_to_end():
     """The benchmark workload at full size - 1M Gaussians SH3, 8 views 1920x1080 on
     the camera path - in the benchmark's launch configuration (tile 16, staging
     depths 256 forward / 64 backward, one CTA per tile, all views in one launch):
-    every view's projection, image, n_contrib and 2D adjoint, all Gaussian
-    gradients and the 8 pose gradients against the FP64 oracle."""
+    every view's projection, image, n_contrib and 2D adjoint, every visible
+    Gaussian's gradients and the 8 pose gradients against the FP64 oracle, with
+    the adjoint input the workload's L1 gradient."""
     sc, cams, _ = synth.multiview_scene()
     # rect edges flagged within 5e-4 px of a tile boundary (the FP32 screen position at 1080p is good to about
-    # 5 ulp of 1400 px, 4e-4 px; the observed flips sat within 1e-4 px); about 70% of the million Gaussians
-    # draw on an excluded pixel or decision somewhere in the 8 views and are excluded from the parameter
-    # gradients (the images, n_contrib and per-view 2D adjoints are compared nearly everywhere)
+    # 5 ulp of 1400 px, 4e-4 px; the observed flips sat within 1e-4 px)
     m = dict(MARGINS, margin_rect_px=5e-4)
-    _, n_excl = compare_views(sc, cams, 3, tile=16, fwd_batch=256, bwd_batch=64, schedule=0, max_amb_frac=0.1,
-                              max_excl_frac=0.8, conditioning=True, min_cond_frac=0.2, margins=m)
+    compare_views(sc, cams, 3, tile=16, fwd_batch=256, bwd_batch=64, schedule=0, max_amb_frac=0.1, margins=m)
+
+
+def test_720p_200k_random_adjoint_end_to_end():
+    """1280x720, 200k Gaussians, SH3, with standard normal dL/dC: the pose is then
+    a near-zero sum of large terms of both signs, the hardest case for its
+    bound, which is reported (the per-item and parameter checks are as strict
+    as with the workload gradient)."""
+    sc, cam, _ = synth.view_720p_scene()
+    compare_views(sc, [cam], 3, grad="random")
 
 
 def test_720p_200k_end_to_end():
