@@ -386,7 +386,10 @@ int gs_scale_opacity(float* mean_opa, int64_t n, float w, void* stream);
  *  - Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
  *  - The first call on each device looks up the array's device address with
  *    that device current (cudaGetSymbolAddress); make that first call before
- *    any stream capture.
+ *    any stream capture. The address belongs to the device's context: after
+ *    cudaDeviceReset (a new primary context) the next call looks it up again,
+ *    so that call too belongs outside a capture. Concurrent first calls from
+ *    several host threads are serialised by a lock.
  *  - Every call shares the one array, which keeps the previous call's
  *    contents; nothing in it needs to start at zero (each pass writes what it
  *    reads). Calls whose kernels overlap on a GPU race on the array: issue them

@@ -10,6 +10,7 @@
 // passed by value) are applied directly. The mask is compacted in pixel order
 // with the device-wide scan, then k_spawn_emit writes the spawned rows.
 #include <cmath>
+#include <cuda.h>
 #include <mutex>
 
 #include "common.cuh"
@@ -225,19 +226,55 @@ static __device__ __align__(256) uint32_t g_spawn_scratch[kNoAllocWords];  // ~1
 
 // Device address of g_spawn_scratch, looked up once per device with that
 // device current (the host-side name of the array is not a device address).
+// The address belongs to the device's context: after cudaDeviceReset the
+// runtime creates a new primary context with the module loaded again, so the
+// cached address is kept with the unique id of the context it came from
+// (cuCtxGetCurrent + cuCtxGetId, resolved through the runtime's driver
+// entry-point query, without linking the driver library) and looked up again
+// when the current context is another one. Where the driver offers neither
+// call, the address is looked up on every call. The mutex orders concurrent
+// first calls from several host threads.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+static bool current_context_id(CtxGetCurrentFn cur, CtxGetIdFn id, unsigned long long* out) {
+    CUcontext ctx = nullptr;
+    return cur && id && cur(&ctx) == CUDA_SUCCESS && ctx && id(ctx, out) == CUDA_SUCCESS;
+}
+
 static uint32_t* noalloc_scratch_for_current_device() {
     static std::mutex mu;
     static uint32_t* ptr[kNoAllocMaxDevices] = {};
+    static unsigned long long ctx_id[kNoAllocMaxDevices] = {};
+    static bool resolved = false;
+    static CtxGetCurrentFn ctx_current = nullptr;
+    static CtxGetIdFn ctx_get_id = nullptr;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) return nullptr;
     std::lock_guard<std::mutex> lock(mu);
-    if (!ptr[dev]) {
+    if (!resolved) {
+        resolved = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            ctx_current = (CtxGetCurrentFn)f;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            ctx_get_id = (CtxGetIdFn)f;
+        (void)cudaGetLastError();
+    }
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(ctx_current, ctx_get_id, &id);
+    if (!ptr[dev] || !have_id || id != ctx_id[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_spawn_scratch) != cudaSuccess) {
             (void)cudaGetLastError();
             return nullptr;
         }
         ptr[dev] = (uint32_t*)p;
+        // the lookup made the device's context current if none was
+        ctx_id[dev] = current_context_id(ctx_current, ctx_get_id, &id) ? id : 0;
     }
     return ptr[dev];
 }

@@ -1,6 +1,7 @@
 """The allocation-free spawn proposal (for callers that cannot allocate device
 memory, e.g. a host application that owns the allocator) must give exactly
-what the workspace-based gs_spawn_propose gives, call after call, although its
+what the workspace-based gs_spawn_propose gives - bit for bit, since both run
+the same kernels - call after call and across frame sizes, although its
 scratch is one array inside the library shared by all calls.
 
 Collected last on purpose: it runs after every other test in a full run, and
@@ -34,25 +35,55 @@ def _frame(seed, W, H):
     return t32(im), t32(rd), t32(depth)
 
 
-def test_noalloc_matches_workspace_entry_point_twice():
-    W, H = 640, 360
-    cam = gs.cameras_tensor([synth.camera(np.eye(3), np.zeros(3), 500.0, W, H)])
-    ws = gs.workspace(gs.gs_spawn_workspace_size(W, H))
-    for call, seed in enumerate((11, 12)):  # two calls in a row: the shared scratch holds the previous call's data
-        im, rd, depth = _frame(seed, W, H)
-        ref = gs.Spawned.alloc(W * H, W * H)
-        got = gs.Spawned.alloc(W * H, W * H)
-        gs.gs_spawn_propose(im, rd, depth, W, H, cam, 1.0, 77, call, ref, ws)
-        assert gs.gs_spawn_propose_noalloc(im, rd, depth, W, H, cam, 1.0, 77, call, got) == gs.GS_OK
-        torch.cuda.synchronize()
-        assert int(got.status.item()) == gs.GS_OK
-        n = int(ref.count.item())
-        assert n > 1000 and int(got.count.item()) == n
-        for a, b in ((got.p_l, ref.p_l), (got.p_pen, ref.p_pen), (got.p_s, ref.p_s), (got.pixel[:n], ref.pixel[:n]),
-                     (got.g.mean_opa[:n], ref.g.mean_opa[:n]), (got.g.scale[:n], ref.g.scale[:n]),
-                     (got.g.quat[:n], ref.g.quat[:n]), (got.g.sh[:n], ref.g.sh[:n])):
-            a, b = a.cpu().numpy(), b.cpu().numpy()
-            assert np.allclose(a, b, rtol=1e-5, atol=1e-7)
+def _check(W, H, seed, call, ws_cache):
+    """One call of each entry point on the same frame: identical outputs, bit for bit
+    (both run the same kernels; only the scratch memory differs)."""
+    cam = gs.cameras_tensor([synth.camera(np.eye(3), np.zeros(3), 0.8 * W, W, H)])
+    if (W, H) not in ws_cache:
+        ws_cache[(W, H)] = gs.workspace(gs.gs_spawn_workspace_size(W, H))
+    im, rd, depth = _frame(seed, W, H)
+    ref = gs.Spawned.alloc(W * H, W * H)
+    got = gs.Spawned.alloc(W * H, W * H)
+    gs.gs_spawn_propose(im, rd, depth, W, H, cam, 1.0, 77, call, ref, ws_cache[(W, H)])
+    assert gs.gs_spawn_propose_noalloc(im, rd, depth, W, H, cam, 1.0, 77, call, got) == gs.GS_OK
+    torch.cuda.synchronize()
+    assert int(got.status.item()) == gs.GS_OK
+    n = int(ref.count.item())
+    assert n > 100 and int(got.count.item()) == n
+    for a, b in ((got.p_l, ref.p_l), (got.p_pen, ref.p_pen), (got.p_s, ref.p_s), (got.pixel[:n], ref.pixel[:n]),
+                 (got.g.mean_opa[:n], ref.g.mean_opa[:n]), (got.g.scale[:n], ref.g.scale[:n]),
+                 (got.g.quat[:n], ref.g.quat[:n]), (got.g.sh[:n], ref.g.sh[:n])):
+        assert np.array_equal(a.cpu().numpy(), b.cpu().numpy())
+    return im, rd, got
+
+
+def test_noalloc_matches_workspace_entry_point_call_after_call():
+    """Calls in a row share the library's scratch array, which keeps the previous
+    call's contents: two frames of one size, then a smaller frame (the words past
+    its pixel count still hold the larger frame's data and must not be read),
+    then the larger size again."""
+    ws = {}
+    for call, (W, H, seed) in enumerate(((640, 360, 11), (640, 360, 12), (320, 200, 13), (640, 360, 14))):
+        _check(W, H, seed, call, ws)
+
+
+def test_noalloc_maps_match_the_oracle():
+    """The allocation-free call's probability maps against the FP64 oracle's
+    (Sec. 4.2, Eq. 1-3), at the spawn tests' 1e-5, on a frame that follows a
+    larger one."""
+    from helpers import assert_close
+    from oracle import build as ob
+    from oracle import oracle as O
+    ob.build()
+    ws = {}
+    _check(640, 360, 21, 0, ws)
+    W, H = 200, 120
+    im, rd, got = _check(W, H, 22, 1, ws)
+    ref = O.spawn_maps(im.cpu().numpy().reshape(3, H, W).astype(np.float64),
+                       rd.cpu().numpy().reshape(3, H, W).astype(np.float64), 1.0, 77, 1)
+    assert_close(got.p_l.cpu().numpy().reshape(H, W), ref["p_l"], 1e-5, what="P_L")
+    assert_close(got.p_pen.cpu().numpy().reshape(H, W), ref["p_pen"], 1e-5, what="P~")
+    assert_close(got.p_s.cpu().numpy().reshape(H, W), ref["p_s"], 1e-5, what="P_s")
 
 
 def test_noalloc_rejects_frames_over_its_limit():
