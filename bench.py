@@ -43,10 +43,43 @@ N_VIEWS = 8
 WIDTH, HEIGHT = 1920, 1080
 SEED = 1002
 
-# Algorithmic work per (pixel, Gaussian) evaluation, counted from the
-# definitions of the compositing forward and its adjoint (FMA = 2 flops).
-FWD_FLOPS_PER_EVAL = 22
+# Algorithmic work per compositing evaluation - one (pixel, Gaussian) pair
+# where the Gaussian reaches alpha_min before the pixel terminates - counted
+# operation by operation from the definitions (3DGS image formation, Sec. 4.3);
+# add, sub, mul = 1 flop, FMA = 2, compares and min/max not counted, shared
+# subexpressions once.
+# Forward (front to back):
+#   d = pixel - mean2d                                  2
+#   exponent -(a dx^2 + c dy^2)/2 - b dx dy: dx^2, dy^2, dx dy (3 mul),
+#     a' dx^2 (1), + c' dy^2 (FMA 2), + b' dx dy (FMA 2)   8
+#   g = exp(exponent)                                   MUFU ex2
+#   o g                                                 1
+#   T (1 - alpha)                                       2
+#   w = alpha T; C += w rgb (3 FMA)                     7
+#   total                                              20 flops, 1 MUFU
+FWD_FLOPS_PER_EVAL = 20
+FWD_MUFU_PER_EVAL = 1
+# Adjoint (back to front, per composited Gaussian):
+#   d, exponent, g, o g as forward                      11, 1 MUFU ex2
+#   r = 1 / (1 - alpha): sub + reciprocal               1, 1 MUFU rcp
+#   T_i = T_{i+1} r; w = alpha T_i                      2
+#   dL/drgb = w gC (3)                                  3
+#   dL/dalpha = sum_ch gC (T c - (A + T_N bg) r): per channel add, mul, mul,
+#     sub, FMA                                         18
+#   A += w c (3 FMA)                                    6
+#   dL/dexponent = dL/dalpha o g; dL/do = dL/dalpha g   2
+#   dL/dmean2d: (a dx + b dy), (b dx + c dy) (mul + FMA each) x dL/dexp  8
+#   dL/dconic: dx^2, dx dy, dy^2 (reused) x dL/dexp      3
+#   sum of the 9 terms over the tile's pixels            9
+#   total                                              63 flops, 2 MUFU
 BWD_FLOPS_PER_EVAL = 63
+BWD_MUFU_PER_EVAL = 2
+# Projection: EWA (world->camera, covariance from scale and rotation, J W S
+# W^T J^T, inverse, radius, rect) about 100 flops, SH degree 3 (16 basis
+# terms x 3 channels FMA + basis) about 150: 250 per visible item; its
+# adjoint about twice that.
+PROJECT_FLOPS_PER_ITEM = 250
+PROJECT_BWD_FLOPS_PER_ITEM = 500
 SMS = 152
 FP32_LANES = 128
 
@@ -539,6 +572,30 @@ def measure_ba(torch, gs, device, iterations=200):
 # ---------------------------------------------------------------------------
 # oracle on the host cores
 # ---------------------------------------------------------------------------
+def measure_peaks(torch, gs, device, sms, reps=5):
+    """FP32 FMA and MUFU throughput measured by the library's probes (one
+    CTA of 256 threads per 1/8 of an SM's threads, i.e. 8 per SM, long enough
+    to time with CUDA events): best of reps, in TFLOP/s and T MUFU ops/s."""
+    blocks = 8 * sms
+    out = torch.empty(blocks * 256, dtype=torch.float32, device=device)
+    res = {}
+    for name, fn, per_iter, iters in (("fp32_tflops", gs.gs_probe_fma, 2 * 128, 2048),
+                                      ("mufu_tops", gs.gs_probe_mufu, 64, 512)):
+        fn(out, blocks, 16)  # warm-up
+        best = None
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn(out, blocks, iters)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            best = ms if best is None else min(best, ms)
+        res[name] = blocks * 256 * per_iter * iters / (best / 1000.0) / 1e12
+        res[name.split("_")[0] + "_ms"] = best
+    return res
+
+
 def oracle_sample(n_views_sample=1, n=N_GAUSS):
     """Times the FP64 oracle's fwd+bwd (incl. pose) on n_views_sample of the
     workload's 1080p views over the full scene. Returns (iters/s, seconds, cores)."""
@@ -736,7 +793,14 @@ def main():
     K = int(J.r.img.n_contrib.to(torch.int64).sum().item())
     loss = float(J.loss.item())
 
-    # ---------------- roofline of the dominant kernel ----------------
+    # ---------------- counted work (untimed) and measured peaks ----------------
+    counts = torch.zeros(3, dtype=torch.int64, device=device)
+    gs.gs_render_fwd_count(J.r.proj, J.r.pairs, J.r.f, J.r.cfg, J.r.img, counts, J.r.ws_render)
+    torch.cuda.synchronize()
+    warp_hits, lane_evals, K_c = (int(x) for x in counts.cpu().tolist())
+    HW = sum(w * h for w, h in W["sizes"])
+    n_tiles = int(J.r.f.tile_base[len(W["sizes"])])
+    probe = measure_peaks(torch, gs, device, SMS)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -744,34 +808,63 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     sm_clock = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak_tflops = SMS * FP32_LANES * 2 * sm_clock * 1e6 / 1e12
-    algo = {
-        "render_fwd": ("alu", FWD_FLOPS_PER_EVAL * K / 1e12, "TFLOP/s"),
-        "composite_bwd": ("alu", BWD_FLOPS_PER_EVAL * K / 1e12, "TFLOP/s"),
-        # attributes read once per Gaussian (the views of one block share them in L2), 52 B written per
-        # visible item and 12 B (tile count, rect) per culled one
-        "project": ("hbm", (16 * args.n + 224 * n_seen + 52 * n_items_vis
-                            + 12 * (args.n * args.views - n_items_vis)) / 1e9, "GB/s"),
-        "project_bwd": ("hbm", ((240 + 240) * args.n + (36 + 12) * n_items_vis + 36 * P) / 1e9, "GB/s"),
-        "adam": ("hbm", 7 * 240 * args.n / 1e9, "GB/s"),
+    fp32_peak_tflops = probe["fp32_tflops"]
+    mufu_peak_tops = probe["mufu_tops"]
+    fp32_derived = SMS * FP32_LANES * 2 * sm_clock * 1e6 / 1e12
+    # algorithmic work per stage: (bytes, flops, MUFU ops); bytes are what the
+    # method must move (each input read once, each output written once)
+    Vs, Vi, N, P = n_seen, n_items_vis, args.n, P
+    work = {
+        # cull read of every Gaussian, attributes of the Gaussians kept in any view read once,
+        # 52 B per visible item and 12 B per culled one written
+        "project": (16 * N + 224 * Vs + 52 * Vi + 12 * (N * args.views - Vi), PROJECT_FLOPS_PER_ITEM * Vi, 0),
+        # visible depth keys + ids sorted, pair keys and ids written once, pairs sorted once, tile ranges
+        "sort": (32 * Vi + 12 * P + 24 * P + 8 * P + 8 * n_tiles, 0, 0),
+        # pair rows read once (id + mean2d + conic/opacity + rgb), colour + T + n_contrib written
+        "render_fwd": (40 * P + 20 * HW, FWD_FLOPS_PER_EVAL * K_c, FWD_MUFU_PER_EVAL * K_c),
+        # colour and target read, dL/dC written
+        "loss": (36 * HW, 3 * HW, 0),
+        # dL/dC, T, n_contrib read, pair rows read, one 9-float partial per pair written
+        "composite_bwd": (20 * HW + 40 * P + 36 * P, BWD_FLOPS_PER_EVAL * K_c, BWD_MUFU_PER_EVAL * K_c),
+        # parameters read, gradients written, item state and pair partials read
+        "project_bwd": (480 * Vs + 48 * Vi + 36 * P, PROJECT_BWD_FLOPS_PER_ITEM * Vi, 0),
+        # parameter, gradient, m, v read; parameter, m, v written, for the visible Gaussians; visibility flags
+        "adam": (7 * 240 * Vs + N, 15 * 60 * Vs, 0),
+        "pose": (0, 0, 0),
     }
     stages = {}
-    for s, msv in stage_ms.items():
-        e = {"ms": msv}
-        if s in algo:
-            bound, work, unit = algo[s]
-            ach = work / (msv / 1000.0)
-            peak = fp32_peak_tflops if bound == "alu" else hbm_peak
-            e.update({"bound": bound, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak})
-        stages[s] = e
-    dom = max(stage_ms, key=lambda s: stage_ms[s])
-    roof = {"kernel": dom, "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None}
-    if dom in algo:
-        d = stages[dom]
-        roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
-                "frac": d["frac"], "traffic": profiled_traffic(dom, args.views),
-                "peak_source": ("FP32 lanes: 152 SMs x 128 x 2 flop x median SM clock sampled under load"
-                                if d["bound"] == "alu" else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
+    floor_ms = 0.0
+    for st, msv in stage_ms.items():
+        by, fl, mu = work.get(st, (0, 0, 0))
+        t_bytes = by / (hbm_peak * 1e9) * 1e3
+        t_flops = fl / (fp32_peak_tflops * 1e12) * 1e3
+        t_mufu = mu / (mufu_peak_tops * 1e12) * 1e3
+        t_floor = max(t_bytes, t_flops, t_mufu)
+        bound = ["hbm", "alu", "mufu"][int(np.argmax([t_bytes, t_flops, t_mufu]))]
+        floor_ms += t_floor
+        e = {"ms": msv, "floor_ms": t_floor, "bound": bound, "frac": t_floor / msv if msv > 0 else None,
+             "bytes": by, "flops": fl, "mufu": mu}
+        if bound == "hbm":
+            e.update(achieved=by / (msv / 1e3) / 1e9, peak=hbm_peak, unit="GB/s")
+        else:
+            e.update(achieved=fl / (msv / 1e3) / 1e12, peak=fp32_peak_tflops, unit="TFLOP/s")
+        stages[st] = e
+    step_ms = ms / args.steps
+    dom = max(stage_ms, key=lambda st: stage_ms[st])
+    d = stages[dom]
+    roof = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
+            "frac": d["achieved"] / d["peak"], "traffic": profiled_traffic(dom, args.views),
+            "peak_source": ("FP32 FMA throughput measured by the library's probe (gs_probe_fma) in this run "
+                            f"({fp32_peak_tflops:.1f} TFLOP/s; 152 SMs x 128 lanes x 2 x {sm_clock:.0f} MHz = "
+                            f"{fp32_derived:.1f})" if d["bound"] == "alu"
+                            else "MEASURED_PEAKS.json hbm_gbs (of measured)"),
+            "work": "flops per compositing evaluation (63 adjoint, 20 forward; derivation in bench.py) x the "
+                    "evaluations that composite, counted by an untimed instantiation of the forward kernel",
+            "evaluations": {"composited": K_c, "live_lane_evaluations": lane_evals, "warp_hits": warp_hits,
+                            "lane_slots": 32 * warp_hits, "list_entries_to_termination": K},
+            "step_frac": floor_ms / step_ms, "step_floor_ms": floor_ms,
+            "peaks": {"hbm_gbs": hbm_peak, "fp32_tflops": fp32_peak_tflops, "mufu_tops": mufu_peak_tops,
+                      "fp32_tflops_derived": fp32_derived}}
     del J
 
     # ---------------- plain arm: per-view launches ----------------
@@ -874,21 +967,30 @@ def main():
                          f"{args.n}-Gaussian scene, FP64"}
 
     if rank == 0:
+        # the full record (stages, side rows, autotune trials) goes to stderr; stdout carries one compact line
+        detail = {"stages": stages, "rows": rows, "launch": tuned, "uneven": uneven, "plain": plain,
+                  "work": {"visible_items": n_items_vis, "pairs": P, "evaluations_composited": K_c,
+                           "list_entries": K, "loss": loss, "status": status}}
+        log("detail " + json.dumps(detail))
+        r3 = lambda x: None if x is None else float(f"{x:.4g}")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(args.n, args.views),
                        "arm": "batched: all views per launch, CUDA graph per stage",
-                       "launch": tuned if tuned else "defaults", "parallelism": "replicas" if world > 1 else "single",
+                       "launch": ({k: tuned[k] for k in ("tile", "fwd_batch", "bwd_batch", "schedule")}
+                                  if tuned else "defaults"),
+                       "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (parameters + Adam state 0.7 GB, projected buffers "
                              f"{args.views * args.n * 52 / 1e9:.2f} GB)"},
-            "plain": plain,
-            "uneven": uneven,
-            "rows": rows,
+            "plain": None if plain is None else {"value": r3(plain["value"]), "ms_per_step": r3(plain["ms_per_step"])},
+            "uneven": None if uneven is None else {
+                "unit": uneven["unit"], "batched": r3(uneven["batched"]["value"]),
+                "plain": r3(uneven["plain"]["value"]), "schedule": uneven["batched"]["config"]["schedule"]},
+            "stage_ms": {k: r3(v["ms"]) for k, v in stages.items()},
+            "stage_frac": {k: r3(v["frac"]) for k, v in stages.items()},
             "roofline": roof,
-            "stages": stages,
-            "work": {"visible_items": n_items_vis, "pairs": P, "evaluations": K, "loss": loss, "status": status},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches_per_step * args.steps),

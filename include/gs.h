@@ -207,6 +207,25 @@ size_t gs_render_workspace_size(const gs_frame* f);
 int gs_render_fwd(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
                   const gs_image* out, void* ws, size_t ws_bytes, void* stream);
 
+/* Measurement (not a step of the method): gs_render_fwd with the same
+ * arguments and outputs, run by a counting instantiation of its kernel that
+ * also writes counts [3] (device, uint64, overwritten): [0] the warp hits its
+ * box test passes (each runs the compositing step on 32 lanes), [1] the lane
+ * evaluations of pixels not yet terminated at those hits, [2] the evaluations
+ * that composite (alpha >= alpha_min, before termination) - the (pixel,
+ * Gaussian) work the compositing definition requires (Sec. 4.3; the 3DGS
+ * image-formation model). Slower than gs_render_fwd: never timed. */
+int gs_render_fwd_count(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
+                        const gs_image* out, void* ws, size_t ws_bytes, unsigned long long* counts, void* stream);
+
+/* Measurement (not a step of the method): throughput probes of the FP32 FMA
+ * and MUFU pipes, timed by the caller. `blocks` CTAs of 256 threads; each
+ * thread performs 128 * iters fused multiply-adds (gs_probe_fma; 2 flops each)
+ * or 64 * iters MUFU operations, half 2^x and half 1/x (gs_probe_mufu), and
+ * writes one float to out [blocks * 256] (device). */
+int gs_probe_fma(float* out, int32_t blocks, int32_t iters, void* stream);
+int gs_probe_mufu(float* out, int32_t blocks, int32_t iters, void* stream);
+
 /* Gradients w.r.t. the Gaussian parameters, same layout as gs_gaussians.
  * visible [n] = 1 if the Gaussian has at least one pair in any view. */
 typedef struct gs_grads {

@@ -7,6 +7,8 @@ the Gaussian's tile rect, then composites front to back exactly as the 3DGS
 image-formation model does (alpha = min(alpha_max, o exp(power)), skip below
 alpha_min, stop before T drops under t_min). It never builds per-tile lists,
 so agreement with the tiled oracle checks the list building and ordering.
+Returns colour, final transmittance and the number of composited Gaussians
+per pixel.
 """
 from __future__ import annotations
 
@@ -22,6 +24,7 @@ def render(proj: dict, width: int, height: int, tile: int, alpha_min=1 / 255, al
     order = sorted(range(n), key=lambda i: (int(keys[i]), i))
     color = np.zeros((3, height, width))
     t_final = np.ones((height, width))
+    n_comp = np.zeros((height, width), np.int32)
     for y in range(height):
         for x in range(width):
             tx, ty = x // tile, y // tile
@@ -46,7 +49,8 @@ def render(proj: dict, width: int, height: int, tile: int, alpha_min=1 / 255, al
                 for ch in range(3):
                     C[ch] += alpha * T * proj["rgb"][i][ch]
                 T = nT
+                n_comp[y, x] += 1
             for ch in range(3):
                 color[ch, y, x] = C[ch] + T * bg[ch]
             t_final[y, x] = T
-    return color, t_final
+    return color, t_final, n_comp

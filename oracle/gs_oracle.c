@@ -523,7 +523,7 @@ static int composite_pixel(const Cfg* g, double px, double py, const int32_t* id
 void or_render_fwd(const double* cam, const double* cfg, const int64_t* tile_start, const int32_t* ids,
                    const double* mean2d, const double* conic, const double* opac, const double* rgb,
                    const double* depth, double* color, double* t_final, int32_t* n_contrib, uint8_t* amb_px,
-                   uint8_t* amb_g) {
+                   uint8_t* amb_g, int32_t* n_comp) {
     Cam k = read_cam(cam);
     Cfg g = read_cfg(cfg);
     int T = g.tile, tx = (k.W + T - 1) / T;
@@ -535,8 +535,10 @@ void or_render_fwd(const double* cam, const double* cfg, const int64_t* tile_sta
         double col[3], Tf;
         int32_t nc;
         uint8_t a = 0;
-        composite_pixel(&g, x + 0.5, y + 0.5, ids + tile_start[t], tile_start[t + 1] - tile_start[t], mean2d,
-                        conic, opac, rgb, depth, col, &Tf, &nc, &a, NULL, amb_g, NULL, NULL, 0, NULL);
+        int nr = composite_pixel(&g, x + 0.5, y + 0.5, ids + tile_start[t], tile_start[t + 1] - tile_start[t],
+                                 mean2d, conic, opac, rgb, depth, col, &Tf, &nc, &a, NULL, amb_g, NULL, NULL, 0,
+                                 NULL);
+        if (n_comp) n_comp[pix] = nr;
         for (int ch = 0; ch < 3; ch++) color[ch * HW + pix] = col[ch];
         t_final[pix] = Tf;
         n_contrib[pix] = nc;

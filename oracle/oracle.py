@@ -41,7 +41,7 @@ def lib():
         _lib.or_render_fwd.restype = None
         dn = np.ctypeslib.ndpointer(np.float64, flags="C")
         opt = C.c_void_p  # optional double array
-        _lib.or_render_fwd.argtypes = [d, d, i64, i32, d, d, d, d, opt, d, d, i32, u8, u8]
+        _lib.or_render_fwd.argtypes = [d, d, i64, i32, d, d, d, d, opt, d, d, i32, u8, u8, i32]
         _lib.or_render_bwd.restype = None
         _lib.or_render_bwd.argtypes = [d, d, i64, i32, d, d, d, d, opt, d, C.c_int64, d, opt, opt]
         _lib.or_project_bwd.restype = None
@@ -150,12 +150,14 @@ def render_fwd(proj, start, ids, cam, cfg: Config) -> dict:
     H, W = cam["height"], cam["width"]
     n = proj["mean2d"].shape[0]
     out = dict(color=np.zeros((3, H, W)), t_final=np.zeros((H, W)), n_contrib=np.zeros((H, W), np.int32),
-               amb=np.zeros((H, W), np.uint8), amb_gauss=np.zeros(max(n, 1), np.uint8))
+               amb=np.zeros((H, W), np.uint8), amb_gauss=np.zeros(max(n, 1), np.uint8),
+               n_composited=np.zeros((H, W), np.int32))
     z, zp = _depth_arg(proj)
     lib().or_render_fwd(cam_array(cam), cfg.array(), _c(start, np.int64), _c(ids, np.int32),
                         _c(proj["mean2d"], np.float64), _c(proj["conic"], np.float64),
                         _c(proj["opacity"], np.float64), _c(proj["rgb"], np.float64), zp,
-                        out["color"], out["t_final"], out["n_contrib"], out["amb"], out["amb_gauss"])
+                        out["color"], out["t_final"], out["n_contrib"], out["amb"], out["amb_gauss"],
+                        out["n_composited"])
     out["amb_gauss"] = out["amb_gauss"][:n]
     return out
 

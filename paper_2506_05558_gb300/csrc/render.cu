@@ -124,7 +124,12 @@ __device__ __forceinline__ int next_tile(const uint32_t* __restrict__ order, uin
 }
 
 // DEPTH: also accumulate the depth integral sum_i alpha_i T_i z_i per pixel.
-template <int TILE, int FB, bool DEPTH>
+// COUNT (measurement only, never the timed instantiation): also count, into
+// counts[0..2], the warp hits the ballot passes (each one runs the compositing
+// step on all 32 lanes), the lane evaluations of pixels not yet terminated at
+// those hits, and the evaluations that composite (alpha >= alpha_min, before
+// termination) - the work the definition requires.
+template <int TILE, int FB, bool DEPTH, bool COUNT = false>
 __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_config cfg,
                                                             const uint32_t* __restrict__ range,
                                                             const uint32_t* __restrict__ src,
@@ -135,8 +140,9 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                                                             int32_t* __restrict__ n_contrib,
                                                             float* __restrict__ depth_out,
                                                             const uint32_t* __restrict__ order, uint32_t* counter,
-                                                            int n_tiles) {
+                                                            int n_tiles, unsigned long long* counts) {
     constexpr int NT = Geom<TILE>::kThreads;
+    unsigned long long n_hit = 0, n_eval = 0, n_comp = 0;
     __shared__ float2 s_xy[FB];
     __shared__ float4 s_abco[FB];
     __shared__ float4 s_rgb[FB];
@@ -175,6 +181,11 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                     const float nT = __fmul_rn(T, 1.f - alpha);
                     const bool term = ok && nT < cfg.t_min;
                     const bool acc = ok && !term;
+                    if (COUNT) {
+                        n_hit += 1;
+                        n_eval += !done;
+                        n_comp += acc;
+                    }
                     done = done || term;
                     const float w = acc ? alpha * T : 0.f;
                     cr += w * c.x; cg += w * c.y; cb += w * c.z;
@@ -207,6 +218,17 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
             if (DEPTH) depth_out[ti.pix] = cz;
         }
         __syncthreads();  // shared buffers are reused by the next tile
+    }
+    if (COUNT) {
+        for (int o = 16; o > 0; o >>= 1) {
+            n_eval += __shfl_xor_sync(FULL, n_eval, o);
+            n_comp += __shfl_xor_sync(FULL, n_comp, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&counts[0], n_hit);  // every lane counted the warp's hits; lane 0 reports them once
+            atomicAdd(&counts[1], n_eval);
+            atomicAdd(&counts[2], n_comp);
+        }
     }
 }
 
@@ -431,10 +453,13 @@ struct RenderLaunch {
     int threads;
 };
 
-static RenderLaunch pick_fwd(int tile, int batch, bool depth = false) {
+static RenderLaunch pick_fwd(int tile, int batch, bool depth = false, bool count = false) {
 #define GS_FWD(T, B)                                                                     \
     if (tile == T && batch == B)                                                         \
-        return {depth ? (const void*)k_render_fwd<T, B, true> : (const void*)k_render_fwd<T, B, false>, T * T};
+        return {count   ? (const void*)k_render_fwd<T, B, false, true>                   \
+                : depth ? (const void*)k_render_fwd<T, B, true>                          \
+                        : (const void*)k_render_fwd<T, B, false>,                        \
+                T * T};
     GS_FWD(8, 64) GS_FWD(8, 128) GS_FWD(8, 256)
     GS_FWD(16, 64) GS_FWD(16, 128) GS_FWD(16, 256)
     GS_FWD(32, 128) GS_FWD(32, 256)
@@ -487,20 +512,24 @@ static bool render_args_ok(const gs_frame* f, const gs_config* cfg) {
            render_batch_supported(cfg->tile, cfg->fwd_batch, cfg->bwd_batch);
 }
 
-extern "C" int gs_render_fwd(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
-                             const gs_image* out, void* ws, size_t ws_bytes, void* stream) {
+static int render_fwd_impl(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
+                           const gs_image* out, void* ws, size_t ws_bytes, void* stream, unsigned long long* counts) {
     if (!p || !pairs || !out || !out->color || !out->t_final || !out->n_contrib || !render_args_ok(f, cfg))
         return GS_ERR_INVALID_ARG;
     const bool persistent = cfg->schedule == 1;
     if (persistent && (!pairs->order || !ws || ws_bytes < 256)) return GS_ERR_INVALID_ARG;
     int n_tiles = f->tile_base[f->n_views];
-    if (n_tiles == 0) return GS_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    if (counts && cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return GS_ERR_CUDA;
+    }
+    if (n_tiles == 0) return GS_OK;
     uint32_t* counter = persistent ? (uint32_t*)ws : nullptr;
     const uint32_t* order = persistent ? pairs->order : nullptr;
     if (persistent) cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
-    const RenderLaunch L =
-        pick_fwd(cfg->tile, cfg->fwd_batch ? cfg->fwd_batch : default_fwd_batch(cfg->tile), out->depth != nullptr);
+    const RenderLaunch L = pick_fwd(cfg->tile, cfg->fwd_batch ? cfg->fwd_batch : default_fwd_batch(cfg->tile),
+                                    out->depth != nullptr && !counts, counts != nullptr);
     gs_frame fv = *f;
     gs_config cv = *cfg;
     const uint32_t* range = pairs->range;
@@ -513,8 +542,21 @@ extern "C" int gs_render_fwd(const gs_projected* p, const gs_pairs* pairs, const
     int32_t* nc = out->n_contrib;
     float* dz = out->depth;
     void* args[] = {&fv, &cv, (void*)&range, (void*)&src, (void*)&m2, (void*)&co, (void*)&rd,
-                    (void*)&color, (void*)&tf, (void*)&nc, (void*)&dz, (void*)&order, (void*)&counter, &n_tiles};
+                    (void*)&color, (void*)&tf, (void*)&nc, (void*)&dz, (void*)&order, (void*)&counter, &n_tiles,
+                    (void*)&counts};
     return launch(L, n_tiles, persistent, args, s);
+}
+
+extern "C" int gs_render_fwd(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f, const gs_config* cfg,
+                             const gs_image* out, void* ws, size_t ws_bytes, void* stream) {
+    return render_fwd_impl(p, pairs, f, cfg, out, ws, ws_bytes, stream, nullptr);
+}
+
+extern "C" int gs_render_fwd_count(const gs_projected* p, const gs_pairs* pairs, const gs_frame* f,
+                                   const gs_config* cfg, const gs_image* out, void* ws, size_t ws_bytes,
+                                   unsigned long long* counts, void* stream) {
+    if (!counts) return GS_ERR_INVALID_ARG;
+    return render_fwd_impl(p, pairs, f, cfg, out, ws, ws_bytes, stream, counts);
 }
 
 namespace gs {

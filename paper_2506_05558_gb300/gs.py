@@ -27,7 +27,8 @@ GS_MAX_VIEWS = 64
 # Every entry point declared in include/gs.h.
 EXPORTS = [
     "gs_config_default", "gs_frame_init", "gs_project", "gs_sort_workspace_size", "gs_sort",
-    "gs_render_workspace_size", "gs_render_fwd", "gs_backward_workspace_size", "gs_render_bwd",
+    "gs_render_workspace_size", "gs_render_fwd", "gs_render_fwd_count", "gs_probe_fma", "gs_probe_mufu",
+    "gs_backward_workspace_size", "gs_render_bwd",
     "gs_adam_step", "gs_pose_step", "gs_l1_loss", "gs_composite_bwd", "gs_project_bwd", "gs_launch_count",
     "gs_spawn_workspace_size", "gs_spawn_propose", "gs_counter_add", "gs_spawn_propose_noalloc",
     "gs_anchor_check", "gs_anchor_offload", "gs_anchor_load",
@@ -131,6 +132,10 @@ def lib():
             "gs_render_workspace_size": (C.c_size_t, [C.POINTER(gs_frame)]),
             "gs_render_fwd": (C.c_int, [C.POINTER(gs_projected), C.POINTER(gs_pairs), C.POINTER(gs_frame),
                                         C.POINTER(gs_config), C.POINTER(gs_image), P, C.c_size_t, P]),
+            "gs_render_fwd_count": (C.c_int, [C.POINTER(gs_projected), C.POINTER(gs_pairs), C.POINTER(gs_frame),
+                                              C.POINTER(gs_config), C.POINTER(gs_image), P, C.c_size_t, P, P]),
+            "gs_probe_fma": (C.c_int, [P, C.c_int32, C.c_int32, P]),
+            "gs_probe_mufu": (C.c_int, [P, C.c_int32, C.c_int32, P]),
             "gs_backward_workspace_size": (C.c_size_t, [C.c_int64, C.POINTER(gs_frame), C.c_int64]),
             "gs_render_bwd": (C.c_int, [C.POINTER(gs_gaussians), P, C.POINTER(gs_projected), C.POINTER(gs_pairs),
                                         C.POINTER(gs_frame), C.POINTER(gs_config), C.POINTER(gs_image), P,
@@ -403,6 +408,30 @@ def gs_render_fwd(p: Projected, pairs: Pairs, f: gs_frame, cfg: gs_config, out: 
     pc, qc, oc = p.c(), pairs.c(), out.c()
     _check(lib().gs_render_fwd(C.byref(pc), C.byref(qc), C.byref(f), C.byref(cfg), C.byref(oc), _ptr(ws),
                                0 if ws is None else ws.numel(), _stream(stream)), "gs_render_fwd")
+
+
+def gs_render_fwd_count(p: Projected, pairs: Pairs, f: gs_frame, cfg: gs_config, out: Image, counts: torch.Tensor,
+                        ws=None, stream=None):
+    """Measurement: the forward with its evaluations counted into counts
+    (int64 [3] on the device): warp hits, lane evaluations of live pixels,
+    compositing evaluations."""
+    assert counts.dtype == torch.int64 and counts.numel() >= 3
+    pc, qc, oc = p.c(), pairs.c(), out.c()
+    _check(lib().gs_render_fwd_count(C.byref(pc), C.byref(qc), C.byref(f), C.byref(cfg), C.byref(oc), _ptr(ws),
+                                     0 if ws is None else ws.numel(), _ptr(counts), _stream(stream)),
+           "gs_render_fwd_count")
+
+
+def gs_probe_fma(out: torch.Tensor, blocks: int, iters: int, stream=None):
+    """Measurement: blocks x 256 threads x 128 iters FMAs; out float32 [blocks * 256]."""
+    assert out.dtype == torch.float32 and out.numel() >= blocks * 256
+    _check(lib().gs_probe_fma(_ptr(out), blocks, iters, _stream(stream)), "gs_probe_fma")
+
+
+def gs_probe_mufu(out: torch.Tensor, blocks: int, iters: int, stream=None):
+    """Measurement: blocks x 256 threads x 64 iters MUFU operations (2^x, 1/x)."""
+    assert out.dtype == torch.float32 and out.numel() >= blocks * 256
+    _check(lib().gs_probe_mufu(_ptr(out), blocks, iters, _stream(stream)), "gs_probe_mufu")
 
 
 def gs_backward_workspace_size(n: int, f: gs_frame, capacity: int) -> int:

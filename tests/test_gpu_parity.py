@@ -651,3 +651,33 @@ def test_downsample_matches_oracle():
         torch.cuda.synchronize()
         ref = O.downsample(im, f)
         assert_close(out.cpu().numpy().reshape(ref.shape), ref, 1e-6, what=f"downsample {W}x{H}/{f}")
+
+
+def test_counting_forward_gives_the_same_image_and_consistent_counts():
+    """The measurement instantiation of the forward (gs_render_fwd_count) writes
+    the same image, transmittance and n_contrib as gs_render_fwd, bit for bit,
+    and its counts are ordered: composited <= live-lane evaluations <= 32 x warp
+    hits, and composited equals the oracle's count of compositing evaluations
+    away from flagged pixels within a small tolerance."""
+    sc, cams, _ = synth.multiview_scene(seed=41, n=6000, n_views=2, sizes=[(160, 96), (96, 128)])
+    sizes = [(c["width"], c["height"]) for c in cams]
+    g = gs.Gaussians.from_scene(sc)
+    camt = gs.cameras_tensor(cams)
+    r = Rasterizer(sc.n, sizes, capacity=1024, cfg=gs.config(sh_degree=3))
+    r.fit_capacity(g, camt)
+    r.forward(g, camt)
+    ref = [t.clone() for t in (r.img.color, r.img.t_final, r.img.n_contrib)]
+    counts = torch.zeros(3, dtype=torch.int64, device="cuda")
+    gs.gs_render_fwd_count(r.proj, r.pairs, r.f, r.cfg, r.img, counts, r.ws_render)
+    torch.cuda.synchronize()
+    for a, b in zip(ref, (r.img.color, r.img.t_final, r.img.n_contrib)):
+        assert torch.equal(a, b)
+    hits, lanes, comp = counts.cpu().tolist()
+    assert 0 < comp <= lanes <= 32 * hits
+    # the oracle's number of compositing evaluations (alpha >= alpha_min, before termination)
+    ocfg = O.Config(sh_degree=3, **MARGINS)
+    total = 0
+    for cam in cams:
+        view = O.render_view(sc, cam, ocfg)
+        total += int(view["n_composited"].sum())
+    assert abs(comp - total) <= 1e-3 * total, (comp, total)

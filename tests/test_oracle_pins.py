@@ -247,7 +247,9 @@ def test_transmittance_bounds_and_colour_bound():
 
 
 def test_brute_force_twin():
-    """Tiled oracle == per-pixel global-order brute force to 1e-12 on tiny scenes."""
+    """Tiled oracle == per-pixel global-order brute force to 1e-12 on tiny scenes,
+    and the same number of composited Gaussians per pixel (the count the
+    benchmark's roofline uses)."""
     for seed in (1, 2, 3):
         sc, cam, _ = synth.tiny_scene(seed=seed, n=50, width=48, height=40, f=60.0)
         # larger Gaussians so that lists overlap across tiles
@@ -255,9 +257,10 @@ def test_brute_force_twin():
         cfg = O.Config(sh_degree=0)
         v = O.render_view(sc, cam, cfg)
         assert len(v["ids"]) > 60
-        col, T = brute.render(v["proj"], cam["width"], cam["height"], cfg.tile)
+        col, T, nc = brute.render(v["proj"], cam["width"], cam["height"], cfg.tile)
         np.testing.assert_allclose(v["color"], col, atol=1e-12)
         np.testing.assert_allclose(v["t_final"], T, atol=1e-12)
+        assert np.array_equal(v["n_composited"], nc)
 
 
 def test_permutation_invariance():
