@@ -150,11 +150,14 @@ int gs_project(const gs_gaussians* g, const gs_camera* cams, const gs_frame* f, 
  *   src     [capacity]  sorted pair -> item index (view * n + g)
  *   emit    [capacity]  sorted pair -> emission slot; the pairs of one item
  *                       occupy slots offset[item] .. offset[item]+n_tiles-1
- *   offset  [n_views*n] first emission slot of each visible item
+ *   offset  [n_views*n] first emission slot of each item: the slots are
+ *           assigned in item order (an exclusive sum of n_tiles over items),
+ *           so the runs of consecutive items are adjacent
  *   range   [2 * total tiles]  [start, end) of each tile's pairs in src/emit
  *   count   device int64[1]: number of pairs (written by gs_sort)
  *   status  device int32[1]: GS_OK, or GS_ERR_CAPACITY if count > capacity (then
- *           only the first `capacity` pairs exist and renders are incomplete)
+ *           only the first `capacity` pairs, by depth, exist: renders are
+ *           incomplete and gs_project_bwd returns zero gradients)
  *   order   [total tiles] optional (NULL to skip): tile indices by decreasing
  *           pair count (stable), the work order of the persistent schedule */
 typedef struct gs_pairs {

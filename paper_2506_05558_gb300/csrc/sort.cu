@@ -23,6 +23,10 @@ struct LoadU32 {
     const uint32_t* p;
     __device__ uint32_t operator()(int64_t i) const { return p[i]; }
 };
+struct LoadTiles {
+    const int32_t* n_tiles;
+    __device__ uint32_t operator()(int64_t i) const { return n_tiles[i] > 0 ? (uint32_t)n_tiles[i] : 0u; }
+};
 struct LoadVisible {
     const int32_t* n_tiles;
     __device__ uint32_t operator()(int64_t i) const { return n_tiles[i] > 0 ? 1u : 0u; }
@@ -317,26 +321,29 @@ __global__ void k_pair_count(const uint32_t* total, int64_t capacity, int64_t* c
     *status = (int64_t)t > capacity ? GS_ERR_CAPACITY : GS_OK;
 }
 
-// One (tile, emission slot) pair per tile of each visible item's rect, the
-// items taken in depth order. A warp owns 32 consecutive sorted items, whose
-// pairs occupy consecutive slots, and writes them together: pair j of the
-// warp's run finds its item by a binary search over the lanes' prefix counts,
-// so consecutive lanes write consecutive slots whatever the rect sizes.
+// One (tile, item) pair per tile of each visible item's rect, the items taken
+// in depth order: pair positions follow depth order (what the stable tile sort
+// needs); each pair also records its item and its emission slot - in item
+// order: the item's first slot (offset) plus the pair's index in the item. A warp
+// owns 32 consecutive sorted items, whose pairs occupy consecutive positions,
+// and writes them together: pair j of the warp's run finds its item by a
+// binary search over the lanes' prefix counts, so consecutive lanes write
+// consecutive positions whatever the rect sizes.
 __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ sorted_item,
                                                    const uint32_t* __restrict__ emit_off, const uint32_t* n_vis,
                                                    const ushort4* __restrict__ rect, int64_t n, gs_frame f,
-                                                   int64_t capacity, uint32_t* __restrict__ offset,
-                                                   uint32_t* __restrict__ pkey, uint32_t* __restrict__ psrc) {
+                                                   int64_t capacity, const uint32_t* __restrict__ offset,
+                                                   uint32_t* __restrict__ pkey, uint2* __restrict__ psrc) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nv = *n_vis;
     if (s - lane >= nv) return;  // uniform over the warp
-    uint32_t item = 0, off = 0, x0 = 0, y0 = 0, wx = 1, cnt = 0, tb = 0, tx = 0;
+    uint32_t item = 0, off = 0, x0 = 0, y0 = 0, wx = 1, cnt = 0, tb = 0, tx = 0, slot0 = 0;
     if (s < nv) {
         item = sorted_item[s];
         off = emit_off[s];
-        offset[item] = off;
+        slot0 = offset[item];
         const int v = (int)(item / (uint64_t)n);
         const ushort4 r = rect[item];
         tb = (uint32_t)f.tile_base[v];
@@ -369,6 +376,7 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
         const uint32_t st = __shfl_sync(FULL, start, L);
         const uint32_t o = __shfl_sync(FULL, off, L);
         const uint32_t it = __shfl_sync(FULL, item, L);
+        const uint32_t sl = __shfl_sync(FULL, slot0, L);
         const uint32_t ax = __shfl_sync(FULL, x0, L), ay = __shfl_sync(FULL, y0, L);
         const uint32_t aw = __shfl_sync(FULL, wx, L), atb = __shfl_sync(FULL, tb, L), atx = __shfl_sync(FULL, tx, L);
         if (j < total) {
@@ -377,21 +385,23 @@ __global__ void __launch_bounds__(256) k_duplicate(const uint32_t* __restrict__ 
             const int64_t e = (int64_t)o + local;
             if (e < capacity) {
                 pkey[e] = atb + (ay + yy) * atx + ax + xx;
-                psrc[e] = it;
+                psrc[e] = make_uint2(it, sl + local);
             }
         }
     }
 }
 
+// Sorted pair p: its item, its emission slot (the item's first slot in item
+// order plus the pair's index within the item) and the tile ranges.
 __global__ void k_finish_pairs(const uint32_t* __restrict__ skey, const uint32_t* __restrict__ sval,
-                               const uint32_t* __restrict__ psrc, const uint32_t* n_eff, uint32_t* __restrict__ src,
+                               const uint2* __restrict__ psrc, const uint32_t* n_eff, uint32_t* __restrict__ src,
                                uint32_t* __restrict__ emit, uint32_t* __restrict__ range) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t cnt = *n_eff;
     if (p >= cnt) return;
-    const uint32_t e = sval[p];
-    emit[p] = e;
-    src[p] = psrc[e];
+    const uint2 q = psrc[sval[p]];  // (item, emission slot) of the pair at that position before the sort
+    src[p] = q.x;
+    emit[p] = q.y;
     const uint32_t t = skey[p];
     if (p == 0 || skey[p - 1] != t) range[2 * (int64_t)t] = (uint32_t)p;
     if (p == cnt - 1 || skey[p + 1] != t) range[2 * (int64_t)t + 1] = (uint32_t)(p + 1);
@@ -413,7 +423,8 @@ __global__ void k_copy_u32(const uint32_t* __restrict__ a, uint32_t* __restrict_
 }
 
 struct SortWs {
-    uint32_t *scan, *vis_pos, *vk0, *vv0, *vk1, *vv1, *emit_off, *pk0, *pv0, *pk1, *pv1, *psrc, *hist, *misc;
+    uint32_t *scan, *vis_pos, *vk0, *vv0, *vk1, *vv1, *emit_off, *pk0, *pv0, *pk1, *pv1, *hist, *misc;
+    uint2* psrc;
     uint32_t *tk0, *tv0, *tk1, *tv1;
 };
 
@@ -434,7 +445,7 @@ static SortWs carve_sort(char* base, size_t cap_bytes, int64_t n_items, int64_t 
     w.pv0 = c.take<uint32_t>(capacity);
     w.pk1 = c.take<uint32_t>(capacity);
     w.pv1 = c.take<uint32_t>(capacity);
-    w.psrc = c.take<uint32_t>(capacity);
+    w.psrc = c.take<uint2>(capacity);
     w.hist = c.take<uint32_t>(256 * radix_blocks(m));
     w.misc = c.take<uint32_t>(8);
     w.tk0 = c.take<uint32_t>(n_tiles);
@@ -496,8 +507,11 @@ extern "C" int gs_sort(const gs_projected* p, int64_t n, const gs_frame* f, cons
     // 2. stable sort of visible items by depth bits
     const bool in1 = radix_sort_pairs(w.vk0, w.vv0, w.vk1, w.vv1, n_items, n_vis, 32, w.hist, w.scan, s, false);
     const uint32_t* sorted_item = in1 ? w.vv1 : w.vv0;
-    // 3. emission offsets in depth order; pair count
+    // 3. pair positions in depth order; pair count; emission slots in item order (each item's pairs
+    //    occupy offset[item] .. offset[item] + n_tiles - 1, so the adjoint's per-item runs of the
+    //    Gaussians of one view are adjacent)
     scan_exclusive(LoadGatherTiles{p->n_tiles, sorted_item}, w.emit_off, n_items, n_vis, p_total, w.scan, s);
+    scan_exclusive(LoadTiles{p->n_tiles}, out->offset, n_items, nullptr, nullptr, w.scan, s);
     k_pair_count<<<1, 1, 0, s>>>(p_total, out->capacity, out->count, n_eff, out->status);
     count_launch();
     // 4. duplicate: one (tile, emission slot) pair per tile of each visible item's rect

@@ -35,7 +35,9 @@ class Rasterizer:
 
     def set_capacity(self, capacity: int):
         self.capacity = max(int(capacity), 1)
-        self.pairs = gs.Pairs.alloc(self.items, self.n_tiles, self.capacity, self.device)
+        # the tile work order is only read by the persistent schedule; without it gs_sort skips that sort
+        self.pairs = gs.Pairs.alloc(self.items, self.n_tiles, self.capacity, self.device,
+                                    with_order=self.cfg.schedule == 1)
         self.ws_sort = gs.workspace(gs.gs_sort_workspace_size(self.n, self.f, self.capacity), self.device)
         self.ws_bwd = gs.workspace(gs.gs_backward_workspace_size(self.n, self.f, self.capacity), self.device)
 
