@@ -157,7 +157,9 @@ int gs_project(const gs_gaussians* g, const gs_camera* cams, const gs_frame* f, 
  *   count   device int64[1]: number of pairs (written by gs_sort)
  *   status  device int32[1]: GS_OK, or GS_ERR_CAPACITY if count > capacity (then
  *           only the first `capacity` pairs, by depth, exist: renders are
- *           incomplete and gs_project_bwd returns zero gradients)
+ *           incomplete and gs_project_bwd returns zero gradients), or
+ *           GS_ERR_TIMEOUT if a scan or radix pass gave up waiting for an
+ *           earlier CTA's count (bounded polls; the lists are then invalid)
  *   order   [total tiles] optional (NULL to skip): tile indices by decreasing
  *           pair count (stable), the work order of the persistent schedule */
 typedef struct gs_pairs {
@@ -178,8 +180,10 @@ size_t gs_sort_workspace_size(int64_t n, const gs_frame* f, int64_t capacity);
 /* Per-tile duplication and ordering. Visible items are first ordered by fp32
  * depth (stable LSD radix sort, ties by item index), their pairs are emitted
  * in that order, then a stable radix sort on the global tile index yields, per
- * tile, the Gaussians in (depth bits, Gaussian id) order. ws: device scratch of
- * at least gs_sort_workspace_size bytes, 256-byte aligned. */
+ * tile, the Gaussians in (depth bits, Gaussian id) order. Scans and radix
+ * passes are single-pass (decoupled look-back between CTAs). ws: device
+ * scratch of at least gs_sort_workspace_size bytes, 256-byte aligned; calls
+ * that share one ws must not overlap on the GPU. */
 int gs_sort(const gs_projected* p, int64_t n, const gs_frame* f, const gs_pairs* out, void* ws, size_t ws_bytes,
             void* stream);
 
