@@ -474,17 +474,22 @@ int gs_mlp_train_step(const gs_mlp_params* p, const gs_mlp_params* m, const gs_m
 int gs_mlp_gemm_bf16(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc,
                      int32_t M, int32_t N, int32_t K, int32_t tensor_path, void* stream);
 
-/* Training targets of the learned proposal from direct sampling: for spawned
- * Gaussians i (pixel index, camera depth, log-scale value) with kept[i] != 0
- * (still present after the frame's optimisation), targets [n_patches][4] =
- * (kept count / 64, their mean depth, mean log-scale value, 1 if any kept
- * else 0) per 8x8 patch. The log-scale value is the quantity the network's
- * third output learns: the offset to direct sampling's log-scale, e.g. the
- * change the optimisation made to it. ws: gs_mlp_targets_workspace_size bytes. */
+/* Training targets of the learned proposal from one frame's spawns after the
+ * frame's optimisation (the primitives direct sampling produces and keeps,
+ * Sec. 4.2). Spawn i: pixel[i], where it was spawned; its Gaussian row after
+ * the optimisation, mean_opa [n_spawn][4] (mean, opacity logit) and scale
+ * [n_spawn][4] (log-scales); scale0 [n_spawn][4], its log-scale when spawned
+ * (x used); cam, the frame's camera (device). Spawn i is kept when
+ * sigmoid(logit) > keep_threshold (still present with some opacity; 0.05 in
+ * the streaming loop). targets [n_patches][4] per 8x8 patch = (kept count /
+ * 64, mean camera depth R_2 . mu + t_2 of the kept, mean over the kept of
+ * (mean of the three log-scales - scale0.x), 1 if any kept else 0): the
+ * change the optimisation made to the log-scale is what the network's third
+ * output learns. Device buffers; ws: gs_mlp_targets_workspace_size bytes. */
 size_t gs_mlp_targets_workspace_size(int32_t width, int32_t height);
-int gs_mlp_targets(const int32_t* pixel, const float* depth, const float* log_scale, const uint8_t* kept,
-                   int64_t n_spawn, int32_t width, int32_t height, float* targets, void* ws, size_t ws_bytes,
-                   void* stream);
+int gs_mlp_targets(const int32_t* pixel, const float* mean_opa, const float* scale, const float* scale0,
+                   const gs_camera* cam, float keep_threshold, int64_t n_spawn, int32_t width, int32_t height,
+                   float* targets, void* ws, size_t ws_bytes, void* stream);
 
 /* Spawning from the learned proposal's outputs mlp_out [n_patches][3]: the
  * network gives each 8x8 patch m its expected number of kept spawns

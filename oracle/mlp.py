@@ -162,6 +162,24 @@ def targets_from_spawns(pixel, depth, log_scale, kept, W, H):
     return out
 
 
+def targets_from_rows(pixel, mean_opa, scale, scale0, cam, keep_threshold, W, H):
+    """Targets from one frame's spawns after its optimisation (Sec. 4.2: the
+    primitives direct sampling produces and keeps): spawn i is kept when
+    sigmoid(opacity logit) > keep_threshold; its depth is the camera depth
+    R_2 . mu + t_2 of its optimised mean; its log-scale value is the mean of
+    its three optimised log-scales minus its log-scale when spawned. Returns
+    (targets as targets_from_spawns, the spawns' opacities) in FP64."""
+    mo = np.asarray(mean_opa, np.float64)
+    sc = np.asarray(scale, np.float64)
+    R = np.asarray(cam["R"], np.float64).reshape(3, 3)
+    t = np.asarray(cam["t"], np.float64)
+    opa = 1.0 / (1.0 + np.exp(-mo[:, 3]))
+    kept = opa > keep_threshold
+    z = mo[:, :3] @ R[2] + t[2]
+    ls = sc[:, :3].mean(1) - np.asarray(scale0, np.float64)[:, 0]
+    return targets_from_spawns(pixel, z, ls, kept, W, H), opa
+
+
 PATCH_FLOOR = 64 * 1e-3  # lower bound of a patch's P_s sum in the placement ratio
 
 

@@ -328,14 +328,25 @@ extern "C" int gs_spawn_propose_noalloc(const float* image, const float* render,
 namespace gs {
 
 // Scatter the kept spawns into per-pixel slots (each pixel spawns at most once).
-__global__ void k_kept_scatter(const int32_t* __restrict__ pixel, const float* __restrict__ depth,
-                               const float* __restrict__ log_scale, const uint8_t* __restrict__ kept, int64_t n,
-                               int64_t hw, float4* __restrict__ pix_slot) {
+// One thread per spawn: kept when its optimised opacity sigmoid(logit) is
+// above the threshold; then its camera depth R_2 . mu + t_2 and the change of
+// its log-scale (mean over the three axes minus the spawned value) go to the
+// spawn's pixel.
+__global__ void k_kept_scatter(const int32_t* __restrict__ pixel, const float4* __restrict__ mean_opa,
+                               const float4* __restrict__ scale, const float4* __restrict__ scale0,
+                               const gs_camera* __restrict__ cam, float keep_threshold, int64_t n, int64_t hw,
+                               float4* __restrict__ pix_slot) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !kept[i]) return;
+    if (i >= n) return;
+    const float4 mo = mean_opa[i];
+    const float o = 1.f / (1.f + expf(-mo.w));
+    if (!(o > keep_threshold)) return;
     const int32_t p = pixel[i];
     if (p < 0 || (int64_t)p >= hw) return;
-    pix_slot[p] = make_float4(1.f, depth[i], log_scale[i], 0.f);
+    const float z = cam->R[6] * mo.x + cam->R[7] * mo.y + cam->R[8] * mo.z + cam->t[2];
+    const float4 s = scale[i];
+    const float ls = (s.x + s.y + s.z) * (1.f / 3.f) - scale0[i].x;
+    pix_slot[p] = make_float4(1.f, z, ls, 0.f);
 }
 
 // One thread per 8x8 patch: kept fraction, mean depth and log-scale, any-kept.
@@ -442,11 +453,11 @@ extern "C" size_t gs_mlp_targets_workspace_size(int32_t width, int32_t height) {
     return align256(sizeof(float4) * (size_t)width * height);
 }
 
-extern "C" int gs_mlp_targets(const int32_t* pixel, const float* depth, const float* log_scale, const uint8_t* kept,
-                              int64_t n_spawn, int32_t width, int32_t height, float* targets, void* ws,
-                              size_t ws_bytes, void* stream) {
+extern "C" int gs_mlp_targets(const int32_t* pixel, const float* mean_opa, const float* scale, const float* scale0,
+                              const gs_camera* cam, float keep_threshold, int64_t n_spawn, int32_t width,
+                              int32_t height, float* targets, void* ws, size_t ws_bytes, void* stream) {
     if (!targets || width <= 0 || height <= 0 || width % 8 || height % 8 || n_spawn < 0 ||
-        (n_spawn > 0 && (!pixel || !depth || !log_scale || !kept)))
+        (n_spawn > 0 && (!pixel || !mean_opa || !scale || !scale0 || !cam)))
         return GS_ERR_INVALID_ARG;
     const int64_t hw = (int64_t)width * height;
     if (!ws || ws_bytes < gs_mlp_targets_workspace_size(width, height) || ((uintptr_t)ws & 255))
@@ -455,8 +466,9 @@ extern "C" int gs_mlp_targets(const int32_t* pixel, const float* depth, const fl
     float4* slot = (float4*)ws;
     cudaMemsetAsync(slot, 0, sizeof(float4) * hw, s);
     if (n_spawn > 0) {
-        k_kept_scatter<<<(unsigned)ceil_div(n_spawn, 256), 256, 0, s>>>(pixel, depth, log_scale, kept, n_spawn, hw,
-                                                                         slot);
+        k_kept_scatter<<<(unsigned)ceil_div(n_spawn, 256), 256, 0, s>>>(
+            pixel, (const float4*)mean_opa, (const float4*)scale, (const float4*)scale0, cam, keep_threshold, n_spawn,
+            hw, slot);
         count_launch();
     }
     const int64_t np = hw / 64;

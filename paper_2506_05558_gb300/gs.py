@@ -186,7 +186,8 @@ def lib():
                                            C.c_int32, P]),
             "gs_mlp_tc_error": (C.c_int, [C.POINTER(C.c_int32)]),
             "gs_mlp_targets_workspace_size": (C.c_size_t, [C.c_int32, C.c_int32]),
-            "gs_mlp_targets": (C.c_int, [P, P, P, P, C.c_int64, C.c_int32, C.c_int32, P, P, C.c_size_t, P]),
+            "gs_mlp_targets": (C.c_int, [P, P, P, P, P, C.c_float, C.c_int64, C.c_int32, C.c_int32, P, P, C.c_size_t,
+                                          P]),
             "gs_spawn_learned": (C.c_int, [P, P, P, P, C.c_int32, C.c_int32, P, C.POINTER(gs_spawn_config),
                                            C.POINTER(gs_spawn_out), P, C.c_size_t, P]),
             "gs_anchor_offload": (C.c_int, [C.POINTER(gs_gaussians)] * 6 + [P]),
@@ -658,10 +659,11 @@ def gs_mlp_tc_error() -> int:
     return int(v.value)
 
 
-def gs_mlp_targets(pixel, depth, log_scale, kept, n_spawn: int, width: int, height: int, targets: torch.Tensor,
-                   ws: torch.Tensor, stream=None):
-    _check(lib().gs_mlp_targets(_ptr(pixel), _ptr(depth), _ptr(log_scale), _ptr(kept), n_spawn, width, height,
-                                _ptr(targets), _ptr(ws), ws.numel(), _stream(stream)), "gs_mlp_targets")
+def gs_mlp_targets(pixel, mean_opa, scale, scale0, cam: torch.Tensor, keep_threshold: float, n_spawn: int,
+                   width: int, height: int, targets: torch.Tensor, ws: torch.Tensor, stream=None):
+    _check(lib().gs_mlp_targets(_ptr(pixel), _ptr(mean_opa), _ptr(scale), _ptr(scale0), _ptr(cam), keep_threshold,
+                                n_spawn, width, height, _ptr(targets), _ptr(ws), ws.numel(), _stream(stream)),
+           "gs_mlp_targets")
 
 
 def gs_mlp_targets_workspace_size(width: int, height: int) -> int:

@@ -105,7 +105,8 @@ class OnTheFly:
                  mlp_warmup_frames: int = 3, mlp_steps: int = 40, keep_threshold: float = 0.05, seed: int = 7,
                  anchor_tau: float = 1.0, anchor_share: float = 0.4, merge_radius: float = 0.5,
                  coarse_to_fine: int = 0, mip_filter: bool = False, lr_decay: float = 1.0,
-                 min_opacity: float = 0.0, guided_neighbours: int = 0, device="cuda"):
+                 min_opacity: float = 0.0, guided_neighbours: int = 0, learned_depth: str = "map",
+                 mlp_online: bool = False, device="cuda"):
         self.store = GaussianStore(capacity, device)
         self.W, self.H = size
         self.window = window
@@ -123,6 +124,11 @@ class OnTheFly:
         self.seed = seed
         self.device = device
         self.keep_threshold = keep_threshold
+        # learned spawning takes its depth from the frame's map where valid ("map") or
+        # from the network everywhere ("predicted"); with mlp_online the network keeps
+        # training on each frame's kept spawns after the warm-up frames
+        self.learned_depth = learned_depth
+        self.mlp_online = mlp_online
         self.mlp_warmup_frames = mlp_warmup_frames
         self.mlp_steps = mlp_steps
         hw = self.W * self.H
@@ -223,7 +229,8 @@ class OnTheFly:
         if use_learned:
             gs.gs_mlp_forward(self.mlp, image, self.W, self.H, self.mlp_out, self.mlp_cfg, self.ws_mlp)
             gs.gs_spawn_learned(image, self.mlp_out, self.W, self.H, cam, self.seed, frame_idx, self.spawned,
-                                self.ws_spawn, depth=depth, render=render)
+                                self.ws_spawn, depth=depth if self.learned_depth == "map" else None,
+                                render=render)
         else:
             gs.gs_spawn_propose(image, render, depth, self.W, self.H, cam, 1.0, self.seed, frame_idx, self.spawned,
                                 self.ws_spawn)
@@ -286,23 +293,16 @@ class OnTheFly:
         return removed
 
     def _train_mlp(self, image, n0, k, cam):
-        """Targets from this frame's spawns that are still opaque after the
-        optimisation: their optimised camera depth and the change of their mean
-        log-scale, so the network learns where spawns survive and how their
+        """Targets from this frame's spawns after the optimisation (kept when
+        still opaque: their optimised camera depth and the change of their mean
+        log-scale), so the network learns where spawns survive and how their
         scale converges; then a few training steps of the proposal network."""
         if k == 0:
             return None
         g, _, _ = self.store.active()
-        opa = torch.sigmoid(g.mean_opa[n0:n0 + k, 3])
-        kept = (opa > self.keep_threshold).to(torch.uint8)
-        pix = self.spawned.pixel[:k]
-        c = gs.cameras_from_tensor(cam)[0]
-        R = torch.tensor(c["R"], dtype=torch.float32, device=self.device)
-        t = torch.tensor(c["t"], dtype=torch.float32, device=self.device)
-        z = (g.mean_opa[n0:n0 + k, :3] @ R[2] + t[2]).contiguous()
-        # the network predicts the change the optimisation made to the spawn's log-scale
-        ls = (g.scale[n0:n0 + k, :3].mean(1) - self.spawned.g.scale[:k, 0]).contiguous()
-        gs.gs_mlp_targets(pix, z, ls, kept, k, self.W, self.H, self.mlp_targets, self.ws_tg)
+        gs.gs_mlp_targets(self.spawned.pixel[:k], g.mean_opa[n0:n0 + k], g.scale[n0:n0 + k],
+                          self.spawned.g.scale[:k], cam, self.keep_threshold, k, self.W, self.H, self.mlp_targets,
+                          self.ws_tg)
         for _ in range(self.mlp_steps):
             self.mlp_step += 1
             gs.gs_mlp_train_step(self.mlp, self.mlp_m, self.mlp_v, image, self.W, self.H, self.mlp_targets,
@@ -338,7 +338,7 @@ class OnTheFly:
         self.frames.append([image, cam, self.c2f])
         loss = self._optimise(self.iters)
         mlp_loss = None
-        if self.mode == "learned" and not learned:
+        if self.mode == "learned" and (not learned or self.mlp_online):
             # the direct-sampling spawns of the warm-up frames that survived
             # the optimisation teach the proposal (before culling moves rows)
             mlp_loss = self._train_mlp(image, n0, k, cam)

@@ -141,20 +141,38 @@ def test_adam_step_matches_oracle(PATH):
 
 
 def test_targets_from_kept_spawns_match_oracle():
+    """The keep decision (sigmoid of the optimised logit above the threshold),
+    camera depth and log-scale change of every spawn, summed per patch, against
+    the FP64 oracle. Logits stay 1e-3 away from the threshold's logit, so FP32
+    takes the same keep decisions."""
+    from paper_2506_05558_gb300 import synth
+    from oracle import oracle as O
     rng = np.random.default_rng(5)
     W, H = 120, 64
     n = 2000
+    thr = 0.05
     pixel = np.sort(rng.choice(W * H, n, replace=False)).astype(np.int32)
-    depth = rng.uniform(1, 20, n).astype(np.float32)
-    ls = rng.normal(-4, 1, n).astype(np.float32)
-    kept = (rng.random(n) < 0.5).astype(np.uint8)
+    mean_opa = np.zeros((n, 4), np.float32)
+    mean_opa[:, :3] = rng.uniform(-3, 3, (n, 3))
+    mean_opa[:, 2] += 8.0
+    logit = rng.normal(-3.0, 1.5, n)
+    l_thr = np.log(thr / (1 - thr))
+    logit = np.where(np.abs(logit - l_thr) < 1e-3, l_thr + 2e-3, logit)
+    mean_opa[:, 3] = logit
+    scale = np.zeros((n, 4), np.float32)
+    scale[:, :3] = rng.normal(-4, 1, (n, 3))
+    scale0 = np.repeat(rng.normal(-4, 0.5, (n, 1)), 4, 1).astype(np.float32)
+    R, t = O.retract_pose(np.eye(3), np.zeros(3), [0.2, -0.1, 0.3, 0.05, 0.1, -0.08])
+    cam = synth.camera(R.astype(np.float32), t.astype(np.float32), 100.0, W, H)
     tg = torch.zeros(((W // 8) * (H // 8), 4), device="cuda")
     ws = gs.workspace(gs.gs_mlp_targets_workspace_size(W, H))
-    c = lambda a: torch.from_numpy(a).cuda()
-    gs.gs_mlp_targets(c(pixel), c(depth), c(ls), c(kept), n, W, H, tg, ws)
+    c = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    gs.gs_mlp_targets(c(pixel), c(mean_opa), c(scale), c(scale0), gs.cameras_tensor([cam]), thr, n, W, H, tg, ws)
     torch.cuda.synchronize()
-    ref = OM.targets_from_spawns(pixel, depth.astype(np.float64), ls.astype(np.float64), kept, W, H)
-    assert_close(tg.cpu().numpy(), ref, 1e-6, what="targets")
+    ref, opa = OM.targets_from_rows(pixel, mean_opa.astype(np.float64), scale.astype(np.float64),
+                                    scale0.astype(np.float64), cam, thr, W, H)
+    assert 0.2 < np.mean(opa > thr) < 0.8
+    assert_close(tg.cpu().numpy(), ref, 1e-5, what="targets")
 
 
 @pytest.mark.parametrize("with_depth,with_render", [(False, False), (True, False), (True, True)])

@@ -1,8 +1,6 @@
-"""End-to-end streaming check of the learned spawn proposal against plain
-direct sampling (Sec. 4.2, the fallback it is measured against): both reconstruct a
-synthetic scene frame by frame with the same iteration budget; the test
-records the PSNR each reaches and the Gaussians each spawned, and requires both
-to reconstruct (PSNR well above the empty render)."""
+"""End-to-end streaming checks (Sec. 4.2-4.4): the learned spawn proposal
+against plain direct sampling (the fallback it is measured against), anchors,
+the training-schedule variants and guided matching in the loop."""
 import json
 import os
 
@@ -48,9 +46,55 @@ def run(mode, frames, size, iters=20):
     return otf.evaluate(ev), otf
 
 
-def test_learned_vs_plain_spawning():
-    """Both modes at 10, 20 and 30 iterations per frame; the report records
-    PSNR and set size per budget."""
+def mono_depth(depth, size, seed, sd=0.1):
+    """A monocular-style estimate: the true depth times exp(sd x a smooth random
+    field) with a little per-pixel noise; uncovered pixels stay 0."""
+    W, H = size
+    gen = torch.Generator(device="cpu").manual_seed(seed)
+    coarse = torch.randn((1, 1, 4, 6), generator=gen)
+    field = torch.nn.functional.interpolate(coarse, size=(H, W), mode="bilinear", align_corners=True)[0, 0]
+    fine = 0.02 * torch.randn((H, W), generator=gen)
+    d = depth.reshape(H, W) * torch.exp(sd * field.cuda() + fine.cuda())
+    return d.reshape(depth.shape).contiguous()
+
+
+def test_learned_proposal_reaches_plain_psnr_in_fewer_iterations():
+    """The learned proposal's target relation on a room of textured opaque
+    surfaces (16 frames of 256x144 on the standard path) where both modes take
+    spawn depths from a monocular-style estimate with a smooth 25% error (the
+    paper's setting, Sec. 4.2; no mode sees the true depth): with 25 iterations
+    per frame the learned proposal must come within 0.2 dB of plain direct
+    sampling with 30. Budgets 15-30 are recorded for both modes, with the
+    Gaussians each spawned, and the same comparison with the true depth."""
+    size = (256, 144)
+    n_frames = 16
+    sc, cams = synth.surface_scene(n_views=n_frames, size=size)
+    g = gs.Gaussians.from_scene(sc)
+    cts = [gs.cameras_tensor([c]) for c in cams]
+    rendered = [render_depth(g, ct, size, gs.config(sh_degree=0)) for ct in cts]
+    monos = [mono_depth(d, size, 100 + i, sd=0.25) for i, (_, d) in enumerate(rendered)]
+    empty = 10 * np.log10(1.0 / torch.mean(rendered[-1][0] ** 2).item())
+    report = {"frames": n_frames, "size": size, "empty_render_psnr": empty, "mono": {}, "true_depth": {}}
+    for depth_kind, budgets in (("mono", (15, 20, 25, 30)), ("true_depth", (20, 30))):
+        frames = [(img, monos[i] if depth_kind == "mono" else d, cts[i]) for i, (img, d) in enumerate(rendered)]
+        for iters in budgets:
+            p_plain, a = run("plain", frames, size, iters)
+            p_learn, b = run("learned", frames, size, iters)
+            report[depth_kind][iters] = {"psnr_plain": p_plain, "psnr_learned": p_learn,
+                                         "gaussians_plain": a.store.n, "gaussians_learned": b.store.n}
+    os.makedirs(REPORT_DIR, exist_ok=True)
+    with open(os.path.join(REPORT_DIR, "stream_learned_report.json"), "w") as f:
+        json.dump(report, f, indent=1)
+    print(json.dumps(report))
+    m = report["mono"]
+    assert m[25]["psnr_learned"] >= m[30]["psnr_plain"] - 0.2, report
+    assert m[30]["psnr_plain"] > empty + 5, report
+
+
+def test_learned_vs_plain_spawning_random_scene():
+    """The same comparison on a scene of random small Gaussians, spawning from
+    the true depth: recorded (the proposal loses here; no relation is
+    asserted beyond both modes reconstructing)."""
     size = (256, 144)
     frames = make_stream(size=size)
     empty = 10 * np.log10(1.0 / torch.mean(frames[-1][0] ** 2).item())
@@ -159,18 +203,6 @@ def render_features(sc, cams, size, channels=16, seed=3, period=(0.3, 1.0)):
         f = f / f.norm(dim=-1, keepdim=True).clamp_min(1e-6)
         out.append(f.to(torch.bfloat16).view(torch.int16).contiguous())
     return out
-
-
-def mono_depth(depth, size, seed, sd=0.1):
-    """A monocular-style estimate: the true depth times exp(sd x a smooth random
-    field) with a little per-pixel noise; uncovered pixels stay 0."""
-    W, H = size
-    gen = torch.Generator(device="cpu").manual_seed(seed)
-    coarse = torch.randn((1, 1, 4, 6), generator=gen)
-    field = torch.nn.functional.interpolate(coarse, size=(H, W), mode="bilinear", align_corners=True)[0, 0]
-    fine = 0.02 * torch.randn((H, W), generator=gen)
-    d = depth.reshape(H, W) * torch.exp(sd * field.cuda() + fine.cuda())
-    return d.reshape(depth.shape).contiguous()
 
 
 def test_guided_matching_refines_the_spawn_depth():

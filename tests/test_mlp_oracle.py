@@ -108,6 +108,25 @@ def test_targets_from_spawns_hand_case():
     np.testing.assert_array_equal(t0, np.zeros((2, 4)))
 
 
+def test_targets_from_rows_hand_case():
+    """Kept by opacity, camera depth and log-scale change of optimised rows,
+    by hand: camera R = rotation about y by 90 degrees (row 2 of R = (-1, 0, 0)),
+    t = (0, 0, 5): z = 5 - mu_x; opacity logits 0 (0.5), -4 (0.018) and 2 (0.88)
+    against the threshold 0.05."""
+    W, H = 16, 8
+    c, s_ = 0.0, 1.0
+    cam = dict(R=np.array([[c, 0, s_], [0, 1, 0], [-s_, 0, c]]), t=np.array([0.0, 0.0, 5.0]))
+    pixel = np.array([0 * W + 1, 3 * W + 7, 2 * W + 9])
+    mean_opa = np.array([[1.0, 9.0, 9.0, 0.0], [2.0, 0.0, 0.0, -4.0], [-3.0, 1.0, 1.0, 2.0]])
+    scale = np.array([[-3.0, -4.0, -5.0, 0.0], [0.0, 0.0, 0.0, 0.0], [-1.0, -1.0, -4.0, 0.0]])
+    scale0 = np.array([[-3.5, -3.5, -3.5, 0.0], [-1.0, -1.0, -1.0, 0.0], [-2.5, -2.5, -2.5, 0.0]])
+    t, opa = M.targets_from_rows(pixel, mean_opa, scale, scale0, cam, 0.05, W, H)
+    np.testing.assert_allclose(opa, [0.5, 1 / (1 + np.exp(4.0)), 1 / (1 + np.exp(-2.0))], rtol=1e-15)
+    # spawn 0 kept in patch 0: z = 5 - 1 = 4, ls = -4 + 3.5 = -0.5; spawn 1 dropped (0.018);
+    # spawn 2 kept in patch 1: z = 5 + 3 = 8, ls = -2 + 2.5 = 0.5
+    np.testing.assert_allclose(t, [[1 / 64, 4.0, -0.5, 1.0], [1 / 64, 8.0, 0.5, 1.0]], rtol=1e-14, atol=1e-14)
+
+
 def _pin_cam(W, H):
     from oracle import oracle as O
     from paper_2506_05558_gb300 import synth
