@@ -572,6 +572,71 @@ def measure_ba(torch, gs, device, iterations=200):
 # ---------------------------------------------------------------------------
 # oracle on the host cores
 # ---------------------------------------------------------------------------
+def measure_stream(torch, gs, synth, device, frames=100, size=(1920, 1080), n_gt=2_000_000, runs=None,
+                   log_every=10):
+    """The streaming workload at full size (Sec. 4.2-4.4): new 1920x1080 frames of
+    a textured corridor along the standard path, spawn depths from a
+    monocular-style estimate (true depth x a smooth 25% error field) for every
+    mode, 3-frame window, anchors at 1 px / 40% with merging, opacity culling
+    at 0.005. runs: (name, mode, iterations per frame, extra OnTheFly options).
+    Per run: per-frame wall time, active set, Gaussians spawned in total, anchors
+    and host bytes offloaded, PSNR of each new frame after its optimisation and
+    of the last five frames rendered from the final active set."""
+    from paper_2506_05558_gb300.stream import OnTheFly, render_depth, psnr
+    if runs is None:
+        runs = [("plain_30", "plain", 30, {}), ("plain_25", "plain", 25, {}), ("learned_30", "learned", 30, {}),
+                ("learned_25", "learned", 25, {}),
+                # the corridor keeps Gaussians above 1 px from the previous camera, so anchors
+                # are also exercised with a 4 px size threshold
+                ("learned_25_anchor_4px", "learned", 25, {"anchor_tau": 4.0})]
+    W_, H_ = size
+    sc, cams = synth.corridor_scene(n=n_gt, n_views=frames, size=size)
+    g_true = gs.Gaussians.from_scene(sc, device)
+    data = []
+    for i, c in enumerate(cams):
+        ct = gs.cameras_tensor([c], device)
+        color, depth = render_depth(g_true, ct, size, gs.config(sh_degree=0), device)
+        fac = torch.from_numpy(synth.monocular_factor(W_, H_, 300 + i)).to(device).reshape(-1)
+        data.append((color, (depth * fac).contiguous(), ct))
+    del g_true
+    torch.cuda.synchronize()
+    out = {"frames": frames, "size": [W_, H_], "ground_truth_gaussians": n_gt, "runs": {}}
+    for name, mode, iters, kw in runs:
+        opts = dict(anchor_tau=1.0, anchor_share=0.4, merge_radius=0.5, min_opacity=0.005)
+        opts.update(kw)
+        otf = OnTheFly(8_000_000, size, window=3, iters=iters, mode=mode, mlp_warmup_frames=3, mlp_steps=30,
+                       device=device, **opts)
+        per = []
+        t_all = time.time()
+        for i, (img, depth, cam) in enumerate(data):
+            torch.cuda.synchronize()
+            t0 = time.time()
+            otf.add_frame(img, depth, cam, i)
+            torch.cuda.synchronize()
+            dt = time.time() - t0
+            p_new = otf.evaluate([(img, cam)])
+            e = otf.log[-1]
+            per.append({"frame": i, "s": dt, "active": otf.store.n, "spawned": e["spawned"], "psnr": p_new,
+                        "culled": e["culled"], "anchor": e["anchor"]})
+            if i % log_every == 0:
+                log(f"stream {name} frame {i}: {dt:.3f} s, active {otf.store.n}, spawned {e['spawned']}, "
+                    f"psnr {p_new:.2f}")
+        total_s = time.time() - t_all
+        last = otf.evaluate([(img, cam) for img, _, cam in data[-5:]])
+        out["runs"][name] = {
+            "mode": mode, "iters_per_frame": iters, "total_s": total_s,
+            "s_per_frame_median": float(np.median([q["s"] for q in per])),
+            "peak_active": max(q["active"] for q in per), "final_active": otf.store.n,
+            "spawned_total": sum(q["spawned"] for q in per), "anchors": len(otf.anchors),
+            "offloaded_bytes": int(sum(a.n for a in otf.anchors) * 3 * 240),
+            "psnr_new_frame_mean": float(np.mean([q["psnr"] for q in per])),
+            "psnr_last5_final": last, "anchor_tau_px": opts["anchor_tau"],
+            "merges": [q["anchor"] for q in per if q["anchor"]], "per_frame": per}
+        del otf
+        torch.cuda.empty_cache()
+    return out
+
+
 def measure_peaks(torch, gs, device, sms, reps=5):
     """FP32 FMA and MUFU throughput measured by the library's probes (one
     CTA of 256 threads per 1/8 of an SM's threads, i.e. 8 per SM, long enough
@@ -696,9 +761,11 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the spawn / MLP / anchor measurements")
     ap.add_argument("--cpu-views", type=int, default=6, help="views of the oracle CPU sample")
-    ap.add_argument("--row", choices=["mini_ba", "pose_refine", "guided_matching"], default=None,
+    ap.add_argument("--row", choices=["mini_ba", "pose_refine", "guided_matching", "stream"], default=None,
                     help="measure only this side row and print its numbers (for profiling)")
     ap.add_argument("--ba-iterations", type=int, default=200)
+    ap.add_argument("--stream-frames", type=int, default=100)
+    ap.add_argument("--stream-gt", type=int, default=2_000_000, help="ground-truth Gaussians of the streaming row")
     args = ap.parse_args()
     if args.warmup < 3:
         log("warm-up raised to 3 (timing rule)")
@@ -730,6 +797,8 @@ def main():
                 r = measure_ba(torch, gs, device, iterations=args.ba_iterations)
             elif args.row == "pose_refine":
                 r = measure_ba_pose(torch, gs, device)
+            elif args.row == "stream":
+                r = measure_stream(torch, gs, synth, device, frames=args.stream_frames, n_gt=args.stream_gt)
             else:
                 r = measure_guided(torch, gs, device, SMS * FP32_LANES * 2 * 2070.0 * 1e6 / 1e12)
             print(json.dumps({"row": args.row, **r}), flush=True)

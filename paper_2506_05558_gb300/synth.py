@@ -388,3 +388,85 @@ def surface_scene(seed=1008, n=120_000, n_views=10, size=(256, 144), f=200.0):
     path = camera_path(rng, n_views)
     cams = [camera(*world_to_camera(R, c), f, size[0], size[1]) for R, c in path]
     return sc, cams
+
+
+def corridor_scene(seed=1009, n=2_000_000, n_views=100, size=(1920, 1080), f=1500.0):
+    """The streaming workload at full size: Gaussians on the surfaces of a long
+    room built around the standard camera path (0.3 m and 5 degrees per
+    frame; drawn first, from its own seed): side walls 3 m beyond the path's
+    extent either side, a floor 2 m below and a ceiling 2.5 m above the
+    cameras, walls 3 m behind the start and 8 m past the end, plus 40 boxes
+    along the side walls - as small flat, nearly opaque discs with random
+    colours (as surface_scene). n_views cameras of the given size, fx = fy = f.
+    Returns (Scene, cameras)."""
+    path = camera_path(_rng(seed + 1), n_views)
+    ctr = np.array([c for _, c in path])
+    x0, x1 = ctr[:, 0].min() - 3.0, ctr[:, 0].max() + 3.0
+    z0, z1 = ctr[:, 2].min() - 3.0, ctr[:, 2].max() + 8.0
+    y0, y1 = -2.5, 2.0
+    wx, wy, wz = x1 - x0, y1 - y0, z1 - z0
+    rng = _rng(seed)
+    rects = [((x0, y0, z1), (wx, 0, 0), (0, wy, 0)),   # end wall
+             ((x0, y0, z0), (wx, 0, 0), (0, wy, 0)),   # start wall
+             ((x0, y1, z0), (wx, 0, 0), (0, 0, wz)),   # floor
+             ((x0, y0, z0), (wx, 0, 0), (0, 0, wz)),   # ceiling
+             ((x0, y0, z0), (0, wy, 0), (0, 0, wz)),   # left wall
+             ((x1, y0, z0), (0, wy, 0), (0, 0, wz))]   # right wall
+    for _ in range(40):
+        zc = rng.uniform(z0 + 2.0, z1 - 2.0)
+        left = rng.random() < 0.5
+        xc = (x0 + rng.uniform(0.3, 0.9)) if left else (x1 - rng.uniform(0.3, 0.9))
+        yc = rng.uniform(0.0, 1.5)
+        hw, hh = rng.uniform(0.2, 0.4), rng.uniform(0.3, 0.5)
+        rects.append(((xc - hw, yc - hh, zc), (2 * hw, 0, 0), (0, 2 * hh, 0)))
+    area = np.array([np.linalg.norm(np.cross(u, v)) for _, u, v in rects])
+    which = rng.choice(len(rects), n, p=area / area.sum())
+    ab = rng.random((n, 2))
+    mean = np.empty((n, 3))
+    quat = np.empty((n, 4))
+    for k, (o, u, v) in enumerate(rects):
+        m = which == k
+        o, u, v = np.asarray(o), np.asarray(u, float), np.asarray(v, float)
+        mean[m] = o + ab[m, :1] * u + ab[m, 1:] * v
+        nrm = np.cross(u, v)
+        nrm /= np.linalg.norm(nrm)
+        axis = np.cross([0.0, 0.0, 1.0], nrm)
+        s, c = np.linalg.norm(axis), nrm[2]
+        if s < 1e-9:
+            q = np.array([1.0, 0.0, 0.0, 0.0])
+        else:
+            ang = math.atan2(s, c)
+            axis /= s
+            q = np.concatenate([[math.cos(ang / 2)], math.sin(ang / 2) * axis])
+        quat[m] = q
+    scale = np.zeros((n, 4))
+    scale[:, 0] = scale[:, 1] = math.log(0.03)
+    scale[:, 2] = math.log(0.003)
+    sh = np.zeros((n, 48))
+    sh[:, :3] = rng.normal(0, DC_STD, (n, 3))
+    mean_opa = np.concatenate([mean, np.full((n, 1), 4.0)], 1)
+    sc = Scene(mean_opa.astype(np.float32), scale.astype(np.float32), quat.astype(np.float32),
+               sh.astype(np.float32), 0)
+    cams = [camera(*world_to_camera(R, c), f, size[0], size[1]) for R, c in path]
+    return sc, cams
+
+
+def monocular_factor(width, height, seed, sd=0.25, noise=0.02):
+    """Multiplicative error of a monocular-style depth estimate: exp(sd x a
+    smooth random field + noise x per-pixel N(0, 1)), the field a 4 x 6 grid of
+    N(0, 1) values interpolated bilinearly (corners at the image corners).
+    Returns float32 [height][width]."""
+    rng = _rng(seed)
+    coarse = rng.standard_normal((4, 6))
+    ys = np.linspace(0, 3, height)
+    xs = np.linspace(0, 5, width)
+    y0 = np.minimum(np.floor(ys).astype(int), 2)
+    x0 = np.minimum(np.floor(xs).astype(int), 4)
+    fy = (ys - y0)[:, None]
+    fx = (xs - x0)[None, :]
+    c00 = coarse[y0][:, x0]
+    c01 = coarse[y0][:, x0 + 1]
+    c10 = coarse[y0 + 1][:, x0]
+    c11 = coarse[y0 + 1][:, x0 + 1]
+    field = (c00 * (1 - fx) + c01 * fx) * (1 - fy) + (c10 * (1 - fx) + c11 * fx) * fy
+    return np.exp(sd * field + noise * rng.standard_normal((height, width))).astype(np.float32)
