@@ -637,6 +637,110 @@ def measure_stream(torch, gs, synth, device, frames=100, size=(1920, 1080), n_gt
     return out
 
 
+def ssim(torch, img, ref, window=11, sigma=1.5):
+    """Mean SSIM of a [3][H][W] pair: 11x11 Gaussian window (sigma 1.5), zero
+    padding, C1 = 0.01^2, C2 = 0.03^2 (the 720p workload's D-SSIM term; PyTorch
+    turns the loss into dL/dC, which is all that crosses the library boundary)."""
+    F = torch.nn.functional
+    x = torch.arange(window, dtype=img.dtype, device=img.device) - window // 2
+    k1 = torch.exp(-x * x / (2 * sigma * sigma))
+    k1 = k1 / k1.sum()
+    k = (k1[:, None] * k1[None, :]).expand(3, 1, window, window).contiguous()
+    f = lambda t: F.conv2d(t[None], k, padding=window // 2, groups=3)[0]
+    mu_x, mu_y = f(img), f(ref)
+    sxx = f(img * img) - mu_x * mu_x
+    syy = f(ref * ref) - mu_y * mu_y
+    sxy = f(img * ref) - mu_x * mu_y
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    m = ((2 * mu_x * mu_y + c1) * (2 * sxy + c2)) / ((mu_x * mu_x + mu_y * mu_y + c1) * (sxx + syy + c2))
+    return m.mean()
+
+
+def config_scene(synth, which):
+    """(scene, camera, rng, sh degree) of the 64x64 (which = 0) or 720p (1) workload."""
+    if which == 0:
+        sc, cam, rng = synth.tiny_scene()
+        return sc, cam, rng, 0
+    sc, cam, rng = synth.view_720p_scene()
+    return sc, cam, rng, 3
+
+
+def oracle_config_time(which, min_s=5.0):
+    """Seconds per fwd+bwd (incl. pose) of the FP64 oracle on one view of the
+    64x64 or 720p workload, repeated for at least min_s seconds (at least once),
+    with the threads OMP_NUM_THREADS gives."""
+    from oracle import build as ob
+    from oracle import oracle as O
+    from paper_2506_05558_gb300 import synth
+    ob.build()
+    sc, cam, rng, shd = config_scene(synth, which)
+    cfg = O.Config(sh_degree=shd)
+    H, W = cam["height"], cam["width"]
+    dL = np.sign(rng.standard_normal((3, H, W))) / (3 * H * W)
+    n, t0 = 0, time.perf_counter()
+    while True:
+        view = O.render_view(sc, cam, cfg)
+        O.backward_view(sc, cam, cfg, view, dL)
+        n += 1
+        if time.perf_counter() - t0 >= min_s:
+            break
+    return (time.perf_counter() - t0) / n
+
+
+def measure_configs(torch, gs, synth, device, reps=(400, 50)):
+    """Iterations per second of the 64x64 and 720p workloads on the GPU (project,
+    sort, forward, loss, adjoint with the pose gradient; no optimiser step; the
+    720p loss is L1 + 0.2 (1 - SSIM) through PyTorch autograd into dL/dC), CUDA
+    events over the repetitions after warm-up; and the FP64 oracle's time per
+    iteration on one host thread and on all host cores (child processes)."""
+    from paper_2506_05558_gb300.raster import Rasterizer
+    out = {}
+    for which in (0, 1):
+        sc, cam, rng, shd = config_scene(synth, which)
+        W_, H_ = cam["width"], cam["height"]
+        cfg = gs.config(sh_degree=shd)
+        g = gs.Gaussians.from_scene(sc, device)
+        cams = gs.cameras_tensor([cam], device)
+        r = Rasterizer(sc.n, [(W_, H_)], 1 << 20, cfg, device)
+        r.fit_capacity(g, cams)
+        r.forward(g, cams)
+        tgt = (r.img.color.view(3, H_, W_) + 0.01 * torch.randn((3, H_, W_), device=device)).contiguous()
+        dL = torch.zeros_like(r.img.color)
+        loss = torch.zeros(1, device=device)
+        ws = gs.workspace(4 * 4096, device)
+
+        def step():
+            r.forward(g, cams)
+            if which == 0:
+                gs.gs_l1_loss(r.img.color, tgt.view(-1), dL, loss, ws)
+            else:
+                img = r.img.color.view(3, H_, W_).detach().requires_grad_(True)
+                lv = (img - tgt).abs().mean() + 0.2 * (1.0 - ssim(torch, img, tgt))
+                lv.backward()
+                dL.copy_(img.grad.view(-1))
+            r.backward(g, cams, dL)
+
+        for _ in range(5):
+            step()
+        ms = event_ms(torch, step, reps[which])
+        assert r.status() == gs.GS_OK
+        t1 = t_all = None
+        for threads in (1, os.cpu_count() or 1):
+            env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+            res = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-config", str(which)],
+                                 capture_output=True, text=True, env=env)
+            sec = float(res.stdout.strip().splitlines()[-1]) if res.returncode == 0 else None
+            if threads == 1:
+                t1 = sec
+            else:
+                t_all = sec
+        name = "64x64, 1k Gaussians SH0, L1" if which == 0 else "1280x720, 200k Gaussians SH3, L1 + 0.2 D-SSIM"
+        out[f"config{which}"] = {"workload": name, "gpu_ms_per_iter": ms, "gpu_iters_per_s": 1000.0 / ms,
+                                 "oracle_s_per_iter_1_thread": t1, "oracle_s_per_iter_all_cores": t_all,
+                                 "host_cores": os.cpu_count()}
+    return out
+
+
 def measure_peaks(torch, gs, device, sms, reps=5):
     """FP32 FMA and MUFU throughput measured by the library's probes (one
     CTA of 256 threads per 1/8 of an SM's threads, i.e. 8 per SM, long enough
@@ -761,7 +865,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the spawn / MLP / anchor measurements")
     ap.add_argument("--cpu-views", type=int, default=6, help="views of the oracle CPU sample")
-    ap.add_argument("--row", choices=["mini_ba", "pose_refine", "guided_matching", "stream"], default=None,
+    ap.add_argument("--oracle-config", type=int, default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--row", choices=["mini_ba", "pose_refine", "guided_matching", "stream", "configs"],
+                    default=None,
                     help="measure only this side row and print its numbers (for profiling)")
     ap.add_argument("--ba-iterations", type=int, default=200)
     ap.add_argument("--stream-frames", type=int, default=100)
@@ -774,6 +880,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.oracle_config is not None:  # child process of the configs row: the oracle alone
+        print(oracle_config_time(args.oracle_config), flush=True)
+        return 0
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -797,6 +906,8 @@ def main():
                 r = measure_ba(torch, gs, device, iterations=args.ba_iterations)
             elif args.row == "pose_refine":
                 r = measure_ba_pose(torch, gs, device)
+            elif args.row == "configs":
+                r = measure_configs(torch, gs, synth, device)
             elif args.row == "stream":
                 r = measure_stream(torch, gs, synth, device, frames=args.stream_frames, n_gt=args.stream_gt)
             else:
