@@ -84,6 +84,10 @@ SMS = 152
 FP32_LANES = 128
 
 
+# render schedules of gs_config.schedule
+SCHEDULES = {0: "grid", 1: "persistent", 2: "ordered grid"}
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -924,7 +928,7 @@ def main():
         cfg, table = autotune.tune(W["g"], W["cams"], W["sizes"], W["targets"], W["cfg"], steps=2, device=device,
                                    log=log)
         tuned = {"tile": cfg.tile, "fwd_batch": cfg.fwd_batch, "bwd_batch": cfg.bwd_batch,
-                 "schedule": "persistent" if cfg.schedule == 1 else "grid",
+                 "schedule": SCHEDULES[cfg.schedule],
                  "trials": [{"tile": t, "fwd_batch": fb, "bwd_batch": bb, "schedule": sc, "ms": ms}
                             for t, fb, bb, sc, ms in table]}
         reset(W)
@@ -1132,7 +1136,7 @@ def main():
                   "batched": {"value": world * pix * args.steps / (ums / 1000.0) / 1e6, "ms_per_step": ums / args.steps,
                               "config": {"tile": cfg_u.tile, "fwd_batch": cfg_u.fwd_batch,
                                          "bwd_batch": cfg_u.bwd_batch,
-                                         "schedule": "persistent" if cfg_u.schedule == 1 else "grid",
+                                         "schedule": SCHEDULES[cfg_u.schedule],
                                          "graph": "whole step"}, "status_ok": u_ok},
                   "plain": {"value": world * pix * args.steps / (pums / 1000.0) / 1e6,
                             "ms_per_step": pums / args.steps, "status_ok": Pu.ok()}}

@@ -74,7 +74,9 @@ typedef struct gs_config {
     float bg[3];                  /* background colour: 0 */
     int32_t pose_grad_through_sh; /* 1: pose gradient also through the SH view direction: 0 */
     int32_t schedule;             /* render scheduling: 0 = one CTA per tile, 1 = persistent CTAs
-                                     pulling tiles, largest first, from a work queue */
+                                     pulling tiles, largest first, from a work queue, 2 = one CTA
+                                     per tile, CTA i taking the i-th tile of the largest-first
+                                     order (no queue); 1 and 2 need gs_pairs.order */
     int32_t accumulate;           /* gs_render_bwd / gs_project_bwd: 0 overwrite the gradient
                                      buffers, 1 add to them (per-view launches of one step): 0 */
     int32_t fwd_batch;            /* Gaussians staged per round in gs_render_fwd: 0 = default;
@@ -161,7 +163,7 @@ int gs_project(const gs_gaussians* g, const gs_camera* cams, const gs_frame* f, 
  *           GS_ERR_TIMEOUT if a scan or radix pass gave up waiting for an
  *           earlier CTA's count (bounded polls; the lists are then invalid)
  *   order   [total tiles] optional (NULL to skip): tile indices by decreasing
- *           pair count (stable), the work order of the persistent schedule */
+ *           pair count (stable), the work order of schedules 1 and 2 */
 typedef struct gs_pairs {
     uint32_t* src;
     uint32_t* emit;

@@ -66,9 +66,10 @@ def tune(g: gs.Gaussians, cams: torch.Tensor, sizes, targets: torch.Tensor, base
         if best is None or ms < best[-1]:
             best = (tile, 0, 0, 0, ms)
     tile = best[0]
-    ms = run(tile, 0, 0, 1)
-    if ms < best[-1]:
-        best = (tile, 0, 0, 1, ms)
+    for sched in (1, 2):
+        ms = run(tile, 0, 0, sched)
+        if ms < best[-1]:
+            best = (tile, 0, 0, sched, ms)
     sched = best[3]
     for fb in FWD_BATCHES[tile]:
         ms = run(tile, fb, 0, sched)

@@ -108,11 +108,13 @@ __device__ __forceinline__ float exponent2(const float4& abco, float dx, float d
                      __fmaf_rn(__fmul_rn(abco.z, dy), dy, __fmul_rn(__fmul_rn(abco.y, dx), dy)));
 }
 
-// Next tile for this CTA: its own (grid schedule, first call only) or the next
-// entry of the work order (persistent schedule). Returns -1 when done.
+// Next tile for this CTA: its own (grid schedule, first call only: tile
+// blockIdx.x, or entry blockIdx.x of the work order in the ordered-grid
+// schedule) or the next entry of the work order (persistent schedule, with
+// the counter). Returns -1 when done.
 __device__ __forceinline__ int next_tile(const uint32_t* __restrict__ order, uint32_t* counter, int n_tiles,
                                          bool first, int* s_item) {
-    if (!order) return first ? (int)blockIdx.x : -1;
+    if (!counter) return first ? (order ? (int)order[blockIdx.x] : (int)blockIdx.x) : -1;
     if (threadIdx.x == 0) {
         const uint32_t it = atomicAdd(counter, 1u);
         *s_item = it < (uint32_t)n_tiles ? (int)order[it] : -1;
@@ -516,8 +518,9 @@ static int render_fwd_impl(const gs_projected* p, const gs_pairs* pairs, const g
                            const gs_image* out, void* ws, size_t ws_bytes, void* stream, unsigned long long* counts) {
     if (!p || !pairs || !out || !out->color || !out->t_final || !out->n_contrib || !render_args_ok(f, cfg))
         return GS_ERR_INVALID_ARG;
-    const bool persistent = cfg->schedule == 1;
+    const bool persistent = cfg->schedule == 1, ordered = cfg->schedule == 2;
     if (persistent && (!pairs->order || !ws || ws_bytes < 256)) return GS_ERR_INVALID_ARG;
+    if (ordered && !pairs->order) return GS_ERR_INVALID_ARG;
     int n_tiles = f->tile_base[f->n_views];
     cudaStream_t s = (cudaStream_t)stream;
     if (counts && cudaMemsetAsync(counts, 0, 3 * sizeof(unsigned long long), s) != cudaSuccess) {
@@ -526,7 +529,7 @@ static int render_fwd_impl(const gs_projected* p, const gs_pairs* pairs, const g
     }
     if (n_tiles == 0) return GS_OK;
     uint32_t* counter = persistent ? (uint32_t*)ws : nullptr;
-    const uint32_t* order = persistent ? pairs->order : nullptr;
+    const uint32_t* order = persistent || ordered ? pairs->order : nullptr;
     if (persistent) cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     const RenderLaunch L = pick_fwd(cfg->tile, cfg->fwd_batch ? cfg->fwd_batch : default_fwd_batch(cfg->tile),
                                     out->depth != nullptr && !counts, counts != nullptr);
@@ -566,9 +569,9 @@ int launch_render_bwd(const gs_projected* p, const gs_pairs* pairs, const gs_fra
     if (!render_args_ok(f, cfg)) return GS_ERR_INVALID_ARG;
     int n_tiles = f->tile_base[f->n_views];
     if (n_tiles == 0) return GS_OK;
-    const bool persistent = cfg->schedule == 1;
-    if (persistent && !pairs->order) return GS_ERR_INVALID_ARG;
-    const uint32_t* order = persistent ? pairs->order : nullptr;
+    const bool persistent = cfg->schedule == 1, ordered = cfg->schedule == 2;
+    if ((persistent || ordered) && !pairs->order) return GS_ERR_INVALID_ARG;
+    const uint32_t* order = persistent || ordered ? pairs->order : nullptr;
     if (!persistent) counter = nullptr;
     if (persistent) cudaMemsetAsync(counter, 0, sizeof(uint32_t), s);
     const RenderLaunch L = pick_bwd(cfg->tile, cfg->bwd_batch ? cfg->bwd_batch : default_bwd_batch(cfg->tile));

@@ -35,9 +35,9 @@ class Rasterizer:
 
     def set_capacity(self, capacity: int):
         self.capacity = max(int(capacity), 1)
-        # the tile work order is only read by the persistent schedule; without it gs_sort skips that sort
+        # the tile work order is only read by schedules 1 and 2; without it gs_sort skips that sort
         self.pairs = gs.Pairs.alloc(self.items, self.n_tiles, self.capacity, self.device,
-                                    with_order=self.cfg.schedule == 1)
+                                    with_order=self.cfg.schedule in (1, 2))
         self.ws_sort = gs.workspace(gs.gs_sort_workspace_size(self.n, self.f, self.capacity), self.device)
         self.ws_bwd = gs.workspace(gs.gs_backward_workspace_size(self.n, self.f, self.capacity), self.device)
 

@@ -36,11 +36,12 @@ def test_descends_each_coordinate_in_order(monkeypatch):
 
     best, table, seen = run_with_cost(monkeypatch, cost)
     assert best == (16, 128, 64, 1)
-    # tiles first, then the schedule at the best tile, then fwd depths, then bwd depths
+    # tiles first, then the schedules (persistent, ordered grid) at the best tile, then fwd depths,
+    # then bwd depths
     assert seen[:3] == [(8, 0, 0, 0), (16, 0, 0, 0), (32, 0, 0, 0)]
-    assert seen[3] == (16, 0, 0, 1)
-    assert seen[4:7] == [(16, fb, 0, 1) for fb in autotune.FWD_BATCHES[16]]
-    assert seen[7:] == [(16, 128, bb, 1) for bb in autotune.BWD_BATCHES[16]]
+    assert seen[3:5] == [(16, 0, 0, 1), (16, 0, 0, 2)]
+    assert seen[5:8] == [(16, fb, 0, 1) for fb in autotune.FWD_BATCHES[16]]
+    assert seen[8:] == [(16, 128, bb, 1) for bb in autotune.BWD_BATCHES[16]]
     assert len(table) == len(seen) and all(len(row) == 5 for row in table)
 
 
@@ -53,6 +54,14 @@ def test_failed_configs_are_never_chosen(monkeypatch):
 
     best, _, _ = run_with_cost(monkeypatch, cost)
     assert best[0] == 16 and best[2] != 32 and best[1] == 256
+
+
+def test_ordered_grid_schedule_chosen_when_fastest(monkeypatch):
+    def cost(tile, fb, bb, sched):
+        return {8: 14.0, 16: 11.0, 32: 22.0}[tile] - {0: 0.0, 1: 0.1, 2: 0.2}[sched]
+
+    best, _, _ = run_with_cost(monkeypatch, cost)
+    assert best == (16, 0, 0, 2)
 
 
 def test_defaults_kept_when_nothing_improves(monkeypatch):

@@ -410,7 +410,7 @@ def test_multiview_sh3_mip_filter_end_to_end():
 
 
 @pytest.mark.parametrize("tile,schedule,fb,bb", [(8, 0, 64, 256), (8, 1, 256, 64), (16, 1, 64, 32),
-                                                 (32, 0, 128, 32), (32, 1, 256, 32)])
+                                                 (16, 2, 256, 64), (32, 0, 128, 32), (32, 1, 256, 32)])
 def test_tiles_batches_schedules_end_to_end(tile, schedule, fb, bb):
     """Every tile size (8, 16, 32), staging depth and both render schedules
     give the oracle's images and gradients (the oracle at the same tile size)."""
@@ -503,7 +503,7 @@ def test_720p_200k_end_to_end():
     compare_views(sc, [cam], 3)
 
 
-@pytest.mark.parametrize("schedule", [0, 1])
+@pytest.mark.parametrize("schedule", [0, 1, 2])
 def test_depth_channel_matches_oracle(schedule):
     """The optional depth-integral output of the forward pass against the
     oracle (three views of different sizes, SH3), with colour and transmittance
