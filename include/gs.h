@@ -119,6 +119,13 @@ int gs_frame_init(gs_frame* f, int32_t n_views, const int32_t* width, const int3
  *   scale    [n][4]  log-scales sx, sy, sz, unused
  *   quat     [n][4]  w, x, y, z (normalised inside)
  *   sh       [n][48] SH coefficient k (k = l^2 + l + m) of channel c at sh[48 g + 3 k + c]
+ *   filter3d [n]     optional (NULL: off): variance v of the 3-D smoothing filter of
+ *                    each Gaussian (Mip-Splatting's 3-D filter, the "proper filtering"
+ *                    of Sec. 4.3; see gs_filter3d). With it, gs_project renders the
+ *                    covariance Sigma + v I (scales sqrt(s^2 + v), same rotation) with
+ *                    the opacity multiplied by sqrt(det Sigma / det(Sigma + v I)) =
+ *                    prod_i s_i / sqrt(s_i^2 + v), and gs_project_bwd differentiates
+ *                    through both (v is a constant of the step)
  * Each row must be 16-byte aligned. */
 typedef struct gs_gaussians {
     float* mean_opa;
@@ -126,7 +133,19 @@ typedef struct gs_gaussians {
     float* quat;
     float* sh;
     int64_t n;
+    const float* filter3d;
 } gs_gaussians;
+
+/* Variance of the 3-D smoothing filter of every Gaussian (Mip-Splatting's 3-D
+ * filter, the "proper filtering" of Sec. 4.3) from the training cameras cams
+ * [n_views] (device): nu = the largest sampling rate fx / z over the views in
+ * which the mean lies in front of near_z and projects inside the image
+ * enlarged by 15% on each side, filter3d[g] = s2 / nu^2 (s2 = 0.2 in
+ * Mip-Splatting); a Gaussian no view samples gets the largest variance of the
+ * sampled ones (0 if none is sampled). Recompute when the cameras or the set
+ * change. ws: 256 bytes of device scratch. Only mean_opa of g is read. */
+int gs_filter3d(const gs_gaussians* g, const gs_camera* cams, int32_t n_views, float near_z, float s2,
+                float* filter3d, void* ws, size_t ws_bytes, void* stream);
 
 /* Per (view, Gaussian) projection outputs, n_views * n items:
  *   mean2d    [items][2]  u, v in pixels

@@ -226,6 +226,94 @@ def pose_jacobian(scene, cam, cfg: Config) -> np.ndarray:
     return jac
 
 
+# ---------------------------------------------------------------------------
+# 3-D smoothing filter (Mip-Splatting's 3-D filter; the "proper filtering" of
+# Sec. 4.3). The filter adds v I to the 3-D covariance and scales the opacity by
+# sqrt(det Sigma / det(Sigma + v I)). With Sigma = R diag(s^2) R^T this is the
+# covariance of scales sqrt(s^2 + v) and the factor prod s / sqrt(s^2 + v), so
+# the filtered Gaussian is a Gaussian of the unfiltered model with new scales
+# and opacity: the oracle renders that one and carries its gradients back.
+# ---------------------------------------------------------------------------
+
+def filter3d_variance(scene, cams, near_z=0.2, s2=0.2, margin=1e-6):
+    """Per Gaussian v = s2 / nu^2, nu = max over the cameras in which the mean
+    is in front of near_z and projects inside the image enlarged by 15% on
+    each side of fx / z; Gaussians no camera samples take the largest v of the
+    sampled ones (0 if none). Returns (v, ambiguous: a visibility test or the
+    maximum within `margin` relative of its threshold)."""
+    mu = np.asarray(scene.mean_opa, np.float64)[:, :3]
+    n = mu.shape[0]
+    nu = np.zeros(n)
+    amb = np.zeros(n, bool)
+    rates = []
+    for c in cams:
+        R = np.asarray(c["R"], np.float64).reshape(3, 3)
+        t = np.asarray(c["t"], np.float64)
+        p = mu @ R.T + t
+        z = p[:, 2]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            u = c["fx"] * p[:, 0] / z + c["cx"]
+            w = c["fy"] * p[:, 1] / z + c["cy"]
+            W, H = c["width"], c["height"]
+            inside = (z > near_z) & (u >= -0.15 * W) & (u <= 1.15 * W) & (w >= -0.15 * H) & (w <= 1.15 * H)
+            edge = (np.abs(z - near_z) < margin * near_z) | (np.abs(u + 0.15 * W) < margin * W) | \
+                   (np.abs(u - 1.15 * W) < margin * W) | (np.abs(w + 0.15 * H) < margin * H) | \
+                   (np.abs(w - 1.15 * H) < margin * H)
+            rate = np.where(inside, c["fx"] / z, 0.0)
+        amb |= edge & (z > 0)
+        rates.append(rate)
+    rates = np.array(rates)
+    nu = rates.max(axis=0)
+    seen = nu > 0
+    v = np.zeros(n)
+    v[seen] = s2 / nu[seen] ** 2
+    if seen.any():
+        v[~seen] = v[seen].max()
+    # two views with nearly equal rates: FP32 may pick either (values agree to the margin)
+    return v, amb
+
+
+def filtered_scene(scene, v):
+    """The scene whose unfiltered Gaussians equal the 3-D-filtered ones: log-scales
+    0.5 log(s^2 + v), opacity logit of sigmoid(logit) prod s / sqrt(s^2 + v); FP64."""
+    mo = np.array(scene.mean_opa, np.float64)
+    ls = np.array(scene.scale, np.float64)
+    v = np.asarray(v, np.float64)
+    s2 = np.exp(2 * ls[:, :3])
+    p2 = s2 + v[:, None]
+    f3 = np.prod(np.sqrt(s2 / p2), axis=1)
+    o = 1.0 / (1.0 + np.exp(-mo[:, 3]))
+    of = o * f3
+    mo[:, 3] = np.log(of) - np.log1p(-of)
+    ls[:, :3] = 0.5 * np.log(p2)
+    return type(scene)(mo, ls, np.asarray(scene.quat, np.float64), np.asarray(scene.sh, np.float64),
+                       scene.sh_degree)
+
+
+def filter3d_chain(scene, v, g, absolute=False):
+    """Gradients with respect to the filtered scene's log-scales and logits
+    (g["log_scale"] [n, 3], g["logit"] [n]) carried back to the original
+    parameters: d log s'_i / d log s_i = s_i^2 / (s_i^2 + v); the filtered logit
+    l' = logit(o f3) has dl'/dl = (1 - o) / (1 - o f3) and
+    dl'/d log s_i = (v / (s_i^2 + v)) / (1 - o f3). Other keys pass through.
+    absolute: the same with |g| (every Jacobian entry is >= 0, so this carries
+    bounds)."""
+    ls = np.asarray(scene.scale, np.float64)[:, :3]
+    lo = np.asarray(scene.mean_opa, np.float64)[:, 3]
+    v = np.asarray(v, np.float64)
+    s2 = np.exp(2 * ls)
+    p2 = s2 + v[:, None]
+    f3 = np.prod(np.sqrt(s2 / p2), axis=1)
+    o = 1.0 / (1.0 + np.exp(-lo))
+    one_m = 1.0 - o * f3
+    gs_ = np.abs(g["log_scale"]) if absolute else g["log_scale"]
+    gl = np.abs(g["logit"]) if absolute else g["logit"]
+    out = dict(g)
+    out["log_scale"] = gs_ * (s2 / p2) + (gl / one_m)[:, None] * (v[:, None] / p2)
+    out["logit"] = gl * (1.0 - o) / one_m
+    return out
+
+
 def _subset(scene, idx):
     return type(scene)(scene.mean_opa[idx], scene.scale[idx], scene.quat[idx], scene.sh[idx], scene.sh_degree)
 

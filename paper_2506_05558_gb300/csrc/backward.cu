@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_item_partials(
 template <int SHD>
 __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
     const float4* __restrict__ mean_opa, const float4* __restrict__ scale, const float4* __restrict__ quat,
-    const float4* __restrict__ sh, int64_t n, const gs_camera* __restrict__ cams, gs_frame f, gs_config cfg,
+    const float4* __restrict__ sh, int64_t n, const float* __restrict__ filter3d, const gs_camera* __restrict__ cams,
+    gs_frame f, gs_config cfg,
     const int32_t* __restrict__ n_tiles, const float4* __restrict__ rec, float4* __restrict__ g_mean_opa,
     float4* __restrict__ g_scale, float4* __restrict__ g_quat, float4* __restrict__ g_sh,
     uint8_t* __restrict__ visible, float* __restrict__ pose_part) {
@@ -110,8 +111,22 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
     Rq[0] = 1.f - 2.f * (qy * qy + qz * qz); Rq[1] = 2.f * (qx * qy - qw * qz); Rq[2] = 2.f * (qx * qz + qw * qy);
     Rq[3] = 2.f * (qx * qy + qw * qz); Rq[4] = 1.f - 2.f * (qx * qx + qz * qz); Rq[5] = 2.f * (qy * qz - qw * qx);
     Rq[6] = 2.f * (qx * qz - qw * qy); Rq[7] = 2.f * (qy * qz + qw * qx); Rq[8] = 1.f - 2.f * (qx * qx + qy * qy);
-    const float sv[3] = {expf(s4.x), expf(s4.y), expf(s4.z)};
+    // with the 3-D filter the projection sees scales s' = sqrt(s^2 + v) and the opacity
+    // factor f3 = prod s / s'; d log s' / d log s = s^2 / s'^2, d log f3 / d log s = v / s'^2
+    float sv[3] = {expf(s4.x), expf(s4.y), expf(s4.z)};
+    float fv = 0.f, f3 = 1.f, dsq[3] = {1.f, 1.f, 1.f};
+    if (filter3d && valid) {
+        fv = filter3d[g];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            const float p2 = sv[k] * sv[k] + fv, p = sqrtf(p2);
+            dsq[k] = sv[k] * sv[k] / p2;
+            f3 *= sv[k] / p;
+            sv[k] = p;
+        }
+    }
     const float opa = 1.f / (1.f + expf(-mo.w));
+    float a3 = 0.f;  // sum over views of dL/d(opacity) x the 2-D filter factor
     const float4* shg = sh + 12 * g;
     // per-Gaussian sums over the views (in view order)
     float am[3] = {0.f, 0.f, 0.f}, alogit = 0.f, als[3] = {0.f, 0.f, 0.f}, aq[4] = {0.f, 0.f, 0.f, 0.f};
@@ -228,7 +243,7 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
                 const float k2 = M0[0] * M1[1] - M0[1] * M1[0];
                 rho = (k0 * k0 + k1 * k1 + k2 * k2) * idet;
                 fmip = sqrtf(rho > 1e-6f ? rho : 1e-6f);
-                if (rho > 1e-6f) g_rho = dop * opa / (2.f * fmip);  // dL/drho through opacity o f
+                if (rho > 1e-6f) g_rho = dop * f3 * opa / (2.f * fmip);  // dL/drho through opacity o f
             }
 
             // conic = S^-1: dL/dS = -Q dL/dQ Q, dL/dQ = [[dA, dB/2], [dB/2, dC]]
@@ -305,7 +320,8 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
             am[0] += gmx + c.R[0] * gpx + c.R[3] * gpy + c.R[6] * gpz;
             am[1] += gmy + c.R[1] * gpx + c.R[4] * gpy + c.R[7] * gpz;
             am[2] += gmz + c.R[2] * gpx + c.R[5] * gpy + c.R[8] * gpz;
-            alogit += dop * fmip * opa * (1.f - opa);
+            alogit += dop * f3 * fmip * opa * (1.f - opa);
+            a3 += dop * fmip;
             // pose, left perturbation: dp = rho + phi x p, dT = phi^ T
             pose[0] += gpx; pose[1] += gpy; pose[2] += gpz;
             pose[3] += y * gpz - z * gpy;
@@ -337,7 +353,10 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
     }
     if (!valid) return;
     float4 om = make_float4(am[0], am[1], am[2], alogit);
-    float4 os = make_float4(als[0], als[1], als[2], 0.f);
+    // back from the filtered scales s' to the log-scales (the opacity factor f3 too)
+    const float l3 = a3 * f3 * opa;  // dL / d log f3
+    float4 os = make_float4(als[0] * dsq[0] + l3 * fv / (sv[0] * sv[0]), als[1] * dsq[1] + l3 * fv / (sv[1] * sv[1]),
+                            als[2] * dsq[2] + l3 * fv / (sv[2] * sv[2]), 0.f);
     float4 oq = make_float4(aq[0], aq[1], aq[2], aq[3]);
     if (cfg.accumulate) {
         const float4 a = g_mean_opa[g], b = g_scale[g], q = g_quat[g];
@@ -461,7 +480,8 @@ extern "C" int gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, cons
     const unsigned grid = (unsigned)ceil_div(g->n, kPBThreads);
 #define GS_PB(D)                                                                                                \
     k_project_bwd<D><<<grid, kPBThreads, 0, s>>>((const float4*)g->mean_opa, (const float4*)g->scale,          \
-                                                 (const float4*)g->quat, (const float4*)g->sh, g->n, cams, *f,  \
+                                                 (const float4*)g->quat, (const float4*)g->sh, g->n,           \
+                                                 g->filter3d, cams, *f,                                         \
                                                  *cfg, p->n_tiles, w.rec, (float4*)grads->mean_opa,               \
                                                  (float4*)grads->scale, (float4*)grads->quat,                     \
                                                  (float4*)grads->sh, grads->visible, w.pose_part)

@@ -14,7 +14,8 @@ namespace gs {
 
 __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean_opa, const float4* __restrict__ scale,
                                                  const float4* __restrict__ quat, const float4* __restrict__ sh,
-                                                 int64_t n, const gs_camera* __restrict__ cams, gs_frame f,
+                                                 int64_t n, const float* __restrict__ filter3d,
+                                                 const gs_camera* __restrict__ cams, gs_frame f,
                                                  gs_config cfg, float2* __restrict__ mean2d,
                                                  float4* __restrict__ conic_opa, float4* __restrict__ rgb_depth,
                                                  ushort4* __restrict__ rect, int32_t* __restrict__ n_tiles) {
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean
     const float z = c.R[6] * mo.x + c.R[7] * mo.y + c.R[8] * mo.z + c.t[2];
     bool keep = z > cfg.near_z;  // false for NaN
 
-    float a = 0.f, b = 0.f, cc = 0.f, det = 0.f, u = 0.f, vv = 0.f, fmip = 1.f;
+    float a = 0.f, b = 0.f, cc = 0.f, det = 0.f, u = 0.f, vv = 0.f, fmip = 1.f, f3 = 1.f;
     int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
     if (keep) {
         const float4 q4 = quat[g];
@@ -46,7 +47,13 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean
         Rq[0] = 1.f - 2.f * (qy * qy + qz * qz); Rq[1] = 2.f * (qx * qy - qw * qz); Rq[2] = 2.f * (qx * qz + qw * qy);
         Rq[3] = 2.f * (qx * qy + qw * qz); Rq[4] = 1.f - 2.f * (qx * qx + qz * qz); Rq[5] = 2.f * (qy * qz - qw * qx);
         Rq[6] = 2.f * (qx * qz - qw * qy); Rq[7] = 2.f * (qy * qz + qw * qx); Rq[8] = 1.f - 2.f * (qx * qx + qy * qy);
-        const float sx = expf(s4.x), sy = expf(s4.y), sz = expf(s4.z);
+        float sx = expf(s4.x), sy = expf(s4.y), sz = expf(s4.z);
+        if (filter3d) {  // 3-D filter: Sigma + v I has scales sqrt(s^2 + v); opacity x prod s / sqrt(s^2 + v)
+            const float fv = filter3d[g];
+            const float px = sqrtf(sx * sx + fv), py = sqrtf(sy * sy + fv), pz = sqrtf(sz * sz + fv);
+            f3 = (sx / px) * (sy / py) * (sz / pz);
+            sx = px; sy = py; sz = pz;
+        }
         // T = R_cam * Rq * diag(s): camera-space principal axes; Sc = T T^T
         float T[9];
 #pragma unroll
@@ -110,7 +117,7 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean
         float Y[16];
         sh_eval_basis(cfg.sh_degree, dx, dy, dz, Y);
         rgb = sh_color(sh + 12 * g, cfg.sh_degree, Y);
-        opa = fmip / (1.f + expf(-mo.w));
+        opa = f3 * fmip / (1.f + expf(-mo.w));
         keep = isfinite(rgb.x) && isfinite(rgb.y) && isfinite(rgb.z) && isfinite(opa);
         rgb.x = fmaxf(rgb.x, 0.f); rgb.y = fmaxf(rgb.y, 0.f); rgb.z = fmaxf(rgb.z, 0.f);
     }
@@ -125,6 +132,43 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean
     rgb_depth[item] = make_float4(rgb.x, rgb.y, rgb.z, z);
     rect[item] = make_ushort4((unsigned short)x0, (unsigned short)y0, (unsigned short)x1, (unsigned short)y1);
     n_tiles[item] = (x1 - x0) * (y1 - y0);
+}
+
+// 3-D filter variance (Mip-Splatting's 3-D smoothing filter): nu = the largest
+// sampling rate fx / z over the views in which the mean lies in front of the
+// near plane and projects inside the image enlarged by 15% on each side;
+// v = s2 / nu^2. Gaussians no view samples get -1 here and the largest v of the
+// sampled ones (the coarsest filter) in k_filter3d_unseen; vmax_bits collects
+// that largest v as float bits (positive floats order like their bits).
+__global__ void k_filter3d(const float4* __restrict__ mean_opa, int64_t n, const gs_camera* __restrict__ cams,
+                           int n_views, float near_z, float s2, float* __restrict__ out, unsigned* vmax_bits) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n) return;
+    const float4 mo = mean_opa[g];
+    float nu = 0.f;
+    for (int v = 0; v < n_views; v++) {
+        const gs_camera& c = cams[v];
+        const float x = c.R[0] * mo.x + c.R[1] * mo.y + c.R[2] * mo.z + c.t[0];
+        const float y = c.R[3] * mo.x + c.R[4] * mo.y + c.R[5] * mo.z + c.t[1];
+        const float z = c.R[6] * mo.x + c.R[7] * mo.y + c.R[8] * mo.z + c.t[2];
+        if (!(z > near_z)) continue;
+        const float u = c.fx * x / z + c.cx, w = c.fy * y / z + c.cy;
+        const float W = (float)c.width, H = (float)c.height;
+        if (!(u >= -0.15f * W && u <= 1.15f * W && w >= -0.15f * H && w <= 1.15f * H)) continue;
+        nu = fmaxf(nu, c.fx / z);
+    }
+    if (nu > 0.f) {
+        const float fv = s2 / (nu * nu);
+        out[g] = fv;
+        atomicMax(vmax_bits, __float_as_uint(fv));
+    } else {
+        out[g] = -1.f;
+    }
+}
+
+__global__ void k_filter3d_unseen(float* __restrict__ out, int64_t n, const unsigned* vmax_bits) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < n && out[g] < 0.f) out[g] = __uint_as_float(*vmax_bits);
 }
 
 }  // namespace gs
@@ -196,8 +240,26 @@ extern "C" int gs_project(const gs_gaussians* g, const gs_camera* cams, const gs
     const int64_t blocks = ceil_div(g->n, 256) * f->n_views;  // <= 2^22 * GS_MAX_VIEWS
     k_project<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
         (const float4*)g->mean_opa, (const float4*)g->scale, (const float4*)g->quat, (const float4*)g->sh, g->n,
-        cams, *f, *cfg, (float2*)out->mean2d, (float4*)out->conic_opa, (float4*)out->rgb_depth,
+        g->filter3d, cams, *f, *cfg, (float2*)out->mean2d, (float4*)out->conic_opa, (float4*)out->rgb_depth,
         (ushort4*)out->rect, out->n_tiles);
+    count_launch();
+    GS_CUDA_CHECK_LAUNCH();
+    return GS_OK;
+}
+
+extern "C" int gs_filter3d(const gs_gaussians* g, const gs_camera* cams, int32_t n_views, float near_z, float s2,
+                           float* filter3d, void* ws, size_t ws_bytes, void* stream) {
+    if (!g || g->n < 0 || !cams || n_views < 1 || n_views > 4096 || !(s2 > 0.f) || !filter3d) return GS_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < 256 || ((uintptr_t)ws & 255)) return GS_ERR_INVALID_ARG;
+    if (g->n == 0) return GS_OK;
+    if (!aligned16(g->mean_opa)) return GS_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned* vmax = (unsigned*)ws;
+    cudaMemsetAsync(vmax, 0, sizeof(unsigned), s);
+    const unsigned grid = (unsigned)ceil_div(g->n, 256);
+    k_filter3d<<<grid, 256, 0, s>>>((const float4*)g->mean_opa, g->n, cams, n_views, near_z, s2, filter3d, vmax);
+    count_launch();
+    k_filter3d_unseen<<<grid, 256, 0, s>>>(filter3d, g->n, vmax);
     count_launch();
     GS_CUDA_CHECK_LAUNCH();
     return GS_OK;

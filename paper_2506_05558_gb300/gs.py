@@ -26,7 +26,7 @@ GS_MAX_VIEWS = 64
 
 # Every entry point declared in include/gs.h.
 EXPORTS = [
-    "gs_config_default", "gs_frame_init", "gs_project", "gs_sort_workspace_size", "gs_sort",
+    "gs_config_default", "gs_frame_init", "gs_filter3d", "gs_project", "gs_sort_workspace_size", "gs_sort",
     "gs_render_workspace_size", "gs_render_fwd", "gs_render_fwd_count", "gs_probe_fma", "gs_probe_mufu",
     "gs_backward_workspace_size", "gs_render_bwd",
     "gs_adam_step", "gs_pose_step", "gs_l1_loss", "gs_composite_bwd", "gs_project_bwd", "gs_launch_count",
@@ -62,7 +62,7 @@ class gs_frame(C.Structure):
 
 class gs_gaussians(C.Structure):
     _fields_ = [("mean_opa", C.c_void_p), ("scale", C.c_void_p), ("quat", C.c_void_p), ("sh", C.c_void_p),
-                ("n", C.c_int64)]
+                ("n", C.c_int64), ("filter3d", C.c_void_p)]
 
 
 class gs_projected(C.Structure):
@@ -124,6 +124,8 @@ def lib():
             "gs_config_default": (None, [C.POINTER(gs_config)]),
             "gs_frame_init": (C.c_int, [C.POINTER(gs_frame), C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                         C.c_int32]),
+            "gs_filter3d": (C.c_int, [C.POINTER(gs_gaussians), P, C.c_int32, C.c_float, C.c_float, P, P,
+                                      C.c_size_t, P]),
             "gs_project": (C.c_int, [C.POINTER(gs_gaussians), P, C.POINTER(gs_frame), C.POINTER(gs_config),
                                      C.POINTER(gs_projected), P]),
             "gs_sort_workspace_size": (C.c_size_t, [C.c_int64, C.POINTER(gs_frame), C.c_int64]),
@@ -275,6 +277,7 @@ class Gaussians:
     scale: torch.Tensor     # [n, 4]
     quat: torch.Tensor      # [n, 4]
     sh: torch.Tensor        # [n, 48]
+    filter3d: torch.Tensor | None = None  # [n] variance of the 3-D smoothing filter, or None (off)
 
     @property
     def n(self) -> int:
@@ -291,7 +294,8 @@ class Gaussians:
         return Gaussians(z(4), z(4), z(4), z(48))
 
     def c(self) -> gs_gaussians:
-        return gs_gaussians(_ptr(self.mean_opa), _ptr(self.scale), _ptr(self.quat), _ptr(self.sh), self.n)
+        return gs_gaussians(_ptr(self.mean_opa), _ptr(self.scale), _ptr(self.quat), _ptr(self.sh), self.n,
+                            _ptr(self.filter3d))
 
 
 @dataclass
@@ -385,6 +389,13 @@ def workspace(nbytes: int, device="cuda") -> torch.Tensor:
 # ---------------------------------------------------------------------------
 # Entry points (same names as the C ABI)
 # ---------------------------------------------------------------------------
+
+def gs_filter3d(g: Gaussians, cams: torch.Tensor, n_views: int, out: torch.Tensor, ws: torch.Tensor,
+                near_z: float = 0.2, s2: float = 0.2, stream=None):
+    gc = g.c()
+    _check(lib().gs_filter3d(C.byref(gc), _ptr(cams), n_views, near_z, s2, _ptr(out), _ptr(ws), ws.numel(),
+                             _stream(stream)), "gs_filter3d")
+
 
 def gs_project(g: Gaussians, cams: torch.Tensor, f: gs_frame, cfg: gs_config, out: Projected, stream=None):
     gc, pc = g.c(), out.c()

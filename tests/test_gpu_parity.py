@@ -209,10 +209,13 @@ def test_render_bwd_deterministic():
 # End to end: project -> sort -> render -> adjoint with pose gradients
 # ---------------------------------------------------------------------------
 
-def run_views(sc, cams, sh_degree, dLs=None, seed=0, pose_through_sh=0, bg=(0.0, 0.0, 0.0), **launch):
+def run_views(sc, cams, sh_degree, dLs=None, seed=0, pose_through_sh=0, bg=(0.0, 0.0, 0.0), filter3d=None,
+              **launch):
     sizes = [(c["width"], c["height"]) for c in cams]
     cfg = gs.config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg, **launch)
     g = gs.Gaussians.from_scene(sc)
+    if filter3d is not None:
+        g.filter3d = t32(filter3d)
     camt = gs.cameras_tensor(cams)
     r = Rasterizer(sc.n, sizes, capacity=1024, cfg=cfg)
     r.fit_capacity(g, camt)
@@ -252,7 +255,8 @@ def last_contributor_tied(view, w, h, tile):
 
 
 def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), max_amb_frac=0.3, max_excl_frac=0.05,
-                  dLs=None, grad="l1", mip=0, margins=None, lam=FP32_LAMBDA, max_pose_share=POSE_SHARE, **launch):
+                  dLs=None, grad="l1", mip=0, margins=None, lam=FP32_LAMBDA, max_pose_share=POSE_SHARE, filter3d=None,
+                  **launch):
     """GPU vs oracle on every view: projection, image, n_contrib, the 2D adjoint
     per item, every visible Gaussian's parameter gradients and the pose
     gradient of each view.
@@ -269,7 +273,15 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
     colour clamp: the adjoint's own path may differ) are left out, and
     counted. With the workload gradient the pose bound must stay below
     max_pose_share of |ref| + rms, except in a view where a Gaussian lies
-    within the FP32 uncertainty of the near plane (reported)."""
+    within the FP32 uncertainty of the near plane (reported).
+
+    filter3d (per-Gaussian variances): the GPU renders with the 3-D smoothing
+    filter; the oracle renders the equivalent unfiltered scene
+    (O.filtered_scene) and its log-scale and logit gradients, and their
+    bounds, are carried back to the original parameters (O.filter3d_chain)."""
+    sc_in = sc
+    if filter3d is not None:
+        sc = O.filtered_scene(sc_in, filter3d)
     dil = 0.1 if mip else 0.3
     tile = launch.get("tile", 16)
     ocfg = O.Config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg, tile=tile, mip_filter=mip,
@@ -282,8 +294,8 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
         else:
             rng = np.random.default_rng(0)
             dLs = [rng.standard_normal((3, c["height"], c["width"])) for c in cams]
-    r, dLs, d_proj = run_views(sc, cams, sh_degree, dLs=dLs, pose_through_sh=pose_through_sh, bg=bg, mip_filter=mip,
-                               dilation=dil, **launch)
+    r, dLs, d_proj = run_views(sc_in, cams, sh_degree, dLs=dLs, pose_through_sh=pose_through_sh, bg=bg,
+                               mip_filter=mip, dilation=dil, filter3d=filter3d, **launch)
     n = sc.n
     keys = ("mean", "logit", "log_scale", "quat", "sh")
     ref = {k: 0.0 for k in keys}
@@ -359,6 +371,9 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
         # wide in front of everything: the pose bound of such a view is that large, and is reported
         if workload and bb["near_plane"] == 0:
             assert share <= max_pose_share, (v, share)
+    if filter3d is not None:
+        ref = O.filter3d_chain(sc_in, filter3d, ref)
+        bnd = O.filter3d_chain(sc_in, filter3d, bnd, absolute=True)
     keep = vis_any & ~excl
     gr = r.grads
     mo = gr.mean_opa.cpu().numpy()
@@ -400,6 +415,28 @@ def test_multiview_sh3_end_to_end(through_sh, grad):
     the workload's L1 gradient or standard normal noise."""
     sc, cams, _ = synth.multiview_scene(seed=5, n=20000, n_views=3, sizes=[(200, 120), (131, 77), (96, 160)])
     compare_views(sc, cams, 3, pose_through_sh=through_sh, grad=grad)
+
+
+@pytest.mark.parametrize("mip", [0, 1])
+def test_filter3d_end_to_end(mip):
+    """The 3-D smoothing filter (with and without the 2-D filter): gs_filter3d's
+    variances from the three cameras against the oracle's sampling-rate rule,
+    then projection, images, adjoint and every gradient against the oracle's
+    equivalent unfiltered scene, the log-scale and logit gradients carried back
+    through the filter."""
+    sc, cams, _ = synth.multiview_scene(seed=5, n=20000, n_views=3, sizes=[(200, 120), (131, 77), (96, 160)])
+    g = gs.Gaussians.from_scene(sc)
+    out = torch.zeros(sc.n, device="cuda")
+    gs.gs_filter3d(g, gs.cameras_tensor(cams), len(cams), out, gs.workspace(256))
+    torch.cuda.synchronize()
+    v_ref, amb = O.filter3d_variance(sc, cams, margin=1e-5)
+    v_gpu = out.cpu().numpy()
+    ok = ~amb
+    assert ok.mean() > 0.99
+    np.testing.assert_allclose(v_gpu[ok], v_ref[ok], rtol=1e-5)
+    # the scene's own scales are about e^-4 = 0.018 m; v makes the filter matter for the distant ones
+    assert np.median(v_ref / np.exp(2 * sc.scale[:, :3].astype(np.float64)).min(1)) > 0.05
+    compare_views(sc, cams, 3, mip=mip, filter3d=v_ref)
 
 
 def test_multiview_sh3_mip_filter_end_to_end():
