@@ -217,32 +217,48 @@ __global__ void k_sum_partials(const float* __restrict__ p, int n, float* __rest
     if (threadIdx.x == 0) *out = s[0];
 }
 
-// Padded bf16 copies W [Ro][Ci] and W^T [Ci][Ro] of a master W [rv][cv].
-__global__ void k_weight_cast(const float* __restrict__ Wm, int rv, int cv, int Ro, int Ci,
-                              __nv_bfloat16* __restrict__ Wb, __nv_bfloat16* __restrict__ Wt) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= Ro * Ci) return;
-    const int r = i / Ci, c = i % Ci;
-    const float v = (r < rv && c < cv) ? Wm[r * cv + c] : 0.f;
+// The four layers' casts in one launch: thread i of the concatenated padded
+// matrices finds its layer from the running sizes.
+struct CastAll {
+    const float* Wm[4];
+    __nv_bfloat16 *Wb[4], *Wt[4];
+    int rv[4], cv[4], Ro[4], Ci[4];
+    int64_t end[4];  // exclusive running sums of Ro * Ci
+};
+__global__ void k_weight_cast_all(CastAll a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int l = 0;
+    while (l < 4 && i >= a.end[l]) l++;
+    if (l == 4) return;
+    const int64_t j = i - (l > 0 ? a.end[l - 1] : 0);
+    const int r = (int)(j / a.Ci[l]), c = (int)(j % a.Ci[l]);
+    const float v = (r < a.rv[l] && c < a.cv[l]) ? a.Wm[l][r * a.cv[l] + c] : 0.f;
     const __nv_bfloat16 b = __float2bfloat16_rn(v);
-    Wb[i] = b;
-    Wt[(int64_t)c * Ro + r] = b;
+    a.Wb[l][j] = b;
+    a.Wt[l][(int64_t)c * a.Ro[l] + r] = b;
 }
 
-// Adam on n fp32 values (masters), bias corrections from the step number.
-__global__ void k_mlp_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
-                           float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps, int32_t step,
-                           const int32_t* __restrict__ step_dev) {
+// Adam over all eight parameter tensors in one launch; the gradients are flat
+// in the order w1, b1, ..., w4, b4 (seg_end: exclusive running sizes).
+struct AdamAll {
+    float *p[8], *m[8], *v[8];
+    int64_t seg_end[8];
+};
+__global__ void k_mlp_adam_all(AdamAll a, const float* __restrict__ g, float lr, float b1, float b2, float eps,
+                               int32_t step, const int32_t* __restrict__ step_dev) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    int k = 0;
+    while (k < 8 && i >= a.seg_end[k]) k++;
+    if (k == 8) return;
+    const int64_t j = i - (k > 0 ? a.seg_end[k - 1] : 0);
     const float t = step_dev ? (float)*step_dev : (float)step;
     const float bc1 = 1.f - powf(b1, t), bc2 = 1.f - powf(b2, t);
     const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
-    m[i] = mi;
-    v[i] = vi;
-    p[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+    const float mi = b1 * a.m[k][j] + (1.f - b1) * gi;
+    const float vi = b2 * a.v[k][j] + (1.f - b2) * gi * gi;
+    a.m[k][j] = mi;
+    a.v[k][j] = vi;
+    a.p[k][j] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
 }
 
 // ---------------------------------------------------------------------------
@@ -303,6 +319,9 @@ static MlpWs carve_mlp(char* base, size_t cap, int64_t M, size_t* used) {
 
 int mlp_forward_fused(const float* const* w, const float* const* b, const float* image, int W, int H, float* out,
                       cudaStream_t s);
+int mlp_train_forward_fused(const float* const* w, const float* const* b, const float* image, int W, int H,
+                            __nv_bfloat16* Xt, float* const* Z, __nv_bfloat16* const* Ht, float* Z3, int64_t Mp,
+                            cudaStream_t s);
 
 struct MlpPtrs {
     float* w[4];
@@ -328,11 +347,35 @@ static bool params_ok(const gs_mlp_params* p) {
 
 // Forward: features, 4 GEMMs with their epilogues; Y and dY written by the loss
 // kernel when targets are given.
+static void cast_weights(const MlpPtrs& P, const MlpWs& w, cudaStream_t s) {
+    CastAll a;
+    int64_t acc = 0;
+    for (int l = 0; l < 4; l++) {
+        a.Wm[l] = P.w[l];
+        a.Wb[l] = w.Wb[l];
+        a.Wt[l] = w.Wt[l];
+        a.rv[l] = kRv[l]; a.cv[l] = kCv[l]; a.Ro[l] = kRo[l]; a.Ci[l] = kCi[l];
+        acc += (int64_t)kRo[l] * kCi[l];
+        a.end[l] = acc;
+    }
+    k_weight_cast_all<<<(unsigned)ceil_div(acc, 256), 256, 0, s>>>(a);
+    count_launch();
+}
+
 static int mlp_forward(const MlpPtrs& P, const float* image, int W, int H, const MlpWs& w, int path,
                        const float* targets, float w_depth, float w_scale, float* out, cudaStream_t s) {
     const int64_t M = w.M, Mp = w.Mp;
-    for (int l = 0; l < 4; l++)
-        GS_LAUNCH1(k_weight_cast, kRo[l] * kCi[l], P.w[l], kRv[l], kCv[l], kRo[l], kCi[l], w.Wb[l], w.Wt[l]);
+    cast_weights(P, w, s);
+    if (path == 1 && targets && ((uintptr_t)image & 15) == 0) {
+        // training forward on the tensor cores in one persistent kernel (weights resident in shared
+        // memory), writing the tensors the backward reads; then the loss as below
+        int rc = mlp_train_forward_fused(P.w, P.b, image, W, H, w.Xt, w.Z, w.Ht, w.Z[3], Mp, s);
+        if (rc != GS_OK) return rc;
+        k_mlp_loss<<<(unsigned)w.nb_loss, 256, 0, s>>>(w.Z[3], P.b[3], targets, M, Mp, w_depth, w_scale, out, w.dY,
+                                                        w.dZ4, w.dZ4t, w.loss_part);
+        count_launch();
+        return GS_OK;
+    }
     k_mlp_features<<<dim3((unsigned)ceil_div(kInPad, 32), (unsigned)ceil_div(Mp, 32)), dim3(32, 8), 0, s>>>(
         image, W, H, M, Mp, w.X, w.Xt);
     count_launch();
@@ -462,15 +505,20 @@ extern "C" int gs_mlp_train_step(const gs_mlp_params* p, const gs_mlp_params* m,
     }
     if (m) {
         const MlpPtrs Pm = ptrs(m), Pv = ptrs(v);
+        AdamAll a;
         int64_t off = 0;
         for (int l = 0; l < 4; l++) {
             const int64_t nw = (int64_t)kRv[l] * kCv[l], nbias = kRv[l];
-            GS_LAUNCH1(k_mlp_adam, nw, P.w[l], w.grad + off, Pm.w[l], Pv.w[l], nw, cfg->lr, cfg->beta1, cfg->beta2,
-                       cfg->eps, step, step_dev);
-            GS_LAUNCH1(k_mlp_adam, nbias, P.b[l], w.grad + off + nw, Pm.b[l], Pv.b[l], nbias, cfg->lr, cfg->beta1,
-                       cfg->beta2, cfg->eps, step, step_dev);
-            off += nw + nbias;
+            a.p[2 * l] = P.w[l]; a.m[2 * l] = Pm.w[l]; a.v[2 * l] = Pv.w[l];
+            a.p[2 * l + 1] = P.b[l]; a.m[2 * l + 1] = Pm.b[l]; a.v[2 * l + 1] = Pv.b[l];
+            off += nw;
+            a.seg_end[2 * l] = off;
+            off += nbias;
+            a.seg_end[2 * l + 1] = off;
         }
+        k_mlp_adam_all<<<(unsigned)ceil_div(off, 256), 256, 0, s>>>(a, w.grad, cfg->lr, cfg->beta1, cfg->beta2,
+                                                                     cfg->eps, step, step_dev);
+        count_launch();
     }
     GS_CUDA_CHECK_LAUNCH();
     return GS_OK;

@@ -258,6 +258,13 @@ __device__ __forceinline__ uint4 pack8_bf16(const float* v) {
     return u;
 }
 
+// Element j (0..7) of eight packed bfloat16 values (j a compile-time constant in
+// unrolled loops, so the value stays in registers).
+__device__ __forceinline__ __nv_bfloat16 bf16_at(const uint4& u, int j) {
+    const uint32_t w = j < 2 ? u.x : j < 4 ? u.y : j < 6 ? u.z : u.w;
+    return __ushort_as_bfloat16((unsigned short)((j & 1) ? (w >> 16) : (w & 0xFFFFu)));
+}
+
 __device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.f + erff(z * 0.70710678118654752f)); }
 
 // W [rows_valid][cols_valid] FP32 (nn.Linear layout) -> bf16 [rows][K] K-major at dst, zero padded.
@@ -276,11 +283,25 @@ __device__ void stage_weight(const float* __restrict__ Wm, int rows_valid, int c
     }
 }
 
+// What the training step's backward needs from the forward, written by the
+// TRAIN instantiation in the layouts of the GEMM-chain forward: the features
+// transposed (Xt [208][Mp], bf16), the pre-activations with their bias (Z[l]
+// [Mp][128] FP32, l < 3) and the activations transposed (Ht[l] [128][Mp], bf16),
+// and the output layer before its bias (Z3 [Mp][16] FP32); rows up to Mp.
+struct TrainFwdOut {
+    __nv_bfloat16* Xt;
+    float* Z[3];
+    __nv_bfloat16* Ht[3];
+    float* Z3;
+    int64_t Mp;
+};
+
+template <bool TRAIN>
 __global__ void __launch_bounds__(kFThreads, 1) k_mlp_forward_tc(
     const float* __restrict__ image, int W, int H, const float* __restrict__ w1, const float* __restrict__ b1,
     const float* __restrict__ w2, const float* __restrict__ b2, const float* __restrict__ w3,
     const float* __restrict__ b3, const float* __restrict__ w4, const float* __restrict__ b4,
-    float* __restrict__ out) {
+    float* __restrict__ out, TrainFwdOut to) {
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tmem;
@@ -288,7 +309,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_forward_tc(
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nx = W >> 3, ny = H >> 3;
     const int64_t M = (int64_t)nx * ny;
-    const int64_t n_tiles = (M + kFM - 1) / kFM;
+    const int64_t n_tiles = TRAIN ? to.Mp / kFM : (M + kFM - 1) / kFM;
     const uint32_t bar = smem_u32(&s_bar);
     float* s_b = reinterpret_cast<float*>(sm + kFOffB);  // b1 | b2 | b3 | b4 (padded to 16)
 
@@ -346,7 +367,12 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_forward_tc(
 #pragma unroll
                 for (int e = 0; e < 8; e++) v[e] = 0.f;
             }
-            *reinterpret_cast<uint4*>(sm + kFOffX + kmajor_off(r, kc * 8, kFInPad)) = pack8_bf16(v);
+            const uint4 pk = pack8_bf16(v);
+            *reinterpret_cast<uint4*>(sm + kFOffX + kmajor_off(r, kc * 8, kFInPad)) = pk;
+            if (TRAIN) {  // X^T: for each of the 8 columns, consecutive threads write consecutive patches
+#pragma unroll
+                for (int e = 0; e < 8; e++) to.Xt[(int64_t)(kc * 8 + e) * to.Mp + p] = bf16_at(pk, e);
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
@@ -401,10 +427,33 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_forward_tc(
                         : "r"(trow + (uint32_t)c0));
                     asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                     float v[16];
+                    if (TRAIN) {
+                        const int64_t p = p0 + r;
+                        float zr[16];
 #pragma unroll
-                    for (int j = 0; j < 16; j++) v[j] = gelu_erf(__uint_as_float(u[j]) + s_b[l * kFHid + c0 + j]);
-                    *reinterpret_cast<uint4*>(sm + kFOffH + kmajor_off(r, c0, kFHid)) = pack8_bf16(v);
-                    *reinterpret_cast<uint4*>(sm + kFOffH + kmajor_off(r, c0 + 8, kFHid)) = pack8_bf16(v + 8);
+                        for (int j = 0; j < 16; j++) zr[j] = __uint_as_float(u[j]) + s_b[l * kFHid + c0 + j];
+                        float* Zl = l == 0 ? to.Z[0] : l == 1 ? to.Z[1] : to.Z[2];  // no dynamic index into the param
+                        float4* zd = reinterpret_cast<float4*>(Zl + p * kFHid + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; j++) zd[j] = make_float4(zr[4 * j], zr[4 * j + 1], zr[4 * j + 2], zr[4 * j + 3]);
+#pragma unroll
+                        for (int j = 0; j < 16; j++) v[j] = gelu_erf(zr[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; j++) v[j] = gelu_erf(__uint_as_float(u[j]) + s_b[l * kFHid + c0 + j]);
+                    }
+                    const uint4 h0 = pack8_bf16(v), h1 = pack8_bf16(v + 8);
+                    *reinterpret_cast<uint4*>(sm + kFOffH + kmajor_off(r, c0, kFHid)) = h0;
+                    *reinterpret_cast<uint4*>(sm + kFOffH + kmajor_off(r, c0 + 8, kFHid)) = h1;
+                    if (TRAIN) {  // H^T: per column, the warp's 32 consecutive patches
+                        const int64_t p = p0 + r;
+                        __nv_bfloat16* Hl = l == 0 ? to.Ht[0] : l == 1 ? to.Ht[1] : to.Ht[2];
+#pragma unroll
+                        for (int j = 0; j < 8; j++) {
+                            Hl[(int64_t)(c0 + j) * to.Mp + p] = bf16_at(h0, j);
+                            Hl[(int64_t)(c0 + 8 + j) * to.Mp + p] = bf16_at(h1, j);
+                        }
+                    }
                 }
             } else if (half == 0) {
                 uint32_t u[16];
@@ -417,7 +466,13 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_forward_tc(
                     : "r"(trow));
                 asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                 const int64_t p = p0 + r;
-                if (p < M) {
+                if (TRAIN) {  // the output layer before its bias, all 16 padded columns, every row up to Mp
+                    float4* zd = reinterpret_cast<float4*>(to.Z3 + p * kFOutPad);
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        zd[j] = make_float4(__uint_as_float(u[4 * j]), __uint_as_float(u[4 * j + 1]),
+                                            __uint_as_float(u[4 * j + 2]), __uint_as_float(u[4 * j + 3]));
+                } else if (p < M) {
 #pragma unroll
                     for (int j = 0; j < kFOut; j++) out[p * kFOut + j] = __uint_as_float(u[j]) + s_b[3 * kFHid + j];
                 }
@@ -435,22 +490,44 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_forward_tc(
     }
 }
 
-int mlp_forward_fused(const float* const* w, const float* const* b, const float* image, int W, int H, float* out,
-                      cudaStream_t s) {
+static int fused_sms() {
     static int n_sm = 0;
-    static bool attr_set = false;
-    if (!attr_set) {
+    if (n_sm == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFSmem);
-        attr_set = true;
+        cudaFuncSetAttribute(k_mlp_forward_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFSmem);
+        cudaFuncSetAttribute(k_mlp_forward_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFSmem);
     }
+    return n_sm > 0 ? n_sm : 1;
+}
+
+int mlp_forward_fused(const float* const* w, const float* const* b, const float* image, int W, int H, float* out,
+                      cudaStream_t s) {
+    const int n_sm = fused_sms();
     const int64_t M = (int64_t)(W / 8) * (H / 8);
     const int64_t n_tiles = (M + kFM - 1) / kFM;
     if (n_tiles == 0) return GS_OK;
     const int grid = (int)(n_tiles < n_sm ? n_tiles : n_sm);
-    k_mlp_forward_tc<<<grid, kFThreads, kFSmem, s>>>(image, W, H, w[0], b[0], w[1], b[1], w[2], b[2], w[3], b[3], out);
+    TrainFwdOut none{};
+    k_mlp_forward_tc<false><<<grid, kFThreads, kFSmem, s>>>(image, W, H, w[0], b[0], w[1], b[1], w[2], b[2], w[3],
+                                                            b[3], out, none);
+    count_launch();
+    return GS_OK;
+}
+
+// The training step's forward in one launch: as mlp_forward_fused, writing the
+// tensors the backward reads (Mp = patches rounded up to a multiple of 128).
+int mlp_train_forward_fused(const float* const* w, const float* const* b, const float* image, int W, int H,
+                            __nv_bfloat16* Xt, float* const* Z, __nv_bfloat16* const* Ht, float* Z3, int64_t Mp,
+                            cudaStream_t s) {
+    const int n_sm = fused_sms();
+    const int64_t n_tiles = Mp / kFM;
+    if (n_tiles == 0) return GS_OK;
+    const int grid = (int)(n_tiles < n_sm ? n_tiles : n_sm);
+    TrainFwdOut to{Xt, {Z[0], Z[1], Z[2]}, {Ht[0], Ht[1], Ht[2]}, Z3, Mp};
+    k_mlp_forward_tc<true><<<grid, kFThreads, kFSmem, s>>>(image, W, H, w[0], b[0], w[1], b[1], w[2], b[2], w[3],
+                                                           b[3], nullptr, to);
     count_launch();
     return GS_OK;
 }
