@@ -309,11 +309,10 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
                 part2[e] = 0.f;
             }
         }
-        // background seen through the final transmittance, folded into the "behind" term
-        const float bgr = Tf * cfg.bg[0], bgg = Tf * cfg.bg[1], bgb = Tf * cfg.bg[2];
-        // Sr, Sg, Sb: colour composited behind the current Gaussian plus the background
-        // seen through T_final
-        float T = Tf, Sr = bgr, Sg = bgg, Sb = bgb;
+        // gS = sum over channels of dL/dC_ch times the colour composited behind the
+        // current Gaussian plus the background seen through T_final: dL/dalpha needs
+        // only this dot product, so one scalar replaces three running colours
+        float T = Tf, gS = Tf * (gr * cfg.bg[0] + gg * cfg.bg[1] + gb * cfg.bg[2]);
         s_pix[w][lane] = make_float4(gr, gg, gb, 0.f);
         int nh = 0;    // hits recorded in this warp's table (warp-uniform)
         int myk = 0;   // the staged index of hit (lane % HB) of the table
@@ -405,9 +404,10 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
                         T = contrib ? T * inv : T;  // transmittance in front of this Gaussian
                         const float4 c = s_rgb[k];
                         const float wgt = contrib ? alpha * T : 0.f;
-                        const float dalpha = gr * (T * c.x - Sr * inv) + gg * (T * c.y - Sg * inv) +
-                                             gb * (T * c.z - Sb * inv);
-                        Sr += wgt * c.x; Sg += wgt * c.y; Sb += wgt * c.z;
+                        // dL/dalpha = sum_ch dL/dC_ch (T c_ch - S_ch / (1 - alpha))
+                        const float gc = gr * c.x + gg * c.y + gb * c.z;
+                        const float dalpha = T * gc - gS * inv;
+                        gS += wgt * gc;
                         // alpha clamped at alpha_max passes no gradient to the exponent or
                         // opacity; selects (not products with 0) keep a non-finite og or G
                         // of a lane outside the Gaussian out of the sums
