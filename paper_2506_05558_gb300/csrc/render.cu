@@ -382,7 +382,9 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
                 const int kk = k0 + lane;
                 const bool cand = kk < cnt && b0 + kk < warp_nc;
                 unsigned m = __ballot_sync(FULL, cand && wb.hits(s_box[cand ? kk : 0]));
-                unsigned written = 0;
+                const unsigned hits = m;
+                unsigned skipped = 0;  // hits where no pixel of the warp composites (rare)
+                const int ncb = nc - b0 - k0;  // this lane's contributors past the chunk start
                 while (m) {  // back to front inside the chunk
                     const int jb = 31 - __clz(m);
                     m &= ~(1u << jb);
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
                     const float alpha = fminf(cfg.alpha_max, og);
                     // same decisions as the forward pass: listed before this pixel's
                     // last contributor, exponent <= 0, alpha >= alpha_min
-                    const bool contrib = b0 + k < nc && !(e > 0.f) && alpha >= cfg.alpha_min;
+                    const bool contrib = jb < ncb && !(e > 0.f) && alpha >= cfg.alpha_min;
                     if (__any_sync(FULL, contrib)) {
                         // predicated adjoint: non-contributing lanes keep their
                         // state and add zeros
@@ -417,11 +419,12 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_bwd(gs_frame f, gs_confi
                         // over the warp's pixels when the table is full
                         s_tdw[w][nh][lane] = make_float2(dpow, wgt);
                         if (lane % kBwdHits == nh) myk = k;
-                        written |= 1u << jb;
                         if (++nh == kBwdHits) flush();
+                    } else {
+                        skipped |= 1u << jb;
                     }
                 }
-                if (lane == 0) s_hit[w][ch] = written;
+                if (lane == 0) s_hit[w][ch] = hits & ~skipped;
             }
             if (nh > 0) flush();
             __syncthreads();
