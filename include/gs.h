@@ -491,7 +491,8 @@ int gs_mlp_train_step(const gs_mlp_params* p, const gs_mlp_params* m, const gs_m
 
 /* The MLP's matrix product on its own, for testing the two tensor-core paths:
  * C [M][N] (ldc) = A [M][K] (lda) . B [N][K]^T (ldb); A, B bfloat16 (uint16
- * bit patterns), K-major; K, N multiples of 16, lda, ldb multiples of 8. */
+ * bit patterns), K-major; K, N multiples of 16, lda, ldb multiples of 8, ldc a
+ * multiple of 4 and C 16-byte aligned. */
 int gs_mlp_gemm_bf16(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc,
                      int32_t M, int32_t N, int32_t K, int32_t tensor_path, void* stream);
 

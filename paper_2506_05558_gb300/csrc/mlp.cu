@@ -189,7 +189,9 @@ __global__ void k_col_sum_part(const float* __restrict__ A, int64_t Mp, int N, f
     if (n >= N) return;
     const int64_t r0 = (int64_t)blockIdx.x * kColRows;
     float s = 0.f;
-    for (int64_t m = r0; m < r0 + kColRows && m < Mp; m++) s += A[m * N + n];
+    const int64_t m1 = min(r0 + kColRows, Mp);
+#pragma unroll 8
+    for (int64_t m = r0; m < m1; m++) s += A[m * N + n];  // loads batched, sum in row order
     part[(int64_t)blockIdx.x * N + n] = s;
 }
 
@@ -200,7 +202,8 @@ __global__ void k_split_sum(const float* __restrict__ part, int S, int R, int C,
     if (i >= Rv * Cv) return;
     const int r = i / Cv, c = i % Cv;
     float s = 0.f;
-    for (int z = 0; z < S; z++) s += part[((int64_t)z * R + r) * C + c];
+#pragma unroll 8
+    for (int z = 0; z < S; z++) s += part[((int64_t)z * R + r) * C + c];  // loads batched, sum in split order
     out[i] = s;
 }
 
@@ -527,7 +530,9 @@ extern "C" int gs_mlp_train_step(const gs_mlp_params* p, const gs_mlp_params* m,
 extern "C" int gs_mlp_gemm_bf16(const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb, float* C, int64_t ldc,
                                 int32_t M, int32_t N, int32_t K, int32_t tensor_path, void* stream) {
     if (!A || !B || !C || M <= 0 || N <= 0 || K <= 0 || (tensor_path != 0 && tensor_path != 1)) return GS_ERR_INVALID_ARG;
-    if (lda < K || ldb < K || ldc < N || (lda % 8) || (ldb % 8) || (K % 16) || (N % 16)) return GS_ERR_INVALID_ARG;
+    if (lda < K || ldb < K || ldc < N || (lda % 8) || (ldb % 8) || (K % 16) || (N % 16) || (ldc % 4) ||
+        ((uintptr_t)C & 15))
+        return GS_ERR_INVALID_ARG;
     const int rc = gemm_tn(tensor_path, (const __nv_bfloat16*)A, lda, (const __nv_bfloat16*)B, ldb, C, ldc, M, N, K,
                            K, 0, (cudaStream_t)stream);
     if (rc != GS_OK) return rc;

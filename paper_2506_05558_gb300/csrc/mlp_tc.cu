@@ -60,8 +60,7 @@ __global__ void __launch_bounds__(128) k_gemm_tn_tc(const __nv_bfloat16* __restr
     __shared__ __align__(8) uint64_t s_bar;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
-    uint8_t* sA = smem;                        // 128 x 64 bf16 = 16 KB
-    uint8_t* sB = smem + kTcM * kTcBK * 2;     // Nt x 64 bf16
+    uint8_t* sA = smem;  // two buffers of A (128 x 64 bf16) followed by B (Nt x 64 bf16)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t m0 = (int64_t)blockIdx.x * kTcM;
     const int64_t kb = (int64_t)blockIdx.z * k_per_split;
@@ -86,36 +85,51 @@ __global__ void __launch_bounds__(128) k_gemm_tn_tc(const __nv_bfloat16* __restr
     const uint32_t idesc = instr_desc_bf16(kTcM, Nt);
     uint32_t phase = 0;
     bool first = true;
-
-    for (int64_t k0 = kb; k0 < ke; k0 += kTcBK) {
-        // stage A (128 rows) and B (Nt rows) as 8x8 core matrices, zero-filled outside
-        const int rows_total = kTcM + Nt;
+    const int rows_total = kTcM + Nt;
+    const uint32_t buf_bytes = (uint32_t)rows_total * kTcBK * 2;
+    // stage k0 into buffer b: 16-byte cp.async copies (zero-filled outside the matrix), one commit group
+    auto issue_stage = [&](int64_t k0, int b) {
+        uint8_t* sAb = sA + b * buf_bytes;
+        uint8_t* sBb = sAb + kTcM * kTcBK * 2;
         for (int i = tid; i < rows_total * (kTcBK / 8); i += 128) {
             const int r = i / (kTcBK / 8), kc = i % (kTcBK / 8);
             const bool isA = r < kTcM;
             const int rr = isA ? r : r - kTcM;
             const int64_t grow = isA ? m0 + rr : rr;
             const int64_t gk = k0 + kc * 8;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
             const bool row_ok = isA ? grow < M : grow < N;
-            if (row_ok && gk + 8 <= ke) {
-                const __nv_bfloat16* src = (isA ? A + grow * lda : B + grow * ldb) + gk;
-                v = *reinterpret_cast<const uint4*>(src);
-            } else if (row_ok) {
+            uint8_t* dst = (isA ? sAb : sBb) + (uint32_t)(((rr >> 3) * (kTcBK / 8) + kc) * 128 + (rr & 7) * 16);
+            if (row_ok && gk < ke && gk + 8 > ke) {  // a K tail inside the chunk: element by element
                 __nv_bfloat16 tmp[8];
                 const __nv_bfloat16* src = (isA ? A + grow * lda : B + grow * ldb);
                 for (int e = 0; e < 8; e++) tmp[e] = (gk + e < ke) ? src[gk + e] : __float2bfloat16_rn(0.f);
-                v = *reinterpret_cast<uint4*>(tmp);
+                *reinterpret_cast<uint4*>(dst) = *reinterpret_cast<uint4*>(tmp);
+                continue;
             }
-            uint8_t* base = isA ? sA : sB;
-            const uint32_t off = (uint32_t)(((rr >> 3) * (kTcBK / 8) + kc) * 128 + (rr & 7) * 16);
-            *reinterpret_cast<uint4*>(base + off) = v;
+            const bool ok = row_ok && gk + 8 <= ke;
+            const __nv_bfloat16* src = ok ? (isA ? A + grow * lda : B + grow * ldb) + gk : A;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(dst)), "l"(src),
+                         "r"(ok ? 16 : 0)
+                         : "memory");
         }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    // double-buffered: the copies of slice s + 1 are in flight while slice s is
+    // waited for and multiplied; a buffer is refilled only after the MMA that
+    // read it has completed (the mbarrier wait at the end of its iteration)
+    if (kb < ke) issue_stage(kb, 0);
+    int buf = 0;
+    for (int64_t k0 = kb; k0 < ke; k0 += kTcBK) {
+        const bool more = k0 + kTcBK < ke;
+        if (more) issue_stage(k0 + kTcBK, buf ^ 1);
+        if (more) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+            const uint32_t a0 = smem_u32(sA + buf * buf_bytes), b0 = a0 + kTcM * kTcBK * 2;
 #pragma unroll
             for (int s = 0; s < kTcBK / 16; s++) {
                 const uint64_t ad = smem_desc(a0 + s * 256, 128, 1024);
@@ -139,9 +153,13 @@ __global__ void __launch_bounds__(128) k_gemm_tn_tc(const __nv_bfloat16* __restr
         }
         first = false;
         phase ^= 1u;
+        buf ^= 1;
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        if (s_fail) break;
+        if (s_fail) {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");  // no copy may land after the exit
+            break;
+        }
     }
 
     if (!s_fail && !first) {
@@ -159,10 +177,12 @@ __global__ void __launch_bounds__(128) k_gemm_tn_tc(const __nv_bfloat16* __restr
                   "=r"(r[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            if (row < M) {
+            if (row < M && c0 < N) {  // N and ldc are multiples of 16: whole 16-column groups, 128-bit stores
+                float4* dst = reinterpret_cast<float4*>(Cz + row * ldc + c0);
 #pragma unroll
-                for (int j = 0; j < 16; j++)
-                    if (c0 + j < N) Cz[row * ldc + c0 + j] = __uint_as_float(r[j]);
+                for (int j = 0; j < 4; j++)
+                    dst[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                         __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
             }
         }
     } else if (s_fail && tid == 0) {
@@ -181,7 +201,7 @@ int gemm_tn_tc(const __nv_bfloat16* A, int64_t lda, const __nv_bfloat16* B, int6
     if (Nt > kTcMaxN || M <= 0 || K <= 0) return GS_ERR_INVALID_ARG;
     uint32_t cols = 32;
     while (cols < (uint32_t)Nt) cols <<= 1;
-    const size_t smem = (size_t)(kTcM + Nt) * kTcBK * 2;
+    const size_t smem = 2 * (size_t)(kTcM + Nt) * kTcBK * 2;  // two stages
     static bool attr_set = false;
     if (!attr_set) {
         // at most ~115 KB of the SM's shared memory per CTA so that at most two
