@@ -340,27 +340,10 @@ def event_ms(torch, fn, reps):
     return a.elapsed_time(b) / reps
 
 
-def measure_rows(torch, gs, W, device, peaks, reps=10):
+def measure_mlp(torch, gs, device, peaks, img, Wd, Hd, rng, reps=10):
+    """The learned proposal on one frame: a training step (forward, loss,
+    backward, Adam) and an inference, on each tensor-core path."""
     out = {}
-    Wd, Hd = WIDTH, HEIGHT
-    hw = Wd * Hd
-    img = W["targets"][:3 * hw]
-    rng = np.random.default_rng(5)
-    depth = torch.tensor(rng.uniform(2, 40, hw).astype(np.float32), device=device)
-    cam0 = W["cams"][:72]
-    # a8: direct spawn sampling on a 1080p frame; the render reproduces the
-    # right half of the frame and is empty on the left, so the left half spawns
-    render = img.clone()
-    render.view(3, Hd, Wd)[:, :, :Wd // 2] = 0.0
-    sp = gs.Spawned.alloc(hw)
-    ws = gs.workspace(gs.gs_spawn_workspace_size(Wd, Hd), device)
-    ms = event_ms(torch, lambda: gs.gs_spawn_propose(img, render, depth, Wd, Hd, cam0, 1.0, 7, 0, sp, ws), reps)
-    n_sp = int(sp.count.item())
-    # image + render + depth read, flags/positions written and read, spawned rows written
-    bytes_ = (3 + 3 + 1) * 4 * hw + 16 * hw + n_sp * 240
-    out["spawn_propose"] = {"ms": ms, "bound": "hbm", "achieved": bytes_ / ms / 1e6, "unit": "GB/s",
-                            "frac": bytes_ / ms / 1e6 / peaks["hbm"], "spawned": n_sp}
-    # a10: learned proposal, one training step and one inference on a 1080p frame
     prng = np.random.default_rng(1)
     layers = [(prng.uniform(-1, 1, (o, i)) / np.sqrt(i), prng.uniform(-1, 1, o) / np.sqrt(i))
               for o, i in ((128, 194), (128, 128), (128, 128), (3, 128))]
@@ -385,6 +368,31 @@ def measure_rows(torch, gs, W, device, peaks, reps=10):
                                   "train_ms": t_ms, "infer_ms": f_ms, "train_tflops": tf, "infer_tflops": itf,
                                   "bound": "tensor", "peak": peaks["bf16"], "frac": tf / peaks["bf16"],
                                   "infer_frac": itf / peaks["bf16"], "patches": n_p}
+    return out
+
+
+def measure_rows(torch, gs, W, device, peaks, reps=10):
+    out = {}
+    Wd, Hd = WIDTH, HEIGHT
+    hw = Wd * Hd
+    img = W["targets"][:3 * hw]
+    rng = np.random.default_rng(5)
+    depth = torch.tensor(rng.uniform(2, 40, hw).astype(np.float32), device=device)
+    cam0 = W["cams"][:72]
+    # a8: direct spawn sampling on a 1080p frame; the render reproduces the
+    # right half of the frame and is empty on the left, so the left half spawns
+    render = img.clone()
+    render.view(3, Hd, Wd)[:, :, :Wd // 2] = 0.0
+    sp = gs.Spawned.alloc(hw)
+    ws = gs.workspace(gs.gs_spawn_workspace_size(Wd, Hd), device)
+    ms = event_ms(torch, lambda: gs.gs_spawn_propose(img, render, depth, Wd, Hd, cam0, 1.0, 7, 0, sp, ws), reps)
+    n_sp = int(sp.count.item())
+    # image + render + depth read, flags/positions written and read, spawned rows written
+    bytes_ = (3 + 3 + 1) * 4 * hw + 16 * hw + n_sp * 240
+    out["spawn_propose"] = {"ms": ms, "bound": "hbm", "achieved": bytes_ / ms / 1e6, "unit": "GB/s",
+                            "frac": bytes_ / ms / 1e6 / peaks["hbm"], "spawned": n_sp}
+    # a10: learned proposal, one training step and one inference on a 1080p frame
+    out.update(measure_mlp(torch, gs, device, peaks, img, Wd, Hd, rng, reps))
     # a9: anchor size test on the 1M set and host offload of the set + Adam moments
     g = W["g"]
     fine = torch.zeros(g.n, dtype=torch.uint8, device=device)
@@ -870,7 +878,7 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="skip the spawn / MLP / anchor measurements")
     ap.add_argument("--cpu-views", type=int, default=6, help="views of the oracle CPU sample")
     ap.add_argument("--oracle-config", type=int, default=None, help=argparse.SUPPRESS)
-    ap.add_argument("--row", choices=["mini_ba", "pose_refine", "guided_matching", "stream", "configs"],
+    ap.add_argument("--row", choices=["mini_ba", "pose_refine", "guided_matching", "stream", "configs", "mlp"],
                     default=None,
                     help="measure only this side row and print its numbers (for profiling)")
     ap.add_argument("--ba-iterations", type=int, default=200)
@@ -910,6 +918,14 @@ def main():
                 r = measure_ba(torch, gs, device, iterations=args.ba_iterations)
             elif args.row == "pose_refine":
                 r = measure_ba_pose(torch, gs, device)
+            elif args.row == "mlp":
+                rng = np.random.default_rng(5)
+                img = torch.tensor(rng.random(3 * WIDTH * HEIGHT).astype(np.float32), device=device)
+                try:
+                    bf16 = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+                except (OSError, KeyError, ValueError):
+                    bf16 = 1900.0  # the pool's earlier GB300 measurement, used when the file is absent
+                r = measure_mlp(torch, gs, device, {"bf16": bf16}, img, WIDTH, HEIGHT, rng)
             elif args.row == "configs":
                 r = measure_configs(torch, gs, synth, device)
             elif args.row == "stream":
