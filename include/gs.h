@@ -87,6 +87,13 @@ typedef struct gs_config {
                                      integral (multi-scale training, Sec. 4.3): opacity times
                                      sqrt(rho), rho = det(Sigma2D) / det(Sigma2D + dilation I)
                                      floored at 1e-6; use dilation 0.1 with it: 0 */
+    int32_t alpha_rect;           /* 1: each tile rect is also bounded by the tiles that the box of
+                                     the ellipse where o exp(-q/2) reaches alpha_min overlaps (x in
+                                     u +- sqrt(2 ln(o / alpha_min) Sigma2D_xx), tiles
+                                     [floor((u - hx)/T), floor((u + hx)/T) + 1), y likewise), and an
+                                     opacity below alpha_min lists the item nowhere: only list
+                                     entries that no pixel composites are dropped; 0: the 3-sigma
+                                     rect alone: 1 */
 } gs_config;
 
 void gs_config_default(gs_config* cfg);

@@ -27,9 +27,16 @@
  * them: FP32 arithmetic on the GPU may legitimately take the other branch.
  *
  * cam[18] = R(9, row-major world->camera), t(3), fx, fy, cx, cy, width, height
- * cfg[17] = tile, sh_degree, near, dilation, alpha_min, alpha_max, t_min,
+ * cfg[18] = tile, sh_degree, near, dilation, alpha_min, alpha_max, t_min,
  *           bg(3), pose_grad_through_sh, margin_geo, margin_alpha, margin_T,
- *           margin_rect_px, margin_depth, mip_filter
+ *           margin_rect_px, margin_depth, mip_filter, alpha_rect
+ * alpha_rect = 1: the tile rect is also bounded by the tiles the box of the
+ * ellipse where o exp(-q/2) reaches alpha_min overlaps: x within u +- hx,
+ * hx = sqrt(2 ln(o / alpha_min) Sigma2D_xx) (y likewise), tiles
+ * [floor((u - hx)/T), floor((u + hx)/T) + 1); the 3-sigma rect and this one
+ * are intersected, and an opacity below alpha_min lists the item nowhere. A
+ * pixel centre where alpha reaches alpha_min lies in the box, so no composited
+ * (pixel, Gaussian) pair is dropped: only list entries no pixel composites.
  * mip_filter = 1: the dilation acts as a 2-D low-pass filter that keeps the
  * splat's integral (the multi-scale filtering of Sec. 4.3): the opacity is
  * multiplied by sqrt(rho), rho = det(Sigma2D) / det(Sigma2D + dil I), with rho
@@ -53,7 +60,7 @@ typedef struct {
 } Cam;
 
 typedef struct {
-    int tile, sh_degree, pose_through_sh, mip;
+    int tile, sh_degree, pose_through_sh, mip, alpha_rect;
     double near_z, dil, a_min, a_max, t_min, bg[3], m_geo, m_alpha, m_T, m_rect, m_depth;
 } Cfg;
 
@@ -74,6 +81,7 @@ static Cfg read_cfg(const double* c) {
     g.pose_through_sh = (int)c[10];
     g.m_geo = c[11]; g.m_alpha = c[12]; g.m_T = c[13]; g.m_rect = c[14]; g.m_depth = c[15];
     g.mip = (int)c[16];
+    g.alpha_rect = (int)c[17];
     return g;
 }
 
@@ -263,27 +271,71 @@ static void project_one(int64_t i, const double* mean_opa, const double* scale, 
     int tx = (k->W + T - 1) / T, ty = (k->H + T - 1) / T;
     double e[4] = {(u - r) / T, (v - r) / T, (u + r + T - 1) / T, (v + r + T - 1) / T};
     double lim[4] = {tx, ty, tx, ty};
+    /* opacity-aware bounds (alpha_rect): edges of the box where alpha reaches alpha_min */
+    double o_eff = st->fmip / (1.0 + exp(-logit));
+    int use_a = g->alpha_rect != 0, a_empty = 0;
+    double ea[4] = {0, 0, 0, 0};
+    if (use_a) {
+        /* bit 64: an opacity within the margin of alpha_min may list the item or not in FP32 */
+        if (fabs(o_eff - g->a_min) < g->m_alpha * g->a_min) a |= 64;
+        if (!(o_eff >= g->a_min)) {
+            a_empty = 1;
+        } else {
+            double ta = 2.0 * log(o_eff / g->a_min);
+            double hx = sqrt(ta * A), hy = sqrt(ta * C);
+            ea[0] = (u - hx) / T; ea[1] = (v - hy) / T; ea[2] = (u + hx) / T + 1.0; ea[3] = (v + hy) / T + 1.0;
+        }
+    }
     /* an edge near a tile boundary inside the grid may round either way in fp32;
      * bits 4, 8, 16, 32 flag edges x0, y0, x1, y1. side (optional) says which
      * way the other rounding goes: bit c set when the edge lies at or above the
      * boundary (floor gives the boundary; the other rounding is one less), bit
      * 4 + c when a radius near an integer may move the edge either way. */
     uint8_t sd = 0;
-    for (int c = 0; c < 4; c++) {
-        double kk = nearbyint(e[c]);
-        if (kk >= 1 && kk <= lim[c] && dist_to_int(e[c]) * T < g->m_rect + r_slack) {
-            a |= (uint8_t)(4 << c);
-            if (e[c] >= kk) sd |= (uint8_t)(1 << c);
-            if (r_slack > 0) sd |= (uint8_t)(16 << c);
-        }
-    }
-    if (side) side[i] = sd;
-    int rc[4];
+    int rc[4], ra[4];
     for (int c = 0; c < 4; c++) {
         double f = floor(e[c]);
         if (f < 0) f = 0;
         if (f > lim[c]) f = lim[c];
         rc[c] = (int)f;
+        double fa = floor(ea[c]);
+        if (fa < 0) fa = 0;
+        if (fa > lim[c]) fa = lim[c];
+        ra[c] = (int)fa;
+    }
+    for (int c = 0; c < 4; c++) {
+        /* the binding edge of the two (the larger lower bound, the smaller upper bound; both when equal) */
+        /* an opacity below alpha_min lists the item nowhere whatever its edges (bit 64 flags it near) */
+        int bind3 = !(use_a && a_empty), binda = 0;
+        if (use_a && !a_empty) {
+            binda = c < 2 ? ra[c] >= rc[c] : ra[c] <= rc[c];
+            bind3 = c < 2 ? rc[c] >= ra[c] : rc[c] <= ra[c];
+        }
+        double kk = nearbyint(e[c]);
+        if (bind3 && kk >= 1 && kk <= lim[c] && dist_to_int(e[c]) * T < g->m_rect + r_slack) {
+            a |= (uint8_t)(4 << c);
+            if (e[c] >= kk) sd |= (uint8_t)(1 << c);
+            if (r_slack > 0) sd |= (uint8_t)(16 << c);
+        } else if (binda) {
+            double ka = nearbyint(ea[c]);
+            if (ka >= 1 && ka <= lim[c] && dist_to_int(ea[c]) * T < g->m_rect) {
+                a |= (uint8_t)(4 << c);
+                if (ea[c] >= ka) sd |= (uint8_t)(1 << c);
+            }
+        }
+    }
+    if (side) side[i] = sd;
+    if (use_a) {
+        if (a_empty) {
+            rc[2] = rc[0];  /* the opacity never reaches alpha_min: listed nowhere */
+        } else {
+            if (ra[0] > rc[0]) rc[0] = ra[0];
+            if (ra[1] > rc[1]) rc[1] = ra[1];
+            if (ra[2] < rc[2]) rc[2] = ra[2];
+            if (ra[3] < rc[3]) rc[3] = ra[3];
+            if (rc[2] < rc[0]) rc[2] = rc[0];
+            if (rc[3] < rc[1]) rc[3] = rc[1];
+        }
     }
     if (amb) amb[i] = a;
     if (!isfinite(u) || !isfinite(v)) return;

@@ -85,12 +85,13 @@ class Config:
     margin_rect_px: float = 2e-3
     margin_depth: float = 1e-6
     mip_filter: int = 0
+    alpha_rect: int = 1
 
     def array(self) -> np.ndarray:
         return np.array([self.tile, self.sh_degree, self.near_z, self.dilation, self.alpha_min,
                          self.alpha_max, self.t_min, *self.bg, self.pose_grad_through_sh,
                          self.margin_geo, self.margin_alpha, self.margin_T, self.margin_rect_px,
-                         self.margin_depth, self.mip_filter], np.float64)
+                         self.margin_depth, self.mip_filter, self.alpha_rect], np.float64)
 
 
 def cam_array(cam: dict) -> np.ndarray:
@@ -354,10 +355,10 @@ def ambiguous_memberships(view: dict, cam, cfg: Config, scene=None):
             out.extend((t, int(i), group) for t in tiles)
             group += 1
 
-    for i in np.nonzero(amb & (1 | 4 | 8 | 16 | 32))[0]:
+    for i in np.nonzero(amb & (1 | 4 | 8 | 16 | 32 | 64))[0]:
         x0, y0, x1, y1 = (int(c) for c in proj["rect"][i])
         a = int(amb[i])
-        if a & 1:
+        if a & (1 | 64):
             if vis[i]:
                 # may vanish: it may leave all of its tiles
                 add([ry * tx + cx for ry in range(y0, y1) for cx in range(x0, x1)], i)
@@ -510,9 +511,13 @@ def _alpha_on(proj, i, xs, ys):
 def ambiguous_tiles(view: dict, cam, cfg: Config, any_alpha: bool = False) -> np.ndarray:
     """Tiles whose list the FP32 path may legitimately build differently.
     Ambiguity bits of or_project: 1 = near plane / determinant (the Gaussian
-    may vanish: its whole rect plus one tile), 4/8/16/32 = rect edge x0/y0/x1/y1
-    near a tile boundary: the tile column (row) just inside or outside that
-    edge may or may not list the Gaussian; a tile of it is flagged only if the
+    may vanish: its whole rect plus one tile), 64 = opacity within the margin
+    of alpha_min (listed or not: only where it reaches alpha_min, i.e. about its
+    centre, can that change the image), 4/8/16/32 = rect edge x0/y0/x1/y1
+    near a tile boundary: the one tile column (row) that edge adds or drops when
+    it rounds the other way (from the side its FP64 value lies on; both columns
+    when the radius itself may round either way) may or may not list the
+    Gaussian; a tile of it is flagged only if the
     Gaussian reaches alpha_min there (a Gaussian below alpha_min everywhere in
     the tile composites to nothing either way), or, with any_alpha, always (its
     presence still shifts the list positions, e.g. n_contrib)."""
@@ -523,30 +528,55 @@ def ambiguous_tiles(view: dict, cam, cfg: Config, any_alpha: bool = False) -> np
     proj = view["proj"]
     amb = proj["amb"]
     thr = cfg.alpha_min * (1 - 10 * cfg.margin_alpha)
-    for i in np.nonzero(amb & (1 | 4 | 8 | 16 | 32))[0]:
+    for i in np.nonzero(amb & (1 | 4 | 8 | 16 | 32 | 64))[0]:
         x0, y0, x1, y1 = (int(c) for c in proj["rect"][i])
         a = int(amb[i])
-        if x1 <= x0 or y1 <= y0 or (a & 1):
+        if x1 <= x0 or y1 <= y0 or (a & (1 | 64)):
             # may vanish or appear: its (possible) rect plus a margin
             u, v = proj["mean2d"][i]
+            blk = np.zeros_like(bad)
             if x1 > x0 and y1 > y0:
-                bad[max(y0 - 1, 0):y1 + 1, max(x0 - 1, 0):x1 + 1] = True
+                blk[max(y0 - 1, 0):y1 + 1, max(x0 - 1, 0):x1 + 1] = True
             elif np.isfinite(u) and np.isfinite(v):
                 cx, cy = int(np.clip(u // T, 0, tx - 1)), int(np.clip(v // T, 0, ty - 1))
-                bad[max(cy - 2, 0):cy + 3, max(cx - 2, 0):cx + 3] = True
+                blk[max(cy - 2, 0):cy + 3, max(cx - 2, 0):cx + 3] = True
+            if any_alpha or (a & 1) or not proj["opacity"][i] > 0:
+                bad |= blk
+            else:
+                # a projected item that only an uncertain edge keeps out of every tile changes the
+                # image only where it reaches alpha_min (the opacity-aware bounds make such items
+                # common: a splat whose alpha_min region is off screen)
+                for ry, cx in zip(*np.nonzero(blk)):
+                    xs = np.arange(cx * T, min(cx * T + T, W), dtype=np.float64)
+                    ys = np.arange(ry * T, min(ry * T + T, H), dtype=np.float64)
+                    if xs.size and ys.size and _alpha_on(proj, i, xs, ys).max() >= thr:
+                        bad[ry, cx] = True
             continue
         u, v = proj["mean2d"][i]
         r_lo, r_hi = max(y0 - 1, 0), min(y1 + 1, ty)
         c_lo, c_hi = max(x0 - 1, 0), min(x1 + 1, tx)
+        # the column (row) an edge toggles follows from the side of the boundary its FP64 value lies
+        # on (edge_side bit c): a lower edge at or above it may round down and add the column before
+        # x0, else round up and drop column x0; an upper edge at or above it may drop column x1 - 1,
+        # else add column x1. A radius near an integer (bit 16 << c) may move the edge either way.
+        sd = int(proj["edge_side"][i])
+
+        def toggled(c, lo, hi):
+            if sd & (16 << c):
+                return [lo - 1, lo] if c < 2 else [hi - 1, hi]
+            if c < 2:
+                return [lo - 1] if sd & (1 << c) else [lo]
+            return [hi - 1] if sd & (1 << c) else [hi]
+
         cols, rows = [], []
         if a & 4:
-            cols += [x0 - 1, x0]
+            cols += toggled(0, x0, x1)
         if a & 16:
-            cols += [x1 - 1, x1]
+            cols += toggled(2, x0, x1)
         if a & 8:
-            rows += [y0 - 1, y0]
+            rows += toggled(1, y0, y1)
         if a & 32:
-            rows += [y1 - 1, y1]
+            rows += toggled(3, y0, y1)
         cand = set()
         for cx in cols:
             if 0 <= cx < tx:

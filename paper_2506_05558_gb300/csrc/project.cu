@@ -101,6 +101,22 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean
             y0 = (int)fminf((float)ty, fmaxf(0.f, floorf((vv - r) / T_)));
             x1 = (int)fminf((float)tx, fmaxf(0.f, floorf((u + r + T_ - 1) / T_)));
             y1 = (int)fminf((float)ty, fmaxf(0.f, floorf((vv + r + T_ - 1) / T_)));
+            if (cfg.alpha_rect) {
+                // only the tiles the box of the ellipse where alpha can reach alpha_min overlaps
+                const float oe = f3 * fmip / (1.f + expf(-mo.w));
+                if (!(oe >= cfg.alpha_min)) {
+                    x1 = x0;  // the opacity never reaches alpha_min: listed nowhere
+                } else {
+                    const float ta = 2.f * logf(oe / cfg.alpha_min);
+                    const float hx = sqrtf(ta * a), hy = sqrtf(ta * cc);
+                    x0 = max(x0, (int)fminf((float)tx, fmaxf(0.f, floorf((u - hx) / T_))));
+                    y0 = max(y0, (int)fminf((float)ty, fmaxf(0.f, floorf((vv - hy) / T_))));
+                    x1 = min(x1, (int)fminf((float)tx, fmaxf(0.f, floorf((u + hx) / T_) + 1.f)));
+                    y1 = min(y1, (int)fminf((float)ty, fmaxf(0.f, floorf((vv + hy) / T_) + 1.f)));
+                    x1 = max(x1, x0);
+                    y1 = max(y1, y0);
+                }
+            }
             keep = (x1 - x0) * (y1 - y0) > 0;
         }
     }
@@ -191,6 +207,7 @@ extern "C" void gs_config_default(gs_config* cfg) {
     cfg->alpha_max = 0.99f;
     cfg->t_min = 1e-4f;
     cfg->mip_filter = 0;
+    cfg->alpha_rect = 1;
     cfg->bg[0] = cfg->bg[1] = cfg->bg[2] = 0.f;
     cfg->pose_grad_through_sh = 0;
     cfg->schedule = 0;

@@ -50,7 +50,8 @@ class gs_config(C.Structure):
     _fields_ = [("tile", C.c_int32), ("sh_degree", C.c_int32), ("near_z", C.c_float), ("dilation", C.c_float),
                 ("alpha_min", C.c_float), ("alpha_max", C.c_float), ("t_min", C.c_float), ("bg", C.c_float * 3),
                 ("pose_grad_through_sh", C.c_int32), ("schedule", C.c_int32), ("accumulate", C.c_int32),
-                ("fwd_batch", C.c_int32), ("bwd_batch", C.c_int32), ("mip_filter", C.c_int32)]
+                ("fwd_batch", C.c_int32), ("bwd_batch", C.c_int32), ("mip_filter", C.c_int32),
+                ("alpha_rect", C.c_int32)]
 
 
 class gs_frame(C.Structure):

@@ -318,7 +318,7 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
         # exact counts and rects away from flagged decisions: bit 1 (near plane,
         # determinant, radius) and bits 4-32 (a rect edge within the margin of a
         # tile boundary, which FP32 may round either way)
-        geo_ok = (proj["amb"] & (1 | 4 | 8 | 16 | 32)) == 0
+        geo_ok = (proj["amb"] & (1 | 4 | 8 | 16 | 32 | 64)) == 0
         assert np.array_equal(nt[geo_ok], proj["n_tiles"][geo_ok]), "n_tiles"
         rect = pg.rect[sl].cpu().numpy().astype(np.int32) & 0xFFFF
         both = geo_ok & vis
@@ -348,7 +348,7 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
         b = O.backward_view(sc, cam, ocfg, view, dLs[v])
         bb = O.adjoint_bounds(sc, view, cam, ocfg, dLs[v])
         b2d = bb["flip"] + lam * bb["fp32"]
-        geo = (proj["amb"] & (1 | 2)) > 0
+        geo = (proj["amb"] & (1 | 2 | 64)) > 0
         excl |= geo
         ok = vis & ~geo
         worst2d = 0.0

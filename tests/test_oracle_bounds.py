@@ -362,15 +362,18 @@ def test_near_plane_item_may_appear_by_its_whole_splat():
     np.testing.assert_allclose(bb["pose_flip"], dpose, rtol=1e-9, atol=1e-12 * dpose.max())
 
 
-def test_edge_sides_and_membership_groups():
+@pytest.mark.parametrize("alpha_rect", [0, 1])
+def test_edge_sides_and_membership_groups(alpha_rect):
     """With a wide rect margin many edges are flagged. The side bit of each
     flagged edge must say on which side of the tile boundary the FP64 edge
     lies (edges recomputed here from the projected conic with numpy's
-    eigvalsh), and the tiles of each membership group must be exactly the
-    tiles whose membership changes when that one edge rounds the other way:
-    catches a side inverted, or a join and a leave swapped."""
+    eigvalsh, and with the opacity-aware bounds on, from the box where alpha
+    reaches alpha_min; the flagged edge is the binding one of the two, the
+    3-sigma edge when both bind), and the tiles of each membership group must
+    be exactly the tiles whose membership changes when that one edge rounds
+    the other way: catches a side inverted, or a join and a leave swapped."""
     sc, cam, rng = _scene(sh_degree=0, seed=29, n=300, size=96)
-    cfg = O.Config(sh_degree=0, **dict(TIGHT, margin_rect_px=3.0))
+    cfg = O.Config(sh_degree=0, alpha_rect=alpha_rect, **dict(TIGHT, margin_rect_px=3.0))
     view, proj = _view(sc, cam, cfg)
     T = cfg.tile
     tx, ty = O.tiles_xy(cam, cfg)
@@ -387,11 +390,22 @@ def test_edge_sides_and_membership_groups():
         assert lam >= np.linalg.eigvalsh(S).max() - 1e-9
         r = np.ceil(3 * np.sqrt(lam))
         u, v = proj["mean2d"][i]
-        e = [(u - r) / T, (v - r) / T, (u + r + T - 1) / T, (v + r + T - 1) / T]
+        e3 = [(u - r) / T, (v - r) / T, (u + r + T - 1) / T, (v + r + T - 1) / T]
+        ta = 2 * np.log(proj["opacity"][i] / cfg.alpha_min)
+        hx, hy = np.sqrt(ta * S[0, 0]), np.sqrt(ta * S[1, 1])
+        ea = [(u - hx) / T, (v - hy) / T, (u + hx) / T + 1, (v + hy) / T + 1]
+        lim = [tx, ty, tx, ty]
         x0, y0, x1, y1 = (int(c) for c in proj["rect"][i])
         for c in range(4):
             if not proj["amb"][i] & (4 << c) or proj["edge_side"][i] & (16 << c):
                 continue
+            f3 = min(max(np.floor(e3[c]), 0), lim[c])
+            fa = min(max(np.floor(ea[c]), 0), lim[c])
+            near = lambda x: 1 <= np.rint(x) <= lim[c] and abs(x - np.rint(x)) * T < cfg.margin_rect_px
+            bind3 = not alpha_rect or (f3 >= fa if c < 2 else f3 <= fa)
+            binda = alpha_rect and (fa >= f3 if c < 2 else fa <= f3)
+            e = e3 if bind3 and near(e3[c]) else ea
+            assert (bind3 and near(e3[c])) or (binda and near(ea[c])), (i, c)
             k = np.rint(e[c])
             assert bool(proj["edge_side"][i] & (1 << c)) == (e[c] >= k), (i, c)
             # the edge rounded the other way

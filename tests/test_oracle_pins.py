@@ -79,22 +79,57 @@ def test_projection_rotation_cancels():
     np.testing.assert_allclose(p2["conic"], p["conic"], rtol=1e-12, atol=1e-14)
 
 
-def test_projection_radius_and_rect():
-    """3-sigma radius from the largest eigenvalue (numpy eigvalsh) and the tile rect."""
+@pytest.mark.parametrize("alpha_rect", [0, 1])
+def test_projection_radius_and_rect(alpha_rect):
+    """3-sigma radius from the largest eigenvalue (numpy eigvalsh) and the tile
+    rect; with the opacity-aware bounds, intersected with the tiles of the box
+    where o exp(-q/2) reaches alpha_min (its half-widths sqrt(2 ln(o / alpha_min)
+    Sigma2D_xx) and likewise in y: the extent of that ellipse)."""
     sc, cam, _ = synth.tiny_scene(n=200)
-    cfg = O.Config(sh_degree=0)
+    cfg = O.Config(sh_degree=0, alpha_rect=alpha_rect)
     p = O.project(sc, cam, cfg)
     T = cfg.tile
+    checked = 0
     for i in np.nonzero(p["n_tiles"])[0][:50]:
         S = sigma2d_from_conic(p["conic"][i])
         lam = np.linalg.eigvalsh(S).max()
         r = math.ceil(3 * math.sqrt(max(lam, 0.5 * np.trace(S) + math.sqrt(0.1))))
         u, v = p["mean2d"][i]
-        x0 = min(max(math.floor((u - r) / T), 0), 4)
-        x1 = min(max(math.floor((u + r + T - 1) / T), 0), 4)
-        y0 = min(max(math.floor((v - r) / T), 0), 4)
-        y1 = min(max(math.floor((v + r + T - 1) / T), 0), 4)
-        assert list(p["rect"][i]) == [x0, y0, x1, y1]
+        cl = lambda f: min(max(f, 0), 4)
+        rect = [cl(math.floor((u - r) / T)), cl(math.floor((v - r) / T)), cl(math.floor((u + r + T - 1) / T)),
+                cl(math.floor((v + r + T - 1) / T))]
+        if alpha_rect:
+            t = 2 * math.log(p["opacity"][i] / cfg.alpha_min)
+            # the ellipse's extent along x: max x of {d : d^T S^-1 d <= t} is sqrt(t S_xx) (Cauchy-Schwarz)
+            hx, hy = math.sqrt(t * S[0, 0]), math.sqrt(t * S[1, 1])
+            box = [cl(math.floor((u - hx) / T)), cl(math.floor((v - hy) / T)), cl(math.floor((u + hx) / T) + 1),
+                   cl(math.floor((v + hy) / T) + 1)]
+            rect = [max(rect[0], box[0]), max(rect[1], box[1]), min(rect[2], box[2]), min(rect[3], box[3])]
+            checked += rect != [cl(math.floor((u - r) / T)), cl(math.floor((v - r) / T)),
+                                cl(math.floor((u + r + T - 1) / T)), cl(math.floor((v + r + T - 1) / T))]
+        assert list(p["rect"][i]) == rect, (i, list(p["rect"][i]), rect)
+    assert not alpha_rect or checked > 0
+
+
+def test_opacity_aware_rect_drops_no_composited_pair():
+    """The opacity-aware tile bounds only drop list entries no pixel composites:
+    the image, the final transmittance and the adjoint equal those of the
+    3-sigma rects (to rounding: the same composited pairs in the same order),
+    with fewer pairs."""
+    sc, cam, rng = synth.tiny_scene(n=1000)
+    w = rng.standard_normal((3, cam["height"], cam["width"]))
+    res = {}
+    for ar in (0, 1):
+        cfg = O.Config(sh_degree=0, alpha_rect=ar)
+        v = O.render_view(sc, cam, cfg)
+        b = O.backward_view(sc, cam, cfg, v, w)
+        res[ar] = (v, b, int(v["proj"]["n_tiles"].sum()))
+    (v0, b0, p0), (v1, b1, p1) = res[0], res[1]
+    assert p1 < 0.95 * p0, (p1, p0)
+    np.testing.assert_allclose(v1["color"], v0["color"], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(v1["t_final"], v0["t_final"], rtol=0, atol=1e-13)
+    for k in ("mean", "logit", "log_scale", "quat", "sh", "pose"):
+        np.testing.assert_allclose(b1[k], b0[k], rtol=1e-12, atol=1e-12 * np.abs(b0[k]).max())
 
 
 def test_near_plane_and_nonfinite_cull():
