@@ -12,13 +12,13 @@
 
 namespace gs {
 
-__global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean_opa, const float4* __restrict__ scale,
-                                                 const float4* __restrict__ quat, const float4* __restrict__ sh,
-                                                 int64_t n, const float* __restrict__ filter3d,
-                                                 const gs_camera* __restrict__ cams, gs_frame f,
-                                                 gs_config cfg, float2* __restrict__ mean2d,
-                                                 float4* __restrict__ conic_opa, float4* __restrict__ rgb_depth,
-                                                 ushort4* __restrict__ rect, int32_t* __restrict__ n_tiles) {
+__global__ void __launch_bounds__(256, 4) k_project(const float4* __restrict__ mean_opa, const float4* __restrict__ scale,
+                                                    const float4* __restrict__ quat, const float4* __restrict__ sh,
+                                                    int64_t n, const float* __restrict__ filter3d,
+                                                    const gs_camera* __restrict__ cams, gs_frame f,
+                                                    gs_config cfg, float2* __restrict__ mean2d,
+                                                    float4* __restrict__ conic_opa, float4* __restrict__ rgb_depth,
+                                                    ushort4* __restrict__ rect, int32_t* __restrict__ n_tiles) {
     __shared__ gs_camera cam_s;
     const int v = (int)(blockIdx.x % (unsigned)f.n_views);
     const int64_t gblock = blockIdx.x / (unsigned)f.n_views;
@@ -96,11 +96,13 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean
             const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - det));
             const float r = ceilf(3.f * sqrtf(lam));
             const int T_ = f.tile;
+            // the tile size is 8, 16 or 32: multiplying by its reciprocal is exactly the division
+            const float iT = 1.f / (float)T_;
             const int tx = f.tiles_x[v], ty = f.tiles_y[v];
-            x0 = (int)fminf((float)tx, fmaxf(0.f, floorf((u - r) / T_)));
-            y0 = (int)fminf((float)ty, fmaxf(0.f, floorf((vv - r) / T_)));
-            x1 = (int)fminf((float)tx, fmaxf(0.f, floorf((u + r + T_ - 1) / T_)));
-            y1 = (int)fminf((float)ty, fmaxf(0.f, floorf((vv + r + T_ - 1) / T_)));
+            x0 = (int)fminf((float)tx, fmaxf(0.f, floorf((u - r) * iT)));
+            y0 = (int)fminf((float)ty, fmaxf(0.f, floorf((vv - r) * iT)));
+            x1 = (int)fminf((float)tx, fmaxf(0.f, floorf((u + r + T_ - 1) * iT)));
+            y1 = (int)fminf((float)ty, fmaxf(0.f, floorf((vv + r + T_ - 1) * iT)));
             if (cfg.alpha_rect) {
                 // only the tiles the box of the ellipse where alpha can reach alpha_min overlaps
                 const float oe = f3 * fmip / (1.f + expf(-mo.w));
@@ -109,10 +111,10 @@ __global__ void __launch_bounds__(256) k_project(const float4* __restrict__ mean
                 } else {
                     const float ta = 2.f * logf(oe / cfg.alpha_min);
                     const float hx = sqrtf(ta * a), hy = sqrtf(ta * cc);
-                    x0 = max(x0, (int)fminf((float)tx, fmaxf(0.f, floorf((u - hx) / T_))));
-                    y0 = max(y0, (int)fminf((float)ty, fmaxf(0.f, floorf((vv - hy) / T_))));
-                    x1 = min(x1, (int)fminf((float)tx, fmaxf(0.f, floorf((u + hx) / T_) + 1.f)));
-                    y1 = min(y1, (int)fminf((float)ty, fmaxf(0.f, floorf((vv + hy) / T_) + 1.f)));
+                    x0 = max(x0, (int)fminf((float)tx, fmaxf(0.f, floorf((u - hx) * iT))));
+                    y0 = max(y0, (int)fminf((float)ty, fmaxf(0.f, floorf((vv - hy) * iT))));
+                    x1 = min(x1, (int)fminf((float)tx, fmaxf(0.f, floorf((u + hx) * iT) + 1.f)));
+                    y1 = min(y1, (int)fminf((float)ty, fmaxf(0.f, floorf((vv + hy) * iT) + 1.f)));
                     x1 = max(x1, x0);
                     y1 = max(y1, y0);
                 }
