@@ -468,6 +468,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_single(Load load, Epi epi
     const int64_t n = valid_count(n_max, n_dev);
     const int64_t cv = min(c1, n);  // end of the valid part of the chunk
     uint32_t sum = 0;
+#pragma unroll 2
     for (int64_t i0 = c0; i0 < cv; i0 += kScanTile) {
         uint32_t part[kScanItems];
 #pragma unroll
@@ -529,7 +530,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_single(Load load, Epi epi
     }
 }
 
-// CTAs of the single-pass scan: two per SM, each with one chunk of whole tiles.
+// CTAs of the single-pass scan: four per SM (each CTA's two walks over its
+// chunk are latency-bound, so shorter chunks finish sooner), each with one
+// chunk of whole tiles.
 static int64_t scan_ctas() {
     static int sms = 0;
     if (sms == 0) {
@@ -538,7 +541,7 @@ static int64_t scan_ctas() {
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
         sms = v > 0 ? v : 152;
     }
-    return 2 * (int64_t)sms;
+    return 4 * (int64_t)sms;
 }
 
 template <class Load, class Epi = NoEpilogue>
