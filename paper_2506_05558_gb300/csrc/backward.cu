@@ -23,8 +23,9 @@ namespace gs {
 constexpr int kPBGauss = 32;     // Gaussians per pose partial (one warp)
 constexpr int kPBThreads = 128;  // threads (Gaussians) per CTA of k_project_bwd
 
-// Record of item i: (du dv dA dB | dC dop dr dg | db 0 0 0), zeros for items
-// without pairs; also the 9 values to d_proj (when given) for items with pairs.
+// Record of item i: (du dv dA dB | dC dop dr dg | db 0 0 0), written only for
+// items with pairs (zeros after a pair-buffer overflow); also the 9 values to
+// d_proj (when given).
 // The runs of a warp's 32 consecutive items form one contiguous slot range:
 // the warp loads it window by window into shared memory with coalesced loads,
 // then each lane adds the slots of its own run in slot order.
@@ -69,7 +70,7 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_item_partials(
         }
         __syncwarp();
     }
-    if (!in) return;
+    if (!in || nt <= 0) return;  // an item without pairs has no record (its reader skips it)
     rec[3 * item] = a0;
     rec[3 * item + 1] = a1;
     rec[3 * item + 2] = make_float4(a2, 0.f, 0.f, 0.f);
@@ -134,8 +135,8 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
 #pragma unroll
     for (int c = 0; c < 3 * NC; c++) ash[c] = 0.f;
     bool vis = false;
-    // the next view's tile count and record are loaded while this view is processed (every item has a
-    // record: zeros without pairs)
+    // the next view's tile count and record are loaded while this view is processed (a record
+    // is used only when its item has pairs: the others were never written)
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
     int nt_nx = valid ? n_tiles[g] : 0;
     float4 r0_nx = valid ? rec[3 * g] : zero4, r1_nx = valid ? rec[3 * g + 1] : zero4;
