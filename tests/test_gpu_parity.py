@@ -256,7 +256,7 @@ def last_contributor_tied(view, w, h, tile):
 
 def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), max_amb_frac=0.3, max_excl_frac=0.05,
                   dLs=None, grad="l1", mip=0, margins=None, lam=FP32_LAMBDA, max_pose_share=POSE_SHARE, filter3d=None,
-                  **launch):
+                  alpha_rect=1, **launch):
     """GPU vs oracle on every view: projection, image, n_contrib, the 2D adjoint
     per item, every visible Gaussian's parameter gradients and the pose
     gradient of each view.
@@ -285,7 +285,7 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
     dil = 0.1 if mip else 0.3
     tile = launch.get("tile", 16)
     ocfg = O.Config(sh_degree=sh_degree, pose_grad_through_sh=pose_through_sh, bg=bg, tile=tile, mip_filter=mip,
-                    dilation=dil, **(margins or MARGINS))
+                    dilation=dil, alpha_rect=alpha_rect, **(margins or MARGINS))
     views = [O.render_view(sc, cam, ocfg) for cam in cams]
     workload = dLs is None and grad == "l1"
     if dLs is None:
@@ -295,7 +295,7 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
             rng = np.random.default_rng(0)
             dLs = [rng.standard_normal((3, c["height"], c["width"])) for c in cams]
     r, dLs, d_proj = run_views(sc_in, cams, sh_degree, dLs=dLs, pose_through_sh=pose_through_sh, bg=bg,
-                               mip_filter=mip, dilation=dil, filter3d=filter3d, **launch)
+                               mip_filter=mip, dilation=dil, filter3d=filter3d, alpha_rect=alpha_rect, **launch)
     n = sc.n
     keys = ("mean", "logit", "log_scale", "quat", "sh")
     ref = {k: 0.0 for k in keys}
@@ -397,6 +397,38 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
     for line in report + shares:
         print("  " + line)
     return r, n_excl
+
+
+def test_three_sigma_rects_end_to_end():
+    """The same three-view SH3 workload with the opacity-aware tile rects off:
+    every Gaussian listed on the whole 3-sigma square of tiles."""
+    sc, cams, _ = synth.multiview_scene(seed=5, n=20000, n_views=3, sizes=[(200, 120), (131, 77), (96, 160)])
+    compare_views(sc, cams, 3, alpha_rect=0)
+
+
+def test_opacity_aware_rects_change_no_output():
+    """The opacity-aware rects drop only list entries whose Gaussian reaches
+    alpha_min at no pixel of the tile: such an entry is skipped by compositing
+    and its partials are exact zeros, so the image, the transmittance and
+    every gradient are bit-identical with and without them (n_contrib, a list
+    position, may move), on fewer pairs; a Gaussian whose opacity lets alpha
+    reach alpha_min nowhere leaves every list, so the visible set can only
+    shrink."""
+    sc, cams, _ = synth.multiview_scene(seed=5, n=20000, n_views=3, sizes=[(200, 120), (131, 77), (96, 160)])
+    rng = np.random.default_rng(9)
+    dLs = [rng.standard_normal((3, c["height"], c["width"])) for c in cams]
+    out = {}
+    for ar in (0, 1):
+        r, _, d_proj = run_views(sc, cams, 3, dLs=dLs, alpha_rect=ar)
+        out[ar] = dict(pairs=int(r.pairs.count.item()), color=r.img.color.cpu().numpy(),
+                       t=r.img.t_final.cpu().numpy(), vis=r.grads.visible.cpu().numpy().astype(bool),
+                       d_proj=d_proj, pose=r.dpose.cpu().numpy(),
+                       **{k: getattr(r.grads, k).cpu().numpy() for k in ("mean_opa", "scale", "quat", "sh")})
+    a, b = out[0], out[1]
+    assert b["pairs"] < a["pairs"], (a["pairs"], b["pairs"])
+    assert not (b["vis"] & ~a["vis"]).any()
+    for k in ("color", "t", "d_proj", "pose", "mean_opa", "scale", "quat", "sh"):
+        assert np.array_equal(a[k], b[k]), k
 
 
 @pytest.mark.parametrize("mip", [0, 1])
