@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                           s_box[j]);
             __syncthreads();
             const int cnt = min((uint32_t)FB, end - b0);
+            const int lbase = (int)(b0 - start) + 1;  // n_contrib of a Gaussian staged at k: lbase + k
             for (int k0 = 0; k0 < cnt; k0 += 32) {
                 if (__all_sync(FULL, done)) break;
                 const int kk = k0 + lane;
@@ -180,7 +181,8 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                     const float og = __fmul_rn(abco.w, fast_exp2(e));
                     const float alpha = fminf(cfg.alpha_max, og);
                     const bool ok = !done && !(e > 0.f) && alpha >= cfg.alpha_min;
-                    const float nT = __fmul_rn(T, 1.f - alpha);
+                    const float aT = __fmul_rn(alpha, T);  // the blending weight
+                    const float nT = __fsub_rn(T, aT);     // T (1 - alpha)
                     const bool term = ok && nT < cfg.t_min;
                     const bool acc = ok && !term;
                     if (COUNT) {
@@ -189,11 +191,11 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                         n_comp += acc;
                     }
                     done = done || term;
-                    const float w = acc ? alpha * T : 0.f;
+                    const float w = acc ? aT : 0.f;
                     cr += w * c.x; cg += w * c.y; cb += w * c.z;
                     if (DEPTH) cz += w * c.w;
                     T = acc ? nT : T;
-                    last = acc ? (int)(b0 - start) + k + 1 : last;
+                    last = acc ? lbase + k : last;
                 };
                 // two hits per round (warp-uniform): both Gaussians' shared
                 // loads are issued before the first composites, in order
