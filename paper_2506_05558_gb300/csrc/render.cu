@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                           s_box[j]);
             __syncthreads();
             const int cnt = min((uint32_t)FB, end - b0);
-            const int lbase = (int)(b0 - start) + 1;  // n_contrib of a Gaussian staged at k: lbase + k
+            int lastk = -1;  // staged index of this batch's last composited Gaussian
             for (int k0 = 0; k0 < cnt; k0 += 32) {
                 if (__all_sync(FULL, done)) break;
                 const int kk = k0 + lane;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                     cr += w * c.x; cg += w * c.y; cb += w * c.z;
                     if (DEPTH) cz += w * c.w;
                     T = acc ? nT : T;
-                    last = acc ? lbase + k : last;
+                    lastk = acc ? k : lastk;
                 };
                 // two hits per round (warp-uniform): both Gaussians' shared
                 // loads are issued before the first composites, in order
@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(TILE * TILE) k_render_fwd(gs_frame f, gs_confi
                     if (two) composite(kb, xyb, abb, cb2);
                 }
             }
+            if (lastk >= 0) last = (int)(b0 - start) + lastk + 1;
         }
         if (ti.inside) {
             color[ti.color_base] = cr + T * cfg.bg[0];
