@@ -11,8 +11,9 @@
 // geometry values and, for SH degree d, the 3 (d + 1)^2 coefficient gradients
 // gc_v[ch] Y_v[k] - so each gradient row is written once, after the last view,
 // without atomics. Each view's pose gradient is summed over the warp's 32
-// Gaussians by a fixed xor tree into one partial per (view, group of 32), and
-// those are summed by k_pose_reduce in a fixed order: the whole backward pass
+// Gaussians by a fixed xor tree and over the CTA's four warps in order into
+// one partial per (view, CTA), and those are summed by k_pose_reduce in a
+// fixed order: the whole backward pass
 // is deterministic. After a pair-buffer overflow (sort status) some slots were
 // never written, and the gradients are zero.
 #include "common.cuh"
@@ -20,8 +21,7 @@
 
 namespace gs {
 
-constexpr int kPBGauss = 32;     // Gaussians per pose partial (one warp)
-constexpr int kPBThreads = 128;  // threads (Gaussians) per CTA of k_project_bwd
+constexpr int kPBThreads = 128;  // threads (Gaussians) per CTA of k_project_bwd, one pose partial per view
 
 // Record of item i: (du dv dA dB | dC dop dr dg | db 0 0 0), written only for
 // items with pairs (zeros after a pair-buffer overflow); also the 9 values to
@@ -91,17 +91,16 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
     uint8_t* __restrict__ visible, float* __restrict__ pose_part) {
     constexpr int NC = (SHD + 1) * (SHD + 1);  // SH coefficients per channel
     constexpr int NR = (3 * NC + 3) / 4;       // float4 rows of SH coefficients in use
+    constexpr int NWP = kPBThreads / 32;
     __shared__ gs_camera s_cam[GS_MAX_VIEWS];
+    __shared__ float s_pose[GS_MAX_VIEWS][NWP][6];  // each warp's pose partial per view
     const unsigned FULL = 0xffffffffu;
     const int nv = f.n_views;
     for (int i = threadIdx.x; i < nv * (int)(sizeof(gs_camera) / 4); i += kPBThreads)
         reinterpret_cast<float*>(s_cam)[i] = reinterpret_cast<const float*>(cams)[i];
     __syncthreads();
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int64_t g = (int64_t)blockIdx.x * kPBThreads + threadIdx.x;
-    const int64_t n_groups = ceil_div(n, kPBGauss);
-    const int64_t group = g / kPBGauss;  // warp-uniform
-    if (group >= n_groups) return;       // whole warps only: the pose reduction needs every lane
     const bool valid = g < n;
     float4 mo = make_float4(0.f, 0.f, 0.f, 0.f), s4 = mo, q4 = make_float4(1.f, 0.f, 0.f, 0.f);
     if (valid) { mo = mean_opa[g]; s4 = scale[g]; q4 = quat[g]; }
@@ -349,8 +348,17 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
             float pv = pose[0];
 #pragma unroll
             for (int c = 1; c < 6; c++) pv = (lane == c) ? pose[c] : pv;
-            pose_part[((int64_t)v * n_groups + group) * 6 + lane] = pv;
+            s_pose[v][wp][lane] = pv;
         }
+    }
+    // one pose partial per (view, CTA): the CTA's warps summed in order
+    __syncthreads();
+    for (int i = threadIdx.x; i < nv * 6; i += kPBThreads) {
+        const int v = i / 6, c = i % 6;
+        float pv = 0.f;
+#pragma unroll
+        for (int q = 0; q < NWP; q++) pv += s_pose[v][q][c];
+        pose_part[((int64_t)v * gridDim.x + blockIdx.x) * 6 + c] = pv;
     }
     if (!valid) return;
     float4 om = make_float4(am[0], am[1], am[2], alogit);
@@ -388,6 +396,7 @@ __global__ void __launch_bounds__(256) k_pose_reduce(const float* __restrict__ p
     __shared__ float s[256][6];
     const int v = blockIdx.x;
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
     for (int64_t b = threadIdx.x; b < nb; b += 256)
 #pragma unroll
         for (int c = 0; c < 6; c++) acc[c] += pose_part[((int64_t)v * nb + b) * 6 + c];
@@ -420,7 +429,7 @@ static BwdWs carve_bwd(char* base, size_t cap, int64_t n, int n_views, int64_t c
     w.part0 = c.take<float4>(capacity);
     w.part1 = c.take<float4>(capacity);
     w.part2 = c.take<float>(capacity);
-    w.pose_part = c.take<float>((size_t)n_views * ceil_div(n, kPBGauss) * 6);
+    w.pose_part = c.take<float>((size_t)n_views * ceil_div(n, kPBThreads) * 6);
     w.counter = c.take<uint32_t>(4);
     w.rec = c.take<float4>((size_t)n_views * n * 3);  // per-item sums of the pair partials
     *used = c.used;
@@ -473,7 +482,7 @@ extern "C" int gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, cons
         GS_CUDA_CHECK_LAUNCH();
         return GS_OK;
     }
-    const int64_t nb = ceil_div(g->n, kPBGauss);  // groups of 32 Gaussians (pose partials per view)
+    const int64_t nb = ceil_div(g->n, kPBThreads);  // CTAs of k_project_bwd (pose partials per view)
     const int64_t n_items = (int64_t)f->n_views * g->n;
     k_item_partials<<<(unsigned)ceil_div(n_items, 32 * kGatherWarps), 32 * kGatherWarps, 0, s>>>(
         n_items, p->n_tiles, pairs->offset, w.part0, w.part1, w.part2, pairs->capacity, pairs->status, w.rec, d_proj);
