@@ -81,7 +81,13 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_item_partials(
     }
 }
 
-template <int SHD>
+// DV > 0 (at most DV views): each view's colour gradient and direction are
+// kept in shared memory and the SH-coefficient sums are formed after the view
+// loop, so their 3 (d + 1)^2 accumulators are not live across it (fewer
+// registers, more resident warps); DV = 0: accumulated view by view.
+constexpr int kPBDeferViews = 8;
+
+template <int SHD, int DV>
 __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
     const float4* __restrict__ mean_opa, const float4* __restrict__ scale, const float4* __restrict__ quat,
     const float4* __restrict__ sh, int64_t n, const float* __restrict__ filter3d, const gs_camera* __restrict__ cams,
@@ -131,8 +137,12 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
     // per-Gaussian sums over the views (in view order)
     float am[3] = {0.f, 0.f, 0.f}, alogit = 0.f, als[3] = {0.f, 0.f, 0.f}, aq[4] = {0.f, 0.f, 0.f, 0.f};
     float ash[3 * NC];
+    if constexpr (DV == 0) {
 #pragma unroll
-    for (int c = 0; c < 3 * NC; c++) ash[c] = 0.f;
+        for (int c = 0; c < 3 * NC; c++) ash[c] = 0.f;
+    }
+    __shared__ float s_gd[DV > 0 ? DV : 1][6][kPBThreads];  // per view: gc[3], direction[3]
+    uint32_t vmask = 0;                                       // views whose entries are set
     bool vis = false;
     // the next view's tile count and record are loaded while this view is processed (a record
     // is used only when its item has pairs: the others were never written)
@@ -180,10 +190,17 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
 #pragma unroll
                 for (int ch = 0; ch < 3; ch++) raw[ch] += Y[kk] * cq[3 * kk + ch];
             const float gc[3] = {raw[0] > 0.f ? dr : 0.f, raw[1] > 0.f ? dg : 0.f, raw[2] > 0.f ? db : 0.f};
+            if constexpr (DV == 0) {
 #pragma unroll
-            for (int kk = 0; kk < NC; kk++)
+                for (int kk = 0; kk < NC; kk++)
 #pragma unroll
-                for (int ch = 0; ch < 3; ch++) ash[3 * kk + ch] += gc[ch] * Y[kk];
+                    for (int ch = 0; ch < 3; ch++) ash[3 * kk + ch] += gc[ch] * Y[kk];
+            } else {
+                const int t = threadIdx.x;
+                s_gd[v][0][t] = gc[0]; s_gd[v][1][t] = gc[1]; s_gd[v][2][t] = gc[2];
+                s_gd[v][3][t] = ddx; s_gd[v][4][t] = ddy; s_gd[v][5][t] = ddz;
+                vmask |= 1u << v;
+            }
             float gmx = 0.f, gmy = 0.f, gmz = 0.f;
             if (SHD > 0) {
                 // direction gradient of sum_k w_k Y_k(d), w_k = sum_ch gc[ch] sh[k][ch]
@@ -361,6 +378,22 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
         pose_part[((int64_t)v * gridDim.x + blockIdx.x) * 6 + c] = pv;
     }
     if (!valid) return;
+    if constexpr (DV > 0) {
+        // the SH-coefficient gradients, summed over the views in order as above
+#pragma unroll
+        for (int c = 0; c < 3 * NC; c++) ash[c] = 0.f;
+        const int t = threadIdx.x;
+        for (int v = 0; v < nv; v++) {
+            if (!((vmask >> v) & 1u)) continue;
+            const float gc[3] = {s_gd[v][0][t], s_gd[v][1][t], s_gd[v][2][t]};
+            float Y[16];
+            sh_eval_basis(SHD, s_gd[v][3][t], s_gd[v][4][t], s_gd[v][5][t], Y);
+#pragma unroll
+            for (int kk = 0; kk < NC; kk++)
+#pragma unroll
+                for (int ch = 0; ch < 3; ch++) ash[3 * kk + ch] += gc[ch] * Y[kk];
+        }
+    }
     float4 om = make_float4(am[0], am[1], am[2], alogit);
     // back from the filtered scales s' to the log-scales (the opacity factor f3 too)
     const float l3 = a3 * f3 * opa;  // dL / d log f3
@@ -489,7 +522,9 @@ extern "C" int gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, cons
     count_launch();
     const unsigned grid = (unsigned)ceil_div(g->n, kPBThreads);
 #define GS_PB(D)                                                                                                \
-    k_project_bwd<D><<<grid, kPBThreads, 0, s>>>((const float4*)g->mean_opa, (const float4*)g->scale,          \
+    if (f->n_views <= kPBDeferViews) { GS_PB2(D, kPBDeferViews); } else { GS_PB2(D, 0); }
+#define GS_PB2(D, DV)                                                                                           \
+    k_project_bwd<D, DV><<<grid, kPBThreads, 0, s>>>((const float4*)g->mean_opa, (const float4*)g->scale,          \
                                                  (const float4*)g->quat, (const float4*)g->sh, g->n,           \
                                                  g->filter3d, cams, *f,                                         \
                                                  *cfg, p->n_tiles, w.rec, (float4*)grads->mean_opa,               \
@@ -502,6 +537,7 @@ extern "C" int gs_project_bwd(const gs_gaussians* g, const gs_camera* cams, cons
         default: GS_PB(3); break;
     }
 #undef GS_PB
+#undef GS_PB2
     count_launch();
     k_pose_reduce<<<f->n_views, 256, 0, s>>>(w.pose_part, nb, dL_dpose);
     count_launch();

@@ -399,6 +399,15 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
     return r, n_excl
 
 
+def test_many_views_end_to_end():
+    """Ten views in one call: above eight views the projection adjoint keeps the
+    SH-coefficient sums in registers view by view instead of forming them after
+    the view loop from shared memory."""
+    sizes = [(64, 48), (72, 40), (48, 64)] * 3 + [(80, 56)]
+    sc, cams, _ = synth.multiview_scene(seed=12, n=4000, n_views=len(sizes), sizes=sizes)
+    compare_views(sc, cams, 3)
+
+
 def test_three_sigma_rects_end_to_end():
     """The same three-view SH3 workload with the opacity-aware tile rects off:
     every Gaussian listed on the whole 3-sigma square of tiles."""
