@@ -7,9 +7,11 @@
 // one thread per Gaussian loads its parameters once and walks the views in
 // order; per visible view it reads the item's record (coalesced across the
 // warp's 32 Gaussians), recomputes the projection, applies the chain rule and
-// adds the result to per-Gaussian accumulators held in registers - 12
-// geometry values and, for SH degree d, the 3 (d + 1)^2 coefficient gradients
-// gc_v[ch] Y_v[k] - so each gradient row is written once, after the last view,
+// adds the result to per-Gaussian accumulators - the mean and opacity terms
+// and H = sum_v R_v^T dL/dT_v, from which the scale and rotation gradients
+// are formed once after the last view, and for SH degree d the 3 (d + 1)^2
+// coefficient gradients gc_v[ch] Y_v[k] (summed after the view loop from
+// shared memory for up to 8 views) - so each gradient row is written once,
 // without atomics. Each view's pose gradient is summed over the warp's 32
 // Gaussians by a fixed xor tree and over the CTA's four warps in order into
 // one partial per (view, CTA), and those are summed by k_pose_reduce in a
@@ -81,14 +83,22 @@ __global__ void __launch_bounds__(32 * kGatherWarps) k_item_partials(
     }
 }
 
+// Rotation matrix (row-major) of the unit quaternion (w, x, y, z).
+__device__ __forceinline__ void quat_rotation(float qw, float qx, float qy, float qz, float (&R)[9]) {
+    R[0] = 1.f - 2.f * (qy * qy + qz * qz); R[1] = 2.f * (qx * qy - qw * qz); R[2] = 2.f * (qx * qz + qw * qy);
+    R[3] = 2.f * (qx * qy + qw * qz); R[4] = 1.f - 2.f * (qx * qx + qz * qz); R[5] = 2.f * (qy * qz - qw * qx);
+    R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
+}
+
 // DV > 0 (at most DV views): each view's colour gradient and direction are
 // kept in shared memory and the SH-coefficient sums are formed after the view
-// loop, so their 3 (d + 1)^2 accumulators are not live across it (fewer
-// registers, more resident warps); DV = 0: accumulated view by view.
+// loop, so their 3 (d + 1)^2 accumulators are not live across it: 128
+// registers (a few bytes spilled), four CTAs per SM; DV = 0: accumulated view
+// by view.
 constexpr int kPBDeferViews = 8;
 
 template <int SHD, int DV>
-__global__ void __launch_bounds__(kPBThreads) k_project_bwd(
+__global__ void __launch_bounds__(kPBThreads, DV > 0 ? 4 : 1) k_project_bwd(
     const float4* __restrict__ mean_opa, const float4* __restrict__ scale, const float4* __restrict__ quat,
     const float4* __restrict__ sh, int64_t n, const float* __restrict__ filter3d, const gs_camera* __restrict__ cams,
     gs_frame f, gs_config cfg,
@@ -110,32 +120,37 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
     const bool valid = g < n;
     float4 mo = make_float4(0.f, 0.f, 0.f, 0.f), s4 = mo, q4 = make_float4(1.f, 0.f, 0.f, 0.f);
     if (valid) { mo = mean_opa[g]; s4 = scale[g]; q4 = quat[g]; }
-    // parameter-space quantities shared by all views
-    const float qi = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
-    const float qw = q4.x * qi, qx = q4.y * qi, qy = q4.z * qi, qz = q4.w * qi;
-    float Rq[9];
-    Rq[0] = 1.f - 2.f * (qy * qy + qz * qz); Rq[1] = 2.f * (qx * qy - qw * qz); Rq[2] = 2.f * (qx * qz + qw * qy);
-    Rq[3] = 2.f * (qx * qy + qw * qz); Rq[4] = 1.f - 2.f * (qx * qx + qz * qz); Rq[5] = 2.f * (qy * qz - qw * qx);
-    Rq[6] = 2.f * (qx * qz - qw * qy); Rq[7] = 2.f * (qy * qz + qw * qx); Rq[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    // parameter-space quantities shared by all views (the rotation and scales are read again
+    // after the view loop, so that they are not held in registers across it)
+    float RS[9];  // Rq diag(s'): the Gaussian's principal axes in world space
+    {
+        const float qi = rsqrtf(q4.x * q4.x + q4.y * q4.y + q4.z * q4.z + q4.w * q4.w);
+        quat_rotation(q4.x * qi, q4.y * qi, q4.z * qi, q4.w * qi, RS);
+    }
     // with the 3-D filter the projection sees scales s' = sqrt(s^2 + v) and the opacity
-    // factor f3 = prod s / s'; d log s' / d log s = s^2 / s'^2, d log f3 / d log s = v / s'^2
+    // factor f3 = prod s / s' (both formed again after the view loop for the log-scale chain)
     float sv[3] = {expf(s4.x), expf(s4.y), expf(s4.z)};
-    float fv = 0.f, f3 = 1.f, dsq[3] = {1.f, 1.f, 1.f};
+    float f3 = 1.f;
     if (filter3d && valid) {
-        fv = filter3d[g];
+        const float fv = filter3d[g];
 #pragma unroll
         for (int k = 0; k < 3; k++) {
-            const float p2 = sv[k] * sv[k] + fv, p = sqrtf(p2);
-            dsq[k] = sv[k] * sv[k] / p2;
+            const float p = sqrtf(sv[k] * sv[k] + fv);
             f3 *= sv[k] / p;
             sv[k] = p;
         }
     }
+#pragma unroll
+    for (int k = 0; k < 9; k++) RS[k] *= sv[k % 3];
     const float opa = 1.f / (1.f + expf(-mo.w));
     float a3 = 0.f;  // sum over views of dL/d(opacity) x the 2-D filter factor
     const float4* shg = sh + 12 * g;
     // per-Gaussian sums over the views (in view order)
-    float am[3] = {0.f, 0.f, 0.f}, alogit = 0.f, als[3] = {0.f, 0.f, 0.f}, aq[4] = {0.f, 0.f, 0.f, 0.f};
+    // and H = sum_v R_v^T dL/dT_v (T_v = R_v Rq diag(s')): the scale and rotation gradients are
+    // linear in H and are formed once, after the view loop
+    float am[3] = {0.f, 0.f, 0.f}, alogit = 0.f, aH[9];
+#pragma unroll
+    for (int k = 0; k < 9; k++) aH[k] = 0.f;
     float ash[3 * NC];
     if constexpr (DV == 0) {
 #pragma unroll
@@ -231,8 +246,7 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
             for (int r = 0; r < 3; r++)
 #pragma unroll
                 for (int kk = 0; kk < 3; kk++)
-                    T[3 * r + kk] =
-                        (c.R[3 * r] * Rq[kk] + c.R[3 * r + 1] * Rq[3 + kk] + c.R[3 * r + 2] * Rq[6 + kk]) * sv[kk];
+                    T[3 * r + kk] = c.R[3 * r] * RS[kk] + c.R[3 * r + 1] * RS[3 + kk] + c.R[3 * r + 2] * RS[6 + kk];
             const float limx = 1.3f * 0.5f * (float)c.width / c.fx;
             const float limy = 1.3f * 0.5f * (float)c.height / c.fy;
             const float iz = 1.f / z;
@@ -290,33 +304,12 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
                 GT[3 + kk] = J11 * GM1[kk];
                 GT[6 + kk] = J02 * GM0[kk] + J12 * GM1[kk];
             }
-            // T = R Rq diag(s): dL/d(Rq diag s) = R^T GT -> log-scale and rotation matrix
-            float gRq[9];
+            // T = R (Rq diag s'): dL/d(Rq diag s') = R^T GT, summed over the views
 #pragma unroll
-            for (int kk = 0; kk < 3; kk++) {
-                float gsk = 0.f;
+            for (int r = 0; r < 3; r++)
 #pragma unroll
-                for (int r = 0; r < 3; r++) {
-                    const float h = c.R[r] * GT[kk] + c.R[3 + r] * GT[3 + kk] + c.R[6 + r] * GT[6 + kk];
-                    gsk += h * Rq[3 * r + kk];
-                    gRq[3 * r + kk] = h * sv[kk];
-                }
-                als[kk] += gsk * sv[kk];
-            }
-            // rotation matrix -> normalised quaternion -> raw quaternion
-            float gq[4];
-            gq[0] = 2.f * (-qz * gRq[1] + qy * gRq[2] + qz * gRq[3] - qx * gRq[5] - qy * gRq[6] + qx * gRq[7]);
-            gq[1] = 2.f * (qy * gRq[1] + qz * gRq[2] + qy * gRq[3] - 2.f * qx * gRq[4] - qw * gRq[5] + qz * gRq[6] +
-                           qw * gRq[7] - 2.f * qx * gRq[8]);
-            gq[2] = 2.f * (-2.f * qy * gRq[0] + qx * gRq[1] + qw * gRq[2] + qx * gRq[3] + qz * gRq[5] - qw * gRq[6] +
-                           qz * gRq[7] - 2.f * qy * gRq[8]);
-            gq[3] = 2.f * (-2.f * qz * gRq[0] - qw * gRq[1] + qx * gRq[2] + qw * gRq[3] - 2.f * qz * gRq[4] +
-                           qy * gRq[5] + qx * gRq[6] + qy * gRq[7]);
-            const float qd = gq[0] * qw + gq[1] * qx + gq[2] * qy + gq[3] * qz;
-            aq[0] += (gq[0] - qw * qd) * qi;
-            aq[1] += (gq[1] - qx * qd) * qi;
-            aq[2] += (gq[2] - qy * qd) * qi;
-            aq[3] += (gq[3] - qz * qd) * qi;
+                for (int kk = 0; kk < 3; kk++)
+                    aH[3 * r + kk] += c.R[r] * GT[kk] + c.R[3 + r] * GT[3 + kk] + c.R[6 + r] * GT[6 + kk];
             // p = (x, y, z): through the 2D mean and J
             float gpx = du * c.fx * iz, gpy = dv * c.fy * iz;
             float gpz = -(du * c.fx * x + dv * c.fy * y) * iz * iz;
@@ -395,11 +388,43 @@ __global__ void __launch_bounds__(kPBThreads) k_project_bwd(
         }
     }
     float4 om = make_float4(am[0], am[1], am[2], alogit);
-    // back from the filtered scales s' to the log-scales (the opacity factor f3 too)
-    const float l3 = a3 * f3 * opa;  // dL / d log f3
-    float4 os = make_float4(als[0] * dsq[0] + l3 * fv / (sv[0] * sv[0]), als[1] * dsq[1] + l3 * fv / (sv[1] * sv[1]),
-                            als[2] * dsq[2] + l3 * fv / (sv[2] * sv[2]), 0.f);
-    float4 oq = make_float4(aq[0], aq[1], aq[2], aq[3]);
+    float4 os = make_float4(0.f, 0.f, 0.f, 0.f), oq = os;  // zeros for a Gaussian no view lists
+    if (vis) {
+        const float4 qe = quat[g], se = scale[g];
+        const float qi = rsqrtf(qe.x * qe.x + qe.y * qe.y + qe.z * qe.z + qe.w * qe.w);
+        const float qw = qe.x * qi, qx = qe.y * qi, qy = qe.z * qi, qz = qe.w * qi;
+        float Rq[9];
+        quat_rotation(qw, qx, qy, qz, Rq);
+        // d/d log s'_k = s'_k sum_r H[r][k] Rq[r][k], then back from the filtered scales s' to the
+        // log-scales (the opacity factor f3 too): d log s' / d log s = s^2 / s'^2, d log f3 / d log s =
+        // v / s'^2
+        const float s0[3] = {expf(se.x), expf(se.y), expf(se.z)};
+        const float fv = filter3d ? filter3d[g] : 0.f;
+        const float l3 = a3 * f3 * opa;  // dL / d log f3
+        float ls[3];
+#pragma unroll
+        for (int kk = 0; kk < 3; kk++) {
+            const float sp = filter3d ? sqrtf(s0[kk] * s0[kk] + fv) : s0[kk];
+            const float dsq = filter3d ? s0[kk] * s0[kk] / (sp * sp) : 1.f;
+            const float gl = (aH[kk] * Rq[kk] + aH[3 + kk] * Rq[3 + kk] + aH[6 + kk] * Rq[6 + kk]) * sp;
+            ls[kk] = gl * dsq + l3 * fv / (sp * sp);
+        }
+        os = make_float4(ls[0], ls[1], ls[2], 0.f);
+        // dL/dRq = H diag(s'), then rotation matrix -> normalised quaternion -> raw quaternion
+        float gRq[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) gRq[k] = aH[k] * (filter3d ? sqrtf(s0[k % 3] * s0[k % 3] + fv) : s0[k % 3]);
+        float gq[4];
+        gq[0] = 2.f * (-qz * gRq[1] + qy * gRq[2] + qz * gRq[3] - qx * gRq[5] - qy * gRq[6] + qx * gRq[7]);
+        gq[1] = 2.f * (qy * gRq[1] + qz * gRq[2] + qy * gRq[3] - 2.f * qx * gRq[4] - qw * gRq[5] + qz * gRq[6] +
+                       qw * gRq[7] - 2.f * qx * gRq[8]);
+        gq[2] = 2.f * (-2.f * qy * gRq[0] + qx * gRq[1] + qw * gRq[2] + qx * gRq[3] + qz * gRq[5] - qw * gRq[6] +
+                       qz * gRq[7] - 2.f * qy * gRq[8]);
+        gq[3] = 2.f * (-2.f * qz * gRq[0] - qw * gRq[1] + qx * gRq[2] + qw * gRq[3] - 2.f * qz * gRq[4] +
+                       qy * gRq[5] + qx * gRq[6] + qy * gRq[7]);
+        const float qd = gq[0] * qw + gq[1] * qx + gq[2] * qy + gq[3] * qz;
+        oq = make_float4((gq[0] - qw * qd) * qi, (gq[1] - qx * qd) * qi, (gq[2] - qy * qd) * qi, (gq[3] - qz * qd) * qi);
+    }
     if (cfg.accumulate) {
         const float4 a = g_mean_opa[g], b = g_scale[g], q = g_quat[g];
         om.x += a.x; om.y += a.y; om.z += a.z; om.w += a.w;
