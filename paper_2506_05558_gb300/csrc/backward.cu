@@ -11,7 +11,7 @@
 // and H = sum_v R_v^T dL/dT_v, from which the scale and rotation gradients
 // are formed once after the last view, and for SH degree d the 3 (d + 1)^2
 // coefficient gradients gc_v[ch] Y_v[k] (summed after the view loop from
-// shared memory for up to 8 views) - so each gradient row is written once,
+// shared memory for up to 16 views) - so each gradient row is written once,
 // without atomics. Each view's pose gradient is summed over the warp's 32
 // Gaussians by a fixed xor tree and over the CTA's four warps in order into
 // one partial per (view, CTA), and those are summed by k_pose_reduce in a
@@ -90,12 +90,12 @@ __device__ __forceinline__ void quat_rotation(float qw, float qx, float qy, floa
     R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
 }
 
-// DV > 0 (at most DV views): each view's colour gradient and direction are
-// kept in shared memory and the SH-coefficient sums are formed after the view
-// loop, so their 3 (d + 1)^2 accumulators are not live across it: 128
-// registers (a few bytes spilled), four CTAs per SM; DV = 0: accumulated view
-// by view.
-constexpr int kPBDeferViews = 8;
+// DV > 0 (at most DV views): each view's colour gradient is kept in shared
+// memory and the SH-coefficient sums are formed after the view loop (the view
+// direction computed again there), so their 3 (d + 1)^2 accumulators are not
+// live across it: 128 registers (a few bytes spilled), four CTAs per SM;
+// DV = 0: accumulated view by view.
+constexpr int kPBDeferViews = 16;
 
 template <int SHD, int DV>
 __global__ void __launch_bounds__(kPBThreads, DV > 0 ? 4 : 1) k_project_bwd(
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kPBThreads, DV > 0 ? 4 : 1) k_project_bwd(
 #pragma unroll
         for (int c = 0; c < 3 * NC; c++) ash[c] = 0.f;
     }
-    __shared__ float s_gd[DV > 0 ? DV : 1][6][kPBThreads];  // per view: gc[3], direction[3]
+    __shared__ float s_gd[DV > 0 ? DV : 1][3][kPBThreads];  // per view: the colour gradient gc[3]
     uint32_t vmask = 0;                                       // views whose entries are set
     bool vis = false;
     // the next view's tile count and record are loaded while this view is processed (a record
@@ -213,7 +213,6 @@ __global__ void __launch_bounds__(kPBThreads, DV > 0 ? 4 : 1) k_project_bwd(
             } else {
                 const int t = threadIdx.x;
                 s_gd[v][0][t] = gc[0]; s_gd[v][1][t] = gc[1]; s_gd[v][2][t] = gc[2];
-                s_gd[v][3][t] = ddx; s_gd[v][4][t] = ddy; s_gd[v][5][t] = ddz;
                 vmask |= 1u << v;
             }
             float gmx = 0.f, gmy = 0.f, gmz = 0.f;
@@ -376,11 +375,20 @@ __global__ void __launch_bounds__(kPBThreads, DV > 0 ? 4 : 1) k_project_bwd(
 #pragma unroll
         for (int c = 0; c < 3 * NC; c++) ash[c] = 0.f;
         const int t = threadIdx.x;
+        const float4 me = mean_opa[g];
         for (int v = 0; v < nv; v++) {
             if (!((vmask >> v) & 1u)) continue;
             const float gc[3] = {s_gd[v][0][t], s_gd[v][1][t], s_gd[v][2][t]};
+            // the view direction exactly as in the view loop
+            const gs_camera& c = s_cam[v];
+            const float ccx = -(c.R[0] * c.t[0] + c.R[3] * c.t[1] + c.R[6] * c.t[2]);
+            const float ccy = -(c.R[1] * c.t[0] + c.R[4] * c.t[1] + c.R[7] * c.t[2]);
+            const float ccz = -(c.R[2] * c.t[0] + c.R[5] * c.t[1] + c.R[8] * c.t[2]);
+            float ddx = me.x - ccx, ddy = me.y - ccy, ddz = me.z - ccz;
+            const float il = rsqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+            ddx *= il; ddy *= il; ddz *= il;
             float Y[16];
-            sh_eval_basis(SHD, s_gd[v][3][t], s_gd[v][4][t], s_gd[v][5][t], Y);
+            sh_eval_basis(SHD, ddx, ddy, ddz, Y);
 #pragma unroll
             for (int kk = 0; kk < NC; kk++)
 #pragma unroll

@@ -399,11 +399,12 @@ def compare_views(sc, cams, sh_degree, pose_through_sh=0, bg=(0.0, 0.0, 0.0), ma
     return r, n_excl
 
 
-def test_many_views_end_to_end():
-    """Ten views in one call: above eight views the projection adjoint keeps the
-    SH-coefficient sums in registers view by view instead of forming them after
-    the view loop from shared memory."""
-    sizes = [(64, 48), (72, 40), (48, 64)] * 3 + [(80, 56)]
+@pytest.mark.parametrize("n_views", [10, 18])
+def test_many_views_end_to_end(n_views):
+    """Many views in one call: up to 16 views the projection adjoint forms the
+    SH-coefficient sums after the view loop from shared memory, above 16 it
+    keeps them in registers view by view."""
+    sizes = ([(64, 48), (72, 40), (48, 64)] * 6)[:n_views - 1] + [(80, 56)]
     sc, cams, _ = synth.multiview_scene(seed=12, n=4000, n_views=len(sizes), sizes=sizes)
     compare_views(sc, cams, 3)
 
